@@ -1,0 +1,180 @@
+/*
+ * teno.h -- C ABI of the GB300 TENO finite-volume library (libteno.so).
+ *
+ * The library computes the semi-discrete finite-volume residual of 2D
+ * hyperbolic conservation laws on unstructured triangular meshes with the
+ * unstructured TENO reconstruction of Ji, Liang & Fu (Sec. 2.1, Eq.
+ * fv_governing_equation_semi_discrete; Sec. 3, Eqs. new_scale_separation,
+ * normalize, cutoff, TENO_reconstruction111/222, TENO_weight), the rotated
+ * Riemann fluxes of Sec. 4, and the SSP-RK3 update of Eq.
+ * fv_time_discretization_01, on one CUDA GPU.
+ *
+ * Conventions
+ *  - Every call returns an int status: TENO_OK (0) or a negative TENO_E*
+ *    code; teno_last_error() returns a message for the last failure.
+ *  - The library owns everything it allocates.  Caller pointers are borrowed
+ *    for the duration of the call only.
+ *  - State arrays are structure-of-arrays [n_var][n_cell] of float64 in the
+ *    caller's cell order ("user order").  n_var = 1 (scalar advection) or 4
+ *    (2D Euler: rho, rho*u, rho*v, E).  Internally cells are renumbered along
+ *    a Hilbert curve; teno_get_permutation() exposes that order.
+ *  - Arguments flagged `on_device` are device pointers on the context's GPU
+ *    when on_device != 0 (stream-ordered on the context's stream, not
+ *    synchronised) and host pointers otherwise (the call synchronises the
+ *    stream before returning).
+ *  - Call order: teno_create -> teno_mesh_load -> teno_precompute_stencils ->
+ *    teno_set_state -> (teno_residual | teno_rk3_step | teno_adjoint_step)*;
+ *    violating it returns TENO_ESTATE.
+ *  - A context is not thread safe; use one context per host thread.
+ */
+#ifndef TENO_H
+#define TENO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct teno_ctx teno_ctx;
+
+enum teno_status {
+  TENO_OK = 0,
+  TENO_EINVAL = -1,   /* bad argument (null pointer, size, option) */
+  TENO_ENOMEM = -2,   /* host or device allocation failed */
+  TENO_ECUDA = -3,    /* a CUDA runtime call failed */
+  TENO_EMESH = -4,    /* degenerate/clockwise cell, non-manifold edge, unmatched boundary face */
+  TENO_ESTENCIL = -5, /* a stencil cannot be filled or its least-squares matrix is rank deficient */
+  TENO_ENONPHYS = -6, /* density or pressure <= 0, or NaN, after a stage */
+  TENO_ETIMEOUT = -7, /* a bounded device-side wait gave up */
+  TENO_ESTATE = -8    /* calls made in the wrong order */
+};
+
+enum teno_flux { TENO_FLUX_UPWIND = 0, TENO_FLUX_HLL = 1, TENO_FLUX_HLLC = 2 };
+enum teno_precision { TENO_FP64 = 0, TENO_FP32_MIXED = 1 };
+
+/* Boundary tags of non-periodic meshes (bface[:,2]). */
+enum teno_bc { TENO_BC_WALL = 1, TENO_BC_INFLOW = 2, TENO_BC_OUTFLOW = 3, TENO_BC_TOP = 4 };
+
+/* Scheme options.  Defaults (teno_default_params) follow the paper:
+ * C_T = 1e-6 (Sec. 3.3), eps = 1e-12 (Eq. new_scale_separation),
+ * CFL 0.4 (Sec. 5), gamma = 1.4. */
+typedef struct teno_params {
+  int32_t order;     /* design order 3..6: polynomial degree r = order-1 on the large stencil */
+  int32_t n_var;     /* 1: scalar advection u_t + a.grad u = 0; 4: 2D Euler */
+  int32_t flux;      /* enum teno_flux; UPWIND only with n_var = 1 */
+  int32_t precision; /* enum teno_precision */
+  int32_t linear;    /* 1: always take the large-stencil polynomial (the paper's "Linear" rows) */
+  int32_t nq;        /* Gauss points per edge; 0 = 2 for order <= 4, 3 otherwise */
+  double ct;         /* cutoff C_T */
+  double eps;        /* epsilon of the scale separation */
+  double gamma;      /* ratio of specific heats */
+  double adv_x, adv_y; /* advection velocity for n_var = 1 */
+  double cfl;        /* CFL number for teno_rk3_step with dt <= 0 */
+} teno_params;
+
+/* Fills *p with the defaults above (order 5, n_var 4, HLL, FP64, cfl 0.4). */
+void teno_default_params(teno_params* p);
+
+/* Create a context on CUDA device `device`, launching on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *ctx receives the
+ * handle, or NULL on failure.  device = -1 creates a host-only context:
+ * teno_mesh_load, teno_precompute_stencils, teno_get_permutation and
+ * teno_get_stencils work without a GPU, every call that needs device work
+ * returns TENO_ESTATE. */
+int teno_create(teno_ctx** ctx, int device, void* cuda_stream);
+
+/* Free every host and device allocation of the context.  NULL is a no-op. */
+int teno_destroy(teno_ctx* ctx);
+
+/* Message of the last failed call on this context ("" if none).  Owned by
+ * the context; valid until the next call on it. */
+const char* teno_last_error(teno_ctx* ctx);
+
+/* Change the stream later calls launch on. */
+int teno_set_stream(teno_ctx* ctx, void* cuda_stream);
+
+/* Load a triangular mesh (Sec. 2.1: elements I_i with faces j).
+ *  xy     host [n_vert][2] vertex coordinates;
+ *  tri    host [n_cell][3] vertex ids, counter-clockwise (the vertex order is
+ *         kept: vertex 0,1,2 map to reference points (0,0),(1,0),(0,1),
+ *         Eq. reconstruction_02);
+ *  bface  host [n_bface][3] (v0, v1, tag) for every boundary edge, or NULL
+ *         when n_bface = 0;
+ *  period host {Lx, Ly} for a doubly periodic mesh whose wrapped vertices
+ *         share ids (coordinates of a cell are unwrapped to lie within half
+ *         a period of its vertex 0), or NULL.
+ * Builds faces, normals and areas and the Hilbert-curve cell order.
+ * Errors: TENO_EINVAL, TENO_EMESH (non-positive area, an edge shared by more
+ * than two cells, a boundary edge without a bface entry). */
+int teno_mesh_load(teno_ctx* ctx, int64_t n_vert, const double* xy, int64_t n_cell,
+                   const int32_t* tri, int64_t n_bface, const int32_t* bface,
+                   const double* period);
+
+/* perm host [n_cell]: perm[i] = user id of internal cell i. */
+int teno_get_permutation(teno_ctx* ctx, int32_t* perm);
+
+/* Stencils and reconstruction matrices (Sec. 3.1 candidate stencils; Eqs.
+ * reconstruction_03..10: A_sl, Householder QR, pseudo-inverse), computed on
+ * the host in FP64 and uploaded in the device layout.  Sizes: m = N_k - 1
+ * unknowns, N_s = 2 N_k large-stencil neighbours, 3 directional stencils of
+ * 12 neighbours.  Errors: TENO_EINVAL, TENO_ESTENCIL, TENO_ENOMEM. */
+int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p);
+
+/* Stencil members in user ids: large host [n_cell][N_s], small host
+ * [n_cell][3][12] (-1 for a directional stencil that could not be filled). */
+int teno_get_stencils(teno_ctx* ctx, int32_t* large, int32_t* small);
+
+/* Sizes: *n_cell, *n_var, *m (unknowns), *n_s (large-stencil size). */
+int teno_get_sizes(teno_ctx* ctx, int64_t* n_cell, int32_t* n_var, int32_t* m, int32_t* n_s);
+
+/* Copy the cell averages U ([n_var][n_cell], user order) in / out. */
+int teno_set_state(teno_ctx* ctx, const double* U, int on_device);
+int teno_get_state(teno_ctx* ctx, double* U, int on_device);
+
+/* Physical time of the current state (used by time-dependent boundary
+ * states). */
+int teno_set_time(teno_ctx* ctx, double t);
+
+/* R = dU/dt of the current state (Eq. fv_governing_equation_semi_discrete),
+ * [n_var][n_cell] user order.  sel (nullable) receives the selection per cell
+ * and variable: 8 = large stencil, otherwise bit k set when directional
+ * stencil k was kept (Eq. TENO_weight). */
+int teno_residual(teno_ctx* ctx, double* R, uint8_t* sel, int on_device);
+
+/* Force the selection ([n_var][n_cell] user order, bytes as above) in every
+ * later residual, step and adjoint; NULL restores the computed selection. */
+int teno_set_selection_override(teno_ctx* ctx, const uint8_t* sel, int on_device);
+
+/* dt = cfl * min_i (4|V_i| / perimeter_i) / (|v_i| + c_i) of the current
+ * state (host result; synchronises). */
+int teno_cfl_dt(teno_ctx* ctx, double* dt);
+
+/* One SSP-RK3 step (Eq. fv_time_discretization_01) of the current state.
+ * dt > 0: fixed step; dt <= 0: the CFL step computed on the device.
+ * dt_used (nullable, host) receives the step; passing it (or a failing
+ * positivity check, see teno_check_state) synchronises the stream. */
+int teno_rk3_step(teno_ctx* ctx, double dt, double* dt_used);
+
+/* n_steps SSP-RK3 steps without host synchronisation. */
+int teno_rk3_steps(teno_ctx* ctx, int32_t n_steps, double dt);
+
+/* TENO_ENONPHYS if any stage since the last check produced rho <= 0,
+ * p <= 0 or NaN (Euler), else TENO_OK; clears the flag; synchronises. */
+int teno_check_state(teno_ctx* ctx);
+
+/* Discrete adjoint (no counterpart in the paper): v = (dR/dU)^T w at the
+ * current state with the stencil selection and flux branches frozen at the
+ * forward pass; w, v [n_var][n_cell] user order. */
+int teno_residual_vjp(teno_ctx* ctx, const double* w, double* v, int on_device);
+
+/* Adjoint of one SSP-RK3 step from the current state U^n with step dt:
+ * lam_n = (dU^{n+1}/dU^n)^T lam_np1, stages replayed on the device with the
+ * forward selection frozen.  The state is not changed. */
+int teno_adjoint_step(teno_ctx* ctx, double dt, const double* lam_np1, double* lam_n,
+                      int on_device);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TENO_H */

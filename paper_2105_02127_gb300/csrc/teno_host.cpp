@@ -1,0 +1,1306 @@
+// teno_host.cpp -- host runtime of libteno: context, mesh topology, Hilbert
+// renumbering, stencil construction and least-squares precompute (FP64), the
+// device layouts, and the C ABI declared in include/teno.h.
+//
+// Precompute (once per mesh and order), following the paper:
+//   Sec. 2.2, Eq. reconstruction_02: affine map of every target triangle onto
+//     the reference triangle, vertex k of the cell -> (0,0), (1,0), (0,1);
+//   Sec. 3.1: one large stencil of N_s = 2 N_k neighbours and three
+//     directional stencils of 12 neighbours (sectors through the faces);
+//   Eqs. reconstruction_05..08: A_sl = int_{V'_s} psi_l with exact monomial
+//     moments of triangles;
+//   Eqs. reconstruction_09/10: pseudo-inverse from a Householder QR,
+//     Ahat = R^-1 Q_1^T;
+//   Eq. WENO_smoothness: the beta quadratic form B over the reference triangle
+//     (exact moments), B = L L^T; the device matrices are L^T Ahat diag|V'_s|,
+//     so a kernel obtains a' = L^T a and beta = |a'|^2, and evaluates the
+//     polynomial with Psi L^{-T}.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "teno_internal.h"
+
+using namespace teno;
+
+// ========================================================================
+// context
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct teno_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // mesh (user order unless stated)
+  bool mesh_ok = false, pre_ok = false, state_ok = false;
+  int64_t nv = 0, nc = 0, npad = 0, nface = 0;
+  bool periodic = false;
+  double L[2] = {0, 0};
+  std::vector<int32_t> tri;
+  std::vector<double> P;     // [nc][3][2] unwrapped vertices
+  std::vector<double> cen;   // [nc][2]
+  std::vector<double> area, perim;
+  std::vector<int32_t> fnbr, fedge, fbc;  // [nc][3] neighbour across edge e (user), its edge, bc tag
+  std::vector<int32_t> v2c_off, v2c;      // vertex -> cells (user)
+  std::vector<int32_t> perm, iperm;       // perm[internal] = user, iperm[user] = internal
+  bool has_time_bc = false;
+  // scheme
+  teno_params prm{};
+  int m = 0, ns = 0, nq = 0, E = 0, SL = 0;
+  std::vector<int32_t> st_large, st_small;  // user ids, [nc][ns], [nc][36]
+  // device data
+  DeviceMesh dm;
+  DevBuf b_ahat, b_nbr, b_smask, b_fcells, b_fedges, b_fgeom, b_cfaces, b_inv_area, b_cfl_len,
+      b_perm;
+  DevBuf b_U, b_U1, b_U2, b_R, b_tmp, b_Uq, b_K, b_sel, b_sel_ovr, b_maxlam, b_flag;
+  bool override_on = false;
+  // adjoint
+  DevBuf b_rev_off, b_rev_idx, b_dbar, b_uself, b_Uqbar, b_l1, b_l2, b_lamn, b_vtmp, b_selA;
+  bool adj_ok = false;
+  std::vector<int64_t> rev_off_h, rev_idx_h;
+  double time = 0.0;
+};
+
+namespace {
+
+int fail(teno_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(teno_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, TENO_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr, where)                               \
+  do {                                                \
+    cudaError_t e_ = (expr);                          \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+int dev_alloc(teno_ctx* ctx, DevBuf& b, size_t bytes) {
+  if (ctx->device < 0) return TENO_OK;  // host-only context
+  if (b.p && b.bytes >= bytes) return TENO_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    cudaGetLastError();
+    return fail(ctx, TENO_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                      cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  return TENO_OK;
+}
+
+void dev_free(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+int upload(teno_ctx* ctx, DevBuf& b, const void* src, size_t bytes) {
+  if (ctx->device < 0) return TENO_OK;  // host-only context
+  int rc = dev_alloc(ctx, b, bytes);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, ctx->stream), "upload");
+  CK(cudaStreamSynchronize(ctx->stream), "upload sync");
+  return TENO_OK;
+}
+
+// ========================================================================
+// mesh topology
+
+// standard rotate/flip Hilbert mapping on an n x n grid, n = 2^16
+uint64_t hilbert_index(uint32_t x, uint32_t y) {
+  const uint32_t n = 1u << 16;
+  uint64_t d = 0;
+  for (uint32_t s = n / 2; s > 0; s /= 2) {
+    uint32_t rx = (x & s) > 0;
+    uint32_t ry = (y & s) > 0;
+    d += (uint64_t)s * (uint64_t)s * ((3 * rx) ^ ry);
+    if (ry == 0) {
+      if (rx == 1) {
+        x = n - 1 - x;
+        y = n - 1 - y;
+      }
+      uint32_t t = x;
+      x = y;
+      y = t;
+    }
+  }
+  return d;
+}
+
+struct EdgeRec {
+  int64_t key;
+  int32_t cell, edge;
+};
+
+int build_mesh(teno_ctx* ctx, const double* xy, const int32_t* tri, int64_t nbf,
+               const int32_t* bface) {
+  const int64_t nc = ctx->nc, nv = ctx->nv;
+  ctx->tri.assign(tri, tri + 3 * nc);
+  ctx->P.resize(6 * nc);
+  ctx->cen.resize(2 * nc);
+  ctx->area.resize(nc);
+  ctx->perim.resize(nc);
+  for (int64_t c = 0; c < nc; ++c) {
+    double* P = &ctx->P[6 * c];
+    for (int k = 0; k < 3; ++k) {
+      int32_t v = tri[3 * c + k];
+      if (v < 0 || v >= nv) return fail(ctx, TENO_EMESH, "vertex id out of range");
+      P[2 * k] = xy[2 * v];
+      P[2 * k + 1] = xy[2 * v + 1];
+    }
+    if (ctx->periodic) {
+      for (int k = 1; k < 3; ++k)
+        for (int a = 0; a < 2; ++a)
+          P[2 * k + a] -= ctx->L[a] * std::round((P[2 * k + a] - P[a]) / ctx->L[a]);
+    }
+    ctx->cen[2 * c] = ((P[0] + P[2]) + P[4]) / 3.0;
+    ctx->cen[2 * c + 1] = ((P[1] + P[3]) + P[5]) / 3.0;
+    double a2 = (P[2] - P[0]) * (P[5] - P[1]) - (P[4] - P[0]) * (P[3] - P[1]);
+    if (!(a2 > 0.0))
+      return fail(ctx, TENO_EMESH, "cell " + std::to_string(c) + " has non-positive area");
+    ctx->area[c] = 0.5 * a2;
+    double pe = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      int k1 = (k + 1) % 3;
+      pe += std::hypot(P[2 * k1] - P[2 * k], P[2 * k1 + 1] - P[2 * k + 1]);
+    }
+    ctx->perim[c] = pe;
+  }
+  // vertex -> cells
+  ctx->v2c_off.assign(nv + 1, 0);
+  for (int64_t i = 0; i < 3 * nc; ++i) ctx->v2c_off[tri[i] + 1]++;
+  for (int64_t v = 0; v < nv; ++v) ctx->v2c_off[v + 1] += ctx->v2c_off[v];
+  ctx->v2c.resize(3 * nc);
+  {
+    std::vector<int32_t> pos(ctx->v2c_off.begin(), ctx->v2c_off.end() - 1);
+    for (int64_t c = 0; c < nc; ++c)
+      for (int k = 0; k < 3; ++k) ctx->v2c[pos[tri[3 * c + k]]++] = (int32_t)c;
+  }
+  // edges: match the two cells of every interior edge
+  std::vector<EdgeRec> ed(3 * nc);
+  for (int64_t c = 0; c < nc; ++c)
+    for (int e = 0; e < 3; ++e) {
+      int64_t a = tri[3 * c + e], b = tri[3 * c + (e + 1) % 3];
+      ed[3 * c + e] = {std::min(a, b) * nv + std::max(a, b), (int32_t)c, e};
+    }
+  std::sort(ed.begin(), ed.end(), [](const EdgeRec& x, const EdgeRec& y) {
+    return x.key != y.key ? x.key < y.key : (x.cell != y.cell ? x.cell < y.cell : x.edge < y.edge);
+  });
+  std::vector<std::pair<int64_t, int32_t>> bkeys;
+  for (int64_t b = 0; b < nbf; ++b) {
+    int64_t a0 = bface[3 * b], a1 = bface[3 * b + 1];
+    bkeys.push_back({std::min(a0, a1) * nv + std::max(a0, a1), bface[3 * b + 2]});
+  }
+  std::sort(bkeys.begin(), bkeys.end());
+  ctx->fnbr.assign(3 * nc, -1);
+  ctx->fedge.assign(3 * nc, -1);
+  ctx->fbc.assign(3 * nc, 0);
+  for (size_t i = 0; i < ed.size();) {
+    size_t j = i;
+    while (j < ed.size() && ed[j].key == ed[i].key) ++j;
+    if (j - i == 2) {
+      const EdgeRec &x = ed[i], &y = ed[i + 1];
+      ctx->fnbr[3 * x.cell + x.edge] = y.cell;
+      ctx->fedge[3 * x.cell + x.edge] = y.edge;
+      ctx->fnbr[3 * y.cell + y.edge] = x.cell;
+      ctx->fedge[3 * y.cell + y.edge] = x.edge;
+    } else if (j - i == 1) {
+      auto it = std::lower_bound(bkeys.begin(), bkeys.end(), std::make_pair(ed[i].key, INT32_MIN));
+      if (it == bkeys.end() || it->first != ed[i].key)
+        return fail(ctx, TENO_EMESH, "boundary edge without a bface entry");
+      ctx->fbc[3 * ed[i].cell + ed[i].edge] = it->second;
+      if (it->second == TENO_BC_TOP) ctx->has_time_bc = true;
+    } else {
+      return fail(ctx, TENO_EMESH, "edge shared by more than two cells");
+    }
+    i = j;
+  }
+  // Hilbert order of centroids
+  double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
+  for (int64_t c = 0; c < nc; ++c)
+    for (int a = 0; a < 2; ++a) {
+      lo[a] = std::min(lo[a], ctx->cen[2 * c + a]);
+      hi[a] = std::max(hi[a], ctx->cen[2 * c + a]);
+    }
+  double span = std::max(hi[0] - lo[0], hi[1] - lo[1]);
+  if (!(span > 0)) span = 1.0;
+  std::vector<uint64_t> key(nc);
+  for (int64_t c = 0; c < nc; ++c) {
+    double fx = (ctx->cen[2 * c] - lo[0]) / span, fy = (ctx->cen[2 * c + 1] - lo[1]) / span;
+    uint32_t ix = (uint32_t)std::min(65535.0, std::max(0.0, fx * 65535.0));
+    uint32_t iy = (uint32_t)std::min(65535.0, std::max(0.0, fy * 65535.0));
+    key[c] = hilbert_index(ix, iy);
+  }
+  ctx->perm.resize(nc);
+  for (int64_t c = 0; c < nc; ++c) ctx->perm[c] = (int32_t)c;
+  std::stable_sort(ctx->perm.begin(), ctx->perm.end(),
+                   [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+  ctx->iperm.resize(nc);
+  for (int64_t i = 0; i < nc; ++i) ctx->iperm[ctx->perm[i]] = (int32_t)i;
+  return TENO_OK;
+}
+
+// ========================================================================
+// reference-triangle data
+
+struct RefData {
+  int m = 0, r = 0, nq = 0;
+  int ex[kMaxM][2];
+  double mean0[kMaxM];
+  double B[kMaxM * kMaxM];
+  double Lc[kMaxM * kMaxM];    // Cholesky factor, B = Lc Lc^T (lower)
+  double Linv[kMaxM * kMaxM];  // Lc^{-1}
+  double gt[kMaxNq], gw[kMaxNq];
+  double psi_t[kMaxPts * kMaxM];  // Psi L^{-T}
+};
+
+struct FactTable {
+  double f[24];
+  FactTable() {
+    f[0] = 1.0;
+    for (int i = 1; i < 24; ++i) f[i] = f[i - 1] * i;
+  }
+};
+const FactTable kFact;
+
+inline double fact(int n) { return kFact.f[n]; }
+
+// int over the reference triangle of xi^a eta^b = a! b! / (a+b+2)!
+double ref_moment(int a, int b) { return fact(a) * fact(b) / fact(a + b + 2); }
+
+double falling(int a, int i) {
+  if (i > a) return 0.0;
+  double c = 1.0;
+  for (int k = 0; k < i; ++k) c *= (a - k);
+  return c;
+}
+
+int make_ref(int order, int nq, RefData& R) {
+  R.r = order - 1;
+  R.nq = nq;
+  int n = 0;
+  for (int d = 1; d <= R.r; ++d) {  // degree by degree: xi^d, eta^d, xi^(d-1) eta, ...
+    R.ex[n][0] = d; R.ex[n][1] = 0; ++n;
+    R.ex[n][0] = 0; R.ex[n][1] = d; ++n;
+    for (int j = 1; j < d; ++j) { R.ex[n][0] = d - j; R.ex[n][1] = j; ++n; }
+  }
+  R.m = n;
+  const int m = n;
+  for (int l = 0; l < m; ++l) R.mean0[l] = 2.0 * ref_moment(R.ex[l][0], R.ex[l][1]);
+  for (int l = 0; l < m; ++l)
+    for (int k = 0; k < m; ++k) {
+      double s = 0.0;
+      for (int q = 1; q <= R.r; ++q)
+        for (int i = 0; i <= q; ++i) {
+          int j = q - i;
+          double cl = falling(R.ex[l][0], i) * falling(R.ex[l][1], j);
+          double ck = falling(R.ex[k][0], i) * falling(R.ex[k][1], j);
+          if (cl == 0.0 || ck == 0.0) continue;
+          s += cl * ck *
+               ref_moment(R.ex[l][0] + R.ex[k][0] - 2 * i, R.ex[l][1] + R.ex[k][1] - 2 * j);
+        }
+      R.B[l * m + k] = s;
+    }
+  // Cholesky B = Lc Lc^T
+  for (int i = 0; i < m * m; ++i) R.Lc[i] = 0.0;
+  for (int j = 0; j < m; ++j) {
+    double d = R.B[j * m + j];
+    for (int k = 0; k < j; ++k) d -= R.Lc[j * m + k] * R.Lc[j * m + k];
+    if (!(d > 0.0)) return TENO_EINVAL;
+    R.Lc[j * m + j] = std::sqrt(d);
+    for (int i = j + 1; i < m; ++i) {
+      double s = R.B[i * m + j];
+      for (int k = 0; k < j; ++k) s -= R.Lc[i * m + k] * R.Lc[j * m + k];
+      R.Lc[i * m + j] = s / R.Lc[j * m + j];
+    }
+  }
+  // Linv = Lc^{-1} (lower triangular)
+  for (int i = 0; i < m * m; ++i) R.Linv[i] = 0.0;
+  for (int col = 0; col < m; ++col)
+    for (int i = col; i < m; ++i) {
+      double s = (i == col) ? 1.0 : 0.0;
+      for (int k = col; k < i; ++k) s -= R.Lc[i * m + k] * R.Linv[k * m + col];
+      R.Linv[i * m + col] = s / R.Lc[i * m + i];
+    }
+  // Gauss-Legendre nodes (closed forms) mapped to [0,1], weights summing to 1
+  double x[4], w[4];
+  if (nq == 1) {
+    x[0] = 0.0; w[0] = 2.0;
+  } else if (nq == 2) {
+    x[0] = -1.0 / std::sqrt(3.0); x[1] = -x[0]; w[0] = w[1] = 1.0;
+  } else if (nq == 3) {
+    x[0] = -std::sqrt(0.6); x[1] = 0.0; x[2] = std::sqrt(0.6);
+    w[0] = w[2] = 5.0 / 9.0; w[1] = 8.0 / 9.0;
+  } else if (nq == 4) {
+    double a = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(1.2));
+    double b = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(1.2));
+    x[0] = -b; x[1] = -a; x[2] = a; x[3] = b;
+    w[1] = w[2] = (18.0 + std::sqrt(30.0)) / 36.0;
+    w[0] = w[3] = (18.0 - std::sqrt(30.0)) / 36.0;
+  } else {
+    return TENO_EINVAL;
+  }
+  for (int k = 0; k < nq; ++k) {
+    R.gt[k] = 0.5 * (x[k] + 1.0);
+    R.gw[k] = 0.5 * w[k];
+  }
+  // Psi' = Psi L^{-T} at the 3*nq reference edge points, row p = edge*nq + q:
+  // edge 0: (t, 0); edge 1: (1-t, t); edge 2: (0, 1-t)
+  for (int i = 0; i < kMaxPts * kMaxM; ++i) R.psi_t[i] = 0.0;
+  for (int e = 0; e < 3; ++e)
+    for (int q = 0; q < nq; ++q) {
+      double t = R.gt[q];
+      double xi = e == 0 ? t : (e == 1 ? 1.0 - t : 0.0);
+      double eta = e == 0 ? 0.0 : (e == 1 ? t : 1.0 - t);
+      double psi[kMaxM];
+      for (int l = 0; l < m; ++l)
+        psi[l] = std::pow(xi, R.ex[l][0]) * std::pow(eta, R.ex[l][1]) - R.mean0[l];
+      for (int l = 0; l < m; ++l) {
+        double s = 0.0;
+        for (int j = 0; j <= l; ++j) s += psi[j] * R.Linv[l * m + j];
+        R.psi_t[(e * nq + q) * kMaxM + l] = s;
+      }
+    }
+  return TENO_OK;
+}
+
+// ========================================================================
+// stencils (user ids)
+
+struct Searcher {
+  const teno_ctx* ctx;
+  std::vector<int32_t> mark;
+  int32_t stamp = 0;
+  std::vector<int32_t> cells;   // cells[0] = target, then layer by layer
+  std::vector<int> layer_begin; // layer k = [layer_begin[k], layer_begin[k+1])
+  bool done = false;
+
+  explicit Searcher(const teno_ctx* c) : ctx(c), mark(c->nc, 0) {}
+
+  void reset(int32_t t) {
+    ++stamp;
+    cells.clear();
+    layer_begin.clear();
+    cells.push_back(t);
+    mark[t] = stamp;
+    layer_begin.push_back(0);
+    layer_begin.push_back(1);
+    done = false;
+  }
+  int layers() const { return (int)layer_begin.size() - 2; }
+  bool grow() {  // adds one vertex-neighbour layer (at most 16)
+    if (done || layers() >= 16) return false;
+    int b = layer_begin[layers()], e = layer_begin[layers() + 1];
+    for (int i = b; i < e; ++i) {
+      int32_t c = cells[i];
+      for (int k = 0; k < 3; ++k) {
+        int32_t v = ctx->tri[3 * c + k];
+        for (int32_t p = ctx->v2c_off[v]; p < ctx->v2c_off[v + 1]; ++p) {
+          int32_t x = ctx->v2c[p];
+          if (mark[x] != stamp && cells.size() < 4096) {
+            mark[x] = stamp;
+            cells.push_back(x);
+          }
+        }
+      }
+    }
+    if ((int)cells.size() == e) {
+      done = true;
+      return false;
+    }
+    layer_begin.push_back((int)cells.size());
+    return true;
+  }
+  // centroid offset c_s - c_t, reduced to the nearest periodic image
+  void offset(int32_t t, int32_t s, double* d) const {
+    d[0] = ctx->cen[2 * s] - ctx->cen[2 * t];
+    d[1] = ctx->cen[2 * s + 1] - ctx->cen[2 * t + 1];
+    if (ctx->periodic)
+      for (int a = 0; a < 2; ++a) d[a] -= ctx->L[a] * std::round(d[a] / ctx->L[a]);
+  }
+  double dist2(int32_t t, int32_t s) const {
+    double d[2];
+    offset(t, s, d);
+    double x2 = d[0] * d[0];
+    double y2 = d[1] * d[1];
+    return x2 + y2;
+  }
+};
+
+// returns TENO_OK; small[j*12..] = -1 when sector j cannot be filled
+int find_stencils(Searcher& S, int32_t t, int ns, int32_t* large, int32_t* small) {
+  S.reset(t);
+  auto nearer = [&](int32_t a, int32_t b) {
+    double da = S.dist2(t, a), db = S.dist2(t, b);
+    return da != db ? da < db : a < b;
+  };
+  // large stencil: whole layers while the count stays <= N_s, then nearest
+  int cnt = 0;
+  bool ok = false;
+  for (int k = 1; !ok; ++k) {
+    if (k > S.layers() && !S.grow()) break;
+    int b = S.layer_begin[k], e = S.layer_begin[k + 1];
+    if (cnt + (e - b) <= ns) {
+      for (int i = b; i < e; ++i) large[cnt++] = S.cells[i];
+      ok = cnt == ns;
+    } else {
+      std::vector<int32_t> lay(S.cells.begin() + b, S.cells.begin() + e);
+      std::sort(lay.begin(), lay.end(), nearer);
+      for (int i = 0; cnt < ns; ++i) large[cnt++] = lay[i];
+      ok = true;
+    }
+  }
+  if (!ok) return TENO_ESTENCIL;
+  // directional stencils: centroids in the sector from the target centroid
+  // through edge j, layers added until 12 are admitted, nearest 12 kept
+  const double* P = &S.ctx->P[6 * t];
+  const double cx = S.ctx->cen[2 * t], cy = S.ctx->cen[2 * t + 1];
+  for (int j = 0; j < kSmallK; ++j) {
+    const int j1 = (j + 1) % 3;
+    const double ea[2] = {P[2 * j] - cx, P[2 * j + 1] - cy};
+    const double eb[2] = {P[2 * j1] - cx, P[2 * j1 + 1] - cy};
+    const double D = ea[0] * eb[1] - ea[1] * eb[0];
+    std::vector<int32_t> adm;
+    bool filled = false;
+    for (int k = 1; !filled; ++k) {
+      if (k > S.layers() && !S.grow()) break;
+      for (int i = S.layer_begin[k]; i < S.layer_begin[k + 1]; ++i) {
+        double d[2];
+        S.offset(t, S.cells[i], d);
+        double al = (d[0] * eb[1] - d[1] * eb[0]) / D;
+        double be = (ea[0] * d[1] - ea[1] * d[0]) / D;
+        if (al >= -1e-10 && be >= -1e-10) adm.push_back(S.cells[i]);
+      }
+      filled = adm.size() >= (size_t)kSmallN;
+    }
+    if (!filled) {
+      for (int i = 0; i < kSmallN; ++i) small[j * kSmallN + i] = -1;
+      continue;
+    }
+    std::sort(adm.begin(), adm.end(), nearer);
+    for (int i = 0; i < kSmallN; ++i) small[j * kSmallN + i] = adm[i];
+  }
+  return TENO_OK;
+}
+
+// ========================================================================
+// per-cell least squares
+
+// exact integral of xi^a eta^b over a triangle with vertices q (reference
+// coordinates): expand the monomial in barycentric coordinates and use
+// int lambda0^e0 lambda1^e1 lambda2^e2 = 2|T| e0! e1! e2! / (e0+e1+e2+2)!
+double tri_moment(const double q[3][2], int a, int b, double two_area) {
+  double px[3][8], py[3][8];
+  for (int k = 0; k < 3; ++k) {
+    px[k][0] = py[k][0] = 1.0;
+    for (int i = 1; i < 8; ++i) {
+      px[k][i] = px[k][i - 1] * q[k][0];
+      py[k][i] = py[k][i - 1] * q[k][1];
+    }
+  }
+  double s = 0.0;
+  for (int i0 = 0; i0 <= a; ++i0)
+    for (int i1 = 0; i1 <= a - i0; ++i1) {
+      int i2 = a - i0 - i1;
+      for (int j0 = 0; j0 <= b; ++j0)
+        for (int j1 = 0; j1 <= b - j0; ++j1) {
+          int j2 = b - j0 - j1;
+          double c = fact(i0 + j0) / (fact(i0) * fact(j0)) * fact(i1 + j1) / (fact(i1) * fact(j1)) *
+                     fact(i2 + j2) / (fact(i2) * fact(j2));
+          s += c * px[0][i0] * py[0][j0] * px[1][i1] * py[1][j1] * px[2][i2] * py[2][j2];
+        }
+    }
+  return two_area * fact(a) * fact(b) / fact(a + b + 2) * s;
+}
+
+// device matrix G = Lc_m^T Ahat diag(vol) (m x n) of one stencil
+int stencil_matrix(const teno_ctx* ctx, const RefData& R, int32_t t, const int32_t* ids, int n,
+                   int m, double* G) {
+  const double* P = &ctx->P[6 * t];
+  const double a = P[2] - P[0], b = P[4] - P[0], c = P[3] - P[1], d = P[5] - P[1];
+  const double det = a * d - b * c;
+  const double Ji[4] = {d / det, -b / det, -c / det, a / det};
+  double A[kMaxNs * kMaxM], vol[kMaxNs];
+  for (int s = 0; s < n; ++s) {
+    const int32_t sc = ids[s];
+    // image shift that brings cell s next to the target
+    double off[2];
+    off[0] = ctx->cen[2 * sc] - ctx->cen[2 * t];
+    off[1] = ctx->cen[2 * sc + 1] - ctx->cen[2 * t + 1];
+    double sh[2] = {0.0, 0.0};
+    if (ctx->periodic)
+      for (int k = 0; k < 2; ++k) sh[k] = -ctx->L[k] * std::round(off[k] / ctx->L[k]);
+    double q[3][2];
+    for (int k = 0; k < 3; ++k) {
+      double x = ctx->P[6 * sc + 2 * k] + sh[0] - P[0];
+      double y = ctx->P[6 * sc + 2 * k + 1] + sh[1] - P[1];
+      q[k][0] = Ji[0] * x + Ji[1] * y;
+      q[k][1] = Ji[2] * x + Ji[3] * y;
+    }
+    double two_area = std::fabs((q[1][0] - q[0][0]) * (q[2][1] - q[0][1]) -
+                                (q[2][0] - q[0][0]) * (q[1][1] - q[0][1]));
+    vol[s] = 0.5 * two_area;
+    for (int l = 0; l < m; ++l)
+      A[s * m + l] = tri_moment(q, R.ex[l][0], R.ex[l][1], two_area) - vol[s] * R.mean0[l];
+  }
+  // Householder QR: Qt accumulates H_m ... H_1, W becomes R
+  double W[kMaxNs * kMaxM], Qt[kMaxNs * kMaxNs];
+  std::copy(A, A + n * m, W);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Qt[i * n + j] = i == j ? 1.0 : 0.0;
+  double rmax = 0.0, rmin = 1e300;
+  for (int k = 0; k < m; ++k) {
+    double sig = 0.0;
+    for (int i = k; i < n; ++i) sig += W[i * m + k] * W[i * m + k];
+    sig = std::sqrt(sig);
+    if (sig == 0.0) return TENO_ESTENCIL;
+    double v[kMaxNs];
+    const double alpha = W[k * m + k] > 0 ? -sig : sig;
+    for (int i = k; i < n; ++i) v[i] = W[i * m + k];
+    v[k] -= alpha;
+    double vv = 0.0;
+    for (int i = k; i < n; ++i) vv += v[i] * v[i];
+    if (vv > 0.0) {
+      for (int j = k; j < m; ++j) {
+        double s = 0.0;
+        for (int i = k; i < n; ++i) s += v[i] * W[i * m + j];
+        s *= 2.0 / vv;
+        for (int i = k; i < n; ++i) W[i * m + j] -= s * v[i];
+      }
+      for (int j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int i = k; i < n; ++i) s += v[i] * Qt[i * n + j];
+        s *= 2.0 / vv;
+        for (int i = k; i < n; ++i) Qt[i * n + j] -= s * v[i];
+      }
+    }
+    rmax = std::max(rmax, std::fabs(W[k * m + k]));
+    rmin = std::min(rmin, std::fabs(W[k * m + k]));
+  }
+  if (!(rmin > 1e-12 * rmax)) return TENO_ESTENCIL;
+  // Ahat = R^-1 Q_1^T
+  double Ah[kMaxM * kMaxNs];
+  for (int s = 0; s < n; ++s)
+    for (int i = m - 1; i >= 0; --i) {
+      double x = Qt[i * n + s];
+      for (int k = i + 1; k < m; ++k) x -= W[i * m + k] * Ah[k * n + s];
+      Ah[i * n + s] = x / W[i * m + i];
+    }
+  // G = Lc^T Ahat diag(vol); Lc^T is upper triangular: G_l = sum_{j>=l} Lc[j][l] Ahat_j
+  const int mr = R.m;
+  for (int l = 0; l < m; ++l)
+    for (int s = 0; s < n; ++s) {
+      double x = 0.0;
+      for (int j = l; j < m; ++j) x += R.Lc[j * mr + l] * Ah[j * n + s];
+      G[l * n + s] = x * vol[s];
+    }
+  return TENO_OK;
+}
+
+int run_precompute(teno_ctx* ctx) {
+  const teno_params& p = ctx->prm;
+  RefData R;
+  if (make_ref(p.order, ctx->nq, R)) return fail(ctx, TENO_EINVAL, "reference data");
+  const int m = R.m, ns = ctx->ns, SL = ctx->SL, E = ctx->E;
+  const int64_t nc = ctx->nc, npad = ctx->npad, ntile = npad / kTile;
+  ctx->st_large.assign(nc * ns, -1);
+  ctx->st_small.assign(nc * kSmallK * kSmallN, -1);
+  const bool f64 = p.precision == TENO_FP64;
+  const size_t esz = f64 ? sizeof(double) : sizeof(float);
+  std::vector<unsigned char> ahat((size_t)ntile * E * kTile * esz, 0);
+  std::vector<int32_t> nbr((size_t)ntile * SL * kTile, 0);
+  std::vector<uint8_t> smask(npad, 0);
+  int rc = TENO_OK;
+  int64_t bad = -1;
+#pragma omp parallel
+  {
+    Searcher S(ctx);
+    std::vector<double> G(kMaxM * kMaxNs);
+#pragma omp for schedule(dynamic, 256)
+    for (int64_t i = 0; i < nc; ++i) {
+      if (rc != TENO_OK) continue;
+      const int32_t t = (int32_t)i;  // user id
+      int32_t* lg = &ctx->st_large[(size_t)t * ns];
+      int32_t* sm = &ctx->st_small[(size_t)t * kSmallK * kSmallN];
+      int r = find_stencils(S, t, ns, lg, sm);
+      const int64_t c = ctx->iperm[t];  // internal index
+      const int64_t tile = c / kTile, lane = c % kTile;
+      auto put = [&](int e, double x) {
+        size_t pos = ((size_t)tile * E + e) * kTile + lane;
+        if (f64)
+          reinterpret_cast<double*>(ahat.data())[pos] = x;
+        else
+          reinterpret_cast<float*>(ahat.data())[pos] = (float)x;
+      };
+      if (!r) r = stencil_matrix(ctx, R, t, lg, ns, m, G.data());
+      if (!r) {
+        for (int s = 0; s < ns; ++s) {
+          nbr[((size_t)tile * SL + s) * kTile + lane] = ctx->iperm[lg[s]];
+          for (int l = 0; l < m; ++l) put(s * m + l, G[l * ns + s]);
+        }
+        uint8_t mask = 0;
+        for (int j = 0; j < kSmallK && !r; ++j) {
+          const int32_t* ids = sm + j * kSmallN;
+          const int slot0 = ns + j * kSmallN;
+          if (ids[0] < 0) {
+            for (int s = 0; s < kSmallN; ++s) {
+              nbr[((size_t)tile * SL + slot0 + s) * kTile + lane] = (int32_t)c;
+              for (int l = 0; l < kSmallM; ++l) put(m * ns + (j * kSmallN + s) * kSmallM + l, 0.0);
+            }
+            continue;
+          }
+          r = stencil_matrix(ctx, R, t, ids, kSmallN, kSmallM, G.data());
+          if (r) break;
+          mask |= (uint8_t)(1u << j);
+          for (int s = 0; s < kSmallN; ++s) {
+            nbr[((size_t)tile * SL + slot0 + s) * kTile + lane] = ctx->iperm[ids[s]];
+            for (int l = 0; l < kSmallM; ++l)
+              put(m * ns + (j * kSmallN + s) * kSmallM + l, G[l * kSmallN + s]);
+          }
+        }
+        smask[c] = mask;
+      }
+      if (r) {
+#pragma omp critical
+        {
+          rc = r;
+          bad = t;
+        }
+      }
+    }
+  }
+  if (rc)
+    return fail(ctx, rc, "stencil or least-squares failure at user cell " + std::to_string(bad));
+  // pad lanes of the last tile point at cell 0
+  for (int64_t c = nc; c < npad; ++c) {
+    const int64_t tile = c / kTile, lane = c % kTile;
+    for (int s = 0; s < SL; ++s) nbr[((size_t)tile * SL + s) * kTile + lane] = 0;
+  }
+  // reverse stencil adjacency (adjoint gather): for every cell the d_bar
+  // positions of the slots that hold it
+  {
+    const int NV = p.n_var;
+    std::vector<int64_t> cnt(nc + 1, 0);
+    for (int64_t c = 0; c < nc; ++c) {
+      const int64_t tile = c / kTile, lane = c % kTile;
+      for (int s = 0; s < SL; ++s) {
+        if (s >= ns && !((smask[c] >> ((s - ns) / kSmallN)) & 1)) continue;
+        cnt[nbr[((size_t)tile * SL + s) * kTile + lane] + 1]++;
+      }
+    }
+    for (int64_t c = 0; c < nc; ++c) cnt[c + 1] += cnt[c];
+    ctx->rev_off_h = cnt;
+    ctx->rev_idx_h.assign(cnt[nc], 0);
+    std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+    for (int64_t c = 0; c < nc; ++c) {
+      const int64_t tile = c / kTile, lane = c % kTile;
+      for (int s = 0; s < SL; ++s) {
+        if (s >= ns && !((smask[c] >> ((s - ns) / kSmallN)) & 1)) continue;
+        int32_t j = nbr[((size_t)tile * SL + s) * kTile + lane];
+        ctx->rev_idx_h[pos[j]++] = ((tile * SL + s) * NV) * kTile + lane;
+      }
+    }
+  }
+  int e = upload(ctx, ctx->b_ahat, ahat.data(), ahat.size());
+  if (!e) e = upload(ctx, ctx->b_nbr, nbr.data(), nbr.size() * sizeof(int32_t));
+  if (!e) e = upload(ctx, ctx->b_smask, smask.data(), smask.size());
+  if (e) return e;
+  // device mesh descriptor
+  DeviceMesh& dm = ctx->dm;
+  dm.n_var = p.n_var;
+  dm.order = p.order;
+  dm.m = m;
+  dm.ns = ns;
+  dm.nq = ctx->nq;
+  dm.e_entries = E;
+  dm.flux = p.flux;
+  dm.precision = p.precision;
+  dm.linear = p.linear;
+  dm.ct = p.ct;
+  dm.eps = p.eps;
+  dm.gamma = p.gamma;
+  dm.adv_x = p.adv_x;
+  dm.adv_y = p.adv_y;
+  dm.cfl = p.cfl;
+  dm.ahat = ctx->b_ahat.p;
+  dm.nbr = (const int32_t*)ctx->b_nbr.p;
+  dm.smask = (const uint8_t*)ctx->b_smask.p;
+  std::copy(R.psi_t, R.psi_t + kMaxPts * kMaxM, dm.eval.psi);
+  for (int k = 0; k < kMaxNq; ++k) {
+    dm.gw[k] = k < ctx->nq ? R.gw[k] : 0.0;
+    dm.gt[k] = k < ctx->nq ? R.gt[k] : 0.0;
+  }
+  return TENO_OK;
+}
+
+int upload_mesh(teno_ctx* ctx) {
+  const int64_t nc = ctx->nc, npad = ctx->npad;
+  // faces in internal order: owner = the side with the smaller internal index
+  std::vector<int32_t> fcells, cfaces(3 * npad, 0);
+  std::vector<int8_t> fedges;
+  std::vector<double> fgeom;
+  for (int64_t c = 0; c < nc; ++c) {
+    const int32_t u = ctx->perm[c];
+    for (int e = 0; e < 3; ++e) {
+      const int32_t nu = ctx->fnbr[3 * u + e];
+      const int64_t n = nu >= 0 ? ctx->iperm[nu] : -1;
+      if (n >= 0 && n < c) continue;
+      const int64_t f = (int64_t)fcells.size() / 2;
+      fcells.push_back((int32_t)c);
+      fcells.push_back((int32_t)n);
+      fedges.push_back((int8_t)e);
+      fedges.push_back((int8_t)(n >= 0 ? ctx->fedge[3 * u + e] : ctx->fbc[3 * u + e]));
+      const double* P = &ctx->P[6 * u];
+      const int e1 = (e + 1) % 3;
+      const double dx = P[2 * e1] - P[2 * e], dy = P[2 * e1 + 1] - P[2 * e + 1];
+      const double len = std::hypot(dx, dy);
+      fgeom.push_back(dy / len);
+      fgeom.push_back(-dx / len);
+      fgeom.push_back(len);
+      fgeom.push_back(P[2 * e]);
+      fgeom.push_back(P[2 * e + 1]);
+      cfaces[3 * c + e] = (int32_t)(2 * f);
+      if (n >= 0) cfaces[3 * n + ctx->fedge[3 * u + e]] = (int32_t)(2 * f + 1);
+    }
+  }
+  ctx->nface = (int64_t)fcells.size() / 2;
+  std::vector<double> inv_area(npad, 0.0), cfl_len(npad, 1.0);
+  for (int64_t c = 0; c < nc; ++c) {
+    const int32_t u = ctx->perm[c];
+    inv_area[c] = 1.0 / ctx->area[u];
+    cfl_len[c] = 4.0 * ctx->area[u] / ctx->perim[u];
+  }
+  int rc = upload(ctx, ctx->b_fcells, fcells.data(), fcells.size() * 4);
+  if (!rc) rc = upload(ctx, ctx->b_fedges, fedges.data(), fedges.size());
+  if (!rc) rc = upload(ctx, ctx->b_fgeom, fgeom.data(), fgeom.size() * 8);
+  if (!rc) rc = upload(ctx, ctx->b_cfaces, cfaces.data(), cfaces.size() * 4);
+  if (!rc) rc = upload(ctx, ctx->b_inv_area, inv_area.data(), inv_area.size() * 8);
+  if (!rc) rc = upload(ctx, ctx->b_cfl_len, cfl_len.data(), cfl_len.size() * 8);
+  if (!rc) rc = upload(ctx, ctx->b_perm, ctx->perm.data(), ctx->perm.size() * 4);
+  if (rc) return rc;
+  DeviceMesh& dm = ctx->dm;
+  dm.n_cell = nc;
+  dm.n_pad = npad;
+  dm.n_face = ctx->nface;
+  dm.f_cells = (const int32_t*)ctx->b_fcells.p;
+  dm.f_edges = (const int8_t*)ctx->b_fedges.p;
+  dm.f_geom = (const double*)ctx->b_fgeom.p;
+  dm.c_faces = (const int32_t*)ctx->b_cfaces.p;
+  dm.inv_area = (const double*)ctx->b_inv_area.p;
+  dm.cfl_len = (const double*)ctx->b_cfl_len.p;
+  return TENO_OK;
+}
+
+// one residual evaluation of state U (internal order) into Uq / K
+int stage_flux(teno_ctx* ctx, const double* U, uint8_t* sel_out, double time) {
+  const uint8_t* sel_in = ctx->override_on ? (const uint8_t*)ctx->b_sel_ovr.p : nullptr;
+  CK(launch_recon(ctx->dm, U, ctx->b_Uq.p, sel_out, sel_in, ctx->stream), "recon launch");
+  CK(launch_face_flux(ctx->dm, ctx->b_Uq.p, ctx->b_K.p, time, ctx->stream), "face flux launch");
+  return TENO_OK;
+}
+
+int check_ready(teno_ctx* ctx, bool need_state) {
+  if (!ctx) return TENO_EINVAL;
+  if (ctx->device < 0) return fail(ctx, TENO_ESTATE, "host-only context: no device work");
+  if (!ctx->mesh_ok || !ctx->pre_ok) return fail(ctx, TENO_ESTATE, "mesh or precompute missing");
+  if (need_state && !ctx->state_ok) return fail(ctx, TENO_ESTATE, "state not set");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  return TENO_OK;
+}
+
+// copy a user-order [n_var][n_cell] array into an internal-order buffer
+int to_internal(teno_ctx* ctx, const double* src, double* dst, int on_device) {
+  const int64_t nc = ctx->nc;
+  const int nvar = ctx->prm.n_var;
+  const double* s = src;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(ctx->b_tmp.p, src, sizeof(double) * nvar * nc, cudaMemcpyHostToDevice,
+                       ctx->stream),
+       "H2D");
+    s = (const double*)ctx->b_tmp.p;
+  }
+  CK(launch_permute(s, dst, (const int32_t*)ctx->b_perm.p, nc, nc, ctx->npad, nvar, 0,
+                    ctx->stream),
+     "permute");
+  return TENO_OK;
+}
+
+int to_user(teno_ctx* ctx, const double* src, double* dst, int on_device) {
+  const int64_t nc = ctx->nc;
+  const int nvar = ctx->prm.n_var;
+  double* d = on_device ? dst : (double*)ctx->b_tmp.p;
+  CK(launch_permute(src, d, (const int32_t*)ctx->b_perm.p, nc, ctx->npad, nc, nvar, 1,
+                    ctx->stream),
+     "permute");
+  if (!on_device) {
+    CK(cudaMemcpyAsync(dst, d, sizeof(double) * nvar * nc, cudaMemcpyDeviceToHost, ctx->stream),
+       "D2H");
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+  }
+  return TENO_OK;
+}
+
+int ensure_adjoint(teno_ctx* ctx) {
+  if (ctx->adj_ok) return TENO_OK;
+  const int64_t npad = ctx->npad, nc = ctx->nc;
+  const int nv = ctx->prm.n_var;
+  const size_t ntile = npad / kTile;
+  int rc = dev_alloc(ctx, ctx->b_dbar, sizeof(double) * ntile * ctx->SL * nv * kTile);
+  if (!rc) rc = dev_alloc(ctx, ctx->b_uself, sizeof(double) * nv * npad);
+  if (!rc) rc = dev_alloc(ctx, ctx->b_Uqbar, sizeof(double) * npad * 3 * ctx->nq * nv);
+  if (!rc) rc = dev_alloc(ctx, ctx->b_l1, sizeof(double) * nv * npad);
+  if (!rc) rc = dev_alloc(ctx, ctx->b_l2, sizeof(double) * nv * npad);
+  if (!rc) rc = dev_alloc(ctx, ctx->b_lamn, sizeof(double) * nv * npad);
+  if (!rc) rc = dev_alloc(ctx, ctx->b_vtmp, sizeof(double) * nv * npad);
+  if (!rc) rc = dev_alloc(ctx, ctx->b_selA, (size_t)nv * npad);
+  if (!rc) rc = upload(ctx, ctx->b_rev_off, ctx->rev_off_h.data(), sizeof(int64_t) * (nc + 1));
+  if (!rc)
+    rc = upload(ctx, ctx->b_rev_idx, ctx->rev_idx_h.data(),
+                sizeof(int64_t) * std::max<size_t>(1, ctx->rev_idx_h.size()));
+  if (rc) return rc;
+  CK(cudaMemsetAsync(ctx->b_dbar.p, 0, ctx->b_dbar.bytes, ctx->stream), "memset");
+  ctx->adj_ok = true;
+  return TENO_OK;
+}
+
+// v = (dR/dU)^T w at U (all internal order)
+int vjp_internal(teno_ctx* ctx, const double* U, const double* w, double* v, double time) {
+  int rc = ensure_adjoint(ctx);
+  if (rc) return rc;
+  uint8_t* sel = (uint8_t*)ctx->b_selA.p;
+  const uint8_t* sel_in = ctx->override_on ? (const uint8_t*)ctx->b_sel_ovr.p : nullptr;
+  CK(launch_recon(ctx->dm, U, ctx->b_Uq.p, sel, sel_in, ctx->stream), "recon launch");
+  if (sel_in) sel = (uint8_t*)ctx->b_sel_ovr.p;
+  CK(launch_face_flux_vjp(ctx->dm, ctx->b_Uq.p, w, (double*)ctx->b_Uqbar.p, time, ctx->stream),
+     "flux vjp launch");
+  CK(launch_recon_vjp(ctx->dm, sel, (const double*)ctx->b_Uqbar.p, (double*)ctx->b_dbar.p,
+                      (double*)ctx->b_uself.p, ctx->stream),
+     "recon vjp launch");
+  CK(launch_scatter_gather(ctx->dm, (const int64_t*)ctx->b_rev_off.p,
+                           (const int64_t*)ctx->b_rev_idx.p, (const double*)ctx->b_dbar.p,
+                           (const double*)ctx->b_uself.p, v, ctx->stream),
+     "scatter launch");
+  return TENO_OK;
+}
+
+// SSP-RK3 stage: out = cn*Un + cs*(Us + dt R(Us))
+int rk_stage(teno_ctx* ctx, const double* Un, const double* Us, double* out, double cn,
+             double cs, double dt, const double* max_lam, double time) {
+  int rc = stage_flux(ctx, Us, nullptr, time);
+  if (rc) return rc;
+  CK(launch_gather(ctx->dm, ctx->b_K.p, Un, Us, out, 1, cn, cs, dt, max_lam,
+                   (int*)ctx->b_flag.p, ctx->stream),
+     "gather launch");
+  return TENO_OK;
+}
+
+}  // namespace
+
+// ========================================================================
+// C ABI
+
+extern "C" {
+
+void teno_default_params(teno_params* p) {
+  if (!p) return;
+  p->order = 5;
+  p->n_var = 4;
+  p->flux = TENO_FLUX_HLL;
+  p->precision = TENO_FP64;
+  p->linear = 0;
+  p->nq = 0;
+  p->ct = 1e-6;
+  p->eps = 1e-12;
+  p->gamma = 1.4;
+  p->adv_x = 1.0;
+  p->adv_y = 1.0;
+  p->cfl = 0.4;
+}
+
+int teno_create(teno_ctx** out, int device, void* cuda_stream) {
+  if (!out) return TENO_EINVAL;
+  *out = nullptr;
+  if (device == -1) {  // host-only: mesh and stencil preprocessing without a GPU
+    teno_ctx* ctx = new (std::nothrow) teno_ctx();
+    if (!ctx) return TENO_ENOMEM;
+    ctx->device = -1;
+    *out = ctx;
+    return TENO_OK;
+  }
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return TENO_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return TENO_ECUDA;
+  teno_ctx* ctx = new (std::nothrow) teno_ctx();
+  if (!ctx) return TENO_ENOMEM;
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  if (dev_alloc(ctx, ctx->b_maxlam, 64) || dev_alloc(ctx, ctx->b_flag, 64)) {
+    delete ctx;
+    return TENO_ENOMEM;
+  }
+  cudaMemset(ctx->b_flag.p, 0, 64);
+  cudaMemset(ctx->b_maxlam.p, 0, 64);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    delete ctx;
+    return TENO_ECUDA;
+  }
+  *out = ctx;
+  return TENO_OK;
+}
+
+int teno_destroy(teno_ctx* ctx) {
+  if (!ctx) return TENO_OK;
+  if (ctx->device < 0) {
+    delete ctx;
+    return TENO_OK;
+  }
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  DevBuf* bufs[] = {&ctx->b_ahat, &ctx->b_nbr, &ctx->b_smask, &ctx->b_fcells, &ctx->b_fedges,
+                    &ctx->b_fgeom, &ctx->b_cfaces, &ctx->b_inv_area, &ctx->b_cfl_len,
+                    &ctx->b_perm, &ctx->b_U, &ctx->b_U1, &ctx->b_U2, &ctx->b_R, &ctx->b_tmp,
+                    &ctx->b_Uq, &ctx->b_K, &ctx->b_sel, &ctx->b_sel_ovr, &ctx->b_maxlam,
+                    &ctx->b_flag, &ctx->b_rev_off, &ctx->b_rev_idx, &ctx->b_dbar, &ctx->b_uself,
+                    &ctx->b_Uqbar, &ctx->b_l1, &ctx->b_l2, &ctx->b_lamn, &ctx->b_vtmp,
+                    &ctx->b_selA};
+  for (DevBuf* b : bufs) dev_free(*b);
+  delete ctx;
+  return TENO_OK;
+}
+
+const char* teno_last_error(teno_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int teno_set_stream(teno_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return TENO_EINVAL;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  return TENO_OK;
+}
+
+int teno_mesh_load(teno_ctx* ctx, int64_t n_vert, const double* xy, int64_t n_cell,
+                   const int32_t* tri, int64_t n_bface, const int32_t* bface,
+                   const double* period) {
+  if (!ctx) return TENO_EINVAL;
+  if (!xy || !tri || n_vert < 3 || n_cell < 1 || n_bface < 0 || (n_bface > 0 && !bface))
+    return fail(ctx, TENO_EINVAL, "mesh_load: bad arguments");
+  if (n_cell > (int64_t)INT32_MAX / 4) return fail(ctx, TENO_EINVAL, "mesh_load: too many cells");
+  if (period && !(period[0] > 0 && period[1] > 0))
+    return fail(ctx, TENO_EINVAL, "mesh_load: non-positive period");
+  if (ctx->device >= 0) CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  ctx->mesh_ok = ctx->pre_ok = ctx->state_ok = ctx->adj_ok = false;
+  ctx->override_on = false;
+  ctx->has_time_bc = false;
+  ctx->nv = n_vert;
+  ctx->nc = n_cell;
+  ctx->npad = (n_cell + kTile - 1) / kTile * kTile;
+  ctx->periodic = period != nullptr;
+  ctx->L[0] = period ? period[0] : 0.0;
+  ctx->L[1] = period ? period[1] : 0.0;
+  int rc = build_mesh(ctx, xy, tri, n_bface, bface);
+  if (!rc) rc = upload_mesh(ctx);
+  if (rc) return rc;
+  ctx->time = 0.0;
+  ctx->mesh_ok = true;
+  return TENO_OK;
+}
+
+int teno_get_permutation(teno_ctx* ctx, int32_t* perm) {
+  if (!ctx || !perm) return TENO_EINVAL;
+  if (!ctx->mesh_ok) return fail(ctx, TENO_ESTATE, "no mesh");
+  std::copy(ctx->perm.begin(), ctx->perm.end(), perm);
+  return TENO_OK;
+}
+
+int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
+  if (!ctx || !p) return TENO_EINVAL;
+  if (!ctx->mesh_ok) return fail(ctx, TENO_ESTATE, "precompute before mesh_load");
+  if (p->order < 3 || p->order > 6 || (p->n_var != 1 && p->n_var != 4) ||
+      (p->precision != TENO_FP64 && p->precision != TENO_FP32_MIXED) || p->flux < 0 ||
+      p->flux > 2 || (p->n_var == 1) != (p->flux == TENO_FLUX_UPWIND) || !(p->ct > 0) ||
+      !(p->eps > 0) || !(p->gamma > 1.0) || !(p->cfl > 0))
+    return fail(ctx, TENO_EINVAL, "precompute: bad parameters");
+  const int nq_default = p->order <= 4 ? 2 : 3;
+  if (p->nq != 0 && p->nq != nq_default)
+    return fail(ctx, TENO_EINVAL, "precompute: only the default Gauss point count is built");
+  if (!ctx->periodic && p->n_var != 4)
+    return fail(ctx, TENO_EINVAL, "precompute: boundary conditions need the Euler equations");
+  if (ctx->device >= 0) CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  ctx->pre_ok = ctx->state_ok = ctx->adj_ok = false;
+  ctx->override_on = false;
+  ctx->prm = *p;
+  ctx->nq = nq_default;
+  ctx->m = unknowns(p->order);
+  ctx->ns = 2 * (ctx->m + 1);
+  ctx->E = ctx->m * ctx->ns + kSmallK * kSmallN * kSmallM;
+  ctx->SL = ctx->ns + kSmallK * kSmallN;
+  int rc = run_precompute(ctx);
+  if (rc) return rc;
+  const int64_t npad = ctx->npad;
+  const int nv = p->n_var;
+  const size_t tsz = p->precision == TENO_FP64 ? 8 : 4;
+  rc = dev_alloc(ctx, ctx->b_U, 8 * nv * npad);
+  if (!rc) rc = dev_alloc(ctx, ctx->b_U1, 8 * nv * npad);
+  if (!rc) rc = dev_alloc(ctx, ctx->b_U2, 8 * nv * npad);
+  if (!rc) rc = dev_alloc(ctx, ctx->b_R, 8 * nv * npad);
+  if (!rc) rc = dev_alloc(ctx, ctx->b_tmp, 8 * nv * npad);
+  if (!rc) rc = dev_alloc(ctx, ctx->b_Uq, tsz * npad * 3 * ctx->nq * nv);
+  if (!rc) rc = dev_alloc(ctx, ctx->b_K, tsz * std::max<int64_t>(1, ctx->nface) * nv);
+  if (!rc) rc = dev_alloc(ctx, ctx->b_sel, (size_t)nv * npad);
+  if (!rc) rc = dev_alloc(ctx, ctx->b_sel_ovr, (size_t)nv * npad);
+  if (rc) return rc;
+  if (ctx->device < 0) {
+    ctx->pre_ok = true;
+    return TENO_OK;
+  }
+  CK(cudaMemsetAsync(ctx->b_U.p, 0, ctx->b_U.bytes, ctx->stream), "memset");
+  CK(cudaMemsetAsync(ctx->b_U1.p, 0, ctx->b_U1.bytes, ctx->stream), "memset");
+  CK(cudaMemsetAsync(ctx->b_U2.p, 0, ctx->b_U2.bytes, ctx->stream), "memset");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  ctx->pre_ok = true;
+  return TENO_OK;
+}
+
+int teno_get_stencils(teno_ctx* ctx, int32_t* large, int32_t* small) {
+  if (!ctx || !large || !small) return TENO_EINVAL;
+  if (!ctx->pre_ok) return fail(ctx, TENO_ESTATE, "no precompute");
+  std::copy(ctx->st_large.begin(), ctx->st_large.end(), large);
+  std::copy(ctx->st_small.begin(), ctx->st_small.end(), small);
+  return TENO_OK;
+}
+
+int teno_get_sizes(teno_ctx* ctx, int64_t* n_cell, int32_t* n_var, int32_t* m, int32_t* n_s) {
+  if (!ctx) return TENO_EINVAL;
+  if (n_cell) *n_cell = ctx->nc;
+  if (n_var) *n_var = ctx->prm.n_var;
+  if (m) *m = ctx->m;
+  if (n_s) *n_s = ctx->ns;
+  return TENO_OK;
+}
+
+int teno_set_state(teno_ctx* ctx, const double* U, int on_device) {
+  int rc = check_ready(ctx, false);
+  if (rc) return rc;
+  if (!U) return fail(ctx, TENO_EINVAL, "set_state: null U");
+  rc = to_internal(ctx, U, (double*)ctx->b_U.p, on_device);
+  if (rc) return rc;
+  if (!on_device) CK(cudaStreamSynchronize(ctx->stream), "sync");
+  ctx->state_ok = true;
+  return TENO_OK;
+}
+
+int teno_get_state(teno_ctx* ctx, double* U, int on_device) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (!U) return fail(ctx, TENO_EINVAL, "get_state: null U");
+  return to_user(ctx, (const double*)ctx->b_U.p, U, on_device);
+}
+
+int teno_set_time(teno_ctx* ctx, double t) {
+  if (!ctx) return TENO_EINVAL;
+  ctx->time = t;
+  return TENO_OK;
+}
+
+int teno_residual(teno_ctx* ctx, double* R, uint8_t* sel, int on_device) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (!R) return fail(ctx, TENO_EINVAL, "residual: null R");
+  rc = stage_flux(ctx, (const double*)ctx->b_U.p, (uint8_t*)ctx->b_sel.p, ctx->time);
+  if (rc) return rc;
+  CK(launch_gather(ctx->dm, ctx->b_K.p, nullptr, nullptr, (double*)ctx->b_R.p, 0, 0, 0, 0,
+                   nullptr, nullptr, ctx->stream),
+     "gather launch");
+  if (sel) {
+    const uint8_t* src = ctx->override_on ? (const uint8_t*)ctx->b_sel_ovr.p
+                                          : (const uint8_t*)ctx->b_sel.p;
+    if (on_device) {
+      CK(launch_permute_u8(src, sel, (const int32_t*)ctx->b_perm.p, ctx->nc, ctx->npad, ctx->nc,
+                           ctx->prm.n_var, 1, ctx->stream),
+         "permute");
+    } else {
+      rc = dev_alloc(ctx, ctx->b_vtmp, sizeof(double) * ctx->prm.n_var * ctx->npad);
+      if (rc) return rc;
+      uint8_t* d = (uint8_t*)ctx->b_vtmp.p;
+      CK(launch_permute_u8(src, d, (const int32_t*)ctx->b_perm.p, ctx->nc, ctx->npad, ctx->nc,
+                           ctx->prm.n_var, 1, ctx->stream),
+         "permute");
+      CK(cudaMemcpyAsync(sel, d, (size_t)ctx->prm.n_var * ctx->nc, cudaMemcpyDeviceToHost,
+                         ctx->stream),
+         "D2H");
+    }
+  }
+  return to_user(ctx, (const double*)ctx->b_R.p, R, on_device);
+}
+
+int teno_set_selection_override(teno_ctx* ctx, const uint8_t* sel, int on_device) {
+  int rc = check_ready(ctx, false);
+  if (rc) return rc;
+  if (!sel) {
+    ctx->override_on = false;
+    return TENO_OK;
+  }
+  const int64_t nc = ctx->nc;
+  const int nv = ctx->prm.n_var;
+  const uint8_t* s = sel;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(ctx->b_tmp.p, sel, (size_t)nv * nc, cudaMemcpyHostToDevice, ctx->stream),
+       "H2D");
+    s = (const uint8_t*)ctx->b_tmp.p;
+  }
+  CK(launch_permute_u8(s, (uint8_t*)ctx->b_sel_ovr.p, (const int32_t*)ctx->b_perm.p, nc, nc,
+                       ctx->npad, nv, 0, ctx->stream),
+     "permute");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  ctx->override_on = true;
+  return TENO_OK;
+}
+
+int teno_cfl_dt(teno_ctx* ctx, double* dt) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (!dt) return fail(ctx, TENO_EINVAL, "cfl_dt: null dt");
+  CK(launch_max_lambda(ctx->dm, (const double*)ctx->b_U.p, (double*)ctx->b_maxlam.p, ctx->stream),
+     "max lambda launch");
+  double lam = 0.0;
+  CK(cudaMemcpyAsync(&lam, ctx->b_maxlam.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+     "D2H");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  if (!(lam > 0.0) || !std::isfinite(lam)) return fail(ctx, TENO_ENONPHYS, "cfl_dt: bad speed");
+  *dt = ctx->prm.cfl / lam;
+  return TENO_OK;
+}
+
+static int rk3_once(teno_ctx* ctx, double dt, double* dt_used) {
+  const double* maxlam = nullptr;
+  if (dt <= 0.0) {
+    if (dt_used || ctx->has_time_bc) {
+      int rc = teno_cfl_dt(ctx, &dt);
+      if (rc) return rc;
+    } else {
+      CK(launch_max_lambda(ctx->dm, (const double*)ctx->b_U.p, (double*)ctx->b_maxlam.p,
+                           ctx->stream),
+         "max lambda launch");
+      maxlam = (const double*)ctx->b_maxlam.p;
+    }
+  }
+  double* U = (double*)ctx->b_U.p;
+  double* U1 = (double*)ctx->b_U1.p;
+  double* U2 = (double*)ctx->b_U2.p;
+  const double t = ctx->time;
+  int rc = rk_stage(ctx, U, U, U1, 0.0, 1.0, dt, maxlam, t);
+  if (!rc) rc = rk_stage(ctx, U, U1, U2, 0.75, 0.25, dt, maxlam, t + dt);
+  if (!rc) rc = rk_stage(ctx, U, U2, U, 1.0 / 3.0, 2.0 / 3.0, dt, maxlam, t + 0.5 * dt);
+  if (rc) return rc;
+  if (dt > 0.0) ctx->time += dt;
+  if (dt_used) *dt_used = dt;
+  return TENO_OK;
+}
+
+int teno_rk3_step(teno_ctx* ctx, double dt, double* dt_used) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  rc = rk3_once(ctx, dt, dt_used);
+  if (rc) return rc;
+  if (dt_used) return teno_check_state(ctx);
+  return TENO_OK;
+}
+
+int teno_rk3_steps(teno_ctx* ctx, int32_t n_steps, double dt) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (n_steps < 0) return fail(ctx, TENO_EINVAL, "rk3_steps: negative count");
+  for (int32_t i = 0; i < n_steps && !rc; ++i) rc = rk3_once(ctx, dt, nullptr);
+  return rc;
+}
+
+int teno_check_state(teno_ctx* ctx) {
+  if (!ctx) return TENO_EINVAL;
+  if (!ctx->pre_ok) return TENO_OK;
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, ctx->b_flag.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
+     "D2H");
+  CK(cudaMemsetAsync(ctx->b_flag.p, 0, sizeof(int), ctx->stream), "memset");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  if (flag) return fail(ctx, TENO_ENONPHYS, "non-physical state (rho <= 0, p <= 0 or NaN)");
+  return TENO_OK;
+}
+
+int teno_residual_vjp(teno_ctx* ctx, const double* w, double* v, int on_device) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (!w || !v) return fail(ctx, TENO_EINVAL, "residual_vjp: null pointer");
+  if (ctx->prm.precision != TENO_FP64)
+    return fail(ctx, TENO_EINVAL, "adjoint: FP64 precision only");
+  rc = ensure_adjoint(ctx);
+  if (rc) return rc;
+  rc = to_internal(ctx, w, (double*)ctx->b_l1.p, on_device);
+  if (!rc)
+    rc = vjp_internal(ctx, (const double*)ctx->b_U.p, (const double*)ctx->b_l1.p,
+                      (double*)ctx->b_vtmp.p, ctx->time);
+  if (!rc) rc = to_user(ctx, (const double*)ctx->b_vtmp.p, v, on_device);
+  return rc;
+}
+
+int teno_adjoint_step(teno_ctx* ctx, double dt, const double* lam_np1, double* lam_n,
+                      int on_device) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (!lam_np1 || !lam_n || !(dt > 0.0)) return fail(ctx, TENO_EINVAL, "adjoint_step: bad args");
+  if (ctx->prm.precision != TENO_FP64)
+    return fail(ctx, TENO_EINVAL, "adjoint: FP64 precision only");
+  rc = ensure_adjoint(ctx);
+  if (rc) return rc;
+  const int64_t n = (int64_t)ctx->prm.n_var * ctx->npad;
+  double* U = (double*)ctx->b_U.p;
+  double* U1 = (double*)ctx->b_U1.p;
+  double* U2 = (double*)ctx->b_U2.p;
+  double* lam = (double*)ctx->b_R.p;  // lambda^{n+1}, internal order
+  double* l1 = (double*)ctx->b_l1.p;
+  double* l2 = (double*)ctx->b_l2.p;
+  double* ln = (double*)ctx->b_lamn.p;
+  double* tmp = (double*)ctx->b_vtmp.p;
+  const double t = ctx->time;
+  rc = to_internal(ctx, lam_np1, lam, on_device);
+  // forward replay of the stage states
+  if (!rc) rc = rk_stage(ctx, U, U, U1, 0.0, 1.0, dt, nullptr, t);
+  if (!rc) rc = rk_stage(ctx, U, U1, U2, 0.75, 0.25, dt, nullptr, t + dt);
+  // stage 3: U^{n+1} = 1/3 U^n + 2/3 U2 + 2/3 dt R(U2)
+  if (!rc) rc = vjp_internal(ctx, U2, lam, tmp, t + 0.5 * dt);
+  if (rc) return rc;
+  CK(launch_axpby(l2, lam, 2.0 / 3.0, tmp, 2.0 / 3.0 * dt, n, ctx->stream), "axpby");
+  CK(launch_axpby(ln, lam, 1.0 / 3.0, lam, 0.0, n, ctx->stream), "axpby");
+  // stage 2: U2 = 3/4 U^n + 1/4 U1 + 1/4 dt R(U1)
+  rc = vjp_internal(ctx, U1, l2, tmp, t + dt);
+  if (rc) return rc;
+  CK(launch_axpby(l1, l2, 0.25, tmp, 0.25 * dt, n, ctx->stream), "axpby");
+  CK(launch_axpby(ln, ln, 1.0, l2, 0.75, n, ctx->stream), "axpby");
+  // stage 1: U1 = U^n + dt R(U^n)
+  rc = vjp_internal(ctx, U, l1, tmp, t);
+  if (rc) return rc;
+  CK(launch_axpby(ln, ln, 1.0, l1, 1.0, n, ctx->stream), "axpby");
+  CK(launch_axpby(ln, ln, 1.0, tmp, dt, n, ctx->stream), "axpby");
+  return to_user(ctx, ln, lam_n, on_device);
+}
+
+}  // extern "C"

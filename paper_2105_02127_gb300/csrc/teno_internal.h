@@ -1,0 +1,84 @@
+// teno_internal.h -- shared declarations of the host runtime (teno_host.cpp)
+// and the CUDA kernels (teno_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/teno.h"
+
+namespace teno {
+
+constexpr int kTile = 32;       // cells per tile of the cell-interleaved layouts
+constexpr int kSmallN = 12;     // neighbours of a directional stencil (2 N_k, r = 2)
+constexpr int kSmallM = 5;      // unknowns of a quadratic polynomial
+constexpr int kSmallK = 3;      // directional stencils per triangle
+constexpr int kMaxM = 20;
+constexpr int kMaxNs = 42;
+constexpr int kMaxNq = 4;
+constexpr int kMaxPts = 3 * kMaxNq;
+
+inline int unknowns(int order) {
+  int r = order - 1;
+  return (r + 1) * (r + 2) / 2 - 1;
+}
+
+// Per-launch constants of the reconstruction: the evaluation matrix of the
+// transformed basis at the 3*nq reference edge points (row p = edge*nq + q).
+struct EvalTable {
+  double psi[kMaxPts * kMaxM];
+};
+
+// Everything the kernels of one residual evaluation need (device pointers).
+struct DeviceMesh {
+  int64_t n_cell = 0, n_pad = 0, n_face = 0;
+  int n_var = 1, order = 3, m = 5, ns = 12, nq = 2, e_entries = 0;
+  int flux = 0, precision = 0, linear = 0;
+  double ct = 1e-6, eps = 1e-12, gamma = 1.4, adv_x = 1, adv_y = 1, cfl = 0.4;
+  // reconstruction data, tile-interleaved [tile][entry][32]
+  const void* ahat = nullptr;     // double or float
+  const int32_t* nbr = nullptr;   // [tile][ns+36][32] internal cell ids
+  const uint8_t* smask = nullptr; // [n_pad] bit k: directional stencil k present
+  // faces
+  const int32_t* f_cells = nullptr; // [n_face][2] owner, neighbour (-1 boundary)
+  const int8_t* f_edges = nullptr;  // [n_face][2] local edge in owner / neighbour (bc tag if boundary)
+  const double* f_geom = nullptr;   // [n_face][5] nx, ny, |A| (outward from owner), x_a, y_a
+  const int32_t* c_faces = nullptr; // [n_pad][3] face*2 + (1 if the cell is the neighbour)
+  const double* inv_area = nullptr; // [n_pad]
+  const double* cfl_len = nullptr;  // [n_pad] 4|V|/perimeter
+  EvalTable eval;
+  double gw[kMaxNq];                // Gauss weights on [0,1], sum 1
+  double gt[kMaxNq];                // Gauss nodes on [0,1], ascending
+};
+
+// launchers (teno_kernels.cu); all return a cudaError_t
+cudaError_t launch_recon(const DeviceMesh& dm, const double* U, void* Uq, uint8_t* sel_out,
+                         const uint8_t* sel_in, cudaStream_t st);
+cudaError_t launch_face_flux(const DeviceMesh& dm, const void* Uq, void* K, double time,
+                             cudaStream_t st);
+// mode 0: R = residual; mode 1: U_out = cn*Un + cs*(Us + dt*R)
+cudaError_t launch_gather(const DeviceMesh& dm, const void* K, const double* Un, const double* Us,
+                          double* out, int mode, double cn, double cs, double dt_fixed,
+                          const double* max_lam, int* flag, cudaStream_t st);
+cudaError_t launch_max_lambda(const DeviceMesh& dm, const double* U, double* max_lam,
+                              cudaStream_t st);
+cudaError_t launch_permute(const double* src, double* dst, const int32_t* perm, int64_t n,
+                           int64_t ld_src, int64_t ld_dst, int n_var, int to_user,
+                           cudaStream_t st);
+cudaError_t launch_permute_u8(const uint8_t* src, uint8_t* dst, const int32_t* perm, int64_t n,
+                              int64_t ld_src, int64_t ld_dst, int n_var, int to_user,
+                              cudaStream_t st);
+cudaError_t launch_axpby(double* out, const double* a, double ca, const double* b, double cb,
+                         int64_t n, cudaStream_t st);
+// adjoint kernels
+cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const double* w,
+                                 double* Uq_bar, double time, cudaStream_t st);
+cudaError_t launch_recon_vjp(const DeviceMesh& dm, const uint8_t* sel, const double* Uq_bar,
+                             double* d_bar, double* u_self, cudaStream_t st);
+cudaError_t launch_scatter_gather(const DeviceMesh& dm, const int64_t* rev_off,
+                                  const int64_t* rev_idx, const double* d_bar,
+                                  const double* u_self, double* v, cudaStream_t st);
+
+}  // namespace teno

@@ -1,0 +1,916 @@
+// teno_kernels.cu -- CUDA kernels of the TENO finite-volume residual for
+// sm_103a (GB300).
+//
+// Per RK stage (Sec. 2.1, Eq. fv_governing_equation_semi_discrete):
+//   recon_kernel      stencil differences, coefficient matvecs (Eqs.
+//                     reconstruction_08/09 with |V'_s| folded into the
+//                     matrices), smoothness indicators (Eq. WENO_smoothness in
+//                     a beta-orthonormal basis, so beta = |a'|^2), TENO scale
+//                     separation, cutoff and two-step selection (Eqs.
+//                     new_scale_separation .. TENO_weight) and evaluation at
+//                     the edge Gauss points;
+//   face_flux_kernel  rotated HLL / HLLC (Sec. 4) or upwind flux at the Gauss
+//                     points of each face, summed with weights and |A|;
+//   gather_kernel     cell-centric, atomic-free sum of the three face fluxes
+//                     (owner +, neighbour -), fused with the SSP-RK3 stage
+//                     combination (Eq. fv_time_discretization_01);
+//   max_lambda_kernel warp-shuffle / block reduction of the CFL signal speed.
+// Adjoint (no counterpart in the paper): face_flux_vjp_kernel (dual-number
+// flux Jacobians), recon_vjp_kernel (transposed matvecs with the selection
+// frozen) and scatter_gather_kernel (reverse-stencil gather, no atomics).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "teno_internal.h"
+
+namespace teno {
+namespace {
+
+constexpr int kSmallEntries = kSmallK * kSmallN * kSmallM;  // 180
+constexpr int kSmallSlots = kSmallK * kSmallN;               // 36
+
+// ---------------------------------------------------------------- scalars
+template <typename T>
+__device__ __forceinline__ T tsqrt(T x);
+template <>
+__device__ __forceinline__ double tsqrt<double>(double x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
+
+// forward-mode dual number with N directions (flux Jacobians of the adjoint)
+template <int N>
+struct Dual {
+  double v;
+  double d[N];
+};
+template <int N>
+__device__ __forceinline__ Dual<N> mk(double v) {
+  Dual<N> r;
+  r.v = v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = 0.0;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator+(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r;
+  r.v = a.v + b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator-(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r;
+  r.v = a.v - b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator-(const Dual<N>& a) {
+  Dual<N> r;
+  r.v = -a.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator*(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator*(double s, const Dual<N>& a) {
+  Dual<N> r;
+  r.v = s * a.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = s * a.d[i];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> operator/(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r;
+  r.v = a.v / b.v;
+  double ib = 1.0 / b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ Dual<N> tsqrt(const Dual<N>& a) {
+  Dual<N> r;
+  r.v = sqrt(a.v);
+  double h = 0.5 / r.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * h;
+  return r;
+}
+__device__ __forceinline__ double val(double x) { return x; }
+__device__ __forceinline__ float val(float x) { return x; }
+template <int N>
+__device__ __forceinline__ double val(const Dual<N>& x) { return x.v; }
+template <typename T>
+__device__ __forceinline__ T vmin(const T& a, const T& b) { return val(a) <= val(b) ? a : b; }
+template <typename T>
+__device__ __forceinline__ T vmax(const T& a, const T& b) { return val(a) >= val(b) ? a : b; }
+template <typename T, typename S>
+__device__ __forceinline__ T cst(S x) { return T(x); }
+template <>
+__device__ __forceinline__ Dual<2> cst<Dual<2>, double>(double x) { return mk<2>(x); }
+template <>
+__device__ __forceinline__ Dual<8> cst<Dual<8>, double>(double x) { return mk<8>(x); }
+
+// ---------------------------------------------------------------- fluxes
+// Euler flux through a face with unit normal n = (nx, ny): the state is
+// expressed in the face frame (normal, tangential velocity), the 1D flux
+// F^x is evaluated there and rotated back (Sec. 4.1, F^n = T^-1 F^x(T U)).
+template <typename T>
+__device__ __forceinline__ void euler_riemann(const T* UL, const T* UR, double nx, double ny,
+                                              double g, int hllc, T* F) {
+  const T one = cst<T>(1.0), half = cst<T>(0.5), zero = cst<T>(0.0);
+  const T gm1 = cst<T>(g - 1.0), gg = cst<T>(g);
+  const T tnx = cst<T>(nx), tny = cst<T>(ny);
+  // left / right primitive variables in the face frame
+  T rL = UL[0], rR = UR[0];
+  T unL = (UL[1] * tnx + UL[2] * tny) / rL;
+  T utL = (UL[2] * tnx - UL[1] * tny) / rL;
+  T unR = (UR[1] * tnx + UR[2] * tny) / rR;
+  T utR = (UR[2] * tnx - UR[1] * tny) / rR;
+  T EL = UL[3], ER = UR[3];
+  T pL = gm1 * (EL - half * rL * (unL * unL + utL * utL));
+  T pR = gm1 * (ER - half * rR * (unR * unR + utR * utR));
+  T cL = tsqrt(gg * pL / rL), cR = tsqrt(gg * pR / rR);
+  T HL = (EL + pL) / rL, HR = (ER + pR) / rR;
+  // Roe averages and Einfeldt wave speeds (Eq. wavespeed)
+  T D = tsqrt(rR / rL);
+  T den = one + D;
+  T ua = (unL + unR * D) / den;
+  T va = (utL + utR * D) / den;
+  T Ha = (HL + HR * D) / den;
+  T ca = tsqrt(gm1 * (Ha - half * (ua * ua + va * va)));
+  T SL = vmin(unL - cL, ua - ca);
+  T SR = vmax(unR + cR, ua + ca);
+  // 1D fluxes and conserved states in the face frame
+  T mL = rL * unL, mR = rR * unR;
+  T FL[4] = {mL, mL * unL + pL, mL * utL, unL * (EL + pL)};
+  T FR[4] = {mR, mR * unR + pR, mR * utR, unR * (ER + pR)};
+  T WL[4] = {rL, mL, rL * utL, EL};
+  T WR[4] = {rR, mR, rR * utR, ER};
+  T Fx[4];
+  if (val(SL) >= 0.0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Fx[k] = FL[k];
+  } else if (val(SR) <= 0.0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Fx[k] = FR[k];
+  } else if (!hllc) {
+    T inv = one / (SR - SL);
+    T sLR = SL * SR;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Fx[k] = (SR * FL[k] - SL * FR[k] + sLR * (WR[k] - WL[k])) * inv;
+  } else {
+    // HLLC: contact speed and star state of the side the face lies in
+    T aL = rL * (SL - unL), aR = rR * (SR - unR);
+    T Ss = (pR - pL + aL * unL - aR * unR) / (aL - aR);
+    bool left = val(Ss) >= 0.0;
+    T r = left ? rL : rR, un = left ? unL : unR, ut = left ? utL : utR;
+    T p = left ? pL : pR, S = left ? SL : SR, E = left ? EL : ER;
+    T f = r * (S - un) / (S - Ss);
+    T es = E / r + (Ss - un) * (Ss + p / (r * (S - un)));
+    T Us[4] = {f, f * Ss, f * ut, f * es};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Fx[k] = (left ? FL[k] : FR[k]) + S * (Us[k] - (left ? WL[k] : WR[k]));
+  }
+  (void)zero;
+  F[0] = Fx[0];
+  F[1] = Fx[1] * tnx - Fx[2] * tny;
+  F[2] = Fx[1] * tny + Fx[2] * tnx;
+  F[3] = Fx[3];
+}
+
+// ghost state of a boundary face point (tag: enum teno_bc)
+template <typename T>
+__device__ __forceinline__ void ghost_state(int tag, const T* UL, double nx, double ny, double x,
+                                            double time, double g, T* UR) {
+  if (tag == TENO_BC_WALL) {
+    T mn = UL[1] * cst<T>(nx) + UL[2] * cst<T>(ny);
+    UR[0] = UL[0];
+    UR[1] = UL[1] - cst<T>(2.0 * nx) * mn;
+    UR[2] = UL[2] - cst<T>(2.0 * ny) * mn;
+    UR[3] = UL[3];
+    return;
+  }
+  bool post = tag == TENO_BC_INFLOW;
+  if (tag == TENO_BC_TOP) post = x < 0.1667 + (1.0 + 20.0 * time) / 1.732;
+  if (tag == TENO_BC_INFLOW || tag == TENO_BC_TOP) {
+    double r = post ? 8.0 : 1.4, u = post ? 7.145 : 0.0, v = post ? -4.125 : 0.0;
+    double p = post ? 116.8333 : 1.0;
+    UR[0] = cst<T>(r);
+    UR[1] = cst<T>(r * u);
+    UR[2] = cst<T>(r * v);
+    UR[3] = cst<T>(p / (g - 1.0) + 0.5 * r * (u * u + v * v));
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) UR[k] = UL[k];
+}
+
+struct ReconArgs {
+  const void* ahat;
+  const int32_t* nbr;
+  const uint8_t* smask;
+  const double* U;
+  void* Uq;
+  uint8_t* sel_out;
+  const uint8_t* sel_in;
+  int64_t n_cell, n_pad;
+  double ct, eps;
+  int linear, e_entries;
+};
+
+// ------------------------------------------------------------ reconstruction
+// thread (lane, v, z): cell tile*32 + lane, variable v.  A warp covers the 32
+// cells of one tile for one variable, so every matrix entry is one coalesced
+// 256-byte (FP64) row; the other variables' warps hit it in L1.
+template <int M, int NS, int NQ, int NV, typename TA>
+__global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const EvalTable ev) {
+  const int lane = threadIdx.x, v = threadIdx.y;
+  const int64_t tile = (int64_t)blockIdx.x * blockDim.z + threadIdx.z;
+  const int64_t c = tile * kTile + lane;
+  if (c >= a.n_cell) return;
+  constexpr int E = M * NS + kSmallEntries;
+  constexpr int SL = NS + kSmallSlots;
+  const double* __restrict__ Uv = a.U + (int64_t)v * a.n_pad;
+  const double u0 = Uv[c];
+  const TA* __restrict__ A = reinterpret_cast<const TA*>(a.ahat) + tile * (int64_t)E * kTile + lane;
+  const int32_t* __restrict__ nb = a.nbr + tile * (int64_t)SL * kTile + lane;
+
+  // large stencil: a' = A'' d  (d_s = U_s - U_0)
+  TA acc[M];
+#pragma unroll
+  for (int l = 0; l < M; ++l) acc[l] = TA(0);
+#pragma unroll 2
+  for (int s = 0; s < NS; ++s) {
+    const int j = __ldg(nb + s * kTile);
+    const TA d = TA(__ldg(Uv + j) - u0);
+    const TA* As = A + (int64_t)s * M * kTile;
+#pragma unroll
+    for (int l = 0; l < M; ++l) acc[l] = fma(__ldg(As + l * kTile), d, acc[l]);
+  }
+  // directional stencils
+  TA as[kSmallK][kSmallM];
+#pragma unroll
+  for (int k = 0; k < kSmallK; ++k) {
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) as[k][l] = TA(0);
+#pragma unroll 2
+    for (int s = 0; s < kSmallN; ++s) {
+      const int j = __ldg(nb + (NS + k * kSmallN + s) * kTile);
+      const TA d = TA(__ldg(Uv + j) - u0);
+      const TA* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) as[k][l] = fma(__ldg(As + l * kTile), d, as[k][l]);
+    }
+  }
+  // smoothness indicators in FP64 (orthonormal basis: beta = |a'|^2)
+  double beta[kSmallK + 1];
+  {
+    double b = 0.0;
+#pragma unroll
+    for (int l = 0; l < M; ++l) b = fma((double)acc[l], (double)acc[l], b);
+    beta[kSmallK] = b;
+#pragma unroll
+    for (int k = 0; k < kSmallK; ++k) {
+      double s = 0.0;
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) s = fma((double)as[k][l], (double)as[k][l], s);
+      beta[k] = s;
+    }
+  }
+  const int present = a.smask[c];
+  uint8_t sel;
+  if (a.sel_in) {
+    sel = a.sel_in[(int64_t)v * a.n_pad + c];
+  } else if (a.linear) {
+    sel = 8;
+  } else {
+    // gamma_k = (beta_k + eps)^-6, chi_k = gamma_k / sum gamma, keep chi_k >= C_T
+    double g[kSmallK + 1], S = 0.0;
+#pragma unroll
+    for (int k = 0; k <= kSmallK; ++k) {
+      bool pr = k == kSmallK || ((present >> k) & 1);
+      double ib = 1.0 / (beta[k] + a.eps);
+      double i2 = ib * ib;
+      g[k] = pr ? i2 * i2 * i2 : 0.0;
+      S += g[k];
+    }
+    if (g[kSmallK] >= a.ct * S) {
+      sel = 8;
+    } else {
+      double S2 = g[0] + g[1] + g[2];
+      sel = 0;
+#pragma unroll
+      for (int k = 0; k < kSmallK; ++k)
+        if (((present >> k) & 1) && g[k] >= a.ct * S2) sel |= (uint8_t)(1u << k);
+    }
+  }
+  if (a.sel_out) a.sel_out[(int64_t)v * a.n_pad + c] = sel;
+  // final polynomial coefficients
+  TA cf[M];
+  if (sel & 8) {
+#pragma unroll
+    for (int l = 0; l < M; ++l) cf[l] = acc[l];
+  } else {
+    int nd = (sel & 1) + ((sel >> 1) & 1) + ((sel >> 2) & 1);
+    TA w = nd ? TA(1.0) / TA(nd) : TA(0);
+#pragma unroll
+    for (int l = 0; l < M; ++l) cf[l] = TA(0);
+#pragma unroll
+    for (int k = 0; k < kSmallK; ++k) {
+      TA wk = ((sel >> k) & 1) ? w : TA(0);
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) cf[l] = fma(wk, as[k][l], cf[l]);
+    }
+  }
+  // values at the 3*NQ edge Gauss points: U_0 + Psi' c'
+  TA* __restrict__ out = reinterpret_cast<TA*>(a.Uq) + c * (3 * NQ * NV) + v;
+#pragma unroll
+  for (int p = 0; p < 3 * NQ; ++p) {
+    TA s = TA(0);
+#pragma unroll
+    for (int l = 0; l < M; ++l) s = fma(cf[l], TA(ev.psi[p * kMaxM + l]), s);
+    out[p * NV] = TA(u0 + (double)s);
+  }
+}
+
+// ------------------------------------------------------------------ fluxes
+struct FaceArgs {
+  const int32_t* f_cells;
+  const int8_t* f_edges;
+  const double* f_geom;
+  int64_t n_face;
+  double gamma, adv_x, adv_y, time;
+  double gw[kMaxNq], gt[kMaxNq];
+};
+
+template <int NV, int NQ, int FLUX, typename T>
+__global__ void __launch_bounds__(256) face_flux_kernel(const FaceArgs a, const T* __restrict__ Uq,
+                                                        T* __restrict__ K) {
+  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= a.n_face) return;
+  const int o = a.f_cells[2 * f], n = a.f_cells[2 * f + 1];
+  const int eo = a.f_edges[2 * f], en = a.f_edges[2 * f + 1];
+  const double nx = a.f_geom[5 * f], ny = a.f_geom[5 * f + 1], len = a.f_geom[5 * f + 2];
+  T acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = T(0);
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    T UL[NV], UR[NV], F[NV];
+    const T* pl = Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) UL[v] = pl[v];
+    if (n >= 0) {
+      const T* pr = Uq + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) UR[v] = pr[v];
+    } else if constexpr (NV == 4) {
+      double x = a.f_geom[5 * f + 3] - ny * len * a.gt[k];
+      ghost_state<T>(en, UL, nx, ny, x, a.time, a.gamma, UR);
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) UR[v] = UL[v];
+    }
+    if constexpr (NV == 1) {
+      const double an = a.adv_x * nx + a.adv_y * ny;
+      F[0] = T(an) * (an >= 0.0 ? UL[0] : UR[0]);
+    } else {
+      euler_riemann<T>(UL, UR, nx, ny, a.gamma, FLUX == TENO_FLUX_HLLC, F);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = fma(T(a.gw[k]), F[v], acc[v]);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) K[f * NV + v] = acc[v] * T(len);
+}
+
+// ------------------------------------------------------------------ gather
+struct GatherArgs {
+  const int32_t* c_faces;
+  const double* inv_area;
+  int64_t n_cell, n_pad;
+  double gamma;
+};
+
+template <int NV, typename TK>
+__global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a, const TK* __restrict__ K,
+                                                     const double* __restrict__ Un,
+                                                     const double* __restrict__ Us,
+                                                     double* __restrict__ out, int mode, double cn,
+                                                     double cs, double dt_fixed, double cfl,
+                                                     const double* __restrict__ max_lam,
+                                                     int* flag) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= a.n_cell) return;
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const int cf = a.c_faces[3 * c + e];
+    const int64_t f = cf >> 1;
+    const double s = (cf & 1) ? -1.0 : 1.0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = fma(s, (double)K[f * NV + v], acc[v]);
+  }
+  const double ia = a.inv_area[c];
+  if (mode == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v * a.n_pad + c] = -acc[v] * ia;
+    return;
+  }
+  const double dt = max_lam ? cfl / *max_lam : dt_fixed;
+  double u[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int64_t i = v * a.n_pad + c;
+    u[v] = cn * Un[i] + cs * (Us[i] - dt * acc[v] * ia);
+    out[i] = u[v];
+  }
+  if constexpr (NV == 4) {
+    const double rho = u[0];
+    const double p = (a.gamma - 1.0) * (u[3] - 0.5 * (u[1] * u[1] + u[2] * u[2]) / rho);
+    if (!(rho > 0.0) || !(p > 0.0)) atomicOr(flag, 1);
+  } else {
+    if (!(u[0] == u[0])) atomicOr(flag, 1);
+  }
+}
+
+// --------------------------------------------------------------- CFL speed
+template <int NV>
+__global__ void __launch_bounds__(256) max_lambda_kernel(const double* __restrict__ U,
+                                                         const double* __restrict__ cfl_len,
+                                                         int64_t n_cell, int64_t n_pad,
+                                                         double gamma, double adv_speed,
+                                                         unsigned long long* out) {
+  double lam = 0.0;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    double s;
+    if constexpr (NV == 1) {
+      s = adv_speed;
+    } else {
+      const double rho = U[c], u = U[n_pad + c] / rho, v = U[2 * n_pad + c] / rho;
+      const double p = (gamma - 1.0) * (U[3 * n_pad + c] - 0.5 * rho * (u * u + v * v));
+      s = sqrt(u * u + v * v) + sqrt(gamma * p / rho);
+    }
+    lam = fmax(lam, s / cfl_len[c]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+  __shared__ double red[32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = lam;
+  __syncthreads();
+  if (w == 0) {
+    lam = l < (int)(blockDim.x >> 5) ? red[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+    // non-negative doubles order like their bit patterns
+    if (l == 0) atomicMax(out, (unsigned long long)__double_as_longlong(lam));
+  }
+}
+
+// -------------------------------------------------------------- utilities
+__global__ void permute_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                               const int32_t* __restrict__ perm, int64_t n, int64_t ld_src,
+                               int64_t ld_dst, int to_user) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (i >= n) return;
+  const int64_t u = perm[i];
+  if (to_user)
+    dst[v * ld_dst + u] = src[v * ld_src + i];
+  else
+    dst[v * ld_dst + i] = src[v * ld_src + u];
+}
+
+__global__ void permute_u8_kernel(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst,
+                                  const int32_t* __restrict__ perm, int64_t n, int64_t ld_src,
+                                  int64_t ld_dst, int to_user) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (i >= n) return;
+  const int64_t u = perm[i];
+  if (to_user)
+    dst[v * ld_dst + u] = src[v * ld_src + i];
+  else
+    dst[v * ld_dst + i] = src[v * ld_src + u];
+}
+
+__global__ void axpby_kernel(double* out, const double* a, double ca, const double* b, double cb,
+                             int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = ca * a[i] + cb * b[i];
+}
+
+// ------------------------------------------------------------------ adjoint
+struct VjpArgs {
+  const int32_t* f_cells;
+  const int8_t* f_edges;
+  const double* f_geom;
+  const double* inv_area;
+  int64_t n_face, n_pad;
+  double gamma, adv_x, adv_y, time;
+  double gw[kMaxNq], gt[kMaxNq];
+};
+
+// Uq_bar[(c,edge,q)] = w_q |A| (dF/dU_side)^T Kbar with Kbar = dJ/dK_f
+// (R_o has -K/|V_o|, R_n has +K/|V_n|); every Gauss slot of every cell is
+// written by exactly one face.
+template <int NV, int NQ, int FLUX>
+__global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
+                                                            const double* __restrict__ Uq,
+                                                            const double* __restrict__ w,
+                                                            double* __restrict__ Uq_bar) {
+  constexpr int ND = 2 * NV;
+  using D = Dual<ND>;
+  const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= a.n_face) return;
+  const int o = a.f_cells[2 * f], n = a.f_cells[2 * f + 1];
+  const int eo = a.f_edges[2 * f], en = a.f_edges[2 * f + 1];
+  const double nx = a.f_geom[5 * f], ny = a.f_geom[5 * f + 1], len = a.f_geom[5 * f + 2];
+  double Kb[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    Kb[v] = -w[v * a.n_pad + o] * a.inv_area[o];
+    if (n >= 0) Kb[v] += w[v * a.n_pad + n] * a.inv_area[n];
+  }
+  for (int k = 0; k < NQ; ++k) {
+    D UL[NV], UR[NV], F[NV];
+    const double* pl = Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      UL[v] = mk<ND>(pl[v]);
+      UL[v].d[v] = 1.0;
+    }
+    if (n >= 0) {
+      const double* pr = Uq + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        UR[v] = mk<ND>(pr[v]);
+        UR[v].d[NV + v] = 1.0;
+      }
+    } else if constexpr (NV == 4) {
+      double x = a.f_geom[5 * f + 3] - ny * len * a.gt[k];
+      ghost_state<D>(en, UL, nx, ny, x, a.time, a.gamma, UR);
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) UR[v] = UL[v];
+    }
+    if constexpr (NV == 1) {
+      const double an = a.adv_x * nx + a.adv_y * ny;
+      F[0] = an * (an >= 0.0 ? UL[0] : UR[0]);
+    } else {
+      euler_riemann<D>(UL, UR, nx, ny, a.gamma, FLUX == TENO_FLUX_HLLC, F);
+    }
+    const double wk = a.gw[k] * len;
+    double* bl = Uq_bar + ((int64_t)(o * 3 + eo) * NQ + k) * NV;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) s = fma(F[i].d[j], Kb[i], s);
+      bl[j] = wk * s;
+    }
+    if (n >= 0) {
+      double* br = Uq_bar + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV;
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) s = fma(F[i].d[NV + j], Kb[i], s);
+        br[j] = wk * s;
+      }
+    }
+  }
+}
+
+// d_bar[tile][slot][v][32] = (A''^T abar)_slot with abar = w_k Psi'^T Uq_bar
+// (selection frozen); u_self = sum_p Uq_bar - sum_slot d_bar (dU_0 terms).
+template <int M, int NS, int NQ, int NV>
+__global__ void __launch_bounds__(128) recon_vjp_kernel(const double* __restrict__ ahat,
+                                                        const uint8_t* __restrict__ sel_in,
+                                                        const double* __restrict__ Uq_bar,
+                                                        double* __restrict__ d_bar,
+                                                        double* __restrict__ u_self,
+                                                        int64_t n_cell, int64_t n_pad,
+                                                        const EvalTable ev) {
+  const int lane = threadIdx.x, v = threadIdx.y;
+  const int64_t tile = (int64_t)blockIdx.x * blockDim.z + threadIdx.z;
+  const int64_t c = tile * kTile + lane;
+  if (c >= n_cell) return;
+  constexpr int E = M * NS + kSmallEntries;
+  constexpr int SL = NS + kSmallSlots;
+  const double* A = ahat + tile * (int64_t)E * kTile + lane;
+  double* db = d_bar + tile * (int64_t)SL * NV * kTile + v * kTile + lane;
+  double cb[M];
+#pragma unroll
+  for (int l = 0; l < M; ++l) cb[l] = 0.0;
+  double u0b = 0.0;
+  const double* ub = Uq_bar + c * (3 * NQ * NV) + v;
+#pragma unroll
+  for (int p = 0; p < 3 * NQ; ++p) {
+    const double b = ub[p * NV];
+    u0b += b;
+#pragma unroll
+    for (int l = 0; l < M; ++l) cb[l] = fma(b, ev.psi[p * kMaxM + l], cb[l]);
+  }
+  const uint8_t sel = sel_in[(int64_t)v * n_pad + c];
+  double tot = 0.0;
+  const bool large = sel & 8;
+#pragma unroll 2
+  for (int s = 0; s < NS; ++s) {
+    double t = 0.0;
+    if (large) {
+#pragma unroll
+      for (int l = 0; l < M; ++l) t = fma(A[(int64_t)(s * M + l) * kTile], cb[l], t);
+    }
+    db[(int64_t)s * NV * kTile] = t;
+    tot += t;
+  }
+  const int nd = (sel & 1) + ((sel >> 1) & 1) + ((sel >> 2) & 1);
+  const double w = (!large && nd) ? 1.0 / nd : 0.0;
+#pragma unroll
+  for (int k = 0; k < kSmallK; ++k) {
+    const double wk = ((sel >> k) & 1) ? w : 0.0;
+    for (int s = 0; s < kSmallN; ++s) {
+      double t = 0.0;
+      if (wk != 0.0) {
+        const double* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
+#pragma unroll
+        for (int l = 0; l < kSmallM; ++l) t = fma(As[l * kTile], cb[l], t);
+        t *= wk;
+      }
+      db[(int64_t)(NS + k * kSmallN + s) * NV * kTile] = t;
+      tot += t;
+    }
+  }
+  u_self[(int64_t)v * n_pad + c] = u0b - tot;
+}
+
+// v[j] = u_self[j] + sum over the stencil slots that hold cell j
+template <int NV>
+__global__ void __launch_bounds__(256) scatter_gather_kernel(const int64_t* __restrict__ rev_off,
+                                                             const int64_t* __restrict__ rev_idx,
+                                                             const double* __restrict__ d_bar,
+                                                             const double* __restrict__ u_self,
+                                                             double* __restrict__ out,
+                                                             int64_t n_cell, int64_t n_pad) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_cell) return;
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = u_self[v * n_pad + j];
+  for (int64_t r = rev_off[j]; r < rev_off[j + 1]; ++r) {
+    const int64_t base = rev_idx[r];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] += d_bar[base + v * kTile];
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[v * n_pad + j] = acc[v];
+}
+
+template <typename F>
+cudaError_t dispatch_order(int order, F&& f) {
+  switch (order) {
+    case 3: return f(std::integral_constant<int, 5>{}, std::integral_constant<int, 12>{});
+    case 4: return f(std::integral_constant<int, 9>{}, std::integral_constant<int, 20>{});
+    case 5: return f(std::integral_constant<int, 14>{}, std::integral_constant<int, 30>{});
+    case 6: return f(std::integral_constant<int, 20>{}, std::integral_constant<int, 42>{});
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_recon(const DeviceMesh& dm, const double* U, void* Uq, uint8_t* sel_out,
+                         const uint8_t* sel_in, cudaStream_t st) {
+  ReconArgs a;
+  a.ahat = dm.ahat;
+  a.nbr = dm.nbr;
+  a.smask = dm.smask;
+  a.U = U;
+  a.Uq = Uq;
+  a.sel_out = sel_out;
+  a.sel_in = sel_in;
+  a.n_cell = dm.n_cell;
+  a.n_pad = dm.n_pad;
+  a.ct = dm.ct;
+  a.eps = dm.eps;
+  a.linear = dm.linear;
+  a.e_entries = dm.e_entries;
+  const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
+  return dispatch_order(dm.order, [&](auto Mc, auto NSc) -> cudaError_t {
+    constexpr int M = decltype(Mc)::value, NS = decltype(NSc)::value;
+    auto go = [&](auto nqc, auto nvc) -> cudaError_t {
+      constexpr int NQ = decltype(nqc)::value, NV = decltype(nvc)::value;
+      constexpr int TZ = 4 / NV;  // 128 threads per block
+      dim3 block(kTile, NV, TZ);
+      dim3 grid((unsigned)((tiles + TZ - 1) / TZ));
+      if (dm.precision == TENO_FP64)
+        recon_kernel<M, NS, NQ, NV, double><<<grid, block, 0, st>>>(a, dm.eval);
+      else
+        recon_kernel<M, NS, NQ, NV, float><<<grid, block, 0, st>>>(a, dm.eval);
+      return cudaGetLastError();
+    };
+    constexpr int NQd = (M <= 9) ? 2 : 3;
+    if (dm.nq != NQd) return cudaErrorInvalidValue;
+    if (dm.n_var == 1) return go(std::integral_constant<int, NQd>{}, std::integral_constant<int, 1>{});
+    return go(std::integral_constant<int, NQd>{}, std::integral_constant<int, 4>{});
+  });
+}
+
+static FaceArgs face_args(const DeviceMesh& dm, double time) {
+  FaceArgs a;
+  a.f_cells = dm.f_cells;
+  a.f_edges = dm.f_edges;
+  a.f_geom = dm.f_geom;
+  a.n_face = dm.n_face;
+  a.gamma = dm.gamma;
+  a.adv_x = dm.adv_x;
+  a.adv_y = dm.adv_y;
+  a.time = time;
+  for (int k = 0; k < kMaxNq; ++k) {
+    a.gw[k] = dm.gw[k];
+    a.gt[k] = dm.gt[k];
+  }
+  return a;
+}
+
+cudaError_t launch_face_flux(const DeviceMesh& dm, const void* Uq, void* K, double time,
+                             cudaStream_t st) {
+  FaceArgs a = face_args(dm, time);
+  const unsigned grid = (unsigned)((dm.n_face + 255) / 256);
+  auto go = [&](auto nvc, auto nqc, auto flc) -> cudaError_t {
+    constexpr int NV = decltype(nvc)::value, NQ = decltype(nqc)::value,
+                  FL = decltype(flc)::value;
+    if (dm.precision == TENO_FP64)
+      face_flux_kernel<NV, NQ, FL, double><<<grid, 256, 0, st>>>(
+          a, (const double*)Uq, (double*)K);
+    else
+      face_flux_kernel<NV, NQ, FL, float><<<grid, 256, 0, st>>>(a, (const float*)Uq, (float*)K);
+    return cudaGetLastError();
+  };
+  using I1 = std::integral_constant<int, 1>;
+  using I2 = std::integral_constant<int, 2>;
+  using I3 = std::integral_constant<int, 3>;
+  using I4 = std::integral_constant<int, 4>;
+  using F0 = std::integral_constant<int, TENO_FLUX_UPWIND>;
+  using F1 = std::integral_constant<int, TENO_FLUX_HLL>;
+  using F2 = std::integral_constant<int, TENO_FLUX_HLLC>;
+  if (dm.n_var == 1) return dm.nq == 2 ? go(I1{}, I2{}, F0{}) : go(I1{}, I3{}, F0{});
+  if (dm.flux == TENO_FLUX_HLL) return dm.nq == 2 ? go(I4{}, I2{}, F1{}) : go(I4{}, I3{}, F1{});
+  return dm.nq == 2 ? go(I4{}, I2{}, F2{}) : go(I4{}, I3{}, F2{});
+}
+
+cudaError_t launch_gather(const DeviceMesh& dm, const void* K, const double* Un, const double* Us,
+                          double* out, int mode, double cn, double cs, double dt_fixed,
+                          const double* max_lam, int* flag, cudaStream_t st) {
+  GatherArgs a{dm.c_faces, dm.inv_area, dm.n_cell, dm.n_pad, dm.gamma};
+  const unsigned grid = (unsigned)((dm.n_cell + 255) / 256);
+  if (dm.n_var == 1) {
+    if (dm.precision == TENO_FP64)
+      gather_kernel<1, double><<<grid, 256, 0, st>>>(a, (const double*)K, Un, Us, out, mode, cn,
+                                                     cs, dt_fixed, dm.cfl, max_lam, flag);
+    else
+      gather_kernel<1, float><<<grid, 256, 0, st>>>(a, (const float*)K, Un, Us, out, mode, cn, cs,
+                                                    dt_fixed, dm.cfl, max_lam, flag);
+  } else {
+    if (dm.precision == TENO_FP64)
+      gather_kernel<4, double><<<grid, 256, 0, st>>>(a, (const double*)K, Un, Us, out, mode, cn,
+                                                     cs, dt_fixed, dm.cfl, max_lam, flag);
+    else
+      gather_kernel<4, float><<<grid, 256, 0, st>>>(a, (const float*)K, Un, Us, out, mode, cn, cs,
+                                                    dt_fixed, dm.cfl, max_lam, flag);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max_lambda(const DeviceMesh& dm, const double* U, double* max_lam,
+                              cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(max_lam, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  int64_t blocks = (dm.n_cell + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  const double adv = sqrt(dm.adv_x * dm.adv_x + dm.adv_y * dm.adv_y);
+  if (dm.n_var == 1)
+    max_lambda_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(
+        U, dm.cfl_len, dm.n_cell, dm.n_pad, dm.gamma, adv, (unsigned long long*)max_lam);
+  else
+    max_lambda_kernel<4><<<(unsigned)blocks, 256, 0, st>>>(
+        U, dm.cfl_len, dm.n_cell, dm.n_pad, dm.gamma, adv, (unsigned long long*)max_lam);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute(const double* src, double* dst, const int32_t* perm, int64_t n,
+                           int64_t ld_src, int64_t ld_dst, int n_var, int to_user,
+                           cudaStream_t st) {
+  dim3 grid((unsigned)((n + 255) / 256), n_var);
+  permute_kernel<<<grid, 256, 0, st>>>(src, dst, perm, n, ld_src, ld_dst, to_user);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute_u8(const uint8_t* src, uint8_t* dst, const int32_t* perm, int64_t n,
+                              int64_t ld_src, int64_t ld_dst, int n_var, int to_user,
+                              cudaStream_t st) {
+  dim3 grid((unsigned)((n + 255) / 256), n_var);
+  permute_u8_kernel<<<grid, 256, 0, st>>>(src, dst, perm, n, ld_src, ld_dst, to_user);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(double* out, const double* a, double ca, const double* b, double cb,
+                         int64_t n, cudaStream_t st) {
+  axpby_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(out, a, ca, b, cb, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const double* w,
+                                 double* Uq_bar, double time, cudaStream_t st) {
+  VjpArgs a;
+  a.f_cells = dm.f_cells;
+  a.f_edges = dm.f_edges;
+  a.f_geom = dm.f_geom;
+  a.inv_area = dm.inv_area;
+  a.n_face = dm.n_face;
+  a.n_pad = dm.n_pad;
+  a.gamma = dm.gamma;
+  a.adv_x = dm.adv_x;
+  a.adv_y = dm.adv_y;
+  a.time = time;
+  for (int k = 0; k < kMaxNq; ++k) {
+    a.gw[k] = dm.gw[k];
+    a.gt[k] = dm.gt[k];
+  }
+  const unsigned grid = (unsigned)((dm.n_face + 127) / 128);
+  const double* U = (const double*)Uq;
+  if (dm.n_var == 1) {
+    if (dm.nq == 2)
+      face_flux_vjp_kernel<1, 2, TENO_FLUX_UPWIND><<<grid, 128, 0, st>>>(a, U, w, Uq_bar);
+    else
+      face_flux_vjp_kernel<1, 3, TENO_FLUX_UPWIND><<<grid, 128, 0, st>>>(a, U, w, Uq_bar);
+  } else if (dm.flux == TENO_FLUX_HLL) {
+    if (dm.nq == 2)
+      face_flux_vjp_kernel<4, 2, TENO_FLUX_HLL><<<grid, 128, 0, st>>>(a, U, w, Uq_bar);
+    else
+      face_flux_vjp_kernel<4, 3, TENO_FLUX_HLL><<<grid, 128, 0, st>>>(a, U, w, Uq_bar);
+  } else {
+    if (dm.nq == 2)
+      face_flux_vjp_kernel<4, 2, TENO_FLUX_HLLC><<<grid, 128, 0, st>>>(a, U, w, Uq_bar);
+    else
+      face_flux_vjp_kernel<4, 3, TENO_FLUX_HLLC><<<grid, 128, 0, st>>>(a, U, w, Uq_bar);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recon_vjp(const DeviceMesh& dm, const uint8_t* sel, const double* Uq_bar,
+                             double* d_bar, double* u_self, cudaStream_t st) {
+  const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
+  return dispatch_order(dm.order, [&](auto Mc, auto NSc) -> cudaError_t {
+    constexpr int M = decltype(Mc)::value, NS = decltype(NSc)::value;
+    constexpr int NQ = (M <= 9) ? 2 : 3;
+    if (dm.nq != NQ) return cudaErrorInvalidValue;
+    if (dm.n_var == 1) {
+      dim3 block(kTile, 1, 4);
+      recon_vjp_kernel<M, NS, NQ, 1><<<(unsigned)((tiles + 3) / 4), block, 0, st>>>(
+          (const double*)dm.ahat, sel, Uq_bar, d_bar, u_self, dm.n_cell, dm.n_pad, dm.eval);
+    } else {
+      dim3 block(kTile, 4, 1);
+      recon_vjp_kernel<M, NS, NQ, 4><<<(unsigned)tiles, block, 0, st>>>(
+          (const double*)dm.ahat, sel, Uq_bar, d_bar, u_self, dm.n_cell, dm.n_pad, dm.eval);
+    }
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_scatter_gather(const DeviceMesh& dm, const int64_t* rev_off,
+                                  const int64_t* rev_idx, const double* d_bar,
+                                  const double* u_self, double* v, cudaStream_t st) {
+  const unsigned grid = (unsigned)((dm.n_cell + 255) / 256);
+  if (dm.n_var == 1)
+    scatter_gather_kernel<1><<<grid, 256, 0, st>>>(rev_off, rev_idx, d_bar, u_self, v, dm.n_cell,
+                                                   dm.n_pad);
+  else
+    scatter_gather_kernel<4><<<grid, 256, 0, st>>>(rev_off, rev_idx, d_bar, u_self, v, dm.n_cell,
+                                                   dm.n_pad);
+  return cudaGetLastError();
+}
+
+}  // namespace teno

@@ -1,0 +1,285 @@
+"""Thin ctypes binding of libteno.so (C ABI in include/teno.h).
+
+Argument marshalling only: every step of the residual, the RK3 update and the
+adjoint runs in the CUDA library.  Arrays may be numpy arrays (host) or torch
+tensors (host or CUDA; CUDA tensors are passed as device pointers and use the
+current torch stream).  There is no fallback: if the library is missing or
+was not built, `lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+TENO_OK, TENO_EINVAL, TENO_ENOMEM, TENO_ECUDA = 0, -1, -2, -3
+TENO_EMESH, TENO_ESTENCIL, TENO_ENONPHYS, TENO_ETIMEOUT, TENO_ESTATE = -4, -5, -6, -7, -8
+FLUX_UPWIND, FLUX_HLL, FLUX_HLLC = 0, 1, 2
+FP64, FP32_MIXED = 0, 1
+SEL_LARGE = 8
+
+_NAMES = {0: "TENO_OK", -1: "TENO_EINVAL", -2: "TENO_ENOMEM", -3: "TENO_ECUDA", -4: "TENO_EMESH",
+          -5: "TENO_ESTENCIL", -6: "TENO_ENONPHYS", -7: "TENO_ETIMEOUT", -8: "TENO_ESTATE"}
+
+
+class TenoError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class teno_params(C.Structure):
+    _fields_ = [("order", C.c_int32), ("n_var", C.c_int32), ("flux", C.c_int32),
+                ("precision", C.c_int32), ("linear", C.c_int32), ("nq", C.c_int32),
+                ("ct", C.c_double), ("eps", C.c_double), ("gamma", C.c_double),
+                ("adv_x", C.c_double), ("adv_y", C.c_double), ("cfl", C.c_double)]
+
+
+_lib = None
+_vp = C.c_void_p
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = False):
+    """Load libteno.so; raises if it is not built (no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libteno.so not built at {path}; run __graft_entry__.build()")
+    L = C.CDLL(path)
+    sig = {
+        "teno_default_params": (None, [_vp]),
+        "teno_create": (C.c_int, [C.POINTER(_vp), C.c_int, _vp]),
+        "teno_destroy": (C.c_int, [_vp]),
+        "teno_last_error": (C.c_char_p, [_vp]),
+        "teno_set_stream": (C.c_int, [_vp, _vp]),
+        "teno_mesh_load": (C.c_int, [_vp, C.c_int64, _vp, C.c_int64, _vp, C.c_int64, _vp, _vp]),
+        "teno_get_permutation": (C.c_int, [_vp, _vp]),
+        "teno_precompute_stencils": (C.c_int, [_vp, _vp]),
+        "teno_get_stencils": (C.c_int, [_vp, _vp, _vp]),
+        "teno_get_sizes": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+        "teno_set_state": (C.c_int, [_vp, _vp, C.c_int]),
+        "teno_get_state": (C.c_int, [_vp, _vp, C.c_int]),
+        "teno_set_time": (C.c_int, [_vp, C.c_double]),
+        "teno_residual": (C.c_int, [_vp, _vp, _vp, C.c_int]),
+        "teno_set_selection_override": (C.c_int, [_vp, _vp, C.c_int]),
+        "teno_cfl_dt": (C.c_int, [_vp, _vp]),
+        "teno_rk3_step": (C.c_int, [_vp, C.c_double, _vp]),
+        "teno_rk3_steps": (C.c_int, [_vp, C.c_int32, C.c_double]),
+        "teno_check_state": (C.c_int, [_vp]),
+        "teno_residual_vjp": (C.c_int, [_vp, _vp, _vp, C.c_int]),
+        "teno_adjoint_step": (C.c_int, [_vp, C.c_double, _vp, _vp, C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """(address, on_device) of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), int(a.is_cuda)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            return None
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def default_params(**kw) -> teno_params:
+    p = teno_params()
+    lib().teno_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "adv":
+            p.adv_x, p.adv_y = float(v[0]), float(v[1])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Teno:
+    """One library context: a mesh, a scheme and a state on one GPU.
+
+    device=-1 creates a host-only context (mesh and stencil preprocessing)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._h = _vp()
+        self.device = device
+        rc = lib().teno_create(C.byref(self._h), device,
+                               _stream_handle(stream) if device >= 0 else None)
+        if rc != 0:
+            raise TenoError(rc, "teno_create failed")
+        self.n_cell = 0
+        self.n_var = 0
+
+    def close(self):
+        if self._h:
+            lib().teno_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc: int):
+        if rc != 0:
+            raise TenoError(rc, lib().teno_last_error(self._h).decode())
+
+    def set_stream(self, stream):
+        self._chk(lib().teno_set_stream(self._h, _stream_handle(stream)))
+
+    # -- mesh and precompute
+    def mesh_load(self, xy, tri, bface=None, period=None):
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        nb = 0
+        bp = None
+        if bface is not None and len(bface):
+            bface = np.ascontiguousarray(bface, dtype=np.int32)
+            nb, bp = bface.shape[0], bface.ctypes.data
+        per = None if period is None else np.ascontiguousarray(period, dtype=np.float64)
+        self._chk(lib().teno_mesh_load(self._h, xy.shape[0], xy.ctypes.data, tri.shape[0],
+                                       tri.ctypes.data, nb, bp,
+                                       None if per is None else per.ctypes.data))
+        self.n_cell = tri.shape[0]
+        return self
+
+    def load(self, mesh):
+        return self.mesh_load(mesh.xy, mesh.tri, mesh.bface, mesh.period)
+
+    def precompute_stencils(self, params: teno_params | None = None, **kw):
+        p = params if params is not None else default_params(**kw)
+        self._chk(lib().teno_precompute_stencils(self._h, C.byref(p)))
+        self.params = p
+        self.n_var = p.n_var
+        n = C.c_int64()
+        nv, m, ns = C.c_int32(), C.c_int32(), C.c_int32()
+        self._chk(lib().teno_get_sizes(self._h, C.byref(n), C.byref(nv), C.byref(m),
+                                       C.byref(ns)))
+        self.m, self.ns = m.value, ns.value
+        return self
+
+    def permutation(self):
+        out = np.empty(self.n_cell, dtype=np.int32)
+        self._chk(lib().teno_get_permutation(self._h, out.ctypes.data))
+        return out
+
+    def stencils(self):
+        large = np.empty((self.n_cell, self.ns), dtype=np.int32)
+        small = np.empty((self.n_cell, 3, 12), dtype=np.int32)
+        self._chk(lib().teno_get_stencils(self._h, large.ctypes.data, small.ctypes.data))
+        return large, small
+
+    # -- state
+    def set_state(self, U):
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.float64)
+        p, dev = _ptr(U)
+        self._chk(lib().teno_set_state(self._h, p, dev))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty((self.n_var, self.n_cell))
+        p, dev = _ptr(out)
+        self._chk(lib().teno_get_state(self._h, p, dev))
+        return out
+
+    def set_time(self, t: float):
+        self._chk(lib().teno_set_time(self._h, float(t)))
+
+    # -- compute
+    def residual(self, out=None, sel=None, want_sel: bool = False):
+        """R [n_var][n_cell] of the current state; returns (R, sel or None)."""
+        if out is None:
+            out = np.empty((self.n_var, self.n_cell))
+            if want_sel and sel is None:
+                sel = np.empty((self.n_var, self.n_cell), dtype=np.uint8)
+        p, dev = _ptr(out)
+        sp, sdev = _ptr(sel)
+        if sel is not None and sdev != dev:
+            raise ValueError("R and sel must both be host or both be device arrays")
+        self._chk(lib().teno_residual(self._h, p, sp, dev))
+        return out, sel
+
+    def set_selection_override(self, sel=None):
+        if sel is None:
+            self._chk(lib().teno_set_selection_override(self._h, None, 0))
+            return
+        if isinstance(sel, np.ndarray):
+            sel = np.ascontiguousarray(sel, dtype=np.uint8)
+        p, dev = _ptr(sel)
+        self._chk(lib().teno_set_selection_override(self._h, p, dev))
+
+    def cfl_dt(self) -> float:
+        dt = C.c_double()
+        self._chk(lib().teno_cfl_dt(self._h, C.byref(dt)))
+        return dt.value
+
+    def rk3_step(self, dt: float = 0.0, sync: bool = True) -> float | None:
+        if sync:
+            used = C.c_double()
+            self._chk(lib().teno_rk3_step(self._h, float(dt), C.byref(used)))
+            return used.value
+        self._chk(lib().teno_rk3_step(self._h, float(dt), None))
+        return None
+
+    def rk3_steps(self, n: int, dt: float = 0.0):
+        self._chk(lib().teno_rk3_steps(self._h, int(n), float(dt)))
+
+    def check_state(self):
+        self._chk(lib().teno_check_state(self._h))
+
+    def residual_vjp(self, w, out=None):
+        if isinstance(w, np.ndarray):
+            w = np.ascontiguousarray(w, dtype=np.float64)
+        if out is None:
+            out = np.empty((self.n_var, self.n_cell))
+        wp, wdev = _ptr(w)
+        op, odev = _ptr(out)
+        if wdev != odev:
+            raise ValueError("w and out must both be host or both be device arrays")
+        self._chk(lib().teno_residual_vjp(self._h, wp, op, wdev))
+        return out
+
+    def adjoint_step(self, dt: float, lam_np1, out=None):
+        if isinstance(lam_np1, np.ndarray):
+            lam_np1 = np.ascontiguousarray(lam_np1, dtype=np.float64)
+        if out is None:
+            out = np.empty((self.n_var, self.n_cell))
+        lp, ldev = _ptr(lam_np1)
+        op, odev = _ptr(out)
+        if ldev != odev:
+            raise ValueError("lam_np1 and out must both be host or both be device arrays")
+        self._chk(lib().teno_adjoint_step(self._h, float(dt), lp, op, ldev))
+        return out

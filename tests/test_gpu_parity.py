@@ -1,0 +1,262 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Bar (FP64 path): normwise relative error max|R_gpu - R_oracle| / max|R_oracle|
+<= 1e-11, and identical stencil selections except where the oracle's cutoff
+margin |chi_k - C_T| is <= 1e-10; such cells are re-run with the oracle's
+selection forced and must then meet the same bound.  FP32-mixed results are
+reported against the FP64 oracle with a loose bound.
+"""
+import numpy as np
+import pytest
+
+from paper_2105_02127_gb300 import inputs
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+TOL = 1e-11
+MARGIN = 1e-10
+
+
+@pytest.fixture(scope="module")
+def T():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_02127_gb300 import build, teno
+    build.build()
+    teno.lib()
+    return teno
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max())
+
+
+def _setup(T, mesh, order, nvar, flux, precision=0, linear=False):
+    t = T.Teno(device=0).load(mesh)
+    t.precompute_stencils(order=order, n_var=nvar, flux=flux, precision=precision,
+                          linear=int(linear))
+    return t
+
+
+def _check_residual(T, oracle_mod, mesh, U, order, nvar, flux, linear=False, tol=TOL):
+    t = _setup(T, mesh, order, nvar, flux, linear=linear)
+    t.set_state(U)
+    R, sel = t.residual(want_sel=True)
+    o = oracle_mod.Oracle(mesh, order=order, n_var=nvar, flux=flux, linear=linear)
+    Ro, selo, mg = o.residual(U)
+    differ = sel != selo
+    assert np.all(~differ | (mg <= MARGIN)), np.argwhere(differ & (mg > MARGIN))[:5]
+    if differ.any():
+        t.set_selection_override(selo)
+        R, _ = t.residual()
+        t.set_selection_override(None)
+    e = rel(R, Ro)
+    assert e <= tol, e
+    return t, o, R, Ro, selo
+
+
+def _blast(mesh, gamma=1.4):
+    """discontinuous periodic Euler state: dense high-pressure square"""
+    def f(x, y):
+        inside = (np.abs(x - 5.0) < 2.0) & (np.abs(y - 5.0) < 2.0)
+        rho = np.where(inside, 1.0, 0.125)
+        p = np.where(inside, 1.0, 0.1)
+        u = 0.3 * np.ones_like(x)
+        v = -0.2 * np.ones_like(x)
+        return inputs.prim_to_cons(rho, u, v, p, gamma)
+    return inputs.cell_average(mesh, f)
+
+
+def test_scalar_teno3_config1(T, oracle_mod):
+    """2D advection on the jittered 32x32 periodic square, TENO3, upwind flux."""
+    mesh = inputs.jittered_mesh(32, 32, seed=1001)
+    U = inputs.cell_average(mesh, inputs.advection_sine)
+    t, o, R, Ro, sel = _check_residual(T, oracle_mod, mesh, U, 3, 1, 0)
+    assert np.all(sel == 8)
+    # full run to t = 0.1 at CFL 0.3 (dt from the device reduction)
+    t.precompute_stencils(T.default_params(order=3, n_var=1, flux=0, cfl=0.3))
+    t.set_state(U)
+    dt_dev = t.cfl_dt()
+    dt_or = o.cfl_dt(U, 0.3)
+    assert abs(dt_dev - dt_or) <= 1e-14 * dt_or
+    nsteps = int(np.ceil(0.1 / dt_or))
+    dt = 0.1 / nsteps
+    Uo = U.copy()
+    for _ in range(nsteps):
+        t.rk3_step(dt)
+        Uo = o.rk3_step(Uo, dt)
+    assert rel(t.get_state(), Uo) <= TOL
+
+
+@pytest.mark.parametrize("order", [3, 4, 5, 6])
+def test_euler_vortex_hll(T, oracle_mod, order):
+    """Isentropic vortex, HLL, FP64 on a 33x31 jittered mesh (2046 cells: 64
+    tiles of 32 and a ragged tail)."""
+    mesh = inputs.jittered_mesh(33, 31, 10.0, 10.0, seed=1002)
+    U = inputs.cell_average(mesh, inputs.isentropic_vortex)
+    _check_residual(T, oracle_mod, mesh, U, order, 4, 1)
+
+
+@pytest.mark.parametrize("order,flux", [(6, 2), (5, 1), (4, 2), (3, 1)])
+def test_euler_discontinuous(T, oracle_mod, order, flux):
+    """A density/pressure square exercises the cutoff and the directional
+    stencils (HLLC and HLL)."""
+    mesh = inputs.jittered_mesh(40, 40, 10.0, 10.0, seed=1007)
+    U = _blast(mesh)
+    t, o, R, Ro, sel = _check_residual(T, oracle_mod, mesh, U, order, 4, flux)
+    assert (sel != 8).mean() > 0.01  # the small stencils are in use
+
+
+@pytest.mark.parametrize("order", [3, 5, 6])
+def test_scalar_step_and_linear(T, oracle_mod, order):
+    mesh = inputs.jittered_mesh(30, 29, seed=1011)
+    V = mesh.unwrapped_vertices().mean(axis=1)
+    U = np.where((V[:, 0] - 0.5) ** 2 + (V[:, 1] - 0.5) ** 2 < 0.09, 1.0, 0.0)[None].copy()
+    U += 0.1 * inputs.cell_average(mesh, inputs.advection_sine)
+    _check_residual(T, oracle_mod, mesh, U, order, 1, 0)
+    _check_residual(T, oracle_mod, mesh, U, order, 1, 0, linear=True)
+
+
+def test_rk3_fixed_and_cfl(T, oracle_mod):
+    mesh = inputs.jittered_mesh(24, 24, 10.0, 10.0, seed=1012)
+    U = inputs.cell_average(mesh, inputs.isentropic_vortex)
+    t = _setup(T, mesh, 5, 4, 1)
+    o = oracle_mod.Oracle(mesh, order=5, n_var=4, flux=1)
+    t.set_state(U)
+    Uo = U.copy()
+    for _ in range(3):
+        t.rk3_step(0.03)
+        Uo = o.rk3_step(Uo, 0.03)
+    assert rel(t.get_state(), Uo) <= TOL
+    dt_used = t.rk3_step(0.0)
+    dt_or = o.cfl_dt(Uo, 0.4)
+    assert abs(dt_used - dt_or) <= 1e-13 * dt_or
+    Uo = o.rk3_step(Uo, dt_or)
+    assert rel(t.get_state(), Uo) <= TOL
+    # device-side CFL step without synchronisation
+    t.rk3_steps(2, 0.0)
+    for _ in range(2):
+        Uo = o.rk3_step(Uo, o.cfl_dt(Uo, 0.4))
+    assert rel(t.get_state(), Uo) <= TOL
+
+
+def test_mixed_precision_report(T, oracle_mod):
+    """FP32-mixed: matvecs and fluxes in FP32, selection and residual
+    accumulation in FP64.  Reports error vs the FP64 oracle and the selection
+    flip rate; both must stay small."""
+    mesh = inputs.jittered_mesh(40, 40, 10.0, 10.0, seed=1013)
+    for U, order, flux in [(inputs.cell_average(mesh, inputs.isentropic_vortex), 5, 1),
+                           (_blast(mesh), 6, 2)]:
+        t = _setup(T, mesh, order, 4, flux, precision=1)
+        t.set_state(U)
+        R, sel = t.residual(want_sel=True)
+        o = oracle_mod.Oracle(mesh, order=order, n_var=4, flux=flux)
+        Ro, selo, _ = o.residual(U)
+        err = rel(R, Ro)
+        flips = float((sel != selo).mean())
+        print(f"mixed order {order}: rel err {err:.2e}, flip rate {flips:.2e}")
+        assert err < 1e-4 and flips < 1e-2
+
+
+def test_torch_device_buffers(T, oracle_mod):
+    import torch
+    mesh = inputs.jittered_mesh(20, 19, 10.0, 10.0, seed=1014)
+    U = inputs.cell_average(mesh, inputs.isentropic_vortex)
+    t = _setup(T, mesh, 5, 4, 1)
+    Ud = torch.from_numpy(U).cuda()
+    t.set_state(Ud)
+    R = torch.empty_like(Ud)
+    sel = torch.empty(U.shape, dtype=torch.uint8, device="cuda")
+    t.residual(out=R, sel=sel)
+    out = torch.empty_like(Ud)
+    t.get_state(out)
+    torch.cuda.synchronize()
+    Ro, selo, _ = oracle_mod.Oracle(mesh, order=5, n_var=4, flux=1).residual(U)
+    assert rel(R.cpu().numpy(), Ro) <= TOL
+    assert np.array_equal(out.cpu().numpy(), U)
+    assert np.array_equal(sel.cpu().numpy(), selo)
+
+
+def test_adjoint_vs_oracle(T, oracle_mod):
+    """Discrete adjoint (frozen selection and flux branches) against the
+    oracle's adjoint: residual VJP and one SSP-RK3 step."""
+    mesh = inputs.jittered_mesh(21, 19, 10.0, 10.0, seed=1004)
+    for U, order, flux in [(inputs.cell_average(mesh, inputs.isentropic_vortex), 5, 1),
+                           (_blast(mesh), 6, 2), (_blast(mesh), 4, 1)]:
+        t = _setup(T, mesh, order, 4, flux)
+        o = oracle_mod.Oracle(mesh, order=order, n_var=4, flux=flux)
+        t.set_state(U)
+        _, selo, _ = o.residual(U)
+        t.set_selection_override(selo)
+        w = inputs.random_directions(3000, 1, U.size)[0].reshape(U.shape)
+        v = t.residual_vjp(w)
+        vo = o.residual_vjp(U, w, sel_override=selo)
+        assert rel(v, vo) <= 1e-10
+        t.set_selection_override(None)
+    mesh = inputs.jittered_mesh(17, 16, 10.0, 10.0, seed=1005)
+    U = inputs.cell_average(mesh, inputs.isentropic_vortex)
+    t = _setup(T, mesh, 5, 4, 1)
+    o = oracle_mod.Oracle(mesh, order=5, n_var=4, flux=1)
+    t.set_state(U)
+    lam = inputs.random_directions(3001, 1, U.size)[0].reshape(U.shape)
+    ln = t.adjoint_step(0.02, lam)
+    lno = o.rk3_vjp(U, lam, 0.02)
+    assert rel(ln, lno) <= 1e-10
+    # the state is unchanged by the adjoint step
+    assert np.array_equal(t.get_state(), U)
+
+
+def test_scalar_adjoint_dot_product(T):
+    """<R(v), w> = <v, R^T w> for linear advection with frozen selection."""
+    mesh = inputs.jittered_mesh(16, 18, seed=1015)
+    t = _setup(T, mesh, 4, 1, 0, linear=True)
+    rng = np.random.default_rng(2)
+    v, w = rng.standard_normal((2, 1, mesh.n_cell))
+    t.set_state(v)
+    Rv, _ = t.residual()
+    JTw = t.residual_vjp(w)
+    lhs, rhs = np.sum(Rv * w), np.sum(v * JTw)
+    assert abs(lhs - rhs) <= 1e-12 * np.sqrt(np.sum(Rv ** 2) * np.sum(w ** 2))
+
+
+def test_full_size_sampled(T, oracle_mod):
+    """512^2 quads on [0,10]^2 (524,288 cells), TENO5, HLL, FP64: the residual
+    at 1500 sampled cells against the oracle computed cell by cell, and
+    discrete conservation of the whole field."""
+    mesh = inputs.jittered_mesh(512, 512, 10.0, 10.0, seed=1002)
+    U = inputs.cell_average(mesh, inputs.isentropic_vortex, n_quad=3)
+    t = _setup(T, mesh, 5, 4, 1)
+    t.set_state(U)
+    R, sel = t.residual(want_sel=True)
+    o = oracle_mod.Oracle(mesh, order=5, n_var=4, flux=1)
+    cells = np.random.default_rng(9).choice(mesh.n_cell, 1500, replace=False)
+    Ro, selo, mg = o.residual_cells(U, cells)
+    Rg = R[:, cells].T
+    ok = np.all((sel[:, cells].T == selo) | (mg <= MARGIN), axis=1)
+    assert ok.mean() == 1.0
+    scale = np.abs(R).max()
+    assert np.abs(Rg - Ro).max() / scale <= TOL
+    V = mesh.unwrapped_vertices()
+    e1, e2 = V[:, 1] - V[:, 0], V[:, 2] - V[:, 0]
+    area = 0.5 * (e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0])
+    for v in range(4):
+        assert abs(np.sum(area * R[v])) <= 1e-12 * np.sum(area * np.abs(R[v]))
+
+
+def test_tiny_and_ragged_meshes(T, oracle_mod):
+    for nx, ny, order in [(6, 6, 3), (5, 7, 3), (9, 7, 4), (12, 11, 6)]:
+        mesh = inputs.jittered_mesh(nx, ny, seed=1016 + nx)
+        U = inputs.cell_average(mesh, inputs.advection_sine)
+        _check_residual(T, oracle_mod, mesh, U, order, 1, 0)
+
+
+def test_nonphysical_state_detected(T):
+    mesh = inputs.jittered_mesh(10, 10, 10.0, 10.0, seed=1017)
+    U = inputs.cell_average(mesh, inputs.isentropic_vortex)
+    U[3, 17] = -1.0  # negative energy -> negative pressure
+    t = _setup(T, mesh, 3, 4, 1)
+    t.set_state(U)
+    with pytest.raises(T.TenoError) as e:
+        t.rk3_step(0.01)
+    assert e.value.code == T.TENO_ENONPHYS
