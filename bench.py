@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Throughput of the TENO finite-volume hot path on one GB300.
+
+Workload: the periodic isentropic vortex on [0,10]^2 (strength 5, free stream
+(1,1,1,1), gamma 1.4) on a jittered 512x512 split-quad mesh (524,288
+triangles), 5th-order TENO (large stencil of 30 cells, three directional
+stencils of 12), HLL flux, SSP-RK3 with the CFL step (0.4) reduced on the
+device.  One "step" = one SSP-RK3 step = 3 residual stages, each running every
+step of the path (stencil differences, matvecs, smoothness indicators, cutoff
+and selection, Gauss-point evaluation, face fluxes, residual gather, RK
+update) plus the CFL reduction.  Metric: cell-stage updates per second =
+n_cell * 3 * steps / time.  The per-cell reconstruction matrices (2.5 GB in
+FP64) are larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (oracle/) on the host cores on a bounded
+sample of the same workload.  Under torchrun every rank runs an independent
+replica (the path needs no collective on one mesh); rank 0 prints one JSON
+line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-stage updates/sec at 1 GB300 (FP64 vs FP32-mixed), % HBM roofline; adjoint/forward time"
+UNIT = "cell-stage/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+# FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (max SM clock)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
+# kernel at this workload (profiles/recon_kernel_vortex512k.md); None when the
+# kernel changed since the capture
+NCU_TRAFFIC = {"fp64": None, "fp32_mixed": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512, help="quads per side (2 n^2 triangles)")
+    ap.add_argument("--order", type=int, default=5)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the mixed, adjoint, e2e and CPU-baseline legs")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def workload(n, order):
+    from paper_2105_02127_gb300 import inputs
+    mesh = inputs.jittered_mesh(n, n, 10.0, 10.0, seed=1002)
+    U = inputs.cell_average(mesh, inputs.isentropic_vortex)
+    return mesh, U
+
+
+def algorithmic_bytes(order, n_var, precision):
+    """Bytes one recon launch must move per cell: the per-cell matrices, the
+    stencil ids, the cell's own state and selection byte; neighbour states are
+    the same state array (read once).  Gauss-point values are implementation
+    overhead and not counted."""
+    r = order - 1
+    m = (r + 1) * (r + 2) // 2 - 1
+    ns = 2 * (m + 1)
+    entries = m * ns + 3 * 12 * 5
+    esz = 8 if precision == "fp64" else 4
+    return entries * esz + (ns + 36) * 4 + n_var * 8 + 1 + n_var
+
+
+def algorithmic_fp64_flops(order, n_var, nq):
+    """FP64 flops per cell of the recon kernel's FP64 path: differences,
+    matvecs, beta, selection and Gauss-point evaluation."""
+    r = order - 1
+    m = (r + 1) * (r + 2) // 2 - 1
+    ns = 2 * (m + 1)
+    entries = m * ns + 3 * 12 * 5
+    per_var = (ns + 36) + 2 * entries + 2 * (m + 15) + 25 + 2 * 3 * nq * m + 3 * nq
+    return per_var * n_var
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader",
+                                       "-i", str(self.index), "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                mx.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def timed_steps(t, steps, stream, barrier):
+    import torch
+    t.profile(True)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t.rk3_steps(steps, 0.0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    kms, launches = t.profile_read()
+    t.profile(False)
+    return ms, kms, launches
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        tt = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+
+    import __graft_entry__ as g
+    g.build()
+    from paper_2105_02127_gb300 import teno
+
+    peaks, peak_src = load_peaks()
+    mesh, U = workload(args.n, args.order)
+    n_cell = mesh.n_cell
+    stream = torch.cuda.current_stream()
+    Ud = torch.from_numpy(U).cuda()
+    nq = 2 if args.order <= 4 else 3
+
+    def make(precision):
+        t = teno.Teno(device=torch.cuda.current_device(), stream=stream).load(mesh)
+        t.precompute_stencils(order=args.order, n_var=4, flux=teno.FLUX_HLL, precision=precision)
+        t.set_state(Ud)
+        return t
+
+    out = {}
+    # ---- FP64 path (primary)
+    t64 = make(teno.FP64)
+    t64.rk3_steps(args.warmup, 0.0)
+    t64.check_state()
+    with Clocks(torch.cuda.current_device()) as clk:
+        ms, kms, launches = timed_steps(t64, args.steps, stream, barrier)
+    t64.check_state()
+    ms = max_over_ranks(ms)
+    value = n_cell * 3 * args.steps * world / (ms / 1e3)
+    rec_ms = kms[0] / max(1, launches[0])
+    flops = algorithmic_fp64_flops(args.order, 4, nq) * n_cell
+    bytes64 = algorithmic_bytes(args.order, 4, "fp64") * n_cell
+    achieved = flops / (rec_ms / 1e3) / 1e12
+    hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
+    out["fp64"] = dict(ms_per_step=ms / args.steps, value=value, kernel_ms=kms.tolist(),
+                       launches=launches.tolist(), recon_ms=rec_ms)
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC["fp64"],
+            "kernel": "recon_kernel<14,30,3,4,double>",
+            "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz",
+            "hbm_achieved_gbs": bytes64 / (rec_ms / 1e3) / 1e9,
+            "hbm_frac": bytes64 / (rec_ms / 1e3) / 1e9 / hbm_gbs}
+    clocks = clk.summary()
+
+    extras = {}
+    if not args.no_extras:
+        # ---- FP32-mixed path
+        tmx = make(teno.FP32_MIXED)
+        tmx.rk3_steps(args.warmup, 0.0)
+        ms_m, kms_m, l_m = timed_steps(tmx, args.steps, stream, barrier)
+        tmx.check_state()
+        ms_m = max_over_ranks(ms_m)
+        rec_m = kms_m[0] / max(1, l_m[0])
+        bmx = algorithmic_bytes(args.order, 4, "fp32_mixed") * n_cell
+        ach_m = bmx / (rec_m / 1e3) / 1e9
+        Um = tmx.get_state()
+        U64 = t64.get_state()
+        extras["fp32_mixed"] = {
+            "value": n_cell * 3 * args.steps * world / (ms_m / 1e3), "unit": UNIT,
+            "ms_per_step": ms_m / args.steps, "dtype": "f32 matvec/flux, f64 selection/update",
+            "roofline": {"bound": "hbm", "achieved": ach_m, "peak": hbm_gbs, "unit": "GB/s",
+                         "frac": ach_m / hbm_gbs, "traffic": NCU_TRAFFIC["fp32_mixed"],
+                         "kernel": "recon_kernel<14,30,3,4,float>",
+                         "peak_source": f"{peak_src} hbm_gbs"},
+            "l1_rho_diff_vs_fp64_after_steps": float(np.abs(Um[0] - U64[0]).mean()),
+            "kernel_ms": kms_m.tolist()}
+        del tmx
+        # ---- adjoint / forward
+        lam = torch.from_numpy(np.ones_like(U)).cuda()
+        lam_out = torch.empty_like(lam)
+        t64.adjoint_step(0.001, lam, lam_out)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        na = max(2, args.steps // 4)
+        e0.record(stream)
+        for _ in range(na):
+            t64.adjoint_step(0.001, lam, lam_out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        adj_ms = e0.elapsed_time(e1) / na
+        extras["adjoint"] = {"ms_per_step": adj_ms, "forward_ms_per_step": ms / args.steps,
+                             "adjoint_over_forward": adj_ms / (ms / args.steps),
+                             "note": "adjoint step replays the two forward stages"}
+        # ---- end to end through the C ABI with pinned host buffers
+        hin = torch.from_numpy(U.copy()).pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        for _ in range(2):
+            t64.set_state(hin)
+            t64.rk3_step(0.0, sync=False)
+            t64.get_state(hout)
+        barrier()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            t64.set_state(hin)
+            t64.rk3_step(0.0, sync=False)
+            t64.get_state(hout)
+        torch.cuda.synchronize()
+        w1 = time.perf_counter()
+        barrier()
+        e2e_s = max_over_ranks(w1 - w0)
+        nbytes = U.size * 8
+        extras["e2e"] = {"value": n_cell * 3 * args.steps * world / e2e_s, "unit": UNIT,
+                         "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        cpu = cpu_baseline(mesh, U, args.order, samples=20)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"isentropic vortex, periodic [0,10]^2, jittered {args.n}x"
+                                   f"{args.n} split quads = {n_cell} triangles, TENO{args.order}, "
+                                   "HLL, SSP-RK3, CFL 0.4 (device dt)",
+                       "n_cell": n_cell, "order": args.order, "l2": "inputs larger than L2 "
+                       "(per-cell matrices 2.5 GB FP64)", "parallelism": f"replicas x{world}"},
+            "roofline": roof, "gpu_launches": int(sum(out["fp64"]["launches"])),
+            "kernel_ms_fp64": out["fp64"]["kernel_ms"],
+            "kernel_kinds": ["recon", "face_flux", "gather_rk", "cfl", "other"],
+            "clocks": clocks,
+        }
+        line.update({"fp32_mixed": extras.get("fp32_mixed"), "adjoint": extras.get("adjoint")})
+        if "e2e" in extras:
+            line["e2e"] = extras["e2e"]
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(mesh, U, order, samples=1):
+    """The oracle, untouched, on the host cores: full-mesh residual stages of
+    the same workload after its own (untimed) stencil precompute."""
+    from oracle.oracle import Oracle
+    o = Oracle(mesh, order=order, n_var=4, flux=1)
+    o.prepare()
+    t0 = time.perf_counter()
+    for _ in range(samples):
+        o.residual(U)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": mesh.n_cell * samples / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{samples} full residual stage(s) of the {mesh.n_cell}-cell mesh "
+                      f"({dt:.1f} s), stencils precomputed beforehand"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import build as ob
+    ob.build()
+    from oracle.oracle import Oracle
+    mesh, U = workload(args.n, args.order)
+    rng = np.random.default_rng(0)
+    cells = np.sort(rng.choice(mesh.n_cell, min(mesh.n_cell, 65536), replace=False))
+    o = Oracle(mesh, order=args.order, n_var=4, flux=1)
+    nb = mesh.tri  # neighbours are prepared inside residual_cells
+    del nb
+    o.prepare(cells)
+    for _ in range(args.warmup):
+        o.residual_cells(U, cells)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for _s in range(3):
+            o.residual_cells(U, cells)
+    dt = time.perf_counter() - t0
+    value = len(cells) * 3 * args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"{len(cells)} sampled cells of the {mesh.n_cell}-cell mesh, 3 residual stages "
+              "per step")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"isentropic vortex, periodic [0,10]^2, jittered {args.n}x"
+                                   f"{args.n} split quads = {mesh.n_cell} triangles, TENO"
+                                   f"{args.order}, HLL, SSP-RK3", "n_cell": mesh.n_cell},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

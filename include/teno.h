@@ -174,6 +174,18 @@ int teno_residual_vjp(teno_ctx* ctx, const double* w, double* v, int on_device);
 int teno_adjoint_step(teno_ctx* ctx, double dt, const double* lam_np1, double* lam_n,
                       int on_device);
 
+/* Kernel timing of this context (measurement support; no counterpart in the
+ * paper).  enable != 0 clears the accumulators and records a CUDA event pair
+ * on the context's stream around every later kernel launch; 0 stops
+ * recording.  Launch counts are kept whether or not recording is on. */
+int teno_profile(teno_ctx* ctx, int enable);
+
+/* Accumulated device time (ms, host [5]) and launch counts (host [5]) per
+ * kernel kind: 0 reconstruction + selection, 1 face flux, 2 residual gather
+ * + RK update, 3 CFL reduction, 4 other.  Synchronises on the recorded
+ * events; either pointer may be NULL. */
+int teno_profile_read(teno_ctx* ctx, double* ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,11 @@
 
 using namespace teno;
 
+namespace {
+constexpr int kProfKinds = 5;  // recon, face flux, gather/update, CFL reduction, other
+enum { K_RECON = 0, K_FLUX = 1, K_GATHER = 2, K_CFL = 3, K_OTHER = 4 };
+}  // namespace
+
 // ========================================================================
 // context
 
@@ -70,6 +75,13 @@ struct teno_ctx {
   bool adj_ok = false;
   std::vector<int64_t> rev_off_h, rev_idx_h;
   double time = 0.0;
+  // kernel timing (teno_profile): event pairs around launches, per kind
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_kind;  // kind of the pair (2*i, 2*i+1)
+  size_t ev_used = 0;
+  int64_t launches[kProfKinds] = {0, 0, 0, 0, 0};
+  double prof_ms[kProfKinds] = {0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -111,6 +123,41 @@ void dev_free(DevBuf& b) {
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;
+}
+
+// fold finished event pairs into the per-kind totals
+int prof_drain(teno_ctx* ctx) {
+  if (ctx->ev_used == 0) return TENO_OK;
+  CK(cudaEventSynchronize(ctx->ev_pool[2 * ctx->ev_used - 1]), "event sync");
+  for (size_t i = 0; i < ctx->ev_used; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev_pool[2 * i], ctx->ev_pool[2 * i + 1]), "elapsed");
+    ctx->prof_ms[ctx->ev_kind[i]] += ms;
+  }
+  ctx->ev_used = 0;
+  return TENO_OK;
+}
+
+// open a timed launch of `kind`; returns the pair index or -1
+long prof_begin(teno_ctx* ctx, int kind) {
+  ctx->launches[kind]++;
+  if (!ctx->prof_on) return -1;
+  if (ctx->ev_used == 2048 && prof_drain(ctx)) return -1;
+  if (ctx->ev_pool.size() < 2 * (ctx->ev_used + 1)) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return -1;
+    ctx->ev_pool.push_back(a);
+    ctx->ev_pool.push_back(b);
+    ctx->ev_kind.push_back(kind);
+  }
+  long i = (long)ctx->ev_used++;
+  ctx->ev_kind[i] = kind;
+  cudaEventRecord(ctx->ev_pool[2 * i], ctx->stream);
+  return i;
+}
+
+void prof_end(teno_ctx* ctx, long i) {
+  if (i >= 0) cudaEventRecord(ctx->ev_pool[2 * i + 1], ctx->stream);
 }
 
 int upload(teno_ctx* ctx, DevBuf& b, const void* src, size_t bytes) {
@@ -813,8 +860,12 @@ int upload_mesh(teno_ctx* ctx) {
 // one residual evaluation of state U (internal order) into Uq / K
 int stage_flux(teno_ctx* ctx, const double* U, uint8_t* sel_out, double time) {
   const uint8_t* sel_in = ctx->override_on ? (const uint8_t*)ctx->b_sel_ovr.p : nullptr;
+  long pe = prof_begin(ctx, K_RECON);
   CK(launch_recon(ctx->dm, U, ctx->b_Uq.p, sel_out, sel_in, ctx->stream), "recon launch");
+  prof_end(ctx, pe);
+  pe = prof_begin(ctx, K_FLUX);
   CK(launch_face_flux(ctx->dm, ctx->b_Uq.p, ctx->b_K.p, time, ctx->stream), "face flux launch");
+  prof_end(ctx, pe);
   return TENO_OK;
 }
 
@@ -907,9 +958,11 @@ int rk_stage(teno_ctx* ctx, const double* Un, const double* Us, double* out, dou
              double cs, double dt, const double* max_lam, double time) {
   int rc = stage_flux(ctx, Us, nullptr, time);
   if (rc) return rc;
+  long pe = prof_begin(ctx, K_GATHER);
   CK(launch_gather(ctx->dm, ctx->b_K.p, Un, Us, out, 1, cn, cs, dt, max_lam,
                    (int*)ctx->b_flag.p, ctx->stream),
      "gather launch");
+  prof_end(ctx, pe);
   return TENO_OK;
 }
 
@@ -986,6 +1039,7 @@ int teno_destroy(teno_ctx* ctx) {
                     &ctx->b_Uqbar, &ctx->b_l1, &ctx->b_l2, &ctx->b_lamn, &ctx->b_vtmp,
                     &ctx->b_selA};
   for (DevBuf* b : bufs) dev_free(*b);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;
   return TENO_OK;
 }
@@ -1198,9 +1252,11 @@ static int rk3_once(teno_ctx* ctx, double dt, double* dt_used) {
       int rc = teno_cfl_dt(ctx, &dt);
       if (rc) return rc;
     } else {
+      long pe = prof_begin(ctx, K_CFL);
       CK(launch_max_lambda(ctx->dm, (const double*)ctx->b_U.p, (double*)ctx->b_maxlam.p,
                            ctx->stream),
          "max lambda launch");
+      prof_end(ctx, pe);
       maxlam = (const double*)ctx->b_maxlam.p;
     }
   }
@@ -1301,6 +1357,35 @@ int teno_adjoint_step(teno_ctx* ctx, double dt, const double* lam_np1, double* l
   CK(launch_axpby(ln, ln, 1.0, l1, 1.0, n, ctx->stream), "axpby");
   CK(launch_axpby(ln, ln, 1.0, tmp, dt, n, ctx->stream), "axpby");
   return to_user(ctx, ln, lam_n, on_device);
+}
+
+int teno_profile(teno_ctx* ctx, int enable) {
+  if (!ctx) return TENO_EINVAL;
+  if (ctx->device < 0) return fail(ctx, TENO_ESTATE, "host-only context");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  int rc = prof_drain(ctx);
+  if (rc) return rc;
+  if (enable) {
+    for (int k = 0; k < kProfKinds; ++k) {
+      ctx->prof_ms[k] = 0.0;
+      ctx->launches[k] = 0;
+    }
+  }
+  ctx->prof_on = enable != 0;
+  return TENO_OK;
+}
+
+int teno_profile_read(teno_ctx* ctx, double* ms, int64_t* launches) {
+  if (!ctx) return TENO_EINVAL;
+  if (ctx->device < 0) return fail(ctx, TENO_ESTATE, "host-only context");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  int rc = prof_drain(ctx);
+  if (rc) return rc;
+  for (int k = 0; k < kProfKinds; ++k) {
+    if (ms) ms[k] = ctx->prof_ms[k];
+    if (launches) launches[k] = ctx->launches[k];
+  }
+  return TENO_OK;
 }
 
 }  // extern "C"

@@ -79,6 +79,8 @@ def lib(build_if_missing: bool = False):
         "teno_check_state": (C.c_int, [_vp]),
         "teno_residual_vjp": (C.c_int, [_vp, _vp, _vp, C.c_int]),
         "teno_adjoint_step": (C.c_int, [_vp, C.c_double, _vp, _vp, C.c_int]),
+        "teno_profile": (C.c_int, [_vp, C.c_int]),
+        "teno_profile_read": (C.c_int, [_vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -259,6 +261,17 @@ class Teno:
 
     def check_state(self):
         self._chk(lib().teno_check_state(self._h))
+
+    def profile(self, enable: bool = True):
+        self._chk(lib().teno_profile(self._h, int(enable)))
+
+    def profile_read(self):
+        """(ms[5], launches[5]) per kernel kind: recon, face flux, gather/update,
+        CFL reduction, other."""
+        ms = np.zeros(5)
+        n = np.zeros(5, dtype=np.int64)
+        self._chk(lib().teno_profile_read(self._h, ms.ctypes.data, n.ctypes.data))
+        return ms, n
 
     def residual_vjp(self, w, out=None):
         if isinstance(w, np.ndarray):

@@ -57,11 +57,14 @@ def _check_residual(T, oracle_mod, mesh, U, order, nvar, flux, linear=False, tol
 
 
 def _blast(mesh, gamma=1.4):
-    """discontinuous periodic Euler state: dense high-pressure square"""
+    """discontinuous periodic Euler state: dense high-pressure square (jumps of
+    10/3 in density and pressure; a Sod-like 8:1 jump makes the conservative
+    reconstruction overshoot to negative pressure at the square's corners in
+    the oracle and the library alike)"""
     def f(x, y):
         inside = (np.abs(x - 5.0) < 2.0) & (np.abs(y - 5.0) < 2.0)
-        rho = np.where(inside, 1.0, 0.125)
-        p = np.where(inside, 1.0, 0.1)
+        rho = np.where(inside, 1.0, 0.3)
+        p = np.where(inside, 1.0, 0.3)
         u = 0.3 * np.ones_like(x)
         v = -0.2 * np.ones_like(x)
         return inputs.prim_to_cons(rho, u, v, p, gamma)
