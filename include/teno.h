@@ -174,6 +174,12 @@ int teno_residual_vjp(teno_ctx* ctx, const double* w, double* v, int on_device);
 int teno_adjoint_step(teno_ctx* ctx, double dt, const double* lam_np1, double* lam_n,
                       int on_device);
 
+/* Values of the last reconstruction at the edge Gauss points (inspection
+ * support): out host [n_cell][3][nq][n_var] in user cell order, edge e of a
+ * cell running from its vertex e to vertex e+1, points in ascending order
+ * along the edge.  Synchronises. */
+int teno_edge_values(teno_ctx* ctx, double* out);
+
 /* Kernel timing of this context (measurement support; no counterpart in the
  * paper).  enable != 0 clears the accumulators and records a CUDA event pair
  * on the context's stream around every later kernel launch; 0 stops

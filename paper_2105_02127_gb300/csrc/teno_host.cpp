@@ -1359,6 +1359,33 @@ int teno_adjoint_step(teno_ctx* ctx, double dt, const double* lam_np1, double* l
   return to_user(ctx, ln, lam_n, on_device);
 }
 
+int teno_edge_values(teno_ctx* ctx, double* out) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (!out) return fail(ctx, TENO_EINVAL, "edge_values: null pointer");
+  const int64_t per = 3 * (int64_t)ctx->nq * ctx->prm.n_var;
+  const bool f64 = ctx->prm.precision == TENO_FP64;
+  std::vector<double> h64;
+  std::vector<float> h32;
+  if (f64) {
+    h64.resize(ctx->npad * per);
+    CK(cudaMemcpyAsync(h64.data(), ctx->b_Uq.p, h64.size() * 8, cudaMemcpyDeviceToHost,
+                       ctx->stream),
+       "D2H");
+  } else {
+    h32.resize(ctx->npad * per);
+    CK(cudaMemcpyAsync(h32.data(), ctx->b_Uq.p, h32.size() * 4, cudaMemcpyDeviceToHost,
+                       ctx->stream),
+       "D2H");
+  }
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  for (int64_t c = 0; c < ctx->nc; ++c) {
+    const int64_t u = ctx->perm[c];
+    for (int64_t i = 0; i < per; ++i) out[u * per + i] = f64 ? h64[c * per + i] : h32[c * per + i];
+  }
+  return TENO_OK;
+}
+
 int teno_profile(teno_ctx* ctx, int enable) {
   if (!ctx) return TENO_EINVAL;
   if (ctx->device < 0) return fail(ctx, TENO_ESTATE, "host-only context");

@@ -79,6 +79,7 @@ def lib(build_if_missing: bool = False):
         "teno_check_state": (C.c_int, [_vp]),
         "teno_residual_vjp": (C.c_int, [_vp, _vp, _vp, C.c_int]),
         "teno_adjoint_step": (C.c_int, [_vp, C.c_double, _vp, _vp, C.c_int]),
+        "teno_edge_values": (C.c_int, [_vp, _vp]),
         "teno_profile": (C.c_int, [_vp, C.c_int]),
         "teno_profile_read": (C.c_int, [_vp, _vp, _vp]),
     }
@@ -261,6 +262,13 @@ class Teno:
 
     def check_state(self):
         self._chk(lib().teno_check_state(self._h))
+
+    def edge_values(self):
+        """Gauss-point values of the last reconstruction, [n_cell][3][nq][n_var]."""
+        nq = 2 if self.params.order <= 4 else 3
+        out = np.empty((self.n_cell, 3, nq, self.n_var))
+        self._chk(lib().teno_edge_values(self._h, out.ctypes.data))
+        return out
 
     def profile(self, enable: bool = True):
         self._chk(lib().teno_profile(self._h, int(enable)))

@@ -57,14 +57,17 @@ def _check_residual(T, oracle_mod, mesh, U, order, nvar, flux, linear=False, tol
 
 
 def _blast(mesh, gamma=1.4):
-    """discontinuous periodic Euler state: dense high-pressure square (jumps of
-    10/3 in density and pressure; a Sod-like 8:1 jump makes the conservative
-    reconstruction overshoot to negative pressure at the square's corners in
-    the oracle and the library alike)"""
+    """Discontinuous periodic Euler state: a square of density 1 and pressure 1
+    in a background of density 0.5 and pressure 0.7 moving at (0.3, -0.2).
+    The two ratios differ on purpose: with equal ratios the sound speed is
+    uniform, the two arguments of the Einfeldt min/max tie at every face
+    (no derivative exists there), and a stronger Sod-like jump makes the
+    conservative reconstruction overshoot to negative density or pressure at
+    the square's corners, in the oracle and the library alike."""
     def f(x, y):
         inside = (np.abs(x - 5.0) < 2.0) & (np.abs(y - 5.0) < 2.0)
-        rho = np.where(inside, 1.0, 0.3)
-        p = np.where(inside, 1.0, 0.3)
+        rho = np.where(inside, 1.0, 0.5)
+        p = np.where(inside, 1.0, 0.7)
         u = 0.3 * np.ones_like(x)
         v = -0.2 * np.ones_like(x)
         return inputs.prim_to_cons(rho, u, v, p, gamma)
