@@ -69,7 +69,9 @@ struct teno_ctx {
   DevBuf b_ahat, b_nbr, b_smask, b_fcells, b_fedges, b_fgeom, b_cfaces, b_inv_area, b_cfl_len,
       b_perm;
   DevBuf b_U, b_U1, b_U2, b_R, b_tmp, b_Uq, b_K, b_sel, b_sel_ovr, b_maxlam, b_flag;
+  DevBuf b_Usplit;  // FP32 hi/lo split of the state being reconstructed (mixed precision)
   bool override_on = false;
+  bool split_ok = false;  // b_Usplit holds split(b_U)
   // adjoint
   DevBuf b_rev_off, b_rev_idx, b_dbar, b_uself, b_Uqbar, b_l1, b_l2, b_lamn, b_vtmp, b_selA;
   bool adj_ok = false;
@@ -858,10 +860,20 @@ int upload_mesh(teno_ctx* ctx) {
 }
 
 // one residual evaluation of state U (internal order) into Uq / K
-int stage_flux(teno_ctx* ctx, const double* U, uint8_t* sel_out, double time) {
+// split_ready: the FP32 split buffer already holds split(U) (written by the
+// previous RK update); otherwise the mixed path splits U first
+int stage_flux(teno_ctx* ctx, const double* U, uint8_t* sel_out, double time,
+               bool split_ready = false) {
   const uint8_t* sel_in = ctx->override_on ? (const uint8_t*)ctx->b_sel_ovr.p : nullptr;
+  const bool mixed = ctx->prm.precision != TENO_FP64;
+  float2* Us = mixed ? (float2*)ctx->b_Usplit.p : nullptr;
+  if (mixed && !split_ready) {
+    long ps = prof_begin(ctx, K_OTHER);
+    CK(launch_split(ctx->dm, U, Us, ctx->stream), "split launch");
+    prof_end(ctx, ps);
+  }
   long pe = prof_begin(ctx, K_RECON);
-  CK(launch_recon(ctx->dm, U, ctx->b_Uq.p, sel_out, sel_in, ctx->stream), "recon launch");
+  CK(launch_recon(ctx->dm, U, Us, ctx->b_Uq.p, sel_out, sel_in, ctx->stream), "recon launch");
   prof_end(ctx, pe);
   pe = prof_begin(ctx, K_FLUX);
   CK(launch_face_flux(ctx->dm, ctx->b_Uq.p, ctx->b_K.p, time, ctx->stream), "face flux launch");
@@ -939,7 +951,7 @@ int vjp_internal(teno_ctx* ctx, const double* U, const double* w, double* v, dou
   if (rc) return rc;
   uint8_t* sel = (uint8_t*)ctx->b_selA.p;
   const uint8_t* sel_in = ctx->override_on ? (const uint8_t*)ctx->b_sel_ovr.p : nullptr;
-  CK(launch_recon(ctx->dm, U, ctx->b_Uq.p, sel, sel_in, ctx->stream), "recon launch");
+  CK(launch_recon(ctx->dm, U, nullptr, ctx->b_Uq.p, sel, sel_in, ctx->stream), "recon launch");
   if (sel_in) sel = (uint8_t*)ctx->b_sel_ovr.p;
   CK(launch_face_flux_vjp(ctx->dm, ctx->b_Uq.p, w, (double*)ctx->b_Uqbar.p, time, ctx->stream),
      "flux vjp launch");
@@ -954,13 +966,16 @@ int vjp_internal(teno_ctx* ctx, const double* U, const double* w, double* v, dou
 }
 
 // SSP-RK3 stage: out = cn*Un + cs*(Us + dt R(Us))
+// (the mixed path keeps split(U) current: each RK update writes the split of
+// its output, which the next stage's reconstruction reads)
 int rk_stage(teno_ctx* ctx, const double* Un, const double* Us, double* out, double cn,
-             double cs, double dt, const double* max_lam, double time) {
-  int rc = stage_flux(ctx, Us, nullptr, time);
+             double cs, double dt, const double* max_lam, double time, bool split_ready) {
+  int rc = stage_flux(ctx, Us, nullptr, time, split_ready);
   if (rc) return rc;
+  const bool mixed = ctx->prm.precision != TENO_FP64;
   long pe = prof_begin(ctx, K_GATHER);
   CK(launch_gather(ctx->dm, ctx->b_K.p, Un, Us, out, 1, cn, cs, dt, max_lam,
-                   (int*)ctx->b_flag.p, ctx->stream),
+                   (int*)ctx->b_flag.p, mixed ? (float2*)ctx->b_Usplit.p : nullptr, ctx->stream),
      "gather launch");
   prof_end(ctx, pe);
   return TENO_OK;
@@ -1035,6 +1050,7 @@ int teno_destroy(teno_ctx* ctx) {
                     &ctx->b_fgeom, &ctx->b_cfaces, &ctx->b_inv_area, &ctx->b_cfl_len,
                     &ctx->b_perm, &ctx->b_U, &ctx->b_U1, &ctx->b_U2, &ctx->b_R, &ctx->b_tmp,
                     &ctx->b_Uq, &ctx->b_K, &ctx->b_sel, &ctx->b_sel_ovr, &ctx->b_maxlam,
+                    &ctx->b_Usplit,
                     &ctx->b_flag, &ctx->b_rev_off, &ctx->b_rev_idx, &ctx->b_dbar, &ctx->b_uself,
                     &ctx->b_Uqbar, &ctx->b_l1, &ctx->b_l2, &ctx->b_lamn, &ctx->b_vtmp,
                     &ctx->b_selA};
@@ -1122,7 +1138,9 @@ int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
   if (!rc) rc = dev_alloc(ctx, ctx->b_K, tsz * std::max<int64_t>(1, ctx->nface) * nv);
   if (!rc) rc = dev_alloc(ctx, ctx->b_sel, (size_t)nv * npad);
   if (!rc) rc = dev_alloc(ctx, ctx->b_sel_ovr, (size_t)nv * npad);
+  if (!rc && p->precision != TENO_FP64) rc = dev_alloc(ctx, ctx->b_Usplit, 8 * nv * npad);
   if (rc) return rc;
+  ctx->split_ok = false;
   if (ctx->device < 0) {
     ctx->pre_ok = true;
     return TENO_OK;
@@ -1160,6 +1178,7 @@ int teno_set_state(teno_ctx* ctx, const double* U, int on_device) {
   if (rc) return rc;
   if (!on_device) CK(cudaStreamSynchronize(ctx->stream), "sync");
   ctx->state_ok = true;
+  ctx->split_ok = false;
   return TENO_OK;
 }
 
@@ -1180,10 +1199,11 @@ int teno_residual(teno_ctx* ctx, double* R, uint8_t* sel, int on_device) {
   int rc = check_ready(ctx, true);
   if (rc) return rc;
   if (!R) return fail(ctx, TENO_EINVAL, "residual: null R");
-  rc = stage_flux(ctx, (const double*)ctx->b_U.p, (uint8_t*)ctx->b_sel.p, ctx->time);
+  rc = stage_flux(ctx, (const double*)ctx->b_U.p, (uint8_t*)ctx->b_sel.p, ctx->time,
+                  ctx->split_ok);
   if (rc) return rc;
   CK(launch_gather(ctx->dm, ctx->b_K.p, nullptr, nullptr, (double*)ctx->b_R.p, 0, 0, 0, 0,
-                   nullptr, nullptr, ctx->stream),
+                   nullptr, nullptr, nullptr, ctx->stream),
      "gather launch");
   if (sel) {
     const uint8_t* src = ctx->override_on ? (const uint8_t*)ctx->b_sel_ovr.p
@@ -1264,9 +1284,10 @@ static int rk3_once(teno_ctx* ctx, double dt, double* dt_used) {
   double* U1 = (double*)ctx->b_U1.p;
   double* U2 = (double*)ctx->b_U2.p;
   const double t = ctx->time;
-  int rc = rk_stage(ctx, U, U, U1, 0.0, 1.0, dt, maxlam, t);
-  if (!rc) rc = rk_stage(ctx, U, U1, U2, 0.75, 0.25, dt, maxlam, t + dt);
-  if (!rc) rc = rk_stage(ctx, U, U2, U, 1.0 / 3.0, 2.0 / 3.0, dt, maxlam, t + 0.5 * dt);
+  int rc = rk_stage(ctx, U, U, U1, 0.0, 1.0, dt, maxlam, t, ctx->split_ok);
+  if (!rc) rc = rk_stage(ctx, U, U1, U2, 0.75, 0.25, dt, maxlam, t + dt, true);
+  if (!rc) rc = rk_stage(ctx, U, U2, U, 1.0 / 3.0, 2.0 / 3.0, dt, maxlam, t + 0.5 * dt, true);
+  ctx->split_ok = ctx->prm.precision != TENO_FP64;
   if (rc) return rc;
   if (dt > 0.0) ctx->time += dt;
   if (dt_used) *dt_used = dt;
@@ -1339,8 +1360,8 @@ int teno_adjoint_step(teno_ctx* ctx, double dt, const double* lam_np1, double* l
   const double t = ctx->time;
   rc = to_internal(ctx, lam_np1, lam, on_device);
   // forward replay of the stage states
-  if (!rc) rc = rk_stage(ctx, U, U, U1, 0.0, 1.0, dt, nullptr, t);
-  if (!rc) rc = rk_stage(ctx, U, U1, U2, 0.75, 0.25, dt, nullptr, t + dt);
+  if (!rc) rc = rk_stage(ctx, U, U, U1, 0.0, 1.0, dt, nullptr, t, false);
+  if (!rc) rc = rk_stage(ctx, U, U1, U2, 0.75, 0.25, dt, nullptr, t + dt, false);
   // stage 3: U^{n+1} = 1/3 U^n + 2/3 U2 + 2/3 dt R(U2)
   if (!rc) rc = vjp_internal(ctx, U2, lam, tmp, t + 0.5 * dt);
   if (rc) return rc;

@@ -54,14 +54,17 @@ struct DeviceMesh {
 };
 
 // launchers (teno_kernels.cu); all return a cudaError_t
-cudaError_t launch_recon(const DeviceMesh& dm, const double* U, void* Uq, uint8_t* sel_out,
-                         const uint8_t* sel_in, cudaStream_t st);
+// Us: FP32 hi/lo split of U, required by the mixed-precision path (else unused)
+cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us, void* Uq,
+                         uint8_t* sel_out, const uint8_t* sel_in, cudaStream_t st);
+cudaError_t launch_split(const DeviceMesh& dm, const double* U, float2* Us, cudaStream_t st);
 cudaError_t launch_face_flux(const DeviceMesh& dm, const void* Uq, void* K, double time,
                              cudaStream_t st);
-// mode 0: R = residual; mode 1: U_out = cn*Un + cs*(Us + dt*R)
+// mode 0: R = residual; mode 1: U_out = cn*Un + cs*(Us + dt*R), and (split
+// non-null) the FP32 hi/lo split of U_out
 cudaError_t launch_gather(const DeviceMesh& dm, const void* K, const double* Un, const double* Us,
                           double* out, int mode, double cn, double cs, double dt_fixed,
-                          const double* max_lam, int* flag, cudaStream_t st);
+                          const double* max_lam, int* flag, float2* split, cudaStream_t st);
 cudaError_t launch_max_lambda(const DeviceMesh& dm, const double* U, double* max_lam,
                               cudaStream_t st);
 cudaError_t launch_permute(const double* src, double* dst, const int32_t* perm, int64_t n,

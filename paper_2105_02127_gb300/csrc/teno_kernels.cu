@@ -226,6 +226,7 @@ struct ReconArgs {
   const int32_t* nbr;
   const uint8_t* smask;
   const double* U;
+  const float2* Us;  // FP32 hi/lo split of U (mixed precision), [n_var][n_pad]
   void* Uq;
   uint8_t* sel_out;
   const uint8_t* sel_in;
@@ -234,12 +235,59 @@ struct ReconArgs {
   int linear, e_entries;
 };
 
+// TENO cutoff and two-step selection in FP64 (Eqs. new_scale_separation,
+// normalize, cutoff, TENO_reconstruction111/222): chi_k >= C_T is evaluated as
+// gamma_k >= C_T * sum_j gamma_j with gamma = (beta + eps)^-6.
+__device__ __forceinline__ uint8_t select_fp64(const double* beta, int present, double ct,
+                                               double eps) {
+  double g[kSmallK + 1], S = 0.0;
+#pragma unroll
+  for (int k = 0; k <= kSmallK; ++k) {
+    bool pr = k == kSmallK || ((present >> k) & 1);
+    double ib = 1.0 / (beta[k] + eps);
+    double i2 = ib * ib;
+    g[k] = pr ? i2 * i2 * i2 : 0.0;
+    S += g[k];
+  }
+  if (g[kSmallK] >= ct * S) return 8;
+  double S2 = g[0] + g[1] + g[2];
+  uint8_t sel = 0;
+#pragma unroll
+  for (int k = 0; k < kSmallK; ++k)
+    if (((present >> k) & 1) && g[k] >= ct * S2) sel |= (uint8_t)(1u << k);
+  return sel;
+}
+
+// FP32 evaluation of chi_k = 1 / sum_j ((beta_k+eps)/(beta_j+eps))^6 over the
+// stencils in `mask`; *near is set when chi_k lies within the guard band
+// 1e-3 C_T of C_T.  The FP32 betas are within 1.3e-6 (relative) of the FP64
+// sums of the same squares, which moves chi by less than 3e-5 relative, so a
+// decision outside the band equals the FP64 decision.
+__device__ __forceinline__ bool chi_keep32(const float* t, int k, int mask, float ct, bool* near) {
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j <= kSmallK; ++j) {
+    if (!((mask >> j) & 1)) continue;
+    float r = t[k] / t[j];
+    float r2 = r * r;
+    s += r2 * r2 * r2;
+  }
+  float chi = 1.f / s;
+  if (fabsf(chi - ct) <= 1e-3f * ct) *near = true;
+  return chi >= ct;
+}
+
 // ------------------------------------------------------------ reconstruction
 // thread (lane, v, z): cell tile*32 + lane, variable v.  A warp covers the 32
 // cells of one tile for one variable, so every matrix entry is one coalesced
-// 256-byte (FP64) row; the other variables' warps hit it in L1.
+// 128/256-byte row; the other variables' warps hit it in L1.
+// TA = double: the FP64 path.  TA = float: the mixed path -- stencil
+// differences from the hi/lo FP32 split of U (as accurate as an FP64
+// subtraction rounded to FP32), FP32 matvecs, FP32 beta and cutoff with an FP64
+// fallback inside the guard band, FP32 Gauss-point values.
 template <int M, int NS, int NQ, int NV, typename TA>
 __global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const EvalTable ev) {
+  constexpr bool kMixed = std::is_same<TA, float>::value;
   const int lane = threadIdx.x, v = threadIdx.y;
   const int64_t tile = (int64_t)blockIdx.x * blockDim.z + threadIdx.z;
   const int64_t c = tile * kTile + lane;
@@ -247,9 +295,23 @@ __global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const Eva
   constexpr int E = M * NS + kSmallEntries;
   constexpr int SL = NS + kSmallSlots;
   const double* __restrict__ Uv = a.U + (int64_t)v * a.n_pad;
-  const double u0 = Uv[c];
+  const float2* __restrict__ Usv = kMixed ? a.Us + (int64_t)v * a.n_pad : nullptr;
+  double u0 = 0.0;
+  float2 u0s = make_float2(0.f, 0.f);
+  if constexpr (kMixed)
+    u0s = Usv[c];
+  else
+    u0 = Uv[c];
   const TA* __restrict__ A = reinterpret_cast<const TA*>(a.ahat) + tile * (int64_t)E * kTile + lane;
   const int32_t* __restrict__ nb = a.nbr + tile * (int64_t)SL * kTile + lane;
+  auto diff = [&](int j) -> TA {
+    if constexpr (kMixed) {
+      const float2 q = __ldg(Usv + j);
+      return (q.x - u0s.x) + (q.y - u0s.y);
+    } else {
+      return __ldg(Uv + j) - u0;
+    }
+  };
 
   // large stencil: a' = A'' d  (d_s = U_s - U_0)
   TA acc[M];
@@ -257,8 +319,7 @@ __global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const Eva
   for (int l = 0; l < M; ++l) acc[l] = TA(0);
 #pragma unroll 2
   for (int s = 0; s < NS; ++s) {
-    const int j = __ldg(nb + s * kTile);
-    const TA d = TA(__ldg(Uv + j) - u0);
+    const TA d = diff(__ldg(nb + s * kTile));
     const TA* As = A + (int64_t)s * M * kTile;
 #pragma unroll
     for (int l = 0; l < M; ++l) acc[l] = fma(__ldg(As + l * kTile), d, acc[l]);
@@ -271,26 +332,10 @@ __global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const Eva
     for (int l = 0; l < kSmallM; ++l) as[k][l] = TA(0);
 #pragma unroll 2
     for (int s = 0; s < kSmallN; ++s) {
-      const int j = __ldg(nb + (NS + k * kSmallN + s) * kTile);
-      const TA d = TA(__ldg(Uv + j) - u0);
+      const TA d = diff(__ldg(nb + (NS + k * kSmallN + s) * kTile));
       const TA* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
 #pragma unroll
       for (int l = 0; l < kSmallM; ++l) as[k][l] = fma(__ldg(As + l * kTile), d, as[k][l]);
-    }
-  }
-  // smoothness indicators in FP64 (orthonormal basis: beta = |a'|^2)
-  double beta[kSmallK + 1];
-  {
-    double b = 0.0;
-#pragma unroll
-    for (int l = 0; l < M; ++l) b = fma((double)acc[l], (double)acc[l], b);
-    beta[kSmallK] = b;
-#pragma unroll
-    for (int k = 0; k < kSmallK; ++k) {
-      double s = 0.0;
-#pragma unroll
-      for (int l = 0; l < kSmallM; ++l) s = fma((double)as[k][l], (double)as[k][l], s);
-      beta[k] = s;
     }
   }
   const int present = a.smask[c];
@@ -300,24 +345,53 @@ __global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const Eva
   } else if (a.linear) {
     sel = 8;
   } else {
-    // gamma_k = (beta_k + eps)^-6, chi_k = gamma_k / sum gamma, keep chi_k >= C_T
-    double g[kSmallK + 1], S = 0.0;
+    bool exact = !kMixed;
+    if constexpr (kMixed) {
+      // FP32 smoothness indicators (orthonormal basis: beta = |a'|^2) and cutoff
+      float t[kSmallK + 1];
+      {
+        float b = 0.f;
 #pragma unroll
-    for (int k = 0; k <= kSmallK; ++k) {
-      bool pr = k == kSmallK || ((present >> k) & 1);
-      double ib = 1.0 / (beta[k] + a.eps);
-      double i2 = ib * ib;
-      g[k] = pr ? i2 * i2 * i2 : 0.0;
-      S += g[k];
+        for (int l = 0; l < M; ++l) b = fmaf(acc[l], acc[l], b);
+        t[kSmallK] = b + (float)a.eps;
+#pragma unroll
+        for (int k = 0; k < kSmallK; ++k) {
+          float q = 0.f;
+#pragma unroll
+          for (int l = 0; l < kSmallM; ++l) q = fmaf(as[k][l], as[k][l], q);
+          t[k] = q + (float)a.eps;
+        }
+      }
+      const float ct = (float)a.ct;
+      bool near = false;
+      const int all = present | 8;
+      if (chi_keep32(t, kSmallK, all, ct, &near)) {
+        sel = 8;
+      } else {
+        sel = 0;
+        const int smallm = present & 7;
+#pragma unroll
+        for (int k = 0; k < kSmallK; ++k)
+          if (((present >> k) & 1) && chi_keep32(t, k, smallm, ct, &near))
+            sel |= (uint8_t)(1u << k);
+      }
+      exact = near;
     }
-    if (g[kSmallK] >= a.ct * S) {
-      sel = 8;
-    } else {
-      double S2 = g[0] + g[1] + g[2];
-      sel = 0;
+    if (exact) {
+      // FP64 smoothness indicators and decision
+      double beta[kSmallK + 1];
+      double b = 0.0;
 #pragma unroll
-      for (int k = 0; k < kSmallK; ++k)
-        if (((present >> k) & 1) && g[k] >= a.ct * S2) sel |= (uint8_t)(1u << k);
+      for (int l = 0; l < M; ++l) b = fma((double)acc[l], (double)acc[l], b);
+      beta[kSmallK] = b;
+#pragma unroll
+      for (int k = 0; k < kSmallK; ++k) {
+        double q = 0.0;
+#pragma unroll
+        for (int l = 0; l < kSmallM; ++l) q = fma((double)as[k][l], (double)as[k][l], q);
+        beta[k] = q;
+      }
+      sel = select_fp64(beta, present, a.ct, a.eps);
     }
   }
   if (a.sel_out) a.sel_out[(int64_t)v * a.n_pad + c] = sel;
@@ -333,9 +407,9 @@ __global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const Eva
     for (int l = 0; l < M; ++l) cf[l] = TA(0);
 #pragma unroll
     for (int k = 0; k < kSmallK; ++k) {
-      TA wk = ((sel >> k) & 1) ? w : TA(0);
+      if (!((sel >> k) & 1)) continue;
 #pragma unroll
-      for (int l = 0; l < kSmallM; ++l) cf[l] = fma(wk, as[k][l], cf[l]);
+      for (int l = 0; l < kSmallM; ++l) cf[l] = fma(w, as[k][l], cf[l]);
     }
   }
   // values at the 3*NQ edge Gauss points: U_0 + Psi' c'
@@ -345,7 +419,22 @@ __global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const Eva
     TA s = TA(0);
 #pragma unroll
     for (int l = 0; l < M; ++l) s = fma(cf[l], TA(ev.psi[p * kMaxM + l]), s);
-    out[p * NV] = TA(u0 + (double)s);
+    if constexpr (kMixed)
+      out[p * NV] = u0s.x + (s + u0s.y);
+    else
+      out[p * NV] = u0 + s;
+  }
+}
+
+// FP32 hi/lo split of a state: hi = fl32(U), lo = fl32(U - hi)
+__global__ void split_kernel(const double* __restrict__ U, float2* __restrict__ Us, int64_t n_cell,
+                             int64_t n_pad, int n_var) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cell) return;
+  for (int v = 0; v < n_var; ++v) {
+    const double u = U[v * n_pad + c];
+    const float hi = (float)u;
+    Us[v * n_pad + c] = make_float2(hi, (float)(u - (double)hi));
   }
 }
 
@@ -415,7 +504,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a, const T
                                                      double* __restrict__ out, int mode, double cn,
                                                      double cs, double dt_fixed, double cfl,
                                                      const double* __restrict__ max_lam,
-                                                     int* flag) {
+                                                     int* flag, float2* __restrict__ split) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= a.n_cell) return;
   double acc[NV];
@@ -442,6 +531,10 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a, const T
     const int64_t i = v * a.n_pad + c;
     u[v] = cn * Un[i] + cs * (Us[i] - dt * acc[v] * ia);
     out[i] = u[v];
+    if (split) {
+      const float hi = (float)u[v];
+      split[i] = make_float2(hi, (float)(u[v] - (double)hi));
+    }
   }
   if constexpr (NV == 4) {
     const double rho = u[0];
@@ -701,13 +794,15 @@ cudaError_t dispatch_order(int order, F&& f) {
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
-cudaError_t launch_recon(const DeviceMesh& dm, const double* U, void* Uq, uint8_t* sel_out,
-                         const uint8_t* sel_in, cudaStream_t st) {
+cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us, void* Uq,
+                         uint8_t* sel_out, const uint8_t* sel_in, cudaStream_t st) {
+  if (dm.precision != TENO_FP64 && !Us) return cudaErrorInvalidValue;
   ReconArgs a;
   a.ahat = dm.ahat;
   a.nbr = dm.nbr;
   a.smask = dm.smask;
   a.U = U;
+  a.Us = Us;
   a.Uq = Uq;
   a.sel_out = sel_out;
   a.sel_in = sel_in;
@@ -783,24 +878,30 @@ cudaError_t launch_face_flux(const DeviceMesh& dm, const void* Uq, void* K, doub
 
 cudaError_t launch_gather(const DeviceMesh& dm, const void* K, const double* Un, const double* Us,
                           double* out, int mode, double cn, double cs, double dt_fixed,
-                          const double* max_lam, int* flag, cudaStream_t st) {
+                          const double* max_lam, int* flag, float2* split, cudaStream_t st) {
   GatherArgs a{dm.c_faces, dm.inv_area, dm.n_cell, dm.n_pad, dm.gamma};
   const unsigned grid = (unsigned)((dm.n_cell + 255) / 256);
   if (dm.n_var == 1) {
     if (dm.precision == TENO_FP64)
       gather_kernel<1, double><<<grid, 256, 0, st>>>(a, (const double*)K, Un, Us, out, mode, cn,
-                                                     cs, dt_fixed, dm.cfl, max_lam, flag);
+                                                     cs, dt_fixed, dm.cfl, max_lam, flag, split);
     else
       gather_kernel<1, float><<<grid, 256, 0, st>>>(a, (const float*)K, Un, Us, out, mode, cn, cs,
-                                                    dt_fixed, dm.cfl, max_lam, flag);
+                                                    dt_fixed, dm.cfl, max_lam, flag, split);
   } else {
     if (dm.precision == TENO_FP64)
       gather_kernel<4, double><<<grid, 256, 0, st>>>(a, (const double*)K, Un, Us, out, mode, cn,
-                                                     cs, dt_fixed, dm.cfl, max_lam, flag);
+                                                     cs, dt_fixed, dm.cfl, max_lam, flag, split);
     else
       gather_kernel<4, float><<<grid, 256, 0, st>>>(a, (const float*)K, Un, Us, out, mode, cn, cs,
-                                                    dt_fixed, dm.cfl, max_lam, flag);
+                                                    dt_fixed, dm.cfl, max_lam, flag, split);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split(const DeviceMesh& dm, const double* U, float2* Us, cudaStream_t st) {
+  split_kernel<<<(unsigned)((dm.n_cell + 255) / 256), 256, 0, st>>>(U, Us, dm.n_cell, dm.n_pad,
+                                                                    dm.n_var);
   return cudaGetLastError();
 }
 
