@@ -40,9 +40,9 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel at this workload (profiles/recon_kernel_vortex512k.md); None when the
-# kernel changed since the capture
-NCU_TRAFFIC = {"fp64": None, "fp32_mixed": None}
+# kernel, scaled to this workload from the small-case captures in profiles/;
+# None when the kernel changed since the capture
+NCU_TRAFFIC = {"fp64": None, "fp32_mixed": None, "fp64_native": None}
 
 
 def parse():
@@ -199,95 +199,77 @@ def run_ours(args):
     from paper_2105_02127_gb300 import teno
 
     peaks, peak_src = load_peaks()
+    hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
     mesh, U = workload(args.n, args.order)
     n_cell = mesh.n_cell
     stream = torch.cuda.current_stream()
     Ud = torch.from_numpy(U).cuda()
     nq = 2 if args.order <= 4 else 3
+    prec_code = {"fp64": teno.FP64, "fp32_mixed": teno.FP32_MIXED,
+                 "fp64_native": teno.FP64_NATIVE}
 
     def make(precision):
         t = teno.Teno(device=torch.cuda.current_device(), stream=stream).load(mesh)
-        t.precompute_stencils(order=args.order, n_var=4, flux=teno.FLUX_HLL, precision=precision)
+        t.precompute_stencils(order=args.order, n_var=4, flux=teno.FLUX_HLL,
+                              precision=prec_code[precision])
         t.set_state(Ud)
         return t
 
-    out = {}
-    if args.precision == "mixed":
-        # primary line on the FP32-mixed path (used for focused profiling)
-        tm = make(teno.FP32_MIXED)
-        tm.rk3_steps(args.warmup, 0.0)
-        tm.check_state()
-        ms, kms, launches = timed_steps(tm, args.steps, stream, barrier)
-        tm.check_state()
+    def measure(precision, clocks=False):
+        t = make(precision)
+        t.rk3_steps(args.warmup, 0.0)
+        t.check_state()
+        clk = Clocks(torch.cuda.current_device()) if clocks else None
+        if clk:
+            clk.__enter__()
+        ms, kms, launches = timed_steps(t, args.steps, stream, barrier)
+        if clk:
+            clk.__exit__()
+        t.check_state()
         ms = max_over_ranks(ms)
         rec_ms = kms[0] / max(1, launches[0])
-        bmx = algorithmic_bytes(args.order, 4, "fp32_mixed") * n_cell
-        hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
-        ach = bmx / (rec_ms / 1e3) / 1e9
-        if rank == 0:
-            print(json.dumps({
-                "metric": METRIC, "value": n_cell * 3 * args.steps * world / (ms / 1e3),
-                "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32 matvec/flux, f64 selection/update",
-                "data": "synthetic", "config": {"workload": f"isentropic vortex {n_cell} cells, "
-                                                            f"TENO{args.order}, HLL, SSP-RK3"},
-                "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s",
-                             "frac": ach / hbm_gbs, "traffic": NCU_TRAFFIC["fp32_mixed"]},
-                "gpu_launches": int(sum(launches)), "kernel_ms": kms.tolist()}))
-        if world > 1:
-            dist.destroy_process_group()
-        return
-    # ---- FP64 path (primary)
-    t64 = make(teno.FP64)
-    t64.rk3_steps(args.warmup, 0.0)
-    t64.check_state()
-    with Clocks(torch.cuda.current_device()) as clk:
-        ms, kms, launches = timed_steps(t64, args.steps, stream, barrier)
-    t64.check_state()
-    ms = max_over_ranks(ms)
-    value = n_cell * 3 * args.steps * world / (ms / 1e3)
-    rec_ms = kms[0] / max(1, launches[0])
-    flops = algorithmic_fp64_flops(args.order, 4, nq) * n_cell
-    bytes64 = algorithmic_bytes(args.order, 4, "fp64") * n_cell
-    achieved = flops / (rec_ms / 1e3) / 1e12
-    hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
-    out["fp64"] = dict(ms_per_step=ms / args.steps, value=value, kernel_ms=kms.tolist(),
-                       launches=launches.tolist(), recon_ms=rec_ms)
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC["fp64"],
-            "kernel": "recon_kernel<14,30,3,4,double>",
-            "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz",
-            "hbm_achieved_gbs": bytes64 / (rec_ms / 1e3) / 1e9,
-            "hbm_frac": bytes64 / (rec_ms / 1e3) / 1e9 / hbm_gbs}
-    clocks = clk.summary()
+        store = "fp32_mixed" if precision == "fp32_mixed" else "fp64"
+        nbytes = algorithmic_bytes(args.order, 4, store) * n_cell
+        gbs = nbytes / (rec_ms / 1e3) / 1e9
+        kernel = {"fp64": f"recon_df_kernel<{args.order}>",
+                  "fp32_mixed": f"recon_kernel<float> (order {args.order})",
+                  "fp64_native": f"recon_kernel<double> (order {args.order})"}[precision]
+        roof_hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
+                    "frac": gbs / hbm_gbs, "traffic": NCU_TRAFFIC.get(precision),
+                    "kernel": kernel, "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)"}
+        if precision == "fp64_native":
+            fl = algorithmic_fp64_flops(args.order, 4, nq) * n_cell / (rec_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": fl / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(precision),
+                    "kernel": kernel,
+                    "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz",
+                    "hbm_achieved_gbs": gbs, "hbm_frac": gbs / hbm_gbs}
+        else:
+            roof = roof_hbm
+        res = {"value": n_cell * 3 * args.steps * world / (ms / 1e3), "unit": UNIT,
+               "ms_per_step": ms / args.steps, "roofline": roof, "kernel_ms": kms.tolist(),
+               "launches": launches.tolist(), "recon_ms_per_launch": rec_ms}
+        if clk:
+            res["clocks"] = clk.summary()
+        return t, res
 
+    primary = "fp32_mixed" if args.precision == "mixed" else "fp64"
+    t_main, main = measure(primary, clocks=True)
     extras = {}
     if not args.no_extras:
-        # ---- FP32-mixed path
-        tmx = make(teno.FP32_MIXED)
-        tmx.rk3_steps(args.warmup, 0.0)
-        ms_m, kms_m, l_m = timed_steps(tmx, args.steps, stream, barrier)
-        tmx.check_state()
-        ms_m = max_over_ranks(ms_m)
-        rec_m = kms_m[0] / max(1, l_m[0])
-        bmx = algorithmic_bytes(args.order, 4, "fp32_mixed") * n_cell
-        ach_m = bmx / (rec_m / 1e3) / 1e9
-        Um = tmx.get_state()
-        U64 = t64.get_state()
-        extras["fp32_mixed"] = {
-            "value": n_cell * 3 * args.steps * world / (ms_m / 1e3), "unit": UNIT,
-            "ms_per_step": ms_m / args.steps, "dtype": "f32 matvec/flux, f64 selection/update",
-            "roofline": {"bound": "hbm", "achieved": ach_m, "peak": hbm_gbs, "unit": "GB/s",
-                         "frac": ach_m / hbm_gbs, "traffic": NCU_TRAFFIC["fp32_mixed"],
-                         "kernel": "recon_kernel<14,30,3,4,float>",
-                         "peak_source": f"{peak_src} hbm_gbs"},
-            "l1_rho_diff_vs_fp64_after_steps": float(np.abs(Um[0] - U64[0]).mean()),
-            "kernel_ms": kms_m.tolist()}
-        del tmx
-        # ---- adjoint / forward
+        U_main = t_main.get_state()
+        for other in ("fp32_mixed", "fp64_native"):
+            if other == primary:
+                continue
+            t_o, r = measure(other)
+            r["l1_rho_diff_vs_primary_after_steps"] = float(np.abs(t_o.get_state()[0] - U_main[0]).mean())
+            extras[other] = r
+            t_o.close()
+        # ---- adjoint / forward (FP64 path)
+        t64 = t_main
         lam = torch.from_numpy(np.ones_like(U)).cuda()
         lam_out = torch.empty_like(lam)
+        t64.set_state(Ud)
         t64.adjoint_step(0.001, lam, lam_out)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -299,9 +281,10 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         adj_ms = e0.elapsed_time(e1) / na
-        extras["adjoint"] = {"ms_per_step": adj_ms, "forward_ms_per_step": ms / args.steps,
-                             "adjoint_over_forward": adj_ms / (ms / args.steps),
-                             "note": "adjoint step replays the two forward stages"}
+        extras["adjoint"] = {"ms_per_step": adj_ms, "forward_ms_per_step": main["ms_per_step"],
+                             "adjoint_over_forward": adj_ms / main["ms_per_step"],
+                             "note": "one adjoint SSP-RK3 step, including the replay of its two "
+                                     "forward stages"}
         # ---- end to end through the C ABI with pinned host buffers
         hin = torch.from_numpy(U.copy()).pin_memory()
         hout = torch.empty_like(hin).pin_memory()
@@ -329,23 +312,27 @@ def run_ours(args):
         cpu = cpu_baseline(mesh, U, args.order, samples=20)
 
     if rank == 0:
+        dtype = {"fp64": "f64 (double-float fp32x2 matvec/beta/evaluation, f64 flux/update)",
+                 "fp32_mixed": "f32 matvec/flux, f64 selection/update"}[primary]
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic",
             "config": {"workload": f"isentropic vortex, periodic [0,10]^2, jittered {args.n}x"
                                    f"{args.n} split quads = {n_cell} triangles, TENO{args.order}, "
                                    "HLL, SSP-RK3, CFL 0.4 (device dt)",
-                       "n_cell": n_cell, "order": args.order, "l2": "inputs larger than L2 "
-                       "(per-cell matrices 2.5 GB FP64)", "parallelism": f"replicas x{world}"},
-            "roofline": roof, "gpu_launches": int(sum(out["fp64"]["launches"])),
-            "kernel_ms_fp64": out["fp64"]["kernel_ms"],
+                       "n_cell": n_cell, "order": args.order,
+                       "l2": "inputs larger than L2 (per-cell matrices 1.3-2.5 GB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": main["roofline"], "gpu_launches": int(sum(main["launches"])),
+            "kernel_ms": main["kernel_ms"],
             "kernel_kinds": ["recon", "face_flux", "gather_rk", "cfl", "other"],
-            "clocks": clocks,
+            "clocks": main.get("clocks"),
         }
-        line.update({"fp32_mixed": extras.get("fp32_mixed"), "adjoint": extras.get("adjoint")})
-        if "e2e" in extras:
-            line["e2e"] = extras["e2e"]
+        for k in ("fp32_mixed", "fp64_native", "adjoint", "e2e"):
+            if k in extras:
+                line[k] = extras[k]
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line))

@@ -51,7 +51,15 @@ enum teno_status {
 };
 
 enum teno_flux { TENO_FLUX_UPWIND = 0, TENO_FLUX_HLL = 1, TENO_FLUX_HLLC = 2 };
-enum teno_precision { TENO_FP64 = 0, TENO_FP32_MIXED = 1 };
+/* TENO_FP64: FP64-accurate path -- matvecs, smoothness indicators and Gauss
+ *   evaluation in double-float (pairs of FP32 numbers, ~48 significant bits)
+ *   on the FP32 pipe, selection decided in FP64 near the cutoff, fluxes,
+ *   residual and update in FP64;
+ * TENO_FP32_MIXED: matvecs and fluxes in FP32 with FP32 accumulation, the
+ *   selection decision (FP64 inside a guard band of C_T) and the residual
+ *   accumulation and update in FP64;
+ * TENO_FP64_NATIVE: everything in FP64 on the FP64 pipe. */
+enum teno_precision { TENO_FP64 = 0, TENO_FP32_MIXED = 1, TENO_FP64_NATIVE = 2 };
 
 /* Boundary tags of non-periodic meshes (bface[:,2]). */
 enum teno_bc { TENO_BC_WALL = 1, TENO_BC_INFLOW = 2, TENO_BC_OUTFLOW = 3, TENO_BC_TOP = 4 };

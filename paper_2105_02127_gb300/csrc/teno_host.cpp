@@ -673,8 +673,10 @@ int run_precompute(teno_ctx* ctx) {
   const int64_t nc = ctx->nc, npad = ctx->npad, ntile = npad / kTile;
   ctx->st_large.assign(nc * ns, -1);
   ctx->st_small.assign(nc * kSmallK * kSmallN, -1);
-  const bool f64 = p.precision == TENO_FP64;
-  const size_t esz = f64 ? sizeof(double) : sizeof(float);
+  // matrix storage: double (native FP64), (hi, lo) float pairs (FP64 via
+  // double-float) or float (mixed)
+  const int store = p.precision;
+  const size_t esz = store == TENO_FP32_MIXED ? sizeof(float) : 8;
   std::vector<unsigned char> ahat((size_t)ntile * E * kTile * esz, 0);
   std::vector<int32_t> nbr((size_t)ntile * SL * kTile, 0);
   std::vector<uint8_t> smask(npad, 0);
@@ -695,10 +697,15 @@ int run_precompute(teno_ctx* ctx) {
       const int64_t tile = c / kTile, lane = c % kTile;
       auto put = [&](int e, double x) {
         size_t pos = ((size_t)tile * E + e) * kTile + lane;
-        if (f64)
+        if (store == TENO_FP64_NATIVE) {
           reinterpret_cast<double*>(ahat.data())[pos] = x;
-        else
+        } else if (store == TENO_FP64) {
+          const float hi = (float)x;
+          reinterpret_cast<float*>(ahat.data())[2 * pos] = hi;
+          reinterpret_cast<float*>(ahat.data())[2 * pos + 1] = (float)(x - (double)hi);
+        } else {
           reinterpret_cast<float*>(ahat.data())[pos] = (float)x;
+        }
       };
       if (!r) r = stencil_matrix(ctx, R, t, lg, ns, m, G.data());
       if (!r) {
@@ -794,6 +801,10 @@ int run_precompute(teno_ctx* ctx) {
   dm.nbr = (const int32_t*)ctx->b_nbr.p;
   dm.smask = (const uint8_t*)ctx->b_smask.p;
   std::copy(R.psi_t, R.psi_t + kMaxPts * kMaxM, dm.eval.psi);
+  for (int i = 0; i < kMaxPts * kMaxM; ++i) {
+    const float hi = (float)R.psi_t[i];
+    dm.eval_df.psi[i] = make_float2(hi, (float)(R.psi_t[i] - (double)hi));
+  }
   for (int k = 0; k < kMaxNq; ++k) {
     dm.gw[k] = k < ctx->nq ? R.gw[k] : 0.0;
     dm.gt[k] = k < ctx->nq ? R.gt[k] : 0.0;
@@ -865,9 +876,9 @@ int upload_mesh(teno_ctx* ctx) {
 int stage_flux(teno_ctx* ctx, const double* U, uint8_t* sel_out, double time,
                bool split_ready = false) {
   const uint8_t* sel_in = ctx->override_on ? (const uint8_t*)ctx->b_sel_ovr.p : nullptr;
-  const bool mixed = ctx->prm.precision != TENO_FP64;
-  float2* Us = mixed ? (float2*)ctx->b_Usplit.p : nullptr;
-  if (mixed && !split_ready) {
+  const bool split = ctx->prm.precision != TENO_FP64_NATIVE;
+  float2* Us = split ? (float2*)ctx->b_Usplit.p : nullptr;
+  if (split && !split_ready) {
     long ps = prof_begin(ctx, K_OTHER);
     CK(launch_split(ctx->dm, U, Us, ctx->stream), "split launch");
     prof_end(ctx, ps);
@@ -951,7 +962,13 @@ int vjp_internal(teno_ctx* ctx, const double* U, const double* w, double* v, dou
   if (rc) return rc;
   uint8_t* sel = (uint8_t*)ctx->b_selA.p;
   const uint8_t* sel_in = ctx->override_on ? (const uint8_t*)ctx->b_sel_ovr.p : nullptr;
-  CK(launch_recon(ctx->dm, U, nullptr, ctx->b_Uq.p, sel, sel_in, ctx->stream), "recon launch");
+  float2* Us = nullptr;
+  if (ctx->prm.precision != TENO_FP64_NATIVE) {
+    Us = (float2*)ctx->b_Usplit.p;
+    CK(launch_split(ctx->dm, U, Us, ctx->stream), "split launch");
+    ctx->split_ok = false;
+  }
+  CK(launch_recon(ctx->dm, U, Us, ctx->b_Uq.p, sel, sel_in, ctx->stream), "recon launch");
   if (sel_in) sel = (uint8_t*)ctx->b_sel_ovr.p;
   CK(launch_face_flux_vjp(ctx->dm, ctx->b_Uq.p, w, (double*)ctx->b_Uqbar.p, time, ctx->stream),
      "flux vjp launch");
@@ -972,10 +989,10 @@ int rk_stage(teno_ctx* ctx, const double* Un, const double* Us, double* out, dou
              double cs, double dt, const double* max_lam, double time, bool split_ready) {
   int rc = stage_flux(ctx, Us, nullptr, time, split_ready);
   if (rc) return rc;
-  const bool mixed = ctx->prm.precision != TENO_FP64;
+  const bool split = ctx->prm.precision != TENO_FP64_NATIVE;
   long pe = prof_begin(ctx, K_GATHER);
   CK(launch_gather(ctx->dm, ctx->b_K.p, Un, Us, out, 1, cn, cs, dt, max_lam,
-                   (int*)ctx->b_flag.p, mixed ? (float2*)ctx->b_Usplit.p : nullptr, ctx->stream),
+                   (int*)ctx->b_flag.p, split ? (float2*)ctx->b_Usplit.p : nullptr, ctx->stream),
      "gather launch");
   prof_end(ctx, pe);
   return TENO_OK;
@@ -1106,7 +1123,7 @@ int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
   if (!ctx || !p) return TENO_EINVAL;
   if (!ctx->mesh_ok) return fail(ctx, TENO_ESTATE, "precompute before mesh_load");
   if (p->order < 3 || p->order > 6 || (p->n_var != 1 && p->n_var != 4) ||
-      (p->precision != TENO_FP64 && p->precision != TENO_FP32_MIXED) || p->flux < 0 ||
+      p->precision < TENO_FP64 || p->precision > TENO_FP64_NATIVE || p->flux < 0 ||
       p->flux > 2 || (p->n_var == 1) != (p->flux == TENO_FLUX_UPWIND) || !(p->ct > 0) ||
       !(p->eps > 0) || !(p->gamma > 1.0) || !(p->cfl > 0))
     return fail(ctx, TENO_EINVAL, "precompute: bad parameters");
@@ -1128,7 +1145,7 @@ int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
   if (rc) return rc;
   const int64_t npad = ctx->npad;
   const int nv = p->n_var;
-  const size_t tsz = p->precision == TENO_FP64 ? 8 : 4;
+  const size_t tsz = p->precision == TENO_FP32_MIXED ? 4 : 8;
   rc = dev_alloc(ctx, ctx->b_U, 8 * nv * npad);
   if (!rc) rc = dev_alloc(ctx, ctx->b_U1, 8 * nv * npad);
   if (!rc) rc = dev_alloc(ctx, ctx->b_U2, 8 * nv * npad);
@@ -1138,7 +1155,7 @@ int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
   if (!rc) rc = dev_alloc(ctx, ctx->b_K, tsz * std::max<int64_t>(1, ctx->nface) * nv);
   if (!rc) rc = dev_alloc(ctx, ctx->b_sel, (size_t)nv * npad);
   if (!rc) rc = dev_alloc(ctx, ctx->b_sel_ovr, (size_t)nv * npad);
-  if (!rc && p->precision != TENO_FP64) rc = dev_alloc(ctx, ctx->b_Usplit, 8 * nv * npad);
+  if (!rc && p->precision != TENO_FP64_NATIVE) rc = dev_alloc(ctx, ctx->b_Usplit, 8 * nv * npad);
   if (rc) return rc;
   ctx->split_ok = false;
   if (ctx->device < 0) {
@@ -1287,7 +1304,7 @@ static int rk3_once(teno_ctx* ctx, double dt, double* dt_used) {
   int rc = rk_stage(ctx, U, U, U1, 0.0, 1.0, dt, maxlam, t, ctx->split_ok);
   if (!rc) rc = rk_stage(ctx, U, U1, U2, 0.75, 0.25, dt, maxlam, t + dt, true);
   if (!rc) rc = rk_stage(ctx, U, U2, U, 1.0 / 3.0, 2.0 / 3.0, dt, maxlam, t + 0.5 * dt, true);
-  ctx->split_ok = ctx->prm.precision != TENO_FP64;
+  ctx->split_ok = ctx->prm.precision != TENO_FP64_NATIVE;
   if (rc) return rc;
   if (dt > 0.0) ctx->time += dt;
   if (dt_used) *dt_used = dt;
@@ -1327,8 +1344,8 @@ int teno_residual_vjp(teno_ctx* ctx, const double* w, double* v, int on_device) 
   int rc = check_ready(ctx, true);
   if (rc) return rc;
   if (!w || !v) return fail(ctx, TENO_EINVAL, "residual_vjp: null pointer");
-  if (ctx->prm.precision != TENO_FP64)
-    return fail(ctx, TENO_EINVAL, "adjoint: FP64 precision only");
+  if (ctx->prm.precision == TENO_FP32_MIXED)
+    return fail(ctx, TENO_EINVAL, "adjoint: FP64 precisions only");
   rc = ensure_adjoint(ctx);
   if (rc) return rc;
   rc = to_internal(ctx, w, (double*)ctx->b_l1.p, on_device);
@@ -1344,8 +1361,8 @@ int teno_adjoint_step(teno_ctx* ctx, double dt, const double* lam_np1, double* l
   int rc = check_ready(ctx, true);
   if (rc) return rc;
   if (!lam_np1 || !lam_n || !(dt > 0.0)) return fail(ctx, TENO_EINVAL, "adjoint_step: bad args");
-  if (ctx->prm.precision != TENO_FP64)
-    return fail(ctx, TENO_EINVAL, "adjoint: FP64 precision only");
+  if (ctx->prm.precision == TENO_FP32_MIXED)
+    return fail(ctx, TENO_EINVAL, "adjoint: FP64 precisions only");
   rc = ensure_adjoint(ctx);
   if (rc) return rc;
   const int64_t n = (int64_t)ctx->prm.n_var * ctx->npad;
@@ -1385,7 +1402,7 @@ int teno_edge_values(teno_ctx* ctx, double* out) {
   if (rc) return rc;
   if (!out) return fail(ctx, TENO_EINVAL, "edge_values: null pointer");
   const int64_t per = 3 * (int64_t)ctx->nq * ctx->prm.n_var;
-  const bool f64 = ctx->prm.precision == TENO_FP64;
+  const bool f64 = ctx->prm.precision != TENO_FP32_MIXED;
   std::vector<double> h64;
   std::vector<float> h32;
   if (f64) {

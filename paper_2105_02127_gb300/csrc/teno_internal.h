@@ -31,6 +31,11 @@ struct EvalTable {
   double psi[kMaxPts * kMaxM];
 };
 
+// The same table split into FP32 (hi, lo) pairs for the double-float path.
+struct DFTable {
+  float2 psi[kMaxPts * kMaxM];
+};
+
 // Everything the kernels of one residual evaluation need (device pointers).
 struct DeviceMesh {
   int64_t n_cell = 0, n_pad = 0, n_face = 0;
@@ -38,7 +43,7 @@ struct DeviceMesh {
   int flux = 0, precision = 0, linear = 0;
   double ct = 1e-6, eps = 1e-12, gamma = 1.4, adv_x = 1, adv_y = 1, cfl = 0.4;
   // reconstruction data, tile-interleaved [tile][entry][32]
-  const void* ahat = nullptr;     // double or float
+  const void* ahat = nullptr;     // double (FP64_NATIVE), float2 (FP64) or float (mixed)
   const int32_t* nbr = nullptr;   // [tile][ns+36][32] internal cell ids
   const uint8_t* smask = nullptr; // [n_pad] bit k: directional stencil k present
   // faces
@@ -49,6 +54,7 @@ struct DeviceMesh {
   const double* inv_area = nullptr; // [n_pad]
   const double* cfl_len = nullptr;  // [n_pad] 4|V|/perimeter
   EvalTable eval;
+  DFTable eval_df;
   double gw[kMaxNq];                // Gauss weights on [0,1], sum 1
   double gt[kMaxNq];                // Gauss nodes on [0,1], ascending
 };

@@ -31,6 +31,11 @@ namespace {
 constexpr int kSmallEntries = kSmallK * kSmallN * kSmallM;  // 180
 constexpr int kSmallSlots = kSmallK * kSmallN;               // 36
 
+template <typename T>
+struct TypeTag {
+  using type = T;
+};
+
 // ---------------------------------------------------------------- scalars
 template <typename T>
 __device__ __forceinline__ T tsqrt(T x);
@@ -136,23 +141,25 @@ __device__ __forceinline__ void euler_riemann(const T* UL, const T* UR, double n
   const T one = cst<T>(1.0), half = cst<T>(0.5), zero = cst<T>(0.0);
   const T gm1 = cst<T>(g - 1.0), gg = cst<T>(g);
   const T tnx = cst<T>(nx), tny = cst<T>(ny);
-  // left / right primitive variables in the face frame
+  // left / right primitive variables in the face frame (one reciprocal per
+  // density; every division below is by one of four reciprocals)
   T rL = UL[0], rR = UR[0];
-  T unL = (UL[1] * tnx + UL[2] * tny) / rL;
-  T utL = (UL[2] * tnx - UL[1] * tny) / rL;
-  T unR = (UR[1] * tnx + UR[2] * tny) / rR;
-  T utR = (UR[2] * tnx - UR[1] * tny) / rR;
+  T irL = one / rL, irR = one / rR;
+  T unL = (UL[1] * tnx + UL[2] * tny) * irL;
+  T utL = (UL[2] * tnx - UL[1] * tny) * irL;
+  T unR = (UR[1] * tnx + UR[2] * tny) * irR;
+  T utR = (UR[2] * tnx - UR[1] * tny) * irR;
   T EL = UL[3], ER = UR[3];
   T pL = gm1 * (EL - half * rL * (unL * unL + utL * utL));
   T pR = gm1 * (ER - half * rR * (unR * unR + utR * utR));
-  T cL = tsqrt(gg * pL / rL), cR = tsqrt(gg * pR / rR);
-  T HL = (EL + pL) / rL, HR = (ER + pR) / rR;
+  T cL = tsqrt(gg * pL * irL), cR = tsqrt(gg * pR * irR);
+  T HL = (EL + pL) * irL, HR = (ER + pR) * irR;
   // Roe averages and Einfeldt wave speeds (Eq. wavespeed)
-  T D = tsqrt(rR / rL);
-  T den = one + D;
-  T ua = (unL + unR * D) / den;
-  T va = (utL + utR * D) / den;
-  T Ha = (HL + HR * D) / den;
+  T D = tsqrt(rR * irL);
+  T iden = one / (one + D);
+  T ua = (unL + unR * D) * iden;
+  T va = (utL + utR * D) * iden;
+  T Ha = (HL + HR * D) * iden;
   T ca = tsqrt(gm1 * (Ha - half * (ua * ua + va * va)));
   T SL = vmin(unL - cL, ua - ca);
   T SR = vmax(unR + cR, ua + ca);
@@ -285,8 +292,8 @@ __device__ __forceinline__ bool chi_keep32(const float* t, int k, int mask, floa
 // differences from the hi/lo FP32 split of U (as accurate as an FP64
 // subtraction rounded to FP32), FP32 matvecs, FP32 beta and cutoff with an FP64
 // fallback inside the guard band, FP32 Gauss-point values.
-template <int M, int NS, int NQ, int NV, typename TA>
-__global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const EvalTable ev) {
+template <int M, int NS, int NQ, int NV, typename TA, typename TT>
+__global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const TT ev) {
   constexpr bool kMixed = std::is_same<TA, float>::value;
   const int lane = threadIdx.x, v = threadIdx.y;
   const int64_t tile = (int64_t)blockIdx.x * blockDim.z + threadIdx.z;
@@ -418,11 +425,175 @@ __global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const Eva
   for (int p = 0; p < 3 * NQ; ++p) {
     TA s = TA(0);
 #pragma unroll
-    for (int l = 0; l < M; ++l) s = fma(cf[l], TA(ev.psi[p * kMaxM + l]), s);
+    for (int l = 0; l < M; ++l) {
+      if constexpr (kMixed)
+        s = fmaf(cf[l], ev.psi[p * kMaxM + l].x, s);  // FP32 table: hi parts
+      else
+        s = fma(cf[l], ev.psi[p * kMaxM + l], s);
+    }
     if constexpr (kMixed)
       out[p * NV] = u0s.x + (s + u0s.y);
     else
       out[p * NV] = u0 + s;
+  }
+}
+
+// ------------------------------------------- double-float (FP32 pair) path
+// Values are unevaluated sums hi + lo of two floats (|lo| <= ulp(hi)/2), about
+// 48 significant bits.  Products use the exact FMA residual, sums Knuth's
+// two-sum; the per-cell matrices are stored as (hi, lo) pairs.
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+// acc += a * b with a, b pairs; acc.l collects the rounding terms (the pair
+// is renormalised by the caller)
+__device__ __forceinline__ void df_mac(DF& acc, float2 a, DF b) {
+  const float p = a.x * b.h;
+  float e = fmaf(a.x, b.h, -p);
+  e = fmaf(a.x, b.l, e);
+  e = fmaf(a.y, b.h, e);
+  const DF s = two_sum(acc.h, p);
+  acc.h = s.h;
+  acc.l += s.l + e;
+}
+__device__ __forceinline__ DF df_norm(DF a) { return two_sum(a.h, a.l); }
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.h + (double)a.l; }
+
+// FP64-accurate reconstruction with double-float arithmetic on the FP32 pipe:
+// stencil differences from the (hi, lo) split of U, matvecs, beta and the
+// Gauss-point evaluation in pairs (relative error ~2^-46 of the summed
+// magnitudes); the cutoff is decided in FP32 with the guard band of the mixed
+// path and in FP64 inside it; Gauss-point values are written in FP64.
+template <int M, int NS, int NQ, int NV>
+__global__ void __launch_bounds__(128) recon_df_kernel(const ReconArgs a, const DFTable ev) {
+  const int lane = threadIdx.x, v = threadIdx.y;
+  const int64_t tile = (int64_t)blockIdx.x * blockDim.z + threadIdx.z;
+  const int64_t c = tile * kTile + lane;
+  if (c >= a.n_cell) return;
+  constexpr int E = M * NS + kSmallEntries;
+  constexpr int SL = NS + kSmallSlots;
+  const float2* __restrict__ Usv = a.Us + (int64_t)v * a.n_pad;
+  const float2 u0s = Usv[c];
+  const float2* __restrict__ A =
+      reinterpret_cast<const float2*>(a.ahat) + tile * (int64_t)E * kTile + lane;
+  const int32_t* __restrict__ nb = a.nbr + tile * (int64_t)SL * kTile + lane;
+  auto diff = [&](int j) -> DF {
+    const float2 q = __ldg(Usv + j);
+    DF s = two_sum(q.x, -u0s.x);
+    s.l += q.y - u0s.y;
+    return two_sum(s.h, s.l);
+  };
+  DF acc[M];
+#pragma unroll
+  for (int l = 0; l < M; ++l) acc[l] = {0.f, 0.f};
+#pragma unroll 2
+  for (int s = 0; s < NS; ++s) {
+    const DF d = diff(__ldg(nb + s * kTile));
+    const float2* As = A + (int64_t)s * M * kTile;
+#pragma unroll
+    for (int l = 0; l < M; ++l) df_mac(acc[l], __ldg(As + l * kTile), d);
+  }
+#pragma unroll
+  for (int l = 0; l < M; ++l) acc[l] = df_norm(acc[l]);
+  DF as[kSmallK][kSmallM];
+#pragma unroll
+  for (int k = 0; k < kSmallK; ++k) {
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) as[k][l] = {0.f, 0.f};
+#pragma unroll 2
+    for (int s = 0; s < kSmallN; ++s) {
+      const DF d = diff(__ldg(nb + (NS + k * kSmallN + s) * kTile));
+      const float2* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) df_mac(as[k][l], __ldg(As + l * kTile), d);
+    }
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) as[k][l] = df_norm(as[k][l]);
+  }
+  const int present = a.smask[c];
+  uint8_t sel;
+  if (a.sel_in) {
+    sel = a.sel_in[(int64_t)v * a.n_pad + c];
+  } else if (a.linear) {
+    sel = 8;
+  } else {
+    // beta = |a'|^2 in pairs
+    DF bt[kSmallK + 1];
+    {
+      DF b = {0.f, 0.f};
+#pragma unroll
+      for (int l = 0; l < M; ++l) df_mac(b, make_float2(acc[l].h, acc[l].l), acc[l]);
+      bt[kSmallK] = df_norm(b);
+#pragma unroll
+      for (int k = 0; k < kSmallK; ++k) {
+        DF q = {0.f, 0.f};
+#pragma unroll
+        for (int l = 0; l < kSmallM; ++l) df_mac(q, make_float2(as[k][l].h, as[k][l].l), as[k][l]);
+        bt[k] = df_norm(q);
+      }
+    }
+    float t[kSmallK + 1];
+#pragma unroll
+    for (int k = 0; k <= kSmallK; ++k) t[k] = bt[k].h + (float)a.eps;
+    const float ct = (float)a.ct;
+    bool near = false;
+    if (chi_keep32(t, kSmallK, present | 8, ct, &near)) {
+      sel = 8;
+    } else {
+      sel = 0;
+#pragma unroll
+      for (int k = 0; k < kSmallK; ++k)
+        if (((present >> k) & 1) && chi_keep32(t, k, present & 7, ct, &near))
+          sel |= (uint8_t)(1u << k);
+    }
+    if (near) {
+      double beta[kSmallK + 1];
+#pragma unroll
+      for (int k = 0; k <= kSmallK; ++k) beta[k] = df_to_double(bt[k]);
+      sel = select_fp64(beta, present, a.ct, a.eps);
+    }
+  }
+  if (a.sel_out) a.sel_out[(int64_t)v * a.n_pad + c] = sel;
+  DF cf[M];
+  if (sel & 8) {
+#pragma unroll
+    for (int l = 0; l < M; ++l) cf[l] = acc[l];
+  } else {
+    // equal weights: sum the kept polynomials, then divide by their number
+    const int nd = (sel & 1) + ((sel >> 1) & 1) + ((sel >> 2) & 1);
+    const float fn = (float)(nd ? nd : 1);
+#pragma unroll
+    for (int l = 0; l < M; ++l) cf[l] = {0.f, 0.f};
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) {
+      DF sum = {0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < kSmallK; ++k) {
+        if (!((sel >> k) & 1)) continue;
+        DF q = two_sum(sum.h, as[k][l].h);
+        q.l += sum.l + as[k][l].l;
+        sum = two_sum(q.h, q.l);
+      }
+      const float qh = sum.h / fn;
+      const float r = fmaf(-qh, fn, sum.h);  // exact remainder
+      cf[l] = two_sum(qh, (r + sum.l) / fn);
+      if (!nd) cf[l] = {0.f, 0.f};
+    }
+  }
+  const double u0 = a.U[(int64_t)v * a.n_pad + c];
+  double* __restrict__ out = reinterpret_cast<double*>(a.Uq) + c * (3 * NQ * NV) + v;
+#pragma unroll
+  for (int p = 0; p < 3 * NQ; ++p) {
+    DF s = {0.f, 0.f};
+#pragma unroll
+    for (int l = 0; l < M; ++l) df_mac(s, ev.psi[p * kMaxM + l], cf[l]);
+    s = df_norm(s);
+    out[p * NV] = u0 + ((double)s.h + (double)s.l);
   }
 }
 
@@ -697,8 +868,8 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
 
 // d_bar[tile][slot][v][32] = (A''^T abar)_slot with abar = w_k Psi'^T Uq_bar
 // (selection frozen); u_self = sum_p Uq_bar - sum_slot d_bar (dU_0 terms).
-template <int M, int NS, int NQ, int NV>
-__global__ void __launch_bounds__(128) recon_vjp_kernel(const double* __restrict__ ahat,
+template <int M, int NS, int NQ, int NV, typename TS>
+__global__ void __launch_bounds__(128) recon_vjp_kernel(const TS* __restrict__ ahat,
                                                         const uint8_t* __restrict__ sel_in,
                                                         const double* __restrict__ Uq_bar,
                                                         double* __restrict__ d_bar,
@@ -711,7 +882,14 @@ __global__ void __launch_bounds__(128) recon_vjp_kernel(const double* __restrict
   if (c >= n_cell) return;
   constexpr int E = M * NS + kSmallEntries;
   constexpr int SL = NS + kSmallSlots;
-  const double* A = ahat + tile * (int64_t)E * kTile + lane;
+  const TS* A = ahat + tile * (int64_t)E * kTile + lane;
+  // matrix entry as FP64 (pairs of the double-float storage are summed)
+  auto ent = [](TS x) -> double {
+    if constexpr (std::is_same<TS, float2>::value)
+      return (double)x.x + (double)x.y;
+    else
+      return x;
+  };
   double* db = d_bar + tile * (int64_t)SL * NV * kTile + v * kTile + lane;
   double cb[M];
 #pragma unroll
@@ -733,7 +911,7 @@ __global__ void __launch_bounds__(128) recon_vjp_kernel(const double* __restrict
     double t = 0.0;
     if (large) {
 #pragma unroll
-      for (int l = 0; l < M; ++l) t = fma(A[(int64_t)(s * M + l) * kTile], cb[l], t);
+      for (int l = 0; l < M; ++l) t = fma(ent(A[(int64_t)(s * M + l) * kTile]), cb[l], t);
     }
     db[(int64_t)s * NV * kTile] = t;
     tot += t;
@@ -746,9 +924,9 @@ __global__ void __launch_bounds__(128) recon_vjp_kernel(const double* __restrict
     for (int s = 0; s < kSmallN; ++s) {
       double t = 0.0;
       if (wk != 0.0) {
-        const double* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
+        const TS* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
 #pragma unroll
-        for (int l = 0; l < kSmallM; ++l) t = fma(As[l * kTile], cb[l], t);
+        for (int l = 0; l < kSmallM; ++l) t = fma(ent(As[l * kTile]), cb[l], t);
         t *= wk;
       }
       db[(int64_t)(NS + k * kSmallN + s) * NV * kTile] = t;
@@ -796,7 +974,7 @@ cudaError_t dispatch_order(int order, F&& f) {
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us, void* Uq,
                          uint8_t* sel_out, const uint8_t* sel_in, cudaStream_t st) {
-  if (dm.precision != TENO_FP64 && !Us) return cudaErrorInvalidValue;
+  if (dm.precision != TENO_FP64_NATIVE && !Us) return cudaErrorInvalidValue;
   ReconArgs a;
   a.ahat = dm.ahat;
   a.nbr = dm.nbr;
@@ -820,10 +998,12 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
       constexpr int TZ = 4 / NV;  // 128 threads per block
       dim3 block(kTile, NV, TZ);
       dim3 grid((unsigned)((tiles + TZ - 1) / TZ));
-      if (dm.precision == TENO_FP64)
-        recon_kernel<M, NS, NQ, NV, double><<<grid, block, 0, st>>>(a, dm.eval);
+      if (dm.precision == TENO_FP64_NATIVE)
+        recon_kernel<M, NS, NQ, NV, double, EvalTable><<<grid, block, 0, st>>>(a, dm.eval);
+      else if (dm.precision == TENO_FP64)
+        recon_df_kernel<M, NS, NQ, NV><<<grid, block, 0, st>>>(a, dm.eval_df);
       else
-        recon_kernel<M, NS, NQ, NV, float><<<grid, block, 0, st>>>(a, dm.eval);
+        recon_kernel<M, NS, NQ, NV, float, DFTable><<<grid, block, 0, st>>>(a, dm.eval_df);
       return cudaGetLastError();
     };
     constexpr int NQd = (M <= 9) ? 2 : 3;
@@ -857,7 +1037,7 @@ cudaError_t launch_face_flux(const DeviceMesh& dm, const void* Uq, void* K, doub
   auto go = [&](auto nvc, auto nqc, auto flc) -> cudaError_t {
     constexpr int NV = decltype(nvc)::value, NQ = decltype(nqc)::value,
                   FL = decltype(flc)::value;
-    if (dm.precision == TENO_FP64)
+    if (dm.precision != TENO_FP32_MIXED)
       face_flux_kernel<NV, NQ, FL, double><<<grid, 256, 0, st>>>(
           a, (const double*)Uq, (double*)K);
     else
@@ -882,14 +1062,14 @@ cudaError_t launch_gather(const DeviceMesh& dm, const void* K, const double* Un,
   GatherArgs a{dm.c_faces, dm.inv_area, dm.n_cell, dm.n_pad, dm.gamma};
   const unsigned grid = (unsigned)((dm.n_cell + 255) / 256);
   if (dm.n_var == 1) {
-    if (dm.precision == TENO_FP64)
+    if (dm.precision != TENO_FP32_MIXED)
       gather_kernel<1, double><<<grid, 256, 0, st>>>(a, (const double*)K, Un, Us, out, mode, cn,
                                                      cs, dt_fixed, dm.cfl, max_lam, flag, split);
     else
       gather_kernel<1, float><<<grid, 256, 0, st>>>(a, (const float*)K, Un, Us, out, mode, cn, cs,
                                                     dt_fixed, dm.cfl, max_lam, flag, split);
   } else {
-    if (dm.precision == TENO_FP64)
+    if (dm.precision != TENO_FP32_MIXED)
       gather_kernel<4, double><<<grid, 256, 0, st>>>(a, (const double*)K, Un, Us, out, mode, cn,
                                                      cs, dt_fixed, dm.cfl, max_lam, flag, split);
     else
@@ -988,14 +1168,22 @@ cudaError_t launch_recon_vjp(const DeviceMesh& dm, const uint8_t* sel, const dou
     constexpr int M = decltype(Mc)::value, NS = decltype(NSc)::value;
     constexpr int NQ = (M <= 9) ? 2 : 3;
     if (dm.nq != NQ) return cudaErrorInvalidValue;
-    if (dm.n_var == 1) {
-      dim3 block(kTile, 1, 4);
-      recon_vjp_kernel<M, NS, NQ, 1><<<(unsigned)((tiles + 3) / 4), block, 0, st>>>(
-          (const double*)dm.ahat, sel, Uq_bar, d_bar, u_self, dm.n_cell, dm.n_pad, dm.eval);
+    auto go = [&](auto nvc, auto tsc) {
+      constexpr int NV = decltype(nvc)::value;
+      using TS = typename decltype(tsc)::type;
+      constexpr int TZ = 4 / NV;
+      dim3 block(kTile, NV, TZ);
+      recon_vjp_kernel<M, NS, NQ, NV, TS><<<(unsigned)((tiles + TZ - 1) / TZ), block, 0, st>>>(
+          (const TS*)dm.ahat, sel, Uq_bar, d_bar, u_self, dm.n_cell, dm.n_pad, dm.eval);
+    };
+    using I1 = std::integral_constant<int, 1>;
+    using I4 = std::integral_constant<int, 4>;
+    if (dm.precision == TENO_FP64) {
+      if (dm.n_var == 1) go(I1{}, TypeTag<float2>{});
+      else go(I4{}, TypeTag<float2>{});
     } else {
-      dim3 block(kTile, 4, 1);
-      recon_vjp_kernel<M, NS, NQ, 4><<<(unsigned)tiles, block, 0, st>>>(
-          (const double*)dm.ahat, sel, Uq_bar, d_bar, u_self, dm.n_cell, dm.n_pad, dm.eval);
+      if (dm.n_var == 1) go(I1{}, TypeTag<double>{});
+      else go(I4{}, TypeTag<double>{});
     }
     return cudaGetLastError();
   });

@@ -18,7 +18,7 @@ from . import build as _build
 TENO_OK, TENO_EINVAL, TENO_ENOMEM, TENO_ECUDA = 0, -1, -2, -3
 TENO_EMESH, TENO_ESTENCIL, TENO_ENONPHYS, TENO_ETIMEOUT, TENO_ESTATE = -4, -5, -6, -7, -8
 FLUX_UPWIND, FLUX_HLL, FLUX_HLLC = 0, 1, 2
-FP64, FP32_MIXED = 0, 1
+FP64, FP32_MIXED, FP64_NATIVE = 0, 1, 2
 SEL_LARGE = 8
 
 _NAMES = {0: "TENO_OK", -1: "TENO_EINVAL", -2: "TENO_ENOMEM", -3: "TENO_ECUDA", -4: "TENO_EMESH",

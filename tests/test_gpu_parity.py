@@ -39,8 +39,9 @@ def _setup(T, mesh, order, nvar, flux, precision=0, linear=False):
     return t
 
 
-def _check_residual(T, oracle_mod, mesh, U, order, nvar, flux, linear=False, tol=TOL):
-    t = _setup(T, mesh, order, nvar, flux, linear=linear)
+def _check_residual(T, oracle_mod, mesh, U, order, nvar, flux, linear=False, tol=TOL,
+                    precision=0):
+    t = _setup(T, mesh, order, nvar, flux, linear=linear, precision=precision)
     t.set_state(U)
     R, sel = t.residual(want_sel=True)
     o = oracle_mod.Oracle(mesh, order=order, n_var=nvar, flux=flux, linear=linear)
@@ -95,27 +96,31 @@ def test_scalar_teno3_config1(T, oracle_mod):
     assert rel(t.get_state(), Uo) <= TOL
 
 
+@pytest.mark.parametrize("precision", [0, 2], ids=["fp64", "fp64native"])
 @pytest.mark.parametrize("order", [3, 4, 5, 6])
-def test_euler_vortex_hll(T, oracle_mod, order):
-    """Isentropic vortex, HLL, FP64 on a 33x31 jittered mesh (2046 cells: 64
-    tiles of 32 and a ragged tail)."""
+def test_euler_vortex_hll(T, oracle_mod, order, precision):
+    """Isentropic vortex, HLL, FP64 (double-float and native) on a 33x31
+    jittered mesh (2046 cells: 64 tiles of 32 and a ragged tail)."""
     mesh = inputs.jittered_mesh(33, 31, 10.0, 10.0, seed=1002)
     U = inputs.cell_average(mesh, inputs.isentropic_vortex)
-    _check_residual(T, oracle_mod, mesh, U, order, 4, 1)
+    _check_residual(T, oracle_mod, mesh, U, order, 4, 1, precision=precision)
 
 
+@pytest.mark.parametrize("precision", [0, 2], ids=["fp64", "fp64native"])
 @pytest.mark.parametrize("order,flux", [(6, 2), (5, 1), (4, 2), (3, 1)])
-def test_euler_discontinuous(T, oracle_mod, order, flux):
+def test_euler_discontinuous(T, oracle_mod, order, flux, precision):
     """A density/pressure square exercises the cutoff and the directional
     stencils (HLLC and HLL)."""
     mesh = inputs.jittered_mesh(40, 40, 10.0, 10.0, seed=1007)
     U = _blast(mesh)
-    t, o, R, Ro, sel = _check_residual(T, oracle_mod, mesh, U, order, 4, flux)
+    t, o, R, Ro, sel = _check_residual(T, oracle_mod, mesh, U, order, 4, flux,
+                                       precision=precision)
     assert (sel != 8).mean() > 0.01  # the small stencils are in use
 
 
 @pytest.mark.parametrize("order", [3, 5, 6])
 def test_scalar_step_and_linear(T, oracle_mod, order):
+    """Scalar advection of a disc (a jump) plus a sine: TENO and linear modes."""
     mesh = inputs.jittered_mesh(30, 29, seed=1011)
     V = mesh.unwrapped_vertices().mean(axis=1)
     U = np.where((V[:, 0] - 0.5) ** 2 + (V[:, 1] - 0.5) ** 2 < 0.09, 1.0, 0.0)[None].copy()
@@ -184,13 +189,14 @@ def test_torch_device_buffers(T, oracle_mod):
     assert np.array_equal(sel.cpu().numpy(), selo)
 
 
-def test_adjoint_vs_oracle(T, oracle_mod):
+@pytest.mark.parametrize("precision", [0, 2], ids=["fp64", "fp64native"])
+def test_adjoint_vs_oracle(T, oracle_mod, precision):
     """Discrete adjoint (frozen selection and flux branches) against the
     oracle's adjoint: residual VJP and one SSP-RK3 step."""
     mesh = inputs.jittered_mesh(21, 19, 10.0, 10.0, seed=1004)
     for U, order, flux in [(inputs.cell_average(mesh, inputs.isentropic_vortex), 5, 1),
                            (_blast(mesh), 6, 2), (_blast(mesh), 4, 1)]:
-        t = _setup(T, mesh, order, 4, flux)
+        t = _setup(T, mesh, order, 4, flux, precision=precision)
         o = oracle_mod.Oracle(mesh, order=order, n_var=4, flux=flux)
         t.set_state(U)
         _, selo, _ = o.residual(U)
@@ -202,7 +208,7 @@ def test_adjoint_vs_oracle(T, oracle_mod):
         t.set_selection_override(None)
     mesh = inputs.jittered_mesh(17, 16, 10.0, 10.0, seed=1005)
     U = inputs.cell_average(mesh, inputs.isentropic_vortex)
-    t = _setup(T, mesh, 5, 4, 1)
+    t = _setup(T, mesh, 5, 4, 1, precision=precision)
     o = oracle_mod.Oracle(mesh, order=5, n_var=4, flux=1)
     t.set_state(U)
     lam = inputs.random_directions(3001, 1, U.size)[0].reshape(U.shape)
@@ -226,13 +232,14 @@ def test_scalar_adjoint_dot_product(T):
     assert abs(lhs - rhs) <= 1e-12 * np.sqrt(np.sum(Rv ** 2) * np.sum(w ** 2))
 
 
-def test_full_size_sampled(T, oracle_mod):
+@pytest.mark.parametrize("precision", [0, 2], ids=["fp64", "fp64native"])
+def test_full_size_sampled(T, oracle_mod, precision):
     """512^2 quads on [0,10]^2 (524,288 cells), TENO5, HLL, FP64: the residual
     at 1500 sampled cells against the oracle computed cell by cell, and
     discrete conservation of the whole field."""
     mesh = inputs.jittered_mesh(512, 512, 10.0, 10.0, seed=1002)
     U = inputs.cell_average(mesh, inputs.isentropic_vortex, n_quad=3)
-    t = _setup(T, mesh, 5, 4, 1)
+    t = _setup(T, mesh, 5, 4, 1, precision=precision)
     t.set_state(U)
     R, sel = t.residual(want_sel=True)
     o = oracle_mod.Oracle(mesh, order=5, n_var=4, flux=1)
