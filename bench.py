@@ -42,13 +42,13 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel, scaled to this workload from the small-case captures in profiles/;
 # None when the kernel changed since the capture
-NCU_TRAFFIC = {"fp64": None, "fp32_mixed": None, "fp64_native": None}
+NCU_TRAFFIC = {"fp64": 2801e6, "fp32_mixed": 1448e6, "fp64_native": 2788e6}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=512, help="quads per side (2 n^2 triangles)")
@@ -115,7 +115,7 @@ class Clocks:
         try:
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader",
-                                       "-i", str(self.index), "-lms", "200"], stdout=self.f,
+                                       "-i", str(self.index), "-lms", "50"], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
