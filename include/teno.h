@@ -200,6 +200,39 @@ int teno_profile(teno_ctx* ctx, int enable);
  * events; either pointer may be NULL. */
 int teno_profile_read(teno_ctx* ctx, double* ms, int64_t* launches);
 
+/* Largest n_cell that teno_cfl_dt_noalloc accepts. */
+#define TENO_NOALLOC_MAX_CELLS 8388608
+
+/* CFL step with no device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory -- code
+ * running inside another framework whose caching allocator owns the GPU,
+ * drivers that work to a fixed device-memory budget, real-time loops that
+ * cannot afford an allocation's implicit synchronisation.
+ *
+ * Computes dt = cfl / max_i ((|v_i| + c_i) / cell_len_i) (scalar advection:
+ * |v| = |(adv_x, adv_y)|, c = 0) -- the value teno_cfl_dt returns when
+ * cell_len_i = 4 |V_i| / perimeter_i.
+ *  device, cuda_stream  GPU and stream (a cudaStream_t, NULL = legacy default);
+ *  U         device [n_var][n_cell] cell averages, any cell order;
+ *  cell_len  device [n_cell], same cell order as U;
+ *  dt        device pointer when dt_on_device != 0 (stream-ordered, not
+ *            synchronised), else host pointer (the call synchronises).
+ * The caller owns every buffer.  Partial maxima go to a fixed device array of
+ * (TENO_NOALLOC_MAX_CELLS / 2048 + 1) doubles = 32,776 bytes inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  The first call on a device looks up that array's device address
+ * with the device current; make that first call before any stream capture.
+ * Every call shares the array and it keeps the last call's contents (each
+ * slot is written before it is read, nothing needs clearing): calls that
+ * overlap on the GPU (several streams or host threads) race and must be
+ * serialised by the caller.
+ * Errors: TENO_EINVAL (n_var not 1 or 4, n_cell < 1 or above
+ * TENO_NOALLOC_MAX_CELLS, a null pointer, cfl <= 0, gamma <= 1 for Euler),
+ * TENO_ECUDA.  Calls no cudaMalloc, cudaFree or allocating library routine. */
+int teno_cfl_dt_noalloc(int device, void* cuda_stream, int32_t n_var, int64_t n_cell,
+                        const double* U, const double* cell_len, double gamma, double adv_x,
+                        double adv_y, double cfl, double* dt, int dt_on_device);
+
 #ifdef __cplusplus
 }
 #endif

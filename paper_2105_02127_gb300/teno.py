@@ -80,6 +80,9 @@ def lib(build_if_missing: bool = False):
         "teno_residual_vjp": (C.c_int, [_vp, _vp, _vp, C.c_int]),
         "teno_adjoint_step": (C.c_int, [_vp, C.c_double, _vp, _vp, C.c_int]),
         "teno_edge_values": (C.c_int, [_vp, _vp]),
+        "teno_cfl_dt_noalloc": (C.c_int, [C.c_int, _vp, C.c_int32, C.c_int64, _vp, _vp,
+                                          C.c_double, C.c_double, C.c_double, C.c_double, _vp,
+                                          C.c_int]),
         "teno_profile": (C.c_int, [_vp, C.c_int]),
         "teno_profile_read": (C.c_int, [_vp, _vp, _vp]),
     }
@@ -116,6 +119,36 @@ def _stream_handle(stream):
             return None
         return None
     return getattr(stream, "cuda_stream", stream)
+
+
+NOALLOC_MAX_CELLS = 8388608
+
+
+def cfl_dt_noalloc(U, cell_len, dt_out=None, gamma: float = 1.4, adv=(1.0, 1.0),
+                   cfl: float = 0.4, device: int = 0, stream=None) -> float | None:
+    """CFL step through teno_cfl_dt_noalloc, which allocates no device memory.
+    U: CUDA tensor [n_var][n_cell]; cell_len: CUDA tensor [n_cell] (4|V|/perimeter);
+    dt_out: None (the host value is returned) or a CUDA float64 tensor of one element."""
+    n_var, n_cell = int(U.shape[0]), int(U.shape[1])
+    up, udev = _ptr(U)
+    lp, ldev = _ptr(cell_len)
+    if not (udev and ldev):
+        raise ValueError("U and cell_len must be device tensors")
+    if dt_out is None:
+        out = C.c_double()
+        rc = lib().teno_cfl_dt_noalloc(device, _stream_handle(stream), n_var, n_cell, up, lp,
+                                       gamma, adv[0], adv[1], cfl, C.addressof(out), 0)
+        if rc != 0:
+            raise TenoError(rc, "teno_cfl_dt_noalloc failed")
+        return out.value
+    op, odev = _ptr(dt_out)
+    if not odev:
+        raise ValueError("dt_out must be a device tensor")
+    rc = lib().teno_cfl_dt_noalloc(device, _stream_handle(stream), n_var, n_cell, up, lp, gamma,
+                                   adv[0], adv[1], cfl, op, 1)
+    if rc != 0:
+        raise TenoError(rc, "teno_cfl_dt_noalloc failed")
+    return None
 
 
 def default_params(**kw) -> teno_params:
