@@ -42,7 +42,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel, scaled to this workload from the small-case captures in profiles/;
 # None when the kernel changed since the capture
-NCU_TRAFFIC = {"fp64": 2801e6, "fp32_mixed": 1448e6, "fp64_native": 2788e6}
+NCU_TRAFFIC = {"fp64": None, "fp32_mixed": None, "fp64_native": 2788e6}
 
 
 def parse():
@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the mixed, adjoint, e2e and CPU-baseline legs")
+    ap.add_argument("--recon-variant", type=int, default=0, choices=[0, 1],
+                    help="0: matrices streamed through TMA bulk copies, 1: direct loads")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="path timed as the primary line (the other one is an extra)")
     return ap.parse_args()
@@ -211,7 +213,7 @@ def run_ours(args):
     def make(precision):
         t = teno.Teno(device=torch.cuda.current_device(), stream=stream).load(mesh)
         t.precompute_stencils(order=args.order, n_var=4, flux=teno.FLUX_HLL,
-                              precision=prec_code[precision])
+                              precision=prec_code[precision], recon_variant=args.recon_variant)
         t.set_state(Ud)
         return t
 
@@ -231,9 +233,10 @@ def run_ours(args):
         store = "fp32_mixed" if precision == "fp32_mixed" else "fp64"
         nbytes = algorithmic_bytes(args.order, 4, store) * n_cell
         gbs = nbytes / (rec_ms / 1e3) / 1e9
-        kernel = {"fp64": f"recon_df_kernel<{args.order}>",
-                  "fp32_mixed": f"recon_kernel<float> (order {args.order})",
-                  "fp64_native": f"recon_kernel<double> (order {args.order})"}[precision]
+        tma = args.recon_variant == 0
+        kernel = {"fp64": ("recon_tma_kernel<df>" if tma else "recon_df_kernel") + f" order {args.order}",
+                  "fp32_mixed": ("recon_tma_kernel<f32>" if tma else "recon_kernel<float>") + f" order {args.order}",
+                  "fp64_native": f"recon_kernel<double> order {args.order}"}[precision]
         roof_hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
                     "frac": gbs / hbm_gbs, "traffic": NCU_TRAFFIC.get(precision),
                     "kernel": kernel, "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)"}

@@ -797,6 +797,8 @@ int run_precompute(teno_ctx* ctx) {
   dm.adv_x = p.adv_x;
   dm.adv_y = p.adv_y;
   dm.cfl = p.cfl;
+  dm.tma = p.recon_variant == 0;
+  dm.err_flag = (int*)ctx->b_flag.p;
   dm.ahat = ctx->b_ahat.p;
   dm.nbr = (const int32_t*)ctx->b_nbr.p;
   dm.smask = (const uint8_t*)ctx->b_smask.p;
@@ -1013,6 +1015,7 @@ void teno_default_params(teno_params* p) {
   p->precision = TENO_FP64;
   p->linear = 0;
   p->nq = 0;
+  p->recon_variant = 0;
   p->ct = 1e-6;
   p->eps = 1e-12;
   p->gamma = 1.4;
@@ -1125,7 +1128,8 @@ int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
   if (p->order < 3 || p->order > 6 || (p->n_var != 1 && p->n_var != 4) ||
       p->precision < TENO_FP64 || p->precision > TENO_FP64_NATIVE || p->flux < 0 ||
       p->flux > 2 || (p->n_var == 1) != (p->flux == TENO_FLUX_UPWIND) || !(p->ct > 0) ||
-      !(p->eps > 0) || !(p->gamma > 1.0) || !(p->cfl > 0))
+      !(p->eps > 0) || !(p->gamma > 1.0) || !(p->cfl > 0) || p->recon_variant < 0 ||
+      p->recon_variant > 1)
     return fail(ctx, TENO_EINVAL, "precompute: bad parameters");
   const int nq_default = p->order <= 4 ? 2 : 3;
   if (p->nq != 0 && p->nq != nq_default)
@@ -1336,6 +1340,7 @@ int teno_check_state(teno_ctx* ctx) {
      "D2H");
   CK(cudaMemsetAsync(ctx->b_flag.p, 0, sizeof(int), ctx->stream), "memset");
   CK(cudaStreamSynchronize(ctx->stream), "sync");
+  if (flag & 2) return fail(ctx, TENO_ETIMEOUT, "a bounded device wait gave up");
   if (flag) return fail(ctx, TENO_ENONPHYS, "non-physical state (rho <= 0, p <= 0 or NaN)");
   return TENO_OK;
 }

@@ -41,6 +41,8 @@ struct DeviceMesh {
   int64_t n_cell = 0, n_pad = 0, n_face = 0;
   int n_var = 1, order = 3, m = 5, ns = 12, nq = 2, e_entries = 0;
   int flux = 0, precision = 0, linear = 0;
+  int tma = 1;              // reconstruction streams its matrices through TMA (Euler, FP64 / mixed)
+  int* err_flag = nullptr;  // device flag: bit 0 non-physical state, bit 1 a bounded wait gave up
   double ct = 1e-6, eps = 1e-12, gamma = 1.4, adv_x = 1, adv_y = 1, cfl = 0.4;
   // reconstruction data, tile-interleaved [tile][entry][32]
   const void* ahat = nullptr;     // double (FP64_NATIVE), float2 (FP64) or float (mixed)

@@ -292,59 +292,13 @@ __device__ __forceinline__ bool chi_keep32(const float* t, int k, int mask, floa
 // differences from the hi/lo FP32 split of U (as accurate as an FP64
 // subtraction rounded to FP32), FP32 matvecs, FP32 beta and cutoff with an FP64
 // fallback inside the guard band, FP32 Gauss-point values.
-template <int M, int NS, int NQ, int NV, typename TA, typename TT>
-__global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const TT ev) {
+// selection, final coefficients and Gauss-point values of cell c, variable v
+// (FP64-native and FP32-mixed paths)
+template <int M, int NQ, int NV, typename TA, typename TT>
+__device__ __forceinline__ void plain_finish(const ReconArgs& a, const TT& ev, int64_t c, int v,
+                                             double u0, float2 u0s, const TA (&acc)[M],
+                                             const TA (&as)[kSmallK][kSmallM]) {
   constexpr bool kMixed = std::is_same<TA, float>::value;
-  const int lane = threadIdx.x, v = threadIdx.y;
-  const int64_t tile = (int64_t)blockIdx.x * blockDim.z + threadIdx.z;
-  const int64_t c = tile * kTile + lane;
-  if (c >= a.n_cell) return;
-  constexpr int E = M * NS + kSmallEntries;
-  constexpr int SL = NS + kSmallSlots;
-  const double* __restrict__ Uv = a.U + (int64_t)v * a.n_pad;
-  const float2* __restrict__ Usv = kMixed ? a.Us + (int64_t)v * a.n_pad : nullptr;
-  double u0 = 0.0;
-  float2 u0s = make_float2(0.f, 0.f);
-  if constexpr (kMixed)
-    u0s = Usv[c];
-  else
-    u0 = Uv[c];
-  const TA* __restrict__ A = reinterpret_cast<const TA*>(a.ahat) + tile * (int64_t)E * kTile + lane;
-  const int32_t* __restrict__ nb = a.nbr + tile * (int64_t)SL * kTile + lane;
-  auto diff = [&](int j) -> TA {
-    if constexpr (kMixed) {
-      const float2 q = __ldg(Usv + j);
-      return (q.x - u0s.x) + (q.y - u0s.y);
-    } else {
-      return __ldg(Uv + j) - u0;
-    }
-  };
-
-  // large stencil: a' = A'' d  (d_s = U_s - U_0)
-  TA acc[M];
-#pragma unroll
-  for (int l = 0; l < M; ++l) acc[l] = TA(0);
-#pragma unroll 2
-  for (int s = 0; s < NS; ++s) {
-    const TA d = diff(__ldg(nb + s * kTile));
-    const TA* As = A + (int64_t)s * M * kTile;
-#pragma unroll
-    for (int l = 0; l < M; ++l) acc[l] = fma(__ldg(As + l * kTile), d, acc[l]);
-  }
-  // directional stencils
-  TA as[kSmallK][kSmallM];
-#pragma unroll
-  for (int k = 0; k < kSmallK; ++k) {
-#pragma unroll
-    for (int l = 0; l < kSmallM; ++l) as[k][l] = TA(0);
-#pragma unroll 2
-    for (int s = 0; s < kSmallN; ++s) {
-      const TA d = diff(__ldg(nb + (NS + k * kSmallN + s) * kTile));
-      const TA* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
-#pragma unroll
-      for (int l = 0; l < kSmallM; ++l) as[k][l] = fma(__ldg(As + l * kTile), d, as[k][l]);
-    }
-  }
   const int present = a.smask[c];
   uint8_t sel;
   if (a.sel_in) {
@@ -438,6 +392,63 @@ __global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const TT 
   }
 }
 
+
+template <int M, int NS, int NQ, int NV, typename TA, typename TT>
+__global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const TT ev) {
+  constexpr bool kMixed = std::is_same<TA, float>::value;
+  const int lane = threadIdx.x, v = threadIdx.y;
+  const int64_t tile = (int64_t)blockIdx.x * blockDim.z + threadIdx.z;
+  const int64_t c = tile * kTile + lane;
+  if (c >= a.n_cell) return;
+  constexpr int E = M * NS + kSmallEntries;
+  constexpr int SL = NS + kSmallSlots;
+  const double* __restrict__ Uv = a.U + (int64_t)v * a.n_pad;
+  const float2* __restrict__ Usv = kMixed ? a.Us + (int64_t)v * a.n_pad : nullptr;
+  double u0 = 0.0;
+  float2 u0s = make_float2(0.f, 0.f);
+  if constexpr (kMixed)
+    u0s = Usv[c];
+  else
+    u0 = Uv[c];
+  const TA* __restrict__ A = reinterpret_cast<const TA*>(a.ahat) + tile * (int64_t)E * kTile + lane;
+  const int32_t* __restrict__ nb = a.nbr + tile * (int64_t)SL * kTile + lane;
+  auto diff = [&](int j) -> TA {
+    if constexpr (kMixed) {
+      const float2 q = __ldg(Usv + j);
+      return (q.x - u0s.x) + (q.y - u0s.y);
+    } else {
+      return __ldg(Uv + j) - u0;
+    }
+  };
+
+  // large stencil: a' = A'' d  (d_s = U_s - U_0)
+  TA acc[M];
+#pragma unroll
+  for (int l = 0; l < M; ++l) acc[l] = TA(0);
+#pragma unroll 2
+  for (int s = 0; s < NS; ++s) {
+    const TA d = diff(__ldg(nb + s * kTile));
+    const TA* As = A + (int64_t)s * M * kTile;
+#pragma unroll
+    for (int l = 0; l < M; ++l) acc[l] = fma(__ldg(As + l * kTile), d, acc[l]);
+  }
+  // directional stencils
+  TA as[kSmallK][kSmallM];
+#pragma unroll
+  for (int k = 0; k < kSmallK; ++k) {
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) as[k][l] = TA(0);
+#pragma unroll 2
+    for (int s = 0; s < kSmallN; ++s) {
+      const TA d = diff(__ldg(nb + (NS + k * kSmallN + s) * kTile));
+      const TA* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) as[k][l] = fma(__ldg(As + l * kTile), d, as[k][l]);
+    }
+  }
+  plain_finish<M, NQ, NV, TA, TT>(a, ev, c, v, u0, u0s, acc, as);
+}
+
 // ------------------------------------------- double-float (FP32 pair) path
 // Values are unevaluated sums hi + lo of two floats (|lo| <= ulp(hi)/2), about
 // 48 significant bits.  Products use the exact FMA residual, sums Knuth's
@@ -469,52 +480,12 @@ __device__ __forceinline__ double df_to_double(DF a) { return (double)a.h + (dou
 // Gauss-point evaluation in pairs (relative error ~2^-46 of the summed
 // magnitudes); the cutoff is decided in FP32 with the guard band of the mixed
 // path and in FP64 inside it; Gauss-point values are written in FP64.
-template <int M, int NS, int NQ, int NV>
-__global__ void __launch_bounds__(128) recon_df_kernel(const ReconArgs a, const DFTable ev) {
-  const int lane = threadIdx.x, v = threadIdx.y;
-  const int64_t tile = (int64_t)blockIdx.x * blockDim.z + threadIdx.z;
-  const int64_t c = tile * kTile + lane;
-  if (c >= a.n_cell) return;
-  constexpr int E = M * NS + kSmallEntries;
-  constexpr int SL = NS + kSmallSlots;
-  const float2* __restrict__ Usv = a.Us + (int64_t)v * a.n_pad;
-  const float2 u0s = Usv[c];
-  const float2* __restrict__ A =
-      reinterpret_cast<const float2*>(a.ahat) + tile * (int64_t)E * kTile + lane;
-  const int32_t* __restrict__ nb = a.nbr + tile * (int64_t)SL * kTile + lane;
-  auto diff = [&](int j) -> DF {
-    const float2 q = __ldg(Usv + j);
-    DF s = two_sum(q.x, -u0s.x);
-    s.l += q.y - u0s.y;
-    return two_sum(s.h, s.l);
-  };
-  DF acc[M];
-#pragma unroll
-  for (int l = 0; l < M; ++l) acc[l] = {0.f, 0.f};
-#pragma unroll 2
-  for (int s = 0; s < NS; ++s) {
-    const DF d = diff(__ldg(nb + s * kTile));
-    const float2* As = A + (int64_t)s * M * kTile;
-#pragma unroll
-    for (int l = 0; l < M; ++l) df_mac(acc[l], __ldg(As + l * kTile), d);
-  }
-#pragma unroll
-  for (int l = 0; l < M; ++l) acc[l] = df_norm(acc[l]);
-  DF as[kSmallK][kSmallM];
-#pragma unroll
-  for (int k = 0; k < kSmallK; ++k) {
-#pragma unroll
-    for (int l = 0; l < kSmallM; ++l) as[k][l] = {0.f, 0.f};
-#pragma unroll 2
-    for (int s = 0; s < kSmallN; ++s) {
-      const DF d = diff(__ldg(nb + (NS + k * kSmallN + s) * kTile));
-      const float2* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
-#pragma unroll
-      for (int l = 0; l < kSmallM; ++l) df_mac(as[k][l], __ldg(As + l * kTile), d);
-    }
-#pragma unroll
-    for (int l = 0; l < kSmallM; ++l) as[k][l] = df_norm(as[k][l]);
-  }
+// selection, final coefficients and Gauss-point values of cell c, variable v
+// (double-float path), from the normalised stencil coefficients
+template <int M, int NQ, int NV>
+__device__ __forceinline__ void df_finish(const ReconArgs& a, const DFTable& ev, int64_t c, int v,
+                                          const DF (&acc)[M],
+                                          const DF (&as)[kSmallK][kSmallM]) {
   const int present = a.smask[c];
   uint8_t sel;
   if (a.sel_in) {
@@ -594,6 +565,281 @@ __global__ void __launch_bounds__(128) recon_df_kernel(const ReconArgs a, const 
     for (int l = 0; l < M; ++l) df_mac(s, ev.psi[p * kMaxM + l], cf[l]);
     s = df_norm(s);
     out[p * NV] = u0 + ((double)s.h + (double)s.l);
+  }
+}
+
+
+template <int M, int NS, int NQ, int NV>
+__global__ void __launch_bounds__(128) recon_df_kernel(const ReconArgs a, const DFTable ev) {
+  const int lane = threadIdx.x, v = threadIdx.y;
+  const int64_t tile = (int64_t)blockIdx.x * blockDim.z + threadIdx.z;
+  const int64_t c = tile * kTile + lane;
+  if (c >= a.n_cell) return;
+  constexpr int E = M * NS + kSmallEntries;
+  constexpr int SL = NS + kSmallSlots;
+  const float2* __restrict__ Usv = a.Us + (int64_t)v * a.n_pad;
+  const float2 u0s = Usv[c];
+  const float2* __restrict__ A =
+      reinterpret_cast<const float2*>(a.ahat) + tile * (int64_t)E * kTile + lane;
+  const int32_t* __restrict__ nb = a.nbr + tile * (int64_t)SL * kTile + lane;
+  auto diff = [&](int j) -> DF {
+    const float2 q = __ldg(Usv + j);
+    DF s = two_sum(q.x, -u0s.x);
+    s.l += q.y - u0s.y;
+    return two_sum(s.h, s.l);
+  };
+  DF acc[M];
+#pragma unroll
+  for (int l = 0; l < M; ++l) acc[l] = {0.f, 0.f};
+#pragma unroll 2
+  for (int s = 0; s < NS; ++s) {
+    const DF d = diff(__ldg(nb + s * kTile));
+    const float2* As = A + (int64_t)s * M * kTile;
+#pragma unroll
+    for (int l = 0; l < M; ++l) df_mac(acc[l], __ldg(As + l * kTile), d);
+  }
+#pragma unroll
+  for (int l = 0; l < M; ++l) acc[l] = df_norm(acc[l]);
+  DF as[kSmallK][kSmallM];
+#pragma unroll
+  for (int k = 0; k < kSmallK; ++k) {
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) as[k][l] = {0.f, 0.f};
+#pragma unroll 2
+    for (int s = 0; s < kSmallN; ++s) {
+      const DF d = diff(__ldg(nb + (NS + k * kSmallN + s) * kTile));
+      const float2* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) df_mac(as[k][l], __ldg(As + l * kTile), d);
+    }
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) as[k][l] = df_norm(as[k][l]);
+  }
+  df_finish<M, NQ, NV>(a, ev, c, v, acc, as);
+}
+
+// -------------------------------------------- TMA-staged reconstruction
+// The per-cell matrices of a 32-cell tile are one contiguous block of global
+// memory ([tile][entry][32]).  One producer lane streams that block into a
+// ring of kRing shared-memory buffers with 1D bulk copies (cp.async.bulk,
+// completion counted in bytes on the buffer's "full" mbarrier); the four
+// consumer warps of the tile (one per conservative variable) wait on "full",
+// accumulate from shared memory, and release the buffer on its "empty"
+// mbarrier.  Every wait is bounded: a wait that gives up sets bit 1 of the
+// error flag and the thread returns (the producer first waits, bounded, for
+// the copies it has in flight).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+constexpr uint32_t kWaitLimit = 1u << 22;
+// wait for the completion of the phase with the given parity; false on give-up
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i)
+    if (mbar_test(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+constexpr int kRing = 4;
+constexpr int kConsumers = 4;  // one warp per conservative variable (Euler)
+
+// stage j of a tile: large-stencil slots in groups of kLPS, then one stage per
+// directional stencil
+template <int M, int NS, int kEsz, int kCap>
+struct StagePlan {
+  static constexpr int kSlotBytes = M * kTile * kEsz;
+  static constexpr int kLPS = (kCap / kSlotBytes) > 0 ? (kCap / kSlotBytes) : 1;
+  static constexpr int kNL = (NS + kLPS - 1) / kLPS;
+  static constexpr int kStages = kNL + kSmallK;
+  static constexpr int kSmallBytes = kSmallN * kSmallM * kTile * kEsz;
+  static constexpr int kBuf = (kLPS * kSlotBytes > kSmallBytes) ? kLPS * kSlotBytes : kSmallBytes;
+  static constexpr int kE = M * NS + kSmallEntries;
+  static constexpr int64_t kTileBytes = (int64_t)kE * kTile * kEsz;
+  static constexpr size_t kSmem = (size_t)kRing * kBuf + 2 * kRing * sizeof(uint64_t);
+  __device__ static void stage(int j, int& slot0, int& nslot, int64_t& off, int& bytes) {
+    if (j < kNL) {
+      slot0 = j * kLPS;
+      nslot = (NS - slot0) < kLPS ? (NS - slot0) : kLPS;
+      off = (int64_t)slot0 * kSlotBytes;
+      bytes = nslot * kSlotBytes;
+    } else {
+      const int k = j - kNL;
+      slot0 = NS + k * kSmallN;
+      nslot = kSmallN;
+      off = (int64_t)(M * NS + k * kSmallN * kSmallM) * kTile * kEsz;
+      bytes = kSmallBytes;
+    }
+  }
+};
+
+template <bool kDF>
+struct TmaTraits {
+  using TE = float2;  // matrix entry: (hi, lo)
+  using Acc = DF;
+  static constexpr int kCap = 16384;
+};
+template <>
+struct TmaTraits<false> {
+  using TE = float;
+  using Acc = float;
+  static constexpr int kCap = 8192;
+};
+
+// kDF: FP64 path (double-float); !kDF: FP32-mixed path.  Euler only.
+template <int M, int NS, int NQ, bool kDF>
+__global__ void __launch_bounds__(kTile * (kConsumers + 1))
+    recon_tma_kernel(const ReconArgs a, const DFTable ev, int* err) {
+  using TR = TmaTraits<kDF>;
+  using TE = typename TR::TE;
+  using P = StagePlan<M, NS, (int)sizeof(TE), TR::kCap>;
+  constexpr int NV = 4;
+  constexpr int SL = NS + kSmallSlots;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kRing * P::kBuf);
+  uint64_t* empty = full + kRing;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tile = blockIdx.x;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kRing; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kConsumers);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (warp == kConsumers) {
+    // ---- producer
+    if (lane == 0) {
+      const unsigned char* src = reinterpret_cast<const unsigned char*>(a.ahat) + tile * P::kTileBytes;
+      for (int j = 0; j < P::kStages; ++j) {
+        const int b = j % kRing;
+        if (j >= kRing && !mbar_wait(&empty[b], ((j / kRing) - 1) & 1)) {
+          atomicOr(err, 2);
+          for (int i = (j >= kRing ? j - kRing : 0); i < j; ++i)
+            mbar_wait(&full[i % kRing], (i / kRing) & 1);
+          return;
+        }
+        int slot0, nslot, bytes;
+        int64_t off;
+        P::stage(j, slot0, nslot, off, bytes);
+        mbar_expect_tx(&full[b], (uint32_t)bytes);
+        bulk_g2s(smem + (size_t)b * P::kBuf, src + off, (uint32_t)bytes, &full[b]);
+      }
+    }
+    return;
+  }
+  // ---- consumers: warp v = variable v of the tile's 32 cells
+  const int v = warp;
+  const int64_t c = tile * kTile + lane;  // may be a pad lane of the last tile
+  const float2* __restrict__ Usv = a.Us + (int64_t)v * a.n_pad;
+  const float2 u0s = Usv[c < a.n_cell ? c : 0];
+  const int32_t* __restrict__ nb = a.nbr + tile * (int64_t)SL * kTile + lane;
+  using Acc = typename TR::Acc;
+  auto diff = [&](int j) -> Acc {
+    const float2 q = __ldg(Usv + j);
+    if constexpr (kDF) {
+      DF s = two_sum(q.x, -u0s.x);
+      s.l += q.y - u0s.y;
+      return two_sum(s.h, s.l);
+    } else {
+      return (q.x - u0s.x) + (q.y - u0s.y);
+    }
+  };
+  auto mac = [](Acc& acc, TE m, Acc d) {
+    if constexpr (kDF)
+      df_mac(acc, m, d);
+    else
+      acc = fmaf(m, d, acc);
+  };
+  Acc acc[M];
+  Acc as[kSmallK][kSmallM];
+#pragma unroll
+  for (int l = 0; l < M; ++l) acc[l] = Acc{};
+#pragma unroll
+  for (int k = 0; k < kSmallK; ++k)
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) as[k][l] = Acc{};
+  for (int j = 0; j < P::kStages; ++j) {
+    const int b = j % kRing;
+    int slot0, nslot, bytes;
+    int64_t off;
+    P::stage(j, slot0, nslot, off, bytes);
+    // neighbour differences of this stage's slots (issued before the wait)
+    Acc dv[P::kLPS > kSmallN ? P::kLPS : kSmallN];
+#pragma unroll
+    for (int s = 0; s < (P::kLPS > kSmallN ? P::kLPS : kSmallN); ++s)
+      if (s < nslot) dv[s] = diff(__ldg(nb + (slot0 + s) * kTile));
+    if (!mbar_wait(&full[b], (j / kRing) & 1)) {
+      atomicOr(err, 2);
+      return;
+    }
+    const TE* buf = reinterpret_cast<const TE*>(smem + (size_t)b * P::kBuf) + lane;
+    if (j < P::kNL) {
+#pragma unroll
+      for (int s = 0; s < P::kLPS; ++s) {
+        if (s < nslot) {
+#pragma unroll
+          for (int l = 0; l < M; ++l) mac(acc[l], buf[(s * M + l) * kTile], dv[s]);
+        }
+      }
+    } else {
+      const int k = j - P::kNL;
+#pragma unroll
+      for (int kk = 0; kk < kSmallK; ++kk) {
+        if (kk != k) continue;
+#pragma unroll
+        for (int s = 0; s < kSmallN; ++s)
+#pragma unroll
+          for (int l = 0; l < kSmallM; ++l) mac(as[kk][l], buf[(s * kSmallM + l) * kTile], dv[s]);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[b]);
+  }
+  if (c >= a.n_cell) return;
+  if constexpr (kDF) {
+#pragma unroll
+    for (int l = 0; l < M; ++l) acc[l] = df_norm(acc[l]);
+#pragma unroll
+    for (int k = 0; k < kSmallK; ++k)
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) as[k][l] = df_norm(as[k][l]);
+    df_finish<M, NQ, NV>(a, ev, c, v, acc, as);
+  } else {
+    plain_finish<M, NQ, NV, float, DFTable>(a, ev, c, v, 0.0, u0s, acc, as);
   }
 }
 
@@ -972,6 +1218,19 @@ cudaError_t dispatch_order(int order, F&& f) {
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
+template <int M, int NS, int NQ, bool kDF>
+cudaError_t launch_recon_tma(const ReconArgs& a, const DeviceMesh& dm, int* err, cudaStream_t st) {
+  using TR = TmaTraits<kDF>;
+  using P = StagePlan<M, NS, (int)sizeof(typename TR::TE), TR::kCap>;
+  auto kern = recon_tma_kernel<M, NS, NQ, kDF>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)P::kSmem);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
+  kern<<<(unsigned)tiles, kTile * (kConsumers + 1), P::kSmem, st>>>(a, dm.eval_df, err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us, void* Uq,
                          uint8_t* sel_out, const uint8_t* sel_in, cudaStream_t st) {
   if (dm.precision != TENO_FP64_NATIVE && !Us) return cudaErrorInvalidValue;
@@ -995,6 +1254,12 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
     constexpr int M = decltype(Mc)::value, NS = decltype(NSc)::value;
     auto go = [&](auto nqc, auto nvc) -> cudaError_t {
       constexpr int NQ = decltype(nqc)::value, NV = decltype(nvc)::value;
+      if constexpr (NV == 4) {
+        if (dm.tma && dm.err_flag && dm.precision != TENO_FP64_NATIVE) {
+          if (dm.precision == TENO_FP64) return launch_recon_tma<M, NS, NQ, true>(a, dm, dm.err_flag, st);
+          return launch_recon_tma<M, NS, NQ, false>(a, dm, dm.err_flag, st);
+        }
+      }
       constexpr int TZ = 4 / NV;  // 128 threads per block
       dim3 block(kTile, NV, TZ);
       dim3 grid((unsigned)((tiles + TZ - 1) / TZ));

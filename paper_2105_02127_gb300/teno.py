@@ -34,6 +34,7 @@ class TenoError(RuntimeError):
 class teno_params(C.Structure):
     _fields_ = [("order", C.c_int32), ("n_var", C.c_int32), ("flux", C.c_int32),
                 ("precision", C.c_int32), ("linear", C.c_int32), ("nq", C.c_int32),
+                ("recon_variant", C.c_int32),
                 ("ct", C.c_double), ("eps", C.c_double), ("gamma", C.c_double),
                 ("adv_x", C.c_double), ("adv_y", C.c_double), ("cfl", C.c_double)]
 

@@ -32,16 +32,16 @@ def rel(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max())
 
 
-def _setup(T, mesh, order, nvar, flux, precision=0, linear=False):
+def _setup(T, mesh, order, nvar, flux, precision=0, linear=False, variant=0):
     t = T.Teno(device=0).load(mesh)
     t.precompute_stencils(order=order, n_var=nvar, flux=flux, precision=precision,
-                          linear=int(linear))
+                          linear=int(linear), recon_variant=variant)
     return t
 
 
 def _check_residual(T, oracle_mod, mesh, U, order, nvar, flux, linear=False, tol=TOL,
-                    precision=0):
-    t = _setup(T, mesh, order, nvar, flux, linear=linear, precision=precision)
+                    precision=0, variant=0):
+    t = _setup(T, mesh, order, nvar, flux, linear=linear, precision=precision, variant=variant)
     t.set_state(U)
     R, sel = t.residual(want_sel=True)
     o = oracle_mod.Oracle(mesh, order=order, n_var=nvar, flux=flux, linear=linear)
@@ -54,6 +54,7 @@ def _check_residual(T, oracle_mod, mesh, U, order, nvar, flux, linear=False, tol
         t.set_selection_override(None)
     e = rel(R, Ro)
     assert e <= tol, e
+    t.check_state()  # no bounded device wait gave up
     return t, o, R, Ro, selo
 
 
@@ -96,25 +97,28 @@ def test_scalar_teno3_config1(T, oracle_mod):
     assert rel(t.get_state(), Uo) <= TOL
 
 
-@pytest.mark.parametrize("precision", [0, 2], ids=["fp64", "fp64native"])
+@pytest.mark.parametrize("precision,variant", [(0, 0), (0, 1), (2, 0)],
+                         ids=["fp64-tma", "fp64-direct", "fp64native"])
 @pytest.mark.parametrize("order", [3, 4, 5, 6])
-def test_euler_vortex_hll(T, oracle_mod, order, precision):
-    """Isentropic vortex, HLL, FP64 (double-float and native) on a 33x31
-    jittered mesh (2046 cells: 64 tiles of 32 and a ragged tail)."""
+def test_euler_vortex_hll(T, oracle_mod, order, precision, variant):
+    """Isentropic vortex, HLL, FP64 (double-float with TMA-staged or direct
+    matrix loads, and native) on a 33x31 jittered mesh (2046 cells: 64 tiles
+    of 32 and a ragged tail)."""
     mesh = inputs.jittered_mesh(33, 31, 10.0, 10.0, seed=1002)
     U = inputs.cell_average(mesh, inputs.isentropic_vortex)
-    _check_residual(T, oracle_mod, mesh, U, order, 4, 1, precision=precision)
+    _check_residual(T, oracle_mod, mesh, U, order, 4, 1, precision=precision, variant=variant)
 
 
-@pytest.mark.parametrize("precision", [0, 2], ids=["fp64", "fp64native"])
+@pytest.mark.parametrize("precision,variant", [(0, 0), (0, 1), (2, 0)],
+                         ids=["fp64-tma", "fp64-direct", "fp64native"])
 @pytest.mark.parametrize("order,flux", [(6, 2), (5, 1), (4, 2), (3, 1)])
-def test_euler_discontinuous(T, oracle_mod, order, flux, precision):
+def test_euler_discontinuous(T, oracle_mod, order, flux, precision, variant):
     """A density/pressure square exercises the cutoff and the directional
     stencils (HLLC and HLL)."""
     mesh = inputs.jittered_mesh(40, 40, 10.0, 10.0, seed=1007)
     U = _blast(mesh)
     t, o, R, Ro, sel = _check_residual(T, oracle_mod, mesh, U, order, 4, flux,
-                                       precision=precision)
+                                       precision=precision, variant=variant)
     assert (sel != 8).mean() > 0.01  # the small stencils are in use
 
 
@@ -152,21 +156,23 @@ def test_rk3_fixed_and_cfl(T, oracle_mod):
     assert rel(t.get_state(), Uo) <= TOL
 
 
-def test_mixed_precision_report(T, oracle_mod):
+@pytest.mark.parametrize("variant", [0, 1], ids=["tma", "direct"])
+def test_mixed_precision_report(T, oracle_mod, variant):
     """FP32-mixed: matvecs and fluxes in FP32, selection and residual
     accumulation in FP64.  Reports error vs the FP64 oracle and the selection
     flip rate; both must stay small."""
     mesh = inputs.jittered_mesh(40, 40, 10.0, 10.0, seed=1013)
     for U, order, flux in [(inputs.cell_average(mesh, inputs.isentropic_vortex), 5, 1),
                            (_blast(mesh), 6, 2)]:
-        t = _setup(T, mesh, order, 4, flux, precision=1)
+        t = _setup(T, mesh, order, 4, flux, precision=1, variant=variant)
         t.set_state(U)
         R, sel = t.residual(want_sel=True)
         o = oracle_mod.Oracle(mesh, order=order, n_var=4, flux=flux)
         Ro, selo, _ = o.residual(U)
         err = rel(R, Ro)
         flips = float((sel != selo).mean())
-        print(f"mixed order {order}: rel err {err:.2e}, flip rate {flips:.2e}")
+        print(f"mixed order {order} variant {variant}: rel err {err:.2e}, flip rate {flips:.2e}")
+        t.check_state()
         assert err < 1e-4 and flips < 1e-2
 
 
