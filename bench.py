@@ -178,23 +178,16 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2105_02127_gb300 import replicas
+
+    rank, world, local = replicas.world()
     if world > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    barrier = replicas.barrier
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        tt = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        return float(tt.item())
+        return replicas.max_over_ranks(x, device="cuda")
 
     import __graft_entry__ as g
     g.build()

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "teno_internal.h"
@@ -676,31 +677,44 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 constexpr int kRing = 4;
 constexpr int kConsumers = 4;  // one warp per conservative variable (Euler)
 
-// stage j of a tile: large-stencil slots in groups of kLPS, then one stage per
-// directional stencil
-template <int M, int NS, int kEsz, int kCap>
+// Stage j of a tile: kLPS large-stencil slots, or kSPS slots of one
+// directional stencil.  A ring buffer holds the stage's matrix entries
+// (bulk-copied) followed by the gathered neighbour states [slot][var][32]
+// (float2 hi/lo splits).
+template <int M, int NS, int kEsz, int kLPS, int kSPS>
 struct StagePlan {
-  static constexpr int kSlotBytes = M * kTile * kEsz;
-  static constexpr int kLPS = (kCap / kSlotBytes) > 0 ? (kCap / kSlotBytes) : 1;
+  static constexpr int kSlotL = M * kTile * kEsz;            // matrix bytes of a large slot
+  static constexpr int kSlotS = kSmallM * kTile * kEsz;      // ... of a directional slot
+  static constexpr int kStateSlot = 4 * kTile * 8;           // gathered states of one slot
   static constexpr int kNL = (NS + kLPS - 1) / kLPS;
-  static constexpr int kStages = kNL + kSmallK;
-  static constexpr int kSmallBytes = kSmallN * kSmallM * kTile * kEsz;
-  static constexpr int kBuf = (kLPS * kSlotBytes > kSmallBytes) ? kLPS * kSlotBytes : kSmallBytes;
+  static constexpr int kPerSmall = kSmallN / kSPS;
+  static constexpr int kStages = kNL + kSmallK * kPerSmall;
+  static constexpr int kMatL = kLPS * kSlotL, kMatS = kSPS * kSlotS;
+  static constexpr int kMat = kMatL > kMatS ? kMatL : kMatS;  // matrix part of a buffer
+  static constexpr int kMaxSlots = kLPS > kSPS ? kLPS : kSPS;
+  static constexpr int kBuf = kMat + kMaxSlots * kStateSlot;
   static constexpr int kE = M * NS + kSmallEntries;
   static constexpr int64_t kTileBytes = (int64_t)kE * kTile * kEsz;
   static constexpr size_t kSmem = (size_t)kRing * kBuf + 2 * kRing * sizeof(uint64_t);
-  __device__ static void stage(int j, int& slot0, int& nslot, int64_t& off, int& bytes) {
+  static_assert(kSmallN % kSPS == 0, "directional stencil split");
+  static_assert(kMat % 16 == 0 && kBuf % 16 == 0, "16-byte aligned buffers");
+  // first slot, slot count, matrix byte offset within the tile block, bytes,
+  // directional stencil index (-1: large)
+  __device__ static void stage(int j, int& slot0, int& nslot, int64_t& off, int& bytes, int& k) {
     if (j < kNL) {
       slot0 = j * kLPS;
       nslot = (NS - slot0) < kLPS ? (NS - slot0) : kLPS;
-      off = (int64_t)slot0 * kSlotBytes;
-      bytes = nslot * kSlotBytes;
+      off = (int64_t)slot0 * kSlotL;
+      bytes = nslot * kSlotL;
+      k = -1;
     } else {
-      const int k = j - kNL;
-      slot0 = NS + k * kSmallN;
-      nslot = kSmallN;
-      off = (int64_t)(M * NS + k * kSmallN * kSmallM) * kTile * kEsz;
-      bytes = kSmallBytes;
+      const int i = j - kNL;
+      k = i / kPerSmall;
+      const int s0 = (i % kPerSmall) * kSPS;  // first slot within the directional stencil
+      slot0 = NS + k * kSmallN + s0;
+      nslot = kSPS;
+      off = (int64_t)(M * NS + (k * kSmallN + s0) * kSmallM) * kTile * kEsz;
+      bytes = kSPS * kSlotS;
     }
   }
 };
@@ -709,137 +723,165 @@ template <bool kDF>
 struct TmaTraits {
   using TE = float2;  // matrix entry: (hi, lo)
   using Acc = DF;
-  static constexpr int kCap = 16384;
+  static constexpr int kLPS = 4, kSPS = 4;
 };
 template <>
 struct TmaTraits<false> {
   using TE = float;
   using Acc = float;
-  static constexpr int kCap = 8192;
+  static constexpr int kLPS = 4, kSPS = 4;
 };
 
-// kDF: FP64 path (double-float); !kDF: FP32-mixed path.  Euler only.
+// Persistent kernel: CTAs loop over tiles; the stage counter g runs on across
+// tiles so the producer keeps up to kRing stages in flight.  kDF: FP64 path
+// (double-float); !kDF: FP32-mixed path.  Euler only.
 template <int M, int NS, int NQ, bool kDF>
 __global__ void __launch_bounds__(kTile * (kConsumers + 1))
     recon_tma_kernel(const ReconArgs a, const DFTable ev, int* err) {
   using TR = TmaTraits<kDF>;
   using TE = typename TR::TE;
-  using P = StagePlan<M, NS, (int)sizeof(TE), TR::kCap>;
+  using P = StagePlan<M, NS, (int)sizeof(TE), TR::kLPS, TR::kSPS>;
   constexpr int NV = 4;
   constexpr int SL = NS + kSmallSlots;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kRing * P::kBuf);
   uint64_t* empty = full + kRing;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t tile = blockIdx.x;
+  const int64_t n_tiles = (a.n_cell + kTile - 1) / kTile;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kRing; ++i) {
-      mbar_init(&full[i], 1);
+      mbar_init(&full[i], 2);  // producer lane 0: expect_tx arrival + gather-done arrival
       mbar_init(&empty[i], kConsumers);
     }
     mbar_fence_init();
   }
   __syncthreads();
   if (warp == kConsumers) {
-    // ---- producer
-    if (lane == 0) {
+    // ---- producer warp: matrices by bulk copy (lane 0), neighbour states by
+    // all lanes
+    int64_t g = 0;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
       const unsigned char* src = reinterpret_cast<const unsigned char*>(a.ahat) + tile * P::kTileBytes;
-      for (int j = 0; j < P::kStages; ++j) {
-        const int b = j % kRing;
-        if (j >= kRing && !mbar_wait(&empty[b], ((j / kRing) - 1) & 1)) {
-          atomicOr(err, 2);
-          for (int i = (j >= kRing ? j - kRing : 0); i < j; ++i)
-            mbar_wait(&full[i % kRing], (i / kRing) & 1);
-          return;
-        }
-        int slot0, nslot, bytes;
+      const int32_t* nb = a.nbr + tile * (int64_t)SL * kTile + lane;
+      for (int j = 0; j < P::kStages; ++j, ++g) {
+        const int b = (int)(g % kRing);
+        int slot0, nslot, bytes, k;
         int64_t off;
-        P::stage(j, slot0, nslot, off, bytes);
-        mbar_expect_tx(&full[b], (uint32_t)bytes);
-        bulk_g2s(smem + (size_t)b * P::kBuf, src + off, (uint32_t)bytes, &full[b]);
+        P::stage(j, slot0, nslot, off, bytes, k);
+        if (g >= kRing) {
+          bool ok = true;
+          if (lane == 0) ok = mbar_wait(&empty[b], (uint32_t)((g / kRing) - 1) & 1);
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (!ok) {
+            if (lane == 0) {
+              atomicOr(err, 2);
+              for (int64_t i = g - kRing; i < g; ++i) mbar_wait(&full[i % kRing], (uint32_t)(i / kRing) & 1);
+            }
+            return;
+          }
+        }
+        unsigned char* buf = smem + (size_t)b * P::kBuf;
+        if (lane == 0) {
+          mbar_expect_tx(&full[b], (uint32_t)bytes);
+          bulk_g2s(buf, src + off, (uint32_t)bytes, &full[b]);
+        }
+        float2* st = reinterpret_cast<float2*>(buf + P::kMat);
+        int idx[P::kMaxSlots];
+#pragma unroll
+        for (int s = 0; s < P::kMaxSlots; ++s) idx[s] = s < nslot ? __ldg(nb + (slot0 + s) * kTile) : 0;
+#pragma unroll
+        for (int s = 0; s < P::kMaxSlots; ++s) {
+          if (s < nslot) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) st[(s * NV + v) * kTile + lane] = __ldg(a.Us + v * a.n_pad + idx[s]);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[b]);
       }
     }
     return;
   }
   // ---- consumers: warp v = variable v of the tile's 32 cells
   const int v = warp;
-  const int64_t c = tile * kTile + lane;  // may be a pad lane of the last tile
-  const float2* __restrict__ Usv = a.Us + (int64_t)v * a.n_pad;
-  const float2 u0s = Usv[c < a.n_cell ? c : 0];
-  const int32_t* __restrict__ nb = a.nbr + tile * (int64_t)SL * kTile + lane;
   using Acc = typename TR::Acc;
-  auto diff = [&](int j) -> Acc {
-    const float2 q = __ldg(Usv + j);
-    if constexpr (kDF) {
-      DF s = two_sum(q.x, -u0s.x);
-      s.l += q.y - u0s.y;
-      return two_sum(s.h, s.l);
-    } else {
-      return (q.x - u0s.x) + (q.y - u0s.y);
-    }
-  };
   auto mac = [](Acc& acc, TE m, Acc d) {
     if constexpr (kDF)
       df_mac(acc, m, d);
     else
       acc = fmaf(m, d, acc);
   };
-  Acc acc[M];
-  Acc as[kSmallK][kSmallM];
+  int64_t g = 0;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t c = tile * kTile + lane;  // may be a pad lane of the last tile
+    const float2 u0s = a.Us[(int64_t)v * a.n_pad + (c < a.n_cell ? c : 0)];
+    Acc acc[M];
+    Acc as[kSmallK][kSmallM];
 #pragma unroll
-  for (int l = 0; l < M; ++l) acc[l] = Acc{};
-#pragma unroll
-  for (int k = 0; k < kSmallK; ++k)
-#pragma unroll
-    for (int l = 0; l < kSmallM; ++l) as[k][l] = Acc{};
-  for (int j = 0; j < P::kStages; ++j) {
-    const int b = j % kRing;
-    int slot0, nslot, bytes;
-    int64_t off;
-    P::stage(j, slot0, nslot, off, bytes);
-    // neighbour differences of this stage's slots (issued before the wait)
-    Acc dv[P::kLPS > kSmallN ? P::kLPS : kSmallN];
-#pragma unroll
-    for (int s = 0; s < (P::kLPS > kSmallN ? P::kLPS : kSmallN); ++s)
-      if (s < nslot) dv[s] = diff(__ldg(nb + (slot0 + s) * kTile));
-    if (!mbar_wait(&full[b], (j / kRing) & 1)) {
-      atomicOr(err, 2);
-      return;
-    }
-    const TE* buf = reinterpret_cast<const TE*>(smem + (size_t)b * P::kBuf) + lane;
-    if (j < P::kNL) {
-#pragma unroll
-      for (int s = 0; s < P::kLPS; ++s) {
-        if (s < nslot) {
-#pragma unroll
-          for (int l = 0; l < M; ++l) mac(acc[l], buf[(s * M + l) * kTile], dv[s]);
-        }
-      }
-    } else {
-      const int k = j - P::kNL;
-#pragma unroll
-      for (int kk = 0; kk < kSmallK; ++kk) {
-        if (kk != k) continue;
-#pragma unroll
-        for (int s = 0; s < kSmallN; ++s)
-#pragma unroll
-          for (int l = 0; l < kSmallM; ++l) mac(as[kk][l], buf[(s * kSmallM + l) * kTile], dv[s]);
-      }
-    }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[b]);
-  }
-  if (c >= a.n_cell) return;
-  if constexpr (kDF) {
-#pragma unroll
-    for (int l = 0; l < M; ++l) acc[l] = df_norm(acc[l]);
+    for (int l = 0; l < M; ++l) acc[l] = Acc{};
 #pragma unroll
     for (int k = 0; k < kSmallK; ++k)
 #pragma unroll
-      for (int l = 0; l < kSmallM; ++l) as[k][l] = df_norm(as[k][l]);
-    df_finish<M, NQ, NV>(a, ev, c, v, acc, as);
-  } else {
-    plain_finish<M, NQ, NV, float, DFTable>(a, ev, c, v, 0.0, u0s, acc, as);
+      for (int l = 0; l < kSmallM; ++l) as[k][l] = Acc{};
+    for (int j = 0; j < P::kStages; ++j, ++g) {
+      const int b = (int)(g % kRing);
+      int slot0, nslot, bytes, k;
+      int64_t off;
+      P::stage(j, slot0, nslot, off, bytes, k);
+      if (!mbar_wait(&full[b], (uint32_t)(g / kRing) & 1)) {
+        atomicOr(err, 2);
+        return;
+      }
+      const unsigned char* buf = smem + (size_t)b * P::kBuf;
+      const TE* mat = reinterpret_cast<const TE*>(buf) + lane;
+      const float2* st = reinterpret_cast<const float2*>(buf + P::kMat) + v * kTile + lane;
+      auto dif = [&](int s) -> Acc {
+        const float2 q = st[s * NV * kTile];
+        if constexpr (kDF) {
+          DF t = two_sum(q.x, -u0s.x);
+          t.l += q.y - u0s.y;
+          return two_sum(t.h, t.l);
+        } else {
+          return (q.x - u0s.x) + (q.y - u0s.y);
+        }
+      };
+      if (k < 0) {
+#pragma unroll
+        for (int s = 0; s < TR::kLPS; ++s) {
+          if (s < nslot) {
+            const Acc d = dif(s);
+#pragma unroll
+            for (int l = 0; l < M; ++l) mac(acc[l], mat[(s * M + l) * kTile], d);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < kSmallK; ++kk) {
+          if (kk != k) continue;
+#pragma unroll
+          for (int s = 0; s < TR::kSPS; ++s) {
+            const Acc d = dif(s);
+#pragma unroll
+            for (int l = 0; l < kSmallM; ++l) mac(as[kk][l], mat[(s * kSmallM + l) * kTile], d);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[b]);
+    }
+    if (c < a.n_cell) {
+      if constexpr (kDF) {
+#pragma unroll
+        for (int l = 0; l < M; ++l) acc[l] = df_norm(acc[l]);
+#pragma unroll
+        for (int k = 0; k < kSmallK; ++k)
+#pragma unroll
+          for (int l = 0; l < kSmallM; ++l) as[k][l] = df_norm(as[k][l]);
+        df_finish<M, NQ, NV>(a, ev, c, v, acc, as);
+      } else {
+        plain_finish<M, NQ, NV, float, DFTable>(a, ev, c, v, 0.0, u0s, acc, as);
+      }
+    }
   }
 }
 
@@ -1221,13 +1263,23 @@ cudaError_t dispatch_order(int order, F&& f) {
 template <int M, int NS, int NQ, bool kDF>
 cudaError_t launch_recon_tma(const ReconArgs& a, const DeviceMesh& dm, int* err, cudaStream_t st) {
   using TR = TmaTraits<kDF>;
-  using P = StagePlan<M, NS, (int)sizeof(typename TR::TE), TR::kCap>;
+  using P = StagePlan<M, NS, (int)sizeof(typename TR::TE), TR::kLPS, TR::kSPS>;
   auto kern = recon_tma_kernel<M, NS, NQ, kDF>;
+  const int threads = kTile * (kConsumers + 1);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)P::kSmem);
   if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, P::kSmem)) !=
+      cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
-  kern<<<(unsigned)tiles, kTile * (kConsumers + 1), P::kSmem, st>>>(a, dm.eval_df, err);
+  const int64_t grid = std::min<int64_t>(tiles, (int64_t)per_sm * sms);
+  kern<<<(unsigned)grid, threads, P::kSmem, st>>>(a, dm.eval_df, err);
   return cudaGetLastError();
 }
 
