@@ -55,8 +55,8 @@ def parse():
     ap.add_argument("--order", type=int, default=5)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the mixed, adjoint, e2e and CPU-baseline legs")
-    ap.add_argument("--recon-variant", type=int, default=0, choices=[0, 1],
-                    help="0: matrices streamed through TMA bulk copies, 1: direct loads")
+    ap.add_argument("--recon-variant", type=int, default=0, choices=[0, 1, 2],
+                    help="reconstruction kernel: 0 halo-staged, 1 direct gathers, 2 TMA-staged")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="path timed as the primary line (the other one is an extra)")
     return ap.parse_args()
@@ -226,10 +226,8 @@ def run_ours(args):
         store = "fp32_mixed" if precision == "fp32_mixed" else "fp64"
         nbytes = algorithmic_bytes(args.order, 4, store) * n_cell
         gbs = nbytes / (rec_ms / 1e3) / 1e9
-        tma = args.recon_variant == 0
-        kernel = {"fp64": ("recon_tma_kernel<df>" if tma else "recon_df_kernel") + f" order {args.order}",
-                  "fp32_mixed": ("recon_tma_kernel<f32>" if tma else "recon_kernel<float>") + f" order {args.order}",
-                  "fp64_native": f"recon_kernel<double> order {args.order}"}[precision]
+        vname = ["recon_halo_kernel", "recon_kernel (direct)", "recon_tma_kernel"][args.recon_variant]
+        kernel = f"{vname} <{precision}> order {args.order}"
         roof_hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
                     "frac": gbs / hbm_gbs, "traffic": NCU_TRAFFIC.get(precision),
                     "kernel": kernel, "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)"}

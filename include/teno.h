@@ -74,8 +74,11 @@ typedef struct teno_params {
   int32_t precision; /* enum teno_precision */
   int32_t linear;    /* 1: always take the large-stencil polynomial (the paper's "Linear" rows) */
   int32_t nq;        /* Gauss points per edge; 0 = 2 for order <= 4, 3 otherwise */
-  int32_t recon_variant; /* 0: per-cell matrices streamed through TMA bulk copies where
-                            available (Euler, TENO_FP64 and TENO_FP32_MIXED); 1: direct loads */
+  int32_t recon_variant; /* reconstruction kernel: 0 the stencil halo of each 32-cell tile
+                            staged in shared memory (falls back to 1 if a halo exceeds 256
+                            cells); 1 direct gathers of neighbour states; 2 matrices and
+                            neighbour states staged through TMA bulk copies by a producer
+                            warp (Euler, TENO_FP64 and TENO_FP32_MIXED; else 1) */
   double ct;         /* cutoff C_T */
   double eps;        /* epsilon of the scale separation */
   double gamma;      /* ratio of specific heats */

@@ -66,6 +66,7 @@ struct teno_ctx {
   std::vector<int32_t> st_large, st_small;  // user ids, [nc][ns], [nc][36]
   // device data
   DeviceMesh dm;
+  DevBuf b_halo_off, b_halo_ids, b_halo_loc;
   DevBuf b_ahat, b_nbr, b_smask, b_fcells, b_fedges, b_fgeom, b_cfaces, b_inv_area, b_cfl_len,
       b_perm;
   DevBuf b_U, b_U1, b_U2, b_R, b_tmp, b_Uq, b_K, b_sel, b_sel_ovr, b_maxlam, b_flag;
@@ -776,8 +777,33 @@ int run_precompute(teno_ctx* ctx) {
       }
     }
   }
+  // per-tile stencil halos (distinct stencil cells of each 32-cell tile)
+  bool halo_ok = true;
+  std::vector<int32_t> hoff(ntile + 1, 0), hids;
+  std::vector<uint16_t> hloc((size_t)ntile * SL * kTile, 0);
+  {
+    std::vector<int32_t> ids;
+    for (int64_t t = 0; t < ntile && halo_ok; ++t) {
+      const int32_t* tn = &nbr[(size_t)t * SL * kTile];
+      ids.assign(tn, tn + (size_t)SL * kTile);
+      std::sort(ids.begin(), ids.end());
+      ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+      if ((int)ids.size() > kHaloMax) {
+        halo_ok = false;
+        break;
+      }
+      for (size_t i = 0; i < (size_t)SL * kTile; ++i)
+        hloc[(size_t)t * SL * kTile + i] =
+            (uint16_t)(std::lower_bound(ids.begin(), ids.end(), tn[i]) - ids.begin());
+      hids.insert(hids.end(), ids.begin(), ids.end());
+      hoff[t + 1] = (int32_t)hids.size();
+    }
+  }
   int e = upload(ctx, ctx->b_ahat, ahat.data(), ahat.size());
   if (!e) e = upload(ctx, ctx->b_nbr, nbr.data(), nbr.size() * sizeof(int32_t));
+  if (!e && halo_ok) e = upload(ctx, ctx->b_halo_off, hoff.data(), hoff.size() * 4);
+  if (!e && halo_ok) e = upload(ctx, ctx->b_halo_ids, hids.data(), hids.size() * 4);
+  if (!e && halo_ok) e = upload(ctx, ctx->b_halo_loc, hloc.data(), hloc.size() * 2);
   if (!e) e = upload(ctx, ctx->b_smask, smask.data(), smask.size());
   if (e) return e;
   // device mesh descriptor
@@ -797,7 +823,13 @@ int run_precompute(teno_ctx* ctx) {
   dm.adv_x = p.adv_x;
   dm.adv_y = p.adv_y;
   dm.cfl = p.cfl;
-  dm.tma = p.recon_variant == 0;
+  dm.variant = p.recon_variant;
+  dm.halo = HaloArgs{};
+  if (halo_ok && ctx->device >= 0) {
+    dm.halo.off = (const int32_t*)ctx->b_halo_off.p;
+    dm.halo.ids = (const int32_t*)ctx->b_halo_ids.p;
+    dm.halo.nbr_loc = (const uint16_t*)ctx->b_halo_loc.p;
+  }
   dm.err_flag = (int*)ctx->b_flag.p;
   dm.ahat = ctx->b_ahat.p;
   dm.nbr = (const int32_t*)ctx->b_nbr.p;
@@ -1066,7 +1098,7 @@ int teno_destroy(teno_ctx* ctx) {
   }
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  DevBuf* bufs[] = {&ctx->b_ahat, &ctx->b_nbr, &ctx->b_smask, &ctx->b_fcells, &ctx->b_fedges,
+  DevBuf* bufs[] = {&ctx->b_halo_off, &ctx->b_halo_ids, &ctx->b_halo_loc, &ctx->b_ahat, &ctx->b_nbr, &ctx->b_smask, &ctx->b_fcells, &ctx->b_fedges,
                     &ctx->b_fgeom, &ctx->b_cfaces, &ctx->b_inv_area, &ctx->b_cfl_len,
                     &ctx->b_perm, &ctx->b_U, &ctx->b_U1, &ctx->b_U2, &ctx->b_R, &ctx->b_tmp,
                     &ctx->b_Uq, &ctx->b_K, &ctx->b_sel, &ctx->b_sel_ovr, &ctx->b_maxlam,
@@ -1129,7 +1161,7 @@ int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
       p->precision < TENO_FP64 || p->precision > TENO_FP64_NATIVE || p->flux < 0 ||
       p->flux > 2 || (p->n_var == 1) != (p->flux == TENO_FLUX_UPWIND) || !(p->ct > 0) ||
       !(p->eps > 0) || !(p->gamma > 1.0) || !(p->cfl > 0) || p->recon_variant < 0 ||
-      p->recon_variant > 1)
+      p->recon_variant > 2)
     return fail(ctx, TENO_EINVAL, "precompute: bad parameters");
   const int nq_default = p->order <= 4 ? 2 : 3;
   if (p->nq != 0 && p->nq != nq_default)
@@ -1422,9 +1454,16 @@ int teno_edge_values(teno_ctx* ctx, double* out) {
        "D2H");
   }
   CK(cudaStreamSynchronize(ctx->stream), "sync");
+  // the FP64 path keeps Gauss-point values as (hi, lo) float pairs
+  const bool pairs = ctx->prm.precision == TENO_FP64;
+  const float* hp = reinterpret_cast<const float*>(h64.data());
   for (int64_t c = 0; c < ctx->nc; ++c) {
     const int64_t u = ctx->perm[c];
-    for (int64_t i = 0; i < per; ++i) out[u * per + i] = f64 ? h64[c * per + i] : h32[c * per + i];
+    for (int64_t i = 0; i < per; ++i) {
+      const int64_t k = c * per + i;
+      out[u * per + i] = pairs ? (double)hp[2 * k] + (double)hp[2 * k + 1]
+                               : (f64 ? h64[k] : (double)h32[k]);
+    }
   }
   return TENO_OK;
 }

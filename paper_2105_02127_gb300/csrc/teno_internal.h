@@ -36,12 +36,22 @@ struct DFTable {
   float2 psi[kMaxPts * kMaxM];
 };
 
+// Per-tile stencil halo: the distinct cells of a tile's stencils (internal
+// ids, at most kHaloMax per tile) and the stencil slots as halo-local indices.
+constexpr int kHaloMax = 256;
+struct HaloArgs {
+  const int32_t* off = nullptr;       // [n_tiles + 1]
+  const int32_t* ids = nullptr;       // [off[n_tiles]]
+  const uint16_t* nbr_loc = nullptr;  // [tile][slot][32]
+};
+
 // Everything the kernels of one residual evaluation need (device pointers).
 struct DeviceMesh {
   int64_t n_cell = 0, n_pad = 0, n_face = 0;
   int n_var = 1, order = 3, m = 5, ns = 12, nq = 2, e_entries = 0;
   int flux = 0, precision = 0, linear = 0;
-  int tma = 1;              // reconstruction streams its matrices through TMA (Euler, FP64 / mixed)
+  int variant = 0;          // reconstruction: 0 halo-staged, 1 direct gathers, 2 TMA-staged
+  HaloArgs halo;            // null when some tile's halo exceeds kHaloMax
   int* err_flag = nullptr;  // device flag: bit 0 non-physical state, bit 1 a bounded wait gave up
   double ct = 1e-6, eps = 1e-12, gamma = 1.4, adv_x = 1, adv_y = 1, cfl = 0.4;
   // reconstruction data, tile-interleaved [tile][entry][32]

@@ -124,6 +124,8 @@ __device__ __forceinline__ double val(const Dual<N>& x) { return x.v; }
 template <typename T>
 __device__ __forceinline__ T vmin(const T& a, const T& b) { return val(a) <= val(b) ? a : b; }
 template <typename T>
+__device__ __forceinline__ bool nonneg(const T& x) { return val(x) >= decltype(val(x))(0); }
+template <typename T>
 __device__ __forceinline__ T vmax(const T& a, const T& b) { return val(a) >= val(b) ? a : b; }
 template <typename T, typename S>
 __device__ __forceinline__ T cst(S x) { return T(x); }
@@ -131,6 +133,85 @@ template <>
 __device__ __forceinline__ Dual<2> cst<Dual<2>, double>(double x) { return mk<2>(x); }
 template <>
 __device__ __forceinline__ Dual<8> cst<Dual<8>, double>(double x) { return mk<8>(x); }
+
+// ------------------------------------------- double-float (FP32 pair) path
+// Values are unevaluated sums hi + lo of two floats (|lo| <= ulp(hi)/2), about
+// 48 significant bits.  Products use the exact FMA residual, sums Knuth's
+// two-sum; the per-cell matrices are stored as (hi, lo) pairs.
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+// acc += a * b with a, b pairs; acc.l collects the rounding terms (the pair
+// is renormalised by the caller)
+__device__ __forceinline__ void df_mac(DF& acc, float2 a, DF b) {
+  const float p = a.x * b.h;
+  float e = fmaf(a.x, b.h, -p);
+  e = fmaf(a.x, b.l, e);
+  e = fmaf(a.y, b.h, e);
+  const DF s = two_sum(acc.h, p);
+  acc.h = s.h;
+  acc.l += s.l + e;
+}
+__device__ __forceinline__ DF df_norm(DF a) { return two_sum(a.h, a.l); }
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.h + (double)a.l; }
+
+
+// arithmetic on pairs (the Riemann flux of the FP64 path): sums renormalise
+// once (fast two-sum), products use the exact FMA residual, quotients and
+// square roots take one correction step from their FP32 approximation
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ DF operator+(DF a, DF b) {
+  DF s = two_sum(a.h, b.h);
+  s.l += a.l + b.l;
+  return fast_two_sum(s.h, s.l);
+}
+__device__ __forceinline__ DF operator-(DF a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ DF operator-(DF a, DF b) { return a + (-b); }
+__device__ __forceinline__ DF operator*(DF a, DF b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ DF operator/(DF a, DF b) {
+  const float q1 = a.h / b.h;
+  const DF r = a - b * DF{q1, 0.f};
+  return fast_two_sum(q1, r.h / b.h);
+}
+__device__ __forceinline__ DF tsqrt(DF a) {
+  const float s = sqrtf(a.h);
+  if (!(a.h > 0.f)) return {s, 0.f};
+  const DF r = a - DF{s, 0.f} * DF{s, 0.f};
+  return fast_two_sum(s, r.h / (2.f * s));
+}
+__device__ __forceinline__ float val(DF x) { return x.h; }
+template <>
+__device__ __forceinline__ DF cst<DF, double>(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ DF vmin(const DF& a, const DF& b) {
+  return (a.h < b.h || (a.h == b.h && a.l <= b.l)) ? a : b;
+}
+__device__ __forceinline__ DF vmax(const DF& a, const DF& b) {
+  return (a.h > b.h || (a.h == b.h && a.l >= b.l)) ? a : b;
+}
+// c + a*b and conversion to FP64 for every scalar type of the flux kernels
+__device__ __forceinline__ double madd(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float madd(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ DF madd(DF a, DF b, DF c) { return a * b + c; }
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+__device__ __forceinline__ double to_d(DF x) { return (double)x.h + (double)x.l; }
 
 // ---------------------------------------------------------------- fluxes
 // Euler flux through a face with unit normal n = (nx, ny): the state is
@@ -171,10 +252,10 @@ __device__ __forceinline__ void euler_riemann(const T* UL, const T* UR, double n
   T WL[4] = {rL, mL, rL * utL, EL};
   T WR[4] = {rR, mR, rR * utR, ER};
   T Fx[4];
-  if (val(SL) >= 0.0) {
+  if (nonneg(SL)) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) Fx[k] = FL[k];
-  } else if (val(SR) <= 0.0) {
+  } else if (nonneg(-SR)) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) Fx[k] = FR[k];
   } else if (!hllc) {
@@ -186,7 +267,7 @@ __device__ __forceinline__ void euler_riemann(const T* UL, const T* UR, double n
     // HLLC: contact speed and star state of the side the face lies in
     T aL = rL * (SL - unL), aR = rR * (SR - unR);
     T Ss = (pR - pL + aL * unL - aR * unR) / (aL - aR);
-    bool left = val(Ss) >= 0.0;
+    bool left = nonneg(Ss);
     T r = left ? rL : rR, un = left ? unL : unR, ut = left ? utL : utR;
     T p = left ? pL : pR, S = left ? SL : SR, E = left ? EL : ER;
     T f = r * (S - un) / (S - Ss);
@@ -450,32 +531,6 @@ __global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const TT 
   plain_finish<M, NQ, NV, TA, TT>(a, ev, c, v, u0, u0s, acc, as);
 }
 
-// ------------------------------------------- double-float (FP32 pair) path
-// Values are unevaluated sums hi + lo of two floats (|lo| <= ulp(hi)/2), about
-// 48 significant bits.  Products use the exact FMA residual, sums Knuth's
-// two-sum; the per-cell matrices are stored as (hi, lo) pairs.
-struct DF {
-  float h, l;
-};
-__device__ __forceinline__ DF two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return {s, (a - (s - bb)) + (b - bb)};
-}
-// acc += a * b with a, b pairs; acc.l collects the rounding terms (the pair
-// is renormalised by the caller)
-__device__ __forceinline__ void df_mac(DF& acc, float2 a, DF b) {
-  const float p = a.x * b.h;
-  float e = fmaf(a.x, b.h, -p);
-  e = fmaf(a.x, b.l, e);
-  e = fmaf(a.y, b.h, e);
-  const DF s = two_sum(acc.h, p);
-  acc.h = s.h;
-  acc.l += s.l + e;
-}
-__device__ __forceinline__ DF df_norm(DF a) { return two_sum(a.h, a.l); }
-__device__ __forceinline__ double df_to_double(DF a) { return (double)a.h + (double)a.l; }
-
 // FP64-accurate reconstruction with double-float arithmetic on the FP32 pipe:
 // stencil differences from the (hi, lo) split of U, matvecs, beta and the
 // Gauss-point evaluation in pairs (relative error ~2^-46 of the summed
@@ -557,15 +612,15 @@ __device__ __forceinline__ void df_finish(const ReconArgs& a, const DFTable& ev,
       if (!nd) cf[l] = {0.f, 0.f};
     }
   }
-  const double u0 = a.U[(int64_t)v * a.n_pad + c];
-  double* __restrict__ out = reinterpret_cast<double*>(a.Uq) + c * (3 * NQ * NV) + v;
+  // Gauss-point values as (hi, lo) pairs: split(U_0) + Psi' c'
+  const float2 u0s = a.Us[(int64_t)v * a.n_pad + c];
+  DF* __restrict__ out = reinterpret_cast<DF*>(a.Uq) + c * (3 * NQ * NV) + v;
 #pragma unroll
   for (int p = 0; p < 3 * NQ; ++p) {
     DF s = {0.f, 0.f};
 #pragma unroll
     for (int l = 0; l < M; ++l) df_mac(s, ev.psi[p * kMaxM + l], cf[l]);
-    s = df_norm(s);
-    out[p * NV] = u0 + ((double)s.h + (double)s.l);
+    out[p * NV] = DF{u0s.x, u0s.y} + df_norm(s);
   }
 }
 
@@ -617,6 +672,135 @@ __global__ void __launch_bounds__(128) recon_df_kernel(const ReconArgs a, const 
     for (int l = 0; l < kSmallM; ++l) as[k][l] = df_norm(as[k][l]);
   }
   df_finish<M, NQ, NV>(a, ev, c, v, acc, as);
+}
+
+// ------------------------------------------ halo-staged reconstruction
+// The union of the stencils of a 32-cell tile (its "halo", <= kHaloMax cells,
+// listed on the host) is gathered once into shared memory; every stencil
+// difference then reads shared memory, and the only global stream of the
+// main loop is the coalesced, independent stream of per-cell matrices.
+// kMode 0: FP64 path (double-float), 1: FP32-mixed, 2: FP64 native.
+template <int kMode>
+struct HaloTraits;
+template <>
+struct HaloTraits<0> {
+  using TE = float2;   // matrix entry
+  using TS = float2;   // staged state (hi, lo split)
+  using Acc = DF;
+  using Tab = DFTable;
+};
+template <>
+struct HaloTraits<1> {
+  using TE = float;
+  using TS = float2;
+  using Acc = float;
+  using Tab = DFTable;
+};
+template <>
+struct HaloTraits<2> {
+  using TE = double;
+  using TS = double;
+  using Acc = double;
+  using Tab = EvalTable;
+};
+
+template <int M, int NS, int NQ, int NV, int kMode>
+__global__ void __launch_bounds__(128) recon_halo_kernel(const ReconArgs a, const HaloArgs h,
+                                                         const typename HaloTraits<kMode>::Tab ev) {
+  using TR = HaloTraits<kMode>;
+  using TE = typename TR::TE;
+  using TS = typename TR::TS;
+  using Acc = typename TR::Acc;
+  constexpr int TZ = 4 / NV;
+  constexpr int E = M * NS + kSmallEntries;
+  constexpr int SL = NS + kSmallSlots;
+  __shared__ TS hs[TZ][NV][kHaloMax];
+  const int lane = threadIdx.x, v = threadIdx.y, z = threadIdx.z;
+  const int64_t n_tiles = (a.n_cell + kTile - 1) / kTile;
+  const int64_t tile = (int64_t)blockIdx.x * TZ + z;
+  const bool tvalid = tile < n_tiles;
+  // cooperative gather of the tile's halo states (all vars) by its NV warps
+  if (tvalid) {
+    const int h0 = h.off[tile], H = h.off[tile + 1] - h0;
+    for (int i = lane + kTile * v; i < H; i += kTile * NV) {
+      const int id = __ldg(h.ids + h0 + i);
+#pragma unroll
+      for (int w = 0; w < NV; ++w) {
+        if constexpr (kMode == 2)
+          hs[z][w][i] = __ldg(a.U + (int64_t)w * a.n_pad + id);
+        else
+          hs[z][w][i] = __ldg(a.Us + (int64_t)w * a.n_pad + id);
+      }
+    }
+  }
+  __syncthreads();
+  if (!tvalid) return;
+  const int64_t c = tile * kTile + lane;  // pad lanes compute, but store nothing
+  const int64_t cc = c < a.n_cell ? c : 0;
+  double u0 = 0.0;
+  float2 u0s = make_float2(0.f, 0.f);
+  if constexpr (kMode == 2)
+    u0 = a.U[(int64_t)v * a.n_pad + cc];
+  else
+    u0s = a.Us[(int64_t)v * a.n_pad + cc];
+  const TS* __restrict__ st = hs[z][v];
+  const TE* __restrict__ A = reinterpret_cast<const TE*>(a.ahat) + tile * (int64_t)E * kTile + lane;
+  const uint16_t* __restrict__ nb = h.nbr_loc + tile * (int64_t)SL * kTile + lane;
+  auto dif = [&](int s) -> Acc {
+    const TS q = st[__ldg(nb + s * kTile)];
+    if constexpr (kMode == 0) {
+      DF t = two_sum(q.x, -u0s.x);
+      t.l += q.y - u0s.y;
+      return two_sum(t.h, t.l);
+    } else if constexpr (kMode == 1) {
+      return (q.x - u0s.x) + (q.y - u0s.y);
+    } else {
+      return q - u0;
+    }
+  };
+  auto mac = [](Acc& acc, TE m, Acc d) {
+    if constexpr (kMode == 0)
+      df_mac(acc, m, d);
+    else
+      acc = fma(m, d, acc);
+  };
+  Acc acc[M];
+#pragma unroll
+  for (int l = 0; l < M; ++l) acc[l] = Acc{};
+#pragma unroll 2
+  for (int s = 0; s < NS; ++s) {
+    const Acc d = dif(s);
+    const TE* As = A + (int64_t)s * M * kTile;
+#pragma unroll
+    for (int l = 0; l < M; ++l) mac(acc[l], __ldg(As + l * kTile), d);
+  }
+  Acc as[kSmallK][kSmallM];
+#pragma unroll
+  for (int k = 0; k < kSmallK; ++k) {
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) as[k][l] = Acc{};
+#pragma unroll 2
+    for (int s = 0; s < kSmallN; ++s) {
+      const Acc d = dif(NS + k * kSmallN + s);
+      const TE* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) mac(as[k][l], __ldg(As + l * kTile), d);
+    }
+  }
+  if (c >= a.n_cell) return;
+  if constexpr (kMode == 0) {
+#pragma unroll
+    for (int l = 0; l < M; ++l) acc[l] = df_norm(acc[l]);
+#pragma unroll
+    for (int k = 0; k < kSmallK; ++k)
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) as[k][l] = df_norm(as[k][l]);
+    df_finish<M, NQ, NV>(a, ev, c, v, acc, as);
+  } else if constexpr (kMode == 1) {
+    plain_finish<M, NQ, NV, float, DFTable>(a, ev, c, v, 0.0, u0s, acc, as);
+  } else {
+    plain_finish<M, NQ, NV, double, EvalTable>(a, ev, c, v, u0, u0s, acc, as);
+  }
 }
 
 // -------------------------------------------- TMA-staged reconstruction
@@ -917,7 +1101,7 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const FaceArgs a, const 
   const double nx = a.f_geom[5 * f], ny = a.f_geom[5 * f + 1], len = a.f_geom[5 * f + 2];
   T acc[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) acc[v] = T(0);
+  for (int v = 0; v < NV; ++v) acc[v] = cst<T>(0.0);
 #pragma unroll
   for (int k = 0; k < NQ; ++k) {
     T UL[NV], UR[NV], F[NV];
@@ -937,15 +1121,17 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const FaceArgs a, const 
     }
     if constexpr (NV == 1) {
       const double an = a.adv_x * nx + a.adv_y * ny;
-      F[0] = T(an) * (an >= 0.0 ? UL[0] : UR[0]);
+      F[0] = cst<T>(an) * (an >= 0.0 ? UL[0] : UR[0]);
     } else {
       euler_riemann<T>(UL, UR, nx, ny, a.gamma, FLUX == TENO_FLUX_HLLC, F);
     }
+    const T wk = cst<T>(a.gw[k]);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = fma(T(a.gw[k]), F[v], acc[v]);
+    for (int v = 0; v < NV; ++v) acc[v] = madd(wk, F[v], acc[v]);
   }
+  const T tl = cst<T>(len);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) K[f * NV + v] = acc[v] * T(len);
+  for (int v = 0; v < NV; ++v) K[f * NV + v] = acc[v] * tl;
 }
 
 // ------------------------------------------------------------------ gather
@@ -975,7 +1161,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a, const T
     const int64_t f = cf >> 1;
     const double s = (cf & 1) ? -1.0 : 1.0;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = fma(s, (double)K[f * NV + v], acc[v]);
+    for (int v = 0; v < NV; ++v) acc[v] = fma(s, to_d(K[f * NV + v]), acc[v]);
   }
   const double ia = a.inv_area[c];
   if (mode == 0) {
@@ -1086,9 +1272,9 @@ struct VjpArgs {
 // Uq_bar[(c,edge,q)] = w_q |A| (dF/dU_side)^T Kbar with Kbar = dJ/dK_f
 // (R_o has -K/|V_o|, R_n has +K/|V_n|); every Gauss slot of every cell is
 // written by exactly one face.
-template <int NV, int NQ, int FLUX>
+template <int NV, int NQ, int FLUX, typename TQ>
 __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
-                                                            const double* __restrict__ Uq,
+                                                            const TQ* __restrict__ Uq,
                                                             const double* __restrict__ w,
                                                             double* __restrict__ Uq_bar) {
   constexpr int ND = 2 * NV;
@@ -1106,17 +1292,17 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
   }
   for (int k = 0; k < NQ; ++k) {
     D UL[NV], UR[NV], F[NV];
-    const double* pl = Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV;
+    const TQ* pl = Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      UL[v] = mk<ND>(pl[v]);
+      UL[v] = mk<ND>(to_d(pl[v]));
       UL[v].d[v] = 1.0;
     }
     if (n >= 0) {
-      const double* pr = Uq + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV;
+      const TQ* pr = Uq + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        UR[v] = mk<ND>(pr[v]);
+        UR[v] = mk<ND>(to_d(pr[v]));
         UR[v].d[NV + v] = 1.0;
       }
     } else if constexpr (NV == 4) {
@@ -1306,8 +1492,20 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
     constexpr int M = decltype(Mc)::value, NS = decltype(NSc)::value;
     auto go = [&](auto nqc, auto nvc) -> cudaError_t {
       constexpr int NQ = decltype(nqc)::value, NV = decltype(nvc)::value;
+      if (dm.variant == 0 && dm.halo.off) {
+        constexpr int TZh = 4 / NV;
+        dim3 block(kTile, NV, TZh);
+        dim3 grid((unsigned)((tiles + TZh - 1) / TZh));
+        if (dm.precision == TENO_FP64)
+          recon_halo_kernel<M, NS, NQ, NV, 0><<<grid, block, 0, st>>>(a, dm.halo, dm.eval_df);
+        else if (dm.precision == TENO_FP32_MIXED)
+          recon_halo_kernel<M, NS, NQ, NV, 1><<<grid, block, 0, st>>>(a, dm.halo, dm.eval_df);
+        else
+          recon_halo_kernel<M, NS, NQ, NV, 2><<<grid, block, 0, st>>>(a, dm.halo, dm.eval);
+        return cudaGetLastError();
+      }
       if constexpr (NV == 4) {
-        if (dm.tma && dm.err_flag && dm.precision != TENO_FP64_NATIVE) {
+        if (dm.variant == 2 && dm.err_flag && dm.precision != TENO_FP64_NATIVE) {
           if (dm.precision == TENO_FP64) return launch_recon_tma<M, NS, NQ, true>(a, dm, dm.err_flag, st);
           return launch_recon_tma<M, NS, NQ, false>(a, dm, dm.err_flag, st);
         }
@@ -1354,9 +1552,11 @@ cudaError_t launch_face_flux(const DeviceMesh& dm, const void* Uq, void* K, doub
   auto go = [&](auto nvc, auto nqc, auto flc) -> cudaError_t {
     constexpr int NV = decltype(nvc)::value, NQ = decltype(nqc)::value,
                   FL = decltype(flc)::value;
-    if (dm.precision != TENO_FP32_MIXED)
+    if (dm.precision == TENO_FP64_NATIVE)
       face_flux_kernel<NV, NQ, FL, double><<<grid, 256, 0, st>>>(
           a, (const double*)Uq, (double*)K);
+    else if (dm.precision == TENO_FP64)
+      face_flux_kernel<NV, NQ, FL, DF><<<grid, 256, 0, st>>>(a, (const DF*)Uq, (DF*)K);
     else
       face_flux_kernel<NV, NQ, FL, float><<<grid, 256, 0, st>>>(a, (const float*)Uq, (float*)K);
     return cudaGetLastError();
@@ -1378,20 +1578,21 @@ cudaError_t launch_gather(const DeviceMesh& dm, const void* K, const double* Un,
                           const double* max_lam, int* flag, float2* split, cudaStream_t st) {
   GatherArgs a{dm.c_faces, dm.inv_area, dm.n_cell, dm.n_pad, dm.gamma};
   const unsigned grid = (unsigned)((dm.n_cell + 255) / 256);
-  if (dm.n_var == 1) {
-    if (dm.precision != TENO_FP32_MIXED)
-      gather_kernel<1, double><<<grid, 256, 0, st>>>(a, (const double*)K, Un, Us, out, mode, cn,
-                                                     cs, dt_fixed, dm.cfl, max_lam, flag, split);
-    else
-      gather_kernel<1, float><<<grid, 256, 0, st>>>(a, (const float*)K, Un, Us, out, mode, cn, cs,
-                                                    dt_fixed, dm.cfl, max_lam, flag, split);
+  auto go = [&](auto nvc, auto tkc) {
+    constexpr int NV = decltype(nvc)::value;
+    using TK = typename decltype(tkc)::type;
+    gather_kernel<NV, TK><<<grid, 256, 0, st>>>(a, (const TK*)K, Un, Us, out, mode, cn, cs,
+                                                dt_fixed, dm.cfl, max_lam, flag, split);
+  };
+  using I1 = std::integral_constant<int, 1>;
+  using I4 = std::integral_constant<int, 4>;
+  const bool one = dm.n_var == 1;
+  if (dm.precision == TENO_FP64_NATIVE) {
+    if (one) go(I1{}, TypeTag<double>{}); else go(I4{}, TypeTag<double>{});
+  } else if (dm.precision == TENO_FP64) {
+    if (one) go(I1{}, TypeTag<DF>{}); else go(I4{}, TypeTag<DF>{});
   } else {
-    if (dm.precision != TENO_FP32_MIXED)
-      gather_kernel<4, double><<<grid, 256, 0, st>>>(a, (const double*)K, Un, Us, out, mode, cn,
-                                                     cs, dt_fixed, dm.cfl, max_lam, flag, split);
-    else
-      gather_kernel<4, float><<<grid, 256, 0, st>>>(a, (const float*)K, Un, Us, out, mode, cn, cs,
-                                                    dt_fixed, dm.cfl, max_lam, flag, split);
+    if (one) go(I1{}, TypeTag<float>{}); else go(I4{}, TypeTag<float>{});
   }
   return cudaGetLastError();
 }
@@ -1458,23 +1659,32 @@ cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const dou
     a.gt[k] = dm.gt[k];
   }
   const unsigned grid = (unsigned)((dm.n_face + 127) / 128);
-  const double* U = (const double*)Uq;
-  if (dm.n_var == 1) {
-    if (dm.nq == 2)
-      face_flux_vjp_kernel<1, 2, TENO_FLUX_UPWIND><<<grid, 128, 0, st>>>(a, U, w, Uq_bar);
-    else
-      face_flux_vjp_kernel<1, 3, TENO_FLUX_UPWIND><<<grid, 128, 0, st>>>(a, U, w, Uq_bar);
-  } else if (dm.flux == TENO_FLUX_HLL) {
-    if (dm.nq == 2)
-      face_flux_vjp_kernel<4, 2, TENO_FLUX_HLL><<<grid, 128, 0, st>>>(a, U, w, Uq_bar);
-    else
-      face_flux_vjp_kernel<4, 3, TENO_FLUX_HLL><<<grid, 128, 0, st>>>(a, U, w, Uq_bar);
-  } else {
-    if (dm.nq == 2)
-      face_flux_vjp_kernel<4, 2, TENO_FLUX_HLLC><<<grid, 128, 0, st>>>(a, U, w, Uq_bar);
-    else
-      face_flux_vjp_kernel<4, 3, TENO_FLUX_HLLC><<<grid, 128, 0, st>>>(a, U, w, Uq_bar);
-  }
+  auto go = [&](auto nvc, auto nqc, auto flc, auto tqc) {
+    constexpr int NV = decltype(nvc)::value, NQ = decltype(nqc)::value,
+                  FL = decltype(flc)::value;
+    using TQ = typename decltype(tqc)::type;
+    face_flux_vjp_kernel<NV, NQ, FL, TQ><<<grid, 128, 0, st>>>(a, (const TQ*)Uq, w, Uq_bar);
+  };
+  using I1 = std::integral_constant<int, 1>;
+  using I2 = std::integral_constant<int, 2>;
+  using I3 = std::integral_constant<int, 3>;
+  using I4 = std::integral_constant<int, 4>;
+  using F0 = std::integral_constant<int, TENO_FLUX_UPWIND>;
+  using F1 = std::integral_constant<int, TENO_FLUX_HLL>;
+  using F2 = std::integral_constant<int, TENO_FLUX_HLLC>;
+  auto pick = [&](auto tqc) {
+    if (dm.n_var == 1) {
+      if (dm.nq == 2) go(I1{}, I2{}, F0{}, tqc); else go(I1{}, I3{}, F0{}, tqc);
+    } else if (dm.flux == TENO_FLUX_HLL) {
+      if (dm.nq == 2) go(I4{}, I2{}, F1{}, tqc); else go(I4{}, I3{}, F1{}, tqc);
+    } else {
+      if (dm.nq == 2) go(I4{}, I2{}, F2{}, tqc); else go(I4{}, I3{}, F2{}, tqc);
+    }
+  };
+  if (dm.precision == TENO_FP64)
+    pick(TypeTag<DF>{});
+  else
+    pick(TypeTag<double>{});
   return cudaGetLastError();
 }
 

@@ -97,20 +97,20 @@ def test_scalar_teno3_config1(T, oracle_mod):
     assert rel(t.get_state(), Uo) <= TOL
 
 
-@pytest.mark.parametrize("precision,variant", [(0, 0), (0, 1), (2, 0)],
-                         ids=["fp64-tma", "fp64-direct", "fp64native"])
+@pytest.mark.parametrize("precision,variant", [(0, 0), (0, 1), (0, 2), (2, 0)],
+                         ids=["fp64-halo", "fp64-direct", "fp64-tma", "fp64native"])
 @pytest.mark.parametrize("order", [3, 4, 5, 6])
 def test_euler_vortex_hll(T, oracle_mod, order, precision, variant):
-    """Isentropic vortex, HLL, FP64 (double-float with TMA-staged or direct
-    matrix loads, and native) on a 33x31 jittered mesh (2046 cells: 64 tiles
-    of 32 and a ragged tail)."""
+    """Isentropic vortex, HLL, FP64 (double-float with halo-staged, direct or
+    TMA-staged loads, and native) on a 33x31 jittered mesh (2046 cells: 64
+    tiles of 32 and a ragged tail)."""
     mesh = inputs.jittered_mesh(33, 31, 10.0, 10.0, seed=1002)
     U = inputs.cell_average(mesh, inputs.isentropic_vortex)
     _check_residual(T, oracle_mod, mesh, U, order, 4, 1, precision=precision, variant=variant)
 
 
-@pytest.mark.parametrize("precision,variant", [(0, 0), (0, 1), (2, 0)],
-                         ids=["fp64-tma", "fp64-direct", "fp64native"])
+@pytest.mark.parametrize("precision,variant", [(0, 0), (0, 1), (0, 2), (2, 0)],
+                         ids=["fp64-halo", "fp64-direct", "fp64-tma", "fp64native"])
 @pytest.mark.parametrize("order,flux", [(6, 2), (5, 1), (4, 2), (3, 1)])
 def test_euler_discontinuous(T, oracle_mod, order, flux, precision, variant):
     """A density/pressure square exercises the cutoff and the directional
@@ -156,7 +156,7 @@ def test_rk3_fixed_and_cfl(T, oracle_mod):
     assert rel(t.get_state(), Uo) <= TOL
 
 
-@pytest.mark.parametrize("variant", [0, 1], ids=["tma", "direct"])
+@pytest.mark.parametrize("variant", [0, 1, 2], ids=["halo", "direct", "tma"])
 def test_mixed_precision_report(T, oracle_mod, variant):
     """FP32-mixed: matvecs and fluxes in FP32, selection and residual
     accumulation in FP64.  Reports error vs the FP64 oracle and the selection
