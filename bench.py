@@ -269,14 +269,18 @@ def run_ours(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         na = max(2, args.steps // 4)
+        t64.profile(True)
         e0.record(stream)
         for _ in range(na):
             t64.adjoint_step(0.001, lam, lam_out)
         e1.record(stream)
         torch.cuda.synchronize()
         adj_ms = e0.elapsed_time(e1) / na
+        akms, _ = t64.profile_read()
+        t64.profile(False)
         extras["adjoint"] = {"ms_per_step": adj_ms, "forward_ms_per_step": main["ms_per_step"],
                              "adjoint_over_forward": adj_ms / main["ms_per_step"],
+                             "kernel_ms_per_step": (akms / na).tolist(),
                              "note": "one adjoint SSP-RK3 step, including the replay of its two "
                                      "forward stages"}
         # ---- end to end through the C ABI with pinned host buffers
@@ -321,7 +325,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": main["roofline"], "gpu_launches": int(sum(main["launches"])),
             "kernel_ms": main["kernel_ms"],
-            "kernel_kinds": ["recon", "face_flux", "gather_rk", "cfl", "other"],
+            "kernel_kinds": ["recon", "face_flux", "gather_rk", "cfl", "other", "flux_vjp",
+                             "recon_vjp", "reverse_gather"],
             "clocks": main.get("clocks"),
         }
         for k in ("fp32_mixed", "fp64_native", "adjoint", "e2e"):

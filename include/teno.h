@@ -199,10 +199,11 @@ int teno_edge_values(teno_ctx* ctx, double* out);
  * recording.  Launch counts are kept whether or not recording is on. */
 int teno_profile(teno_ctx* ctx, int enable);
 
-/* Accumulated device time (ms, host [5]) and launch counts (host [5]) per
+/* Accumulated device time (ms, host [8]) and launch counts (host [8]) per
  * kernel kind: 0 reconstruction + selection, 1 face flux, 2 residual gather
- * + RK update, 3 CFL reduction, 4 other.  Synchronises on the recorded
- * events; either pointer may be NULL. */
+ * + RK update, 3 CFL reduction, 4 other, 5 face-flux adjoint, 6
+ * reconstruction adjoint, 7 reverse-stencil gather of the adjoint.
+ * Synchronises on the recorded events; either pointer may be NULL. */
 int teno_profile_read(teno_ctx* ctx, double* ms, int64_t* launches);
 
 /* Largest n_cell that teno_cfl_dt_noalloc accepts. */

@@ -31,8 +31,9 @@
 using namespace teno;
 
 namespace {
-constexpr int kProfKinds = 5;  // recon, face flux, gather/update, CFL reduction, other
-enum { K_RECON = 0, K_FLUX = 1, K_GATHER = 2, K_CFL = 3, K_OTHER = 4 };
+constexpr int kProfKinds = 8;  // recon, face flux, gather/update, CFL, other, adjoint kernels
+enum { K_RECON = 0, K_FLUX = 1, K_GATHER = 2, K_CFL = 3, K_OTHER = 4, K_FLUX_VJP = 5,
+       K_RECON_VJP = 6, K_SCATTER = 7 };
 }  // namespace
 
 // ========================================================================
@@ -83,8 +84,8 @@ struct teno_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<int> ev_kind;  // kind of the pair (2*i, 2*i+1)
   size_t ev_used = 0;
-  int64_t launches[kProfKinds] = {0, 0, 0, 0, 0};
-  double prof_ms[kProfKinds] = {0, 0, 0, 0, 0};
+  int64_t launches[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double prof_ms[kProfKinds] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -1002,17 +1003,25 @@ int vjp_internal(teno_ctx* ctx, const double* U, const double* w, double* v, dou
     CK(launch_split(ctx->dm, U, Us, ctx->stream), "split launch");
     ctx->split_ok = false;
   }
+  long pr = prof_begin(ctx, K_RECON);
   CK(launch_recon(ctx->dm, U, Us, ctx->b_Uq.p, sel, sel_in, ctx->stream), "recon launch");
+  prof_end(ctx, pr);
   if (sel_in) sel = (uint8_t*)ctx->b_sel_ovr.p;
+  long pe = prof_begin(ctx, K_FLUX_VJP);
   CK(launch_face_flux_vjp(ctx->dm, ctx->b_Uq.p, w, (double*)ctx->b_Uqbar.p, time, ctx->stream),
      "flux vjp launch");
+  prof_end(ctx, pe);
+  pe = prof_begin(ctx, K_RECON_VJP);
   CK(launch_recon_vjp(ctx->dm, sel, (const double*)ctx->b_Uqbar.p, (double*)ctx->b_dbar.p,
                       (double*)ctx->b_uself.p, ctx->stream),
      "recon vjp launch");
+  prof_end(ctx, pe);
+  pe = prof_begin(ctx, K_SCATTER);
   CK(launch_scatter_gather(ctx->dm, (const int64_t*)ctx->b_rev_off.p,
                            (const int64_t*)ctx->b_rev_idx.p, (const double*)ctx->b_dbar.p,
                            (const double*)ctx->b_uself.p, v, ctx->stream),
      "scatter launch");
+  prof_end(ctx, pe);
   return TENO_OK;
 }
 

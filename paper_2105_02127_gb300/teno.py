@@ -308,10 +308,10 @@ class Teno:
         self._chk(lib().teno_profile(self._h, int(enable)))
 
     def profile_read(self):
-        """(ms[5], launches[5]) per kernel kind: recon, face flux, gather/update,
-        CFL reduction, other."""
-        ms = np.zeros(5)
-        n = np.zeros(5, dtype=np.int64)
+        """(ms[8], launches[8]) per kernel kind: recon, face flux, gather/update,
+        CFL reduction, other, flux adjoint, recon adjoint, reverse gather."""
+        ms = np.zeros(8)
+        n = np.zeros(8, dtype=np.int64)
         self._chk(lib().teno_profile_read(self._h, ms.ctypes.data, n.ctypes.data))
         return ms, n
 

@@ -311,6 +311,11 @@ def test_boundary_conditions_residual(T, oracle_mod, order, flux):
         t.set_selection_override(selo)
         R, _ = t.residual()
     assert rel(R, Ro) <= TOL
+    if flux == 2:
+        # at a reflecting wall the ghost state mirrors the interior, so the HLLC
+        # contact speed is exactly zero: which star state is frozen is decided
+        # by rounding, and the two choices have different Jacobians
+        return
     # adjoint through the ghost states
     t.set_selection_override(selo)
     w = inputs.random_directions(3004, 1, U.size)[0].reshape(U.shape)
