@@ -46,20 +46,33 @@ NCU_TRAFFIC = {"fp64": None, "fp32_mixed": None, "fp64_native": 2788e6}
 
 
 def parse():
+    """Command line; workload-dependent defaults are filled in after parsing."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=512, help="quads per side (2 n^2 triangles)")
-    ap.add_argument("--order", type=int, default=5)
+    ap.add_argument("--workload", default="vortex", choices=["vortex", "shear"],
+                    help="vortex: isentropic vortex on [0,10]^2 (default); shear: periodic "
+                         "shear layer on [0,1]^2")
+    ap.add_argument("--n", type=int, default=None,
+                    help="quads per side, 2 n^2 triangles (vortex 512, shear 2048)")
+    ap.add_argument("--order", type=int, default=None, help="TENO order (vortex 5, shear 6)")
+    ap.add_argument("--extras", default="mixed,native,adjoint,e2e,cpu",
+                    help="comma list of extra legs: mixed, native, adjoint, e2e, cpu")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the mixed, adjoint, e2e and CPU-baseline legs")
     ap.add_argument("--recon-variant", type=int, default=0, choices=[0, 1, 2],
                     help="reconstruction kernel: 0 halo-staged, 1 direct gathers, 2 TMA-staged")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="path timed as the primary line (the other one is an extra)")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.n is None:
+        a.n = 512 if a.workload == "vortex" else 2048
+    if a.order is None:
+        a.order = 5 if a.workload == "vortex" else 6
+    a.extra_set = set() if a.no_extras else {e for e in a.extras.split(",") if e}
+    return a
 
 
 def load_peaks():
@@ -71,11 +84,24 @@ def load_peaks():
     return PEAKS_FALLBACK, "fallback"
 
 
-def workload(n, order):
+def workload(n, order, kind="vortex"):
     from paper_2105_02127_gb300 import inputs
+    if kind == "shear":
+        mesh = inputs.jittered_mesh(n, n, 1.0, 1.0, seed=1005)
+        U = inputs.cell_average(mesh, inputs.shear_layer(seed=2005), n_quad=3)
+        return mesh, U
     mesh = inputs.jittered_mesh(n, n, 10.0, 10.0, seed=1002)
     U = inputs.cell_average(mesh, inputs.isentropic_vortex)
     return mesh, U
+
+
+def workload_name(args, n_cell):
+    if args.workload == "shear":
+        return (f"periodic shear layer on [0,1]^2 (density 2/1, u = -+0.5, 8-mode seeded v "
+                f"perturbation), jittered {args.n}x{args.n} split quads = {n_cell} triangles, "
+                f"TENO{args.order}, HLL, SSP-RK3, CFL 0.4 (device dt)")
+    return (f"isentropic vortex, periodic [0,10]^2, jittered {args.n}x{args.n} split quads = "
+            f"{n_cell} triangles, TENO{args.order}, HLL, SSP-RK3, CFL 0.4 (device dt)")
 
 
 def algorithmic_bytes(order, n_var, precision):
@@ -195,7 +221,7 @@ def run_ours(args):
 
     peaks, peak_src = load_peaks()
     hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
-    mesh, U = workload(args.n, args.order)
+    mesh, U = workload(args.n, args.order, args.workload)
     n_cell = mesh.n_cell
     stream = torch.cuda.current_stream()
     Ud = torch.from_numpy(U).cuda()
@@ -250,17 +276,19 @@ def run_ours(args):
     primary = "fp32_mixed" if args.precision == "mixed" else "fp64"
     t_main, main = measure(primary, clocks=True)
     extras = {}
-    if not args.no_extras:
+    ex = args.extra_set
+    t64 = t_main
+    if ex:
         U_main = t_main.get_state()
-        for other in ("fp32_mixed", "fp64_native"):
-            if other == primary:
+        for other, key in (("fp32_mixed", "mixed"), ("fp64_native", "native")):
+            if other == primary or key not in ex:
                 continue
             t_o, r = measure(other)
             r["l1_rho_diff_vs_primary_after_steps"] = float(np.abs(t_o.get_state()[0] - U_main[0]).mean())
             extras[other] = r
             t_o.close()
+    if "adjoint" in ex:
         # ---- adjoint / forward (FP64 path)
-        t64 = t_main
         lam = torch.from_numpy(np.ones_like(U)).cuda()
         lam_out = torch.empty_like(lam)
         t64.set_state(Ud)
@@ -283,6 +311,7 @@ def run_ours(args):
                              "kernel_ms_per_step": (akms / na).tolist(),
                              "note": "one adjoint SSP-RK3 step, including the replay of its two "
                                      "forward stages"}
+    if "e2e" in ex:
         # ---- end to end through the C ABI with pinned host buffers
         hin = torch.from_numpy(U.copy()).pin_memory()
         hout = torch.empty_like(hin).pin_memory()
@@ -306,20 +335,19 @@ def run_ours(args):
                          "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_extras:
+    if rank == 0 and world == 1 and "cpu" in ex:
         cpu = cpu_baseline(mesh, U, args.order, samples=20)
 
     if rank == 0:
-        dtype = {"fp64": "f64 (double-float fp32x2 matvec/beta/evaluation, f64 flux/update)",
+        dtype = {"fp64": "f64 (reconstruction and flux in double-float fp32x2 arithmetic, "
+                         "~48-bit; residual accumulation and RK update in f64)",
                  "fp32_mixed": "f32 matvec/flux, f64 selection/update"}[primary]
         line = {
             "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic",
-            "config": {"workload": f"isentropic vortex, periodic [0,10]^2, jittered {args.n}x"
-                                   f"{args.n} split quads = {n_cell} triangles, TENO{args.order}, "
-                                   "HLL, SSP-RK3, CFL 0.4 (device dt)",
+            "config": {"workload": workload_name(args, n_cell),
                        "n_cell": n_cell, "order": args.order,
                        "l2": "inputs larger than L2 (per-cell matrices 1.3-2.5 GB)",
                        "parallelism": f"replicas x{world}"},

@@ -30,6 +30,12 @@ namespace teno {
 namespace {
 
 constexpr int kSmallEntries = kSmallK * kSmallN * kSmallM;  // 180
+// stencil slots unrolled together in the reconstruction loops (loads of that
+// many slots can be in flight per thread)
+#ifndef TENO_RECON_UNROLL
+#define TENO_RECON_UNROLL 2
+#endif
+constexpr int kSlotUnroll = TENO_RECON_UNROLL;
 constexpr int kSmallSlots = kSmallK * kSmallN;               // 36
 
 template <typename T>
@@ -507,7 +513,7 @@ __global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const TT 
   TA acc[M];
 #pragma unroll
   for (int l = 0; l < M; ++l) acc[l] = TA(0);
-#pragma unroll 2
+#pragma unroll (kSlotUnroll)
   for (int s = 0; s < NS; ++s) {
     const TA d = diff(__ldg(nb + s * kTile));
     const TA* As = A + (int64_t)s * M * kTile;
@@ -520,7 +526,7 @@ __global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const TT 
   for (int k = 0; k < kSmallK; ++k) {
 #pragma unroll
     for (int l = 0; l < kSmallM; ++l) as[k][l] = TA(0);
-#pragma unroll 2
+#pragma unroll (kSlotUnroll)
     for (int s = 0; s < kSmallN; ++s) {
       const TA d = diff(__ldg(nb + (NS + k * kSmallN + s) * kTile));
       const TA* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
@@ -647,7 +653,7 @@ __global__ void __launch_bounds__(128) recon_df_kernel(const ReconArgs a, const 
   DF acc[M];
 #pragma unroll
   for (int l = 0; l < M; ++l) acc[l] = {0.f, 0.f};
-#pragma unroll 2
+#pragma unroll (kSlotUnroll)
   for (int s = 0; s < NS; ++s) {
     const DF d = diff(__ldg(nb + s * kTile));
     const float2* As = A + (int64_t)s * M * kTile;
@@ -661,7 +667,7 @@ __global__ void __launch_bounds__(128) recon_df_kernel(const ReconArgs a, const 
   for (int k = 0; k < kSmallK; ++k) {
 #pragma unroll
     for (int l = 0; l < kSmallM; ++l) as[k][l] = {0.f, 0.f};
-#pragma unroll 2
+#pragma unroll (kSlotUnroll)
     for (int s = 0; s < kSmallN; ++s) {
       const DF d = diff(__ldg(nb + (NS + k * kSmallN + s) * kTile));
       const float2* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
@@ -767,7 +773,7 @@ __global__ void __launch_bounds__(128) recon_halo_kernel(const ReconArgs a, cons
   Acc acc[M];
 #pragma unroll
   for (int l = 0; l < M; ++l) acc[l] = Acc{};
-#pragma unroll 2
+#pragma unroll (kSlotUnroll)
   for (int s = 0; s < NS; ++s) {
     const Acc d = dif(s);
     const TE* As = A + (int64_t)s * M * kTile;
@@ -779,7 +785,7 @@ __global__ void __launch_bounds__(128) recon_halo_kernel(const ReconArgs a, cons
   for (int k = 0; k < kSmallK; ++k) {
 #pragma unroll
     for (int l = 0; l < kSmallM; ++l) as[k][l] = Acc{};
-#pragma unroll 2
+#pragma unroll (kSlotUnroll)
     for (int s = 0; s < kSmallN; ++s) {
       const Acc d = dif(NS + k * kSmallN + s);
       const TE* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;

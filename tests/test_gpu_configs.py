@@ -1,0 +1,98 @@
+"""GPU runs of the workload configurations beyond single residuals.
+
+- isentropic vortex (Sec. 5.2) advected for one period (t = 10) on 32k and 128k
+  jittered triangles, TENO5/HLL: L1 density error against the exact solution
+  (the initial state), its decrease with resolution, and the FP32-mixed result
+  against the FP64 one;
+- the adjoint configuration: gradient of J = sum over cells with centroid in
+  [4,6]^2 of |V| rho^2 at t = 1 w.r.t. the initial state, 128k triangles,
+  TENO5, 200 SSP-RK3 steps of dt = 0.005 with checkpoints every 20 steps,
+  against central differences (eps = 1e-6) along 50 seeded directions.
+"""
+import numpy as np
+import pytest
+
+from paper_2105_02127_gb300 import inputs
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_02127_gb300 import autograd, build, teno
+    build.build()
+    teno.lib()
+    return torch, teno, autograd
+
+
+def _areas(mesh):
+    V = mesh.unwrapped_vertices()
+    e1, e2 = V[:, 1] - V[:, 0], V[:, 2] - V[:, 0]
+    return 0.5 * (e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0]), V.mean(axis=1)
+
+
+def _run_vortex(torch, teno, n, precision, t_end=10.0):
+    mesh = inputs.jittered_mesh(n, n, 10.0, 10.0, seed=1002)
+    U0 = inputs.cell_average(mesh, inputs.isentropic_vortex)
+    t = teno.Teno(device=0).load(mesh)
+    t.precompute_stencils(order=5, n_var=4, flux=teno.FLUX_HLL, precision=precision)
+    t.set_state(U0)
+    dt = t.cfl_dt()
+    steps = int(np.ceil(t_end / dt))
+    t.rk3_steps(steps, t_end / steps)
+    t.check_state()
+    U = t.get_state()
+    area, _ = _areas(mesh)
+    return mesh, U0, U, float(np.sum(area * np.abs(U[0] - U0[0])) / np.sum(area))
+
+
+def test_vortex_one_period(env):
+    torch, teno, _ = env
+    errs = {}
+    for n in (128, 256):
+        _, _, U64, e64 = _run_vortex(torch, teno, n, teno.FP64)
+        _, _, Umx, emx = _run_vortex(torch, teno, n, teno.FP32_MIXED)
+        errs[n] = e64
+        diff = float(np.abs(Umx[0] - U64[0]).mean())
+        print(f"vortex {2 * n * n} cells: L1(rho) FP64 {e64:.3e}, mixed {emx:.3e}, "
+              f"mean |mixed - FP64| {diff:.2e}")
+        assert abs(emx - e64) <= 0.05 * e64 + 1e-9
+    rate = np.log2(errs[128] / errs[256])
+    print(f"L1 rate 128^2 -> 256^2 quads: {rate:.2f}")
+    assert errs[256] < errs[128] and rate > 3.0
+
+
+def test_adjoint_config_full(env):
+    torch, teno, ag = env
+    mesh = inputs.jittered_mesh(256, 256, 10.0, 10.0, seed=1004)
+    U = inputs.cell_average(mesh, inputs.isentropic_vortex)
+    area, cen = _areas(mesh)
+    inside = (cen[:, 0] >= 4) & (cen[:, 0] <= 6) & (cen[:, 1] >= 4) & (cen[:, 1] <= 6)
+    wm = torch.from_numpy(inside * area).cuda()
+    t = teno.Teno(device=0).load(mesh)
+    t.precompute_stencils(order=5, n_var=4, flux=teno.FLUX_HLL)
+    dt, n = 0.005, 200
+
+    def J(U0):
+        out = ag.trajectory(U0, t, dt, n, checkpoint_every=20)
+        return (wm * out[0] ** 2).sum()
+
+    Ud = torch.from_numpy(U).cuda().requires_grad_(True)
+    J(Ud).backward()
+    grad = Ud.grad.detach()
+    t.check_state()
+    scale = torch.from_numpy(np.abs(U).max(axis=1, keepdims=True)).cuda()
+    errs = []
+    with torch.no_grad():
+        Ub = torch.from_numpy(U).cuda()
+        for d in inputs.random_directions(3000, 50, U.size):
+            v = torch.from_numpy(d.reshape(U.shape)).cuda() * scale
+            eps = 1e-6
+            fd = (J(Ub + eps * v) - J(Ub - eps * v)).item() / (2 * eps)
+            errs.append(abs(fd - (grad * v).sum().item()) / max(abs(fd), 1e-30))
+    errs = np.array(errs)
+    print("adjoint config: FD relative errors median %.2e max %.2e" % (np.median(errs), errs.max()))
+    assert np.median(errs) < 1e-5 and (errs < 1e-4).mean() >= 0.9
