@@ -36,6 +36,12 @@ constexpr int kSmallEntries = kSmallK * kSmallN * kSmallM;  // 180
 #define TENO_RECON_UNROLL 2
 #endif
 constexpr int kSlotUnroll = TENO_RECON_UNROLL;
+// the FP32-mixed kernels keep more slots in flight (4 measured best, 2 for
+// the double-float and FP64 kernels)
+#ifndef TENO_RECON_UNROLL_MIXED
+#define TENO_RECON_UNROLL_MIXED 4
+#endif
+constexpr int kSlotUnrollMixed = TENO_RECON_UNROLL_MIXED;
 constexpr int kSmallSlots = kSmallK * kSmallN;               // 36
 
 template <typename T>
@@ -139,6 +145,10 @@ template <>
 __device__ __forceinline__ Dual<2> cst<Dual<2>, double>(double x) { return mk<2>(x); }
 template <>
 __device__ __forceinline__ Dual<8> cst<Dual<8>, double>(double x) { return mk<8>(x); }
+template <>
+__device__ __forceinline__ Dual<4> cst<Dual<4>, double>(double x) { return mk<4>(x); }
+template <>
+__device__ __forceinline__ Dual<1> cst<Dual<1>, double>(double x) { return mk<1>(x); }
 
 // ------------------------------------------- double-float (FP32 pair) path
 // Values are unevaluated sums hi + lo of two floats (|lo| <= ulp(hi)/2), about
@@ -513,7 +523,7 @@ __global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const TT 
   TA acc[M];
 #pragma unroll
   for (int l = 0; l < M; ++l) acc[l] = TA(0);
-#pragma unroll (kSlotUnroll)
+#pragma unroll (std::is_same<TA, float>::value ? kSlotUnrollMixed : kSlotUnroll)
   for (int s = 0; s < NS; ++s) {
     const TA d = diff(__ldg(nb + s * kTile));
     const TA* As = A + (int64_t)s * M * kTile;
@@ -526,7 +536,7 @@ __global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const TT 
   for (int k = 0; k < kSmallK; ++k) {
 #pragma unroll
     for (int l = 0; l < kSmallM; ++l) as[k][l] = TA(0);
-#pragma unroll (kSlotUnroll)
+#pragma unroll (std::is_same<TA, float>::value ? kSlotUnrollMixed : kSlotUnroll)
     for (int s = 0; s < kSmallN; ++s) {
       const TA d = diff(__ldg(nb + (NS + k * kSmallN + s) * kTile));
       const TA* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
@@ -773,7 +783,7 @@ __global__ void __launch_bounds__(128) recon_halo_kernel(const ReconArgs a, cons
   Acc acc[M];
 #pragma unroll
   for (int l = 0; l < M; ++l) acc[l] = Acc{};
-#pragma unroll (kSlotUnroll)
+#pragma unroll (kMode == 1 ? kSlotUnrollMixed : kSlotUnroll)
   for (int s = 0; s < NS; ++s) {
     const Acc d = dif(s);
     const TE* As = A + (int64_t)s * M * kTile;
@@ -785,7 +795,7 @@ __global__ void __launch_bounds__(128) recon_halo_kernel(const ReconArgs a, cons
   for (int k = 0; k < kSmallK; ++k) {
 #pragma unroll
     for (int l = 0; l < kSmallM; ++l) as[k][l] = Acc{};
-#pragma unroll (kSlotUnroll)
+#pragma unroll (kMode == 1 ? kSlotUnrollMixed : kSlotUnroll)
     for (int s = 0; s < kSmallN; ++s) {
       const Acc d = dif(NS + k * kSmallN + s);
       const TE* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
@@ -867,29 +877,40 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 constexpr int kRing = 4;
 constexpr int kConsumers = 4;  // one warp per conservative variable (Euler)
 
-// Stage j of a tile: kLPS large-stencil slots, or kSPS slots of one
-// directional stencil.  A ring buffer holds the stage's matrix entries
-// (bulk-copied) followed by the gathered neighbour states [slot][var][32]
-// (float2 hi/lo splits).
+// cp.async (8-byte asynchronous global->shared copies) for the halo prefetch
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// barrier of the four consumer warps only (the producer warp does not take part)
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kConsumers * kTile) : "memory");
+}
+
+// Stage j of a tile's matrix block: kLPS large-stencil slots, or kSPS slots of
+// one directional stencil.
 template <int M, int NS, int kEsz, int kLPS, int kSPS>
 struct StagePlan {
-  static constexpr int kSlotL = M * kTile * kEsz;            // matrix bytes of a large slot
-  static constexpr int kSlotS = kSmallM * kTile * kEsz;      // ... of a directional slot
-  static constexpr int kStateSlot = 4 * kTile * 8;           // gathered states of one slot
+  static constexpr int kSlotL = M * kTile * kEsz;
+  static constexpr int kSlotS = kSmallM * kTile * kEsz;
   static constexpr int kNL = (NS + kLPS - 1) / kLPS;
   static constexpr int kPerSmall = kSmallN / kSPS;
   static constexpr int kStages = kNL + kSmallK * kPerSmall;
   static constexpr int kMatL = kLPS * kSlotL, kMatS = kSPS * kSlotS;
-  static constexpr int kMat = kMatL > kMatS ? kMatL : kMatS;  // matrix part of a buffer
-  static constexpr int kMaxSlots = kLPS > kSPS ? kLPS : kSPS;
-  static constexpr int kBuf = kMat + kMaxSlots * kStateSlot;
+  static constexpr int kMat = kMatL > kMatS ? kMatL : kMatS;
   static constexpr int kE = M * NS + kSmallEntries;
   static constexpr int64_t kTileBytes = (int64_t)kE * kTile * kEsz;
-  static constexpr size_t kSmem = (size_t)kRing * kBuf + 2 * kRing * sizeof(uint64_t);
+  static constexpr size_t kHaloBytes = (size_t)2 * 4 * kHaloMax * sizeof(float2);
+  static constexpr size_t kSmem = (size_t)kRing * kMat + kHaloBytes + 2 * kRing * sizeof(uint64_t);
   static_assert(kSmallN % kSPS == 0, "directional stencil split");
-  static_assert(kMat % 16 == 0 && kBuf % 16 == 0, "16-byte aligned buffers");
-  // first slot, slot count, matrix byte offset within the tile block, bytes,
-  // directional stencil index (-1: large)
+  static_assert(kMat % 16 == 0, "16-byte aligned buffers");
   __device__ static void stage(int j, int& slot0, int& nslot, int64_t& off, int& bytes, int& k) {
     if (j < kNL) {
       slot0 = j * kLPS;
@@ -900,7 +921,7 @@ struct StagePlan {
     } else {
       const int i = j - kNL;
       k = i / kPerSmall;
-      const int s0 = (i % kPerSmall) * kSPS;  // first slot within the directional stencil
+      const int s0 = (i % kPerSmall) * kSPS;
       slot0 = NS + k * kSmallN + s0;
       nslot = kSPS;
       off = (int64_t)(M * NS + (k * kSmallN + s0) * kSmallM) * kTile * kEsz;
@@ -922,79 +943,71 @@ struct TmaTraits<false> {
   static constexpr int kLPS = 4, kSPS = 4;
 };
 
-// Persistent kernel: CTAs loop over tiles; the stage counter g runs on across
-// tiles so the producer keeps up to kRing stages in flight.  kDF: FP64 path
-// (double-float); !kDF: FP32-mixed path.  Euler only.
+// Persistent kernel, Euler only.  Producer lane: the matrix block of every
+// tile in kRing-deep bulk-copy stages.  Consumer warps (one per variable):
+// the tile's stencil halo in a double-buffered shared-memory area, prefetched
+// with cp.async one tile ahead; stencil differences from the halo, matrices
+// from the ring.  kDF: FP64 path (double-float); !kDF: FP32-mixed path.
 template <int M, int NS, int NQ, bool kDF>
 __global__ void __launch_bounds__(kTile * (kConsumers + 1))
-    recon_tma_kernel(const ReconArgs a, const DFTable ev, int* err) {
+    recon_tma_kernel(const ReconArgs a, const HaloArgs h, const DFTable ev, int* err) {
   using TR = TmaTraits<kDF>;
   using TE = typename TR::TE;
   using P = StagePlan<M, NS, (int)sizeof(TE), TR::kLPS, TR::kSPS>;
   constexpr int NV = 4;
   constexpr int SL = NS + kSmallSlots;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kRing * P::kBuf);
+  float2* halo = reinterpret_cast<float2*>(smem + (size_t)kRing * P::kMat);  // [2][NV][kHaloMax]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kRing * P::kMat + P::kHaloBytes);
   uint64_t* empty = full + kRing;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n_tiles = (a.n_cell + kTile - 1) / kTile;
   if (threadIdx.x == 0) {
     for (int i = 0; i < kRing; ++i) {
-      mbar_init(&full[i], 2);  // producer lane 0: expect_tx arrival + gather-done arrival
+      mbar_init(&full[i], 1);
       mbar_init(&empty[i], kConsumers);
     }
     mbar_fence_init();
   }
   __syncthreads();
   if (warp == kConsumers) {
-    // ---- producer warp: matrices by bulk copy (lane 0), neighbour states by
-    // all lanes
-    int64_t g = 0;
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-      const unsigned char* src = reinterpret_cast<const unsigned char*>(a.ahat) + tile * P::kTileBytes;
-      const int32_t* nb = a.nbr + tile * (int64_t)SL * kTile + lane;
-      for (int j = 0; j < P::kStages; ++j, ++g) {
-        const int b = (int)(g % kRing);
-        int slot0, nslot, bytes, k;
-        int64_t off;
-        P::stage(j, slot0, nslot, off, bytes, k);
-        if (g >= kRing) {
-          bool ok = true;
-          if (lane == 0) ok = mbar_wait(&empty[b], (uint32_t)((g / kRing) - 1) & 1);
-          ok = __shfl_sync(0xffffffffu, ok, 0);
-          if (!ok) {
-            if (lane == 0) {
-              atomicOr(err, 2);
-              for (int64_t i = g - kRing; i < g; ++i) mbar_wait(&full[i % kRing], (uint32_t)(i / kRing) & 1);
-            }
+    // ---- producer lane: matrix blocks, tile after tile
+    if (lane == 0) {
+      int64_t g = 0;
+      for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const unsigned char* src =
+            reinterpret_cast<const unsigned char*>(a.ahat) + tile * P::kTileBytes;
+        for (int j = 0; j < P::kStages; ++j, ++g) {
+          const int b = (int)(g % kRing);
+          if (g >= kRing && !mbar_wait(&empty[b], (uint32_t)((g / kRing) - 1) & 1)) {
+            atomicOr(err, 2);
+            for (int64_t i = g - kRing; i < g; ++i)
+              mbar_wait(&full[i % kRing], (uint32_t)(i / kRing) & 1);
             return;
           }
-        }
-        unsigned char* buf = smem + (size_t)b * P::kBuf;
-        if (lane == 0) {
+          int slot0, nslot, bytes, k;
+          int64_t off;
+          P::stage(j, slot0, nslot, off, bytes, k);
           mbar_expect_tx(&full[b], (uint32_t)bytes);
-          bulk_g2s(buf, src + off, (uint32_t)bytes, &full[b]);
+          bulk_g2s(smem + (size_t)b * P::kMat, src + off, (uint32_t)bytes, &full[b]);
         }
-        float2* st = reinterpret_cast<float2*>(buf + P::kMat);
-        int idx[P::kMaxSlots];
-#pragma unroll
-        for (int s = 0; s < P::kMaxSlots; ++s) idx[s] = s < nslot ? __ldg(nb + (slot0 + s) * kTile) : 0;
-#pragma unroll
-        for (int s = 0; s < P::kMaxSlots; ++s) {
-          if (s < nslot) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) st[(s * NV + v) * kTile + lane] = __ldg(a.Us + v * a.n_pad + idx[s]);
-          }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&full[b]);
       }
     }
     return;
   }
-  // ---- consumers: warp v = variable v of the tile's 32 cells
-  const int v = warp;
+  // ---- consumers
+  const int v = warp, tid = threadIdx.x;
   using Acc = typename TR::Acc;
+  auto prefetch = [&](int64_t tile, int hb) {
+    const int h0 = h.off[tile], H = h.off[tile + 1] - h0;
+    for (int i = tid; i < H; i += kConsumers * kTile) {
+      const int id = __ldg(h.ids + h0 + i);
+#pragma unroll
+      for (int w = 0; w < NV; ++w)
+        cp_async8(&halo[(hb * NV + w) * kHaloMax + i], a.Us + (int64_t)w * a.n_pad + id);
+    }
+    cp_async_commit();
+  };
   auto mac = [](Acc& acc, TE m, Acc d) {
     if constexpr (kDF)
       df_mac(acc, m, d);
@@ -1002,9 +1015,31 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
       acc = fmaf(m, d, acc);
   };
   int64_t g = 0;
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  int hb = 0;
+  if ((int64_t)blockIdx.x < n_tiles) prefetch(blockIdx.x, 0);
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, hb ^= 1) {
+    consumer_sync();  // every consumer is done with the other halo buffer
+    const int64_t nxt = tile + gridDim.x;
+    if (nxt < n_tiles)
+      prefetch(nxt, hb ^ 1);
+    else
+      cp_async_commit();  // empty group keeps the group count uniform
+    cp_async_wait<1>();   // this thread's copies of the current halo have landed
+    consumer_sync();      // ... and everyone's
+    const float2* st = halo + (hb * NV + v) * kHaloMax;
+    const uint16_t* nb = h.nbr_loc + tile * (int64_t)SL * kTile + lane;
     const int64_t c = tile * kTile + lane;  // may be a pad lane of the last tile
     const float2 u0s = a.Us[(int64_t)v * a.n_pad + (c < a.n_cell ? c : 0)];
+    auto dif = [&](int idx) -> Acc {
+      const float2 q = st[idx];
+      if constexpr (kDF) {
+        DF t = two_sum(q.x, -u0s.x);
+        t.l += q.y - u0s.y;
+        return two_sum(t.h, t.l);
+      } else {
+        return (q.x - u0s.x) + (q.y - u0s.y);
+      }
+    };
     Acc acc[M];
     Acc as[kSmallK][kSmallM];
 #pragma unroll
@@ -1018,28 +1053,21 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
       int slot0, nslot, bytes, k;
       int64_t off;
       P::stage(j, slot0, nslot, off, bytes, k);
+      constexpr int kMaxSlots = TR::kLPS > TR::kSPS ? TR::kLPS : TR::kSPS;
+      int loc[kMaxSlots];
+#pragma unroll
+      for (int s = 0; s < kMaxSlots; ++s) loc[s] = s < nslot ? __ldg(nb + (slot0 + s) * kTile) : 0;
       if (!mbar_wait(&full[b], (uint32_t)(g / kRing) & 1)) {
         atomicOr(err, 2);
+        cp_async_wait<0>();
         return;
       }
-      const unsigned char* buf = smem + (size_t)b * P::kBuf;
-      const TE* mat = reinterpret_cast<const TE*>(buf) + lane;
-      const float2* st = reinterpret_cast<const float2*>(buf + P::kMat) + v * kTile + lane;
-      auto dif = [&](int s) -> Acc {
-        const float2 q = st[s * NV * kTile];
-        if constexpr (kDF) {
-          DF t = two_sum(q.x, -u0s.x);
-          t.l += q.y - u0s.y;
-          return two_sum(t.h, t.l);
-        } else {
-          return (q.x - u0s.x) + (q.y - u0s.y);
-        }
-      };
+      const TE* mat = reinterpret_cast<const TE*>(smem + (size_t)b * P::kMat) + lane;
       if (k < 0) {
 #pragma unroll
         for (int s = 0; s < TR::kLPS; ++s) {
           if (s < nslot) {
-            const Acc d = dif(s);
+            const Acc d = dif(loc[s]);
 #pragma unroll
             for (int l = 0; l < M; ++l) mac(acc[l], mat[(s * M + l) * kTile], d);
           }
@@ -1050,7 +1078,7 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
           if (kk != k) continue;
 #pragma unroll
           for (int s = 0; s < TR::kSPS; ++s) {
-            const Acc d = dif(s);
+            const Acc d = dif(loc[s]);
 #pragma unroll
             for (int l = 0; l < kSmallM; ++l) mac(as[kk][l], mat[(s * kSmallM + l) * kTile], d);
           }
@@ -1073,6 +1101,7 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
       }
     }
   }
+  cp_async_wait<0>();
 }
 
 // FP32 hi/lo split of a state: hi = fl32(U), lo = fl32(U - hi)
@@ -1283,7 +1312,9 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
                                                             const TQ* __restrict__ Uq,
                                                             const double* __restrict__ w,
                                                             double* __restrict__ Uq_bar) {
-  constexpr int ND = 2 * NV;
+  // two forward-mode passes of NV directions each (left seeds, then right
+  // seeds): half the live derivative values of a single 2*NV pass
+  constexpr int ND = NV;
   using D = Dual<ND>;
   const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= a.n_face) return;
@@ -1297,50 +1328,50 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
     if (n >= 0) Kb[v] += w[v * a.n_pad + n] * a.inv_area[n];
   }
   for (int k = 0; k < NQ; ++k) {
-    D UL[NV], UR[NV], F[NV];
+    double ul[NV], ur[NV];
     const TQ* pl = Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      UL[v] = mk<ND>(to_d(pl[v]));
-      UL[v].d[v] = 1.0;
-    }
+    for (int v = 0; v < NV; ++v) ul[v] = to_d(pl[v]);
     if (n >= 0) {
       const TQ* pr = Uq + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        UR[v] = mk<ND>(to_d(pr[v]));
-        UR[v].d[NV + v] = 1.0;
-      }
-    } else if constexpr (NV == 4) {
-      double x = a.f_geom[5 * f + 3] - ny * len * a.gt[k];
-      ghost_state<D>(en, UL, nx, ny, x, a.time, a.gamma, UR);
-    } else {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) UR[v] = UL[v];
-    }
-    if constexpr (NV == 1) {
-      const double an = a.adv_x * nx + a.adv_y * ny;
-      F[0] = an * (an >= 0.0 ? UL[0] : UR[0]);
-    } else {
-      euler_riemann<D>(UL, UR, nx, ny, a.gamma, FLUX == TENO_FLUX_HLLC, F);
+      for (int v = 0; v < NV; ++v) ur[v] = to_d(pr[v]);
     }
     const double wk = a.gw[k] * len;
-    double* bl = Uq_bar + ((int64_t)(o * 3 + eo) * NQ + k) * NV;
+    const double x = a.f_geom[5 * f + 3] - ny * len * a.gt[k];
+    for (int side = 0; side < (n >= 0 ? 2 : 1); ++side) {
+      D UL[NV], UR[NV], F[NV];
 #pragma unroll
-    for (int j = 0; j < NV; ++j) {
-      double s = 0.0;
+      for (int v = 0; v < NV; ++v) {
+        UL[v] = mk<ND>(ul[v]);
+        if (side == 0) UL[v].d[v] = 1.0;
+      }
+      if (n >= 0) {
 #pragma unroll
-      for (int i = 0; i < NV; ++i) s = fma(F[i].d[j], Kb[i], s);
-      bl[j] = wk * s;
-    }
-    if (n >= 0) {
-      double* br = Uq_bar + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV;
+        for (int v = 0; v < NV; ++v) {
+          UR[v] = mk<ND>(ur[v]);
+          if (side == 1) UR[v].d[v] = 1.0;
+        }
+      } else if constexpr (NV == 4) {
+        ghost_state<D>(en, UL, nx, ny, x, a.time, a.gamma, UR);  // carries dUR/dUL
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) UR[v] = UL[v];
+      }
+      if constexpr (NV == 1) {
+        const double an = a.adv_x * nx + a.adv_y * ny;
+        F[0] = an * (an >= 0.0 ? UL[0] : UR[0]);
+      } else {
+        euler_riemann<D>(UL, UR, nx, ny, a.gamma, FLUX == TENO_FLUX_HLLC, F);
+      }
+      double* out = side == 0 ? Uq_bar + ((int64_t)(o * 3 + eo) * NQ + k) * NV
+                              : Uq_bar + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV;
 #pragma unroll
       for (int j = 0; j < NV; ++j) {
-        double s = 0.0;
+        double sacc = 0.0;
 #pragma unroll
-        for (int i = 0; i < NV; ++i) s = fma(F[i].d[NV + j], Kb[i], s);
-        br[j] = wk * s;
+        for (int i = 0; i < NV; ++i) sacc = fma(F[i].d[j], Kb[i], sacc);
+        out[j] = wk * sacc;
       }
     }
   }
@@ -1416,26 +1447,117 @@ __global__ void __launch_bounds__(128) recon_vjp_kernel(const TS* __restrict__ a
   u_self[(int64_t)v * n_pad + c] = u0b - tot;
 }
 
+// Double-float version for the FP64 path (matrices stored as (hi, lo)
+// pairs): the transposed matvecs run on the FP32 pipe; d_bar is written as
+// pairs, u_self in FP64.
+__device__ __forceinline__ DF d_to_df(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ DF df_div_small(DF a, int n) {  // a / n for n in 1..3
+  const float fn = (float)n;
+  const float qh = a.h / fn;
+  const float r = fmaf(-qh, fn, a.h);  // exact remainder
+  return two_sum(qh, (r + a.l) / fn);
+}
+
+template <int M, int NS, int NQ, int NV>
+__global__ void __launch_bounds__(128) recon_vjp_df_kernel(const float2* __restrict__ ahat,
+                                                           const uint8_t* __restrict__ sel_in,
+                                                           const double* __restrict__ Uq_bar,
+                                                           DF* __restrict__ d_bar,
+                                                           double* __restrict__ u_self,
+                                                           int64_t n_cell, int64_t n_pad,
+                                                           const DFTable ev) {
+  const int lane = threadIdx.x, v = threadIdx.y;
+  const int64_t tile = (int64_t)blockIdx.x * blockDim.z + threadIdx.z;
+  const int64_t c = tile * kTile + lane;
+  if (c >= n_cell) return;
+  constexpr int E = M * NS + kSmallEntries;
+  constexpr int SL = NS + kSmallSlots;
+  const float2* A = ahat + tile * (int64_t)E * kTile + lane;
+  DF* db = d_bar + tile * (int64_t)SL * NV * kTile + v * kTile + lane;
+  DF cb[M];
+#pragma unroll
+  for (int l = 0; l < M; ++l) cb[l] = {0.f, 0.f};
+  DF u0b = {0.f, 0.f};
+  const double* ub = Uq_bar + c * (3 * NQ * NV) + v;
+#pragma unroll
+  for (int p = 0; p < 3 * NQ; ++p) {
+    const DF b = d_to_df(ub[p * NV]);
+    u0b = u0b + b;
+#pragma unroll
+    for (int l = 0; l < M; ++l) df_mac(cb[l], ev.psi[p * kMaxM + l], b);
+  }
+#pragma unroll
+  for (int l = 0; l < M; ++l) cb[l] = df_norm(cb[l]);
+  const uint8_t sel = sel_in[(int64_t)v * n_pad + c];
+  DF tot = {0.f, 0.f};
+  const bool large = sel & 8;
+#pragma unroll 2
+  for (int s = 0; s < NS; ++s) {
+    DF t = {0.f, 0.f};
+    if (large) {
+#pragma unroll
+      for (int l = 0; l < M; ++l)
+        df_mac(t, A[(int64_t)(s * M + l) * kTile], cb[l]);
+      t = df_norm(t);
+    }
+    db[(int64_t)s * NV * kTile] = t;
+    tot = tot + t;
+  }
+  const int nd = (sel & 1) + ((sel >> 1) & 1) + ((sel >> 2) & 1);
+#pragma unroll
+  for (int k = 0; k < kSmallK; ++k) {
+    const bool on = !large && ((sel >> k) & 1);
+    for (int s = 0; s < kSmallN; ++s) {
+      DF t = {0.f, 0.f};
+      if (on) {
+        const float2* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
+#pragma unroll
+        for (int l = 0; l < kSmallM; ++l) df_mac(t, As[l * kTile], cb[l]);
+        t = df_div_small(df_norm(t), nd);
+      }
+      db[(int64_t)(NS + k * kSmallN + s) * NV * kTile] = t;
+      tot = tot + t;
+    }
+  }
+  u_self[(int64_t)v * n_pad + c] = to_d(u0b - tot);
+}
+
 // v[j] = u_self[j] + sum over the stencil slots that hold cell j
-template <int NV>
+template <int NV, typename TD>
 __global__ void __launch_bounds__(256) scatter_gather_kernel(const int64_t* __restrict__ rev_off,
                                                              const int64_t* __restrict__ rev_idx,
-                                                             const double* __restrict__ d_bar,
+                                                             const TD* __restrict__ d_bar,
                                                              const double* __restrict__ u_self,
                                                              double* __restrict__ out,
                                                              int64_t n_cell, int64_t n_pad) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n_cell) return;
-  double acc[NV];
+  if constexpr (std::is_same<TD, DF>::value) {
+    DF acc[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) acc[v] = u_self[v * n_pad + j];
-  for (int64_t r = rev_off[j]; r < rev_off[j + 1]; ++r) {
-    const int64_t base = rev_idx[r];
+    for (int v = 0; v < NV; ++v) acc[v] = d_to_df(u_self[v * n_pad + j]);
+    for (int64_t r = rev_off[j]; r < rev_off[j + 1]; ++r) {
+      const int64_t base = rev_idx[r];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] += d_bar[base + v * kTile];
+      for (int v = 0; v < NV; ++v) acc[v] = acc[v] + d_bar[base + v * kTile];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v * n_pad + j] = to_d(acc[v]);
+  } else {
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = u_self[v * n_pad + j];
+    for (int64_t r = rev_off[j]; r < rev_off[j + 1]; ++r) {
+      const int64_t base = rev_idx[r];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += d_bar[base + v * kTile];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v * n_pad + j] = acc[v];
   }
-#pragma unroll
-  for (int v = 0; v < NV; ++v) out[v * n_pad + j] = acc[v];
 }
 
 template <typename F>
@@ -1471,7 +1593,7 @@ cudaError_t launch_recon_tma(const ReconArgs& a, const DeviceMesh& dm, int* err,
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)per_sm * sms);
-  kern<<<(unsigned)grid, threads, P::kSmem, st>>>(a, dm.eval_df, err);
+  kern<<<(unsigned)grid, threads, P::kSmem, st>>>(a, dm.halo, dm.eval_df, err);
   return cudaGetLastError();
 }
 
@@ -1511,7 +1633,7 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
         return cudaGetLastError();
       }
       if constexpr (NV == 4) {
-        if (dm.variant == 2 && dm.err_flag && dm.precision != TENO_FP64_NATIVE) {
+        if (dm.variant == 2 && dm.err_flag && dm.halo.off && dm.precision != TENO_FP64_NATIVE) {
           if (dm.precision == TENO_FP64) return launch_recon_tma<M, NS, NQ, true>(a, dm, dm.err_flag, st);
           return launch_recon_tma<M, NS, NQ, false>(a, dm, dm.err_flag, st);
         }
@@ -1706,8 +1828,14 @@ cudaError_t launch_recon_vjp(const DeviceMesh& dm, const uint8_t* sel, const dou
       using TS = typename decltype(tsc)::type;
       constexpr int TZ = 4 / NV;
       dim3 block(kTile, NV, TZ);
-      recon_vjp_kernel<M, NS, NQ, NV, TS><<<(unsigned)((tiles + TZ - 1) / TZ), block, 0, st>>>(
-          (const TS*)dm.ahat, sel, Uq_bar, d_bar, u_self, dm.n_cell, dm.n_pad, dm.eval);
+      const unsigned grid = (unsigned)((tiles + TZ - 1) / TZ);
+      if constexpr (std::is_same<TS, float2>::value)
+        recon_vjp_df_kernel<M, NS, NQ, NV><<<grid, block, 0, st>>>(
+            (const float2*)dm.ahat, sel, Uq_bar, (DF*)d_bar, u_self, dm.n_cell, dm.n_pad,
+            dm.eval_df);
+      else
+        recon_vjp_kernel<M, NS, NQ, NV, TS><<<grid, block, 0, st>>>(
+            (const TS*)dm.ahat, sel, Uq_bar, d_bar, u_self, dm.n_cell, dm.n_pad, dm.eval);
     };
     using I1 = std::integral_constant<int, 1>;
     using I4 = std::integral_constant<int, 4>;
@@ -1726,13 +1854,22 @@ cudaError_t launch_scatter_gather(const DeviceMesh& dm, const int64_t* rev_off,
                                   const int64_t* rev_idx, const double* d_bar,
                                   const double* u_self, double* v, cudaStream_t st) {
   const unsigned grid = (unsigned)((dm.n_cell + 255) / 256);
-  if (dm.n_var == 1)
-    scatter_gather_kernel<1><<<grid, 256, 0, st>>>(rev_off, rev_idx, d_bar, u_self, v, dm.n_cell,
-                                                   dm.n_pad);
-  else
-    scatter_gather_kernel<4><<<grid, 256, 0, st>>>(rev_off, rev_idx, d_bar, u_self, v, dm.n_cell,
-                                                   dm.n_pad);
+  const bool pairs = dm.precision == TENO_FP64;  // d_bar holds (hi, lo) pairs
+  if (dm.n_var == 1) {
+    if (pairs)
+      scatter_gather_kernel<1, DF><<<grid, 256, 0, st>>>(rev_off, rev_idx, (const DF*)d_bar,
+                                                         u_self, v, dm.n_cell, dm.n_pad);
+    else
+      scatter_gather_kernel<1, double><<<grid, 256, 0, st>>>(rev_off, rev_idx, d_bar, u_self, v,
+                                                             dm.n_cell, dm.n_pad);
+  } else {
+    if (pairs)
+      scatter_gather_kernel<4, DF><<<grid, 256, 0, st>>>(rev_off, rev_idx, (const DF*)d_bar,
+                                                         u_self, v, dm.n_cell, dm.n_pad);
+    else
+      scatter_gather_kernel<4, double><<<grid, 256, 0, st>>>(rev_off, rev_idx, d_bar, u_self, v,
+                                                             dm.n_cell, dm.n_pad);
+  }
   return cudaGetLastError();
 }
-
 }  // namespace teno
