@@ -75,10 +75,13 @@ typedef struct teno_params {
   int32_t linear;    /* 1: always take the large-stencil polynomial (the paper's "Linear" rows) */
   int32_t nq;        /* Gauss points per edge; 0 = 2 for order <= 4, 3 otherwise */
   int32_t recon_variant; /* reconstruction kernel: 0 the stencil halo of each 32-cell tile
-                            staged in shared memory (falls back to 1 if a halo exceeds 256
-                            cells); 1 direct gathers of neighbour states; 2 matrices and
-                            neighbour states staged through TMA bulk copies by a producer
-                            warp (Euler, TENO_FP64 and TENO_FP32_MIXED; else 1) */
+                            staged in shared memory; 1 direct gathers of neighbour states;
+                            2 (default) persistent kernel whose producer lane streams the
+                            per-cell matrices through a TMA bulk-copy ring while the
+                            tile's stencil halo is double-buffered with cp.async (Euler,
+                            TENO_FP64 and TENO_FP32_MIXED; else 0).  0 and 2 fall back to 1
+                            where a tile's halo exceeds 256 cells.  All variants give
+                            bitwise identical results. */
   double ct;         /* cutoff C_T */
   double eps;        /* epsilon of the scale separation */
   double gamma;      /* ratio of specific heats */
@@ -86,7 +89,8 @@ typedef struct teno_params {
   double cfl;        /* CFL number for teno_rk3_step with dt <= 0 */
 } teno_params;
 
-/* Fills *p with the defaults above (order 5, n_var 4, HLL, FP64, cfl 0.4). */
+/* Fills *p with the defaults above (order 5, n_var 4, HLL, FP64, recon_variant 2,
+   cfl 0.4). */
 void teno_default_params(teno_params* p);
 
 /* Create a context on CUDA device `device`, launching on `cuda_stream`

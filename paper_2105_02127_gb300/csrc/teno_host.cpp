@@ -76,8 +76,10 @@ struct teno_ctx {
   bool split_ok = false;  // b_Usplit holds split(b_U)
   // adjoint
   DevBuf b_rev_off, b_rev_idx, b_dbar, b_uself, b_Uqbar, b_l1, b_l2, b_lamn, b_vtmp, b_selA;
+  DevBuf b_Uq_st[2], b_sel_st[2];  // stage 1, 2 reconstructions kept by the adjoint replay
   bool adj_ok = false;
-  std::vector<int64_t> rev_off_h, rev_idx_h;
+  std::vector<int64_t> rev_off_h;
+  std::vector<int32_t> rev_idx_h;
   double time = 0.0;
   // kernel timing (teno_profile): event pairs around launches, per kind
   bool prof_on = false;
@@ -754,9 +756,11 @@ int run_precompute(teno_ctx* ctx) {
     for (int s = 0; s < SL; ++s) nbr[((size_t)tile * SL + s) * kTile + lane] = 0;
   }
   // reverse stencil adjacency (adjoint gather): for every cell the d_bar
-  // positions of the slots that hold it
-  {
-    const int NV = p.n_var;
+  // entries (tile * SL + slot) * 32 + lane of the slots that hold it (int32:
+  // built for meshes with npad * SL < 2^31; the adjoint refuses larger ones)
+  ctx->rev_off_h.clear();
+  ctx->rev_idx_h.clear();
+  if ((int64_t)npad * SL < ((int64_t)1 << 31)) {
     std::vector<int64_t> cnt(nc + 1, 0);
     for (int64_t c = 0; c < nc; ++c) {
       const int64_t tile = c / kTile, lane = c % kTile;
@@ -774,7 +778,7 @@ int run_precompute(teno_ctx* ctx) {
       for (int s = 0; s < SL; ++s) {
         if (s >= ns && !((smask[c] >> ((s - ns) / kSmallN)) & 1)) continue;
         int32_t j = nbr[((size_t)tile * SL + s) * kTile + lane];
-        ctx->rev_idx_h[pos[j]++] = ((tile * SL + s) * NV) * kTile + lane;
+        ctx->rev_idx_h[pos[j]++] = (int32_t)((tile * SL + s) * kTile + lane);
       }
     }
   }
@@ -909,7 +913,8 @@ int upload_mesh(teno_ctx* ctx) {
 // split_ready: the FP32 split buffer already holds split(U) (written by the
 // previous RK update); otherwise the mixed path splits U first
 int stage_flux(teno_ctx* ctx, const double* U, uint8_t* sel_out, double time,
-               bool split_ready = false) {
+               bool split_ready = false, void* uq = nullptr) {
+  if (!uq) uq = ctx->b_Uq.p;
   const uint8_t* sel_in = ctx->override_on ? (const uint8_t*)ctx->b_sel_ovr.p : nullptr;
   const bool split = ctx->prm.precision != TENO_FP64_NATIVE;
   float2* Us = split ? (float2*)ctx->b_Usplit.p : nullptr;
@@ -919,10 +924,10 @@ int stage_flux(teno_ctx* ctx, const double* U, uint8_t* sel_out, double time,
     prof_end(ctx, ps);
   }
   long pe = prof_begin(ctx, K_RECON);
-  CK(launch_recon(ctx->dm, U, Us, ctx->b_Uq.p, sel_out, sel_in, ctx->stream), "recon launch");
+  CK(launch_recon(ctx->dm, U, Us, uq, sel_out, sel_in, ctx->stream), "recon launch");
   prof_end(ctx, pe);
   pe = prof_begin(ctx, K_FLUX);
-  CK(launch_face_flux(ctx->dm, ctx->b_Uq.p, ctx->b_K.p, time, ctx->stream), "face flux launch");
+  CK(launch_face_flux(ctx->dm, uq, ctx->b_K.p, time, ctx->stream), "face flux launch");
   prof_end(ctx, pe);
   return TENO_OK;
 }
@@ -970,6 +975,9 @@ int to_user(teno_ctx* ctx, const double* src, double* dst, int on_device) {
 
 int ensure_adjoint(teno_ctx* ctx) {
   if (ctx->adj_ok) return TENO_OK;
+  if (ctx->rev_off_h.empty())
+    return fail(ctx, TENO_EINVAL,
+                "adjoint: mesh too large for 32-bit stencil-entry indices (cells x slots >= 2^31)");
   const int64_t npad = ctx->npad, nc = ctx->nc;
   const int nv = ctx->prm.n_var;
   const size_t ntile = npad / kTile;
@@ -981,34 +989,46 @@ int ensure_adjoint(teno_ctx* ctx) {
   if (!rc) rc = dev_alloc(ctx, ctx->b_lamn, sizeof(double) * nv * npad);
   if (!rc) rc = dev_alloc(ctx, ctx->b_vtmp, sizeof(double) * nv * npad);
   if (!rc) rc = dev_alloc(ctx, ctx->b_selA, (size_t)nv * npad);
+  for (int k = 0; k < 2 && !rc; ++k) {
+    rc = dev_alloc(ctx, ctx->b_Uq_st[k], ctx->b_Uq.bytes);
+    if (!rc) rc = dev_alloc(ctx, ctx->b_sel_st[k], (size_t)nv * npad);
+  }
   if (!rc) rc = upload(ctx, ctx->b_rev_off, ctx->rev_off_h.data(), sizeof(int64_t) * (nc + 1));
   if (!rc)
     rc = upload(ctx, ctx->b_rev_idx, ctx->rev_idx_h.data(),
-                sizeof(int64_t) * std::max<size_t>(1, ctx->rev_idx_h.size()));
+                sizeof(int32_t) * std::max<size_t>(1, ctx->rev_idx_h.size()));
   if (rc) return rc;
   CK(cudaMemsetAsync(ctx->b_dbar.p, 0, ctx->b_dbar.bytes, ctx->stream), "memset");
   ctx->adj_ok = true;
   return TENO_OK;
 }
 
-// v = (dR/dU)^T w at U (all internal order)
-int vjp_internal(teno_ctx* ctx, const double* U, const double* w, double* v, double time) {
+// v = (dR/dU)^T w at U (all internal order).  With uq_saved / sel_saved (the
+// Gauss-point values and selection a forward stage at U already produced)
+// the reconstruction is not repeated.
+int vjp_internal(teno_ctx* ctx, const double* U, const double* w, double* v, double time,
+                 const void* uq_saved = nullptr, const uint8_t* sel_saved = nullptr) {
   int rc = ensure_adjoint(ctx);
   if (rc) return rc;
-  uint8_t* sel = (uint8_t*)ctx->b_selA.p;
   const uint8_t* sel_in = ctx->override_on ? (const uint8_t*)ctx->b_sel_ovr.p : nullptr;
-  float2* Us = nullptr;
-  if (ctx->prm.precision != TENO_FP64_NATIVE) {
-    Us = (float2*)ctx->b_Usplit.p;
-    CK(launch_split(ctx->dm, U, Us, ctx->stream), "split launch");
-    ctx->split_ok = false;
+  const uint8_t* sel = sel_in ? sel_in : sel_saved;
+  const void* uq = uq_saved;
+  if (!uq) {
+    uint8_t* sel_out = (uint8_t*)ctx->b_selA.p;
+    float2* Us = nullptr;
+    if (ctx->prm.precision != TENO_FP64_NATIVE) {
+      Us = (float2*)ctx->b_Usplit.p;
+      CK(launch_split(ctx->dm, U, Us, ctx->stream), "split launch");
+      ctx->split_ok = false;
+    }
+    long pr = prof_begin(ctx, K_RECON);
+    CK(launch_recon(ctx->dm, U, Us, ctx->b_Uq.p, sel_out, sel_in, ctx->stream), "recon launch");
+    prof_end(ctx, pr);
+    uq = ctx->b_Uq.p;
+    if (!sel_in) sel = sel_out;
   }
-  long pr = prof_begin(ctx, K_RECON);
-  CK(launch_recon(ctx->dm, U, Us, ctx->b_Uq.p, sel, sel_in, ctx->stream), "recon launch");
-  prof_end(ctx, pr);
-  if (sel_in) sel = (uint8_t*)ctx->b_sel_ovr.p;
   long pe = prof_begin(ctx, K_FLUX_VJP);
-  CK(launch_face_flux_vjp(ctx->dm, ctx->b_Uq.p, w, (double*)ctx->b_Uqbar.p, time, ctx->stream),
+  CK(launch_face_flux_vjp(ctx->dm, uq, w, (double*)ctx->b_Uqbar.p, time, ctx->stream),
      "flux vjp launch");
   prof_end(ctx, pe);
   pe = prof_begin(ctx, K_RECON_VJP);
@@ -1018,7 +1038,7 @@ int vjp_internal(teno_ctx* ctx, const double* U, const double* w, double* v, dou
   prof_end(ctx, pe);
   pe = prof_begin(ctx, K_SCATTER);
   CK(launch_scatter_gather(ctx->dm, (const int64_t*)ctx->b_rev_off.p,
-                           (const int64_t*)ctx->b_rev_idx.p, (const double*)ctx->b_dbar.p,
+                           (const int32_t*)ctx->b_rev_idx.p, (const double*)ctx->b_dbar.p,
                            (const double*)ctx->b_uself.p, v, ctx->stream),
      "scatter launch");
   prof_end(ctx, pe);
@@ -1029,8 +1049,9 @@ int vjp_internal(teno_ctx* ctx, const double* U, const double* w, double* v, dou
 // (the mixed path keeps split(U) current: each RK update writes the split of
 // its output, which the next stage's reconstruction reads)
 int rk_stage(teno_ctx* ctx, const double* Un, const double* Us, double* out, double cn,
-             double cs, double dt, const double* max_lam, double time, bool split_ready) {
-  int rc = stage_flux(ctx, Us, nullptr, time, split_ready);
+             double cs, double dt, const double* max_lam, double time, bool split_ready,
+             void* uq = nullptr, uint8_t* sel_out = nullptr) {
+  int rc = stage_flux(ctx, Us, sel_out, time, split_ready, uq);
   if (rc) return rc;
   const bool split = ctx->prm.precision != TENO_FP64_NATIVE;
   long pe = prof_begin(ctx, K_GATHER);
@@ -1056,7 +1077,7 @@ void teno_default_params(teno_params* p) {
   p->precision = TENO_FP64;
   p->linear = 0;
   p->nq = 0;
-  p->recon_variant = 0;
+  p->recon_variant = 2;
   p->ct = 1e-6;
   p->eps = 1e-12;
   p->gamma = 1.4;
@@ -1114,7 +1135,8 @@ int teno_destroy(teno_ctx* ctx) {
                     &ctx->b_Usplit,
                     &ctx->b_flag, &ctx->b_rev_off, &ctx->b_rev_idx, &ctx->b_dbar, &ctx->b_uself,
                     &ctx->b_Uqbar, &ctx->b_l1, &ctx->b_l2, &ctx->b_lamn, &ctx->b_vtmp,
-                    &ctx->b_selA};
+                    &ctx->b_selA, &ctx->b_Uq_st[0], &ctx->b_Uq_st[1], &ctx->b_sel_st[0],
+                    &ctx->b_sel_st[1]};
   for (DevBuf* b : bufs) dev_free(*b);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;
@@ -1422,21 +1444,26 @@ int teno_adjoint_step(teno_ctx* ctx, double dt, const double* lam_np1, double* l
   double* tmp = (double*)ctx->b_vtmp.p;
   const double t = ctx->time;
   rc = to_internal(ctx, lam_np1, lam, on_device);
-  // forward replay of the stage states
-  if (!rc) rc = rk_stage(ctx, U, U, U1, 0.0, 1.0, dt, nullptr, t, false);
-  if (!rc) rc = rk_stage(ctx, U, U1, U2, 0.75, 0.25, dt, nullptr, t + dt, false);
+  // forward replay of the stage states; the Gauss-point values and
+  // selections of stages 1 and 2 are kept for their VJPs
+  void* uq0 = ctx->b_Uq_st[0].p;
+  void* uq1 = ctx->b_Uq_st[1].p;
+  uint8_t* s0 = (uint8_t*)ctx->b_sel_st[0].p;
+  uint8_t* s1 = (uint8_t*)ctx->b_sel_st[1].p;
+  if (!rc) rc = rk_stage(ctx, U, U, U1, 0.0, 1.0, dt, nullptr, t, false, uq0, s0);
+  if (!rc) rc = rk_stage(ctx, U, U1, U2, 0.75, 0.25, dt, nullptr, t + dt, false, uq1, s1);
   // stage 3: U^{n+1} = 1/3 U^n + 2/3 U2 + 2/3 dt R(U2)
   if (!rc) rc = vjp_internal(ctx, U2, lam, tmp, t + 0.5 * dt);
   if (rc) return rc;
   CK(launch_axpby(l2, lam, 2.0 / 3.0, tmp, 2.0 / 3.0 * dt, n, ctx->stream), "axpby");
   CK(launch_axpby(ln, lam, 1.0 / 3.0, lam, 0.0, n, ctx->stream), "axpby");
   // stage 2: U2 = 3/4 U^n + 1/4 U1 + 1/4 dt R(U1)
-  rc = vjp_internal(ctx, U1, l2, tmp, t + dt);
+  rc = vjp_internal(ctx, U1, l2, tmp, t + dt, uq1, s1);
   if (rc) return rc;
   CK(launch_axpby(l1, l2, 0.25, tmp, 0.25 * dt, n, ctx->stream), "axpby");
   CK(launch_axpby(ln, ln, 1.0, l2, 0.75, n, ctx->stream), "axpby");
   // stage 1: U1 = U^n + dt R(U^n)
-  rc = vjp_internal(ctx, U, l1, tmp, t);
+  rc = vjp_internal(ctx, U, l1, tmp, t, uq0, s0);
   if (rc) return rc;
   CK(launch_axpby(ln, ln, 1.0, l1, 1.0, n, ctx->stream), "axpby");
   CK(launch_axpby(ln, ln, 1.0, tmp, dt, n, ctx->stream), "axpby");

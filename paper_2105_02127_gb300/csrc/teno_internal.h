@@ -99,7 +99,7 @@ cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const dou
 cudaError_t launch_recon_vjp(const DeviceMesh& dm, const uint8_t* sel, const double* Uq_bar,
                              double* d_bar, double* u_self, cudaStream_t st);
 cudaError_t launch_scatter_gather(const DeviceMesh& dm, const int64_t* rev_off,
-                                  const int64_t* rev_idx, const double* d_bar,
+                                  const int32_t* rev_idx, const double* d_bar,
                                   const double* u_self, double* v, cudaStream_t st);
 
 }  // namespace teno

@@ -57,98 +57,107 @@ __device__ __forceinline__ double tsqrt<double>(double x) { return sqrt(x); }
 template <>
 __device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
 
-// forward-mode dual number with N directions (flux Jacobians of the adjoint)
-template <int N>
+// scalar constants of every arithmetic type used by the flux templates
+template <typename T>
+struct Cst {
+  __device__ __forceinline__ static T from(double x) { return T(x); }
+};
+template <typename T>
+__device__ __forceinline__ T cst(double x) {
+  return Cst<T>::from(x);
+}
+
+// forward-mode dual number with N directions over scalar type S (flux
+// Jacobians of the adjoint)
+template <int N, typename S = double>
 struct Dual {
-  double v;
-  double d[N];
+  S v;
+  S d[N];
+};
+template <int N, typename S>
+struct Cst<Dual<N, S>> {
+  __device__ __forceinline__ static Dual<N, S> from(double x) {
+    Dual<N, S> r;
+    r.v = Cst<S>::from(x);
+#pragma unroll
+    for (int i = 0; i < N; ++i) r.d[i] = Cst<S>::from(0.0);
+    return r;
+  }
 };
 template <int N>
 __device__ __forceinline__ Dual<N> mk(double v) {
-  Dual<N> r;
-  r.v = v;
-#pragma unroll
-  for (int i = 0; i < N; ++i) r.d[i] = 0.0;
-  return r;
+  return Cst<Dual<N>>::from(v);
 }
-template <int N>
-__device__ __forceinline__ Dual<N> operator+(const Dual<N>& a, const Dual<N>& b) {
-  Dual<N> r;
+template <int N, typename S>
+__device__ __forceinline__ Dual<N, S> operator+(const Dual<N, S>& a, const Dual<N, S>& b) {
+  Dual<N, S> r;
   r.v = a.v + b.v;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
   return r;
 }
-template <int N>
-__device__ __forceinline__ Dual<N> operator-(const Dual<N>& a, const Dual<N>& b) {
-  Dual<N> r;
+template <int N, typename S>
+__device__ __forceinline__ Dual<N, S> operator-(const Dual<N, S>& a, const Dual<N, S>& b) {
+  Dual<N, S> r;
   r.v = a.v - b.v;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i];
   return r;
 }
-template <int N>
-__device__ __forceinline__ Dual<N> operator-(const Dual<N>& a) {
-  Dual<N> r;
+template <int N, typename S>
+__device__ __forceinline__ Dual<N, S> operator-(const Dual<N, S>& a) {
+  Dual<N, S> r;
   r.v = -a.v;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = -a.d[i];
   return r;
 }
-template <int N>
-__device__ __forceinline__ Dual<N> operator*(const Dual<N>& a, const Dual<N>& b) {
-  Dual<N> r;
+template <int N, typename S>
+__device__ __forceinline__ Dual<N, S> operator*(const Dual<N, S>& a, const Dual<N, S>& b) {
+  Dual<N, S> r;
   r.v = a.v * b.v;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
   return r;
 }
-template <int N>
-__device__ __forceinline__ Dual<N> operator*(double s, const Dual<N>& a) {
-  Dual<N> r;
-  r.v = s * a.v;
+template <int N, typename S>
+__device__ __forceinline__ Dual<N, S> operator*(double s, const Dual<N, S>& a) {
+  const S ss = Cst<S>::from(s);
+  Dual<N, S> r;
+  r.v = ss * a.v;
 #pragma unroll
-  for (int i = 0; i < N; ++i) r.d[i] = s * a.d[i];
+  for (int i = 0; i < N; ++i) r.d[i] = ss * a.d[i];
   return r;
 }
-template <int N>
-__device__ __forceinline__ Dual<N> operator/(const Dual<N>& a, const Dual<N>& b) {
-  Dual<N> r;
+template <int N, typename S>
+__device__ __forceinline__ Dual<N, S> operator/(const Dual<N, S>& a, const Dual<N, S>& b) {
+  Dual<N, S> r;
   r.v = a.v / b.v;
-  double ib = 1.0 / b.v;
+  const S ib = Cst<S>::from(1.0) / b.v;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
   return r;
 }
-template <int N>
-__device__ __forceinline__ Dual<N> tsqrt(const Dual<N>& a) {
-  Dual<N> r;
-  r.v = sqrt(a.v);
-  double h = 0.5 / r.v;
+template <int N, typename S>
+__device__ __forceinline__ Dual<N, S> tsqrt(const Dual<N, S>& a) {
+  Dual<N, S> r;
+  r.v = tsqrt(a.v);
+  const S h = Cst<S>::from(0.5) / r.v;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * h;
   return r;
 }
 __device__ __forceinline__ double val(double x) { return x; }
 __device__ __forceinline__ float val(float x) { return x; }
-template <int N>
-__device__ __forceinline__ double val(const Dual<N>& x) { return x.v; }
+template <int N, typename S>
+__device__ __forceinline__ auto val(const Dual<N, S>& x) { return val(x.v); }
 template <typename T>
 __device__ __forceinline__ T vmin(const T& a, const T& b) { return val(a) <= val(b) ? a : b; }
 template <typename T>
 __device__ __forceinline__ bool nonneg(const T& x) { return val(x) >= decltype(val(x))(0); }
 template <typename T>
 __device__ __forceinline__ T vmax(const T& a, const T& b) { return val(a) >= val(b) ? a : b; }
-template <typename T, typename S>
-__device__ __forceinline__ T cst(S x) { return T(x); }
-template <>
-__device__ __forceinline__ Dual<2> cst<Dual<2>, double>(double x) { return mk<2>(x); }
-template <>
-__device__ __forceinline__ Dual<8> cst<Dual<8>, double>(double x) { return mk<8>(x); }
-template <>
-__device__ __forceinline__ Dual<4> cst<Dual<4>, double>(double x) { return mk<4>(x); }
-template <>
-__device__ __forceinline__ Dual<1> cst<Dual<1>, double>(double x) { return mk<1>(x); }
+
 
 // ------------------------------------------- double-float (FP32 pair) path
 // Values are unevaluated sums hi + lo of two floats (|lo| <= ulp(hi)/2), about
@@ -211,10 +220,12 @@ __device__ __forceinline__ DF tsqrt(DF a) {
 }
 __device__ __forceinline__ float val(DF x) { return x.h; }
 template <>
-__device__ __forceinline__ DF cst<DF, double>(double x) {
-  const float h = (float)x;
-  return {h, (float)(x - (double)h)};
-}
+struct Cst<DF> {
+  __device__ __forceinline__ static DF from(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+  }
+};
 __device__ __forceinline__ DF vmin(const DF& a, const DF& b) {
   return (a.h < b.h || (a.h == b.h && a.l <= b.l)) ? a : b;
 }
@@ -228,6 +239,21 @@ __device__ __forceinline__ DF madd(DF a, DF b, DF c) { return a * b + c; }
 __device__ __forceinline__ double to_d(double x) { return x; }
 __device__ __forceinline__ double to_d(float x) { return (double)x; }
 __device__ __forceinline__ double to_d(DF x) { return (double)x.h + (double)x.l; }
+// a stored Gauss-point value as the flux scalar type
+template <typename S>
+__device__ __forceinline__ S lift(double x) { return Cst<S>::from(x); }
+template <typename S>
+__device__ __forceinline__ S lift(float x) { return Cst<S>::from((double)x); }
+template <typename S>
+__device__ __forceinline__ S lift(DF x) {
+  if constexpr (std::is_same<S, DF>::value)
+    return x;
+  else
+    return S(to_d(x));
+}
+// branch decisions on dual numbers over pairs compare the exact pair sums
+template <int N>
+__device__ __forceinline__ double val(const Dual<N, DF>& x) { return to_d(x.v); }
 
 // ---------------------------------------------------------------- fluxes
 // Euler flux through a face with unit normal n = (nx, ny): the state is
@@ -1306,16 +1332,17 @@ struct VjpArgs {
 
 // Uq_bar[(c,edge,q)] = w_q |A| (dF/dU_side)^T Kbar with Kbar = dJ/dK_f
 // (R_o has -K/|V_o|, R_n has +K/|V_n|); every Gauss slot of every cell is
-// written by exactly one face.
-template <int NV, int NQ, int FLUX, typename TQ>
+// written by exactly one face.  The Jacobian columns come from forward-mode
+// dual numbers over scalar S, ND seeded directions per pass: an interior face
+// seeds the NV components of U_L, then those of U_R (2 NV / ND passes); a
+// boundary face only U_L (the ghost state carries dU_R/dU_L).
+template <int NV, int NQ, int FLUX, typename TQ, typename S, int ND>
 __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
                                                             const TQ* __restrict__ Uq,
                                                             const double* __restrict__ w,
                                                             double* __restrict__ Uq_bar) {
-  // two forward-mode passes of NV directions each (left seeds, then right
-  // seeds): half the live derivative values of a single 2*NV pass
-  constexpr int ND = NV;
-  using D = Dual<ND>;
+  static_assert((2 * NV) % ND == 0, "directions per pass must divide 2 NV");
+  using D = Dual<ND, S>;
   const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= a.n_face) return;
   const int o = a.f_cells[2 * f], n = a.f_cells[2 * f + 1];
@@ -1327,30 +1354,36 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
     Kb[v] = -w[v * a.n_pad + o] * a.inv_area[o];
     if (n >= 0) Kb[v] += w[v * a.n_pad + n] * a.inv_area[n];
   }
+  const int n_pass = ((n >= 0 ? 2 * NV : NV) + ND - 1) / ND;
   for (int k = 0; k < NQ; ++k) {
-    double ul[NV], ur[NV];
+    TQ ul[NV], ur[NV];
     const TQ* pl = Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) ul[v] = to_d(pl[v]);
+    for (int v = 0; v < NV; ++v) ul[v] = pl[v];
     if (n >= 0) {
       const TQ* pr = Uq + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) ur[v] = to_d(pr[v]);
+      for (int v = 0; v < NV; ++v) ur[v] = pr[v];
     }
     const double wk = a.gw[k] * len;
     const double x = a.f_geom[5 * f + 3] - ny * len * a.gt[k];
-    for (int side = 0; side < (n >= 0 ? 2 : 1); ++side) {
+    double* outL = Uq_bar + ((int64_t)(o * 3 + eo) * NQ + k) * NV;
+    double* outR = n >= 0 ? Uq_bar + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV : outL;
+    for (int pass = 0; pass < n_pass; ++pass) {
+      const int dir0 = pass * ND;  // directions dir0 .. dir0+ND-1 of [U_L, U_R]
       D UL[NV], UR[NV], F[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        UL[v] = mk<ND>(ul[v]);
-        if (side == 0) UL[v].d[v] = 1.0;
+        UL[v] = cst<D>(0.0);
+        UL[v].v = lift<S>(ul[v]);
+        if (v >= dir0 && v < dir0 + ND) UL[v].d[v - dir0] = cst<S>(1.0);
       }
       if (n >= 0) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          UR[v] = mk<ND>(ur[v]);
-          if (side == 1) UR[v].d[v] = 1.0;
+          UR[v] = cst<D>(0.0);
+          UR[v].v = lift<S>(ur[v]);
+          if (NV + v >= dir0 && NV + v < dir0 + ND) UR[v].d[NV + v - dir0] = cst<S>(1.0);
         }
       } else if constexpr (NV == 4) {
         ghost_state<D>(en, UL, nx, ny, x, a.time, a.gamma, UR);  // carries dUR/dUL
@@ -1364,14 +1397,16 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
       } else {
         euler_riemann<D>(UL, UR, nx, ny, a.gamma, FLUX == TENO_FLUX_HLLC, F);
       }
-      double* out = side == 0 ? Uq_bar + ((int64_t)(o * 3 + eo) * NQ + k) * NV
-                              : Uq_bar + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV;
 #pragma unroll
-      for (int j = 0; j < NV; ++j) {
+      for (int j = 0; j < ND; ++j) {
         double sacc = 0.0;
 #pragma unroll
-        for (int i = 0; i < NV; ++i) sacc = fma(F[i].d[j], Kb[i], sacc);
-        out[j] = wk * sacc;
+        for (int i = 0; i < NV; ++i) sacc = fma(to_d(F[i].d[j]), Kb[i], sacc);
+        const int g = dir0 + j;
+        if (g < NV)
+          outL[g] = wk * sacc;
+        else if (n >= 0)
+          outR[g - NV] = wk * sacc;
       }
     }
   }
@@ -1401,7 +1436,7 @@ __global__ void __launch_bounds__(128) recon_vjp_kernel(const TS* __restrict__ a
     else
       return x;
   };
-  double* db = d_bar + tile * (int64_t)SL * NV * kTile + v * kTile + lane;
+  double* db = d_bar + tile * (int64_t)SL * NV * kTile + lane * NV + v;
   double cb[M];
 #pragma unroll
   for (int l = 0; l < M; ++l) cb[l] = 0.0;
@@ -1476,7 +1511,7 @@ __global__ void __launch_bounds__(128) recon_vjp_df_kernel(const float2* __restr
   constexpr int E = M * NS + kSmallEntries;
   constexpr int SL = NS + kSmallSlots;
   const float2* A = ahat + tile * (int64_t)E * kTile + lane;
-  DF* db = d_bar + tile * (int64_t)SL * NV * kTile + v * kTile + lane;
+  DF* db = d_bar + tile * (int64_t)SL * NV * kTile + lane * NV + v;
   DF cb[M];
 #pragma unroll
   for (int l = 0; l < M; ++l) cb[l] = {0.f, 0.f};
@@ -1525,24 +1560,37 @@ __global__ void __launch_bounds__(128) recon_vjp_df_kernel(const float2* __restr
   u_self[(int64_t)v * n_pad + c] = to_d(u0b - tot);
 }
 
-// v[j] = u_self[j] + sum over the stencil slots that hold cell j
+// v[j] = u_self[j] + sum over the stencil slots that hold cell j.  d_bar is
+// [tile][slot][lane][var]: the NV values of one slot entry are one 32-byte
+// sector (NV = 4), read with vector loads; rev_idx holds entry numbers
+// (tile * SL + slot) * 32 + lane.
 template <int NV, typename TD>
 __global__ void __launch_bounds__(256) scatter_gather_kernel(const int64_t* __restrict__ rev_off,
-                                                             const int64_t* __restrict__ rev_idx,
+                                                             const int32_t* __restrict__ rev_idx,
                                                              const TD* __restrict__ d_bar,
                                                              const double* __restrict__ u_self,
                                                              double* __restrict__ out,
                                                              int64_t n_cell, int64_t n_pad) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n_cell) return;
+  const int64_t r0 = rev_off[j], r1 = rev_off[j + 1];
   if constexpr (std::is_same<TD, DF>::value) {
     DF acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = d_to_df(u_self[v * n_pad + j]);
-    for (int64_t r = rev_off[j]; r < rev_off[j + 1]; ++r) {
-      const int64_t base = rev_idx[r];
+    for (int64_t r = r0; r < r1; ++r) {
+      const TD* e = d_bar + (int64_t)rev_idx[r] * NV;
+      if constexpr (NV == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(e));
+        const float4 b = __ldg(reinterpret_cast<const float4*>(e) + 1);
+        acc[0] = acc[0] + DF{a.x, a.y};
+        acc[1] = acc[1] + DF{a.z, a.w};
+        acc[2] = acc[2] + DF{b.x, b.y};
+        acc[3] = acc[3] + DF{b.z, b.w};
+      } else {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] = acc[v] + d_bar[base + v * kTile];
+        for (int v = 0; v < NV; ++v) acc[v] = acc[v] + e[v];
+      }
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) out[v * n_pad + j] = to_d(acc[v]);
@@ -1550,10 +1598,19 @@ __global__ void __launch_bounds__(256) scatter_gather_kernel(const int64_t* __re
     double acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = u_self[v * n_pad + j];
-    for (int64_t r = rev_off[j]; r < rev_off[j + 1]; ++r) {
-      const int64_t base = rev_idx[r];
+    for (int64_t r = r0; r < r1; ++r) {
+      const TD* e = d_bar + (int64_t)rev_idx[r] * NV;
+      if constexpr (NV == 4) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(e));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(e) + 1);
+        acc[0] += a.x;
+        acc[1] += a.y;
+        acc[2] += b.x;
+        acc[3] += b.y;
+      } else {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] += d_bar[base + v * kTile];
+        for (int v = 0; v < NV; ++v) acc[v] += e[v];
+      }
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) out[v * n_pad + j] = acc[v];
@@ -1620,7 +1677,11 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
     constexpr int M = decltype(Mc)::value, NS = decltype(NSc)::value;
     auto go = [&](auto nqc, auto nvc) -> cudaError_t {
       constexpr int NQ = decltype(nqc)::value, NV = decltype(nvc)::value;
-      if (dm.variant == 0 && dm.halo.off) {
+      // the TMA kernel covers Euler on the pair and mixed paths; variant 2
+      // elsewhere takes the halo kernel
+      const bool tma = NV == 4 && dm.variant == 2 && dm.err_flag && dm.halo.off &&
+                       dm.precision != TENO_FP64_NATIVE;
+      if ((dm.variant == 0 || (dm.variant == 2 && !tma)) && dm.halo.off) {
         constexpr int TZh = 4 / NV;
         dim3 block(kTile, NV, TZh);
         dim3 grid((unsigned)((tiles + TZh - 1) / TZh));
@@ -1633,7 +1694,7 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
         return cudaGetLastError();
       }
       if constexpr (NV == 4) {
-        if (dm.variant == 2 && dm.err_flag && dm.halo.off && dm.precision != TENO_FP64_NATIVE) {
+        if (tma) {
           if (dm.precision == TENO_FP64) return launch_recon_tma<M, NS, NQ, true>(a, dm, dm.err_flag, st);
           return launch_recon_tma<M, NS, NQ, false>(a, dm, dm.err_flag, st);
         }
@@ -1769,6 +1830,11 @@ cudaError_t launch_axpby(double* out, const double* a, double ca, const double* 
   return cudaGetLastError();
 }
 
+#ifndef TENO_VJP_DIRS
+#define TENO_VJP_DIRS 2
+#endif
+constexpr int kVjpDirs = TENO_VJP_DIRS;
+
 cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const double* w,
                                  double* Uq_bar, double time, cudaStream_t st) {
   VjpArgs a;
@@ -1791,7 +1857,16 @@ cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const dou
     constexpr int NV = decltype(nvc)::value, NQ = decltype(nqc)::value,
                   FL = decltype(flc)::value;
     using TQ = typename decltype(tqc)::type;
-    face_flux_vjp_kernel<NV, NQ, FL, TQ><<<grid, 128, 0, st>>>(a, (const TQ*)Uq, w, Uq_bar);
+    // pairs: FP32-pipe dual numbers, kVjpDirs directions per pass; FP64:
+    // all 2 NV directions of an interior face in one pass
+    if constexpr (std::is_same<TQ, DF>::value) {
+      constexpr int ND = NV < kVjpDirs ? NV : kVjpDirs;
+      face_flux_vjp_kernel<NV, NQ, FL, TQ, DF, ND><<<grid, 128, 0, st>>>(a, (const TQ*)Uq, w,
+                                                                        Uq_bar);
+    } else {
+      face_flux_vjp_kernel<NV, NQ, FL, TQ, double, 2 * NV><<<grid, 128, 0, st>>>(
+          a, (const TQ*)Uq, w, Uq_bar);
+    }
   };
   using I1 = std::integral_constant<int, 1>;
   using I2 = std::integral_constant<int, 2>;
@@ -1851,7 +1926,7 @@ cudaError_t launch_recon_vjp(const DeviceMesh& dm, const uint8_t* sel, const dou
 }
 
 cudaError_t launch_scatter_gather(const DeviceMesh& dm, const int64_t* rev_off,
-                                  const int64_t* rev_idx, const double* d_bar,
+                                  const int32_t* rev_idx, const double* d_bar,
                                   const double* u_self, double* v, cudaStream_t st) {
   const unsigned grid = (unsigned)((dm.n_cell + 255) / 256);
   const bool pairs = dm.precision == TENO_FP64;  // d_bar holds (hi, lo) pairs
