@@ -353,7 +353,10 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": workload_name(args, n_cell),
                        "n_cell": n_cell, "order": args.order,
-                       "l2": "inputs larger than L2 (per-cell matrices 1.3-2.5 GB)",
+                       "l2": "inputs larger than L2 (a reconstruction launch reads %.2f GB "
+                             "on the FP64 path, %.2f GB FP32-mixed)" % (
+                                 algorithmic_bytes(args.order, 4, "fp64") * n_cell / 1e9,
+                                 algorithmic_bytes(args.order, 4, "fp32_mixed") * n_cell / 1e9),
                        "parallelism": f"replicas x{world}"},
             "roofline": main["roofline"], "gpu_launches": int(sum(main["launches"])),
             "kernel_ms": main["kernel_ms"],

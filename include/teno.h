@@ -80,8 +80,14 @@ typedef struct teno_params {
                             per-cell matrices through a TMA bulk-copy ring while the
                             tile's stencil halo is double-buffered with cp.async (Euler,
                             TENO_FP64 and TENO_FP32_MIXED; else 0).  0 and 2 fall back to 1
-                            where a tile's halo exceeds 256 cells.  All variants give
-                            bitwise identical results. */
+                            where a tile's halo exceeds 256 cells.  Variants 0 and 1 give
+                            bitwise identical results; variant 2 on TENO_FP64 evaluates
+                            the large polynomial at the Gauss points through per-cell
+                            products Psi' G stored at precompute and takes the cutoff
+                            decision from FP32 coefficients with a rigorous error bound
+                            (falling back to pairs and FP64 where the bound does not
+                            separate chi from C_T): equal up to rounding; it keeps
+                            4.8 KB more per cell (TENO5) in device memory. */
   double ct;         /* cutoff C_T */
   double eps;        /* epsilon of the scale separation */
   double gamma;      /* ratio of specific heats */

@@ -67,7 +67,7 @@ struct teno_ctx {
   std::vector<int32_t> st_large, st_small;  // user ids, [nc][ns], [nc][36]
   // device data
   DeviceMesh dm;
-  DevBuf b_halo_off, b_halo_ids, b_halo_loc;
+  DevBuf b_halo_off, b_halo_ids, b_halo_loc, b_g32, b_wq;
   DevBuf b_ahat, b_nbr, b_smask, b_fcells, b_fedges, b_fgeom, b_cfaces, b_inv_area, b_cfl_len,
       b_perm;
   DevBuf b_U, b_U1, b_U2, b_R, b_tmp, b_Uq, b_K, b_sel, b_sel_ovr, b_maxlam, b_flag;
@@ -682,6 +682,14 @@ int run_precompute(teno_ctx* ctx) {
   const int store = p.precision;
   const size_t esz = store == TENO_FP32_MIXED ? sizeof(float) : 8;
   std::vector<unsigned char> ahat((size_t)ntile * E * kTile * esz, 0);
+  // Euler on the pair path with the TMA kernel: FP32 selection matrices with
+  // column sums of |G| (large slots M + 1 floats, directional slots 5 + 1) and
+  // W = Psi' G, the large polynomial's Gauss-point values per unit difference
+  const bool wform = store == TENO_FP64 && p.n_var == 4 && p.recon_variant == 2;
+  const int nq3 = 3 * ctx->nq;
+  const int E32 = ns * (m + 1) + kSmallK * kSmallN * (kSmallM + 1), EW = ns * nq3;
+  std::vector<float> g32(wform ? (size_t)ntile * E32 * kTile : 0, 0.f);
+  std::vector<float2> wq(wform ? (size_t)ntile * EW * kTile : 0, make_float2(0.f, 0.f));
   std::vector<int32_t> nbr((size_t)ntile * SL * kTile, 0);
   std::vector<uint8_t> smask(npad, 0);
   int rc = TENO_OK;
@@ -711,11 +719,31 @@ int run_precompute(teno_ctx* ctx) {
           reinterpret_cast<float*>(ahat.data())[pos] = (float)x;
         }
       };
+      // FP32 rows plus an upper bound of their absolute column sum
+      auto put32 = [&](int e0, const double* col, int stride, int rows) {
+        double cs = 0.0;
+        for (int l = 0; l < rows; ++l) {
+          const float x = (float)col[l * stride];
+          g32[((size_t)tile * E32 + e0 + l) * kTile + lane] = x;
+          cs += std::fabs((double)x);
+        }
+        g32[((size_t)tile * E32 + e0 + rows) * kTile + lane] = (float)(cs * (1.0 + 1e-6));
+      };
       if (!r) r = stencil_matrix(ctx, R, t, lg, ns, m, G.data());
       if (!r) {
         for (int s = 0; s < ns; ++s) {
           nbr[((size_t)tile * SL + s) * kTile + lane] = ctx->iperm[lg[s]];
           for (int l = 0; l < m; ++l) put(s * m + l, G[l * ns + s]);
+          if (wform) {
+            put32(s * (m + 1), &G[s], ns, m);
+            for (int q = 0; q < nq3; ++q) {
+              double w = 0.0;
+              for (int l = 0; l < m; ++l) w += R.psi_t[q * kMaxM + l] * G[l * ns + s];
+              const float hi = (float)w;
+              wq[((size_t)tile * EW + s * nq3 + q) * kTile + lane] =
+                  make_float2(hi, (float)(w - (double)hi));
+            }
+          }
         }
         uint8_t mask = 0;
         for (int j = 0; j < kSmallK && !r; ++j) {
@@ -735,6 +763,8 @@ int run_precompute(teno_ctx* ctx) {
             nbr[((size_t)tile * SL + slot0 + s) * kTile + lane] = ctx->iperm[ids[s]];
             for (int l = 0; l < kSmallM; ++l)
               put(m * ns + (j * kSmallN + s) * kSmallM + l, G[l * kSmallN + s]);
+            if (wform)
+              put32(ns * (m + 1) + (j * kSmallN + s) * (kSmallM + 1), &G[s], kSmallN, kSmallM);
           }
         }
         smask[c] = mask;
@@ -810,6 +840,8 @@ int run_precompute(teno_ctx* ctx) {
   if (!e && halo_ok) e = upload(ctx, ctx->b_halo_ids, hids.data(), hids.size() * 4);
   if (!e && halo_ok) e = upload(ctx, ctx->b_halo_loc, hloc.data(), hloc.size() * 2);
   if (!e) e = upload(ctx, ctx->b_smask, smask.data(), smask.size());
+  if (!e && wform) e = upload(ctx, ctx->b_g32, g32.data(), g32.size() * sizeof(float));
+  if (!e && wform) e = upload(ctx, ctx->b_wq, wq.data(), wq.size() * sizeof(float2));
   if (e) return e;
   // device mesh descriptor
   DeviceMesh& dm = ctx->dm;
@@ -837,6 +869,8 @@ int run_precompute(teno_ctx* ctx) {
   }
   dm.err_flag = (int*)ctx->b_flag.p;
   dm.ahat = ctx->b_ahat.p;
+  dm.g32 = wform ? (const float*)ctx->b_g32.p : nullptr;
+  dm.wq = wform ? (const float2*)ctx->b_wq.p : nullptr;
   dm.nbr = (const int32_t*)ctx->b_nbr.p;
   dm.smask = (const uint8_t*)ctx->b_smask.p;
   std::copy(R.psi_t, R.psi_t + kMaxPts * kMaxM, dm.eval.psi);
@@ -1128,7 +1162,7 @@ int teno_destroy(teno_ctx* ctx) {
   }
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  DevBuf* bufs[] = {&ctx->b_halo_off, &ctx->b_halo_ids, &ctx->b_halo_loc, &ctx->b_ahat, &ctx->b_nbr, &ctx->b_smask, &ctx->b_fcells, &ctx->b_fedges,
+  DevBuf* bufs[] = {&ctx->b_halo_off, &ctx->b_halo_ids, &ctx->b_halo_loc, &ctx->b_g32, &ctx->b_wq, &ctx->b_ahat, &ctx->b_nbr, &ctx->b_smask, &ctx->b_fcells, &ctx->b_fedges,
                     &ctx->b_fgeom, &ctx->b_cfaces, &ctx->b_inv_area, &ctx->b_cfl_len,
                     &ctx->b_perm, &ctx->b_U, &ctx->b_U1, &ctx->b_U2, &ctx->b_R, &ctx->b_tmp,
                     &ctx->b_Uq, &ctx->b_K, &ctx->b_sel, &ctx->b_sel_ovr, &ctx->b_maxlam,

@@ -259,12 +259,32 @@ __device__ __forceinline__ double val(const Dual<N, DF>& x) { return to_d(x.v); 
 // Euler flux through a face with unit normal n = (nx, ny): the state is
 // expressed in the face frame (normal, tangential velocity), the 1D flux
 // F^x is evaluated there and rotated back (Sec. 4.1, F^n = T^-1 F^x(T U)).
+// constants of one face in the flux scalar type, converted once per face
 template <typename T>
-__device__ __forceinline__ void euler_riemann(const T* UL, const T* UR, double nx, double ny,
-                                              double g, int hllc, T* F) {
-  const T one = cst<T>(1.0), half = cst<T>(0.5), zero = cst<T>(0.0);
-  const T gm1 = cst<T>(g - 1.0), gg = cst<T>(g);
-  const T tnx = cst<T>(nx), tny = cst<T>(ny);
+struct RiemannK {
+  T one, half, gm1, gg, tnx, tny;
+};
+template <typename T>
+__device__ __forceinline__ RiemannK<T> riemann_k(double nx, double ny, double g) {
+  return {cst<T>(1.0), cst<T>(0.5), cst<T>(g - 1.0), cst<T>(g), cst<T>(nx), cst<T>(ny)};
+}
+// the same constants as dual numbers (zero derivatives; no conversion)
+template <int N, typename S>
+__device__ __forceinline__ RiemannK<Dual<N, S>> riemann_k_dual(const RiemannK<S>& k) {
+  auto c = [](S x) {
+    Dual<N, S> r = cst<Dual<N, S>>(0.0);
+    r.v = x;
+    return r;
+  };
+  return {c(k.one), c(k.half), c(k.gm1), c(k.gg), c(k.tnx), c(k.tny)};
+}
+
+template <typename T>
+__device__ __forceinline__ void euler_riemann(const T* UL, const T* UR, const RiemannK<T>& K,
+                                              int hllc, T* F) {
+  const T one = K.one, half = K.half;
+  const T gm1 = K.gm1, gg = K.gg;
+  const T tnx = K.tnx, tny = K.tny;
   // left / right primitive variables in the face frame (one reciprocal per
   // density; every division below is by one of four reciprocals)
   T rL = UL[0], rR = UR[0];
@@ -318,7 +338,6 @@ __device__ __forceinline__ void euler_riemann(const T* UL, const T* UR, double n
 #pragma unroll
     for (int k = 0; k < 4; ++k) Fx[k] = (left ? FL[k] : FR[k]) + S * (Us[k] - (left ? WL[k] : WR[k]));
   }
-  (void)zero;
   F[0] = Fx[0];
   F[1] = Fx[1] * tnx - Fx[2] * tny;
   F[2] = Fx[1] * tny + Fx[2] * tnx;
@@ -394,7 +413,8 @@ __device__ __forceinline__ uint8_t select_fp64(const double* beta, int present, 
 // 1e-3 C_T of C_T.  The FP32 betas are within 1.3e-6 (relative) of the FP64
 // sums of the same squares, which moves chi by less than 3e-5 relative, so a
 // decision outside the band equals the FP64 decision.
-__device__ __forceinline__ bool chi_keep32(const float* t, int k, int mask, float ct, bool* near) {
+__device__ __forceinline__ bool chi_keep32(const float* t, int k, int mask, float ct, bool* near,
+                                           float band = 1e-3f) {
   float s = 0.f;
 #pragma unroll
   for (int j = 0; j <= kSmallK; ++j) {
@@ -404,7 +424,7 @@ __device__ __forceinline__ bool chi_keep32(const float* t, int k, int mask, floa
     s += r2 * r2 * r2;
   }
   float chi = 1.f / s;
-  if (fabsf(chi - ct) <= 1e-3f * ct) *near = true;
+  if (!(fabsf(chi - ct) > band * ct)) *near = true;
   return chi >= ct;
 }
 
@@ -852,9 +872,12 @@ __global__ void __launch_bounds__(128) recon_halo_kernel(const ReconArgs a, cons
 // completion counted in bytes on the buffer's "full" mbarrier); the four
 // consumer warps of the tile (one per conservative variable) wait on "full",
 // accumulate from shared memory, and release the buffer on its "empty"
-// mbarrier.  Every wait is bounded: a wait that gives up sets bit 1 of the
-// error flag and the thread returns (the producer first waits, bounded, for
-// the copies it has in flight).
+// mbarrier.  Every wait is bounded.  A wait that gives up sets bit 1 of the
+// error flag and the block's abort flag in shared memory; from then on the
+// consumers skip every wait and all work but still pass the consumer-only
+// barriers of the remaining tiles (so no warp is left at a barrier), and the
+// producer stops issuing, waits (bounded) for the copies it has in flight and
+// returns.
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -890,6 +913,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   for (uint32_t i = 0; i < kWaitLimit; ++i)
     if (mbar_test(bar, parity)) return true;
   return false;
+}
+// as mbar_wait, also watching the block's abort flag: 1 phase complete, 0 gave
+// up, 2 another thread of the block gave up first
+__device__ __forceinline__ int mbar_wait_or_abort(uint64_t* bar, uint32_t parity,
+                                                  const volatile int* abort) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    if (mbar_test(bar, parity)) return 1;
+    if (*abort) return 2;
+  }
+  return 0;
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
                                          uint64_t* bar) {
@@ -930,11 +963,17 @@ struct StagePlan {
   static constexpr int kPerSmall = kSmallN / kSPS;
   static constexpr int kStages = kNL + kSmallK * kPerSmall;
   static constexpr int kMatL = kLPS * kSlotL, kMatS = kSPS * kSlotS;
-  static constexpr int kMat = kMatL > kMatS ? kMatL : kMatS;
+  static constexpr int kMaxSlots = kLPS > kSPS ? kLPS : kSPS;
+  static constexpr int kSlotN = kTile * 2;  // halo positions (uint16) of one slot
+  // ring buffer: [matrix rows][halo positions]
+  static constexpr int kNOff = kMatL > kMatS ? kMatL : kMatS;
+  static constexpr int kMat = kNOff + kMaxSlots * kSlotN;
+  static constexpr int kSL = NS + kSmallSlots;
   static constexpr int kE = M * NS + kSmallEntries;
   static constexpr int64_t kTileBytes = (int64_t)kE * kTile * kEsz;
   static constexpr size_t kHaloBytes = (size_t)2 * 4 * kHaloMax * sizeof(float2);
-  static constexpr size_t kSmem = (size_t)kRing * kMat + kHaloBytes + 2 * kRing * sizeof(uint64_t);
+  static constexpr size_t kSmem =
+      (size_t)kRing * kMat + kHaloBytes + 2 * kRing * sizeof(uint64_t) + 16;
   static_assert(kSmallN % kSPS == 0, "directional stencil split");
   static_assert(kMat % 16 == 0, "16-byte aligned buffers");
   __device__ static void stage(int j, int& slot0, int& nslot, int64_t& off, int& bytes, int& k) {
@@ -986,9 +1025,11 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
   float2* halo = reinterpret_cast<float2*>(smem + (size_t)kRing * P::kMat);  // [2][NV][kHaloMax]
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kRing * P::kMat + P::kHaloBytes);
   uint64_t* empty = full + kRing;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kRing);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n_tiles = (a.n_cell + kTile - 1) / kTile;
   if (threadIdx.x == 0) {
+    *abort_flag = 0;
     for (int i = 0; i < kRing; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], kConsumers);
@@ -1003,19 +1044,30 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
       for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const unsigned char* src =
             reinterpret_cast<const unsigned char*>(a.ahat) + tile * P::kTileBytes;
+        const unsigned char* sn =
+            reinterpret_cast<const unsigned char*>(h.nbr_loc) + tile * (int64_t)P::kSL * P::kSlotN;
         for (int j = 0; j < P::kStages; ++j, ++g) {
           const int b = (int)(g % kRing);
-          if (g >= kRing && !mbar_wait(&empty[b], (uint32_t)((g / kRing) - 1) & 1)) {
-            atomicOr(err, 2);
-            for (int64_t i = g - kRing; i < g; ++i)
-              mbar_wait(&full[i % kRing], (uint32_t)(i / kRing) & 1);
-            return;
+          if (g >= kRing) {
+            const int w = mbar_wait_or_abort(&empty[b], (uint32_t)((g / kRing) - 1) & 1, abort_flag);
+            if (w != 1) {
+              if (w == 0) {
+                atomicOr(err, 2);
+                *abort_flag = 1;
+              }
+              for (int64_t i = g - kRing; i < g; ++i)
+                mbar_wait(&full[i % kRing], (uint32_t)(i / kRing) & 1);
+              return;
+            }
           }
           int slot0, nslot, bytes, k;
           int64_t off;
           P::stage(j, slot0, nslot, off, bytes, k);
-          mbar_expect_tx(&full[b], (uint32_t)bytes);
-          bulk_g2s(smem + (size_t)b * P::kMat, src + off, (uint32_t)bytes, &full[b]);
+          const uint32_t bn = (uint32_t)(nslot * P::kSlotN);
+          unsigned char* dst = smem + (size_t)b * P::kMat;
+          mbar_expect_tx(&full[b], (uint32_t)bytes + bn);
+          bulk_g2s(dst, src + off, (uint32_t)bytes, &full[b]);
+          bulk_g2s(dst + P::kNOff, sn + slot0 * P::kSlotN, bn, &full[b]);
         }
       }
     }
@@ -1042,6 +1094,7 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
   };
   int64_t g = 0;
   int hb = 0;
+  bool dead = false;  // a bounded wait of this block gave up: skip all work
   if ((int64_t)blockIdx.x < n_tiles) prefetch(blockIdx.x, 0);
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, hb ^= 1) {
     consumer_sync();  // every consumer is done with the other halo buffer
@@ -1079,21 +1132,23 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
       int slot0, nslot, bytes, k;
       int64_t off;
       P::stage(j, slot0, nslot, off, bytes, k);
-      constexpr int kMaxSlots = TR::kLPS > TR::kSPS ? TR::kLPS : TR::kSPS;
-      int loc[kMaxSlots];
-#pragma unroll
-      for (int s = 0; s < kMaxSlots; ++s) loc[s] = s < nslot ? __ldg(nb + (slot0 + s) * kTile) : 0;
-      if (!mbar_wait(&full[b], (uint32_t)(g / kRing) & 1)) {
-        atomicOr(err, 2);
-        cp_async_wait<0>();
-        return;
+      if (!dead) {
+        const int w = mbar_wait_or_abort(&full[b], (uint32_t)(g / kRing) & 1, abort_flag);
+        if (w == 0) {
+          atomicOr(err, 2);
+          *abort_flag = 1;
+        }
+        dead = __any_sync(0xffffffffu, w != 1);
       }
       const TE* mat = reinterpret_cast<const TE*>(smem + (size_t)b * P::kMat) + lane;
-      if (k < 0) {
+      const uint16_t* nl = reinterpret_cast<const uint16_t*>(smem + (size_t)b * P::kMat + P::kNOff) + lane;
+      if (dead) {
+        // skip the stage
+      } else if (k < 0) {
 #pragma unroll
         for (int s = 0; s < TR::kLPS; ++s) {
           if (s < nslot) {
-            const Acc d = dif(loc[s]);
+            const Acc d = dif(nl[s * kTile]);
 #pragma unroll
             for (int l = 0; l < M; ++l) mac(acc[l], mat[(s * M + l) * kTile], d);
           }
@@ -1104,16 +1159,16 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
           if (kk != k) continue;
 #pragma unroll
           for (int s = 0; s < TR::kSPS; ++s) {
-            const Acc d = dif(loc[s]);
+            const Acc d = dif(nl[s * kTile]);
 #pragma unroll
             for (int l = 0; l < kSmallM; ++l) mac(as[kk][l], mat[(s * kSmallM + l) * kTile], d);
           }
         }
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[b]);
+      if (lane == 0 && !dead) mbar_arrive(&empty[b]);
     }
-    if (c < a.n_cell) {
+    if (!dead && c < a.n_cell) {
       if constexpr (kDF) {
 #pragma unroll
         for (int l = 0; l < M; ++l) acc[l] = df_norm(acc[l]);
@@ -1126,6 +1181,388 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
         plain_finish<M, NQ, NV, float, DFTable>(a, ev, c, v, 0.0, u0s, acc, as);
       }
     }
+  }
+  cp_async_wait<0>();
+}
+
+// ------------------------------------------- FP64 path, W form (variant 2)
+// Algebraically the same reconstruction as recon_tma_kernel<kDF = true>, with
+// the work split by what each quantity needs:
+//  - the Gauss-point values of the large polynomial, U_0 + Psi' (G d), are
+//    accumulated in pairs as U_0 + W d with W = Psi' G precomputed per cell
+//    (3 N_q pair products per stencil slot instead of m);
+//  - the smoothness indicators feed only the cutoff decision, so the stencil
+//    coefficients for beta are FP32 products G d with a rigorous error bound
+//    (per slot the column sum sum_l |G_ls| is stored next to the rows);
+//    where the bound does not separate chi from C_T the coefficients and
+//    beta are recomputed in pairs from the (hi, lo) matrices and the
+//    decision is taken in FP64;
+//  - directional-stencil values (cells where the large stencil is cut) are
+//    evaluated in pairs from the (hi, lo) matrices.
+#ifndef TENO_W_BLOCKS
+#define TENO_W_BLOCKS 3  // 3: three blocks per SM; 0: four where the ring fits
+#endif
+constexpr int kWBlocks = TENO_W_BLOCKS;
+
+template <int M, int NS, int NQ3, int kLPS, int kSPS>
+struct WPlan {
+  static constexpr int kG = M + 1, kGs = kSmallM + 1;
+  static constexpr int kSlotG = kG * kTile * 4, kSlotW = NQ3 * kTile * 8;
+  static constexpr int kSlotS = kGs * kTile * 4;
+  static constexpr int kSlotN = kTile * 2;  // halo positions (uint16) of one slot
+  static constexpr int kNL = (NS + kLPS - 1) / kLPS;
+  static constexpr int kPerSmall = kSmallN / kSPS;
+  static constexpr int kStages = kNL + kSmallK * kPerSmall;
+  static constexpr int kMaxSlots = kLPS > kSPS ? kLPS : kSPS;
+  // ring buffer: [FP32 rows][W pairs][halo positions]
+  static constexpr int kGReg = kLPS * kSlotG > kSPS * kSlotS ? kLPS * kSlotG : kSPS * kSlotS;
+  static constexpr int kWOff = kGReg, kNOff = kGReg + kLPS * kSlotW;
+  static constexpr int kMat = kNOff + kMaxSlots * kSlotN;
+  static constexpr int kE32 = NS * kG + kSmallK * kSmallN * kGs;  // floats per lane per tile
+  static constexpr int kEW = NS * NQ3;                            // pairs per lane per tile
+  static constexpr int kSL = NS + kSmallSlots;
+  static constexpr size_t kHaloBytes = (size_t)2 * 4 * kHaloMax * sizeof(float2);
+  static constexpr size_t kFixed = kHaloBytes + 2 * 4 * 8 + 16;
+  // blocks of 160 threads per SM (228 KB of shared memory, 1 KB reserved per
+  // block): four with a 3-deep ring where that fits, else three (4-deep
+  // ring if it fits)
+  static constexpr bool kFour = kWBlocks != 3 &&
+                                4 * ((size_t)3 * kMat + kFixed + 1024) <= (size_t)228 * 1024;
+  static constexpr int kRingW =
+      kFour ? 3 : (3 * ((size_t)4 * kMat + kFixed + 1024) <= (size_t)228 * 1024 ? 4 : 3);
+  static constexpr int kBlocks = kFour ? 4 : 3;
+  static constexpr size_t kSmem = (size_t)kRingW * kMat + kHaloBytes + 2 * kRingW * 8 + 16;
+  static_assert(kSmallN % kSPS == 0, "directional stencil split");
+  static_assert(kSlotG % 16 == 0 && kSlotW % 16 == 0 && kSlotS % 16 == 0 && kMat % 16 == 0,
+                "bulk-copy sizes");
+  // stage j: slots [slot0, slot0 + nslot) of stencil k (-1: large); byte
+  // offsets / sizes of its FP32 block (og, bg) and W block (ow, bw) in the tile
+  __device__ static void stage(int j, int& slot0, int& nslot, int& k, int& og, int& bg, int& ow,
+                               int& bw) {
+    if (j < kNL) {
+      slot0 = j * kLPS;
+      nslot = (NS - slot0) < kLPS ? (NS - slot0) : kLPS;
+      k = -1;
+      og = slot0 * kSlotG;
+      bg = nslot * kSlotG;
+      ow = slot0 * kSlotW;
+      bw = nslot * kSlotW;
+    } else {
+      const int i = j - kNL;
+      k = i / kPerSmall;
+      const int s0 = (i % kPerSmall) * kSPS;
+      slot0 = NS + k * kSmallN + s0;
+      nslot = kSPS;
+      og = NS * kSlotG + (k * kSmallN + s0) * kSlotS;
+      bg = kSPS * kSlotS;
+      ow = 0;
+      bw = 0;
+    }
+  }
+};
+
+// Upper bound of |beta_fp32 - beta| relative to beta_fp32 + eps for m FP32
+// coefficients from n-term FP32 dot products whose absolute error is at most
+// (n + 6) u e_abs each (e_abs = sum_s colsum_s |d_s|, u = 2^-24), including
+// the rounding of the FP32 sum of squares.  Returns a value >= 1 when the
+// bound is not informative.
+__device__ __forceinline__ float beta_rel_bound(float beta32, float e_abs, int n, int m,
+                                                float eps) {
+  const float u = 5.9604645e-8f;
+  const float em = (float)(n + 6) * u * e_abs * 1.0001f;
+  const float eb = (float)(m + 2) * u * beta32 + em * (2.f * sqrtf((float)m * beta32) + (float)m * em);
+  const float t = beta32 + eps;
+  if (!(eb < 0.5f * t)) return 1.f;
+  return eb / (t - eb);
+}
+
+template <int M, int NS, int NQ>
+__global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ, 3, 4>::kBlocks))
+    recon_tma_w_kernel(const ReconArgs a, const HaloArgs h, const DFTable ev,
+                       const float* __restrict__ g32, const float2* __restrict__ wq, int* err) {
+  constexpr int NQ3 = 3 * NQ;
+  using P = WPlan<M, NS, NQ3, 3, 4>;
+  constexpr int kR = P::kRingW;
+  constexpr int NV = 4;
+  constexpr int SL = NS + kSmallSlots;
+  constexpr int E = M * NS + kSmallEntries;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float2* halo = reinterpret_cast<float2*>(smem + (size_t)kR * P::kMat);  // [2][NV][kHaloMax]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kR * P::kMat + P::kHaloBytes);
+  uint64_t* empty = full + kR;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kR);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n_tiles = (a.n_cell + kTile - 1) / kTile;
+  if (threadIdx.x == 0) {
+    *abort_flag = 0;
+    for (int i = 0; i < kR; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kConsumers);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (warp == kConsumers) {
+    // ---- producer lane: FP32 and W blocks of every tile
+    if (lane == 0) {
+      int64_t g = 0;
+      for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const unsigned char* sg =
+            reinterpret_cast<const unsigned char*>(g32) + tile * (int64_t)P::kE32 * kTile * 4;
+        const unsigned char* sw =
+            reinterpret_cast<const unsigned char*>(wq) + tile * (int64_t)P::kEW * kTile * 8;
+        const unsigned char* sn =
+            reinterpret_cast<const unsigned char*>(h.nbr_loc) + tile * (int64_t)P::kSL * P::kSlotN;
+        for (int j = 0; j < P::kStages; ++j, ++g) {
+          const int b = (int)(g % kR);
+          if (g >= kR) {
+            const int w = mbar_wait_or_abort(&empty[b], (uint32_t)((g / kR) - 1) & 1, abort_flag);
+            if (w != 1) {
+              if (w == 0) {
+                atomicOr(err, 2);
+                *abort_flag = 1;
+              }
+              for (int64_t i = g - kR; i < g; ++i) mbar_wait(&full[i % kR], (uint32_t)(i / kR) & 1);
+              return;
+            }
+          }
+          int slot0, nslot, k, og, bg, ow, bw;
+          P::stage(j, slot0, nslot, k, og, bg, ow, bw);
+          unsigned char* dst = smem + (size_t)b * P::kMat;
+          const uint32_t bn = (uint32_t)(nslot * P::kSlotN);
+          mbar_expect_tx(&full[b], (uint32_t)(bg + bw) + bn);
+          bulk_g2s(dst, sg + og, (uint32_t)bg, &full[b]);
+          if (bw) bulk_g2s(dst + P::kWOff, sw + ow, (uint32_t)bw, &full[b]);
+          bulk_g2s(dst + P::kNOff, sn + slot0 * P::kSlotN, bn, &full[b]);
+        }
+      }
+    }
+    return;
+  }
+  // ---- consumers
+  const int v = warp, tid = threadIdx.x;
+  auto prefetch = [&](int64_t tile, int hb) {
+    const int h0 = h.off[tile], H = h.off[tile + 1] - h0;
+    for (int i = tid; i < H; i += kConsumers * kTile) {
+      const int id = __ldg(h.ids + h0 + i);
+#pragma unroll
+      for (int w = 0; w < NV; ++w)
+        cp_async8(&halo[(hb * NV + w) * kHaloMax + i], a.Us + (int64_t)w * a.n_pad + id);
+    }
+    cp_async_commit();
+  };
+  int64_t g = 0;
+  int hb = 0;
+  bool dead = false;  // a bounded wait of this block gave up: skip all work
+  if ((int64_t)blockIdx.x < n_tiles) prefetch(blockIdx.x, 0);
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, hb ^= 1) {
+    consumer_sync();  // every consumer is done with the other halo buffer
+    const int64_t nxt = tile + gridDim.x;
+    if (nxt < n_tiles)
+      prefetch(nxt, hb ^ 1);
+    else
+      cp_async_commit();
+    cp_async_wait<1>();
+    consumer_sync();
+    const float2* st = halo + (hb * NV + v) * kHaloMax;
+    const uint16_t* nb = h.nbr_loc + tile * (int64_t)SL * kTile + lane;
+    const int64_t c = tile * kTile + lane;  // may be a pad lane of the last tile
+    const float2 u0s = a.Us[(int64_t)v * a.n_pad + (c < a.n_cell ? c : 0)];
+    auto dif = [&](int idx) -> DF {  // d_s = U_s - U_0 in pairs
+      const float2 q = st[idx];
+      DF t = two_sum(q.x, -u0s.x);
+      t.l += q.y - u0s.y;
+      return two_sum(t.h, t.l);
+    };
+    float a32[M], s32[kSmallK][kSmallM], eL = 0.f, eS[kSmallK];
+    DF uq[NQ3];
+#pragma unroll
+    for (int l = 0; l < M; ++l) a32[l] = 0.f;
+#pragma unroll
+    for (int k = 0; k < kSmallK; ++k) {
+      eS[k] = 0.f;
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) s32[k][l] = 0.f;
+    }
+#pragma unroll
+    for (int p = 0; p < NQ3; ++p) uq[p] = DF{0.f, 0.f};
+    // selection and Gauss-point values of cell c (after all stages of its tile)
+    auto finish_cell = [&](int64_t tile, int64_t c) {
+      const int present = a.smask[c];
+      const float2* A = reinterpret_cast<const float2*>(a.ahat) + tile * (int64_t)E * kTile + lane;
+      DF as[kSmallK][kSmallM];
+      bool have_small = false;
+      // directional coefficients in pairs for the stencils in kmask
+      auto small_df = [&](int kmask) {
+#pragma unroll
+        for (int k = 0; k < kSmallK; ++k) {
+#pragma unroll
+          for (int l = 0; l < kSmallM; ++l) as[k][l] = DF{0.f, 0.f};
+          if (!((kmask >> k) & 1)) continue;
+          for (int s = 0; s < kSmallN; ++s) {
+            const DF d = dif(__ldg(nb + (NS + k * kSmallN + s) * kTile));
+            const float2* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
+#pragma unroll
+            for (int l = 0; l < kSmallM; ++l) df_mac(as[k][l], __ldg(As + l * kTile), d);
+          }
+#pragma unroll
+          for (int l = 0; l < kSmallM; ++l) as[k][l] = df_norm(as[k][l]);
+        }
+        have_small = true;
+      };
+      uint8_t sel;
+      if (a.sel_in) {
+        sel = a.sel_in[(int64_t)v * a.n_pad + c];
+      } else if (a.linear) {
+        sel = 8;
+      } else {
+        float t[kSmallK + 1];
+        float rho = 0.f;
+        {
+          float bsum = 0.f;
+#pragma unroll
+          for (int l = 0; l < M; ++l) bsum = fmaf(a32[l], a32[l], bsum);
+          t[kSmallK] = bsum + (float)a.eps;
+          rho = beta_rel_bound(bsum, eL, NS, M, (float)a.eps);
+#pragma unroll
+          for (int k = 0; k < kSmallK; ++k) {
+            float q = 0.f;
+#pragma unroll
+            for (int l = 0; l < kSmallM; ++l) q = fmaf(s32[k][l], s32[k][l], q);
+            t[k] = q + (float)a.eps;
+            if ((present >> k) & 1)
+              rho = fmaxf(rho, beta_rel_bound(q, eS[k], kSmallN, kSmallM, (float)a.eps));
+          }
+        }
+        // chi moves by at most ~12 rho (relative) under the beta bounds
+        bool near = !(rho < 1e-2f);
+        const float band = fmaxf(1e-3f, 15.f * rho);
+        const float ct = (float)a.ct;
+        if (chi_keep32(t, kSmallK, present | 8, ct, &near, band)) {
+          sel = 8;
+        } else {
+          sel = 0;
+#pragma unroll
+          for (int k = 0; k < kSmallK; ++k)
+            if (((present >> k) & 1) && chi_keep32(t, k, present & 7, ct, &near, band))
+              sel |= (uint8_t)(1u << k);
+        }
+        if (near) {
+          // coefficients and beta in pairs, decision in FP64
+          DF al[M];
+#pragma unroll
+          for (int l = 0; l < M; ++l) al[l] = DF{0.f, 0.f};
+          for (int s = 0; s < NS; ++s) {
+            const DF d = dif(__ldg(nb + s * kTile));
+#pragma unroll
+            for (int l = 0; l < M; ++l) df_mac(al[l], __ldg(A + (int64_t)(s * M + l) * kTile), d);
+          }
+          DF bl = {0.f, 0.f};
+#pragma unroll
+          for (int l = 0; l < M; ++l) {
+            const DF x = df_norm(al[l]);
+            df_mac(bl, make_float2(x.h, x.l), x);
+          }
+          small_df(present & 7);
+          double beta[kSmallK + 1];
+          beta[kSmallK] = df_to_double(df_norm(bl));
+#pragma unroll
+          for (int k = 0; k < kSmallK; ++k) {
+            DF q = {0.f, 0.f};
+#pragma unroll
+            for (int l = 0; l < kSmallM; ++l) df_mac(q, make_float2(as[k][l].h, as[k][l].l), as[k][l]);
+            beta[k] = df_to_double(df_norm(q));
+          }
+          sel = select_fp64(beta, present, a.ct, a.eps);
+        }
+      }
+      if (a.sel_out) a.sel_out[(int64_t)v * a.n_pad + c] = sel;
+      // ---- Gauss-point values as (hi, lo) pairs
+      DF* __restrict__ out = reinterpret_cast<DF*>(a.Uq) + c * (NQ3 * NV) + v;
+      const DF u0 = {u0s.x, u0s.y};
+      if (sel & 8) {
+#pragma unroll
+        for (int p = 0; p < NQ3; ++p) out[p * NV] = u0 + df_norm(uq[p]);
+      } else {
+        if (!have_small) small_df(sel & 7);
+        // equal weights: sum the kept polynomials, then divide by their number
+        const int nd = (sel & 1) + ((sel >> 1) & 1) + ((sel >> 2) & 1);
+        const float fn = (float)(nd ? nd : 1);
+        DF cf[kSmallM];
+#pragma unroll
+        for (int l = 0; l < kSmallM; ++l) {
+          DF sum = {0.f, 0.f};
+#pragma unroll
+          for (int k = 0; k < kSmallK; ++k) {
+            if (!((sel >> k) & 1)) continue;
+            DF q = two_sum(sum.h, as[k][l].h);
+            q.l += sum.l + as[k][l].l;
+            sum = two_sum(q.h, q.l);
+          }
+          const float qh = sum.h / fn;
+          const float r = fmaf(-qh, fn, sum.h);  // exact remainder
+          cf[l] = two_sum(qh, (r + sum.l) / fn);
+          if (!nd) cf[l] = DF{0.f, 0.f};
+        }
+#pragma unroll
+        for (int p = 0; p < NQ3; ++p) {
+          DF sp = {0.f, 0.f};
+#pragma unroll
+          for (int l = 0; l < kSmallM; ++l) df_mac(sp, ev.psi[p * kMaxM + l], cf[l]);
+          out[p * NV] = u0 + df_norm(sp);
+        }
+      }
+    };
+    for (int j = 0; j < P::kStages; ++j, ++g) {
+      const int b = (int)(g % kR);
+      int slot0, nslot, k, og, bg, ow, bw;
+      P::stage(j, slot0, nslot, k, og, bg, ow, bw);
+      if (!dead) {
+        const int w = mbar_wait_or_abort(&full[b], (uint32_t)(g / kR) & 1, abort_flag);
+        if (w == 0) {
+          atomicOr(err, 2);
+          *abort_flag = 1;
+        }
+        dead = __any_sync(0xffffffffu, w != 1);
+      }
+      const unsigned char* buf = smem + (size_t)b * P::kMat;
+      const uint16_t* nl = reinterpret_cast<const uint16_t*>(buf + P::kNOff) + lane;
+      if (dead) {
+        // skip the stage
+      } else if (k < 0) {
+        const float* gm = reinterpret_cast<const float*>(buf) + lane;
+        const float2* wm = reinterpret_cast<const float2*>(buf + P::kWOff) + lane;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+          if (s < nslot) {
+            const DF d = dif(nl[s * kTile]);
+#pragma unroll
+            for (int l = 0; l < M; ++l) a32[l] = fmaf(gm[(s * P::kG + l) * kTile], d.h, a32[l]);
+            eL = fmaf(gm[(s * P::kG + M) * kTile], fabsf(d.h), eL);
+#pragma unroll
+            for (int p = 0; p < NQ3; ++p) df_mac(uq[p], wm[(s * NQ3 + p) * kTile], d);
+          }
+        }
+      } else {
+        const float* gm = reinterpret_cast<const float*>(buf) + lane;
+#pragma unroll
+        for (int kk = 0; kk < kSmallK; ++kk) {
+          if (kk != k) continue;
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            const float2 q = st[nl[s * kTile]];
+            const float dh = (q.x - u0s.x) + (q.y - u0s.y);
+#pragma unroll
+            for (int l = 0; l < kSmallM; ++l)
+              s32[kk][l] = fmaf(gm[(s * P::kGs + l) * kTile], dh, s32[kk][l]);
+            eS[kk] = fmaf(gm[(s * P::kGs + kSmallM) * kTile], fabsf(dh), eS[kk]);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0 && !dead) mbar_arrive(&empty[b]);
+    }
+    if (!dead && c < a.n_cell) finish_cell(tile, c);
   }
   cp_async_wait<0>();
 }
@@ -1163,6 +1600,7 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const FaceArgs a, const 
   T acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = cst<T>(0.0);
+  const RiemannK<T> rk = riemann_k<T>(nx, ny, a.gamma);
 #pragma unroll
   for (int k = 0; k < NQ; ++k) {
     T UL[NV], UR[NV], F[NV];
@@ -1184,7 +1622,7 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const FaceArgs a, const 
       const double an = a.adv_x * nx + a.adv_y * ny;
       F[0] = cst<T>(an) * (an >= 0.0 ? UL[0] : UR[0]);
     } else {
-      euler_riemann<T>(UL, UR, nx, ny, a.gamma, FLUX == TENO_FLUX_HLLC, F);
+      euler_riemann<T>(UL, UR, rk, FLUX == TENO_FLUX_HLLC, F);
     }
     const T wk = cst<T>(a.gw[k]);
 #pragma unroll
@@ -1211,18 +1649,38 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a, const T
                                                      double cs, double dt_fixed, double cfl,
                                                      const double* __restrict__ max_lam,
                                                      int* flag, float2* __restrict__ split) {
+  // the step size once per block (one FP64 division)
+  __shared__ double s_dt;
+  if (mode != 0 && threadIdx.x == 0) s_dt = max_lam ? cfl / *max_lam : dt_fixed;
+  if (mode != 0) __syncthreads();
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= a.n_cell) return;
   double acc[NV];
+  if constexpr (std::is_same<TK, DF>::value) {
+    // pair fluxes summed in pairs (FP32 pipe), one conversion per variable
+    DF sum[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+    for (int v = 0; v < NV; ++v) sum[v] = DF{0.f, 0.f};
 #pragma unroll
-  for (int e = 0; e < 3; ++e) {
-    const int cf = a.c_faces[3 * c + e];
-    const int64_t f = cf >> 1;
-    const double s = (cf & 1) ? -1.0 : 1.0;
+    for (int e = 0; e < 3; ++e) {
+      const int cf = a.c_faces[3 * c + e];
+      const int64_t f = cf >> 1;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = fma(s, to_d(K[f * NV + v]), acc[v]);
+      for (int v = 0; v < NV; ++v) sum[v] = (cf & 1) ? sum[v] - K[f * NV + v] : sum[v] + K[f * NV + v];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = to_d(sum[v]);
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const int cf = a.c_faces[3 * c + e];
+      const int64_t f = cf >> 1;
+      const double s = (cf & 1) ? -1.0 : 1.0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] = fma(s, to_d(K[f * NV + v]), acc[v]);
+    }
   }
   const double ia = a.inv_area[c];
   if (mode == 0) {
@@ -1230,7 +1688,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a, const T
     for (int v = 0; v < NV; ++v) out[v * a.n_pad + c] = -acc[v] * ia;
     return;
   }
-  const double dt = max_lam ? cfl / *max_lam : dt_fixed;
+  const double dt = s_dt;
   double u[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -1243,9 +1701,10 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a, const T
     }
   }
   if constexpr (NV == 4) {
+    // rho > 0 and p > 0, the latter as rho E - |m|^2 / 2 > 0 (no division)
     const double rho = u[0];
-    const double p = (a.gamma - 1.0) * (u[3] - 0.5 * (u[1] * u[1] + u[2] * u[2]) / rho);
-    if (!(rho > 0.0) || !(p > 0.0)) atomicOr(flag, 1);
+    const double pr = u[3] * rho - 0.5 * (u[1] * u[1] + u[2] * u[2]);
+    if (!(rho > 0.0) || !(pr > 0.0)) atomicOr(flag, 1);
   } else {
     if (!(u[0] == u[0])) atomicOr(flag, 1);
   }
@@ -1355,6 +1814,8 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
     if (n >= 0) Kb[v] += w[v * a.n_pad + n] * a.inv_area[n];
   }
   const int n_pass = ((n >= 0 ? 2 * NV : NV) + ND - 1) / ND;
+  const RiemannK<S> rks = riemann_k<S>(nx, ny, a.gamma);
+  const RiemannK<D> rk = riemann_k_dual<ND, S>(rks);
   for (int k = 0; k < NQ; ++k) {
     TQ ul[NV], ur[NV];
     const TQ* pl = Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV;
@@ -1367,6 +1828,9 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
     }
     const double wk = a.gw[k] * len;
     const double x = a.f_geom[5 * f + 3] - ny * len * a.gt[k];
+    S Kw[NV];  // w_k |A| Kbar in the flux scalar type
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Kw[v] = cst<S>(wk * Kb[v]);
     double* outL = Uq_bar + ((int64_t)(o * 3 + eo) * NQ + k) * NV;
     double* outR = n >= 0 ? Uq_bar + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV : outL;
     for (int pass = 0; pass < n_pass; ++pass) {
@@ -1395,18 +1859,18 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
         const double an = a.adv_x * nx + a.adv_y * ny;
         F[0] = an * (an >= 0.0 ? UL[0] : UR[0]);
       } else {
-        euler_riemann<D>(UL, UR, nx, ny, a.gamma, FLUX == TENO_FLUX_HLLC, F);
+        euler_riemann<D>(UL, UR, rk, FLUX == TENO_FLUX_HLLC, F);
       }
 #pragma unroll
       for (int j = 0; j < ND; ++j) {
-        double sacc = 0.0;
+        S sacc = cst<S>(0.0);
 #pragma unroll
-        for (int i = 0; i < NV; ++i) sacc = fma(to_d(F[i].d[j]), Kb[i], sacc);
+        for (int i = 0; i < NV; ++i) sacc = madd(F[i].d[j], Kw[i], sacc);
         const int g = dir0 + j;
         if (g < NV)
-          outL[g] = wk * sacc;
+          outL[g] = to_d(sacc);
         else if (n >= 0)
-          outR[g - NV] = wk * sacc;
+          outR[g - NV] = to_d(sacc);
       }
     }
   }
@@ -1654,6 +2118,29 @@ cudaError_t launch_recon_tma(const ReconArgs& a, const DeviceMesh& dm, int* err,
   return cudaGetLastError();
 }
 
+template <int M, int NS, int NQ>
+cudaError_t launch_recon_tma_w(const ReconArgs& a, const DeviceMesh& dm, int* err,
+                               cudaStream_t st) {
+  using P = WPlan<M, NS, 3 * NQ, 3, 4>;
+  auto kern = recon_tma_w_kernel<M, NS, NQ>;
+  const int threads = kTile * (kConsumers + 1);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)P::kSmem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, P::kSmem)) !=
+      cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
+  const int64_t grid = std::min<int64_t>(tiles, (int64_t)per_sm * sms);
+  kern<<<(unsigned)grid, threads, P::kSmem, st>>>(a, dm.halo, dm.eval_df, dm.g32, dm.wq, err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us, void* Uq,
                          uint8_t* sel_out, const uint8_t* sel_in, cudaStream_t st) {
   if (dm.precision != TENO_FP64_NATIVE && !Us) return cudaErrorInvalidValue;
@@ -1695,6 +2182,8 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
       }
       if constexpr (NV == 4) {
         if (tma) {
+          if (dm.precision == TENO_FP64 && dm.g32 && dm.wq)
+            return launch_recon_tma_w<M, NS, NQ>(a, dm, dm.err_flag, st);
           if (dm.precision == TENO_FP64) return launch_recon_tma<M, NS, NQ, true>(a, dm, dm.err_flag, st);
           return launch_recon_tma<M, NS, NQ, false>(a, dm, dm.err_flag, st);
         }
