@@ -39,10 +39,17 @@ UNIT = "cell-stage/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (max SM clock)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel, scaled to this workload from the small-case captures in profiles/;
-# None when the kernel changed since the capture
-NCU_TRAFFIC = {"fp64": None, "fp32_mixed": None, "fp64_native": 2788e6}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the
+# dominant kernel per cell, (path, order) -> bytes, from the small-case
+# captures summarised in profiles/ (64,800-cell vortex mesh); a launch's
+# traffic is this times the cells it processes.  Absent when the kernel
+# changed since the capture.
+NCU_TRAFFIC_PER_CELL = {}
+
+
+def ncu_traffic(precision, order, n_cell):
+    b = NCU_TRAFFIC_PER_CELL.get((precision, order))
+    return None if b is None else b * n_cell
 
 
 def parse():
@@ -257,14 +264,16 @@ def run_ours(args):
             var = 0  # the TMA kernel covers the double-float and mixed paths only;
             # variant 2 takes the halo kernel there
         vname = ["recon_halo_kernel", "recon_kernel (direct)", "recon_tma_kernel"][var]
+        if precision == "fp64" and var == 2:
+            vname = "recon_tma_w_kernel"  # the W form of the pair path
         kernel = f"{vname} <{precision}> order {args.order}"
         roof_hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
-                    "frac": gbs / hbm_gbs, "traffic": NCU_TRAFFIC.get(precision),
+                    "frac": gbs / hbm_gbs, "traffic": ncu_traffic(precision, args.order, n_cell),
                     "kernel": kernel, "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)"}
         if precision == "fp64_native":
             fl = algorithmic_fp64_flops(args.order, 4, nq) * n_cell / (rec_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": fl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": fl / FP64_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(precision),
+                    "frac": fl / FP64_PEAK_TFLOPS, "traffic": ncu_traffic(precision, args.order, n_cell),
                     "kernel": kernel,
                     "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz",
                     "hbm_achieved_gbs": gbs, "hbm_frac": gbs / hbm_gbs}

@@ -67,8 +67,8 @@ struct teno_ctx {
   std::vector<int32_t> st_large, st_small;  // user ids, [nc][ns], [nc][36]
   // device data
   DeviceMesh dm;
-  DevBuf b_halo_off, b_halo_ids, b_halo_loc, b_g32, b_wq;
-  DevBuf b_ahat, b_nbr, b_smask, b_fcells, b_fedges, b_fgeom, b_cfaces, b_inv_area, b_cfl_len,
+  DevBuf b_halo_off, b_halo_ids, b_halo_loc, b_g32, b_wq, b_psi;
+  DevBuf b_ahat, b_nbr, b_smask, b_fcells, b_fedges, b_fgeom, b_fgeom2, b_cfaces, b_inv_area, b_cfl_len,
       b_perm;
   DevBuf b_U, b_U1, b_U2, b_R, b_tmp, b_Uq, b_K, b_sel, b_sel_ovr, b_maxlam, b_flag;
   DevBuf b_Usplit;  // FP32 hi/lo split of the state being reconstructed (mixed precision)
@@ -878,6 +878,12 @@ int run_precompute(teno_ctx* ctx) {
     const float hi = (float)R.psi_t[i];
     dm.eval_df.psi[i] = make_float2(hi, (float)(R.psi_t[i] - (double)hi));
   }
+  dm.psi_df = nullptr;
+  if (wform) {
+    int e2 = upload(ctx, ctx->b_psi, dm.eval_df.psi, sizeof(dm.eval_df.psi));
+    if (e2) return e2;
+    dm.psi_df = (const float2*)ctx->b_psi.p;
+  }
   for (int k = 0; k < kMaxNq; ++k) {
     dm.gw[k] = k < ctx->nq ? R.gw[k] : 0.0;
     dm.gt[k] = k < ctx->nq ? R.gt[k] : 0.0;
@@ -925,6 +931,14 @@ int upload_mesh(teno_ctx* ctx) {
   int rc = upload(ctx, ctx->b_fcells, fcells.data(), fcells.size() * 4);
   if (!rc) rc = upload(ctx, ctx->b_fedges, fedges.data(), fedges.size());
   if (!rc) rc = upload(ctx, ctx->b_fgeom, fgeom.data(), fgeom.size() * 8);
+  std::vector<float2> fgeom2(3 * (size_t)ctx->nface);
+  for (int64_t f = 0; f < ctx->nface; ++f)
+    for (int i = 0; i < 3; ++i) {
+      const double x = fgeom[5 * f + i];
+      const float h = (float)x;
+      fgeom2[3 * f + i] = make_float2(h, (float)(x - (double)h));
+    }
+  if (!rc) rc = upload(ctx, ctx->b_fgeom2, fgeom2.data(), fgeom2.size() * sizeof(float2));
   if (!rc) rc = upload(ctx, ctx->b_cfaces, cfaces.data(), cfaces.size() * 4);
   if (!rc) rc = upload(ctx, ctx->b_inv_area, inv_area.data(), inv_area.size() * 8);
   if (!rc) rc = upload(ctx, ctx->b_cfl_len, cfl_len.data(), cfl_len.size() * 8);
@@ -937,6 +951,7 @@ int upload_mesh(teno_ctx* ctx) {
   dm.f_cells = (const int32_t*)ctx->b_fcells.p;
   dm.f_edges = (const int8_t*)ctx->b_fedges.p;
   dm.f_geom = (const double*)ctx->b_fgeom.p;
+  dm.f_geom2 = (const float2*)ctx->b_fgeom2.p;
   dm.c_faces = (const int32_t*)ctx->b_cfaces.p;
   dm.inv_area = (const double*)ctx->b_inv_area.p;
   dm.cfl_len = (const double*)ctx->b_cfl_len.p;
@@ -1162,8 +1177,8 @@ int teno_destroy(teno_ctx* ctx) {
   }
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  DevBuf* bufs[] = {&ctx->b_halo_off, &ctx->b_halo_ids, &ctx->b_halo_loc, &ctx->b_g32, &ctx->b_wq, &ctx->b_ahat, &ctx->b_nbr, &ctx->b_smask, &ctx->b_fcells, &ctx->b_fedges,
-                    &ctx->b_fgeom, &ctx->b_cfaces, &ctx->b_inv_area, &ctx->b_cfl_len,
+  DevBuf* bufs[] = {&ctx->b_halo_off, &ctx->b_halo_ids, &ctx->b_halo_loc, &ctx->b_g32, &ctx->b_wq, &ctx->b_psi, &ctx->b_ahat, &ctx->b_nbr, &ctx->b_smask, &ctx->b_fcells, &ctx->b_fedges,
+                    &ctx->b_fgeom, &ctx->b_fgeom2, &ctx->b_cfaces, &ctx->b_inv_area, &ctx->b_cfl_len,
                     &ctx->b_perm, &ctx->b_U, &ctx->b_U1, &ctx->b_U2, &ctx->b_R, &ctx->b_tmp,
                     &ctx->b_Uq, &ctx->b_K, &ctx->b_sel, &ctx->b_sel_ovr, &ctx->b_maxlam,
                     &ctx->b_Usplit,

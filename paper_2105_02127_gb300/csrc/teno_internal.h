@@ -63,10 +63,12 @@ struct DeviceMesh {
   // 36*6][32]), and W = Psi' G as (hi, lo) pairs ([tile][ns*3*nq][32])
   const float* g32 = nullptr;
   const float2* wq = nullptr;
+  const float2* psi_df = nullptr;   // device copy of eval_df.psi
   // faces
   const int32_t* f_cells = nullptr; // [n_face][2] owner, neighbour (-1 boundary)
   const int8_t* f_edges = nullptr;  // [n_face][2] local edge in owner / neighbour (bc tag if boundary)
   const double* f_geom = nullptr;   // [n_face][5] nx, ny, |A| (outward from owner), x_a, y_a
+  const float2* f_geom2 = nullptr;  // [n_face][3] nx, ny, |A| as (hi, lo) float pairs
   const int32_t* c_faces = nullptr; // [n_pad][3] face*2 + (1 if the cell is the neighbour)
   const double* inv_area = nullptr; // [n_pad]
   const double* cfl_len = nullptr;  // [n_pad] 4|V|/perimeter

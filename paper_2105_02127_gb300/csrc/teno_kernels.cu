@@ -251,9 +251,24 @@ __device__ __forceinline__ S lift(DF x) {
   else
     return S(to_d(x));
 }
-// branch decisions on dual numbers over pairs compare the exact pair sums
+// branch decisions on dual numbers over pairs compare the (normalised) pairs
+// lexicographically, which orders them as their exact sums; no conversion to
+// FP64 on the device
+__device__ __forceinline__ bool df_le(const DF& a, const DF& b) {
+  return a.h < b.h || (a.h == b.h && a.l <= b.l);
+}
 template <int N>
-__device__ __forceinline__ double val(const Dual<N, DF>& x) { return to_d(x.v); }
+__device__ __forceinline__ Dual<N, DF> vmin(const Dual<N, DF>& a, const Dual<N, DF>& b) {
+  return df_le(a.v, b.v) ? a : b;
+}
+template <int N>
+__device__ __forceinline__ Dual<N, DF> vmax(const Dual<N, DF>& a, const Dual<N, DF>& b) {
+  return df_le(b.v, a.v) ? a : b;
+}
+template <int N>
+__device__ __forceinline__ bool nonneg(const Dual<N, DF>& x) {
+  return x.v.h > 0.f || (x.v.h == 0.f && x.v.l >= 0.f);
+}
 
 // ---------------------------------------------------------------- fluxes
 // Euler flux through a face with unit normal n = (nx, ny): the state is
@@ -1276,9 +1291,116 @@ __device__ __forceinline__ float beta_rel_bound(float beta32, float e_abs, int n
   return eb / (t - eb);
 }
 
+// pair difference U_s - U_0 of a halo cell (FP32 hi/lo splits of the states)
+__device__ __forceinline__ DF halo_dif(const float2* st, int idx, float2 u0s) {
+  const float2 q = st[idx];
+  DF t = two_sum(q.x, -u0s.x);
+  t.l += q.y - u0s.y;
+  return two_sum(t.h, t.l);
+}
+
+// Rare paths of the W-form kernel, kept out of line so that their registers
+// do not weigh on the main loop.  A: the cell's (hi, lo) matrices at its lane,
+// nb: its halo positions, st: the tile's halo of its variable.
+//
+// Cutoff decision in FP64 from coefficients and beta in pairs.
+template <int M, int NS>
+__device__ __noinline__ uint8_t w_select_pairs(const float2* A, const uint16_t* nb,
+                                               const float2* st, float2 u0s, int present,
+                                               double ct, double eps) {
+  DF al[M];
+#pragma unroll
+  for (int l = 0; l < M; ++l) al[l] = DF{0.f, 0.f};
+  for (int s = 0; s < NS; ++s) {
+    const DF d = halo_dif(st, nb[s * kTile], u0s);
+#pragma unroll
+    for (int l = 0; l < M; ++l) df_mac(al[l], __ldg(A + (int64_t)(s * M + l) * kTile), d);
+  }
+  double beta[kSmallK + 1];
+  {
+    DF bl = {0.f, 0.f};
+#pragma unroll
+    for (int l = 0; l < M; ++l) {
+      const DF x = df_norm(al[l]);
+      df_mac(bl, make_float2(x.h, x.l), x);
+    }
+    beta[kSmallK] = df_to_double(df_norm(bl));
+  }
+#pragma unroll
+  for (int k = 0; k < kSmallK; ++k) {
+    DF as[kSmallM];
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) as[l] = DF{0.f, 0.f};
+    if ((present >> k) & 1) {
+      for (int s = 0; s < kSmallN; ++s) {
+        const DF d = halo_dif(st, nb[(NS + k * kSmallN + s) * kTile], u0s);
+        const float2* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
+#pragma unroll
+        for (int l = 0; l < kSmallM; ++l) df_mac(as[l], __ldg(As + l * kTile), d);
+      }
+    }
+    DF q = {0.f, 0.f};
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) {
+      const DF x = df_norm(as[l]);
+      df_mac(q, make_float2(x.h, x.l), x);
+    }
+    beta[k] = df_to_double(df_norm(q));
+  }
+  return select_fp64(beta, present, ct, eps);
+}
+
+// Gauss-point values of the equally weighted kept directional polynomials
+// (step ii of the selection), in pairs; psi: the [point][kMaxM] table of
+// Psi' as pairs.
+template <int M, int NS, int NQ3, int NV>
+__device__ __noinline__ void w_small_values(const float2* A, const uint16_t* nb, const float2* st,
+                                            float2 u0s, uint8_t sel, const float2* psi,
+                                            DF* out) {
+  DF sum[kSmallM];
+#pragma unroll
+  for (int l = 0; l < kSmallM; ++l) sum[l] = DF{0.f, 0.f};
+  for (int k = 0; k < kSmallK; ++k) {
+    if (!((sel >> k) & 1)) continue;
+    DF as[kSmallM];
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) as[l] = DF{0.f, 0.f};
+    for (int s = 0; s < kSmallN; ++s) {
+      const DF d = halo_dif(st, nb[(NS + k * kSmallN + s) * kTile], u0s);
+      const float2* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) df_mac(as[l], __ldg(As + l * kTile), d);
+    }
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) {
+      const DF x = df_norm(as[l]);
+      DF q = two_sum(sum[l].h, x.h);
+      q.l += sum[l].l + x.l;
+      sum[l] = two_sum(q.h, q.l);
+    }
+  }
+  // divide by the number of kept stencils (exact remainder correction)
+  const int nd = (sel & 1) + ((sel >> 1) & 1) + ((sel >> 2) & 1);
+  const float fn = (float)(nd ? nd : 1);
+  DF cf[kSmallM];
+#pragma unroll
+  for (int l = 0; l < kSmallM; ++l) {
+    const float qh = sum[l].h / fn;
+    const float r = fmaf(-qh, fn, sum[l].h);
+    cf[l] = nd ? two_sum(qh, (r + sum[l].l) / fn) : DF{0.f, 0.f};
+  }
+  const DF u0 = {u0s.x, u0s.y};
+  for (int p = 0; p < NQ3; ++p) {
+    DF sp = {0.f, 0.f};
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) df_mac(sp, __ldg(psi + p * kMaxM + l), cf[l]);
+    out[p * NV] = u0 + df_norm(sp);
+  }
+}
+
 template <int M, int NS, int NQ>
 __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ, 3, 4>::kBlocks))
-    recon_tma_w_kernel(const ReconArgs a, const HaloArgs h, const DFTable ev,
+    recon_tma_w_kernel(const ReconArgs a, const HaloArgs h, const float2* __restrict__ psi,
                        const float* __restrict__ g32, const float2* __restrict__ wq, int* err) {
   constexpr int NQ3 = 3 * NQ;
   using P = WPlan<M, NS, NQ3, 3, 4>;
@@ -1390,26 +1512,6 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
     auto finish_cell = [&](int64_t tile, int64_t c) {
       const int present = a.smask[c];
       const float2* A = reinterpret_cast<const float2*>(a.ahat) + tile * (int64_t)E * kTile + lane;
-      DF as[kSmallK][kSmallM];
-      bool have_small = false;
-      // directional coefficients in pairs for the stencils in kmask
-      auto small_df = [&](int kmask) {
-#pragma unroll
-        for (int k = 0; k < kSmallK; ++k) {
-#pragma unroll
-          for (int l = 0; l < kSmallM; ++l) as[k][l] = DF{0.f, 0.f};
-          if (!((kmask >> k) & 1)) continue;
-          for (int s = 0; s < kSmallN; ++s) {
-            const DF d = dif(__ldg(nb + (NS + k * kSmallN + s) * kTile));
-            const float2* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
-#pragma unroll
-            for (int l = 0; l < kSmallM; ++l) df_mac(as[k][l], __ldg(As + l * kTile), d);
-          }
-#pragma unroll
-          for (int l = 0; l < kSmallM; ++l) as[k][l] = df_norm(as[k][l]);
-        }
-        have_small = true;
-      };
       uint8_t sel;
       if (a.sel_in) {
         sel = a.sel_in[(int64_t)v * a.n_pad + c];
@@ -1447,70 +1549,17 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
             if (((present >> k) & 1) && chi_keep32(t, k, present & 7, ct, &near, band))
               sel |= (uint8_t)(1u << k);
         }
-        if (near) {
-          // coefficients and beta in pairs, decision in FP64
-          DF al[M];
-#pragma unroll
-          for (int l = 0; l < M; ++l) al[l] = DF{0.f, 0.f};
-          for (int s = 0; s < NS; ++s) {
-            const DF d = dif(__ldg(nb + s * kTile));
-#pragma unroll
-            for (int l = 0; l < M; ++l) df_mac(al[l], __ldg(A + (int64_t)(s * M + l) * kTile), d);
-          }
-          DF bl = {0.f, 0.f};
-#pragma unroll
-          for (int l = 0; l < M; ++l) {
-            const DF x = df_norm(al[l]);
-            df_mac(bl, make_float2(x.h, x.l), x);
-          }
-          small_df(present & 7);
-          double beta[kSmallK + 1];
-          beta[kSmallK] = df_to_double(df_norm(bl));
-#pragma unroll
-          for (int k = 0; k < kSmallK; ++k) {
-            DF q = {0.f, 0.f};
-#pragma unroll
-            for (int l = 0; l < kSmallM; ++l) df_mac(q, make_float2(as[k][l].h, as[k][l].l), as[k][l]);
-            beta[k] = df_to_double(df_norm(q));
-          }
-          sel = select_fp64(beta, present, a.ct, a.eps);
-        }
+        if (near) sel = w_select_pairs<M, NS>(A, nb, st, u0s, present, a.ct, a.eps);
       }
       if (a.sel_out) a.sel_out[(int64_t)v * a.n_pad + c] = sel;
-      // ---- Gauss-point values as (hi, lo) pairs
+      // Gauss-point values as (hi, lo) pairs
       DF* __restrict__ out = reinterpret_cast<DF*>(a.Uq) + c * (NQ3 * NV) + v;
-      const DF u0 = {u0s.x, u0s.y};
       if (sel & 8) {
+        const DF u0 = {u0s.x, u0s.y};
 #pragma unroll
         for (int p = 0; p < NQ3; ++p) out[p * NV] = u0 + df_norm(uq[p]);
       } else {
-        if (!have_small) small_df(sel & 7);
-        // equal weights: sum the kept polynomials, then divide by their number
-        const int nd = (sel & 1) + ((sel >> 1) & 1) + ((sel >> 2) & 1);
-        const float fn = (float)(nd ? nd : 1);
-        DF cf[kSmallM];
-#pragma unroll
-        for (int l = 0; l < kSmallM; ++l) {
-          DF sum = {0.f, 0.f};
-#pragma unroll
-          for (int k = 0; k < kSmallK; ++k) {
-            if (!((sel >> k) & 1)) continue;
-            DF q = two_sum(sum.h, as[k][l].h);
-            q.l += sum.l + as[k][l].l;
-            sum = two_sum(q.h, q.l);
-          }
-          const float qh = sum.h / fn;
-          const float r = fmaf(-qh, fn, sum.h);  // exact remainder
-          cf[l] = two_sum(qh, (r + sum.l) / fn);
-          if (!nd) cf[l] = DF{0.f, 0.f};
-        }
-#pragma unroll
-        for (int p = 0; p < NQ3; ++p) {
-          DF sp = {0.f, 0.f};
-#pragma unroll
-          for (int l = 0; l < kSmallM; ++l) df_mac(sp, ev.psi[p * kMaxM + l], cf[l]);
-          out[p * NV] = u0 + df_norm(sp);
-        }
+        w_small_values<M, NS, NQ3, NV>(A, nb, st, u0s, sel, psi, out);
       }
     };
     for (int j = 0; j < P::kStages; ++j, ++g) {
@@ -1584,10 +1633,48 @@ struct FaceArgs {
   const int32_t* f_cells;
   const int8_t* f_edges;
   const double* f_geom;
+  const float2* f_geom2;  // [n_face][3] nx, ny, |A| as (hi, lo) pairs
   int64_t n_face;
   double gamma, adv_x, adv_y, time;
   double gw[kMaxNq], gt[kMaxNq];
+  float2 gw2[kMaxNq], g2, gm12;  // Gauss weights, gamma, gamma - 1 as pairs
 };
+
+// face constants in the flux scalar type: FP64 from the double geometry,
+// pairs and floats from the copy split on the host (no FP64 conversions)
+template <typename T>
+__device__ __forceinline__ void face_k(const double* fg, const float2* fg2, int64_t f, double g,
+                                       float2 g2, float2 gm12, RiemannK<T>& rk, T& tl) {
+  if constexpr (std::is_same<T, double>::value) {
+    rk = riemann_k<double>(fg[5 * f], fg[5 * f + 1], g);
+    tl = fg[5 * f + 2];
+  } else if constexpr (std::is_same<T, DF>::value) {
+    const float2 nx = fg2[3 * f], ny = fg2[3 * f + 1], ln = fg2[3 * f + 2];
+    rk = {DF{1.f, 0.f}, DF{0.5f, 0.f}, DF{gm12.x, gm12.y}, DF{g2.x, g2.y}, DF{nx.x, nx.y},
+          DF{ny.x, ny.y}};
+    tl = DF{ln.x, ln.y};
+  } else {
+    rk = {1.f, 0.5f, gm12.x, g2.x, fg2[3 * f].x, fg2[3 * f + 1].x};
+    tl = fg2[3 * f + 2].x;
+  }
+}
+template <typename T>
+__device__ __forceinline__ T gauss_w(double w, float2 w2) {
+  if constexpr (std::is_same<T, double>::value)
+    return w;
+  else if constexpr (std::is_same<T, DF>::value)
+    return DF{w2.x, w2.y};
+  else
+    return w2.x;
+}
+
+// Gauss points of a face unrolled in the flux kernel: the pair-arithmetic
+// solver is large enough that one copy of its code runs faster (fewer
+// instruction-fetch stalls) than three; the FP32 and FP64 ones unroll
+#ifndef TENO_FLUX_UNROLL_PAIRS
+#define TENO_FLUX_UNROLL_PAIRS 1
+#endif
+constexpr int kFluxUnrollPairs = TENO_FLUX_UNROLL_PAIRS;
 
 template <int NV, int NQ, int FLUX, typename T>
 __global__ void __launch_bounds__(256) face_flux_kernel(const FaceArgs a, const T* __restrict__ Uq,
@@ -1600,8 +1687,10 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const FaceArgs a, const 
   T acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = cst<T>(0.0);
-  const RiemannK<T> rk = riemann_k<T>(nx, ny, a.gamma);
-#pragma unroll
+  RiemannK<T> rk;
+  T tl;
+  face_k<T>(a.f_geom, a.f_geom2, f, a.gamma, a.g2, a.gm12, rk, tl);
+#pragma unroll (std::is_same<T, DF>::value ? kFluxUnrollPairs : 4)
   for (int k = 0; k < NQ; ++k) {
     T UL[NV], UR[NV], F[NV];
     const T* pl = Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV;
@@ -1624,11 +1713,10 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const FaceArgs a, const 
     } else {
       euler_riemann<T>(UL, UR, rk, FLUX == TENO_FLUX_HLLC, F);
     }
-    const T wk = cst<T>(a.gw[k]);
+    const T wk = gauss_w<T>(a.gw[k], a.gw2[k]);
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = madd(wk, F[v], acc[v]);
   }
-  const T tl = cst<T>(len);
 #pragma unroll
   for (int v = 0; v < NV; ++v) K[f * NV + v] = acc[v] * tl;
 }
@@ -1783,6 +1871,8 @@ struct VjpArgs {
   const int32_t* f_cells;
   const int8_t* f_edges;
   const double* f_geom;
+  const float2* f_geom2;
+  float2 g2, gm12;
   const double* inv_area;
   int64_t n_face, n_pad;
   double gamma, adv_x, adv_y, time;
@@ -1814,7 +1904,9 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
     if (n >= 0) Kb[v] += w[v * a.n_pad + n] * a.inv_area[n];
   }
   const int n_pass = ((n >= 0 ? 2 * NV : NV) + ND - 1) / ND;
-  const RiemannK<S> rks = riemann_k<S>(nx, ny, a.gamma);
+  RiemannK<S> rks;
+  S tl_unused;
+  face_k<S>(a.f_geom, a.f_geom2, f, a.gamma, a.g2, a.gm12, rks, tl_unused);
   const RiemannK<D> rk = riemann_k_dual<ND, S>(rks);
   for (int k = 0; k < NQ; ++k) {
     TQ ul[NV], ur[NV];
@@ -2137,7 +2229,7 @@ cudaError_t launch_recon_tma_w(const ReconArgs& a, const DeviceMesh& dm, int* er
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)per_sm * sms);
-  kern<<<(unsigned)grid, threads, P::kSmem, st>>>(a, dm.halo, dm.eval_df, dm.g32, dm.wq, err);
+  kern<<<(unsigned)grid, threads, P::kSmem, st>>>(a, dm.halo, dm.psi_df, dm.g32, dm.wq, err);
   return cudaGetLastError();
 }
 
@@ -2182,7 +2274,7 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
       }
       if constexpr (NV == 4) {
         if (tma) {
-          if (dm.precision == TENO_FP64 && dm.g32 && dm.wq)
+          if (dm.precision == TENO_FP64 && dm.g32 && dm.wq && dm.psi_df)
             return launch_recon_tma_w<M, NS, NQ>(a, dm, dm.err_flag, st);
           if (dm.precision == TENO_FP64) return launch_recon_tma<M, NS, NQ, true>(a, dm, dm.err_flag, st);
           return launch_recon_tma<M, NS, NQ, false>(a, dm, dm.err_flag, st);
@@ -2206,11 +2298,18 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
   });
 }
 
+// (hi, lo) float pair of a double, on the host
+static float2 split2(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
 static FaceArgs face_args(const DeviceMesh& dm, double time) {
   FaceArgs a;
   a.f_cells = dm.f_cells;
   a.f_edges = dm.f_edges;
   a.f_geom = dm.f_geom;
+  a.f_geom2 = dm.f_geom2;
   a.n_face = dm.n_face;
   a.gamma = dm.gamma;
   a.adv_x = dm.adv_x;
@@ -2219,7 +2318,10 @@ static FaceArgs face_args(const DeviceMesh& dm, double time) {
   for (int k = 0; k < kMaxNq; ++k) {
     a.gw[k] = dm.gw[k];
     a.gt[k] = dm.gt[k];
+    a.gw2[k] = split2(dm.gw[k]);
   }
+  a.g2 = split2(dm.gamma);
+  a.gm12 = split2(dm.gamma - 1.0);
   return a;
 }
 
@@ -2330,6 +2432,9 @@ cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const dou
   a.f_cells = dm.f_cells;
   a.f_edges = dm.f_edges;
   a.f_geom = dm.f_geom;
+  a.f_geom2 = dm.f_geom2;
+  a.g2 = split2(dm.gamma);
+  a.gm12 = split2(dm.gamma - 1.0);
   a.inv_area = dm.inv_area;
   a.n_face = dm.n_face;
   a.n_pad = dm.n_pad;
