@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -396,7 +397,49 @@ def cpu_baseline(mesh, U, order, samples=1):
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": mesh.n_cell * samples / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{samples} full residual stage(s) of the {mesh.n_cell}-cell mesh "
-                      f"({dt:.1f} s), stencils precomputed beforehand"}
+                      f"({dt:.1f} s), stencils precomputed beforehand",
+            "cpu_model": cpu_model(), "single_thread": cpu_single_thread(order)}
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
+_SINGLE = """
+import sys, time, numpy as np
+sys.path.insert(0, {root!r})
+import bench
+from oracle.oracle import Oracle
+mesh, U = bench.workload(512, {order})
+cells = np.sort(np.random.default_rng(0).choice(mesh.n_cell, 16384, replace=False))
+o = Oracle(mesh, order={order}, n_var=4, flux=1)
+o.prepare(cells)
+o.residual_cells(U, cells)
+t0 = time.perf_counter()
+o.residual_cells(U, cells)
+print(len(cells) / (time.perf_counter() - t0))
+"""
+
+
+def cpu_single_thread(order):
+    """The same oracle on one core (OMP_NUM_THREADS=1, a fresh process): one
+    residual stage of 16,384 sampled cells of the vortex mesh."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", _SINGLE.format(root=ROOT, order=order)],
+                           capture_output=True, text=True, timeout=300, env=env)
+        v = float(r.stdout.strip().splitlines()[-1])
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return None
+    return {"value": v, "unit": UNIT, "cores": 1,
+            "sample": "one residual stage of 16,384 sampled cells of the 512x512 vortex mesh"}
 
 
 def run_reference(args):

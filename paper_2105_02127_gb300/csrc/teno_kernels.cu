@@ -359,6 +359,268 @@ __device__ __forceinline__ void euler_riemann(const T* UL, const T* UR, const Ri
   F[3] = Fx[3];
 }
 
+// a <= b in the order the forward solver's min/max use (pairs: lexicographic)
+template <typename T>
+__device__ __forceinline__ bool le_ord(const T& a, const T& b) {
+  if constexpr (std::is_same<T, DF>::value)
+    return a.h < b.h || (a.h == b.h && a.l <= b.l);
+  else
+    return a <= b;
+}
+
+// Reverse mode of euler_riemann: given Fb = dJ/dF (face frame rotated back,
+// the kernel's output frame), adds (dF/dU_L)^T Fb to ULb and (dF/dU_R)^T Fb
+// to URb, with every branch (wave-speed min/max, HLL/HLLC region, HLLC side)
+// frozen at the forward state.  The forward values are recomputed first;
+// the adjoint statements then run in reverse order of the forward ones.
+template <typename T>
+__device__ __forceinline__ void euler_riemann_vjp(const T* UL, const T* UR, const RiemannK<T>& K,
+                                                  int hllc, const T* Fb, T* ULb, T* URb) {
+  const T one = K.one, half = K.half, two = K.one + K.one;
+  const T gm1 = K.gm1, gg = K.gg, tnx = K.tnx, tny = K.tny;
+  const T zero = one - one;
+  // ---- forward
+  const T rL = UL[0], rR = UR[0];
+  const T irL = one / rL, irR = one / rR;
+  const T mnL = UL[1] * tnx + UL[2] * tny, mtL = UL[2] * tnx - UL[1] * tny;
+  const T mnR = UR[1] * tnx + UR[2] * tny, mtR = UR[2] * tnx - UR[1] * tny;
+  const T unL = mnL * irL, utL = mtL * irL, unR = mnR * irR, utR = mtR * irR;
+  const T EL = UL[3], ER = UR[3];
+  const T qL = unL * unL + utL * utL, qR = unR * unR + utR * utR;
+  const T pL = gm1 * (EL - half * rL * qL), pR = gm1 * (ER - half * rR * qR);
+  const T cL = tsqrt(gg * pL * irL), cR = tsqrt(gg * pR * irR);
+  const T HL = (EL + pL) * irL, HR = (ER + pR) * irR;
+  const T D = tsqrt(rR * irL);
+  const T iden = one / (one + D);
+  const T ua = (unL + unR * D) * iden, va = (utL + utR * D) * iden;
+  const T Ha = (HL + HR * D) * iden;
+  const T ca = tsqrt(gm1 * (Ha - half * (ua * ua + va * va)));
+  const bool sl0 = le_ord(unL - cL, ua - ca);  // SL from the left state
+  const bool sr0 = le_ord(ua + ca, unR + cR);  // SR from the right state
+  const T SL = sl0 ? unL - cL : ua - ca;
+  const T SR = sr0 ? unR + cR : ua + ca;
+  const T mL = rL * unL, mR = rR * unR;
+  const T FL[4] = {mL, mL * unL + pL, mL * utL, unL * (EL + pL)};
+  const T FR[4] = {mR, mR * unR + pR, mR * utR, unR * (ER + pR)};
+  const T WL[4] = {rL, mL, rL * utL, EL};
+  const T WR[4] = {rR, mR, rR * utR, ER};
+  // ---- reverse
+  T Fxb[4];
+  Fxb[0] = Fb[0];
+  Fxb[1] = Fb[1] * tnx + Fb[2] * tny;
+  Fxb[2] = Fb[2] * tnx - Fb[1] * tny;
+  Fxb[3] = Fb[3];
+  T FLb[4], FRb[4], WLb[4], WRb[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) FLb[k] = FRb[k] = WLb[k] = WRb[k] = zero;
+  T SLb = zero, SRb = zero;
+  T rLb = zero, rRb = zero, unLb = zero, unRb = zero, utLb = zero, utRb = zero;
+  T pLb = zero, pRb = zero, ELb = zero, ERb = zero;
+  if (nonneg(SL)) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) FLb[k] = Fxb[k];
+  } else if (nonneg(-SR)) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) FRb[k] = Fxb[k];
+  } else if (!hllc) {
+    const T inv = one / (SR - SL), sLR = SL * SR;
+    T invb = zero, sLRb = zero;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const T G = SR * FL[k] - SL * FR[k] + sLR * (WR[k] - WL[k]);
+      invb = invb + Fxb[k] * G;
+      const T Gb = Fxb[k] * inv;
+      FLb[k] = Gb * SR;
+      FRb[k] = zero - Gb * SL;
+      WRb[k] = Gb * sLR;
+      WLb[k] = zero - Gb * sLR;
+      SRb = SRb + Gb * FL[k];
+      SLb = SLb - Gb * FR[k];
+      sLRb = sLRb + Gb * (WR[k] - WL[k]);
+    }
+    SRb = SRb + sLRb * SL;
+    SLb = SLb + sLRb * SR;
+    const T db = zero - invb * inv * inv;  // d(SR - SL)
+    SRb = SRb + db;
+    SLb = SLb - db;
+  } else {
+    const T aL = rL * (SL - unL), aR = rR * (SR - unR);
+    const T Nn = pR - pL + aL * unL - aR * unR, Dn = aL - aR;
+    const T Ss = Nn / Dn;
+    const bool left = nonneg(Ss);
+    const T r = left ? rL : rR, un = left ? unL : unR, ut = left ? utL : utR;
+    const T p = left ? pL : pR, S = left ? SL : SR, E = left ? EL : ER;
+    const T gq = r * (S - un), den = S - Ss;
+    const T f = gq / den;
+    const T h = p / gq;
+    const T es = E / r + (Ss - un) * (Ss + h);
+    const T Us[4] = {f, f * Ss, f * ut, f * es};
+    const T* Wsd = left ? WL : WR;
+    T Sb = zero, Ssb = zero, rb = zero, unb = zero, utb = zero, pb = zero, Eb = zero;
+    T Usb[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      Sb = Sb + Fxb[k] * (Us[k] - Wsd[k]);
+      Usb[k] = S * Fxb[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (left) {
+        FLb[k] = Fxb[k];
+        WLb[k] = zero - S * Fxb[k];
+      } else {
+        FRb[k] = Fxb[k];
+        WRb[k] = zero - S * Fxb[k];
+      }
+    }
+    // Us = f * (1, Ss, ut, es)
+    const T fb = Usb[0] + Usb[1] * Ss + Usb[2] * ut + Usb[3] * es;
+    Ssb = Ssb + Usb[1] * f;
+    utb = utb + Usb[2] * f;
+    const T esb = Usb[3] * f;
+    // es = E / r + (Ss - un) (Ss + h), h = p / gq, gq = r (S - un)
+    Eb = Eb + esb / r;
+    rb = rb - esb * E / (r * r);
+    const T t1 = esb * (Ss + h), t2 = esb * (Ss - un);
+    Ssb = Ssb + t1 + t2;
+    unb = unb - t1;
+    const T hb = t2;
+    pb = pb + hb / gq;
+    T gqb = zero - hb * h / gq;
+    // f = gq / den, den = S - Ss
+    gqb = gqb + fb / den;
+    const T denb = zero - fb * f / den;
+    Sb = Sb + denb;
+    Ssb = Ssb - denb;
+    rb = rb + gqb * (S - un);
+    Sb = Sb + gqb * r;
+    unb = unb - gqb * r;
+    // Ss = Nn / Dn, Nn = pR - pL + aL unL - aR unR, Dn = aL - aR
+    const T Nb = Ssb / Dn, Dnb = zero - Ssb * Ss / Dn;
+    pRb = pRb + Nb;
+    pLb = pLb - Nb;
+    const T aLb = Nb * unL + Dnb, aRb = zero - Nb * unR - Dnb;
+    unLb = unLb + Nb * aL;
+    unRb = unRb - Nb * aR;
+    // aL = rL (SL - unL), aR = rR (SR - unR)
+    rLb = rLb + aLb * (SL - unL);
+    SLb = SLb + aLb * rL;
+    unLb = unLb - aLb * rL;
+    rRb = rRb + aRb * (SR - unR);
+    SRb = SRb + aRb * rR;
+    unRb = unRb - aRb * rR;
+    // the chosen side's variables
+    if (left) {
+      rLb = rLb + rb; unLb = unLb + unb; utLb = utLb + utb; pLb = pLb + pb; SLb = SLb + Sb;
+      ELb = ELb + Eb;
+    } else {
+      rRb = rRb + rb; unRb = unRb + unb; utRb = utRb + utb; pRb = pRb + pb; SRb = SRb + Sb;
+      ERb = ERb + Eb;
+    }
+  }
+  // wave speeds (frozen min / max branches)
+  T uab = zero, cab = zero, cLb = zero, cRb = zero;
+  if (sl0) {
+    unLb = unLb + SLb;
+    cLb = cLb - SLb;
+  } else {
+    uab = uab + SLb;
+    cab = cab - SLb;
+  }
+  if (sr0) {
+    unRb = unRb + SRb;
+    cRb = cRb + SRb;
+  } else {
+    uab = uab + SRb;
+    cab = cab + SRb;
+  }
+  // F and W of both sides
+  {
+    const T mLb = FLb[0] + FLb[1] * unL + FLb[2] * utL + WLb[1];
+    unLb = unLb + FLb[1] * mL + FLb[3] * (EL + pL) + mLb * rL;
+    pLb = pLb + FLb[1] + FLb[3] * unL;
+    utLb = utLb + FLb[2] * mL + WLb[2] * rL;
+    ELb = ELb + FLb[3] * unL + WLb[3];
+    rLb = rLb + WLb[0] + WLb[2] * utL + mLb * unL;
+    const T mRb = FRb[0] + FRb[1] * unR + FRb[2] * utR + WRb[1];
+    unRb = unRb + FRb[1] * mR + FRb[3] * (ER + pR) + mRb * rR;
+    pRb = pRb + FRb[1] + FRb[3] * unR;
+    utRb = utRb + FRb[2] * mR + WRb[2] * rR;
+    ERb = ERb + FRb[3] * unR + WRb[3];
+    rRb = rRb + WRb[0] + WRb[2] * utR + mRb * unR;
+  }
+  // Roe averages: ca = sqrt(gm1 (Ha - (ua^2 + va^2)/2)), ua, va, Ha, iden, D
+  const T ca2b = cab / (two * ca);
+  const T Hab = ca2b * gm1;
+  uab = uab - ca2b * gm1 * ua;
+  const T vab = zero - ca2b * gm1 * va;
+  unLb = unLb + uab * iden;
+  unRb = unRb + uab * D * iden;
+  utLb = utLb + vab * iden;
+  utRb = utRb + vab * D * iden;
+  T HLb = Hab * iden, HRb = Hab * D * iden;
+  const T idenb = uab * (unL + unR * D) + vab * (utL + utR * D) + Hab * (HL + HR * D);
+  const T Db = uab * unR * iden + vab * utR * iden + Hab * HR * iden - idenb * iden * iden;
+  const T rrb = Db / (two * D);  // d(rR irL)
+  rRb = rRb + rrb * irL;
+  T irLb = rrb * rR, irRb = zero;
+  // H, c, p, q, u of both sides
+  ELb = ELb + HLb * irL;
+  pLb = pLb + HLb * irL;
+  irLb = irLb + HLb * (EL + pL);
+  ERb = ERb + HRb * irR;
+  pRb = pRb + HRb * irR;
+  irRb = irRb + HRb * (ER + pR);
+  {
+    const T c2b = cLb / (two * cL);
+    pLb = pLb + c2b * gg * irL;
+    irLb = irLb + c2b * gg * pL;
+    const T c2bR = cRb / (two * cR);
+    pRb = pRb + c2bR * gg * irR;
+    irRb = irRb + c2bR * gg * pR;
+  }
+  ELb = ELb + pLb * gm1;
+  rLb = rLb - pLb * gm1 * half * qL;
+  const T qLb = zero - pLb * gm1 * half * rL;
+  ERb = ERb + pRb * gm1;
+  rRb = rRb - pRb * gm1 * half * qR;
+  const T qRb = zero - pRb * gm1 * half * rR;
+  unLb = unLb + two * qLb * unL;
+  utLb = utLb + two * qLb * utL;
+  unRb = unRb + two * qRb * unR;
+  utRb = utRb + two * qRb * utR;
+  const T mnLb = unLb * irL, mtLb = utLb * irL, mnRb = unRb * irR, mtRb = utRb * irR;
+  irLb = irLb + unLb * mnL + utLb * mtL;
+  irRb = irRb + unRb * mnR + utRb * mtR;
+  rLb = rLb - irLb * irL * irL;
+  rRb = rRb - irRb * irR * irR;
+  ULb[0] = ULb[0] + rLb;
+  ULb[1] = ULb[1] + mnLb * tnx - mtLb * tny;
+  ULb[2] = ULb[2] + mnLb * tny + mtLb * tnx;
+  ULb[3] = ULb[3] + ELb;
+  URb[0] = URb[0] + rRb;
+  URb[1] = URb[1] + mnRb * tnx - mtRb * tny;
+  URb[2] = URb[2] + mnRb * tny + mtRb * tnx;
+  URb[3] = URb[3] + ERb;
+}
+
+// (dU_R/dU_L)^T URb added to ULb for the ghost state of a boundary point:
+// mirror at a wall, identity at an outflow, constant at inflow and top
+template <typename T>
+__device__ __forceinline__ void ghost_vjp(int tag, const RiemannK<T>& K, const T* URb, T* ULb) {
+  if (tag == TENO_BC_WALL) {
+    const T two = K.one + K.one;
+    const T mnb = (URb[1] * K.tnx + URb[2] * K.tny) * two;
+    ULb[0] = ULb[0] + URb[0];
+    ULb[1] = ULb[1] + URb[1] - mnb * K.tnx;
+    ULb[2] = ULb[2] + URb[2] - mnb * K.tny;
+    ULb[3] = ULb[3] + URb[3];
+  } else if (tag == TENO_BC_OUTFLOW) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ULb[k] = ULb[k] + URb[k];
+  }
+}
+
 // ghost state of a boundary face point (tag: enum teno_bc)
 template <typename T>
 __device__ __forceinline__ void ghost_state(int tag, const T* UL, double nx, double ny, double x,
@@ -1881,10 +2143,19 @@ struct VjpArgs {
 
 // Uq_bar[(c,edge,q)] = w_q |A| (dF/dU_side)^T Kbar with Kbar = dJ/dK_f
 // (R_o has -K/|V_o|, R_n has +K/|V_n|); every Gauss slot of every cell is
-// written by exactly one face.  The Jacobian columns come from forward-mode
-// dual numbers over scalar S, ND seeded directions per pass: an interior face
-// seeds the NV components of U_L, then those of U_R (2 NV / ND passes); a
-// boundary face only U_L (the ghost state carries dU_R/dU_L).
+// written by exactly one face.  Euler: the hand-written reverse sweep of the
+// Riemann solver (euler_riemann_vjp, ghost_vjp).  Scalar advection, and Euler
+// when built with TENO_VJP_REVERSE=0: Jacobian columns from forward-mode dual
+// numbers over scalar S, ND seeded directions per pass (an interior face
+// seeds the NV components of U_L, then those of U_R; a boundary face only U_L,
+// the ghost state carrying dU_R/dU_L).
+// Euler flux VJP by the hand-written reverse sweep (1) or by forward-mode
+// dual numbers (0; kept as the cross-check of the reverse sweep)
+#ifndef TENO_VJP_REVERSE
+#define TENO_VJP_REVERSE 1
+#endif
+constexpr bool kVjpReverse = TENO_VJP_REVERSE != 0;
+
 template <int NV, int NQ, int FLUX, typename TQ, typename S, int ND>
 __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
                                                             const TQ* __restrict__ Uq,
@@ -1925,44 +2196,68 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
     for (int v = 0; v < NV; ++v) Kw[v] = cst<S>(wk * Kb[v]);
     double* outL = Uq_bar + ((int64_t)(o * 3 + eo) * NQ + k) * NV;
     double* outR = n >= 0 ? Uq_bar + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV : outL;
-    for (int pass = 0; pass < n_pass; ++pass) {
-      const int dir0 = pass * ND;  // directions dir0 .. dir0+ND-1 of [U_L, U_R]
-      D UL[NV], UR[NV], F[NV];
+    if constexpr (NV == 4 && kVjpReverse) {
+      // reverse mode: one forward recomputation and its adjoint sweep
+      S uL[NV], uR[NV], ULb[NV], URb[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        UL[v] = cst<D>(0.0);
-        UL[v].v = lift<S>(ul[v]);
-        if (v >= dir0 && v < dir0 + ND) UL[v].d[v - dir0] = cst<S>(1.0);
+        uL[v] = lift<S>(ul[v]);
+        ULb[v] = cst<S>(0.0);
+        URb[v] = cst<S>(0.0);
       }
       if (n >= 0) {
 #pragma unroll
+        for (int v = 0; v < NV; ++v) uR[v] = lift<S>(ur[v]);
+      } else {
+        ghost_state<S>(en, uL, nx, ny, x, a.time, a.gamma, uR);
+      }
+      euler_riemann_vjp<S>(uL, uR, rks, FLUX == TENO_FLUX_HLLC, Kw, ULb, URb);
+      if (n < 0) ghost_vjp<S>(en, rks, URb, ULb);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        outL[v] = to_d(ULb[v]);
+        if (n >= 0) outR[v] = to_d(URb[v]);
+      }
+    } else {
+      for (int pass = 0; pass < n_pass; ++pass) {
+        const int dir0 = pass * ND;  // directions dir0 .. dir0+ND-1 of [U_L, U_R]
+        D UL[NV], UR[NV], F[NV];
+#pragma unroll
         for (int v = 0; v < NV; ++v) {
-          UR[v] = cst<D>(0.0);
-          UR[v].v = lift<S>(ur[v]);
-          if (NV + v >= dir0 && NV + v < dir0 + ND) UR[v].d[NV + v - dir0] = cst<S>(1.0);
+          UL[v] = cst<D>(0.0);
+          UL[v].v = lift<S>(ul[v]);
+          if (v >= dir0 && v < dir0 + ND) UL[v].d[v - dir0] = cst<S>(1.0);
         }
-      } else if constexpr (NV == 4) {
-        ghost_state<D>(en, UL, nx, ny, x, a.time, a.gamma, UR);  // carries dUR/dUL
-      } else {
+        if (n >= 0) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) UR[v] = UL[v];
-      }
-      if constexpr (NV == 1) {
-        const double an = a.adv_x * nx + a.adv_y * ny;
-        F[0] = an * (an >= 0.0 ? UL[0] : UR[0]);
-      } else {
-        euler_riemann<D>(UL, UR, rk, FLUX == TENO_FLUX_HLLC, F);
-      }
+          for (int v = 0; v < NV; ++v) {
+            UR[v] = cst<D>(0.0);
+            UR[v].v = lift<S>(ur[v]);
+            if (NV + v >= dir0 && NV + v < dir0 + ND) UR[v].d[NV + v - dir0] = cst<S>(1.0);
+          }
+        } else if constexpr (NV == 4) {
+          ghost_state<D>(en, UL, nx, ny, x, a.time, a.gamma, UR);  // carries dUR/dUL
+        } else {
 #pragma unroll
-      for (int j = 0; j < ND; ++j) {
-        S sacc = cst<S>(0.0);
+          for (int v = 0; v < NV; ++v) UR[v] = UL[v];
+        }
+        if constexpr (NV == 1) {
+          const double an = a.adv_x * nx + a.adv_y * ny;
+          F[0] = an * (an >= 0.0 ? UL[0] : UR[0]);
+        } else {
+          euler_riemann<D>(UL, UR, rk, FLUX == TENO_FLUX_HLLC, F);
+        }
 #pragma unroll
-        for (int i = 0; i < NV; ++i) sacc = madd(F[i].d[j], Kw[i], sacc);
-        const int g = dir0 + j;
-        if (g < NV)
-          outL[g] = to_d(sacc);
-        else if (n >= 0)
-          outR[g - NV] = to_d(sacc);
+        for (int j = 0; j < ND; ++j) {
+          S sacc = cst<S>(0.0);
+#pragma unroll
+          for (int i = 0; i < NV; ++i) sacc = madd(F[i].d[j], Kw[i], sacc);
+          const int g = dir0 + j;
+          if (g < NV)
+            outL[g] = to_d(sacc);
+          else if (n >= 0)
+            outR[g - NV] = to_d(sacc);
+        }
       }
     }
   }

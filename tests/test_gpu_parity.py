@@ -32,7 +32,9 @@ def rel(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max())
 
 
-def _setup(T, mesh, order, nvar, flux, precision=0, linear=False, variant=0):
+def _setup(T, mesh, order, nvar, flux, precision=0, linear=False, variant=2):
+    """variant 2 is the library default (the TMA kernels; the W form on the
+    FP64 path for Euler, the halo kernel for scalar and native FP64)."""
     t = T.Teno(device=0).load(mesh)
     t.precompute_stencils(order=order, n_var=nvar, flux=flux, precision=precision,
                           linear=int(linear), recon_variant=variant)
@@ -40,7 +42,7 @@ def _setup(T, mesh, order, nvar, flux, precision=0, linear=False, variant=0):
 
 
 def _check_residual(T, oracle_mod, mesh, U, order, nvar, flux, linear=False, tol=TOL,
-                    precision=0, variant=0):
+                    precision=0, variant=2):
     t = _setup(T, mesh, order, nvar, flux, linear=linear, precision=precision, variant=variant)
     t.set_state(U)
     R, sel = t.residual(want_sel=True)
