@@ -50,8 +50,8 @@ def lib():
         L.oracle_rk3_step.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double]
         L.oracle_residual_vjp.argtypes = [C.c_void_p, _dp, C.c_double, _dp, _dp, C.c_void_p]
         L.oracle_rk3_vjp.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp, _dp]
-        L.oracle_flux.argtypes = [C.c_void_p, _dp, _dp, C.c_double, C.c_double, _dp, C.c_void_p,
-                                  C.c_void_p]
+        L.oracle_flux.argtypes = [C.c_void_p, _dp, _dp, C.c_double, C.c_double, C.c_double,
+                                  C.c_double, _dp, C.c_void_p, C.c_void_p]
         L.oracle_geometry.argtypes = [C.c_void_p, _dp, _dp, _ip]
         L.oracle_gauss_legendre.argtypes = [C.c_int, _dp, _dp]
     return _lib
@@ -75,7 +75,10 @@ class Oracle:
 
     def __init__(self, mesh, order: int = 3, n_var: int = 1, flux: int = FLUX_UPWIND,
                  linear: bool = False, ct: float = 1e-6, eps: float = 1e-12, gamma: float = 1.4,
-                 adv=(1.0, 1.0), nq: int | None = None):
+                 adv=(1.0, 1.0), nq: int | None = None, rotation=None):
+        """rotation: (x_c, y_c, omega) for scalar advection by the rigid rotation
+        v = omega (-(y - y_c), x - x_c) (the solid-body case of Sec. 5 is
+        (0.5, 0.5, 1.0)); otherwise the constant velocity adv."""
         self.mesh = mesh
         self.order, self.n_var = order, n_var
         self.m = n_unknowns(order)
@@ -85,8 +88,11 @@ class Oracle:
         self._tri = np.ascontiguousarray(mesh.tri, dtype=np.int32)
         self._bf = np.ascontiguousarray(mesh.bface, dtype=np.int32)
         self._per = None if mesh.period is None else np.asarray(mesh.period, dtype=np.float64)
-        iopt = np.array([order, self.nq, n_var, flux, int(linear)], dtype=np.int32)
-        dopt = np.array([ct, eps, gamma, adv[0], adv[1]], dtype=np.float64)
+        rot = (0.0, 0.0, 0.0) if rotation is None else tuple(rotation)
+        iopt = np.array([order, self.nq, n_var, flux, int(linear), int(rotation is not None)],
+                        dtype=np.int32)
+        dopt = np.array([ct, eps, gamma, adv[0], adv[1], rot[0], rot[1], rot[2]],
+                        dtype=np.float64)
         st = C.c_int32(0)
         self._h = lib().oracle_new(self._xy.shape[0], self._xy, self._tri.shape[0], self._tri,
                                    self._bf.shape[0], _opt(self._bf if len(self._bf) else None),
@@ -192,16 +198,19 @@ class Oracle:
         self._chk(lib().oracle_rk3_vjp(self._h, Un, time, dt, lam, out), "rk3_vjp")
         return out
 
-    def flux(self, UL, UR, nx: float, ny: float, jac: bool = False):
+    def flux(self, UL, UR, nx: float, ny: float, jac: bool = False, x: float = 0.0,
+             y: float = 0.0):
+        """numerical flux at face point (x, y) (the point matters only for the
+        rotation field of scalar advection)"""
         UL = np.ascontiguousarray(UL, dtype=np.float64)
         UR = np.ascontiguousarray(UR, dtype=np.float64)
         F = np.empty(self.n_var)
         if jac:
             JL = np.empty((self.n_var, self.n_var))
             JR = np.empty((self.n_var, self.n_var))
-            lib().oracle_flux(self._h, UL, UR, nx, ny, F, _opt(JL), _opt(JR))
+            lib().oracle_flux(self._h, UL, UR, nx, ny, x, y, F, _opt(JL), _opt(JR))
             return F, JL, JR
-        lib().oracle_flux(self._h, UL, UR, nx, ny, F, None, None)
+        lib().oracle_flux(self._h, UL, UR, nx, ny, x, y, F, None, None)
         return F
 
     def geometry(self):

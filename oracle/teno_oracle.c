@@ -26,7 +26,8 @@
  *   Eq. (fv_governing_equation_semi_discrete): Gauss-point evaluation on the
  *       faces, rotated flux F^n = T^-1 F^x(T U) (Sec. 4.1) with HLL and the
  *       Einfeldt wave speeds (Sec. 4.2, Eq. wavespeed), HLLC (cited in Sec. 5)
- *       or upwind for scalar advection; residual gather;
+ *       or upwind for scalar advection by a constant velocity or by the rigid
+ *       rotation of the solid-body case (Sec. 5); residual gather;
  *   Eq. (fv_time_discretization_01): SSP-RK3.
  * The discrete adjoint (vector-Jacobian product) of a residual and of an
  * SSP-RK3 step, with the selection and the flux branches frozen at the
@@ -169,6 +170,8 @@ typedef struct {
   double L[2];
   int order, r, m, ns, nq, nvar, flux, linear;
   double ct, eps, gam, adv[2], time;
+  int field;      /* scalar advection velocity: 0 constant adv, 1 rigid rotation */
+  double rot[3];  /* rotation centre (x, y) and angular velocity omega */
   /* geometry (user cell order) */
   double* P;    /* [nc][3][2] unwrapped vertices */
   double* cen;  /* [nc][2] */
@@ -825,10 +828,20 @@ static void unrotate(double nx, double ny, const double* W, double* U) {
 }
 
 /* numerical flux through a face with unit normal (nx, ny) from L to R */
+/* normal advection speed v(x, y) . n of the scalar equation: a constant
+ * velocity, or the rigid rotation v = omega (-(y - y_c), x - x_c) of the
+ * solid-body rotation case (Sec. 5, v = (0.5 - y, x - 0.5)) */
+static double adv_normal(const omesh* M, double x, double y, double nx, double ny) {
+  if (M->field == 1)
+    return M->rot[2] * (-(y - M->rot[1]) * nx + (x - M->rot[0]) * ny);
+  return M->adv[0] * nx + M->adv[1] * ny;
+}
+
+/* numerical flux at a face point (x, y) with unit normal (nx, ny) */
 static void num_flux(const omesh* M, const double* UL, const double* UR, double nx, double ny,
-                     double* F) {
+                     double x, double y, double* F) {
   if (M->flux == FLUX_UPWIND) {
-    double an = M->adv[0] * nx + M->adv[1] * ny;
+    double an = adv_normal(M, x, y, nx, ny);
     F[0] = an * (an >= 0.0 ? UL[0] : UR[0]);
     return;
   }
@@ -939,9 +952,9 @@ static void euler_fx_d(double g, const dual* W, dual* F) {
 }
 
 static void num_flux_d(const omesh* M, const dual* UL, const dual* UR, double nx, double ny,
-                       dual* F) {
+                       double x, double y, dual* F) {
   if (M->flux == FLUX_UPWIND) {
-    double an = M->adv[0] * nx + M->adv[1] * ny;
+    double an = adv_normal(M, x, y, nx, ny);
     F[0] = dscale(an, an >= 0.0 ? UL[0] : UR[0]);
     return;
   }
@@ -1009,7 +1022,7 @@ static void num_flux_d(const omesh* M, const dual* UL, const dual* UR, double nx
 
 /* Jacobians dF/dUL and dF/dUR, [nvar][nvar] each, row = flux component */
 static void flux_jac(const omesh* M, const double* UL, const double* UR, double nx, double ny,
-                     double* JL, double* JR) {
+                     double x, double y, double* JL, double* JR) {
   int nv = M->nvar;
   dual L[4], R[4], F[4];
   for (int k = 0; k < 4; ++k) L[k] = R[k] = dc(0.0);
@@ -1019,7 +1032,7 @@ static void flux_jac(const omesh* M, const double* UL, const double* UR, double 
     L[k].d[k] = 1.0;
     R[k].d[nv + k] = 1.0;
   }
-  num_flux_d(M, L, R, nx, ny, F);
+  num_flux_d(M, L, R, nx, ny, x, y, F);
   for (int i = 0; i < nv; ++i)
     for (int k = 0; k < nv; ++k) {
       JL[i * nv + k] = F[i].d[k];
@@ -1085,6 +1098,10 @@ void* oracle_new(int64_t nv, const double* xy, int64_t nc, const int32_t* tri, i
   M->gam = dopt[2];
   M->adv[0] = dopt[3];
   M->adv[1] = dopt[4];
+  M->field = iopt[5];
+  M->rot[0] = dopt[5];
+  M->rot[1] = dopt[6];
+  M->rot[2] = dopt[7];
   M->r = M->order - 1;
   M->m = (M->r + 1) * (M->r + 2) / 2 - 1;
   M->ns = 2 * (M->m + 1);
@@ -1255,7 +1272,7 @@ static void face_flux(const omesh* M, int64_t c, int e, const double* U, const r
       eval_point(M, n, U, Rn, x, y, UR);
     else
       ghost_state(M, M->fbc[3 * c + e], UL, nx, ny, x, y, UR);
-    num_flux(M, UL, UR, nx, ny, F);
+    num_flux(M, UL, UR, nx, ny, x, y, F);
     for (int v = 0; v < M->nvar; ++v) {
       K[v] += M->gw[k] * F[v];
       if (ULq) ULq[k * M->nvar + v] = UL[v];
@@ -1378,7 +1395,16 @@ double oracle_cfl_dt(void* h, const double* U, double cfl) {
   double best = 1e300;
   for (int64_t c = 0; c < M->nc; ++c) {
     double s;
-    if (M->nvar == 1) {
+    if (M->nvar == 1 && M->field == 1) {
+      /* largest speed over the cell: at the vertex farthest from the centre */
+      double rmax = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        double dx = M->P[6 * c + 2 * k] - M->rot[0], dy = M->P[6 * c + 2 * k + 1] - M->rot[1];
+        double r = sqrt(dx * dx + dy * dy);
+        if (r > rmax) rmax = r;
+      }
+      s = fabs(M->rot[2]) * rmax;
+    } else if (M->nvar == 1) {
       s = sqrt(M->adv[0] * M->adv[0] + M->adv[1] * M->adv[1]);
     } else {
       double rho = U[c], u = U[M->nc + c] / rho, v = U[2 * M->nc + c] / rho;
@@ -1449,7 +1475,7 @@ int oracle_residual_vjp(void* h, const double* U, double time, const double* w, 
           eval_point(M, n, U, &RC[n], x, y, UR);
         else
           ghost_state(M, M->fbc[3 * c + e], UL, nx, ny, x, y, UR);
-        flux_jac(M, UL, UR, nx, ny, JL, JR);
+        flux_jac(M, UL, UR, nx, ny, x, y, JL, JR);
         double wk = M->gw[k] * len;
         double bl[4] = {0, 0, 0, 0}, br[4] = {0, 0, 0, 0};
         for (int i = 0; i < nvar; ++i)
@@ -1583,12 +1609,13 @@ int oracle_rk3_vjp(void* h, const double* Un, double time, double dt, const doub
   return rc;
 }
 
-/* flux access for pins: F [nvar], JL/JR [nvar*nvar] optional */
-void oracle_flux(void* h, const double* UL, const double* UR, double nx, double ny, double* F,
-                 double* JL, double* JR) {
+/* flux access for pins at face point (x, y): F [nvar], JL/JR [nvar*nvar]
+ * optional */
+void oracle_flux(void* h, const double* UL, const double* UR, double nx, double ny, double x,
+                 double y, double* F, double* JL, double* JR) {
   omesh* M = (omesh*)h;
-  num_flux(M, UL, UR, nx, ny, F);
-  if (JL && JR) flux_jac(M, UL, UR, nx, ny, JL, JR);
+  num_flux(M, UL, UR, nx, ny, x, y, F);
+  if (JL && JR) flux_jac(M, UL, UR, nx, ny, x, y, JL, JR);
 }
 
 void oracle_geometry(void* h, double* area, double* cen, int32_t* fnbr) {

@@ -67,7 +67,7 @@ struct teno_ctx {
   std::vector<int32_t> st_large, st_small;  // user ids, [nc][ns], [nc][36]
   // device data
   DeviceMesh dm;
-  DevBuf b_halo_off, b_halo_ids, b_halo_loc, b_g32, b_wq, b_psi;
+  DevBuf b_halo_off, b_halo_ids, b_halo_loc, b_g32, b_wq, b_psi, b_cspeed;
   DevBuf b_ahat, b_nbr, b_smask, b_fcells, b_fedges, b_fgeom, b_fgeom2, b_cfaces, b_inv_area, b_cfl_len,
       b_perm;
   DevBuf b_U, b_U1, b_U2, b_R, b_tmp, b_Uq, b_K, b_sel, b_sel_ovr, b_maxlam, b_flag;
@@ -859,6 +859,27 @@ int run_precompute(teno_ctx* ctx) {
   dm.gamma = p.gamma;
   dm.adv_x = p.adv_x;
   dm.adv_y = p.adv_y;
+  dm.adv_field = p.adv_field;
+  dm.adv_cx = p.adv_cx;
+  dm.adv_cy = p.adv_cy;
+  dm.adv_omega = p.adv_omega;
+  dm.cell_speed = nullptr;
+  if (p.n_var == 1 && p.adv_field == 1) {
+    // CFL speed: |omega| times the largest vertex distance from the centre
+    std::vector<double> sp(npad, 0.0);
+    for (int64_t c = 0; c < nc; ++c) {
+      const double* P = &ctx->P[6 * (size_t)ctx->perm[c]];
+      double rmax = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        const double dx = P[2 * k] - p.adv_cx, dy = P[2 * k + 1] - p.adv_cy;
+        rmax = std::max(rmax, std::sqrt(dx * dx + dy * dy));
+      }
+      sp[c] = std::fabs(p.adv_omega) * rmax;
+    }
+    int e3 = upload(ctx, ctx->b_cspeed, sp.data(), sp.size() * sizeof(double));
+    if (e3) return e3;
+    dm.cell_speed = (const double*)ctx->b_cspeed.p;
+  }
   dm.cfl = p.cfl;
   dm.variant = p.recon_variant;
   dm.halo = HaloArgs{};
@@ -915,8 +936,18 @@ int upload_mesh(teno_ctx* ctx) {
       fgeom.push_back(dy / len);
       fgeom.push_back(-dx / len);
       fgeom.push_back(len);
-      fgeom.push_back(P[2 * e]);
-      fgeom.push_back(P[2 * e + 1]);
+      // start point of the edge in the frame of the adjacent cell with the
+      // smaller user id (differs from the owner's frame only across a
+      // periodic wrap): there the neighbour's edge runs the other way
+      if (n >= 0 && nu < u) {
+        const double* Pn = &ctx->P[6 * (size_t)nu];
+        const int s0 = (ctx->fedge[3 * u + e] + 1) % 3;
+        fgeom.push_back(Pn[2 * s0]);
+        fgeom.push_back(Pn[2 * s0 + 1]);
+      } else {
+        fgeom.push_back(P[2 * e]);
+        fgeom.push_back(P[2 * e + 1]);
+      }
       cfaces[3 * c + e] = (int32_t)(2 * f);
       if (n >= 0) cfaces[3 * n + ctx->fedge[3 * u + e]] = (int32_t)(2 * f + 1);
     }
@@ -1132,6 +1163,10 @@ void teno_default_params(teno_params* p) {
   p->gamma = 1.4;
   p->adv_x = 1.0;
   p->adv_y = 1.0;
+  p->adv_field = 0;
+  p->adv_cx = 0.5;
+  p->adv_cy = 0.5;
+  p->adv_omega = 1.0;
   p->cfl = 0.4;
 }
 
@@ -1177,7 +1212,7 @@ int teno_destroy(teno_ctx* ctx) {
   }
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  DevBuf* bufs[] = {&ctx->b_halo_off, &ctx->b_halo_ids, &ctx->b_halo_loc, &ctx->b_g32, &ctx->b_wq, &ctx->b_psi, &ctx->b_ahat, &ctx->b_nbr, &ctx->b_smask, &ctx->b_fcells, &ctx->b_fedges,
+  DevBuf* bufs[] = {&ctx->b_halo_off, &ctx->b_halo_ids, &ctx->b_halo_loc, &ctx->b_g32, &ctx->b_wq, &ctx->b_psi, &ctx->b_cspeed, &ctx->b_ahat, &ctx->b_nbr, &ctx->b_smask, &ctx->b_fcells, &ctx->b_fedges,
                     &ctx->b_fgeom, &ctx->b_fgeom2, &ctx->b_cfaces, &ctx->b_inv_area, &ctx->b_cfl_len,
                     &ctx->b_perm, &ctx->b_U, &ctx->b_U1, &ctx->b_U2, &ctx->b_R, &ctx->b_tmp,
                     &ctx->b_Uq, &ctx->b_K, &ctx->b_sel, &ctx->b_sel_ovr, &ctx->b_maxlam,
@@ -1241,7 +1276,9 @@ int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
       p->precision < TENO_FP64 || p->precision > TENO_FP64_NATIVE || p->flux < 0 ||
       p->flux > 2 || (p->n_var == 1) != (p->flux == TENO_FLUX_UPWIND) || !(p->ct > 0) ||
       !(p->eps > 0) || !(p->gamma > 1.0) || !(p->cfl > 0) || p->recon_variant < 0 ||
-      p->recon_variant > 2)
+      p->recon_variant > 2 || p->adv_field < 0 || p->adv_field > 1 ||
+      (p->adv_field == 1 && (p->n_var != 1 || !std::isfinite(p->adv_omega) ||
+                             !std::isfinite(p->adv_cx) || !std::isfinite(p->adv_cy))))
     return fail(ctx, TENO_EINVAL, "precompute: bad parameters");
   const int nq_default = p->order <= 4 ? 2 : 3;
   if (p->nq != 0 && p->nq != nq_default)

@@ -359,6 +359,16 @@ __device__ __forceinline__ void euler_riemann(const T* UL, const T* UR, const Ri
   F[3] = Fx[3];
 }
 
+// normal advection speed of the scalar equation at face point (x, y): the
+// constant velocity, or the rigid rotation omega (-(y - y_c), x - x_c) of the
+// solid-body case (Sec. 5)
+__device__ __forceinline__ double adv_normal(int field, double ax, double ay, double cx,
+                                             double cy, double om, double x, double y,
+                                             double nx, double ny) {
+  if (field == 1) return om * (-(y - cy) * nx + (x - cx) * ny);
+  return ax * nx + ay * ny;
+}
+
 // a <= b in the order the forward solver's min/max use (pairs: lexicographic)
 template <typename T>
 __device__ __forceinline__ bool le_ord(const T& a, const T& b) {
@@ -1898,6 +1908,8 @@ struct FaceArgs {
   const float2* f_geom2;  // [n_face][3] nx, ny, |A| as (hi, lo) pairs
   int64_t n_face;
   double gamma, adv_x, adv_y, time;
+  int adv_field;
+  double adv_cx, adv_cy, adv_omega;
   double gw[kMaxNq], gt[kMaxNq];
   float2 gw2[kMaxNq], g2, gm12;  // Gauss weights, gamma, gamma - 1 as pairs
 };
@@ -1970,7 +1982,10 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const FaceArgs a, const 
       for (int v = 0; v < NV; ++v) UR[v] = UL[v];
     }
     if constexpr (NV == 1) {
-      const double an = a.adv_x * nx + a.adv_y * ny;
+      const double xq = a.f_geom[5 * f + 3] - ny * len * a.gt[k];
+      const double yq = a.f_geom[5 * f + 4] + nx * len * a.gt[k];
+      const double an = adv_normal(a.adv_field, a.adv_x, a.adv_y, a.adv_cx, a.adv_cy,
+                                   a.adv_omega, xq, yq, nx, ny);
       F[0] = cst<T>(an) * (an >= 0.0 ? UL[0] : UR[0]);
     } else {
       euler_riemann<T>(UL, UR, rk, FLUX == TENO_FLUX_HLLC, F);
@@ -2066,13 +2081,14 @@ __global__ void __launch_bounds__(256) max_lambda_kernel(const double* __restric
                                                          const double* __restrict__ cfl_len,
                                                          int64_t n_cell, int64_t n_pad,
                                                          double gamma, double adv_speed,
+                                                         const double* __restrict__ cell_speed,
                                                          unsigned long long* out) {
   double lam = 0.0;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cell;
        c += (int64_t)gridDim.x * blockDim.x) {
     double s;
     if constexpr (NV == 1) {
-      s = adv_speed;
+      s = cell_speed ? cell_speed[c] : adv_speed;
     } else {
       const double rho = U[c], u = U[n_pad + c] / rho, v = U[2 * n_pad + c] / rho;
       const double p = (gamma - 1.0) * (U[3 * n_pad + c] - 0.5 * rho * (u * u + v * v));
@@ -2135,6 +2151,8 @@ struct VjpArgs {
   const double* f_geom;
   const float2* f_geom2;
   float2 g2, gm12;
+  int adv_field;
+  double adv_cx, adv_cy, adv_omega;
   const double* inv_area;
   int64_t n_face, n_pad;
   double gamma, adv_x, adv_y, time;
@@ -2242,7 +2260,9 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
           for (int v = 0; v < NV; ++v) UR[v] = UL[v];
         }
         if constexpr (NV == 1) {
-          const double an = a.adv_x * nx + a.adv_y * ny;
+          const double yq = a.f_geom[5 * f + 4] + nx * len * a.gt[k];
+          const double an = adv_normal(a.adv_field, a.adv_x, a.adv_y, a.adv_cx, a.adv_cy,
+                                       a.adv_omega, x, yq, nx, ny);
           F[0] = an * (an >= 0.0 ? UL[0] : UR[0]);
         } else {
           euler_riemann<D>(UL, UR, rk, FLUX == TENO_FLUX_HLLC, F);
@@ -2609,6 +2629,10 @@ static FaceArgs face_args(const DeviceMesh& dm, double time) {
   a.gamma = dm.gamma;
   a.adv_x = dm.adv_x;
   a.adv_y = dm.adv_y;
+  a.adv_field = dm.adv_field;
+  a.adv_cx = dm.adv_cx;
+  a.adv_cy = dm.adv_cy;
+  a.adv_omega = dm.adv_omega;
   a.time = time;
   for (int k = 0; k < kMaxNq; ++k) {
     a.gw[k] = dm.gw[k];
@@ -2687,10 +2711,12 @@ cudaError_t launch_max_lambda(const DeviceMesh& dm, const double* U, double* max
   const double adv = sqrt(dm.adv_x * dm.adv_x + dm.adv_y * dm.adv_y);
   if (dm.n_var == 1)
     max_lambda_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(
-        U, dm.cfl_len, dm.n_cell, dm.n_pad, dm.gamma, adv, (unsigned long long*)max_lam);
+        U, dm.cfl_len, dm.n_cell, dm.n_pad, dm.gamma, adv, dm.cell_speed,
+        (unsigned long long*)max_lam);
   else
     max_lambda_kernel<4><<<(unsigned)blocks, 256, 0, st>>>(
-        U, dm.cfl_len, dm.n_cell, dm.n_pad, dm.gamma, adv, (unsigned long long*)max_lam);
+        U, dm.cfl_len, dm.n_cell, dm.n_pad, dm.gamma, adv, nullptr,
+        (unsigned long long*)max_lam);
   return cudaGetLastError();
 }
 
@@ -2736,6 +2762,10 @@ cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const dou
   a.gamma = dm.gamma;
   a.adv_x = dm.adv_x;
   a.adv_y = dm.adv_y;
+  a.adv_field = dm.adv_field;
+  a.adv_cx = dm.adv_cx;
+  a.adv_cy = dm.adv_cy;
+  a.adv_omega = dm.adv_omega;
   a.time = time;
   for (int k = 0; k < kMaxNq; ++k) {
     a.gw[k] = dm.gw[k];

@@ -191,6 +191,26 @@ def advection_sine_product(x, y):
     return np.sin(2.0 * np.pi * x) * np.sin(2.0 * np.pi * y)
 
 
+def solid_bodies(x, y):
+    """Initial field of the solid-body rotation case (Sec. 5, table of the
+    rotation case): a cosine hump centred (0.25, 0.5), a sharp cone at
+    (0.5, 0.25) and a slotted cylinder at (0.5, 0.75), each of radius 0.15.
+    Readings of the garbled table: r is the distance to the body's centre
+    divided by r_0 and capped at 1, so every body is zero outside its disc
+    (the hump as 1/4 (1 + cos(pi r)), the cone as 1 - r); the cylinder is 1 in
+    its disc except the slot |x - x_0| < 0.025, y < 0.85."""
+    r0 = 0.15
+
+    def rr(x0, y0):
+        return np.minimum(np.hypot(x - x0, y - y0), r0) / r0
+
+    hump = 0.25 * (1.0 + np.cos(np.pi * rr(0.25, 0.5)))
+    cone = 1.0 - rr(0.5, 0.25)
+    inside = np.hypot(x - 0.5, y - 0.75) <= r0
+    cyl = np.where(inside & ((np.abs(x - 0.5) >= 0.025) | (y >= 0.85)), 1.0, 0.0)
+    return hump + cone + cyl
+
+
 def isentropic_vortex(x, y, t: float = 0.0, strength: float = 5.0, gamma: float = GAMMA,
                       L: float = 10.0, images: int = 1):
     """Isentropic vortex of Sec. 5.2 (centre (5,5), free stream (1,1,1,1)),

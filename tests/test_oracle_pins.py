@@ -523,12 +523,13 @@ def test_cfl_dt_definition(oracle_mod):
 
 
 # ------------------------------------------------------ brute-force residual
-def _brute_residual(mesh, U, order, ct=1e-6, eps=1e-12, adv=(1.0, 1.0)):
+def _brute_residual(mesh, U, order, ct=1e-6, eps=1e-12, adv=(1.0, 1.0), vel=None):
     """Scalar-advection residual written straight from the paper with library
     routines: stencils by the brute-force restatement, least squares by
     numpy.linalg.lstsq, integrals by a 6x6 collapsed Gauss rule, beta from the
     derivatives of the polynomial at quadrature points, the cutoff with
-    divisions as printed, upwind flux at 2 Gauss-Legendre points per edge."""
+    divisions as printed, upwind flux at 2 Gauss-Legendre points per edge.
+    vel(X) -> velocity at a face point (default: the constant adv)."""
     r = order - 1
     ex = []
     for d in range(1, r + 1):
@@ -616,21 +617,62 @@ def _brute_residual(mesh, U, order, ct=1e-6, eps=1e-12, adv=(1.0, 1.0)):
             owner.setdefault(key, []).append((t, e))
     R = np.zeros(mesh.n_cell)
     for key, sides in owner.items():
-        (t, e), (n, _) = sides
+        (t, e), (n, _) = sorted(sides)  # the face's points in the frame of the smaller id
         P0, P1 = V[t, e], V[t, (e + 1) % 3]
         dvec = P1 - P0
         length = np.hypot(*dvec)
         nrm = np.array([dvec[1], -dvec[0]]) / length
-        an = adv[0] * nrm[0] + adv[1] * nrm[1]
         K = 0.0
         for x, w in zip(gl, gwl):
             X = P0 + 0.5 * (x + 1) * dvec
+            v = adv if vel is None else vel(X)
+            an = v[0] * nrm[0] + v[1] * nrm[1]
             K += 0.5 * w * an * (value(t, X) if an >= 0 else value(n, X))
         R[t] -= K * length
         R[n] += K * length
     area = 0.5 * np.abs(np.cross(np.c_[V[:, 1] - V[:, 0], np.zeros(len(V))],
                                  np.c_[V[:, 2] - V[:, 0], np.zeros(len(V))])[:, 2])
     return R / area
+
+
+def _bodies(x, y):
+    """the three solid bodies of the rotation case (slotted cylinder, cone,
+    cosine hump); each vanishes outside its disc of radius 0.15"""
+    from paper_2105_02127_gb300 import inputs
+    return inputs.solid_bodies(x, y)
+
+
+def test_rotation_residual_brute_force(oracle_mod):
+    """Scalar advection by the rigid rotation v = (0.5 - y, x - 0.5) (Sec. 5,
+    solid-body case): the TENO3 residual of the bodies against the brute-force
+    restatement with the velocity evaluated at every Gauss point."""
+    from paper_2105_02127_gb300 import inputs
+    mesh = _mesh(12, seed=1240)
+    U = inputs.cell_average(mesh, _bodies)[0]
+    o = oracle_mod.Oracle(mesh, order=3, rotation=(0.5, 0.5, 1.0))
+    R, sel, _ = o.residual(U[None].copy())
+    assert (sel != 8).mean() > 0.05
+    Rb = _brute_residual(mesh, U, 3, vel=lambda X: (0.5 - X[1], X[0] - 0.5))
+    np.testing.assert_allclose(R[0], Rb, rtol=0, atol=1e-10 * np.abs(Rb).max())
+
+
+def test_rotation_freestream_and_cfl(oracle_mod):
+    """A divergence-free linear velocity with Gauss quadrature exact for it: a
+    constant state has zero residual on a bounded mesh (outflow copies); the
+    CFL step uses the speed at the vertex farthest from the centre."""
+    from paper_2105_02127_gb300 import inputs
+    mesh = inputs.jittered_mesh(10, 9, 1.0, 1.0, seed=1241, periodic=False)  # outflow sides
+    for order in (3, 5):
+        o = oracle_mod.Oracle(mesh, order=order, rotation=(0.4, 0.55, 2.0))
+        R, _, _ = o.residual(np.full((1, mesh.n_cell), 1.7))
+        assert np.abs(R).max() < 1e-12
+    V = mesh.unwrapped_vertices()
+    area = 0.5 * np.abs((V[:, 1, 0] - V[:, 0, 0]) * (V[:, 2, 1] - V[:, 0, 1])
+                        - (V[:, 2, 0] - V[:, 0, 0]) * (V[:, 1, 1] - V[:, 0, 1]))
+    perim = sum(np.hypot(*(V[:, (k + 1) % 3] - V[:, k]).T) for k in range(3))
+    rmax = np.hypot(V[..., 0] - 0.4, V[..., 1] - 0.55).max(axis=1)
+    dt = 0.3 * np.min(4 * area / perim / (2.0 * rmax))
+    assert abs(o.cfl_dt(np.zeros((1, mesh.n_cell)), 0.3) - dt) <= 1e-14 * dt
 
 
 def test_residual_brute_force_on_jump(oracle_mod):
