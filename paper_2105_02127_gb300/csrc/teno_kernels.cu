@@ -715,6 +715,27 @@ __device__ __forceinline__ bool chi_keep32(const float* t, int k, int mask, floa
   return chi >= ct;
 }
 
+// As chi_keep32, for smoothness indicators known only to within a relative
+// bound rho each (t_j = beta_j + eps in [t32_j / (1 + rho), t32_j / (1 - rho)]
+// or tighter): every ratio t_k / t_j then lies within a factor
+// (1 + rho) / (1 - rho) of its FP32 value, so chi lies within the factor
+// f = ((1 + rho) / (1 - rho))^6 of the FP32 chi (times 1 + 1e-4 for the FP32
+// evaluation itself); *near is set when that interval contains C_T.
+__device__ __forceinline__ bool chi_keep32_bound(const float* t, int k, int mask, float ct,
+                                                 float f, bool* near) {
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j <= kSmallK; ++j) {
+    if (!((mask >> j) & 1)) continue;
+    float r = t[k] / t[j];
+    float r2 = r * r;
+    s += r2 * r2 * r2;
+  }
+  const float chi = 1.f / s;
+  if (!(chi > ct * f) && !(chi * f < ct)) *near = true;
+  return chi >= ct;
+}
+
 // ------------------------------------------------------------ reconstruction
 // thread (lane, v, z): cell tile*32 + lane, variable v.  A warp covers the 32
 // cells of one tile for one variable, so every matrix entry is one coalesced
@@ -1549,15 +1570,18 @@ struct WPlan {
 };
 
 // Upper bound of |beta_fp32 - beta| relative to beta_fp32 + eps for m FP32
-// coefficients from n-term FP32 dot products whose absolute error is at most
-// (n + 6) u e_abs each (e_abs = sum_s colsum_s |d_s|, u = 2^-24), including
-// the rounding of the FP32 sum of squares.  Returns a value >= 1 when the
-// bound is not informative.
+// coefficients a32_l from n-term FP32 dot products.  Coefficient l errs by at
+// most e_l = (n + 6) u S_l with S_l = sum_s |G_ls| |d_s| (u = 2^-24; the
+// stored matrix and difference roundings included), and sum_l S_l = e_abs =
+// sum_s colsum_s |d_s|.  With E = sum_l e_l, Cauchy-Schwarz gives
+// |sum a32^2 - sum a^2| <= sum e_l (2 |a32_l| + e_l) <= 2 E sqrt(beta32) + E^2;
+// the FP32 sum of squares adds (m + 2) u beta32.  Returns a value >= 1 when
+// the bound is not informative.
 __device__ __forceinline__ float beta_rel_bound(float beta32, float e_abs, int n, int m,
                                                 float eps) {
   const float u = 5.9604645e-8f;
-  const float em = (float)(n + 6) * u * e_abs * 1.0001f;
-  const float eb = (float)(m + 2) * u * beta32 + em * (2.f * sqrtf((float)m * beta32) + (float)m * em);
+  const float E = (float)(n + 6) * u * e_abs * 1.0001f;
+  const float eb = (float)(m + 2) * u * beta32 + E * (2.f * sqrtf(beta32) + E);
   const float t = beta32 + eps;
   if (!(eb < 0.5f * t)) return 1.f;
   return eb / (t - eb);
@@ -1808,17 +1832,19 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
               rho = fmaxf(rho, beta_rel_bound(q, eS[k], kSmallN, kSmallM, (float)a.eps));
           }
         }
-        // chi moves by at most ~12 rho (relative) under the beta bounds
-        bool near = !(rho < 1e-2f);
-        const float band = fmaxf(1e-3f, 15.f * rho);
+        // chi lies within the factor f of its FP32 value under the beta bounds
+        bool near = !(rho < 0.25f);
+        const float q = (1.f + rho) / (1.f - fminf(rho, 0.5f));
+        const float q2 = q * q;
+        const float f = q2 * q2 * q2 * 1.0001f;
         const float ct = (float)a.ct;
-        if (chi_keep32(t, kSmallK, present | 8, ct, &near, band)) {
+        if (chi_keep32_bound(t, kSmallK, present | 8, ct, f, &near)) {
           sel = 8;
         } else {
           sel = 0;
 #pragma unroll
           for (int k = 0; k < kSmallK; ++k)
-            if (((present >> k) & 1) && chi_keep32(t, k, present & 7, ct, &near, band))
+            if (((present >> k) & 1) && chi_keep32_bound(t, k, present & 7, ct, f, &near))
               sel |= (uint8_t)(1u << k);
         }
         if (near) sel = w_select_pairs<M, NS>(A, nb, st, u0s, present, a.ct, a.eps);
