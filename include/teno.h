@@ -94,18 +94,21 @@ typedef struct teno_params {
   double adv_x, adv_y; /* advection velocity for n_var = 1 and adv_field = 0 */
   double cfl;        /* CFL number for teno_rk3_step with dt <= 0 */
   int32_t adv_field; /* n_var = 1: 0 the constant velocity (adv_x, adv_y); 1 the rigid
-                        rotation v = adv_omega (-(y - adv_cy), x - adv_cx) of the
-                        solid-body case (Sec. 5: centre (0.5, 0.5), omega 1).  The
-                        velocity is evaluated at every face Gauss point; on a periodic
-                        mesh a face on the wrap takes its points in the frame of the
-                        adjacent cell with the smaller user id (the field itself is not
-                        periodic).  The CFL speed of a cell is |omega| times the largest
-                        distance of its vertices from the centre. */
+                        rotation v = adv_omega phi(r) (-(y - adv_cy), x - adv_cx) of the
+                        solid-body case (Sec. 5: centre (0.5, 0.5), omega 1), with the
+                        radial taper phi = 1 for r <= adv_r1, a smoothstep to 0 at adv_r2
+                        (no taper when adv_r2 <= adv_r1; an azimuthal field is
+                        divergence-free for any phi, and the taper makes it periodic).
+                        The velocity is evaluated at every face Gauss point; on a
+                        periodic mesh a face on the wrap takes its points in the frame of
+                        the adjacent cell with the smaller user id.  The CFL speed of a
+                        cell is |omega| times the largest r phi(r) over its vertices. */
   double adv_cx, adv_cy, adv_omega;
+  double adv_r1, adv_r2;
 } teno_params;
 
 /* Fills *p with the defaults above (order 5, n_var 4, HLL, FP64, recon_variant 2,
-   cfl 0.4, adv (1, 1), adv_field 0, rotation centre (0.5, 0.5), omega 1). */
+   cfl 0.4, adv (1, 1), adv_field 0, rotation centre (0.5, 0.5), omega 1, no taper). */
 void teno_default_params(teno_params* p);
 
 /* Create a context on CUDA device `device`, launching on `cuda_stream`

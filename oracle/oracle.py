@@ -75,10 +75,13 @@ class Oracle:
 
     def __init__(self, mesh, order: int = 3, n_var: int = 1, flux: int = FLUX_UPWIND,
                  linear: bool = False, ct: float = 1e-6, eps: float = 1e-12, gamma: float = 1.4,
-                 adv=(1.0, 1.0), nq: int | None = None, rotation=None):
-        """rotation: (x_c, y_c, omega) for scalar advection by the rigid rotation
-        v = omega (-(y - y_c), x - x_c) (the solid-body case of Sec. 5 is
-        (0.5, 0.5, 1.0)); otherwise the constant velocity adv."""
+                 adv=(1.0, 1.0), nq: int | None = None, rotation=None, scheme: str = "teno",
+                 cweno_dk: float = 1e4):
+        """rotation: (x_c, y_c, omega) or (x_c, y_c, omega, r1, r2) for scalar
+        advection by the rigid rotation v = omega phi(r) (-(y - y_c), x - x_c)
+        (the solid-body case of Sec. 5 is (0.5, 0.5, 1.0)), phi a smoothstep
+        taper from 1 at r1 to 0 at r2 (none when omitted); otherwise the
+        constant velocity adv."""
         self.mesh = mesh
         self.order, self.n_var = order, n_var
         self.m = n_unknowns(order)
@@ -88,11 +91,15 @@ class Oracle:
         self._tri = np.ascontiguousarray(mesh.tri, dtype=np.int32)
         self._bf = np.ascontiguousarray(mesh.bface, dtype=np.int32)
         self._per = None if mesh.period is None else np.asarray(mesh.period, dtype=np.float64)
-        rot = (0.0, 0.0, 0.0) if rotation is None else tuple(rotation)
-        iopt = np.array([order, self.nq, n_var, flux, int(linear), int(rotation is not None)],
-                        dtype=np.int32)
-        dopt = np.array([ct, eps, gamma, adv[0], adv[1], rot[0], rot[1], rot[2]],
-                        dtype=np.float64)
+        rot = (0.0, 0.0, 0.0, 0.0, 0.0) if rotation is None else tuple(rotation)
+        if len(rot) == 3:
+            rot = rot + (0.0, 0.0)
+        if scheme not in ("teno", "cweno"):
+            raise ValueError("scheme must be 'teno' or 'cweno'")
+        iopt = np.array([order, self.nq, n_var, flux, int(linear), int(rotation is not None),
+                         int(scheme == "cweno")], dtype=np.int32)
+        dopt = np.array([ct, eps, gamma, adv[0], adv[1], rot[0], rot[1], rot[2], rot[3], rot[4],
+                         cweno_dk], dtype=np.float64)
         st = C.c_int32(0)
         self._h = lib().oracle_new(self._xy.shape[0], self._xy, self._tri.shape[0], self._tri,
                                    self._bf.shape[0], _opt(self._bf if len(self._bf) else None),

@@ -29,6 +29,9 @@
  *       or upwind for scalar advection by a constant velocity or by the rigid
  *       rotation of the solid-body case (Sec. 5); residual gather;
  *   Eq. (fv_time_discretization_01): SSP-RK3.
+ * The CWENO reconstruction of Sec. 2.3 (Eqs. CWENO_reconstruction,
+ * CWENOweight, CWENOOptimalLinearweight/02) on the same stencils is the
+ * comparison scheme (scheme = 1).
  * The discrete adjoint (vector-Jacobian product) of a residual and of an
  * SSP-RK3 step, with the selection and the flux branches frozen at the
  * forward state, has no counterpart in the paper; flux Jacobians come from
@@ -170,8 +173,10 @@ typedef struct {
   double L[2];
   int order, r, m, ns, nq, nvar, flux, linear;
   double ct, eps, gam, adv[2], time;
+  int scheme;     /* 0 TENO, 1 CWENO (the comparison scheme of Sec. 2.3) */
+  double cw_dk;   /* CWENO d'_K (d_K = 1 - 1/d'_K) */
   int field;      /* scalar advection velocity: 0 constant adv, 1 rigid rotation */
-  double rot[3];  /* rotation centre (x, y) and angular velocity omega */
+  double rot[5];  /* rotation centre (x, y), angular velocity omega, taper radii r1 < r2 */
   /* geometry (user cell order) */
   double* P;    /* [nc][3][2] unwrapped vertices */
   double* cen;  /* [nc][2] */
@@ -726,7 +731,33 @@ static void reconstruct(const omesh* M, int64_t t, const double* U, const unsign
     }
     if (M->linear) margin = 1e300;
     if (sel_in) sel = sel_in[(int64_t)v * M->nc + t];
-    if (sel & 8) {
+    if (M->scheme == 1 && !M->linear) {
+      /* CWENO (Eqs. CWENO_reconstruction, CWENOweight,
+       * CWENOOptimalLinearweight/02): d_K = 1 - 1/d'_K, d_k = (1 - d_K)/K over the K
+       * present directional stencils, alpha = d / (beta + eps)^4, w = alpha / sum,
+       * P = (w_K / d_K)(P_K - sum_k d_k P_k) + sum_k w_k P_k */
+      int K = 0;
+      for (int k = 0; k < KSM; ++k) K += nsm[k] != 0;
+      double dK = K ? 1.0 - 1.0 / M->cw_dk : 1.0, dk = K ? (1.0 - dK) / K : 0.0;
+      double al[KSM + 1], asum = 0.0;
+      for (int k = 0; k < KSM; ++k) {
+        al[k] = nsm[k] ? dk / pow(beta[k] + M->eps, 4.0) : 0.0;
+        asum += al[k];
+      }
+      al[KSM] = dK / pow(beta[KSM] + M->eps, 4.0);
+      asum += al[KSM];
+      double wK = al[KSM] / asum;
+      for (int l = 0; l < M->m; ++l) {
+        double c = wK / dK * a[l];
+        if (l < MSM)
+          for (int k = 0; k < KSM; ++k)
+            if (nsm[k]) c += (al[k] / asum - wK / dK * dk) * as[k][l];
+        out->coef[v][l] = c;
+      }
+      for (int k = 0; k < KSM; ++k) w[k] = nsm[k] ? al[k] / asum : 0.0;
+      sel = 8;
+      margin = 1e300;
+    } else if (sel & 8) {
       for (int l = 0; l < M->m; ++l) out->coef[v][l] = a[l];
     } else {
       int nd = 0;
@@ -828,12 +859,25 @@ static void unrotate(double nx, double ny, const double* W, double* U) {
 }
 
 /* numerical flux through a face with unit normal (nx, ny) from L to R */
+/* radial taper of the rotation field: 1 for r <= r1, smoothstep to 0 at r2
+ * (no taper when r2 <= r1) */
+static double rot_taper(const omesh* M, double r) {
+  double r1 = M->rot[3], r2 = M->rot[4];
+  if (!(r2 > r1) || r <= r1) return 1.0;
+  if (r >= r2) return 0.0;
+  double s = (r - r1) / (r2 - r1);
+  return 1.0 - s * s * (3.0 - 2.0 * s);
+}
+
 /* normal advection speed v(x, y) . n of the scalar equation: a constant
- * velocity, or the rigid rotation v = omega (-(y - y_c), x - x_c) of the
- * solid-body rotation case (Sec. 5, v = (0.5 - y, x - 0.5)) */
+ * velocity, or the rigid rotation v = omega phi(r) (-(y - y_c), x - x_c) of the
+ * solid-body rotation case (Sec. 5, v = (0.5 - y, x - 0.5)) with the radial
+ * taper phi (azimuthal, hence divergence-free for any phi) */
 static double adv_normal(const omesh* M, double x, double y, double nx, double ny) {
-  if (M->field == 1)
-    return M->rot[2] * (-(y - M->rot[1]) * nx + (x - M->rot[0]) * ny);
+  if (M->field == 1) {
+    double dx = x - M->rot[0], dy = y - M->rot[1];
+    return M->rot[2] * rot_taper(M, sqrt(dx * dx + dy * dy)) * (-dy * nx + dx * ny);
+  }
   return M->adv[0] * nx + M->adv[1] * ny;
 }
 
@@ -1102,6 +1146,10 @@ void* oracle_new(int64_t nv, const double* xy, int64_t nc, const int32_t* tri, i
   M->rot[0] = dopt[5];
   M->rot[1] = dopt[6];
   M->rot[2] = dopt[7];
+  M->rot[3] = dopt[8];
+  M->rot[4] = dopt[9];
+  M->scheme = iopt[6];
+  M->cw_dk = dopt[10];
   M->r = M->order - 1;
   M->m = (M->r + 1) * (M->r + 2) / 2 - 1;
   M->ns = 2 * (M->m + 1);
@@ -1397,13 +1445,15 @@ double oracle_cfl_dt(void* h, const double* U, double cfl) {
     double s;
     if (M->nvar == 1 && M->field == 1) {
       /* largest speed over the cell: at the vertex farthest from the centre */
-      double rmax = 0.0;
+      double smax = 0.0;
       for (int k = 0; k < 3; ++k) {
         double dx = M->P[6 * c + 2 * k] - M->rot[0], dy = M->P[6 * c + 2 * k + 1] - M->rot[1];
         double r = sqrt(dx * dx + dy * dy);
-        if (r > rmax) rmax = r;
+        double sv = r * rot_taper(M, r);
+        if (sv > smax) smax = sv;
       }
-      s = fabs(M->rot[2]) * rmax;
+      s = fabs(M->rot[2]) * smax;
+      if (!(s > 0.0)) s = 1e-300; /* a cell at rest does not limit the step */
     } else if (M->nvar == 1) {
       s = sqrt(M->adv[0] * M->adv[0] + M->adv[1] * M->adv[1]);
     } else {

@@ -863,18 +863,29 @@ int run_precompute(teno_ctx* ctx) {
   dm.adv_cx = p.adv_cx;
   dm.adv_cy = p.adv_cy;
   dm.adv_omega = p.adv_omega;
+  dm.adv_r1 = p.adv_r1;
+  dm.adv_r2 = p.adv_r2;
   dm.cell_speed = nullptr;
   if (p.n_var == 1 && p.adv_field == 1) {
-    // CFL speed: |omega| times the largest vertex distance from the centre
-    std::vector<double> sp(npad, 0.0);
+    // CFL speed: |omega| times the largest r phi(r) over the vertices (a cell
+    // at rest does not limit the step)
+    auto taper = [&](double r) {
+      if (!(p.adv_r2 > p.adv_r1) || r <= p.adv_r1) return 1.0;
+      if (r >= p.adv_r2) return 0.0;
+      const double s = (r - p.adv_r1) / (p.adv_r2 - p.adv_r1);
+      return 1.0 - s * s * (3.0 - 2.0 * s);
+    };
+    std::vector<double> sp(npad, 1e-300);
     for (int64_t c = 0; c < nc; ++c) {
       const double* P = &ctx->P[6 * (size_t)ctx->perm[c]];
-      double rmax = 0.0;
+      double smax = 0.0;
       for (int k = 0; k < 3; ++k) {
         const double dx = P[2 * k] - p.adv_cx, dy = P[2 * k + 1] - p.adv_cy;
-        rmax = std::max(rmax, std::sqrt(dx * dx + dy * dy));
+        const double r = std::sqrt(dx * dx + dy * dy);
+        smax = std::max(smax, r * taper(r));
       }
-      sp[c] = std::fabs(p.adv_omega) * rmax;
+      const double sc = std::fabs(p.adv_omega) * smax;
+      sp[c] = sc > 0.0 ? sc : 1e-300;
     }
     int e3 = upload(ctx, ctx->b_cspeed, sp.data(), sp.size() * sizeof(double));
     if (e3) return e3;
@@ -1167,6 +1178,8 @@ void teno_default_params(teno_params* p) {
   p->adv_cx = 0.5;
   p->adv_cy = 0.5;
   p->adv_omega = 1.0;
+  p->adv_r1 = 0.0;
+  p->adv_r2 = 0.0;
   p->cfl = 0.4;
 }
 
@@ -1278,7 +1291,8 @@ int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
       !(p->eps > 0) || !(p->gamma > 1.0) || !(p->cfl > 0) || p->recon_variant < 0 ||
       p->recon_variant > 2 || p->adv_field < 0 || p->adv_field > 1 ||
       (p->adv_field == 1 && (p->n_var != 1 || !std::isfinite(p->adv_omega) ||
-                             !std::isfinite(p->adv_cx) || !std::isfinite(p->adv_cy))))
+                             !std::isfinite(p->adv_cx) || !std::isfinite(p->adv_cy) ||
+                             !std::isfinite(p->adv_r1) || !std::isfinite(p->adv_r2))))
     return fail(ctx, TENO_EINVAL, "precompute: bad parameters");
   const int nq_default = p->order <= 4 ? 2 : 3;
   if (p->nq != 0 && p->nq != nq_default)

@@ -55,7 +55,7 @@ struct DeviceMesh {
   int* err_flag = nullptr;  // device flag: bit 0 non-physical state, bit 1 a bounded wait gave up
   double ct = 1e-6, eps = 1e-12, gamma = 1.4, adv_x = 1, adv_y = 1, cfl = 0.4;
   int adv_field = 0;                 // scalar velocity: 0 constant, 1 rigid rotation
-  double adv_cx = 0.5, adv_cy = 0.5, adv_omega = 1.0;
+  double adv_cx = 0.5, adv_cy = 0.5, adv_omega = 1.0, adv_r1 = 0.0, adv_r2 = 0.0;
   const double* cell_speed = nullptr;  // [n_pad] CFL speed per cell (rotation field)
   // reconstruction data, tile-interleaved [tile][entry][32]
   const void* ahat = nullptr;     // double (FP64_NATIVE), float2 (FP64) or float (mixed)

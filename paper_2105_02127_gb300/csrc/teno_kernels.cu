@@ -360,12 +360,26 @@ __device__ __forceinline__ void euler_riemann(const T* UL, const T* UR, const Ri
 }
 
 // normal advection speed of the scalar equation at face point (x, y): the
-// constant velocity, or the rigid rotation omega (-(y - y_c), x - x_c) of the
-// solid-body case (Sec. 5)
+// constant velocity, or the rigid rotation omega phi(r) (-(y - y_c), x - x_c)
+// of the solid-body case (Sec. 5) with the smoothstep taper phi from 1 at r1
+// to 0 at r2 (none when r2 <= r1)
 __device__ __forceinline__ double adv_normal(int field, double ax, double ay, double cx,
-                                             double cy, double om, double x, double y,
-                                             double nx, double ny) {
-  if (field == 1) return om * (-(y - cy) * nx + (x - cx) * ny);
+                                             double cy, double om, double r1, double r2,
+                                             double x, double y, double nx, double ny) {
+  if (field == 1) {
+    const double dx = x - cx, dy = y - cy;
+    double phi = 1.0;
+    if (r2 > r1) {
+      const double r = sqrt(dx * dx + dy * dy);
+      if (r >= r2) {
+        phi = 0.0;
+      } else if (r > r1) {
+        const double s = (r - r1) / (r2 - r1);
+        phi = 1.0 - s * s * (3.0 - 2.0 * s);
+      }
+    }
+    return om * phi * (-dy * nx + dx * ny);
+  }
   return ax * nx + ay * ny;
 }
 
@@ -1935,7 +1949,7 @@ struct FaceArgs {
   int64_t n_face;
   double gamma, adv_x, adv_y, time;
   int adv_field;
-  double adv_cx, adv_cy, adv_omega;
+  double adv_cx, adv_cy, adv_omega, adv_r1, adv_r2;
   double gw[kMaxNq], gt[kMaxNq];
   float2 gw2[kMaxNq], g2, gm12;  // Gauss weights, gamma, gamma - 1 as pairs
 };
@@ -2011,7 +2025,7 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const FaceArgs a, const 
       const double xq = a.f_geom[5 * f + 3] - ny * len * a.gt[k];
       const double yq = a.f_geom[5 * f + 4] + nx * len * a.gt[k];
       const double an = adv_normal(a.adv_field, a.adv_x, a.adv_y, a.adv_cx, a.adv_cy,
-                                   a.adv_omega, xq, yq, nx, ny);
+                                   a.adv_omega, a.adv_r1, a.adv_r2, xq, yq, nx, ny);
       F[0] = cst<T>(an) * (an >= 0.0 ? UL[0] : UR[0]);
     } else {
       euler_riemann<T>(UL, UR, rk, FLUX == TENO_FLUX_HLLC, F);
@@ -2178,7 +2192,7 @@ struct VjpArgs {
   const float2* f_geom2;
   float2 g2, gm12;
   int adv_field;
-  double adv_cx, adv_cy, adv_omega;
+  double adv_cx, adv_cy, adv_omega, adv_r1, adv_r2;
   const double* inv_area;
   int64_t n_face, n_pad;
   double gamma, adv_x, adv_y, time;
@@ -2288,7 +2302,7 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
         if constexpr (NV == 1) {
           const double yq = a.f_geom[5 * f + 4] + nx * len * a.gt[k];
           const double an = adv_normal(a.adv_field, a.adv_x, a.adv_y, a.adv_cx, a.adv_cy,
-                                       a.adv_omega, x, yq, nx, ny);
+                                       a.adv_omega, a.adv_r1, a.adv_r2, x, yq, nx, ny);
           F[0] = an * (an >= 0.0 ? UL[0] : UR[0]);
         } else {
           euler_riemann<D>(UL, UR, rk, FLUX == TENO_FLUX_HLLC, F);
@@ -2659,6 +2673,8 @@ static FaceArgs face_args(const DeviceMesh& dm, double time) {
   a.adv_cx = dm.adv_cx;
   a.adv_cy = dm.adv_cy;
   a.adv_omega = dm.adv_omega;
+  a.adv_r1 = dm.adv_r1;
+  a.adv_r2 = dm.adv_r2;
   a.time = time;
   for (int k = 0; k < kMaxNq; ++k) {
     a.gw[k] = dm.gw[k];
@@ -2792,6 +2808,8 @@ cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const dou
   a.adv_cx = dm.adv_cx;
   a.adv_cy = dm.adv_cy;
   a.adv_omega = dm.adv_omega;
+  a.adv_r1 = dm.adv_r1;
+  a.adv_r2 = dm.adv_r2;
   a.time = time;
   for (int k = 0; k < kMaxNq; ++k) {
     a.gw[k] = dm.gw[k];

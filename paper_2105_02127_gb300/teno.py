@@ -38,7 +38,7 @@ class teno_params(C.Structure):
                 ("ct", C.c_double), ("eps", C.c_double), ("gamma", C.c_double),
                 ("adv_x", C.c_double), ("adv_y", C.c_double), ("cfl", C.c_double),
                 ("adv_field", C.c_int32), ("adv_cx", C.c_double), ("adv_cy", C.c_double),
-                ("adv_omega", C.c_double)]
+                ("adv_omega", C.c_double), ("adv_r1", C.c_double), ("adv_r2", C.c_double)]
 
 
 _lib = None
@@ -160,12 +160,13 @@ def default_params(**kw) -> teno_params:
     for k, v in kw.items():
         if k == "adv":
             p.adv_x, p.adv_y = float(v[0]), float(v[1])
-        elif k == "rotation":  # (x_c, y_c, omega): rigid-rotation velocity, n_var = 1
+        elif k == "rotation":  # (x_c, y_c, omega[, r1, r2]): rigid rotation, n_var = 1
             if v is None:
                 p.adv_field = 0
             else:
                 p.adv_field = 1
                 p.adv_cx, p.adv_cy, p.adv_omega = float(v[0]), float(v[1]), float(v[2])
+                p.adv_r1, p.adv_r2 = (float(v[3]), float(v[4])) if len(v) > 3 else (0.0, 0.0)
         else:
             setattr(p, k, v)
     return p

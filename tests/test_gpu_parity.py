@@ -228,6 +228,7 @@ def test_adjoint_vs_oracle(T, oracle_mod, precision):
 
 
 ROT = (0.5, 0.5, 1.0)  # v = (0.5 - y, x - 0.5), the solid-body case of Sec. 5
+ROT_TAPER = (0.5, 0.5, 1.0, 0.45, 0.5)  # the same, tapered to zero at r = 0.5
 
 
 @pytest.mark.parametrize("order,precision", [(3, 0), (4, 0), (5, 0), (6, 0), (5, 2), (5, 1)],
@@ -238,12 +239,18 @@ def test_scalar_rotation(T, oracle_mod, order, precision):
     against the oracle (FP64 paths at the 1e-11 bar, FP32-mixed reported and
     within 1e-4), then one SSP-RK3 step with the device CFL step."""
     mesh = inputs.jittered_mesh(40, 40, seed=1017)
+    # the bodies plus a smooth ring that reaches the taper (r1 = 0.45, r2 = 0.5)
+    V = mesh.unwrapped_vertices().mean(axis=1)
     U = inputs.cell_average(mesh, inputs.solid_bodies)
+    U = U + 0.3 * np.exp(-((np.hypot(V[:, 0] - 0.5, V[:, 1] - 0.5) - 0.47) / 0.03) ** 2)
+    rot = ROT_TAPER if order in (4, 6) else ROT
     t = _setup(T, mesh, order, 1, 0, precision=precision)
     t.params.adv_field = 1
-    t.params.adv_cx, t.params.adv_cy, t.params.adv_omega = ROT
+    t.params.adv_cx, t.params.adv_cy, t.params.adv_omega = rot[:3]
+    if len(rot) > 3:
+        t.params.adv_r1, t.params.adv_r2 = rot[3:]
     t.precompute_stencils(t.params)
-    o = oracle_mod.Oracle(mesh, order=order, rotation=ROT)
+    o = oracle_mod.Oracle(mesh, order=order, rotation=rot)
     t.set_state(U)
     R, sel = t.residual(want_sel=True)
     Ro, selo, mg = o.residual(U)
