@@ -66,8 +66,8 @@ def parse():
     ap.add_argument("--n", type=int, default=None,
                     help="quads per side, 2 n^2 triangles (vortex 512, shear 2048)")
     ap.add_argument("--order", type=int, default=None, help="TENO order (vortex 5, shear 6)")
-    ap.add_argument("--extras", default="mixed,native,adjoint,e2e,cpu",
-                    help="comma list of extra legs: mixed, native, adjoint, e2e, cpu")
+    ap.add_argument("--extras", default="mixed,native,cweno,adjoint,e2e,cpu",
+                    help="comma list of extra legs: mixed, native, cweno, adjoint, e2e, cpu")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the mixed, adjoint, e2e and CPU-baseline legs")
     ap.add_argument("--recon-variant", type=int, default=2, choices=[0, 1, 2],
@@ -237,15 +237,16 @@ def run_ours(args):
     prec_code = {"fp64": teno.FP64, "fp32_mixed": teno.FP32_MIXED,
                  "fp64_native": teno.FP64_NATIVE}
 
-    def make(precision):
+    def make(precision, scheme="teno"):
         t = teno.Teno(device=torch.cuda.current_device(), stream=stream).load(mesh)
         t.precompute_stencils(order=args.order, n_var=4, flux=teno.FLUX_HLL,
-                              precision=prec_code[precision], recon_variant=args.recon_variant)
+                              precision=prec_code[precision], recon_variant=args.recon_variant,
+                              scheme=scheme)
         t.set_state(Ud)
         return t
 
-    def measure(precision, clocks=False):
-        t = make(precision)
+    def measure(precision, clocks=False, scheme="teno"):
+        t = make(precision, scheme)
         t.rk3_steps(args.warmup, 0.0)
         t.check_state()
         clk = Clocks(torch.cuda.current_device()) if clocks else None
@@ -265,7 +266,7 @@ def run_ours(args):
             var = 0  # the TMA kernel covers the double-float and mixed paths only;
             # variant 2 takes the halo kernel there
         vname = ["recon_halo_kernel", "recon_kernel (direct)", "recon_tma_kernel"][var]
-        if precision == "fp64" and var == 2:
+        if precision == "fp64" and var == 2 and scheme == "teno":
             vname = "recon_tma_w_kernel"  # the W form of the pair path
         kernel = f"{vname} <{precision}> order {args.order}"
         roof_hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
@@ -301,6 +302,14 @@ def run_ours(args):
             r["l1_rho_diff_vs_primary_after_steps"] = float(np.abs(t_o.get_state()[0] - U_main[0]).mean())
             extras[other] = r
             t_o.close()
+    if "cweno" in ex and primary == "fp64":
+        # ---- the comparison scheme on the same stencils (the paper's TENO vs
+        # CWENO cost comparison, Sec. 5): FP64 path, same workload
+        t_c, r = measure("fp64", scheme="cweno")
+        r["scheme"] = "CWENO, d'_K = 1e4, eps = 1e-14"
+        r["cweno_over_teno_time"] = r["ms_per_step"] / main["ms_per_step"]
+        extras["cweno"] = r
+        t_c.close()
     if "adjoint" in ex:
         # ---- adjoint / forward (FP64 path)
         lam = torch.from_numpy(np.ones_like(U)).cuda()
@@ -374,7 +383,7 @@ def run_ours(args):
                              "recon_vjp", "reverse_gather"],
             "clocks": main.get("clocks"),
         }
-        for k in ("fp32_mixed", "fp64_native", "adjoint", "e2e"):
+        for k in ("fp32_mixed", "fp64_native", "cweno", "adjoint", "e2e"):
             if k in extras:
                 line[k] = extras[k]
         if cpu is not None:

@@ -105,10 +105,20 @@ typedef struct teno_params {
                         cell is |omega| times the largest r phi(r) over its vertices. */
   double adv_cx, adv_cy, adv_omega;
   double adv_r1, adv_r2;
+  int32_t scheme;    /* 0 TENO (the paper's scheme); 1 CWENO, the comparison scheme of
+                        Sec. 2.3 on the same stencils: P = (w_K/d_K)(P_K - sum_k d_k P_k)
+                        + sum_k w_k P_k with alpha = d/(beta + eps)^4, d_K = 1 - 1/cweno_dk,
+                        d_k = (1 - d_K)/K over the present directional stencils (the
+                        paper uses eps = 1e-14 for CWENO).  CWENO runs on the pair,
+                        native and mixed paths with recon_variant 0, 1 or 2 (variant 2
+                        uses the pair TMA kernel, not the W form); the adjoint entry
+                        points take TENO only. */
+  double cweno_dk;   /* CWENO d'_K, default 1e4 */
 } teno_params;
 
 /* Fills *p with the defaults above (order 5, n_var 4, HLL, FP64, recon_variant 2,
-   cfl 0.4, adv (1, 1), adv_field 0, rotation centre (0.5, 0.5), omega 1, no taper). */
+   cfl 0.4, adv (1, 1), adv_field 0, rotation centre (0.5, 0.5), omega 1, no taper,
+   scheme TENO, cweno_dk 1e4). */
 void teno_default_params(teno_params* p);
 
 /* Create a context on CUDA device `device`, launching on `cuda_stream`

@@ -685,7 +685,7 @@ int run_precompute(teno_ctx* ctx) {
   // Euler on the pair path with the TMA kernel: FP32 selection matrices with
   // column sums of |G| (large slots M + 1 floats, directional slots 5 + 1) and
   // W = Psi' G, the large polynomial's Gauss-point values per unit difference
-  const bool wform = store == TENO_FP64 && p.n_var == 4 && p.recon_variant == 2;
+  const bool wform = store == TENO_FP64 && p.n_var == 4 && p.recon_variant == 2 && p.scheme == 0;
   const int nq3 = 3 * ctx->nq;
   const int E32 = ns * (m + 1) + kSmallK * kSmallN * (kSmallM + 1), EW = ns * nq3;
   std::vector<float> g32(wform ? (size_t)ntile * E32 * kTile : 0, 0.f);
@@ -865,6 +865,8 @@ int run_precompute(teno_ctx* ctx) {
   dm.adv_omega = p.adv_omega;
   dm.adv_r1 = p.adv_r1;
   dm.adv_r2 = p.adv_r2;
+  dm.scheme = p.scheme;
+  dm.cweno_dk = p.cweno_dk;
   dm.cell_speed = nullptr;
   if (p.n_var == 1 && p.adv_field == 1) {
     // CFL speed: |omega| times the largest r phi(r) over the vertices (a cell
@@ -1180,6 +1182,8 @@ void teno_default_params(teno_params* p) {
   p->adv_omega = 1.0;
   p->adv_r1 = 0.0;
   p->adv_r2 = 0.0;
+  p->scheme = 0;
+  p->cweno_dk = 1e4;
   p->cfl = 0.4;
 }
 
@@ -1292,7 +1296,8 @@ int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
       p->recon_variant > 2 || p->adv_field < 0 || p->adv_field > 1 ||
       (p->adv_field == 1 && (p->n_var != 1 || !std::isfinite(p->adv_omega) ||
                              !std::isfinite(p->adv_cx) || !std::isfinite(p->adv_cy) ||
-                             !std::isfinite(p->adv_r1) || !std::isfinite(p->adv_r2))))
+                             !std::isfinite(p->adv_r1) || !std::isfinite(p->adv_r2))) ||
+      p->scheme < 0 || p->scheme > 1 || (p->scheme == 1 && !(p->cweno_dk > 1.0)))
     return fail(ctx, TENO_EINVAL, "precompute: bad parameters");
   const int nq_default = p->order <= 4 ? 2 : 3;
   if (p->nq != 0 && p->nq != nq_default)
@@ -1514,6 +1519,7 @@ int teno_residual_vjp(teno_ctx* ctx, const double* w, double* v, int on_device) 
   if (!w || !v) return fail(ctx, TENO_EINVAL, "residual_vjp: null pointer");
   if (ctx->prm.precision == TENO_FP32_MIXED)
     return fail(ctx, TENO_EINVAL, "adjoint: FP64 precisions only");
+  if (ctx->prm.scheme != 0) return fail(ctx, TENO_EINVAL, "adjoint: TENO only");
   rc = ensure_adjoint(ctx);
   if (rc) return rc;
   rc = to_internal(ctx, w, (double*)ctx->b_l1.p, on_device);
@@ -1531,6 +1537,7 @@ int teno_adjoint_step(teno_ctx* ctx, double dt, const double* lam_np1, double* l
   if (!lam_np1 || !lam_n || !(dt > 0.0)) return fail(ctx, TENO_EINVAL, "adjoint_step: bad args");
   if (ctx->prm.precision == TENO_FP32_MIXED)
     return fail(ctx, TENO_EINVAL, "adjoint: FP64 precisions only");
+  if (ctx->prm.scheme != 0) return fail(ctx, TENO_EINVAL, "adjoint: TENO only");
   rc = ensure_adjoint(ctx);
   if (rc) return rc;
   const int64_t n = (int64_t)ctx->prm.n_var * ctx->npad;

@@ -54,6 +54,8 @@ struct DeviceMesh {
   HaloArgs halo;            // null when some tile's halo exceeds kHaloMax
   int* err_flag = nullptr;  // device flag: bit 0 non-physical state, bit 1 a bounded wait gave up
   double ct = 1e-6, eps = 1e-12, gamma = 1.4, adv_x = 1, adv_y = 1, cfl = 0.4;
+  int scheme = 0;                    // 0 TENO, 1 CWENO
+  double cweno_dk = 1e4;             // CWENO d'_K
   int adv_field = 0;                 // scalar velocity: 0 constant, 1 rigid rotation
   double adv_cx = 0.5, adv_cy = 0.5, adv_omega = 1.0, adv_r1 = 0.0, adv_r2 = 0.0;
   const double* cell_speed = nullptr;  // [n_pad] CFL speed per cell (rotation field)

@@ -684,7 +684,32 @@ struct ReconArgs {
   int64_t n_cell, n_pad;
   double ct, eps;
   int linear, e_entries;
+  int scheme;   // 0 TENO, 1 CWENO
+  double cw_dK; // CWENO d_K = 1 - 1/d'_K
 };
+
+// CWENO weights (Eqs. CWENOweight, CWENOOptimalLinearweight/02) from the
+// smoothness indicators: alpha = d / (beta + eps)^4 with d_K = cw_dK and
+// d_k = (1 - d_K)/K over the K present directional stencils; returns the
+// factors of P = sK P_K + sum_k s[k] P_k, i.e. sK = w_K / d_K and
+// s[k] = w_k - sK d_k (0 for absent stencils).
+__device__ __forceinline__ void cweno_factors(const double* beta, int present, double dK_in,
+                                              double eps, double& sK, double* s) {
+  const int K = (present & 1) + ((present >> 1) & 1) + ((present >> 2) & 1);
+  const double dK = K ? dK_in : 1.0, dk = K ? (1.0 - dK) / K : 0.0;
+  double al[kSmallK + 1], sum = 0.0;
+#pragma unroll
+  for (int k = 0; k <= kSmallK; ++k) {
+    const bool pr = k == kSmallK || ((present >> k) & 1);
+    const double ib = 1.0 / (beta[k] + eps);
+    const double i2 = ib * ib;
+    al[k] = pr ? (k == kSmallK ? dK : dk) * (i2 * i2) : 0.0;
+    sum += al[k];
+  }
+  sK = al[kSmallK] / sum / dK;
+#pragma unroll
+  for (int k = 0; k < kSmallK; ++k) s[k] = ((present >> k) & 1) ? al[k] / sum - sK * dk : 0.0;
+}
 
 // TENO cutoff and two-step selection in FP64 (Eqs. new_scale_separation,
 // normalize, cutoff, TENO_reconstruction111/222): chi_k >= C_T is evaluated as
@@ -767,7 +792,32 @@ __device__ __forceinline__ void plain_finish(const ReconArgs& a, const TT& ev, i
   constexpr bool kMixed = std::is_same<TA, float>::value;
   const int present = a.smask[c];
   uint8_t sel;
-  if (a.sel_in) {
+  const bool cweno = a.scheme == 1 && !a.linear;
+  TA cf[M];
+  if (cweno) {
+    // beta and weights in FP64 (from the FP32 coefficients on the mixed path)
+    double beta[kSmallK + 1];
+    double b = 0.0;
+#pragma unroll
+    for (int l = 0; l < M; ++l) b = fma((double)acc[l], (double)acc[l], b);
+    beta[kSmallK] = b;
+#pragma unroll
+    for (int k = 0; k < kSmallK; ++k) {
+      double q = 0.0;
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) q = fma((double)as[k][l], (double)as[k][l], q);
+      beta[k] = q;
+    }
+    double sK, sk[kSmallK];
+    cweno_factors(beta, present, a.cw_dK, a.eps, sK, sk);
+#pragma unroll
+    for (int l = 0; l < M; ++l) cf[l] = TA(sK) * acc[l];
+#pragma unroll
+    for (int k = 0; k < kSmallK; ++k)
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) cf[l] = fma(TA(sk[k]), as[k][l], cf[l]);
+    sel = 8;
+  } else if (a.sel_in) {
     sel = a.sel_in[(int64_t)v * a.n_pad + c];
   } else if (a.linear) {
     sel = 8;
@@ -823,8 +873,9 @@ __device__ __forceinline__ void plain_finish(const ReconArgs& a, const TT& ev, i
   }
   if (a.sel_out) a.sel_out[(int64_t)v * a.n_pad + c] = sel;
   // final polynomial coefficients
-  TA cf[M];
-  if (sel & 8) {
+  if (cweno) {
+    // formed above
+  } else if (sel & 8) {
 #pragma unroll
     for (int l = 0; l < M; ++l) cf[l] = acc[l];
   } else {
@@ -928,7 +979,37 @@ __device__ __forceinline__ void df_finish(const ReconArgs& a, const DFTable& ev,
                                           const DF (&as)[kSmallK][kSmallM]) {
   const int present = a.smask[c];
   uint8_t sel;
-  if (a.sel_in) {
+  const bool cweno = a.scheme == 1 && !a.linear;
+  DF cf[M];
+  if (cweno) {
+    // beta = |a'|^2 in pairs, weights in FP64, combination in pairs
+    double beta[kSmallK + 1];
+    {
+      DF b = {0.f, 0.f};
+#pragma unroll
+      for (int l = 0; l < M; ++l) df_mac(b, make_float2(acc[l].h, acc[l].l), acc[l]);
+      beta[kSmallK] = df_to_double(df_norm(b));
+#pragma unroll
+      for (int k = 0; k < kSmallK; ++k) {
+        DF q = {0.f, 0.f};
+#pragma unroll
+        for (int l = 0; l < kSmallM; ++l) df_mac(q, make_float2(as[k][l].h, as[k][l].l), as[k][l]);
+        beta[k] = df_to_double(df_norm(q));
+      }
+    }
+    double sK, sk[kSmallK];
+    cweno_factors(beta, present, a.cw_dK, a.eps, sK, sk);
+    const DF fK = cst<DF>(sK);
+#pragma unroll
+    for (int l = 0; l < M; ++l) cf[l] = fK * acc[l];
+#pragma unroll
+    for (int k = 0; k < kSmallK; ++k) {
+      const DF fk = cst<DF>(sk[k]);
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) cf[l] = cf[l] + fk * as[k][l];
+    }
+    sel = 8;
+  } else if (a.sel_in) {
     sel = a.sel_in[(int64_t)v * a.n_pad + c];
   } else if (a.linear) {
     sel = 8;
@@ -970,8 +1051,9 @@ __device__ __forceinline__ void df_finish(const ReconArgs& a, const DFTable& ev,
     }
   }
   if (a.sel_out) a.sel_out[(int64_t)v * a.n_pad + c] = sel;
-  DF cf[M];
-  if (sel & 8) {
+  if (cweno) {
+    // coefficients formed above
+  } else if (sel & 8) {
 #pragma unroll
     for (int l = 0; l < M; ++l) cf[l] = acc[l];
   } else {
@@ -2606,6 +2688,8 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
   a.eps = dm.eps;
   a.linear = dm.linear;
   a.e_entries = dm.e_entries;
+  a.scheme = dm.scheme;
+  a.cw_dK = 1.0 - 1.0 / dm.cweno_dk;
   const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
   return dispatch_order(dm.order, [&](auto Mc, auto NSc) -> cudaError_t {
     constexpr int M = decltype(Mc)::value, NS = decltype(NSc)::value;
@@ -2629,7 +2713,7 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
       }
       if constexpr (NV == 4) {
         if (tma) {
-          if (dm.precision == TENO_FP64 && dm.g32 && dm.wq && dm.psi_df)
+          if (dm.precision == TENO_FP64 && dm.scheme == 0 && dm.g32 && dm.wq && dm.psi_df)
             return launch_recon_tma_w<M, NS, NQ>(a, dm, dm.err_flag, st);
           if (dm.precision == TENO_FP64) return launch_recon_tma<M, NS, NQ, true>(a, dm, dm.err_flag, st);
           return launch_recon_tma<M, NS, NQ, false>(a, dm, dm.err_flag, st);

@@ -38,7 +38,8 @@ class teno_params(C.Structure):
                 ("ct", C.c_double), ("eps", C.c_double), ("gamma", C.c_double),
                 ("adv_x", C.c_double), ("adv_y", C.c_double), ("cfl", C.c_double),
                 ("adv_field", C.c_int32), ("adv_cx", C.c_double), ("adv_cy", C.c_double),
-                ("adv_omega", C.c_double), ("adv_r1", C.c_double), ("adv_r2", C.c_double)]
+                ("adv_omega", C.c_double), ("adv_r1", C.c_double), ("adv_r2", C.c_double),
+                ("scheme", C.c_int32), ("cweno_dk", C.c_double)]
 
 
 _lib = None
@@ -154,9 +155,22 @@ def cfl_dt_noalloc(U, cell_len, dt_out=None, gamma: float = 1.4, adv=(1.0, 1.0),
     return None
 
 
+SCHEME_TENO, SCHEME_CWENO = 0, 1
+
+
 def default_params(**kw) -> teno_params:
+    """Library defaults overridden by keyword: teno_params fields, plus
+    adv=(ax, ay), rotation=(x_c, y_c, omega[, r1, r2]) and scheme='teno' |
+    'cweno' (CWENO takes eps = 1e-14, the paper's value, unless eps is given)."""
     p = teno_params()
     lib().teno_default_params(C.byref(p))
+    if isinstance(kw.get("scheme"), str):
+        name = kw.pop("scheme")
+        if name not in ("teno", "cweno"):
+            raise ValueError("scheme must be 'teno' or 'cweno'")
+        p.scheme = SCHEME_CWENO if name == "cweno" else SCHEME_TENO
+        if p.scheme == SCHEME_CWENO and "eps" not in kw:
+            p.eps = 1e-14
     for k, v in kw.items():
         if k == "adv":
             p.adv_x, p.adv_y = float(v[0]), float(v[1])

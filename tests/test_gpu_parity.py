@@ -227,6 +227,33 @@ def test_adjoint_vs_oracle(T, oracle_mod, precision):
     assert np.array_equal(t.get_state(), U)
 
 
+@pytest.mark.parametrize("precision,variant", [(0, 2), (0, 0), (2, 2), (1, 2)],
+                         ids=["pairs-tma", "pairs-halo", "native", "mixed"])
+@pytest.mark.parametrize("order,flux", [(5, 1), (6, 2)])
+def test_cweno(T, oracle_mod, order, flux, precision, variant):
+    """CWENO comparison scheme (Sec. 2.3) on the vortex and on the
+    discontinuous state: residual against the oracle (FP64 paths at the 1e-11
+    bar; FP32-mixed reported, below 1e-4)."""
+    for mesh, U in [(inputs.jittered_mesh(33, 31, 10.0, 10.0, seed=1019), None),
+                    (inputs.jittered_mesh(40, 40, 10.0, 10.0, seed=1007), "blast")]:
+        U = _blast(mesh) if U == "blast" else inputs.cell_average(mesh, inputs.isentropic_vortex)
+        t = T.Teno(device=0).load(mesh)
+        t.precompute_stencils(order=order, n_var=4, flux=flux, precision=precision,
+                              recon_variant=variant, scheme="cweno")
+        t.set_state(U)
+        R, _ = t.residual()
+        o = oracle_mod.Oracle(mesh, order=order, n_var=4, flux=flux, scheme="cweno", eps=1e-14)
+        Ro, _, _ = o.residual(U)
+        e = rel(R, Ro)
+        print(f"CWENO{order} flux {flux} precision {precision} variant {variant}: rel err {e:.2e}")
+        assert e <= (TOL if precision != 1 else 1e-4)
+        t.check_state()
+        if precision == 0:
+            with pytest.raises(T.TenoError) as ei:
+                t.residual_vjp(np.zeros_like(U))
+            assert ei.value.code == T.TENO_EINVAL  # the adjoint takes TENO only
+
+
 ROT = (0.5, 0.5, 1.0)  # v = (0.5 - y, x - 0.5), the solid-body case of Sec. 5
 ROT_TAPER = (0.5, 0.5, 1.0, 0.45, 0.5)  # the same, tapered to zero at r = 0.5
 

@@ -382,9 +382,9 @@ def test_upwind_flux(oracle_mod):
 
 
 # ---------------------------------------------------------------- orders
-def _advect_error(oracle_mod, order, n, t_end, cfl_frac):
+def _advect_error(oracle_mod, order, n, t_end, cfl_frac, **kw):
     mesh = _mesh(n, seed=1001)
-    o = oracle_mod.Oracle(mesh, order=order)
+    o = oracle_mod.Oracle(mesh, order=order, **kw)
     U = inputs.cell_average(mesh, inputs.advection_sine)
     h = 1.0 / n
     nsteps = int(np.ceil(t_end / (cfl_frac * h)))
@@ -418,6 +418,68 @@ def test_convergence_order(oracle_mod, order, cfl):
     rate = np.log2(e1 / e2)
     # jittered meshes, so allow a quarter order below the paper's figure
     assert rate > _paper_orders()[order] - 0.25, (e1, e2, rate)
+
+
+# ------------------------------------------------------------------ CWENO
+@pytest.mark.parametrize("order", [3, 5, 6])
+def test_cweno_quadratic_exactness(oracle_mod, order):
+    """CWENO (Sec. 2.3): when every candidate reproduces the data, P_K = P_k = p
+    and (w_K/d_K)(p - sum d_k p) + sum w_k p = p for any weights, because
+    sum_k d_k = 1 - d_K; quadratic data are therefore reproduced exactly at
+    points of the cell whatever the smoothness indicators."""
+    n = 16
+    mesh = _mesh(n)
+    rng = np.random.default_rng(40 + order)
+    c = rng.standard_normal(6)
+
+    def quad(x, y):
+        return (c[0] + c[1] * x + c[2] * y + c[3] * x * x + c[4] * x * y + c[5] * y * y)
+
+    U = inputs.cell_average(mesh, quad, n_quad=8)
+    o = oracle_mod.Oracle(mesh, order=order, scheme="cweno", eps=1e-14)
+    c0 = _centre_cell(n)
+    cf, beta, _, _ = o.recon_cell(U, c0)
+    assert beta.min() > 1e-8  # weights far from their linear values
+    ref = o.reference_data()
+    V = mesh.unwrapped_vertices()[c0]
+    for (u, v) in [(0.2, 0.3), (0.6, 0.1), (0.05, 0.9)]:
+        x = V[0] + u * (V[1] - V[0]) + v * (V[2] - V[0])
+        psi = u ** ref["ex"][:, 0] * v ** ref["ex"][:, 1] - ref["mean0"]
+        assert abs(U[0, c0] + cf[0] @ psi - quad(x[0], x[1])) < 1e-11
+
+
+def test_cweno_limits(oracle_mod):
+    """Two limits of the CWENO weights: with d'_K = 1e15 (d_K -> 1) smooth data
+    give the large-stencil (linear) reconstruction to rounding; next to a jump,
+    a directional stencil lying in the constant region (beta = 0, alpha ~ 1e56)
+    takes all the weight, so the reconstruction is that constant."""
+    mesh = _mesh(12, seed=1242)
+    U = inputs.cell_average(mesh, inputs.advection_sine)
+    o_cw = oracle_mod.Oracle(mesh, order=5, scheme="cweno", eps=1e-14, cweno_dk=1e15)
+    o_lin = oracle_mod.Oracle(mesh, order=5, linear=True)
+    R1, _, _ = o_cw.residual(U)
+    R2, _, _ = o_lin.residual(U)
+    assert np.abs(R1 - R2).max() <= 1e-9 * np.abs(R2).max()
+    V = mesh.unwrapped_vertices().mean(axis=1)
+    Uj = np.where(V[:, 0] < 0.5, 1.0, 3.0)[None].copy()
+    o = oracle_mod.Oracle(mesh, order=5, scheme="cweno", eps=1e-14)
+    hits = 0
+    for c in range(mesh.n_cell):
+        cf, beta, _, _ = o.recon_cell(Uj, c)
+        if beta[0, 3] > 1e-3 and (beta[0, :3] == 0.0).any():
+            assert np.abs(cf[0]).max() < 1e-12 * 2.0
+            hits += 1
+    assert hits > 5
+
+
+def test_cweno_convergence_order(oracle_mod):
+    """CWENO5 on smooth advection keeps the order of its large stencil (the
+    paper's claim in Sec. 2.3): 32^2 -> 64^2 rate above 4.5."""
+    kw = dict(scheme="cweno", eps=1e-14)
+    e1 = _advect_error(oracle_mod, 5, 32, 0.05, 0.06, **kw)
+    e2 = _advect_error(oracle_mod, 5, 64, 0.05, 0.06, **kw)
+    rate = np.log2(e1 / e2)
+    assert rate > 4.5, (e1, e2, rate)
 
 
 # ---------------------------------------------------------------- adjoint
