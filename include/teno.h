@@ -150,8 +150,11 @@ int teno_set_stream(teno_ctx* ctx, void* cuda_stream);
  *         share ids (coordinates of a cell are unwrapped to lie within half
  *         a period of its vertex 0), or NULL.
  * Builds faces, normals and areas and the Hilbert-curve cell order.
- * Errors: TENO_EINVAL, TENO_EMESH (non-positive area, an edge shared by more
- * than two cells, a boundary edge without a bface entry). */
+ * Errors: TENO_EINVAL (null pointers, n_cell < 1 or n_vert < 3), TENO_EMESH (a
+ * vertex id out of range, non-positive area, an edge shared by more than two
+ * cells, a boundary edge without a bface entry).  A mesh too small for the
+ * stencils of the requested order loads, and teno_precompute_stencils then
+ * returns TENO_ESTENCIL. */
 int teno_mesh_load(teno_ctx* ctx, int64_t n_vert, const double* xy, int64_t n_cell,
                    const int32_t* tri, int64_t n_bface, const int32_t* bface,
                    const double* period);

@@ -95,6 +95,17 @@ def test_errors(teno):
     with pytest.raises(teno.TenoError) as e:
         t.set_state(np.zeros((1, mesh.n_cell)))
     assert e.value.code == teno.TENO_ESTATE  # host-only context does no device work
+    # empty input, and a mesh too small for the sixth-order stencils (42
+    # distinct neighbours are not there on 18 periodic cells)
+    with pytest.raises(teno.TenoError) as e:
+        teno.Teno(device=-1).mesh_load(np.zeros((0, 2)), np.zeros((0, 3), dtype=np.int32), None,
+                                       (1.0, 1.0))
+    assert e.value.code == teno.TENO_EINVAL
+    small = teno.Teno(device=-1).load(inputs.jittered_mesh(3, 3, seed=5))
+    with pytest.raises(teno.TenoError) as e:
+        small.precompute_stencils(order=6, n_var=1, flux=0)
+    assert e.value.code == teno.TENO_ESTENCIL
+    small.precompute_stencils(order=3, n_var=1, flux=0)  # the third-order stencils fit
     # a boundary edge without a bface entry
     mb = inputs.jittered_mesh(6, 6, seed=3, periodic=False)
     with pytest.raises(teno.TenoError) as e:
