@@ -270,7 +270,8 @@ def run_ours(args):
             vname = "recon_tma_w_kernel"  # the W form of the pair path
         kernel = f"{vname} <{precision}> order {args.order}"
         roof_hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
-                    "frac": gbs / hbm_gbs, "traffic": ncu_traffic(precision, args.order, n_cell),
+                    "frac": gbs / hbm_gbs,
+                    "traffic": ncu_traffic(precision, args.order, n_cell) if scheme == "teno" else None,
                     "kernel": kernel, "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)"}
         if precision == "fp64_native":
             fl = algorithmic_fp64_flops(args.order, 4, nq) * n_cell / (rec_ms / 1e3) / 1e12
@@ -456,7 +457,7 @@ def run_reference(args):
     from oracle import build as ob
     ob.build()
     from oracle.oracle import Oracle
-    mesh, U = workload(args.n, args.order)
+    mesh, U = workload(args.n, args.order, args.workload)
     rng = np.random.default_rng(0)
     cells = np.sort(rng.choice(mesh.n_cell, min(mesh.n_cell, 65536), replace=False))
     o = Oracle(mesh, order=args.order, n_var=4, flux=1)
@@ -478,9 +479,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": f"isentropic vortex, periodic [0,10]^2, jittered {args.n}x"
-                                   f"{args.n} split quads = {mesh.n_cell} triangles, TENO"
-                                   f"{args.order}, HLL, SSP-RK3", "n_cell": mesh.n_cell},
+            "config": {"workload": workload_name(args, mesh.n_cell), "n_cell": mesh.n_cell,
+                       "order": args.order, "parallelism": "oracle on the host cores"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
