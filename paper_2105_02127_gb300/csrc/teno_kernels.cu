@@ -2405,6 +2405,13 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
   }
 }
 
+// stencil slots unrolled in the reconstruction VJP kernels (matrix loads in
+// flight per thread)
+#ifndef TENO_VJP_SLOT_UNROLL
+#define TENO_VJP_SLOT_UNROLL 2
+#endif
+constexpr int kVjpSlotUnroll = TENO_VJP_SLOT_UNROLL;
+
 // d_bar[tile][slot][v][32] = (A''^T abar)_slot with abar = w_k Psi'^T Uq_bar
 // (selection frozen); u_self = sum_p Uq_bar - sum_slot d_bar (dU_0 terms).
 template <int M, int NS, int NQ, int NV, typename TS>
@@ -2445,7 +2452,7 @@ __global__ void __launch_bounds__(128) recon_vjp_kernel(const TS* __restrict__ a
   const uint8_t sel = sel_in[(int64_t)v * n_pad + c];
   double tot = 0.0;
   const bool large = sel & 8;
-#pragma unroll 2
+#pragma unroll (kVjpSlotUnroll)
   for (int s = 0; s < NS; ++s) {
     double t = 0.0;
     if (large) {
@@ -2522,7 +2529,7 @@ __global__ void __launch_bounds__(128) recon_vjp_df_kernel(const float2* __restr
   const uint8_t sel = sel_in[(int64_t)v * n_pad + c];
   DF tot = {0.f, 0.f};
   const bool large = sel & 8;
-#pragma unroll 2
+#pragma unroll (kVjpSlotUnroll)
   for (int s = 0; s < NS; ++s) {
     DF t = {0.f, 0.f};
     if (large) {
@@ -2553,6 +2560,10 @@ __global__ void __launch_bounds__(128) recon_vjp_df_kernel(const float2* __restr
   u_self[(int64_t)v * n_pad + c] = to_d(u0b - tot);
 }
 
+#ifndef TENO_SCATTER_BATCH
+#define TENO_SCATTER_BATCH 4
+#endif
+constexpr int kScatterBatch = TENO_SCATTER_BATCH;
 // v[j] = u_self[j] + sum over the stencil slots that hold cell j.  d_bar is
 // [tile][slot][lane][var]: the NV values of one slot entry are one 32-byte
 // sector (NV = 4), read with vector loads; rev_idx holds entry numbers
@@ -2571,7 +2582,31 @@ __global__ void __launch_bounds__(256) scatter_gather_kernel(const int64_t* __re
     DF acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = d_to_df(u_self[v * n_pad + j]);
-    for (int64_t r = r0; r < r1; ++r) {
+    int64_t r = r0;
+    if constexpr (NV == 4) {
+      // kScatterBatch entries per round: every index, then every sector, is
+      // requested before any is used (independent loads in flight)
+      for (; r + kScatterBatch <= r1; r += kScatterBatch) {
+        int id[kScatterBatch];
+#pragma unroll
+        for (int i = 0; i < kScatterBatch; ++i) id[i] = __ldg(rev_idx + r + i);
+        float4 a[kScatterBatch], b[kScatterBatch];
+#pragma unroll
+        for (int i = 0; i < kScatterBatch; ++i) {
+          const float4* e = reinterpret_cast<const float4*>(d_bar + (int64_t)id[i] * NV);
+          a[i] = __ldg(e);
+          b[i] = __ldg(e + 1);
+        }
+#pragma unroll
+        for (int i = 0; i < kScatterBatch; ++i) {
+          acc[0] = acc[0] + DF{a[i].x, a[i].y};
+          acc[1] = acc[1] + DF{a[i].z, a[i].w};
+          acc[2] = acc[2] + DF{b[i].x, b[i].y};
+          acc[3] = acc[3] + DF{b[i].z, b[i].w};
+        }
+      }
+    }
+    for (; r < r1; ++r) {
       const TD* e = d_bar + (int64_t)rev_idx[r] * NV;
       if constexpr (NV == 4) {
         const float4 a = __ldg(reinterpret_cast<const float4*>(e));
