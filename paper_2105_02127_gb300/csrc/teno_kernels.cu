@@ -2143,8 +2143,9 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a, const T
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= a.n_cell) return;
   double acc[NV];
-  if constexpr (std::is_same<TK, DF>::value) {
-    // pair fluxes summed in pairs (FP32 pipe), one conversion per variable
+  if constexpr (std::is_same<TK, DF>::value || std::is_same<TK, float>::value) {
+    // pair (or FP32) fluxes summed in pairs on the FP32 pipe, one conversion
+    // per variable; three FP32 terms sum exactly in a pair
     DF sum[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) sum[v] = DF{0.f, 0.f};
@@ -2153,7 +2154,14 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a, const T
       const int cf = a.c_faces[3 * c + e];
       const int64_t f = cf >> 1;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sum[v] = (cf & 1) ? sum[v] - K[f * NV + v] : sum[v] + K[f * NV + v];
+      for (int v = 0; v < NV; ++v) {
+        DF k;
+        if constexpr (std::is_same<TK, DF>::value)
+          k = K[f * NV + v];
+        else
+          k = DF{K[f * NV + v], 0.f};
+        sum[v] = (cf & 1) ? sum[v] - k : sum[v] + k;
+      }
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = to_d(sum[v]);
