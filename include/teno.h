@@ -114,11 +114,22 @@ typedef struct teno_params {
                         uses the pair TMA kernel, not the W form); the adjoint entry
                         points take TENO only. */
   double cweno_dk;   /* CWENO d'_K, default 1e4 */
+  int32_t charvar;   /* Euler, TENO: 1 reconstructs characteristic variables (Sec. 2.3: they
+                        suppress oscillations better than conservative ones).  For every
+                        local edge of a cell the large and directional coefficients of the
+                        four conservative variables are projected on the characteristic
+                        fields of the edge's outward normal direction at the cell-average
+                        state, each field takes its own TENO selection, and the result is
+                        mapped back.  The reconstruction kernels then write their
+                        coefficients (FP64, 4 (m+15) values per cell) and a second kernel
+                        does the projection, selection and evaluation in FP64.  The
+                        selection output reports 8; the adjoint entry points take
+                        conservative variables only. */
 } teno_params;
 
 /* Fills *p with the defaults above (order 5, n_var 4, HLL, FP64, recon_variant 2,
    cfl 0.4, adv (1, 1), adv_field 0, rotation centre (0.5, 0.5), omega 1, no taper,
-   scheme TENO, cweno_dk 1e4). */
+   scheme TENO, cweno_dk 1e4, charvar 0). */
 void teno_default_params(teno_params* p);
 
 /* Create a context on CUDA device `device`, launching on `cuda_stream`

@@ -53,6 +53,7 @@ def lib():
         L.oracle_flux.argtypes = [C.c_void_p, _dp, _dp, C.c_double, C.c_double, C.c_double,
                                   C.c_double, _dp, C.c_void_p, C.c_void_p]
         L.oracle_geometry.argtypes = [C.c_void_p, _dp, _dp, _ip]
+        L.oracle_char_basis.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp, _dp]
         L.oracle_gauss_legendre.argtypes = [C.c_int, _dp, _dp]
     return _lib
 
@@ -76,12 +77,13 @@ class Oracle:
     def __init__(self, mesh, order: int = 3, n_var: int = 1, flux: int = FLUX_UPWIND,
                  linear: bool = False, ct: float = 1e-6, eps: float = 1e-12, gamma: float = 1.4,
                  adv=(1.0, 1.0), nq: int | None = None, rotation=None, scheme: str = "teno",
-                 cweno_dk: float = 1e4):
+                 cweno_dk: float = 1e4, charvar: bool = False):
         """rotation: (x_c, y_c, omega) or (x_c, y_c, omega, r1, r2) for scalar
         advection by the rigid rotation v = omega phi(r) (-(y - y_c), x - x_c)
         (the solid-body case of Sec. 5 is (0.5, 0.5, 1.0)), phi a smoothstep
         taper from 1 at r1 to 0 at r2 (none when omitted); otherwise the
-        constant velocity adv."""
+        constant velocity adv.  charvar: Euler reconstruction in characteristic
+        variables per face (TENO only)."""
         self.mesh = mesh
         self.order, self.n_var = order, n_var
         self.m = n_unknowns(order)
@@ -97,7 +99,7 @@ class Oracle:
         if scheme not in ("teno", "cweno"):
             raise ValueError("scheme must be 'teno' or 'cweno'")
         iopt = np.array([order, self.nq, n_var, flux, int(linear), int(rotation is not None),
-                         int(scheme == "cweno")], dtype=np.int32)
+                         int(scheme == "cweno"), int(charvar)], dtype=np.int32)
         dopt = np.array([ct, eps, gamma, adv[0], adv[1], rot[0], rot[1], rot[2], rot[3], rot[4],
                          cweno_dk], dtype=np.float64)
         st = C.c_int32(0)
@@ -219,6 +221,14 @@ class Oracle:
             return F, JL, JR
         lib().oracle_flux(self._h, UL, UR, nx, ny, x, y, F, None, None)
         return F
+
+    def char_basis(self, W, nx: float, ny: float):
+        """left / right eigenvector matrices (4x4) of the Euler flux in
+        direction (nx, ny) at conservative state W"""
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        Lm, Rm = np.empty(16), np.empty(16)
+        lib().oracle_char_basis(self._h, W, nx, ny, Lm, Rm)
+        return Lm.reshape(4, 4), Rm.reshape(4, 4)
 
     def geometry(self):
         area = np.empty(self.n_cell)

@@ -174,6 +174,7 @@ typedef struct {
   int order, r, m, ns, nq, nvar, flux, linear;
   double ct, eps, gam, adv[2], time;
   int scheme;     /* 0 TENO, 1 CWENO (the comparison scheme of Sec. 2.3) */
+  int charvar;    /* Euler: reconstruct characteristic variables per face */
   double cw_dk;   /* CWENO d'_K (d_K = 1 - 1/d'_K) */
   int field;      /* scalar advection velocity: 0 constant adv, 1 rigid rotation */
   double rot[5];  /* rotation centre (x, y), angular velocity omega, taper radii r1 < r2 */
@@ -649,6 +650,10 @@ typedef struct {
   double a_large[MAXVAR][MAXM];
   double a_small[MAXVAR][KSM][MSM];
   double w[MAXVAR][KSM]; /* weights of the small polynomials (0 if large) */
+  /* characteristic-variable reconstruction: conservative-equivalent final
+   * coefficients per local edge (charf = 1), used instead of coef */
+  int charf;
+  double coef_f[3][MAXVAR][MAXM];
 } recon_t;
 
 static double quad_form(int n, const double* B, const double* a) {
@@ -656,6 +661,137 @@ static double quad_form(int n, const double* B, const double* a) {
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) s += a[i] * B[i * n + j] * a[j];
   return s;
+}
+
+/* TENO selection (Eqs. new_scale_separation, normalize, cutoff,
+ * TENO_reconstruction111/222) of one field from its large and directional
+ * coefficients; returns the final coefficients, the selection byte and the
+ * smallest |chi - C_T| */
+static unsigned char teno_field(const omesh* M, const int32_t* nsm, const double* a,
+                                double as[KSM][MSM], double* c, double* margin) {
+  double beta[KSM + 1];
+  for (int j = 0; j < KSM; ++j) beta[j] = quad_form(MSM, M->B2, as[j]);
+  beta[KSM] = quad_form(M->m, M->Br, a);
+  double gam[KSM + 1], sum = 0.0;
+  for (int k = 0; k <= KSM; ++k) {
+    int present = k == KSM || nsm[k];
+    gam[k] = present ? 1.0 / pow(beta[k] + M->eps, 6.0) : 0.0;
+    sum += gam[k];
+  }
+  *margin = 1e300;
+  if (M->linear) {
+    for (int l = 0; l < M->m; ++l) c[l] = a[l];
+    return 8;
+  }
+  for (int k = 0; k <= KSM; ++k) {
+    int present = k == KSM || nsm[k];
+    double d = fabs(gam[k] / sum - M->ct);
+    if (present && d < *margin) *margin = d;
+  }
+  if (!(gam[KSM] / sum < M->ct)) {
+    for (int l = 0; l < M->m; ++l) c[l] = a[l];
+    return 8;
+  }
+  double s2 = gam[0] + gam[1] + gam[2];
+  int nd = 0;
+  unsigned char sel = 0;
+  for (int k = 0; k < KSM; ++k) {
+    if (!nsm[k]) continue;
+    double chi = gam[k] / s2;
+    if (fabs(chi - M->ct) < *margin) *margin = fabs(chi - M->ct);
+    if (!(chi < M->ct)) {
+      sel |= (unsigned char)(1 << k);
+      ++nd;
+    }
+  }
+  for (int l = 0; l < M->m; ++l) {
+    double v = 0.0;
+    if (l < MSM)
+      for (int k = 0; k < KSM; ++k)
+        if ((sel >> k) & 1) v += as[k][l] / nd;
+    c[l] = v;
+  }
+  return sel;
+}
+
+/* Eigenvectors of the Euler flux Jacobian in the direction (nx, ny) at state
+ * W (conservative), as matrices acting on conservative variables: L (rows,
+ * characteristic fields u-c, u (entropy), u (shear), u+c) and R = L^-1.  They
+ * are the textbook 1D eigenvectors in the face frame (normal velocity un,
+ * tangential ut) composed with the rotation T: L = L' T, R = T^T R'. */
+static void char_basis(double g, const double* W, double nx, double ny, double L[4][4],
+                       double R[4][4]) {
+  double r = W[0], un = (W[1] * nx + W[2] * ny) / r, ut = (W[2] * nx - W[1] * ny) / r;
+  double q2 = un * un + ut * ut, p = (g - 1.0) * (W[3] - 0.5 * r * q2);
+  double c = sqrt(g * p / r), H = (W[3] + p) / r;
+  double b1 = (g - 1.0) / (c * c), b2 = 0.5 * b1 * q2;
+  double Lf[4][4] = {{0.5 * (b2 + un / c), 0.5 * (-b1 * un - 1.0 / c), -0.5 * b1 * ut, 0.5 * b1},
+                     {1.0 - b2, b1 * un, b1 * ut, -b1},
+                     {-ut, 0.0, 1.0, 0.0},
+                     {0.5 * (b2 - un / c), 0.5 * (-b1 * un + 1.0 / c), -0.5 * b1 * ut, 0.5 * b1}};
+  double Rf[4][4] = {{1.0, 1.0, 0.0, 1.0},
+                     {un - c, un, 0.0, un + c},
+                     {ut, ut, 1.0, ut},
+                     {H - un * c, 0.5 * q2, ut, H + un * c}};
+  double T[4][4] = {{1, 0, 0, 0}, {0, nx, ny, 0}, {0, -ny, nx, 0}, {0, 0, 0, 1}};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double sl = 0.0, sr = 0.0;
+      for (int k = 0; k < 4; ++k) {
+        sl += Lf[i][k] * T[k][j];
+        sr += T[k][i] * Rf[k][j];
+      }
+      L[i][j] = sl;
+      R[i][j] = sr;
+    }
+}
+
+/* Characteristic-variable reconstruction (Sec. 2.3: characteristic variables
+ * suppress oscillations better than conservative ones): for each local edge
+ * e of cell t, the coefficients of the four conservative variables are
+ * projected on the characteristic fields of the edge's outward normal
+ * direction at the cell-average state, each field takes its own TENO
+ * selection, and the result is mapped back.  Since the projection is linear
+ * and constant over the cell, the edge's reconstruction is again a
+ * polynomial of the same basis with coefficients R c~. */
+static void char_faces(const omesh* M, int64_t t, const double* U, recon_t* out) {
+  const int32_t* nsm = M->nsm + (int64_t)KSM * t;
+  const double* P = M->P + 6 * t;
+  double W[4];
+  for (int v = 0; v < 4; ++v) W[v] = U[(int64_t)v * M->nc + t];
+  for (int v = 0; v < 4; ++v) out->margin[v] = 1e300;
+  for (int e = 0; e < 3; ++e) {
+    int e1 = (e + 1) % 3;
+    double dx = P[2 * e1] - P[2 * e], dy = P[2 * e1 + 1] - P[2 * e + 1];
+    double len = hypot(dx, dy);
+    double L[4][4], R[4][4];
+    char_basis(M->gam, W, dy / len, -dx / len, L, R);
+    double cc[4][MAXM];
+    for (int i = 0; i < 4; ++i) {
+      double a[MAXM], as[KSM][MSM], mg;
+      for (int l = 0; l < M->m; ++l) {
+        double s_ = 0.0;
+        for (int v = 0; v < 4; ++v) s_ += L[i][v] * out->a_large[v][l];
+        a[l] = s_;
+      }
+      for (int k = 0; k < KSM; ++k)
+        for (int l = 0; l < MSM; ++l) {
+          double s_ = 0.0;
+          for (int v = 0; v < 4; ++v) s_ += L[i][v] * out->a_small[v][k][l];
+          as[k][l] = s_;
+        }
+      unsigned char sl = teno_field(M, nsm, a, as, cc[i], &mg);
+      if (e == 0) out->sel[i] = sl;
+      if (mg < out->margin[i]) out->margin[i] = mg;
+    }
+    for (int v = 0; v < 4; ++v)
+      for (int l = 0; l < M->m; ++l) {
+        double s_ = 0.0;
+        for (int i = 0; i < 4; ++i) s_ += R[v][i] * cc[i][l];
+        out->coef_f[e][v][l] = s_;
+      }
+  }
+  out->charf = 1;
 }
 
 static void reconstruct(const omesh* M, int64_t t, const double* U, const unsigned char* sel_in,
@@ -779,11 +915,15 @@ static void reconstruct(const omesh* M, int64_t t, const double* U, const unsign
       out->w[v][k] = w[k];
     }
   }
+  out->charf = 0;
+  if (M->charvar && M->nvar == 4 && M->scheme == 0) char_faces(M, t, U, out);
 }
 
 /* value of the reconstruction of cell t at physical point (x, y) */
-static void eval_point(const omesh* M, int64_t t, const double* U, const recon_t* R, double x,
-                       double y, double* val) {
+/* value at physical point (x, y) of the reconstruction of cell t used on its
+ * local edge e (e only matters for the characteristic reconstruction) */
+static void eval_point(const omesh* M, int64_t t, const double* U, const recon_t* R, int e,
+                       double x, double y, double* val) {
   double Ji[4], x0[2], xi[2];
   ref_map(M, t, Ji, x0);
   /* bring (x, y) to the periodic image nearest the cell centroid */
@@ -795,8 +935,9 @@ static void eval_point(const omesh* M, int64_t t, const double* U, const recon_t
   to_ref(Ji, x0, x, y, xi);
   for (int v = 0; v < M->nvar; ++v) {
     double s = U[(int64_t)v * M->nc + t];
+    const double* cf = R->charf ? R->coef_f[e][v] : R->coef[v];
     for (int l = 0; l < M->m; ++l)
-      s += R->coef[v][l] * (ipow(xi[0], M->ex[l][0]) * ipow(xi[1], M->ex[l][1]) - M->mean0[l]);
+      s += cf[l] * (ipow(xi[0], M->ex[l][0]) * ipow(xi[1], M->ex[l][1]) - M->mean0[l]);
     val[v] = s;
   }
 }
@@ -1149,6 +1290,7 @@ void* oracle_new(int64_t nv, const double* xy, int64_t nc, const int32_t* tri, i
   M->rot[3] = dopt[8];
   M->rot[4] = dopt[9];
   M->scheme = iopt[6];
+  M->charvar = iopt[7];
   M->cw_dk = dopt[10];
   M->r = M->order - 1;
   M->m = (M->r + 1) * (M->r + 2) / 2 - 1;
@@ -1315,9 +1457,9 @@ static void face_flux(const omesh* M, int64_t c, int e, const double* U, const r
   for (int k = 0; k < M->nq; ++k) {
     double x = P[2 * e] + M->gt[k] * dx, y = P[2 * e + 1] + M->gt[k] * dy;
     double UL[4], UR[4], F[4];
-    eval_point(M, c, U, Rc, x, y, UL);
+    eval_point(M, c, U, Rc, e, x, y, UL);
     if (n >= 0)
-      eval_point(M, n, U, Rn, x, y, UR);
+      eval_point(M, n, U, Rn, M->fedge[3 * c + e], x, y, UR);
     else
       ghost_state(M, M->fbc[3 * c + e], UL, nx, ny, x, y, UR);
     num_flux(M, UL, UR, nx, ny, x, y, F);
@@ -1492,6 +1634,7 @@ int oracle_rk3_step(void* h, double* U, double time, double dt) {
  * given by sel_in), flux branches frozen at the forward states */
 int oracle_residual_vjp(void* h, const double* U, double time, const double* w, double* vout,
                         const uint8_t* sel_in) {
+  if (((omesh*)h)->charvar || ((omesh*)h)->scheme) return E_INVAL; /* TENO, conservative variables */
   omesh* M = (omesh*)h;
   M->time = time;
   int rc = oracle_prepare(h, 0, NULL);
@@ -1520,9 +1663,9 @@ int oracle_residual_vjp(void* h, const double* U, double time, const double* w, 
       for (int k = 0; k < nq; ++k) {
         double x = P[2 * e] + M->gt[k] * dx, y = P[2 * e + 1] + M->gt[k] * dy;
         double UL[4], UR[4], JL[16], JR[16];
-        eval_point(M, c, U, &RC[c], x, y, UL);
+        eval_point(M, c, U, &RC[c], e, x, y, UL);
         if (n >= 0)
-          eval_point(M, n, U, &RC[n], x, y, UR);
+          eval_point(M, n, U, &RC[n], M->fedge[3 * c + e], x, y, UR);
         else
           ghost_state(M, M->fbc[3 * c + e], UL, nx, ny, x, y, UR);
         flux_jac(M, UL, UR, nx, ny, x, y, JL, JR);
@@ -1623,6 +1766,7 @@ int oracle_residual_vjp(void* h, const double* U, double time, const double* w, 
  * lam_np1, selection frozen at each stage's state (sel1..3 optional) */
 int oracle_rk3_vjp(void* h, const double* Un, double time, double dt, const double* lam_np1,
                    double* lam_n) {
+  if (((omesh*)h)->charvar || ((omesh*)h)->scheme) return E_INVAL; /* TENO, conservative variables */
   omesh* M = (omesh*)h;
   int64_t N = M->nc * M->nvar;
   double* R = (double*)malloc(sizeof(double) * N);
@@ -1657,6 +1801,20 @@ int oracle_rk3_vjp(void* h, const double* Un, double time, double dt, const doub
   free(l1);
   free(tmp);
   return rc;
+}
+
+/* characteristic basis of the Euler flux in direction (nx, ny) at W, for
+ * pins: L, R row-major 4x4 */
+void oracle_char_basis(void* h, const double* W, double nx, double ny, double* Lout,
+                       double* Rout) {
+  omesh* M = (omesh*)h;
+  double L[4][4], R[4][4];
+  char_basis(M->gam, W, nx, ny, L, R);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      Lout[4 * i + j] = L[i][j];
+      Rout[4 * i + j] = R[i][j];
+    }
 }
 
 /* flux access for pins at face point (x, y): F [nvar], JL/JR [nvar*nvar]

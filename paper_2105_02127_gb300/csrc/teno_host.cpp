@@ -67,7 +67,7 @@ struct teno_ctx {
   std::vector<int32_t> st_large, st_small;  // user ids, [nc][ns], [nc][36]
   // device data
   DeviceMesh dm;
-  DevBuf b_halo_off, b_halo_ids, b_halo_loc, b_g32, b_wq, b_psi, b_cspeed;
+  DevBuf b_halo_off, b_halo_ids, b_halo_loc, b_g32, b_wq, b_psi, b_cspeed, b_coef;
   DevBuf b_ahat, b_nbr, b_smask, b_fcells, b_fedges, b_fgeom, b_fgeom2, b_cfaces, b_inv_area, b_cfl_len,
       b_perm;
   DevBuf b_U, b_U1, b_U2, b_R, b_tmp, b_Uq, b_K, b_sel, b_sel_ovr, b_maxlam, b_flag;
@@ -685,7 +685,8 @@ int run_precompute(teno_ctx* ctx) {
   // Euler on the pair path with the TMA kernel: FP32 selection matrices with
   // column sums of |G| (large slots M + 1 floats, directional slots 5 + 1) and
   // W = Psi' G, the large polynomial's Gauss-point values per unit difference
-  const bool wform = store == TENO_FP64 && p.n_var == 4 && p.recon_variant == 2 && p.scheme == 0;
+  const bool wform = store == TENO_FP64 && p.n_var == 4 && p.recon_variant == 2 && p.scheme == 0 &&
+                     p.charvar == 0;
   const int nq3 = 3 * ctx->nq;
   const int E32 = ns * (m + 1) + kSmallK * kSmallN * (kSmallM + 1), EW = ns * nq3;
   std::vector<float> g32(wform ? (size_t)ntile * E32 * kTile : 0, 0.f);
@@ -867,6 +868,13 @@ int run_precompute(teno_ctx* ctx) {
   dm.adv_r2 = p.adv_r2;
   dm.scheme = p.scheme;
   dm.cweno_dk = p.cweno_dk;
+  dm.charvar = p.charvar;
+  dm.coef_out = nullptr;
+  if (p.charvar && ctx->device >= 0) {
+    int e4 = dev_alloc(ctx, ctx->b_coef, sizeof(double) * (size_t)npad * 4 * (m + 15));
+    if (e4) return e4;
+    dm.coef_out = (double*)ctx->b_coef.p;
+  }
   dm.cell_speed = nullptr;
   if (p.n_var == 1 && p.adv_field == 1) {
     // CFL speed: |omega| times the largest r phi(r) over the vertices (a cell
@@ -1018,6 +1026,7 @@ int stage_flux(teno_ctx* ctx, const double* U, uint8_t* sel_out, double time,
   }
   long pe = prof_begin(ctx, K_RECON);
   CK(launch_recon(ctx->dm, U, Us, uq, sel_out, sel_in, ctx->stream), "recon launch");
+  if (ctx->dm.charvar) CK(launch_char_finish(ctx->dm, U, uq, ctx->stream), "char finish launch");
   prof_end(ctx, pe);
   pe = prof_begin(ctx, K_FLUX);
   CK(launch_face_flux(ctx->dm, uq, ctx->b_K.p, time, ctx->stream), "face flux launch");
@@ -1184,6 +1193,7 @@ void teno_default_params(teno_params* p) {
   p->adv_r2 = 0.0;
   p->scheme = 0;
   p->cweno_dk = 1e4;
+  p->charvar = 0;
   p->cfl = 0.4;
 }
 
@@ -1229,7 +1239,7 @@ int teno_destroy(teno_ctx* ctx) {
   }
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  DevBuf* bufs[] = {&ctx->b_halo_off, &ctx->b_halo_ids, &ctx->b_halo_loc, &ctx->b_g32, &ctx->b_wq, &ctx->b_psi, &ctx->b_cspeed, &ctx->b_ahat, &ctx->b_nbr, &ctx->b_smask, &ctx->b_fcells, &ctx->b_fedges,
+  DevBuf* bufs[] = {&ctx->b_halo_off, &ctx->b_halo_ids, &ctx->b_halo_loc, &ctx->b_g32, &ctx->b_wq, &ctx->b_psi, &ctx->b_cspeed, &ctx->b_coef, &ctx->b_ahat, &ctx->b_nbr, &ctx->b_smask, &ctx->b_fcells, &ctx->b_fedges,
                     &ctx->b_fgeom, &ctx->b_fgeom2, &ctx->b_cfaces, &ctx->b_inv_area, &ctx->b_cfl_len,
                     &ctx->b_perm, &ctx->b_U, &ctx->b_U1, &ctx->b_U2, &ctx->b_R, &ctx->b_tmp,
                     &ctx->b_Uq, &ctx->b_K, &ctx->b_sel, &ctx->b_sel_ovr, &ctx->b_maxlam,
@@ -1297,7 +1307,8 @@ int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
       (p->adv_field == 1 && (p->n_var != 1 || !std::isfinite(p->adv_omega) ||
                              !std::isfinite(p->adv_cx) || !std::isfinite(p->adv_cy) ||
                              !std::isfinite(p->adv_r1) || !std::isfinite(p->adv_r2))) ||
-      p->scheme < 0 || p->scheme > 1 || (p->scheme == 1 && !(p->cweno_dk > 1.0)))
+      p->scheme < 0 || p->scheme > 1 || (p->scheme == 1 && !(p->cweno_dk > 1.0)) ||
+      p->charvar < 0 || p->charvar > 1 || (p->charvar == 1 && (p->n_var != 4 || p->scheme != 0)))
     return fail(ctx, TENO_EINVAL, "precompute: bad parameters");
   const int nq_default = p->order <= 4 ? 2 : 3;
   if (p->nq != 0 && p->nq != nq_default)
@@ -1519,7 +1530,8 @@ int teno_residual_vjp(teno_ctx* ctx, const double* w, double* v, int on_device) 
   if (!w || !v) return fail(ctx, TENO_EINVAL, "residual_vjp: null pointer");
   if (ctx->prm.precision == TENO_FP32_MIXED)
     return fail(ctx, TENO_EINVAL, "adjoint: FP64 precisions only");
-  if (ctx->prm.scheme != 0) return fail(ctx, TENO_EINVAL, "adjoint: TENO only");
+  if (ctx->prm.scheme != 0 || ctx->prm.charvar != 0)
+    return fail(ctx, TENO_EINVAL, "adjoint: TENO in conservative variables only");
   rc = ensure_adjoint(ctx);
   if (rc) return rc;
   rc = to_internal(ctx, w, (double*)ctx->b_l1.p, on_device);
@@ -1537,7 +1549,8 @@ int teno_adjoint_step(teno_ctx* ctx, double dt, const double* lam_np1, double* l
   if (!lam_np1 || !lam_n || !(dt > 0.0)) return fail(ctx, TENO_EINVAL, "adjoint_step: bad args");
   if (ctx->prm.precision == TENO_FP32_MIXED)
     return fail(ctx, TENO_EINVAL, "adjoint: FP64 precisions only");
-  if (ctx->prm.scheme != 0) return fail(ctx, TENO_EINVAL, "adjoint: TENO only");
+  if (ctx->prm.scheme != 0 || ctx->prm.charvar != 0)
+    return fail(ctx, TENO_EINVAL, "adjoint: TENO in conservative variables only");
   rc = ensure_adjoint(ctx);
   if (rc) return rc;
   const int64_t n = (int64_t)ctx->prm.n_var * ctx->npad;

@@ -686,7 +686,24 @@ struct ReconArgs {
   int linear, e_entries;
   int scheme;   // 0 TENO, 1 CWENO
   double cw_dK; // CWENO d_K = 1 - 1/d'_K
+  double* coef_out;  // characteristic mode: [n_pad][4][m + 15] coefficients out
 };
+
+// characteristic mode: store the cell's large and directional coefficients of
+// variable v in FP64 for char_finish_kernel, in place of selection and
+// evaluation
+template <int M, typename TC>
+__device__ __forceinline__ void store_coefs(const ReconArgs& a, int64_t c, int v, const TC* acc,
+                                            const TC (&as)[kSmallK][kSmallM]) {
+  double* o = a.coef_out + ((int64_t)c * 4 + v) * (M + kSmallK * kSmallM);
+#pragma unroll
+  for (int l = 0; l < M; ++l) o[l] = to_d(acc[l]);
+#pragma unroll
+  for (int k = 0; k < kSmallK; ++k)
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) o[M + k * kSmallM + l] = to_d(as[k][l]);
+  if (a.sel_out) a.sel_out[(int64_t)v * a.n_pad + c] = 8;
+}
 
 // CWENO weights (Eqs. CWENOweight, CWENOOptimalLinearweight/02) from the
 // smoothness indicators: alpha = d / (beta + eps)^4 with d_K = cw_dK and
@@ -790,6 +807,10 @@ __device__ __forceinline__ void plain_finish(const ReconArgs& a, const TT& ev, i
                                              double u0, float2 u0s, const TA (&acc)[M],
                                              const TA (&as)[kSmallK][kSmallM]) {
   constexpr bool kMixed = std::is_same<TA, float>::value;
+  if (a.coef_out) {
+    store_coefs<M, TA>(a, c, v, acc, as);
+    return;
+  }
   const int present = a.smask[c];
   uint8_t sel;
   const bool cweno = a.scheme == 1 && !a.linear;
@@ -977,6 +998,10 @@ template <int M, int NQ, int NV>
 __device__ __forceinline__ void df_finish(const ReconArgs& a, const DFTable& ev, int64_t c, int v,
                                           const DF (&acc)[M],
                                           const DF (&as)[kSmallK][kSmallM]) {
+  if (a.coef_out) {
+    store_coefs<M, DF>(a, c, v, acc, as);
+    return;
+  }
   const int present = a.smask[c];
   uint8_t sel;
   const bool cweno = a.scheme == 1 && !a.linear;
@@ -2010,6 +2035,133 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
   cp_async_wait<0>();
 }
 
+// ------------------------------------ characteristic variables (charvar)
+// Characteristic reconstruction (Sec. 2.3 prefers characteristic variables):
+// thread (cell, local edge e).  The coefficients of the four conservative
+// variables are projected on the characteristic fields of the edge's outward
+// normal at the cell-average state, L = L' T and R = T^T R' with T the
+// rotation to the edge frame and L', R' the textbook eigenvectors of the 1D
+// Euler flux Jacobian in that frame (fields u-c, entropy, shear, u+c).  Each
+// field takes its own TENO selection (select_fp64), and the edge's Gauss-point
+// values are U_0 + R (Psi' c~).  FP64 throughout; the values are stored in the
+// path's Gauss-point type.
+template <typename TQ>
+__device__ __forceinline__ TQ from_d(double x) {
+  if constexpr (std::is_same<TQ, DF>::value) {
+    const float h = (float)x;
+    return DF{h, (float)(x - (double)h)};
+  } else {
+    return (TQ)x;
+  }
+}
+
+template <int M, int NQ, typename TQ>
+__global__ void __launch_bounds__(128) char_finish_kernel(
+    const double* __restrict__ coef, const double* __restrict__ U,
+    const uint8_t* __restrict__ smask, const int32_t* __restrict__ c_faces,
+    const double* __restrict__ f_geom, const EvalTable ev, TQ* __restrict__ Uq, int64_t n_cell,
+    int64_t n_pad, double g, double ct, double eps, int linear) {
+  constexpr int C = M + kSmallK * kSmallM;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_cell * 3) return;
+  const int64_t c = idx / 3;
+  const int e = (int)(idx % 3);
+  const int cf = c_faces[3 * c + e];
+  const int64_t f = cf >> 1;
+  const double sg = (cf & 1) ? -1.0 : 1.0;  // the neighbour's normal is the opposite one
+  const double nx = sg * f_geom[5 * f], ny = sg * f_geom[5 * f + 1];
+  double W[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) W[v] = U[(int64_t)v * n_pad + c];
+  // eigenvectors at the cell average
+  const double r = W[0], un = (W[1] * nx + W[2] * ny) / r, ut = (W[2] * nx - W[1] * ny) / r;
+  const double q2 = un * un + ut * ut, p = (g - 1.0) * (W[3] - 0.5 * r * q2);
+  const double cs = sqrt(g * p / r), H = (W[3] + p) / r;
+  const double b1 = (g - 1.0) / (cs * cs), b2 = 0.5 * b1 * q2;
+  const double Lf[4][4] = {
+      {0.5 * (b2 + un / cs), 0.5 * (-b1 * un - 1.0 / cs), -0.5 * b1 * ut, 0.5 * b1},
+      {1.0 - b2, b1 * un, b1 * ut, -b1},
+      {-ut, 0.0, 1.0, 0.0},
+      {0.5 * (b2 - un / cs), 0.5 * (-b1 * un + 1.0 / cs), -0.5 * b1 * ut, 0.5 * b1}};
+  const double Rf[4][4] = {{1.0, 1.0, 0.0, 1.0},
+                           {un - cs, un, 0.0, un + cs},
+                           {ut, ut, 1.0, ut},
+                           {H - un * cs, 0.5 * q2, ut, H + un * cs}};
+  // L = L' T, R = T^T R' with T = rotation (m_x, m_y) -> (m_n, m_t)
+  double L[4][4], R[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    L[i][0] = Lf[i][0];
+    L[i][1] = Lf[i][1] * nx - Lf[i][2] * ny;
+    L[i][2] = Lf[i][1] * ny + Lf[i][2] * nx;
+    L[i][3] = Lf[i][3];
+    R[0][i] = Rf[0][i];
+    R[1][i] = nx * Rf[1][i] - ny * Rf[2][i];
+    R[2][i] = ny * Rf[1][i] + nx * Rf[2][i];
+    R[3][i] = Rf[3][i];
+  }
+  const int present = smask[c];
+  const double* cv = coef + c * 4 * C;
+  double corr[4][NQ];
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) corr[v][q] = 0.0;
+#pragma unroll 1
+  for (int i = 0; i < 4; ++i) {
+    double ch[C];
+#pragma unroll
+    for (int l = 0; l < C; ++l)
+      ch[l] = L[i][0] * cv[l] + L[i][1] * cv[C + l] + L[i][2] * cv[2 * C + l] +
+              L[i][3] * cv[3 * C + l];
+    uint8_t sel = 8;
+    if (!linear) {
+      double beta[kSmallK + 1];
+      double b = 0.0;
+#pragma unroll
+      for (int l = 0; l < M; ++l) b = fma(ch[l], ch[l], b);
+      beta[kSmallK] = b;
+#pragma unroll
+      for (int k = 0; k < kSmallK; ++k) {
+        double bq = 0.0;
+#pragma unroll
+        for (int l = 0; l < kSmallM; ++l) bq = fma(ch[M + k * kSmallM + l], ch[M + k * kSmallM + l], bq);
+        beta[k] = bq;
+      }
+      sel = select_fp64(beta, present, ct, eps);
+    }
+    double cfin[M];
+    if (sel & 8) {
+#pragma unroll
+      for (int l = 0; l < M; ++l) cfin[l] = ch[l];
+    } else {
+      const int nd = (sel & 1) + ((sel >> 1) & 1) + ((sel >> 2) & 1);
+      const double w = nd ? 1.0 / nd : 0.0;
+#pragma unroll
+      for (int l = 0; l < M; ++l) cfin[l] = 0.0;
+#pragma unroll
+      for (int k = 0; k < kSmallK; ++k) {
+        if (!((sel >> k) & 1)) continue;
+#pragma unroll
+        for (int l = 0; l < kSmallM; ++l) cfin[l] = fma(w, ch[M + k * kSmallM + l], cfin[l]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double gq = 0.0;
+#pragma unroll
+      for (int l = 0; l < M; ++l) gq = fma(cfin[l], ev.psi[(e * NQ + q) * kMaxM + l], gq);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) corr[v][q] = fma(R[v][i], gq, corr[v][q]);
+    }
+  }
+  TQ* out = Uq + ((int64_t)(c * 3 + e) * NQ) * 4;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[q * 4 + v] = from_d<TQ>(W[v] + corr[v][q]);
+}
+
 // FP32 hi/lo split of a state: hi = fl32(U), lo = fl32(U - hi)
 __global__ void split_kernel(const double* __restrict__ U, float2* __restrict__ Us, int64_t n_cell,
                              int64_t n_pad, int n_var) {
@@ -2713,6 +2865,27 @@ cudaError_t launch_recon_tma_w(const ReconArgs& a, const DeviceMesh& dm, int* er
   return cudaGetLastError();
 }
 
+cudaError_t launch_char_finish(const DeviceMesh& dm, const double* U, void* Uq, cudaStream_t st) {
+  if (!dm.coef_out || dm.n_var != 4) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)((dm.n_cell * 3 + 127) / 128);
+  return dispatch_order(dm.order, [&](auto Mc, auto NSc) -> cudaError_t {
+    constexpr int M = decltype(Mc)::value;
+    (void)NSc;
+    constexpr int NQ = (M <= 9) ? 2 : 3;
+    if (dm.nq != NQ) return cudaErrorInvalidValue;
+    auto go = [&](auto tq) -> cudaError_t {
+      using TQ = typename decltype(tq)::type;
+      char_finish_kernel<M, NQ, TQ><<<grid, 128, 0, st>>>(
+          dm.coef_out, U, dm.smask, dm.c_faces, dm.f_geom, dm.eval, (TQ*)Uq, dm.n_cell, dm.n_pad,
+          dm.gamma, dm.ct, dm.eps, dm.linear);
+      return cudaGetLastError();
+    };
+    if (dm.precision == TENO_FP64) return go(TypeTag<DF>{});
+    if (dm.precision == TENO_FP32_MIXED) return go(TypeTag<float>{});
+    return go(TypeTag<double>{});
+  });
+}
+
 cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us, void* Uq,
                          uint8_t* sel_out, const uint8_t* sel_in, cudaStream_t st) {
   if (dm.precision != TENO_FP64_NATIVE && !Us) return cudaErrorInvalidValue;
@@ -2733,6 +2906,7 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
   a.e_entries = dm.e_entries;
   a.scheme = dm.scheme;
   a.cw_dK = 1.0 - 1.0 / dm.cweno_dk;
+  a.coef_out = dm.charvar ? dm.coef_out : nullptr;
   const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
   return dispatch_order(dm.order, [&](auto Mc, auto NSc) -> cudaError_t {
     constexpr int M = decltype(Mc)::value, NS = decltype(NSc)::value;

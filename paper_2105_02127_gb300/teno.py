@@ -39,7 +39,7 @@ class teno_params(C.Structure):
                 ("adv_x", C.c_double), ("adv_y", C.c_double), ("cfl", C.c_double),
                 ("adv_field", C.c_int32), ("adv_cx", C.c_double), ("adv_cy", C.c_double),
                 ("adv_omega", C.c_double), ("adv_r1", C.c_double), ("adv_r2", C.c_double),
-                ("scheme", C.c_int32), ("cweno_dk", C.c_double)]
+                ("scheme", C.c_int32), ("cweno_dk", C.c_double), ("charvar", C.c_int32)]
 
 
 _lib = None

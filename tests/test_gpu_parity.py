@@ -254,6 +254,34 @@ def test_cweno(T, oracle_mod, order, flux, precision, variant):
             assert ei.value.code == T.TENO_EINVAL  # the adjoint takes TENO only
 
 
+@pytest.mark.parametrize("precision,variant", [(0, 2), (0, 1), (2, 2), (1, 2)],
+                         ids=["pairs-tma", "pairs-direct", "native", "mixed"])
+@pytest.mark.parametrize("order,flux", [(4, 1), (5, 1), (6, 2)])
+def test_characteristic(T, oracle_mod, order, flux, precision, variant):
+    """TENO in characteristic variables per face (Sec. 2.3) on the vortex and
+    on the discontinuous state: residual against the oracle (FP64 paths at the
+    1e-11 bar; FP32-mixed reported, below 1e-4); the adjoint refuses it."""
+    for mesh, kind in [(inputs.jittered_mesh(33, 31, 10.0, 10.0, seed=1019), "vortex"),
+                       (inputs.jittered_mesh(40, 40, 10.0, 10.0, seed=1007), "blast")]:
+        U = _blast(mesh) if kind == "blast" else inputs.cell_average(mesh, inputs.isentropic_vortex)
+        t = T.Teno(device=0).load(mesh)
+        t.precompute_stencils(order=order, n_var=4, flux=flux, precision=precision,
+                              recon_variant=variant, charvar=1)
+        t.set_state(U)
+        R, _ = t.residual()
+        o = oracle_mod.Oracle(mesh, order=order, n_var=4, flux=flux, charvar=True)
+        Ro, _, mg = o.residual(U)
+        e = rel(R, Ro)
+        print(f"characteristic TENO{order} {kind} precision {precision} variant {variant}: "
+              f"rel err {e:.2e}, smallest oracle margin {mg.min():.1e}")
+        assert e <= (TOL if precision != 1 else 1e-4)
+        t.check_state()
+        if precision == 0:
+            with pytest.raises(T.TenoError) as ei:
+                t.residual_vjp(np.zeros_like(U))
+            assert ei.value.code == T.TENO_EINVAL
+
+
 ROT = (0.5, 0.5, 1.0)  # v = (0.5 - y, x - 0.5), the solid-body case of Sec. 5
 ROT_TAPER = (0.5, 0.5, 1.0, 0.45, 0.5)  # the same, tapered to zero at r = 0.5
 

@@ -482,6 +482,76 @@ def test_cweno_convergence_order(oracle_mod):
     assert rate > 4.5, (e1, e2, rate)
 
 
+# --------------------------------------------- characteristic variables
+def test_char_basis_diagonalises_flux_jacobian(oracle_mod):
+    """L (dF_n/dU) R = diag(u_n - c, u_n, u_n, u_n + c) and L R = I, with the
+    Jacobian of the Euler normal flux taken by central differences of the flux
+    written out here."""
+    mesh = _mesh(4)
+    o = oracle_mod.Oracle(mesh, order=3, n_var=4, flux=1)
+    g = 1.4
+
+    def Fn(U, nx, ny):
+        r, mx, my, E = U
+        u, v = mx / r, my / r
+        p = (g - 1) * (E - 0.5 * r * (u * u + v * v))
+        un = u * nx + v * ny
+        return np.array([r * un, mx * un + p * nx, my * un + p * ny, (E + p) * un])
+
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        r, u, v, p = 0.5 + rng.random(), rng.standard_normal(), rng.standard_normal(), 0.5 + rng.random()
+        W = np.array([r, r * u, r * v, p / (g - 1) + 0.5 * r * (u * u + v * v)])
+        th = rng.random() * 2 * np.pi
+        nx, ny = np.cos(th), np.sin(th)
+        Lm, Rm = o.char_basis(W, nx, ny)
+        assert np.abs(Lm @ Rm - np.eye(4)).max() < 1e-12
+        h = 1e-6
+        A = np.stack([(Fn(W + h * e, nx, ny) - Fn(W - h * e, nx, ny)) / (2 * h)
+                      for e in np.eye(4)], axis=1)
+        c, un = np.sqrt(g * p / r), u * nx + v * ny
+        D = Lm @ A @ Rm
+        assert np.abs(D - np.diag([un - c, un, un, un + c])).max() < 1e-7 * (1 + abs(un) + c)
+
+
+def test_char_linear_equals_conservative(oracle_mod):
+    """With the linear scheme every field keeps the large stencil and
+    R (L a) = a: the characteristic reconstruction equals the conservative one
+    to rounding (vortex with HLL, discontinuous state with HLLC)."""
+    mesh = inputs.jittered_mesh(14, 13, 10.0, 10.0, seed=1250)
+    V = mesh.unwrapped_vertices().mean(axis=1)
+    Uv = inputs.cell_average(mesh, inputs.isentropic_vortex)
+    inside = (np.abs(V[:, 0] - 5) < 2) & (np.abs(V[:, 1] - 5) < 2)
+    Ub = inputs.prim_to_cons(np.where(inside, 1.0, 0.5), 0.3 + 0 * V[:, 0], -0.2 + 0 * V[:, 0],
+                             np.where(inside, 1.0, 0.7))
+    for U, flux in [(Uv, 1), (Ub, 2)]:
+        Rc, _, _ = oracle_mod.Oracle(mesh, order=5, n_var=4, flux=flux, linear=True).residual(U)
+        Rh, _, _ = oracle_mod.Oracle(mesh, order=5, n_var=4, flux=flux, linear=True,
+                                     charvar=True).residual(U)
+        assert np.abs(Rc - Rh).max() <= 1e-12 * np.abs(Rc).max()
+
+
+def test_char_contact_keeps_velocity_and_pressure(oracle_mod):
+    """A contact (density jump, uniform velocity and pressure): its differences
+    lie along the entropy eigenvector, the other fields vanish, so the
+    reconstruction keeps u and p at every Gauss point and the residual obeys
+    R_m = u R_rho and R_E = |u|^2/2 R_rho to rounding, although the TENO
+    selection cuts the large stencil near the jump."""
+    mesh = inputs.jittered_mesh(16, 16, 10.0, 10.0, seed=1251)
+    V = mesh.unwrapped_vertices().mean(axis=1)
+    u0, v0, p0 = 0.4, -0.3, 1.0
+    rho = np.where(np.hypot(V[:, 0] - 5, V[:, 1] - 5) < 2.5, 2.0, 1.0)
+    U = inputs.prim_to_cons(rho, u0 + 0 * rho, v0 + 0 * rho, p0 + 0 * rho)
+    o = oracle_mod.Oracle(mesh, order=5, n_var=4, flux=1, charvar=True)
+    R, sel, _ = o.residual(U)
+    assert (sel[1] != 8).any()  # the entropy field drops the large stencil somewhere
+    s = np.abs(R[0]).max()
+    assert s > 1e-3
+    assert np.abs(R[1] - u0 * R[0]).max() <= 1e-11 * s * abs(u0)
+    assert np.abs(R[2] - v0 * R[0]).max() <= 1e-11 * s * abs(v0)
+    assert np.abs(R[3] - 0.5 * (u0 * u0 + v0 * v0) * R[0]).max() <= 1e-11 * s
+
+
 # ---------------------------------------------------------------- adjoint
 def test_residual_adjoint_dot_product_linear(oracle_mod):
     """Scalar advection with frozen selection is linear in U, so
