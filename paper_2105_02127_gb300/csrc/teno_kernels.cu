@@ -207,16 +207,35 @@ __device__ __forceinline__ DF operator*(DF a, DF b) {
   e = fmaf(a.l, b.h, e);
   return fast_two_sum(p, e);
 }
+// Quotients: q1 from the correctly rounded reciprocal of b.h (1.5 ulp), the
+// exact remainder a - b q1 in pairs, and its quotient by the same reciprocal
+// (the correction carries a relative error of about one ulp); square roots:
+// the correctly rounded FP32 root and a correction scaled by rsqrt/2.  Build
+// with TENO_DF_IEEE_DIV=1 for IEEE FP32 divisions in both steps instead.
+#ifndef TENO_DF_IEEE_DIV
+#define TENO_DF_IEEE_DIV 0
+#endif
 __device__ __forceinline__ DF operator/(DF a, DF b) {
+#if TENO_DF_IEEE_DIV
   const float q1 = a.h / b.h;
   const DF r = a - b * DF{q1, 0.f};
   return fast_two_sum(q1, r.h / b.h);
+#else
+  const float rb = __frcp_rn(b.h);
+  const float q1 = a.h * rb;
+  const DF r = a - b * DF{q1, 0.f};
+  return fast_two_sum(q1, r.h * rb);
+#endif
 }
 __device__ __forceinline__ DF tsqrt(DF a) {
   const float s = sqrtf(a.h);
   if (!(a.h > 0.f)) return {s, 0.f};
   const DF r = a - DF{s, 0.f} * DF{s, 0.f};
+#if TENO_DF_IEEE_DIV
   return fast_two_sum(s, r.h / (2.f * s));
+#else
+  return fast_two_sum(s, r.h * (0.5f * rsqrtf(a.h)));
+#endif
 }
 __device__ __forceinline__ float val(DF x) { return x.h; }
 template <>
