@@ -729,8 +729,17 @@ __device__ __forceinline__ void store_coefs(const ReconArgs& a, int64_t c, int v
 // d_k = (1 - d_K)/K over the K present directional stencils; returns the
 // factors of P = sK P_K + sum_k s[k] P_k, i.e. sK = w_K / d_K and
 // s[k] = w_k - sK d_k (0 for absent stencils).
-__device__ __forceinline__ void cweno_factors(const double* beta, int present, double dK_in,
-                                              double eps, double& sK, double* s) {
+struct CwenoF {
+  double sK, s[kSmallK];
+};
+// out of line: the CWENO option must not raise the register count of the
+// TENO reconstruction kernels that share the finish code
+__device__ __noinline__ CwenoF cweno_factors(double b0, double b1, double b2, double bK,
+                                             int present, double dK_in, double eps) {
+  const double beta[kSmallK + 1] = {b0, b1, b2, bK};
+  CwenoF out;
+  double& sK = out.sK;
+  double* s = out.s;
   const int K = (present & 1) + ((present >> 1) & 1) + ((present >> 2) & 1);
   const double dK = K ? dK_in : 1.0, dk = K ? (1.0 - dK) / K : 0.0;
   double al[kSmallK + 1], sum = 0.0;
@@ -745,6 +754,7 @@ __device__ __forceinline__ void cweno_factors(const double* beta, int present, d
   sK = al[kSmallK] / sum / dK;
 #pragma unroll
   for (int k = 0; k < kSmallK; ++k) s[k] = ((present >> k) & 1) ? al[k] / sum - sK * dk : 0.0;
+  return out;
 }
 
 // TENO cutoff and two-step selection in FP64 (Eqs. new_scale_separation,
@@ -821,18 +831,22 @@ __device__ __forceinline__ bool chi_keep32_bound(const float* t, int k, int mask
 // fallback inside the guard band, FP32 Gauss-point values.
 // selection, final coefficients and Gauss-point values of cell c, variable v
 // (FP64-native and FP32-mixed paths)
-template <int M, int NQ, int NV, typename TA, typename TT>
+// kExt: compile the CWENO and characteristic-mode branches (the TENO-only
+// instantiations keep the register count of the default kernels down)
+template <int M, int NQ, int NV, typename TA, typename TT, bool kExt = true>
 __device__ __forceinline__ void plain_finish(const ReconArgs& a, const TT& ev, int64_t c, int v,
                                              double u0, float2 u0s, const TA (&acc)[M],
                                              const TA (&as)[kSmallK][kSmallM]) {
   constexpr bool kMixed = std::is_same<TA, float>::value;
-  if (a.coef_out) {
-    store_coefs<M, TA>(a, c, v, acc, as);
-    return;
+  if constexpr (kExt) {
+    if (a.coef_out) {
+      store_coefs<M, TA>(a, c, v, acc, as);
+      return;
+    }
   }
   const int present = a.smask[c];
   uint8_t sel;
-  const bool cweno = a.scheme == 1 && !a.linear;
+  const bool cweno = kExt && a.scheme == 1 && !a.linear;
   TA cf[M];
   if (cweno) {
     // beta and weights in FP64 (from the FP32 coefficients on the mixed path)
@@ -848,8 +862,10 @@ __device__ __forceinline__ void plain_finish(const ReconArgs& a, const TT& ev, i
       for (int l = 0; l < kSmallM; ++l) q = fma((double)as[k][l], (double)as[k][l], q);
       beta[k] = q;
     }
-    double sK, sk[kSmallK];
-    cweno_factors(beta, present, a.cw_dK, a.eps, sK, sk);
+    const CwenoF cw = cweno_factors(beta[0], beta[1], beta[2], beta[kSmallK], present, a.cw_dK,
+                                    a.eps);
+    const double sK = cw.sK;
+    const double* sk = cw.s;
 #pragma unroll
     for (int l = 0; l < M; ++l) cf[l] = TA(sK) * acc[l];
 #pragma unroll
@@ -1013,17 +1029,19 @@ __global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const TT 
 // path and in FP64 inside it; Gauss-point values are written in FP64.
 // selection, final coefficients and Gauss-point values of cell c, variable v
 // (double-float path), from the normalised stencil coefficients
-template <int M, int NQ, int NV>
+template <int M, int NQ, int NV, bool kExt = true>
 __device__ __forceinline__ void df_finish(const ReconArgs& a, const DFTable& ev, int64_t c, int v,
                                           const DF (&acc)[M],
                                           const DF (&as)[kSmallK][kSmallM]) {
-  if (a.coef_out) {
-    store_coefs<M, DF>(a, c, v, acc, as);
-    return;
+  if constexpr (kExt) {
+    if (a.coef_out) {
+      store_coefs<M, DF>(a, c, v, acc, as);
+      return;
+    }
   }
   const int present = a.smask[c];
   uint8_t sel;
-  const bool cweno = a.scheme == 1 && !a.linear;
+  const bool cweno = kExt && a.scheme == 1 && !a.linear;
   DF cf[M];
   if (cweno) {
     // beta = |a'|^2 in pairs, weights in FP64, combination in pairs
@@ -1041,8 +1059,10 @@ __device__ __forceinline__ void df_finish(const ReconArgs& a, const DFTable& ev,
         beta[k] = df_to_double(df_norm(q));
       }
     }
-    double sK, sk[kSmallK];
-    cweno_factors(beta, present, a.cw_dK, a.eps, sK, sk);
+    const CwenoF cw = cweno_factors(beta[0], beta[1], beta[2], beta[kSmallK], present, a.cw_dK,
+                                    a.eps);
+    const double sK = cw.sK;
+    const double* sk = cw.s;
     const DF fK = cst<DF>(sK);
 #pragma unroll
     for (int l = 0; l < M; ++l) cf[l] = fK * acc[l];
@@ -1305,11 +1325,11 @@ __global__ void __launch_bounds__(128) recon_halo_kernel(const ReconArgs a, cons
     for (int k = 0; k < kSmallK; ++k)
 #pragma unroll
       for (int l = 0; l < kSmallM; ++l) as[k][l] = df_norm(as[k][l]);
-    df_finish<M, NQ, NV>(a, ev, c, v, acc, as);
+    df_finish<M, NQ, NV, false>(a, ev, c, v, acc, as);
   } else if constexpr (kMode == 1) {
-    plain_finish<M, NQ, NV, float, DFTable>(a, ev, c, v, 0.0, u0s, acc, as);
+    plain_finish<M, NQ, NV, float, DFTable, false>(a, ev, c, v, 0.0, u0s, acc, as);
   } else {
-    plain_finish<M, NQ, NV, double, EvalTable>(a, ev, c, v, u0, u0s, acc, as);
+    plain_finish<M, NQ, NV, double, EvalTable, false>(a, ev, c, v, u0, u0s, acc, as);
   }
 }
 
@@ -1461,7 +1481,7 @@ struct TmaTraits<false> {
 // the tile's stencil halo in a double-buffered shared-memory area, prefetched
 // with cp.async one tile ahead; stencil differences from the halo, matrices
 // from the ring.  kDF: FP64 path (double-float); !kDF: FP32-mixed path.
-template <int M, int NS, int NQ, bool kDF>
+template <int M, int NS, int NQ, bool kDF, bool kExt>
 __global__ void __launch_bounds__(kTile * (kConsumers + 1))
     recon_tma_kernel(const ReconArgs a, const HaloArgs h, const DFTable ev, int* err) {
   using TR = TmaTraits<kDF>;
@@ -1624,9 +1644,9 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
         for (int k = 0; k < kSmallK; ++k)
 #pragma unroll
           for (int l = 0; l < kSmallM; ++l) as[k][l] = df_norm(as[k][l]);
-        df_finish<M, NQ, NV>(a, ev, c, v, acc, as);
+        df_finish<M, NQ, NV, kExt>(a, ev, c, v, acc, as);
       } else {
-        plain_finish<M, NQ, NV, float, DFTable>(a, ev, c, v, 0.0, u0s, acc, as);
+        plain_finish<M, NQ, NV, float, DFTable, kExt>(a, ev, c, v, 0.0, u0s, acc, as);
       }
     }
   }
@@ -2838,11 +2858,11 @@ cudaError_t dispatch_order(int order, F&& f) {
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
-template <int M, int NS, int NQ, bool kDF>
+template <int M, int NS, int NQ, bool kDF, bool kExt>
 cudaError_t launch_recon_tma(const ReconArgs& a, const DeviceMesh& dm, int* err, cudaStream_t st) {
   using TR = TmaTraits<kDF>;
   using P = StagePlan<M, NS, (int)sizeof(typename TR::TE), TR::kLPS, TR::kSPS>;
-  auto kern = recon_tma_kernel<M, NS, NQ, kDF>;
+  auto kern = recon_tma_kernel<M, NS, NQ, kDF, kExt>;
   const int threads = kTile * (kConsumers + 1);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)P::kSmem);
@@ -2932,10 +2952,13 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
     auto go = [&](auto nqc, auto nvc) -> cudaError_t {
       constexpr int NQ = decltype(nqc)::value, NV = decltype(nvc)::value;
       // the TMA kernel covers Euler on the pair and mixed paths; variant 2
-      // elsewhere takes the halo kernel
+      // elsewhere takes the halo kernel. CWENO and the characteristic mode
+      // take the TMA or the direct kernels: the halo kernel is compiled for
+      // TENO in conservative variables only.
+      const bool ext = dm.scheme != 0 || dm.charvar != 0;
       const bool tma = NV == 4 && dm.variant == 2 && dm.err_flag && dm.halo.off &&
                        dm.precision != TENO_FP64_NATIVE;
-      if ((dm.variant == 0 || (dm.variant == 2 && !tma)) && dm.halo.off) {
+      if (!ext && (dm.variant == 0 || (dm.variant == 2 && !tma)) && dm.halo.off) {
         constexpr int TZh = 4 / NV;
         dim3 block(kTile, NV, TZh);
         dim3 grid((unsigned)((tiles + TZh - 1) / TZh));
@@ -2951,8 +2974,14 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
         if (tma) {
           if (dm.precision == TENO_FP64 && dm.scheme == 0 && dm.g32 && dm.wq && dm.psi_df)
             return launch_recon_tma_w<M, NS, NQ>(a, dm, dm.err_flag, st);
-          if (dm.precision == TENO_FP64) return launch_recon_tma<M, NS, NQ, true>(a, dm, dm.err_flag, st);
-          return launch_recon_tma<M, NS, NQ, false>(a, dm, dm.err_flag, st);
+          if (ext) {
+            if (dm.precision == TENO_FP64)
+              return launch_recon_tma<M, NS, NQ, true, true>(a, dm, dm.err_flag, st);
+            return launch_recon_tma<M, NS, NQ, false, true>(a, dm, dm.err_flag, st);
+          }
+          if (dm.precision == TENO_FP64)
+            return launch_recon_tma<M, NS, NQ, true, false>(a, dm, dm.err_flag, st);
+          return launch_recon_tma<M, NS, NQ, false, false>(a, dm, dm.err_flag, st);
         }
       }
       constexpr int TZ = 4 / NV;  // 128 threads per block
