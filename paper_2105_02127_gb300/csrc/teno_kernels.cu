@@ -163,7 +163,8 @@ __device__ __forceinline__ T vmax(const T& a, const T& b) { return val(a) >= val
 // Values are unevaluated sums hi + lo of two floats (|lo| <= ulp(hi)/2), about
 // 48 significant bits.  Products use the exact FMA residual, sums Knuth's
 // two-sum; the per-cell matrices are stored as (hi, lo) pairs.
-struct DF {
+// 8-byte aligned so that a pair moves through memory in one access
+struct __align__(8) DF {
   float h, l;
 };
 __device__ __forceinline__ DF two_sum(float a, float b) {
@@ -836,7 +837,8 @@ __device__ __forceinline__ bool chi_keep32_bound(const float* t, int k, int mask
 template <int M, int NQ, int NV, typename TA, typename TT, bool kExt = true>
 __device__ __forceinline__ void plain_finish(const ReconArgs& a, const TT& ev, int64_t c, int v,
                                              double u0, float2 u0s, const TA (&acc)[M],
-                                             const TA (&as)[kSmallK][kSmallM]) {
+                                             const TA (&as)[kSmallK][kSmallM],
+                                             TA* ostage = nullptr) {
   constexpr bool kMixed = std::is_same<TA, float>::value;
   if constexpr (kExt) {
     if (a.coef_out) {
@@ -946,8 +948,9 @@ __device__ __forceinline__ void plain_finish(const ReconArgs& a, const TT& ev, i
       for (int l = 0; l < kSmallM; ++l) cf[l] = fma(w, as[k][l], cf[l]);
     }
   }
-  // values at the 3*NQ edge Gauss points: U_0 + Psi' c'
-  TA* __restrict__ out = reinterpret_cast<TA*>(a.Uq) + c * (3 * NQ * NV) + v;
+  // values at the 3*NQ edge Gauss points: U_0 + Psi' c' (to Uq, or to the
+  // caller's shared-memory stage with the same point stride NV)
+  TA* __restrict__ out = ostage ? ostage : reinterpret_cast<TA*>(a.Uq) + c * (3 * NQ * NV) + v;
 #pragma unroll
   for (int p = 0; p < 3 * NQ; ++p) {
     TA s = TA(0);
@@ -1032,7 +1035,8 @@ __global__ void __launch_bounds__(128) recon_kernel(const ReconArgs a, const TT 
 template <int M, int NQ, int NV, bool kExt = true>
 __device__ __forceinline__ void df_finish(const ReconArgs& a, const DFTable& ev, int64_t c, int v,
                                           const DF (&acc)[M],
-                                          const DF (&as)[kSmallK][kSmallM]) {
+                                          const DF (&as)[kSmallK][kSmallM],
+                                          float2* ostage = nullptr) {
   if constexpr (kExt) {
     if (a.coef_out) {
       store_coefs<M, DF>(a, c, v, acc, as);
@@ -1144,13 +1148,15 @@ __device__ __forceinline__ void df_finish(const ReconArgs& a, const DFTable& ev,
   }
   // Gauss-point values as (hi, lo) pairs: split(U_0) + Psi' c'
   const float2 u0s = a.Us[(int64_t)v * a.n_pad + c];
-  DF* __restrict__ out = reinterpret_cast<DF*>(a.Uq) + c * (3 * NQ * NV) + v;
+  float2* __restrict__ out =
+      ostage ? ostage : reinterpret_cast<float2*>(a.Uq) + c * (3 * NQ * NV) + v;
 #pragma unroll
   for (int p = 0; p < 3 * NQ; ++p) {
     DF s = {0.f, 0.f};
 #pragma unroll
     for (int l = 0; l < M; ++l) df_mac(s, ev.psi[p * kMaxM + l], cf[l]);
-    out[p * NV] = DF{u0s.x, u0s.y} + df_norm(s);
+    const DF r = DF{u0s.x, u0s.y} + df_norm(s);
+    out[p * NV] = make_float2(r.h, r.l);
   }
 }
 
@@ -1421,6 +1427,33 @@ __device__ __forceinline__ void consumer_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(kConsumers * kTile) : "memory");
 }
 
+// Output stage of the TMA kernels.  Each variable warp writes its lanes'
+// Gauss-point values to shared memory laid out [cell][point][variable] with
+// an odd cell stride of kPer + 1 elements (conflict-free), and the consumer
+// threads then store the tile's contiguous block of Uq with coalesced writes
+// instead of one 32-sector store per point and variable.
+#ifndef TENO_STAGE_OUT
+#define TENO_STAGE_OUT 1
+#endif
+// the W-form kernel measured faster with its direct 8-byte pair stores (the
+// stage costs it a ring slot and a barrier per tile)
+#ifndef TENO_STAGE_OUT_W
+#define TENO_STAGE_OUT_W 0
+#endif
+template <int kPer, typename TO>
+__device__ __forceinline__ void store_out_stage(const TO* stg, TO* __restrict__ dst, int nvalid,
+                                                int tid) {
+#pragma unroll 3
+  for (int e = tid; e < nvalid * kPer; e += kConsumers * kTile) {
+    const int cl = e / kPer;
+    dst[e] = stg[cl * (kPer + 1) + (e - cl * kPer)];
+  }
+}
+template <int kPer, typename TO>
+constexpr size_t out_stage_bytes() {
+  return ((size_t)kTile * (kPer + 1) * sizeof(TO) + 15) / 16 * 16;
+}
+
 // Stage j of a tile's matrix block: kLPS large-stencil slots, or kSPS slots of
 // one directional stencil.
 template <int M, int NS, int kEsz, int kLPS, int kSPS>
@@ -1489,8 +1522,13 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
   using P = StagePlan<M, NS, (int)sizeof(TE), TR::kLPS, TR::kSPS>;
   constexpr int NV = 4;
   constexpr int SL = NS + kSmallSlots;
+  constexpr int kPer = 3 * NQ * NV;  // Gauss-point values per cell
+  // output stage on the FP32-mixed TENO path (the pair path would lose a
+  // block per SM to it)
+  constexpr bool kStage = TENO_STAGE_OUT && !kExt && !kDF;
   extern __shared__ __align__(128) unsigned char smem[];
   float2* halo = reinterpret_cast<float2*>(smem + (size_t)kRing * P::kMat);  // [2][NV][kHaloMax]
+  float* ostg = reinterpret_cast<float*>(smem + P::kSmem);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kRing * P::kMat + P::kHaloBytes);
   uint64_t* empty = full + kRing;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kRing);
@@ -1646,8 +1684,16 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
           for (int l = 0; l < kSmallM; ++l) as[k][l] = df_norm(as[k][l]);
         df_finish<M, NQ, NV, kExt>(a, ev, c, v, acc, as);
       } else {
-        plain_finish<M, NQ, NV, float, DFTable, kExt>(a, ev, c, v, 0.0, u0s, acc, as);
+        plain_finish<M, NQ, NV, float, DFTable, kExt>(a, ev, c, v, 0.0, u0s, acc, as,
+                                                      kStage ? ostg + lane * (kPer + 1) + v
+                                                             : nullptr);
       }
+    }
+    if constexpr (kStage) {
+      consumer_sync();  // the tile's values are staged
+      if (!dead)
+        store_out_stage<kPer>(ostg, reinterpret_cast<float*>(a.Uq) + tile * kTile * kPer,
+                              (int)min((int64_t)kTile, a.n_cell - tile * kTile), tid);
     }
   }
   cp_async_wait<0>();
@@ -1690,7 +1736,9 @@ struct WPlan {
   static constexpr int kEW = NS * NQ3;                            // pairs per lane per tile
   static constexpr int kSL = NS + kSmallSlots;
   static constexpr size_t kHaloBytes = (size_t)2 * 4 * kHaloMax * sizeof(float2);
-  static constexpr size_t kFixed = kHaloBytes + 2 * 4 * 8 + 16;
+  // output stage of the Gauss-point pairs of one tile (float2 elements)
+  static constexpr size_t kOut = TENO_STAGE_OUT_W ? out_stage_bytes<NQ3 * 4, float2>() : 0;
+  static constexpr size_t kFixed = kHaloBytes + 2 * 4 * 8 + 16 + kOut;
   // blocks of 160 threads per SM (228 KB of shared memory, 1 KB reserved per
   // block): four with a 3-deep ring where that fits, else three (4-deep
   // ring if it fits)
@@ -1699,7 +1747,8 @@ struct WPlan {
   static constexpr int kRingW =
       kFour ? 3 : (3 * ((size_t)4 * kMat + kFixed + 1024) <= (size_t)228 * 1024 ? 4 : 3);
   static constexpr int kBlocks = kFour ? 4 : 3;
-  static constexpr size_t kSmem = (size_t)kRingW * kMat + kHaloBytes + 2 * kRingW * 8 + 16;
+  static constexpr size_t kOutOff = (size_t)kRingW * kMat + kHaloBytes + 2 * kRingW * 8 + 16;
+  static constexpr size_t kSmem = kOutOff + kOut;
   static_assert(kSmallN % kSPS == 0, "directional stencil split");
   static_assert(kSlotG % 16 == 0 && kSlotW % 16 == 0 && kSlotS % 16 == 0 && kMat % 16 == 0,
                 "bulk-copy sizes");
@@ -1812,7 +1861,7 @@ __device__ __noinline__ uint8_t w_select_pairs(const float2* A, const uint16_t* 
 template <int M, int NS, int NQ3, int NV>
 __device__ __noinline__ void w_small_values(const float2* A, const uint16_t* nb, const float2* st,
                                             float2 u0s, uint8_t sel, const float2* psi,
-                                            DF* out) {
+                                            float2* out) {
   DF sum[kSmallM];
 #pragma unroll
   for (int l = 0; l < kSmallM; ++l) sum[l] = DF{0.f, 0.f};
@@ -1850,7 +1899,8 @@ __device__ __noinline__ void w_small_values(const float2* A, const uint16_t* nb,
     DF sp = {0.f, 0.f};
 #pragma unroll
     for (int l = 0; l < kSmallM; ++l) df_mac(sp, __ldg(psi + p * kMaxM + l), cf[l]);
-    out[p * NV] = u0 + df_norm(sp);
+    const DF r = u0 + df_norm(sp);
+    out[p * NV] = make_float2(r.h, r.l);
   }
 }
 
@@ -1864,8 +1914,10 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
   constexpr int NV = 4;
   constexpr int SL = NS + kSmallSlots;
   constexpr int E = M * NS + kSmallEntries;
+  constexpr int kPer = NQ3 * NV;  // Gauss-point pairs per cell
   extern __shared__ __align__(128) unsigned char smem[];
   float2* halo = reinterpret_cast<float2*>(smem + (size_t)kR * P::kMat);  // [2][NV][kHaloMax]
+  float2* ostg = reinterpret_cast<float2*>(smem + P::kOutOff);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kR * P::kMat + P::kHaloBytes);
   uint64_t* empty = full + kR;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kR);
@@ -2010,12 +2062,17 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
         if (near) sel = w_select_pairs<M, NS>(A, nb, st, u0s, present, a.ct, a.eps);
       }
       if (a.sel_out) a.sel_out[(int64_t)v * a.n_pad + c] = sel;
-      // Gauss-point values as (hi, lo) pairs
-      DF* __restrict__ out = reinterpret_cast<DF*>(a.Uq) + c * (NQ3 * NV) + v;
+      // Gauss-point values as (hi, lo) pairs, to the output stage or to Uq
+      float2* __restrict__ out = TENO_STAGE_OUT_W
+                                     ? ostg + lane * (kPer + 1) + v
+                                     : reinterpret_cast<float2*>(a.Uq) + c * kPer + v;
       if (sel & 8) {
         const DF u0 = {u0s.x, u0s.y};
 #pragma unroll
-        for (int p = 0; p < NQ3; ++p) out[p * NV] = u0 + df_norm(uq[p]);
+        for (int p = 0; p < NQ3; ++p) {
+          const DF r = u0 + df_norm(uq[p]);
+          out[p * NV] = make_float2(r.h, r.l);
+        }
       } else {
         w_small_values<M, NS, NQ3, NV>(A, nb, st, u0s, sel, psi, out);
       }
@@ -2070,6 +2127,12 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
       if (lane == 0 && !dead) mbar_arrive(&empty[b]);
     }
     if (!dead && c < a.n_cell) finish_cell(tile, c);
+    if constexpr (TENO_STAGE_OUT_W != 0) {
+      consumer_sync();  // the tile's values are staged
+      if (!dead)
+        store_out_stage<kPer>(ostg, reinterpret_cast<float2*>(a.Uq) + tile * kTile * kPer,
+                              (int)min((int64_t)kTile, a.n_cell - tile * kTile), tid);
+    }
   }
   cp_async_wait<0>();
 }
@@ -2258,6 +2321,43 @@ __device__ __forceinline__ T gauss_w(double w, float2 w2) {
 // Gauss points of a face unrolled in the flux kernel: the pair-arithmetic
 // solver is large enough that one copy of its code runs faster (fewer
 // instruction-fetch stalls) than three; the FP32 and FP64 ones unroll
+// Groups of NV = 4 values (the states at one Gauss point, the flux of one
+// face) as 16-byte accesses; the arrays are cudaMalloc'd and indexed in whole
+// groups, so every group starts on a 16-byte boundary.
+template <int NV, typename T>
+__device__ __forceinline__ void ld_group(const T* __restrict__ p, T (&x)[NV]) {
+  if constexpr (NV == 4 && std::is_same<T, float>::value) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    x[0] = q.x, x[1] = q.y, x[2] = q.z, x[3] = q.w;
+  } else if constexpr (NV == 4 && std::is_same<T, DF>::value) {
+    const float4 q0 = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 q1 = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    x[0] = DF{q0.x, q0.y}, x[1] = DF{q0.z, q0.w}, x[2] = DF{q1.x, q1.y}, x[3] = DF{q1.z, q1.w};
+  } else if constexpr (NV == 4 && std::is_same<T, double>::value) {
+    const double2 q0 = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 q1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    x[0] = q0.x, x[1] = q0.y, x[2] = q1.x, x[3] = q1.y;
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) x[v] = p[v];
+  }
+}
+template <int NV, typename T>
+__device__ __forceinline__ void st_group(T* __restrict__ p, const T (&x)[NV]) {
+  if constexpr (NV == 4 && std::is_same<T, float>::value) {
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+  } else if constexpr (NV == 4 && std::is_same<T, DF>::value) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(x[0].h, x[0].l, x[1].h, x[1].l);
+    reinterpret_cast<float4*>(p)[1] = make_float4(x[2].h, x[2].l, x[3].h, x[3].l);
+  } else if constexpr (NV == 4 && std::is_same<T, double>::value) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(x[0], x[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(x[2], x[3]);
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) p[v] = x[v];
+  }
+}
+
 #ifndef TENO_FLUX_UNROLL_PAIRS
 #define TENO_FLUX_UNROLL_PAIRS 1
 #endif
@@ -2280,13 +2380,9 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const FaceArgs a, const 
 #pragma unroll (std::is_same<T, DF>::value ? kFluxUnrollPairs : 4)
   for (int k = 0; k < NQ; ++k) {
     T UL[NV], UR[NV], F[NV];
-    const T* pl = Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) UL[v] = pl[v];
+    ld_group<NV>(Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV, UL);
     if (n >= 0) {
-      const T* pr = Uq + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) UR[v] = pr[v];
+      ld_group<NV>(Uq + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV, UR);
     } else if constexpr (NV == 4) {
       double x = a.f_geom[5 * f + 3] - ny * len * a.gt[k];
       ghost_state<T>(en, UL, nx, ny, x, a.time, a.gamma, UR);
@@ -2308,7 +2404,8 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const FaceArgs a, const 
     for (int v = 0; v < NV; ++v) acc[v] = madd(wk, F[v], acc[v]);
   }
 #pragma unroll
-  for (int v = 0; v < NV; ++v) K[f * NV + v] = acc[v] * tl;
+  for (int v = 0; v < NV; ++v) acc[v] = acc[v] * tl;
+  st_group<NV>(K + f * NV, acc);
 }
 
 // ------------------------------------------------------------------ gather
@@ -2344,13 +2441,15 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a, const T
     for (int e = 0; e < 3; ++e) {
       const int cf = a.c_faces[3 * c + e];
       const int64_t f = cf >> 1;
+      TK kf[NV];
+      ld_group<NV>(K + f * NV, kf);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         DF k;
         if constexpr (std::is_same<TK, DF>::value)
-          k = K[f * NV + v];
+          k = kf[v];
         else
-          k = DF{K[f * NV + v], 0.f};
+          k = DF{kf[v], 0.f};
         sum[v] = (cf & 1) ? sum[v] - k : sum[v] + k;
       }
     }
@@ -2364,8 +2463,10 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a, const T
       const int cf = a.c_faces[3 * c + e];
       const int64_t f = cf >> 1;
       const double s = (cf & 1) ? -1.0 : 1.0;
+      TK kf[NV];
+      ld_group<NV>(K + f * NV, kf);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] = fma(s, to_d(K[f * NV + v]), acc[v]);
+      for (int v = 0; v < NV; ++v) acc[v] = fma(s, to_d(kf[v]), acc[v]);
     }
   }
   const double ia = a.inv_area[c];
@@ -2520,14 +2621,8 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
   const RiemannK<D> rk = riemann_k_dual<ND, S>(rks);
   for (int k = 0; k < NQ; ++k) {
     TQ ul[NV], ur[NV];
-    const TQ* pl = Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) ul[v] = pl[v];
-    if (n >= 0) {
-      const TQ* pr = Uq + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) ur[v] = pr[v];
-    }
+    ld_group<NV>(Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV, ul);
+    if (n >= 0) ld_group<NV>(Uq + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV, ur);
     const double wk = a.gw[k] * len;
     const double x = a.f_geom[5 * f + 3] - ny * len * a.gt[k];
     S Kw[NV];  // w_k |A| Kbar in the flux scalar type
@@ -2864,20 +2959,22 @@ cudaError_t launch_recon_tma(const ReconArgs& a, const DeviceMesh& dm, int* err,
   using P = StagePlan<M, NS, (int)sizeof(typename TR::TE), TR::kLPS, TR::kSPS>;
   auto kern = recon_tma_kernel<M, NS, NQ, kDF, kExt>;
   const int threads = kTile * (kConsumers + 1);
+  constexpr bool kStage = TENO_STAGE_OUT && !kExt && !kDF;
+  const size_t smem = P::kSmem + (kStage ? out_stage_bytes<3 * NQ * 4, float>() : 0);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)P::kSmem);
+                                       (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, P::kSmem)) !=
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) !=
       cudaSuccess)
     return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)per_sm * sms);
-  kern<<<(unsigned)grid, threads, P::kSmem, st>>>(a, dm.halo, dm.eval_df, err);
+  kern<<<(unsigned)grid, threads, smem, st>>>(a, dm.halo, dm.eval_df, err);
   return cudaGetLastError();
 }
 
