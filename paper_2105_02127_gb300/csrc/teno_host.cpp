@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <memory>
 #include <string>
@@ -80,6 +81,12 @@ struct teno_ctx {
   bool adj_ok = false;
   std::vector<int64_t> rev_off_h;
   std::vector<int32_t> rev_idx_h;
+  // tiled adjoint (FP64 path, Euler): reverse map over the per-tile halo
+  // entries and the per-entry partial sums written by the tiled VJP kernel
+  DevBuf b_hrev_off, b_hrev_idx, b_hpart;
+  std::vector<int64_t> hrev_off_h;
+  std::vector<int32_t> hrev_idx_h;
+  bool adj_tiled = false;
   double time = 0.0;
   // kernel timing (teno_profile): event pairs around launches, per kind
   bool prof_on = false;
@@ -786,6 +793,129 @@ int run_precompute(teno_ctx* ctx) {
     const int64_t tile = c / kTile, lane = c % kTile;
     for (int s = 0; s < SL; ++s) nbr[((size_t)tile * SL + s) * kTile + lane] = 0;
   }
+  // Slot order of the large stencils (for the adjoint's halo accumulation):
+  // within each tile the members of the cells' large stencils are assigned
+  // to the ns slots by a proper edge colouring of the bipartite graph (lane,
+  // member cell) with ns colours, so that no two lanes of a tile hold the
+  // same cell in the same slot.  Such a colouring exists when no cell lies in
+  // more than ns of the tile's large stencils (Konig's edge-colouring
+  // theorem); it is built edge by edge, swapping the two colours along an
+  // alternating path where needed.  Tiles with a busier cell keep the
+  // stencil-search order.  Matrix columns move with their slots: the
+  // reconstruction is the same sum in another order.
+  {
+    const size_t E32s = wform ? (size_t)E32 : 0, EWs = wform ? (size_t)EW : 0;
+#pragma omp parallel
+    {
+      std::vector<int32_t> cells, eR, deg, colL, colR, perm;
+      std::vector<int32_t> pl, pr, pc;
+      std::vector<unsigned char> tmp;
+#pragma omp for schedule(dynamic, 64)
+      for (int64_t t = 0; t < ntile; ++t) {
+        const int nval = (int)std::min<int64_t>(kTile, nc - t * kTile);
+        auto member = [&](int ln, int s) { return nbr[((size_t)t * SL + s) * kTile + ln]; };
+        cells.clear();
+        for (int ln = 0; ln < nval; ++ln)
+          for (int s = 0; s < ns; ++s) cells.push_back(member(ln, s));
+        std::sort(cells.begin(), cells.end());
+        cells.erase(std::unique(cells.begin(), cells.end()), cells.end());
+        const int nr = (int)cells.size();
+        eR.assign((size_t)nval * ns, 0);
+        deg.assign(nr, 0);
+        int dmax = 0;
+        for (int ln = 0; ln < nval; ++ln)
+          for (int s = 0; s < ns; ++s) {
+            const int r = (int)(std::lower_bound(cells.begin(), cells.end(), member(ln, s)) -
+                                cells.begin());
+            eR[(size_t)ln * ns + s] = r;
+            dmax = std::max(dmax, ++deg[r]);
+          }
+        if (dmax > ns) continue;
+        colL.assign((size_t)nval * ns, -1);  // [lane][colour] -> member index
+        colR.assign((size_t)nr * ns, -1);    // [member][colour] -> lane
+        for (int ln = 0; ln < nval; ++ln)
+          for (int s = 0; s < ns; ++s) {
+            const int w = eR[(size_t)ln * ns + s];
+            int a = 0, b = 0;
+            while (colL[(size_t)ln * ns + a] >= 0) ++a;
+            while (colR[(size_t)w * ns + b] >= 0) ++b;
+            int c = a;
+            if (colR[(size_t)w * ns + a] >= 0) {
+              if (colL[(size_t)ln * ns + b] < 0) {
+                c = b;
+              } else {
+                // swap a and b along the alternating path from w (it cannot
+                // reach lane ln in a bipartite graph)
+                pl.clear(), pr.clear(), pc.clear();
+                int r = w, col = a;
+                while (true) {
+                  const int l = colR[(size_t)r * ns + col];
+                  if (l < 0) break;
+                  pl.push_back(l), pr.push_back(r), pc.push_back(col);
+                  const int col2 = col == a ? b : a;
+                  const int r2 = colL[(size_t)l * ns + col2];
+                  if (r2 < 0) break;
+                  pl.push_back(l), pr.push_back(r2), pc.push_back(col2);
+                  r = r2;
+                }
+                for (size_t i = 0; i < pl.size(); ++i) {
+                  colL[(size_t)pl[i] * ns + pc[i]] = -1;
+                  colR[(size_t)pr[i] * ns + pc[i]] = -1;
+                }
+                for (size_t i = 0; i < pl.size(); ++i) {
+                  const int o = pc[i] == a ? b : a;
+                  colL[(size_t)pl[i] * ns + o] = pr[i];
+                  colR[(size_t)pr[i] * ns + o] = pl[i];
+                }
+              }
+            }
+            colL[(size_t)ln * ns + c] = w;
+            colR[(size_t)w * ns + c] = ln;
+          }
+        // the colouring is proper: every lane has one member per colour and
+        // the two tables agree (else the tile keeps its order)
+        bool proper = true;
+        for (int ln = 0; ln < nval && proper; ++ln)
+          for (int c = 0; c < ns && proper; ++c) {
+            const int w = colL[(size_t)ln * ns + c];
+            proper = w >= 0 && colR[(size_t)w * ns + c] == ln;
+          }
+        if (!proper) continue;
+        // move every lane's slot s to its colour
+        perm.assign(ns, 0);
+        for (int ln = 0; ln < nval; ++ln) {
+          for (int s = 0; s < ns; ++s) {
+            const int w = eR[(size_t)ln * ns + s];
+            int c = 0;
+            while (colL[(size_t)ln * ns + c] != w) ++c;
+            perm[s] = c;
+          }
+          // entries s * per_slot + l of lane ln in a [tile][entry][lane] array
+          auto permute = [&](auto* base, size_t stride_e, size_t per_slot) {
+            using T = std::remove_pointer_t<decltype(base)>;
+            T* tb = reinterpret_cast<T*>(tmp.data());
+            T* row = base + (size_t)t * stride_e * kTile + ln;
+            for (int s = 0; s < ns; ++s)
+              for (size_t l = 0; l < per_slot; ++l)
+                tb[(size_t)perm[s] * per_slot + l] = row[((size_t)s * per_slot + l) * kTile];
+            for (size_t e = 0; e < (size_t)ns * per_slot; ++e) row[e * kTile] = tb[e];
+          };
+          tmp.resize((size_t)ns * (size_t)std::max({m * 8, (m + 1) * 4, nq3 * 8, 4}));
+          permute(nbr.data(), SL, 1);
+          if (store == TENO_FP64_NATIVE)
+            permute(reinterpret_cast<double*>(ahat.data()), E, m);
+          else if (store == TENO_FP64)
+            permute(reinterpret_cast<float2*>(ahat.data()), E, m);
+          else
+            permute(reinterpret_cast<float*>(ahat.data()), E, m);
+          if (wform) {
+            permute(g32.data(), E32s, m + 1);
+            permute(wq.data(), EWs, nq3);
+          }
+        }
+      }
+    }
+  }
   // reverse stencil adjacency (adjoint gather): for every cell the d_bar
   // entries (tile * SL + slot) * 32 + lane of the slots that hold it (int32:
   // built for meshes with npad * SL < 2^31; the adjoint refuses larger ones)
@@ -828,12 +958,34 @@ int run_precompute(teno_ctx* ctx) {
         halo_ok = false;
         break;
       }
-      for (size_t i = 0; i < (size_t)SL * kTile; ++i)
-        hloc[(size_t)t * SL * kTile + i] =
-            (uint16_t)(std::lower_bound(ids.begin(), ids.end(), tn[i]) - ids.begin());
+      // halo position (bits 0-7) and, for the adjoint, the lane's rank among
+      // the tile's valid lanes with the same position in the slot (bits 8-12)
+      const int nval = (int)std::min<int64_t>(kTile, nc - t * kTile);
+      for (int s = 0; s < SL; ++s)
+        for (int ln = 0; ln < kTile; ++ln) {
+          const size_t i = (size_t)s * kTile + ln;
+          const int pos = (int)(std::lower_bound(ids.begin(), ids.end(), tn[i]) - ids.begin());
+          int rank = 0;
+          if (ln < nval)
+            for (int j = 0; j < ln; ++j) rank += tn[(size_t)s * kTile + j] == tn[i];
+          hloc[(size_t)t * SL * kTile + i] = (uint16_t)(pos | (rank << 8));
+        }
       hids.insert(hids.end(), ids.begin(), ids.end());
       hoff[t + 1] = (int32_t)hids.size();
     }
+  }
+  // reverse map of the halo entries (tiled adjoint): for every cell the
+  // indices i with hids[i] == cell, in increasing i
+  ctx->hrev_off_h.clear();
+  ctx->hrev_idx_h.clear();
+  if (halo_ok) {
+    std::vector<int64_t> cnt(nc + 1, 0);
+    for (int32_t j : hids) cnt[(size_t)j + 1]++;
+    for (int64_t c = 0; c < nc; ++c) cnt[c + 1] += cnt[c];
+    ctx->hrev_off_h = cnt;
+    ctx->hrev_idx_h.assign(hids.size(), 0);
+    std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+    for (size_t i = 0; i < hids.size(); ++i) ctx->hrev_idx_h[pos[hids[i]]++] = (int32_t)i;
   }
   int e = upload(ctx, ctx->b_ahat, ahat.data(), ahat.size());
   if (!e) e = upload(ctx, ctx->b_nbr, nbr.data(), nbr.size() * sizeof(int32_t));
@@ -1077,13 +1229,34 @@ int to_user(teno_ctx* ctx, const double* src, double* dst, int on_device) {
 
 int ensure_adjoint(teno_ctx* ctx) {
   if (ctx->adj_ok) return TENO_OK;
-  if (ctx->rev_off_h.empty())
-    return fail(ctx, TENO_EINVAL,
-                "adjoint: mesh too large for 32-bit stencil-entry indices (cells x slots >= 2^31)");
   const int64_t npad = ctx->npad, nc = ctx->nc;
   const int nv = ctx->prm.n_var;
   const size_t ntile = npad / kTile;
-  int rc = dev_alloc(ctx, ctx->b_dbar, sizeof(double) * ntile * ctx->SL * nv * kTile);
+  // tiled VJP with the W-form reconstruction (variant 2, FP64 path, Euler,
+  // every tile with its halo); otherwise the per-slot d_bar and the reverse
+  // stencil map
+  ctx->adj_tiled = ctx->prm.precision == TENO_FP64 && nv == 4 && ctx->prm.recon_variant == 2 &&
+                   ctx->dm.halo.off && ctx->dm.wq && !ctx->hrev_off_h.empty() &&
+                   ctx->dm.err_flag;
+  if (!ctx->adj_tiled && ctx->rev_off_h.empty())
+    return fail(ctx, TENO_EINVAL,
+                "adjoint: mesh too large for 32-bit stencil-entry indices (cells x slots >= 2^31)");
+  int rc = TENO_OK;
+  if (ctx->adj_tiled) {
+    rc = dev_alloc(ctx, ctx->b_hpart, sizeof(double) * std::max<size_t>(1, ctx->hrev_idx_h.size()) * nv);
+    if (!rc)
+      rc = upload(ctx, ctx->b_hrev_off, ctx->hrev_off_h.data(), sizeof(int64_t) * (nc + 1));
+    if (!rc)
+      rc = upload(ctx, ctx->b_hrev_idx, ctx->hrev_idx_h.data(),
+                  sizeof(int32_t) * std::max<size_t>(1, ctx->hrev_idx_h.size()));
+  } else {
+    rc = dev_alloc(ctx, ctx->b_dbar, sizeof(double) * ntile * ctx->SL * nv * kTile);
+    if (!rc) rc = upload(ctx, ctx->b_rev_off, ctx->rev_off_h.data(), sizeof(int64_t) * (nc + 1));
+    if (!rc)
+      rc = upload(ctx, ctx->b_rev_idx, ctx->rev_idx_h.data(),
+                  sizeof(int32_t) * std::max<size_t>(1, ctx->rev_idx_h.size()));
+    if (!rc) CK(cudaMemsetAsync(ctx->b_dbar.p, 0, ctx->b_dbar.bytes, ctx->stream), "memset");
+  }
   if (!rc) rc = dev_alloc(ctx, ctx->b_uself, sizeof(double) * nv * npad);
   if (!rc) rc = dev_alloc(ctx, ctx->b_Uqbar, sizeof(double) * npad * 3 * ctx->nq * nv);
   if (!rc) rc = dev_alloc(ctx, ctx->b_l1, sizeof(double) * nv * npad);
@@ -1095,12 +1268,7 @@ int ensure_adjoint(teno_ctx* ctx) {
     rc = dev_alloc(ctx, ctx->b_Uq_st[k], ctx->b_Uq.bytes);
     if (!rc) rc = dev_alloc(ctx, ctx->b_sel_st[k], (size_t)nv * npad);
   }
-  if (!rc) rc = upload(ctx, ctx->b_rev_off, ctx->rev_off_h.data(), sizeof(int64_t) * (nc + 1));
-  if (!rc)
-    rc = upload(ctx, ctx->b_rev_idx, ctx->rev_idx_h.data(),
-                sizeof(int32_t) * std::max<size_t>(1, ctx->rev_idx_h.size()));
   if (rc) return rc;
-  CK(cudaMemsetAsync(ctx->b_dbar.p, 0, ctx->b_dbar.bytes, ctx->stream), "memset");
   ctx->adj_ok = true;
   return TENO_OK;
 }
@@ -1134,15 +1302,26 @@ int vjp_internal(teno_ctx* ctx, const double* U, const double* w, double* v, dou
      "flux vjp launch");
   prof_end(ctx, pe);
   pe = prof_begin(ctx, K_RECON_VJP);
-  CK(launch_recon_vjp(ctx->dm, sel, (const double*)ctx->b_Uqbar.p, (double*)ctx->b_dbar.p,
-                      (double*)ctx->b_uself.p, ctx->stream),
-     "recon vjp launch");
+  if (ctx->adj_tiled)
+    CK(launch_recon_vjp_tma(ctx->dm, sel, (const double*)ctx->b_Uqbar.p, (double*)ctx->b_hpart.p,
+                            (double*)ctx->b_uself.p, ctx->stream),
+       "recon vjp launch");
+  else
+    CK(launch_recon_vjp(ctx->dm, sel, (const double*)ctx->b_Uqbar.p, (double*)ctx->b_dbar.p,
+                        (double*)ctx->b_uself.p, ctx->stream),
+       "recon vjp launch");
   prof_end(ctx, pe);
   pe = prof_begin(ctx, K_SCATTER);
-  CK(launch_scatter_gather(ctx->dm, (const int64_t*)ctx->b_rev_off.p,
-                           (const int32_t*)ctx->b_rev_idx.p, (const double*)ctx->b_dbar.p,
-                           (const double*)ctx->b_uself.p, v, ctx->stream),
-     "scatter launch");
+  if (ctx->adj_tiled)
+    CK(launch_scatter_gather(ctx->dm, (const int64_t*)ctx->b_hrev_off.p,
+                             (const int32_t*)ctx->b_hrev_idx.p, (const double*)ctx->b_hpart.p,
+                             (const double*)ctx->b_uself.p, v, ctx->stream),
+       "scatter launch");
+  else
+    CK(launch_scatter_gather(ctx->dm, (const int64_t*)ctx->b_rev_off.p,
+                             (const int32_t*)ctx->b_rev_idx.p, (const double*)ctx->b_dbar.p,
+                             (const double*)ctx->b_uself.p, v, ctx->stream),
+       "scatter launch");
   prof_end(ctx, pe);
   return TENO_OK;
 }
@@ -1245,6 +1424,7 @@ int teno_destroy(teno_ctx* ctx) {
                     &ctx->b_Uq, &ctx->b_K, &ctx->b_sel, &ctx->b_sel_ovr, &ctx->b_maxlam,
                     &ctx->b_Usplit,
                     &ctx->b_flag, &ctx->b_rev_off, &ctx->b_rev_idx, &ctx->b_dbar, &ctx->b_uself,
+                    &ctx->b_hrev_off, &ctx->b_hrev_idx, &ctx->b_hpart,
                     &ctx->b_Uqbar, &ctx->b_l1, &ctx->b_l2, &ctx->b_lamn, &ctx->b_vtmp,
                     &ctx->b_selA, &ctx->b_Uq_st[0], &ctx->b_Uq_st[1], &ctx->b_sel_st[0],
                     &ctx->b_sel_st[1]};

@@ -39,6 +39,11 @@ struct DFTable {
 // Per-tile stencil halo: the distinct cells of a tile's stencils (internal
 // ids, at most kHaloMax per tile) and the stencil slots as halo-local indices.
 constexpr int kHaloMax = 256;
+// nbr_loc entries: halo position in bits 0-7, and in bits 8-12 the lane's
+// rank among the tile's lanes that hold the same cell in that slot (the
+// order of the adjoint's halo accumulation)
+constexpr int kHaloPosMask = 0xFF;
+static_assert(kHaloMax <= kHaloPosMask + 1, "halo positions must fit in 8 bits");
 struct HaloArgs {
   const int32_t* off = nullptr;       // [n_tiles + 1]
   const int32_t* ids = nullptr;       // [off[n_tiles]]
@@ -115,6 +120,12 @@ cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const dou
                                  double* Uq_bar, double time, cudaStream_t st);
 cudaError_t launch_recon_vjp(const DeviceMesh& dm, const uint8_t* sel, const double* Uq_bar,
                              double* d_bar, double* u_self, cudaStream_t st);
+// Tiled reconstruction VJP (FP64 path, Euler, per-tile halos present):
+// part[halo entry][var] = pair sums of the tile's d_bar at its halo cells,
+// u_self as in launch_recon_vjp; the reverse gather over halo entries
+// (launch_scatter_gather with the halo reverse map) completes the VJP.
+cudaError_t launch_recon_vjp_tma(const DeviceMesh& dm, const uint8_t* sel, const double* Uq_bar,
+                                 double* part, double* u_self, cudaStream_t st);
 cudaError_t launch_scatter_gather(const DeviceMesh& dm, const int64_t* rev_off,
                                   const int32_t* rev_idx, const double* d_bar,
                                   const double* u_self, double* v, cudaStream_t st);

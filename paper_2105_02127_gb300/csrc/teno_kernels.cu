@@ -1283,7 +1283,7 @@ __global__ void __launch_bounds__(128) recon_halo_kernel(const ReconArgs a, cons
   const TE* __restrict__ A = reinterpret_cast<const TE*>(a.ahat) + tile * (int64_t)E * kTile + lane;
   const uint16_t* __restrict__ nb = h.nbr_loc + tile * (int64_t)SL * kTile + lane;
   auto dif = [&](int s) -> Acc {
-    const TS q = st[__ldg(nb + s * kTile)];
+    const TS q = st[__ldg(nb + s * kTile) & kHaloPosMask];
     if constexpr (kMode == 0) {
       DF t = two_sum(q.x, -u0s.x);
       t.l += q.y - u0s.y;
@@ -1413,6 +1413,11 @@ constexpr int kConsumers = 4;  // one warp per conservative variable (Euler)
 // cp.async (8-byte asynchronous global->shared copies) for the halo prefetch
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+// 16-byte asynchronous copy (both addresses 16-byte aligned), L2 only
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
                : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
@@ -1654,7 +1659,7 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
 #pragma unroll
         for (int s = 0; s < TR::kLPS; ++s) {
           if (s < nslot) {
-            const Acc d = dif(nl[s * kTile]);
+            const Acc d = dif(nl[s * kTile] & kHaloPosMask);
 #pragma unroll
             for (int l = 0; l < M; ++l) mac(acc[l], mat[(s * M + l) * kTile], d);
           }
@@ -1665,7 +1670,7 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
           if (kk != k) continue;
 #pragma unroll
           for (int s = 0; s < TR::kSPS; ++s) {
-            const Acc d = dif(nl[s * kTile]);
+            const Acc d = dif(nl[s * kTile] & kHaloPosMask);
 #pragma unroll
             for (int l = 0; l < kSmallM; ++l) mac(as[kk][l], mat[(s * kSmallM + l) * kTile], d);
           }
@@ -1817,7 +1822,7 @@ __device__ __noinline__ uint8_t w_select_pairs(const float2* A, const uint16_t* 
 #pragma unroll
   for (int l = 0; l < M; ++l) al[l] = DF{0.f, 0.f};
   for (int s = 0; s < NS; ++s) {
-    const DF d = halo_dif(st, nb[s * kTile], u0s);
+    const DF d = halo_dif(st, nb[s * kTile] & kHaloPosMask, u0s);
 #pragma unroll
     for (int l = 0; l < M; ++l) df_mac(al[l], __ldg(A + (int64_t)(s * M + l) * kTile), d);
   }
@@ -1838,7 +1843,7 @@ __device__ __noinline__ uint8_t w_select_pairs(const float2* A, const uint16_t* 
     for (int l = 0; l < kSmallM; ++l) as[l] = DF{0.f, 0.f};
     if ((present >> k) & 1) {
       for (int s = 0; s < kSmallN; ++s) {
-        const DF d = halo_dif(st, nb[(NS + k * kSmallN + s) * kTile], u0s);
+        const DF d = halo_dif(st, nb[(NS + k * kSmallN + s) * kTile] & kHaloPosMask, u0s);
         const float2* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
 #pragma unroll
         for (int l = 0; l < kSmallM; ++l) df_mac(as[l], __ldg(As + l * kTile), d);
@@ -1871,7 +1876,7 @@ __device__ __noinline__ void w_small_values(const float2* A, const uint16_t* nb,
 #pragma unroll
     for (int l = 0; l < kSmallM; ++l) as[l] = DF{0.f, 0.f};
     for (int s = 0; s < kSmallN; ++s) {
-      const DF d = halo_dif(st, nb[(NS + k * kSmallN + s) * kTile], u0s);
+      const DF d = halo_dif(st, nb[(NS + k * kSmallN + s) * kTile] & kHaloPosMask, u0s);
       const float2* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
 #pragma unroll
       for (int l = 0; l < kSmallM; ++l) df_mac(as[l], __ldg(As + l * kTile), d);
@@ -2099,7 +2104,7 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
           if (s < nslot) {
-            const DF d = dif(nl[s * kTile]);
+            const DF d = dif(nl[s * kTile] & kHaloPosMask);
 #pragma unroll
             for (int l = 0; l < M; ++l) a32[l] = fmaf(gm[(s * P::kG + l) * kTile], d.h, a32[l]);
             eL = fmaf(gm[(s * P::kG + M) * kTile], fabsf(d.h), eL);
@@ -2114,7 +2119,7 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
           if (kk != k) continue;
 #pragma unroll
           for (int s = 0; s < 4; ++s) {
-            const float2 q = st[nl[s * kTile]];
+            const float2 q = st[nl[s * kTile] & kHaloPosMask];
             const float dh = (q.x - u0s.x) + (q.y - u0s.y);
 #pragma unroll
             for (int l = 0; l < kSmallM; ++l)
@@ -2854,6 +2859,309 @@ __global__ void __launch_bounds__(128) recon_vjp_df_kernel(const float2* __restr
   u_self[(int64_t)v * n_pad + c] = to_d(u0b - tot);
 }
 
+// Tiled reconstruction VJP (FP64 path, Euler, W form).  With the selection
+// frozen, Uq_p = U_0 + sum_s W_ps d_s for the large polynomial (W = Psi' G,
+// the per-cell pairs the forward W-form kernel uses), so d_bar_s =
+// sum_p W_ps Uq_bar_p: NQ3 pair products per slot and no coefficient
+// adjoint.  Directional stencils (cells whose large stencil is cut) take
+// d_bar_s = (G_k^T Psi_k^T Uq_bar)_s / n_kept from their (hi, lo) matrices;
+// their stages are streamed only for tiles where some (cell, variable) keeps
+// a directional stencil, a predicate the producer and the consumers evaluate
+// from the same selection bytes.  Each lane adds its d_bar_s to the tile's
+// halo accumulator in shared memory at the slot's halo position (lanes with
+// equal positions in lane order, by ranks the host stores next to the
+// positions; slots in stencil order: deterministic sums).  The host assigns
+// the large-stencil members to slots so that the lanes of a tile do not
+// share a cell within a slot, and these slots take one round.  At the end of the tile the
+// accumulator is written as one pair per (halo entry, variable), so the
+// reverse gather reads the few halo entries that hold a cell instead of
+// every stencil slot that holds it.  The tile's Uq_bar block is prefetched
+// with cp.async one tile ahead.
+constexpr int kRingV = 4;
+constexpr int kUbStride = 38;  // doubles per cell in the Uq_bar stage (16-byte rows)
+constexpr int kHaccStride = kHaloMax + 4;  // pairs per variable row (conflict-free transpose)
+
+template <int M, int NS, int NQ3>
+struct VjpPlan {
+  static constexpr int kLPS = 4, kSPS = 4;
+  static constexpr int kSlotW = NQ3 * kTile * 8;      // W pairs of one large slot
+  static constexpr int kSlotS = kSmallM * kTile * 8;  // matrix pairs of one directional slot
+  static constexpr int kSlotN = kTile * 2;            // halo positions (uint16) of one slot
+  static constexpr int kNL = (NS + kLPS - 1) / kLPS;
+  static constexpr int kPerSmall = kSmallN / kSPS;
+  static constexpr int kStages = kNL + kSmallK * kPerSmall;
+  static constexpr int kNOff = kLPS * kSlotW > kSPS * kSlotS ? kLPS * kSlotW : kSPS * kSlotS;
+  static constexpr int kMat = kNOff + 4 * kSlotN;
+  static constexpr int kSL = NS + kSmallSlots;
+  static constexpr int64_t kTileW = (int64_t)NS * NQ3 * kTile * 8;
+  static constexpr int64_t kTileA = (int64_t)(M * NS + kSmallEntries) * kTile * 8;
+  static constexpr size_t kUbOff = (size_t)kRingV * kMat;
+  static constexpr size_t kUbBytes = (size_t)2 * kTile * kUbStride * 8;
+  static constexpr size_t kHaccOff = kUbOff + kUbBytes;
+  static constexpr size_t kHaccBytes = (size_t)4 * kHaccStride * 8;
+  static constexpr size_t kBarOff = kHaccOff + kHaccBytes;
+  static constexpr size_t kSmem = kBarOff + 2 * kRingV * 8 + 16 + 16;
+  static_assert(NQ3 * 4 <= kUbStride, "Uq_bar row");
+  static_assert(kSmallN % kSPS == 0, "directional stencil split");
+  static_assert(kMat % 16 == 0 && kUbOff % 16 == 0 && kHaccOff % 16 == 0 && kBarOff % 8 == 0,
+                "alignment");
+  // stage j: slots [slot0, slot0 + nslot) of stencil k (-1: large, from W;
+  // else from the directional matrices), source byte offset in the tile's
+  // W or matrix block
+  __device__ static void stage(int j, int& slot0, int& nslot, int& k, int64_t& off, int& bytes) {
+    if (j < kNL) {
+      slot0 = j * kLPS;
+      nslot = (NS - slot0) < kLPS ? (NS - slot0) : kLPS;
+      k = -1;
+      off = (int64_t)slot0 * kSlotW;
+      bytes = nslot * kSlotW;
+    } else {
+      const int i = j - kNL;
+      k = i / kPerSmall;
+      const int s0 = (i % kPerSmall) * kSPS;
+      slot0 = NS + k * kSmallN + s0;
+      nslot = kSPS;
+      off = (int64_t)(M * NS + (k * kSmallN + s0) * kSmallM) * kTile * 8;
+      bytes = kSPS * kSlotS;
+    }
+  }
+};
+
+// some valid (cell, variable) of the tile keeps a directional stencil
+__device__ __forceinline__ bool vjp_needs_small(uint8_t sel) {
+  return !(sel & 8) && (sel & 7);
+}
+
+template <int M, int NS, int NQ>
+__global__ void __launch_bounds__(kTile * (kConsumers + 1), 3)
+    recon_vjp_tma_kernel(const float2* __restrict__ ahat, const float2* __restrict__ wq,
+                         const HaloArgs h, const uint8_t* __restrict__ sel_in,
+                         const double* __restrict__ Uq_bar, float2* __restrict__ part,
+                         double* __restrict__ u_self, int64_t n_cell, int64_t n_pad,
+                         const DFTable ev, int* err) {
+  constexpr int NV = 4, NQ3 = 3 * NQ, kPer = NQ3 * NV;
+  using VP = VjpPlan<M, NS, NQ3>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  double* ubs = reinterpret_cast<double*>(smem + VP::kUbOff);     // [2][32][kUbStride]
+  float2* hacc = reinterpret_cast<float2*>(smem + VP::kHaccOff);  // [NV][kHaccStride]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + VP::kBarOff);
+  uint64_t* empty = full + kRingV;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kRingV);
+  int* need = const_cast<int*>(abort_flag) + 4;  // [NV] per-variable small-stencil flags
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n_tiles = (n_cell + kTile - 1) / kTile;
+  if (threadIdx.x == 0) {
+    *abort_flag = 0;
+    for (int i = 0; i < kRingV; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kConsumers);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (warp == kConsumers) {
+    // ---- producer lane: W blocks (and directional matrices where needed)
+    if (lane == 0) {
+      int64_t g = 0;
+      for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const unsigned char* sw = reinterpret_cast<const unsigned char*>(wq) + tile * VP::kTileW;
+        const unsigned char* sa = reinterpret_cast<const unsigned char*>(ahat) + tile * VP::kTileA;
+        const unsigned char* sn =
+            reinterpret_cast<const unsigned char*>(h.nbr_loc) + tile * (int64_t)VP::kSL * VP::kSlotN;
+        // the tile's selection bytes: 2 x 16 per variable (rows of n_pad, a
+        // multiple of 32), pad lanes masked
+        const int nval = (int)min((int64_t)kTile, n_cell - tile * kTile);
+        uint4 sw4[2 * NV];
+#pragma unroll
+        for (int w = 0; w < NV; ++w)
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+            sw4[2 * w + q] =
+                __ldg(reinterpret_cast<const uint4*>(sel_in + (int64_t)w * n_pad + tile * kTile) + q);
+        bool small = false;
+#pragma unroll
+        for (int w = 0; w < NV; ++w)
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const uint32_t words[4] = {sw4[2 * w + q].x, sw4[2 * w + q].y, sw4[2 * w + q].z,
+                                       sw4[2 * w + q].w};
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const uint8_t b = (uint8_t)(words[i >> 2] >> (8 * (i & 3)));
+              small |= (16 * q + i < nval) && vjp_needs_small(b);
+            }
+          }
+        const int n_stages = small ? VP::kStages : VP::kNL;
+        for (int j = 0; j < n_stages; ++j, ++g) {
+          const int b = (int)(g % kRingV);
+          if (g >= kRingV) {
+            const int w =
+                mbar_wait_or_abort(&empty[b], (uint32_t)((g / kRingV) - 1) & 1, abort_flag);
+            if (w != 1) {
+              if (w == 0) {
+                atomicOr(err, 2);
+                *abort_flag = 1;
+              }
+              for (int64_t i = g - kRingV; i < g; ++i)
+                mbar_wait(&full[i % kRingV], (uint32_t)(i / kRingV) & 1);
+              return;
+            }
+          }
+          int slot0, nslot, k, bytes;
+          int64_t off;
+          VP::stage(j, slot0, nslot, k, off, bytes);
+          const uint32_t bn = (uint32_t)(nslot * VP::kSlotN);
+          unsigned char* dst = smem + (size_t)b * VP::kMat;
+          mbar_expect_tx(&full[b], (uint32_t)bytes + bn);
+          bulk_g2s(dst, (k < 0 ? sw : sa) + off, (uint32_t)bytes, &full[b]);
+          bulk_g2s(dst + VP::kNOff, sn + slot0 * VP::kSlotN, bn, &full[b]);
+        }
+      }
+    }
+    return;
+  }
+  // ---- consumers (warp v: variable v)
+  const int v = warp, tid = threadIdx.x;
+  // Uq_bar block of a tile (contiguous [cell][point][variable]) into stage hb
+  auto prefetch = [&](int64_t tile, int hb) {
+    const int nval = (int)min((int64_t)kTile, n_cell - tile * kTile);
+    const double* src = Uq_bar + tile * kTile * kPer;
+    double* dst = ubs + (size_t)hb * kTile * kUbStride;
+    for (int e = tid; e < nval * (kPer / 2); e += kConsumers * kTile) {
+      const int cl = e / (kPer / 2), w = e - cl * (kPer / 2);
+      cp_async16(dst + cl * kUbStride + 2 * w, src + (int64_t)cl * kPer + 2 * w);
+    }
+    cp_async_commit();
+  };
+  float2* hrow = hacc + v * kHaccStride;
+  // add t at the halo position of code (bits 0-7); lanes with equal
+  // positions in the order of their precomputed ranks (bits 8-12)
+  auto accumulate = [&](bool act, int code, DF t) {
+    const int hp = code & kHaloPosMask;
+    const unsigned rank = (unsigned)code >> 8;
+    const unsigned rmax = __reduce_max_sync(0xffffffffu, act ? rank : 0u);
+    for (unsigned r = 0; r <= rmax; ++r) {
+      if (act && rank == r) {
+        const float2 q = hrow[hp];
+        const DF s = DF{q.x, q.y} + t;
+        hrow[hp] = make_float2(s.h, s.l);
+      }
+      __syncwarp();
+    }
+  };
+  int64_t g = 0;
+  int hb = 0;
+  bool dead = false;
+  if ((int64_t)blockIdx.x < n_tiles) prefetch(blockIdx.x, 0);
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, hb ^= 1) {
+    consumer_sync();  // the previous tile's accumulator, flags and Uq_bar stage are released
+    const int64_t nxt = tile + gridDim.x;
+    if (nxt < n_tiles)
+      prefetch(nxt, hb ^ 1);
+    else
+      cp_async_commit();
+    const int h0 = h.off[tile], H = h.off[tile + 1] - h0;
+    for (int i = lane; i < H; i += kTile) hrow[i] = make_float2(0.f, 0.f);
+    const int64_t c = tile * kTile + lane;
+    const bool valid = c < n_cell;
+    const uint8_t sel = valid ? sel_in[(int64_t)v * n_pad + c] : (uint8_t)0;
+    const bool vs = __any_sync(0xffffffffu, valid && vjp_needs_small(sel));
+    if (lane == 0) need[v] = vs;
+    cp_async_wait<1>();
+    consumer_sync();  // the tile's Uq_bar has landed; the flags are set
+    const bool small = need[0] | need[1] | need[2] | need[3];
+    const int n_stages = small ? VP::kStages : VP::kNL;
+    // Uq_bar of (c, v) at the Gauss points as pairs; the dU_0 term
+    DF ub[NQ3];
+    DF u0b = {0.f, 0.f};
+    {
+      const double* us = ubs + (size_t)hb * kTile * kUbStride + lane * kUbStride + v;
+#pragma unroll
+      for (int p = 0; p < NQ3; ++p) {
+        ub[p] = valid ? d_to_df(us[p * NV]) : DF{0.f, 0.f};
+        u0b = u0b + ub[p];
+      }
+    }
+    const bool large = valid && (sel & 8);
+    const int nd = (sel & 1) + ((sel >> 1) & 1) + ((sel >> 2) & 1);
+    // coefficient adjoints of the directional polynomials (first kSmallM
+    // basis functions), only where some lane of the block needs them
+    DF cbs[kSmallM];
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) cbs[l] = {0.f, 0.f};
+    if (small && valid && !large) {
+#pragma unroll
+      for (int p = 0; p < NQ3; ++p)
+#pragma unroll
+        for (int l = 0; l < kSmallM; ++l) df_mac(cbs[l], ev.psi[p * kMaxM + l], ub[p]);
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) cbs[l] = df_norm(cbs[l]);
+    }
+    DF tot = {0.f, 0.f};
+    for (int j = 0; j < n_stages; ++j, ++g) {
+      const int b = (int)(g % kRingV);
+      int slot0, nslot, k, bytes;
+      int64_t off;
+      VP::stage(j, slot0, nslot, k, off, bytes);
+      if (!dead) {
+        const int w = mbar_wait_or_abort(&full[b], (uint32_t)(g / kRingV) & 1, abort_flag);
+        if (w == 0) {
+          atomicOr(err, 2);
+          *abort_flag = 1;
+        }
+        dead = __any_sync(0xffffffffu, w != 1);
+      }
+      const float2* mat = reinterpret_cast<const float2*>(smem + (size_t)b * VP::kMat) + lane;
+      const uint16_t* nl =
+          reinterpret_cast<const uint16_t*>(smem + (size_t)b * VP::kMat + VP::kNOff) + lane;
+      if (dead) {
+        // skip the stage
+      } else if (k < 0) {
+        if (__any_sync(0xffffffffu, large)) {
+#pragma unroll
+          for (int s = 0; s < VP::kLPS; ++s) {
+            if (s < nslot) {
+              DF t = {0.f, 0.f};
+              if (large) {
+#pragma unroll
+                for (int p = 0; p < NQ3; ++p) df_mac(t, mat[(s * NQ3 + p) * kTile], ub[p]);
+                t = df_norm(t);
+              }
+              accumulate(large, nl[s * kTile], t);
+              tot = tot + t;
+            }
+          }
+        }
+      } else {
+        const bool on = valid && !large && ((sel >> k) & 1);
+        if (__any_sync(0xffffffffu, on)) {
+#pragma unroll
+          for (int s = 0; s < VP::kSPS; ++s) {
+            DF t = {0.f, 0.f};
+            if (on) {
+#pragma unroll
+              for (int l = 0; l < kSmallM; ++l) df_mac(t, mat[(s * kSmallM + l) * kTile], cbs[l]);
+              t = df_div_small(df_norm(t), nd);
+            }
+            accumulate(on, nl[s * kTile], t);
+            tot = tot + t;
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0 && !dead) mbar_arrive(&empty[b]);
+    }
+    if (valid && !dead) u_self[(int64_t)v * n_pad + c] = to_d(u0b - tot);
+    consumer_sync();  // every variable's accumulator is complete
+    if (!dead) {
+      float2* dst = part + (int64_t)h0 * NV;
+      for (int e = tid; e < H * NV; e += kConsumers * kTile)
+        dst[e] = hacc[(e & 3) * kHaccStride + (e >> 2)];
+    }
+  }
+  cp_async_wait<0>();
+}
+
 #ifndef TENO_SCATTER_BATCH
 #define TENO_SCATTER_BATCH 4
 #endif
@@ -3331,6 +3639,44 @@ cudaError_t launch_recon_vjp(const DeviceMesh& dm, const uint8_t* sel, const dou
       else go(I4{}, TypeTag<double>{});
     }
     return cudaGetLastError();
+  });
+}
+
+template <int M, int NS, int NQ>
+cudaError_t launch_recon_vjp_tma_t(const DeviceMesh& dm, const uint8_t* sel, const double* Uq_bar,
+                                   float2* part, double* u_self, cudaStream_t st) {
+  using VP = VjpPlan<M, NS, 3 * NQ>;
+  auto kern = recon_vjp_tma_kernel<M, NS, NQ>;
+  const int threads = kTile * (kConsumers + 1);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)VP::kSmem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, VP::kSmem)) !=
+      cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
+  const int64_t grid = std::min<int64_t>(tiles, (int64_t)per_sm * sms);
+  kern<<<(unsigned)grid, threads, VP::kSmem, st>>>((const float2*)dm.ahat, dm.wq, dm.halo, sel,
+                                                   Uq_bar, part, u_self, dm.n_cell, dm.n_pad,
+                                                   dm.eval_df, dm.err_flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recon_vjp_tma(const DeviceMesh& dm, const uint8_t* sel, const double* Uq_bar,
+                                 double* part, double* u_self, cudaStream_t st) {
+  if (dm.precision != TENO_FP64 || dm.n_var != 4 || !dm.halo.off || !dm.wq || !dm.err_flag)
+    return cudaErrorInvalidValue;
+  return dispatch_order(dm.order, [&](auto Mc, auto NSc) -> cudaError_t {
+    constexpr int M = decltype(Mc)::value, NS = decltype(NSc)::value;
+    constexpr int NQ = (M <= 9) ? 2 : 3;
+    if (dm.nq != NQ) return cudaErrorInvalidValue;
+    return launch_recon_vjp_tma_t<M, NS, NQ>(dm, sel, Uq_bar, reinterpret_cast<float2*>(part),
+                                             u_self, st);
   });
 }
 

@@ -197,14 +197,17 @@ def test_torch_device_buffers(T, oracle_mod):
     assert np.array_equal(sel.cpu().numpy(), selo)
 
 
-@pytest.mark.parametrize("precision", [0, 2], ids=["fp64", "fp64native"])
-def test_adjoint_vs_oracle(T, oracle_mod, precision):
+@pytest.mark.parametrize("precision,variant", [(0, 2), (0, 1), (2, 2)],
+                         ids=["fp64-tiled", "fp64-per-slot", "fp64native"])
+def test_adjoint_vs_oracle(T, oracle_mod, precision, variant):
     """Discrete adjoint (frozen selection and flux branches) against the
-    oracle's adjoint: residual VJP and one SSP-RK3 step."""
+    oracle's adjoint: residual VJP and one SSP-RK3 step.  FP64 with variant 2
+    runs the tiled reconstruction VJP (halo partial sums), variant 1 the
+    per-slot d_bar and the reverse stencil map."""
     mesh = inputs.jittered_mesh(21, 19, 10.0, 10.0, seed=1004)
     for U, order, flux in [(inputs.cell_average(mesh, inputs.isentropic_vortex), 5, 1),
                            (_blast(mesh), 6, 2), (_blast(mesh), 4, 1)]:
-        t = _setup(T, mesh, order, 4, flux, precision=precision)
+        t = _setup(T, mesh, order, 4, flux, precision=precision, variant=variant)
         o = oracle_mod.Oracle(mesh, order=order, n_var=4, flux=flux)
         t.set_state(U)
         _, selo, _ = o.residual(U)
@@ -216,7 +219,7 @@ def test_adjoint_vs_oracle(T, oracle_mod, precision):
         t.set_selection_override(None)
     mesh = inputs.jittered_mesh(17, 16, 10.0, 10.0, seed=1005)
     U = inputs.cell_average(mesh, inputs.isentropic_vortex)
-    t = _setup(T, mesh, 5, 4, 1, precision=precision)
+    t = _setup(T, mesh, 5, 4, 1, precision=precision, variant=variant)
     o = oracle_mod.Oracle(mesh, order=5, n_var=4, flux=1)
     t.set_state(U)
     lam = inputs.random_directions(3001, 1, U.size)[0].reshape(U.shape)
