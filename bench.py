@@ -45,7 +45,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # captures summarised in profiles/ (64,800-cell vortex mesh); a launch's
 # traffic is this times the cells it processes.  Absent when the kernel
 # changed since the capture.
-NCU_TRAFFIC_PER_CELL = {("fp64", 5): 5235.4, ("fp32_mixed", 5): 2674.4, ("fp64_native", 5): 5213.7}
+NCU_TRAFFIC_PER_CELL = {("fp64_native", 5): 5213.7}
 
 
 def ncu_traffic(precision, order, n_cell):
@@ -123,6 +123,20 @@ def algorithmic_bytes(order, n_var, precision):
     entries = m * ns + 3 * 12 * 5
     esz = 8 if precision == "fp64" else 4
     return entries * esz + (ns + 36) * 4 + n_var * 8 + 1 + n_var
+
+
+def algorithmic_vjp_bytes(order, nq):
+    """Bytes one tiled reconstruction-VJP launch must move per cell (Euler,
+    FP64 path, large stencil kept): the per-cell W = Psi' G pairs, the halo
+    positions of the large-stencil slots, Uq_bar at the 3 nq Gauss points,
+    the selection bytes and the cell's own dU_0 term.  The per-tile halo
+    partial sums are implementation overhead and not counted; tiles where a
+    cell keeps a directional stencil also stream its (hi, lo) matrices."""
+    r = order - 1
+    m = (r + 1) * (r + 2) // 2 - 1
+    ns = 2 * (m + 1)
+    nq3 = 3 * nq
+    return ns * nq3 * 8 + ns * 2 + nq3 * 4 * 8 + 4 + 4 * 8
 
 
 def algorithmic_fp64_flops(order, n_var, nq):
@@ -328,10 +342,20 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         adj_ms = e0.elapsed_time(e1) / na
-        akms, _ = t64.profile_read()
+        akms, alaunch = t64.profile_read()
         t64.profile(False)
+        # dominant adjoint kernel: the tiled reconstruction VJP (kind 6)
+        vjp_ms = akms[6] / max(1, alaunch[6])
+        vjp_gbs = algorithmic_vjp_bytes(args.order, nq) * n_cell / (vjp_ms / 1e3) / 1e9
+        vjp_roof = {"bound": "hbm", "achieved": vjp_gbs, "peak": hbm_gbs, "unit": "GB/s",
+                    "frac": vjp_gbs / hbm_gbs,
+                    "traffic": ncu_traffic("adjoint_vjp", args.order, n_cell),
+                    "kernel": f"recon_vjp_tma_kernel <fp64> order {args.order}",
+                    "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)",
+                    "ms_per_launch": vjp_ms}
         extras["adjoint"] = {"ms_per_step": adj_ms, "forward_ms_per_step": main["ms_per_step"],
                              "adjoint_over_forward": adj_ms / main["ms_per_step"],
+                             "roofline": vjp_roof,
                              "kernel_ms_per_step": (akms / na).tolist(),
                              "note": "one adjoint SSP-RK3 step, including the replay of its two "
                                      "forward stages"}

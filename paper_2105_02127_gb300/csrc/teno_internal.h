@@ -115,7 +115,9 @@ cudaError_t launch_permute_u8(const uint8_t* src, uint8_t* dst, const int32_t* p
                               cudaStream_t st);
 cudaError_t launch_axpby(double* out, const double* a, double ca, const double* b, double cb,
                          int64_t n, cudaStream_t st);
-// adjoint kernels
+// adjoint kernels.  Uq_bar ([cell][edge point][var], 8 bytes an entry)
+// holds (hi, lo) float pairs on the TENO_FP64 path and doubles on the native
+// path; the reconstruction VJPs read it in the same form.
 cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const double* w,
                                  double* Uq_bar, double time, cudaStream_t st);
 cudaError_t launch_recon_vjp(const DeviceMesh& dm, const uint8_t* sel, const double* Uq_bar,

@@ -2601,6 +2601,17 @@ struct VjpArgs {
 #endif
 constexpr bool kVjpReverse = TENO_VJP_REVERSE != 0;
 
+// Uq_bar entry i: (hi, lo) pairs on the pair path (S = DF; read as pairs by
+// the reconstruction VJP, no FP64 conversion on either side), FP64 on the
+// native path
+template <typename S>
+__device__ __forceinline__ void store_bar(double* base, int i, S x) {
+  if constexpr (std::is_same<S, DF>::value)
+    reinterpret_cast<float2*>(base)[i] = make_float2(x.h, x.l);
+  else
+    base[i] = to_d(x);
+}
+
 template <int NV, int NQ, int FLUX, typename TQ, typename S, int ND>
 __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
                                                             const TQ* __restrict__ Uq,
@@ -2652,10 +2663,12 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
       }
       euler_riemann_vjp<S>(uL, uR, rks, FLUX == TENO_FLUX_HLLC, Kw, ULb, URb);
       if (n < 0) ghost_vjp<S>(en, rks, URb, ULb);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        outL[v] = to_d(ULb[v]);
-        if (n >= 0) outR[v] = to_d(URb[v]);
+      if constexpr (std::is_same<S, DF>::value) {
+        st_group<NV>(reinterpret_cast<DF*>(outL), ULb);
+        if (n >= 0) st_group<NV>(reinterpret_cast<DF*>(outR), URb);
+      } else {
+        st_group<NV>(outL, ULb);
+        if (n >= 0) st_group<NV>(outR, URb);
       }
     } else {
       for (int pass = 0; pass < n_pass; ++pass) {
@@ -2695,9 +2708,9 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
           for (int i = 0; i < NV; ++i) sacc = madd(F[i].d[j], Kw[i], sacc);
           const int g = dir0 + j;
           if (g < NV)
-            outL[g] = to_d(sacc);
+            store_bar<S>(outL, g, sacc);
           else if (n >= 0)
-            outR[g - NV] = to_d(sacc);
+            store_bar<S>(outR, g - NV, sacc);
         }
       }
     }
@@ -2815,10 +2828,11 @@ __global__ void __launch_bounds__(128) recon_vjp_df_kernel(const float2* __restr
 #pragma unroll
   for (int l = 0; l < M; ++l) cb[l] = {0.f, 0.f};
   DF u0b = {0.f, 0.f};
-  const double* ub = Uq_bar + c * (3 * NQ * NV) + v;
+  // Uq_bar as (hi, lo) pairs (written so by the pair-path flux VJP)
+  const float2* ub = reinterpret_cast<const float2*>(Uq_bar) + c * (3 * NQ * NV) + v;
 #pragma unroll
   for (int p = 0; p < 3 * NQ; ++p) {
-    const DF b = d_to_df(ub[p * NV]);
+    const DF b = {ub[p * NV].x, ub[p * NV].y};
     u0b = u0b + b;
 #pragma unroll
     for (int l = 0; l < M; ++l) df_mac(cb[l], ev.psi[p * kMaxM + l], b);
@@ -3071,14 +3085,16 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), 3)
     consumer_sync();  // the tile's Uq_bar has landed; the flags are set
     const bool small = need[0] | need[1] | need[2] | need[3];
     const int n_stages = small ? VP::kStages : VP::kNL;
-    // Uq_bar of (c, v) at the Gauss points as pairs; the dU_0 term
+    // Uq_bar of (c, v) at the Gauss points (stored as pairs); the dU_0 term
     DF ub[NQ3];
     DF u0b = {0.f, 0.f};
     {
-      const double* us = ubs + (size_t)hb * kTile * kUbStride + lane * kUbStride + v;
+      const float2* us = reinterpret_cast<const float2*>(ubs) +
+                         (size_t)hb * kTile * kUbStride + lane * kUbStride + v;
 #pragma unroll
       for (int p = 0; p < NQ3; ++p) {
-        ub[p] = valid ? d_to_df(us[p * NV]) : DF{0.f, 0.f};
+        const float2 q = us[p * NV];
+        ub[p] = valid ? DF{q.x, q.y} : DF{0.f, 0.f};
         u0b = u0b + ub[p];
       }
     }
@@ -3118,17 +3134,25 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), 3)
         // skip the stage
       } else if (k < 0) {
         if (__any_sync(0xffffffffu, large)) {
+          // the stage's slot values first (independent chains), then their
+          // accumulation slot by slot
+          DF ts[VP::kLPS];
+#pragma unroll
+          for (int s = 0; s < VP::kLPS; ++s) {
+            ts[s] = {0.f, 0.f};
+            if (large && s < nslot) {
+#pragma unroll
+              for (int p = 0; p < NQ3; ++p) df_mac(ts[s], mat[(s * NQ3 + p) * kTile], ub[p]);
+              ts[s] = df_norm(ts[s]);
+            }
+          }
 #pragma unroll
           for (int s = 0; s < VP::kLPS; ++s) {
             if (s < nslot) {
-              DF t = {0.f, 0.f};
-              if (large) {
-#pragma unroll
-                for (int p = 0; p < NQ3; ++p) df_mac(t, mat[(s * NQ3 + p) * kTile], ub[p]);
-                t = df_norm(t);
-              }
-              accumulate(large, nl[s * kTile], t);
-              tot = tot + t;
+              accumulate(large, nl[s * kTile], ts[s]);
+              const DF q = two_sum(tot.h, ts[s].h);  // running sum, renormalised at the end
+              tot.h = q.h;
+              tot.l += q.l + ts[s].l;
             }
           }
         }
@@ -3144,14 +3168,16 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), 3)
               t = df_div_small(df_norm(t), nd);
             }
             accumulate(on, nl[s * kTile], t);
-            tot = tot + t;
+            const DF q = two_sum(tot.h, t.h);
+            tot.h = q.h;
+            tot.l += q.l + t.l;
           }
         }
       }
       __syncwarp();
       if (lane == 0 && !dead) mbar_arrive(&empty[b]);
     }
-    if (valid && !dead) u_self[(int64_t)v * n_pad + c] = to_d(u0b - tot);
+    if (valid && !dead) u_self[(int64_t)v * n_pad + c] = to_d(u0b - df_norm(tot));
     consumer_sync();  // every variable's accumulator is complete
     if (!dead) {
       float2* dst = part + (int64_t)h0 * NV;
