@@ -2584,6 +2584,7 @@ struct VjpArgs {
   int64_t n_face, n_pad;
   double gamma, adv_x, adv_y, time;
   double gw[kMaxNq], gt[kMaxNq];
+  float2 gw2[kMaxNq];  // Gauss weights as (hi, lo) pairs
 };
 
 // Uq_bar[(c,edge,q)] = w_q |A| (dF/dU_side)^T Kbar with Kbar = dJ/dK_f
@@ -2624,26 +2625,29 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
   const int o = a.f_cells[2 * f], n = a.f_cells[2 * f + 1];
   const int eo = a.f_edges[2 * f], en = a.f_edges[2 * f + 1];
   const double nx = a.f_geom[5 * f], ny = a.f_geom[5 * f + 1], len = a.f_geom[5 * f + 2];
-  double Kb[NV];
+  // Kbar in FP64 from the FP64 weights, once per face in the flux scalar type
+  S Kb[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    Kb[v] = -w[v * a.n_pad + o] * a.inv_area[o];
-    if (n >= 0) Kb[v] += w[v * a.n_pad + n] * a.inv_area[n];
+    double kb = -w[v * a.n_pad + o] * a.inv_area[o];
+    if (n >= 0) kb = fma(w[v * a.n_pad + n], a.inv_area[n], kb);
+    Kb[v] = cst<S>(kb);
   }
   const int n_pass = ((n >= 0 ? 2 * NV : NV) + ND - 1) / ND;
   RiemannK<S> rks;
-  S tl_unused;
-  face_k<S>(a.f_geom, a.f_geom2, f, a.gamma, a.g2, a.gm12, rks, tl_unused);
+  S tl;  // |A| in the flux scalar type
+  face_k<S>(a.f_geom, a.f_geom2, f, a.gamma, a.g2, a.gm12, rks, tl);
   const RiemannK<D> rk = riemann_k_dual<ND, S>(rks);
   for (int k = 0; k < NQ; ++k) {
     TQ ul[NV], ur[NV];
     ld_group<NV>(Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV, ul);
     if (n >= 0) ld_group<NV>(Uq + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV, ur);
-    const double wk = a.gw[k] * len;
-    const double x = a.f_geom[5 * f + 3] - ny * len * a.gt[k];
+    // x of the Gauss point (ghost states and the scalar field only)
+    auto xq = [&]() { return a.f_geom[5 * f + 3] - ny * len * a.gt[k]; };
+    const S wl = gauss_w<S>(a.gw[k], a.gw2[k]) * tl;
     S Kw[NV];  // w_k |A| Kbar in the flux scalar type
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Kw[v] = cst<S>(wk * Kb[v]);
+    for (int v = 0; v < NV; ++v) Kw[v] = wl * Kb[v];
     double* outL = Uq_bar + ((int64_t)(o * 3 + eo) * NQ + k) * NV;
     double* outR = n >= 0 ? Uq_bar + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV : outL;
     if constexpr (NV == 4 && kVjpReverse) {
@@ -2659,7 +2663,7 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
 #pragma unroll
         for (int v = 0; v < NV; ++v) uR[v] = lift<S>(ur[v]);
       } else {
-        ghost_state<S>(en, uL, nx, ny, x, a.time, a.gamma, uR);
+        ghost_state<S>(en, uL, nx, ny, xq(), a.time, a.gamma, uR);
       }
       euler_riemann_vjp<S>(uL, uR, rks, FLUX == TENO_FLUX_HLLC, Kw, ULb, URb);
       if (n < 0) ghost_vjp<S>(en, rks, URb, ULb);
@@ -2688,7 +2692,7 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
             if (NV + v >= dir0 && NV + v < dir0 + ND) UR[v].d[NV + v - dir0] = cst<S>(1.0);
           }
         } else if constexpr (NV == 4) {
-          ghost_state<D>(en, UL, nx, ny, x, a.time, a.gamma, UR);  // carries dUR/dUL
+          ghost_state<D>(en, UL, nx, ny, xq(), a.time, a.gamma, UR);  // carries dUR/dUL
         } else {
 #pragma unroll
           for (int v = 0; v < NV; ++v) UR[v] = UL[v];
@@ -2696,7 +2700,7 @@ __global__ void __launch_bounds__(128) face_flux_vjp_kernel(const VjpArgs a,
         if constexpr (NV == 1) {
           const double yq = a.f_geom[5 * f + 4] + nx * len * a.gt[k];
           const double an = adv_normal(a.adv_field, a.adv_x, a.adv_y, a.adv_cx, a.adv_cy,
-                                       a.adv_omega, a.adv_r1, a.adv_r2, x, yq, nx, ny);
+                                       a.adv_omega, a.adv_r1, a.adv_r2, xq(), yq, nx, ny);
           F[0] = an * (an >= 0.0 ? UL[0] : UR[0]);
         } else {
           euler_riemann<D>(UL, UR, rk, FLUX == TENO_FLUX_HLLC, F);
@@ -3594,6 +3598,7 @@ cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const dou
   for (int k = 0; k < kMaxNq; ++k) {
     a.gw[k] = dm.gw[k];
     a.gt[k] = dm.gt[k];
+    a.gw2[k] = split2(dm.gw[k]);
   }
   const unsigned grid = (unsigned)((dm.n_face + 127) / 128);
   auto go = [&](auto nvc, auto nqc, auto flc, auto tqc) {
