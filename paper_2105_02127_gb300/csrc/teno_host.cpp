@@ -69,7 +69,7 @@ struct teno_ctx {
   // device data
   DeviceMesh dm;
   DevBuf b_halo_off, b_halo_ids, b_halo_loc, b_g32, b_wq, b_psi, b_cspeed, b_coef;
-  DevBuf b_ahat, b_nbr, b_smask, b_fcells, b_fedges, b_fgeom, b_fgeom2, b_cfaces, b_inv_area, b_cfl_len,
+  DevBuf b_ahat, b_nbr, b_smask, b_fcells, b_fedges, b_fgeom, b_fgeom2, b_cfaces, b_inv_area, b_cfl_len, b_cfl_ilen2,
       b_perm;
   DevBuf b_U, b_U1, b_U2, b_R, b_tmp, b_Uq, b_K, b_sel, b_sel_ovr, b_maxlam, b_flag;
   DevBuf b_Usplit;  // FP32 hi/lo split of the state being reconstructed (mixed precision)
@@ -1146,6 +1146,15 @@ int upload_mesh(teno_ctx* ctx) {
   if (!rc) rc = upload(ctx, ctx->b_cfaces, cfaces.data(), cfaces.size() * 4);
   if (!rc) rc = upload(ctx, ctx->b_inv_area, inv_area.data(), inv_area.size() * 8);
   if (!rc) rc = upload(ctx, ctx->b_cfl_len, cfl_len.data(), cfl_len.size() * 8);
+  if (!rc) {
+    std::vector<float2> ilen2(npad);
+    for (int64_t c = 0; c < npad; ++c) {
+      const double x = 1.0 / cfl_len[c];
+      const float h = (float)x;
+      ilen2[c] = make_float2(h, (float)(x - (double)h));
+    }
+    rc = upload(ctx, ctx->b_cfl_ilen2, ilen2.data(), ilen2.size() * sizeof(float2));
+  }
   if (!rc) rc = upload(ctx, ctx->b_perm, ctx->perm.data(), ctx->perm.size() * 4);
   if (rc) return rc;
   DeviceMesh& dm = ctx->dm;
@@ -1159,6 +1168,7 @@ int upload_mesh(teno_ctx* ctx) {
   dm.c_faces = (const int32_t*)ctx->b_cfaces.p;
   dm.inv_area = (const double*)ctx->b_inv_area.p;
   dm.cfl_len = (const double*)ctx->b_cfl_len.p;
+  dm.cfl_ilen2 = (const float2*)ctx->b_cfl_ilen2.p;
   return TENO_OK;
 }
 
@@ -1419,7 +1429,7 @@ int teno_destroy(teno_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   DevBuf* bufs[] = {&ctx->b_halo_off, &ctx->b_halo_ids, &ctx->b_halo_loc, &ctx->b_g32, &ctx->b_wq, &ctx->b_psi, &ctx->b_cspeed, &ctx->b_coef, &ctx->b_ahat, &ctx->b_nbr, &ctx->b_smask, &ctx->b_fcells, &ctx->b_fedges,
-                    &ctx->b_fgeom, &ctx->b_fgeom2, &ctx->b_cfaces, &ctx->b_inv_area, &ctx->b_cfl_len,
+                    &ctx->b_fgeom, &ctx->b_fgeom2, &ctx->b_cfaces, &ctx->b_inv_area, &ctx->b_cfl_len, &ctx->b_cfl_ilen2,
                     &ctx->b_perm, &ctx->b_U, &ctx->b_U1, &ctx->b_U2, &ctx->b_R, &ctx->b_tmp,
                     &ctx->b_Uq, &ctx->b_K, &ctx->b_sel, &ctx->b_sel_ovr, &ctx->b_maxlam,
                     &ctx->b_Usplit,
@@ -1653,9 +1663,15 @@ static int rk3_once(teno_ctx* ctx, double dt, double* dt_used) {
       if (rc) return rc;
     } else {
       long pe = prof_begin(ctx, K_CFL);
-      CK(launch_max_lambda(ctx->dm, (const double*)ctx->b_U.p, (double*)ctx->b_maxlam.p,
-                           ctx->stream),
-         "max lambda launch");
+      // from the (hi, lo) split of U where the FP64 or mixed path holds it
+      if (ctx->split_ok && ctx->prm.n_var == 4 && ctx->prm.precision != TENO_FP64_NATIVE)
+        CK(launch_max_lambda_split(ctx->dm, (const float2*)ctx->b_Usplit.p,
+                                   (double*)ctx->b_maxlam.p, ctx->stream),
+           "max lambda launch");
+      else
+        CK(launch_max_lambda(ctx->dm, (const double*)ctx->b_U.p, (double*)ctx->b_maxlam.p,
+                             ctx->stream),
+           "max lambda launch");
       prof_end(ctx, pe);
       maxlam = (const double*)ctx->b_maxlam.p;
     }

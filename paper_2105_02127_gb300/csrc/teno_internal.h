@@ -83,7 +83,8 @@ struct DeviceMesh {
   const float2* f_geom2 = nullptr;  // [n_face][3] nx, ny, |A| as (hi, lo) float pairs
   const int32_t* c_faces = nullptr; // [n_pad][3] face*2 + (1 if the cell is the neighbour)
   const double* inv_area = nullptr; // [n_pad]
-  const double* cfl_len = nullptr;  // [n_pad] 4|V|/perimeter
+  const double* cfl_len = nullptr;    // [n_pad] 4|V|/perimeter
+  const float2* cfl_ilen2 = nullptr;  // [n_pad] 1 / cfl_len as (hi, lo) pairs
   EvalTable eval;
   DFTable eval_df;
   double gw[kMaxNq];                // Gauss weights on [0,1], sum 1
@@ -105,6 +106,9 @@ cudaError_t launch_face_flux(const DeviceMesh& dm, const void* Uq, void* K, doub
 cudaError_t launch_gather(const DeviceMesh& dm, const void* K, const double* Un, const double* Us,
                           double* out, int mode, double cn, double cs, double dt_fixed,
                           const double* max_lam, int* flag, float2* split, cudaStream_t st);
+// the same maximum from the (hi, lo) state split (Euler, FP64 and mixed paths)
+cudaError_t launch_max_lambda_split(const DeviceMesh& dm, const float2* Us, double* max_lam,
+                                    cudaStream_t st);
 cudaError_t launch_max_lambda(const DeviceMesh& dm, const double* U, double* max_lam,
                               cudaStream_t st);
 cudaError_t launch_permute(const double* src, double* dst, const int32_t* perm, int64_t n,

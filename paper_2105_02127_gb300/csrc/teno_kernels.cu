@@ -2564,6 +2564,46 @@ __global__ void __launch_bounds__(256) max_lambda_kernel(const double* __restric
   }
 }
 
+// The same maximum from the (hi, lo) split of the state that the FP64 and
+// mixed paths keep for the reconstruction (Euler): lambda_c = (|u| + c) / L_c
+// in pair arithmetic on the FP32 pipe (relative error ~1e-14, far below what
+// a CFL step needs) with 1/L_c as host-split pairs; the maximum as FP64
+// bits.  Non-physical cells (NaN speed) are skipped as fmax skips them.
+__global__ void __launch_bounds__(256) max_lambda_split_kernel(const float2* __restrict__ Us,
+                                                               const float2* __restrict__ ilen2,
+                                                               int64_t n_cell, int64_t n_pad,
+                                                               float2 g2, float2 gm12,
+                                                               unsigned long long* out) {
+  const DF one = {1.f, 0.f}, half = {0.5f, 0.f}, gg = {g2.x, g2.y}, gm1 = {gm12.x, gm12.y};
+  DF lam = {0.f, 0.f};
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const float2 q0 = Us[c], q1 = Us[n_pad + c], q2 = Us[2 * n_pad + c], q3 = Us[3 * n_pad + c];
+    const DF rho = {q0.x, q0.y}, mx = {q1.x, q1.y}, my = {q2.x, q2.y}, E = {q3.x, q3.y};
+    const DF ir = one / rho;
+    const DF u = mx * ir, v = my * ir;
+    const DF q = u * u + v * v;
+    const DF p = gm1 * (E - half * rho * q);
+    const DF sp = tsqrt(q) + tsqrt(gg * p * ir);
+    const float2 il = ilen2[c];
+    const DF l = sp * DF{il.x, il.y};
+    if (l.h == l.h) lam = vmax(lam, l);
+  }
+  double d = to_d(lam);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+  __shared__ double red[32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = d;
+  __syncthreads();
+  if (w == 0) {
+    d = l < (int)(blockDim.x >> 5) ? red[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+    if (l == 0) atomicMax(out, (unsigned long long)__double_as_longlong(d));
+  }
+}
+
 // -------------------------------------------------------------- utilities
 __global__ void permute_kernel(const double* __restrict__ src, double* __restrict__ dst,
                                const int32_t* __restrict__ perm, int64_t n, int64_t ld_src,
@@ -3575,6 +3615,19 @@ cudaError_t launch_max_lambda(const DeviceMesh& dm, const double* U, double* max
     max_lambda_kernel<4><<<(unsigned)blocks, 256, 0, st>>>(
         U, dm.cfl_len, dm.n_cell, dm.n_pad, dm.gamma, adv, nullptr,
         (unsigned long long*)max_lam);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max_lambda_split(const DeviceMesh& dm, const float2* Us, double* max_lam,
+                                    cudaStream_t st) {
+  if (dm.n_var != 4 || !dm.cfl_ilen2 || !Us) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(max_lam, 0, sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  int64_t blocks = (dm.n_cell + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  max_lambda_split_kernel<<<(unsigned)blocks, 256, 0, st>>>(
+      Us, dm.cfl_ilen2, dm.n_cell, dm.n_pad, split2(dm.gamma), split2(dm.gamma - 1.0),
+      (unsigned long long*)max_lam);
   return cudaGetLastError();
 }
 
