@@ -1487,7 +1487,7 @@ constexpr size_t out_stage_bytes() {
 
 // Stage j of a tile's matrix block: kLPS large-stencil slots, or kSPS slots of
 // one directional stencil.
-template <int M, int NS, int kEsz, int kLPS, int kSPS>
+template <int M, int NS, int kEsz, int kLPS, int kSPS, int kRingT = kRing>
 struct StagePlan {
   static constexpr int kSlotL = M * kTile * kEsz;
   static constexpr int kSlotS = kSmallM * kTile * kEsz;
@@ -1505,7 +1505,7 @@ struct StagePlan {
   static constexpr int64_t kTileBytes = (int64_t)kE * kTile * kEsz;
   static constexpr size_t kHaloBytes = (size_t)2 * 4 * kHaloMax * sizeof(float2);
   static constexpr size_t kSmem =
-      (size_t)kRing * kMat + kHaloBytes + 2 * kRing * sizeof(uint64_t) + 16;
+      (size_t)kRingT * kMat + kHaloBytes + 2 * kRingT * sizeof(uint64_t) + 16;
   static_assert(kSmallN % kSPS == 0, "directional stencil split");
   static_assert(kMat % 16 == 0, "16-byte aligned buffers");
   __device__ static void stage(int j, int& slot0, int& nslot, int64_t& off, int& bytes, int& k) {
@@ -1527,17 +1527,32 @@ struct StagePlan {
   }
 };
 
-template <bool kDF>
+// Ring depth of the FP32-mixed bulk-copy reconstruction: 4 stages unless
+// they keep the kernel below four blocks per SM, then 3 (TENO6: 3 -> 4 blocks,
+// 7 % faster; TENO5 fits four blocks with 4 stages).  TENO_RING_MIXED > 0
+// overrides.
+#ifndef TENO_RING_MIXED
+#define TENO_RING_MIXED 0
+#endif
+template <int M, int NS, int NQ>
+struct MixedRing {
+  static constexpr size_t kBlock4 = StagePlan<M, NS, 4, 4, 4, 4>::kSmem +
+                                    (TENO_STAGE_OUT ? out_stage_bytes<3 * NQ * 4, float>() : 0) +
+                                    1024;
+  static constexpr int value =
+      TENO_RING_MIXED > 0 ? TENO_RING_MIXED : (4 * kBlock4 <= (size_t)228 * 1024 ? 4 : 3);
+};
+template <bool kDF, int M, int NS, int NQ>
 struct TmaTraits {
   using TE = float2;  // matrix entry: (hi, lo)
   using Acc = DF;
-  static constexpr int kLPS = 4, kSPS = 4;
+  static constexpr int kLPS = 4, kSPS = 4, kRing = 4;
 };
-template <>
-struct TmaTraits<false> {
+template <int M, int NS, int NQ>
+struct TmaTraits<false, M, NS, NQ> {
   using TE = float;
   using Acc = float;
-  static constexpr int kLPS = 4, kSPS = 4;
+  static constexpr int kLPS = 4, kSPS = 4, kRing = MixedRing<M, NS, NQ>::value;
 };
 
 // Persistent kernel, Euler only.  Producer lane: the matrix block of every
@@ -1548,9 +1563,10 @@ struct TmaTraits<false> {
 template <int M, int NS, int NQ, bool kDF, bool kExt>
 __global__ void __launch_bounds__(kTile * (kConsumers + 1))
     recon_tma_kernel(const ReconArgs a, const HaloArgs h, const DFTable ev, int* err) {
-  using TR = TmaTraits<kDF>;
+  using TR = TmaTraits<kDF, M, NS, NQ>;
   using TE = typename TR::TE;
-  using P = StagePlan<M, NS, (int)sizeof(TE), TR::kLPS, TR::kSPS>;
+  constexpr int kRing = TR::kRing;
+  using P = StagePlan<M, NS, (int)sizeof(TE), TR::kLPS, TR::kSPS, kRing>;
   constexpr int NV = 4;
   constexpr int SL = NS + kSmallSlots;
   constexpr int kPer = 3 * NQ * NV;  // Gauss-point values per cell
@@ -2506,12 +2522,12 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs a, const T
     for (int v = 0; v < NV; ++v) out[v * a.n_pad + c] = -acc[v] * ia;
     return;
   }
-  const double dt = s_dt;
+  const double wr = cs * s_dt * ia;  // the stage's weight of the face-flux sum
   double u[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const int64_t i = v * a.n_pad + c;
-    u[v] = cn * Un[i] + cs * (Us[i] - dt * acc[v] * ia);
+    u[v] = fma(-wr, acc[v], fma(cn, Un[i], cs * Us[i]));
     out[i] = u[v];
     if (split) {
       const float hi = (float)u[v];
@@ -3365,8 +3381,8 @@ cudaError_t dispatch_order(int order, F&& f) {
 // ---------------------------------------------------------------- launchers
 template <int M, int NS, int NQ, bool kDF, bool kExt>
 cudaError_t launch_recon_tma(const ReconArgs& a, const DeviceMesh& dm, int* err, cudaStream_t st) {
-  using TR = TmaTraits<kDF>;
-  using P = StagePlan<M, NS, (int)sizeof(typename TR::TE), TR::kLPS, TR::kSPS>;
+  using TR = TmaTraits<kDF, M, NS, NQ>;
+  using P = StagePlan<M, NS, (int)sizeof(typename TR::TE), TR::kLPS, TR::kSPS, TR::kRing>;
   auto kern = recon_tma_kernel<M, NS, NQ, kDF, kExt>;
   const int threads = kTile * (kConsumers + 1);
   constexpr bool kStage = TENO_STAGE_OUT && !kExt && !kDF;
