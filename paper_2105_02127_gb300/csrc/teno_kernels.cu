@@ -864,7 +864,7 @@ template <int M, int NQ, int NV, typename TA, typename TT, bool kExt = true>
 __device__ __forceinline__ void plain_finish(const ReconArgs& a, const TT& ev, int64_t c, int v,
                                              double u0, float2 u0s, const TA (&acc)[M],
                                              const TA (&as)[kSmallK][kSmallM],
-                                             TA* ostage = nullptr) {
+                                             TA* ostage = nullptr, int present_in = -1) {
   constexpr bool kMixed = std::is_same<TA, float>::value;
   if constexpr (kExt) {
     if (a.coef_out) {
@@ -872,7 +872,7 @@ __device__ __forceinline__ void plain_finish(const ReconArgs& a, const TT& ev, i
       return;
     }
   }
-  const int present = a.smask[c];
+  const int present = present_in >= 0 ? present_in : a.smask[c];
   uint8_t sel;
   const bool cweno = kExt && a.scheme == 1 && !a.linear;
   TA cf[M];
@@ -1062,14 +1062,14 @@ template <int M, int NQ, int NV, bool kExt = true>
 __device__ __forceinline__ void df_finish(const ReconArgs& a, const DFTable& ev, int64_t c, int v,
                                           const DF (&acc)[M],
                                           const DF (&as)[kSmallK][kSmallM],
-                                          float2* ostage = nullptr) {
+                                          float2* ostage = nullptr, int present_in = -1) {
   if constexpr (kExt) {
     if (a.coef_out) {
       store_coefs<M, DF>(a, c, v, acc, as);
       return;
     }
   }
-  const int present = a.smask[c];
+  const int present = present_in >= 0 ? present_in : a.smask[c];
   uint8_t sel;
   const bool cweno = kExt && a.scheme == 1 && !a.linear;
   DF cf[M];
@@ -1555,6 +1555,66 @@ struct TmaTraits<false, M, NS, NQ> {
   static constexpr int kLPS = 4, kSPS = 4, kRing = MixedRing<M, NS, NQ>::value;
 };
 
+// Halo prefetch pipeline of the bulk-copy reconstruction kernels (consumer
+// threads).  The cp.async copies of a tile's halo need its halo ids, and the
+// ids need the tile's halo offsets: the offsets are loaded two tiles ahead
+// and the ids one tile ahead (two per thread: a halo has at most 256 cells
+// and there are 128 consumer threads), so issuing the copies never waits on
+// a global load.  Tiles advance by the grid size.
+struct HaloPipe {
+  static constexpr int kCT = kConsumers * kTile;
+  static_assert(kHaloMax <= 2 * kCT, "two halo ids per consumer thread");
+  const HaloArgs& h;
+  const float2* Us;
+  int64_t n_pad, n_tiles;
+  int tid;
+  int H1 = 0, id0 = 0, id1 = 0;  // ids of the next tile
+  int h02 = 0, H2 = 0;           // offsets of the tile after it
+  __device__ HaloPipe(const HaloArgs& h_, const float2* Us_, int64_t n_pad_, int64_t n_tiles_,
+                      int tid_)
+      : h(h_), Us(Us_), n_pad(n_pad_), n_tiles(n_tiles_), tid(tid_) {}
+  __device__ void offsets(int64_t tile, int& h0, int& H) const {
+    h0 = 0, H = 0;
+    if (tile < n_tiles) {
+      h0 = h.off[tile];
+      H = h.off[tile + 1] - h0;
+    }
+  }
+  __device__ void ids(int h0, int H) {
+    H1 = H, id0 = 0, id1 = 0;
+    if (tid < H) id0 = __ldg(h.ids + h0 + tid);
+    if (tid + kCT < H) id1 = __ldg(h.ids + h0 + tid + kCT);
+  }
+  // copies of the halo whose ids are held into buffer hb, one commit group
+  __device__ void issue(float2* halo, int hb) const {
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      if (tid < H1) cp_async8(&halo[(hb * 4 + w) * kHaloMax + tid], Us + (int64_t)w * n_pad + id0);
+      if (tid + kCT < H1)
+        cp_async8(&halo[(hb * 4 + w) * kHaloMax + tid + kCT], Us + (int64_t)w * n_pad + id1);
+    }
+    cp_async_commit();
+  }
+  // prologue: the first tile's halo into buffer 0 (waits once), the ids of
+  // the second tile and the offsets of the third
+  __device__ void start(int64_t t0, int64_t G, float2* halo) {
+    int h0, H;
+    offsets(t0, h0, H);
+    ids(h0, H);
+    issue(halo, 0);
+    offsets(t0 + G, h0, H);
+    ids(h0, H);
+    offsets(t0 + 2 * G, h02, H2);
+  }
+  // at tile t: the halo of t + G into buffer hb (an empty group past the
+  // end), then the ids of t + 2G and the offsets of t + 3G
+  __device__ void advance(int64_t t, int64_t G, float2* halo, int hb) {
+    issue(halo, hb);
+    ids(h02, H2);
+    offsets(t + 3 * G, h02, H2);
+  }
+};
+
 // Persistent kernel, Euler only.  Producer lane: the matrix block of every
 // tile in kRing-deep bulk-copy stages.  Consumer warps (one per variable):
 // the tile's stencil halo in a double-buffered shared-memory area, prefetched
@@ -1629,16 +1689,7 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
   // ---- consumers
   const int v = warp, tid = threadIdx.x;
   using Acc = typename TR::Acc;
-  auto prefetch = [&](int64_t tile, int hb) {
-    const int h0 = h.off[tile], H = h.off[tile + 1] - h0;
-    for (int i = tid; i < H; i += kConsumers * kTile) {
-      const int id = __ldg(h.ids + h0 + i);
-#pragma unroll
-      for (int w = 0; w < NV; ++w)
-        cp_async8(&halo[(hb * NV + w) * kHaloMax + i], a.Us + (int64_t)w * a.n_pad + id);
-    }
-    cp_async_commit();
-  };
+  HaloPipe hp(h, a.Us, a.n_pad, n_tiles, tid);
   auto mac = [](Acc& acc, TE m, Acc d) {
     if constexpr (kDF)
       df_mac(acc, m, d);
@@ -1648,20 +1699,28 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
   int64_t g = 0;
   int hb = 0;
   bool dead = false;  // a bounded wait of this block gave up: skip all work
-  if ((int64_t)blockIdx.x < n_tiles) prefetch(blockIdx.x, 0);
+  hp.start(blockIdx.x, gridDim.x, halo);
+  // the cell's own split state and stencil mask, loaded a tile ahead
+  auto own = [&](int64_t tile, float2& u, int& pm) {
+    const int64_t cc = tile * kTile + lane;
+    const int64_t ci = (tile < n_tiles && cc < a.n_cell) ? cc : 0;
+    u = a.Us[(int64_t)v * a.n_pad + ci];
+    pm = a.smask[ci];
+  };
+  float2 u0n;
+  int pmn;
+  own(blockIdx.x, u0n, pmn);
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, hb ^= 1) {
     consumer_sync();  // every consumer is done with the other halo buffer
-    const int64_t nxt = tile + gridDim.x;
-    if (nxt < n_tiles)
-      prefetch(nxt, hb ^ 1);
-    else
-      cp_async_commit();  // empty group keeps the group count uniform
-    cp_async_wait<1>();   // this thread's copies of the current halo have landed
-    consumer_sync();      // ... and everyone's
+    hp.advance(tile, gridDim.x, halo, hb ^ 1);  // halo of the next tile, ids a tile ahead
+    const float2 u0s = u0n;
+    const int present = pmn;
+    own(tile + gridDim.x, u0n, pmn);
+    cp_async_wait<1>();  // this thread's copies of the current halo have landed
+    consumer_sync();     // ... and everyone's
     const float2* st = halo + (hb * NV + v) * kHaloMax;
     const uint16_t* nb = h.nbr_loc + tile * (int64_t)SL * kTile + lane;
     const int64_t c = tile * kTile + lane;  // may be a pad lane of the last tile
-    const float2 u0s = a.Us[(int64_t)v * a.n_pad + (c < a.n_cell ? c : 0)];
     auto dif = [&](int idx) -> Acc {
       const float2 q = st[idx];
       if constexpr (kDF) {
@@ -1729,11 +1788,12 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
         for (int k = 0; k < kSmallK; ++k)
 #pragma unroll
           for (int l = 0; l < kSmallM; ++l) as[k][l] = df_norm(as[k][l]);
-        df_finish<M, NQ, NV, kExt>(a, ev, c, v, acc, as);
+        df_finish<M, NQ, NV, kExt>(a, ev, c, v, acc, as, nullptr, present);
       } else {
         plain_finish<M, NQ, NV, float, DFTable, kExt>(a, ev, c, v, 0.0, u0s, acc, as,
                                                       kStage ? ostg + lane * (kPer + 1) + v
-                                                             : nullptr);
+                                                             : nullptr,
+                                                      present);
       }
     }
     if constexpr (kStage) {
@@ -2016,7 +2076,8 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
     }
     return;
   }
-  // ---- consumers
+  // ---- consumers (the halo pipeline of recon_tma_kernel measured slower
+  // here: this kernel is at its register limit)
   const int v = warp, tid = threadIdx.x;
   auto prefetch = [&](int64_t tile, int hb) {
     const int h0 = h.off[tile], H = h.off[tile + 1] - h0;
