@@ -184,6 +184,22 @@ int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p);
  * [n_cell][3][12] (-1 for a directional stencil that could not be filled). */
 int teno_get_stencils(teno_ctx* ctx, int32_t* large, int32_t* small);
 
+/* Slot assignment used by teno_precompute_stencils for the large stencils of
+ * every 32-cell tile (the adjoint adds each lane's stencil contributions to
+ * the tile's halo slot by slot; with no cell in two lanes' same slot every
+ * slot takes one round).  members host [n_lanes][n_slots]: the stencil
+ * members (cell ids) of each lane, distinct within a lane.  slot_of host
+ * [n_lanes][n_slots] receives the slot of each member: a proper edge
+ * colouring of the bipartite (lane, member) graph with n_slots colours,
+ * which exists exactly when no cell is a member of more than n_slots lanes
+ * (Konig's edge-colouring theorem).  Returns 1 when coloured, 0 when some
+ * cell is a member of more than n_slots lanes (slot_of untouched; the
+ * precompute then keeps the stencil-search order), TENO_EINVAL for n_lanes
+ * < 0, n_slots < 1, null arrays or a lane with a repeated member.  Needs no
+ * context and no GPU. */
+int teno_colour_slots(int32_t n_lanes, int32_t n_slots, const int32_t* members,
+                      int32_t* slot_of);
+
 /* Sizes: *n_cell, *n_var, *m (unknowns), *n_s (large-stencil size). */
 int teno_get_sizes(teno_ctx* ctx, int64_t* n_cell, int32_t* n_var, int32_t* m, int32_t* n_s);
 

@@ -676,6 +676,94 @@ int stencil_matrix(const teno_ctx* ctx, const RefData& R, int32_t t, const int32
   return TENO_OK;
 }
 
+// Assigns the ns members of each of nval lanes to the ns slots so that no
+// cell is the member of two lanes in the same slot: a proper edge colouring
+// of the bipartite (lane, member cell) graph with ns colours, built edge by
+// edge; where the two free colours at an edge's ends differ, they are
+// swapped along the alternating path from the cell end (it cannot reach the
+// lane end in a bipartite graph).  Such a colouring exists exactly when no
+// cell is a member of more than ns lanes (Konig's edge-colouring theorem).
+// members [nval][ns] (distinct within a lane); slot_of [nval][ns] receives
+// the slot of each member.  Returns 1 when coloured, 0 when some cell is a
+// member of more than ns lanes (slot_of then untouched), -1 on bad input.
+int colour_slots(int nval, int ns, const int32_t* members, int32_t* slot_of) {
+  if (nval < 0 || ns < 1 || (nval > 0 && (!members || !slot_of))) return -1;
+  std::vector<int32_t> cells(members, members + (size_t)nval * ns);
+  std::sort(cells.begin(), cells.end());
+  cells.erase(std::unique(cells.begin(), cells.end()), cells.end());
+  const int nr = (int)cells.size();
+  std::vector<int32_t> eR((size_t)nval * ns), deg(nr, 0);
+  int dmax = 0;
+  for (int ln = 0; ln < nval; ++ln)
+    for (int s = 0; s < ns; ++s) {
+      const int r = (int)(std::lower_bound(cells.begin(), cells.end(),
+                                           members[(size_t)ln * ns + s]) -
+                          cells.begin());
+      eR[(size_t)ln * ns + s] = r;
+      dmax = std::max(dmax, ++deg[r]);
+    }
+  for (int ln = 0; ln < nval; ++ln)  // members of a lane must be distinct
+    for (int s = 0; s < ns; ++s)
+      for (int s2 = 0; s2 < s; ++s2)
+        if (eR[(size_t)ln * ns + s] == eR[(size_t)ln * ns + s2]) return -1;
+  if (dmax > ns) return 0;
+  std::vector<int32_t> colL((size_t)nval * ns, -1);  // [lane][colour] -> member index
+  std::vector<int32_t> colR((size_t)nr * ns, -1);    // [member][colour] -> lane
+  std::vector<int32_t> pl, pr, pc;
+  for (int ln = 0; ln < nval; ++ln)
+    for (int s = 0; s < ns; ++s) {
+      const int w = eR[(size_t)ln * ns + s];
+      int a = 0, b = 0;
+      while (colL[(size_t)ln * ns + a] >= 0) ++a;
+      while (colR[(size_t)w * ns + b] >= 0) ++b;
+      int c = a;
+      if (colR[(size_t)w * ns + a] >= 0) {
+        if (colL[(size_t)ln * ns + b] < 0) {
+          c = b;
+        } else {
+          pl.clear(), pr.clear(), pc.clear();
+          int r = w, col = a;
+          while (true) {
+            const int l = colR[(size_t)r * ns + col];
+            if (l < 0) break;
+            pl.push_back(l), pr.push_back(r), pc.push_back(col);
+            const int col2 = col == a ? b : a;
+            const int r2 = colL[(size_t)l * ns + col2];
+            if (r2 < 0) break;
+            pl.push_back(l), pr.push_back(r2), pc.push_back(col2);
+            r = r2;
+          }
+          for (size_t i = 0; i < pl.size(); ++i) {
+            colL[(size_t)pl[i] * ns + pc[i]] = -1;
+            colR[(size_t)pr[i] * ns + pc[i]] = -1;
+          }
+          for (size_t i = 0; i < pl.size(); ++i) {
+            const int o = pc[i] == a ? b : a;
+            colL[(size_t)pl[i] * ns + o] = pr[i];
+            colR[(size_t)pr[i] * ns + o] = pl[i];
+          }
+        }
+      }
+      colL[(size_t)ln * ns + c] = w;
+      colR[(size_t)w * ns + c] = ln;
+    }
+  // the colouring is proper: every lane has one member per colour and the
+  // two tables agree
+  for (int ln = 0; ln < nval; ++ln)
+    for (int c = 0; c < ns; ++c) {
+      const int w = colL[(size_t)ln * ns + c];
+      if (w < 0 || colR[(size_t)w * ns + c] != ln) return -1;
+    }
+  for (int ln = 0; ln < nval; ++ln)
+    for (int s = 0; s < ns; ++s) {
+      const int w = eR[(size_t)ln * ns + s];
+      int c = 0;
+      while (colL[(size_t)ln * ns + c] != w) ++c;
+      slot_of[(size_t)ln * ns + s] = c;
+    }
+  return 1;
+}
+
 int run_precompute(teno_ctx* ctx) {
   const teno_params& p = ctx->prm;
   RefData R;
@@ -807,89 +895,21 @@ int run_precompute(teno_ctx* ctx) {
     const size_t E32s = wform ? (size_t)E32 : 0, EWs = wform ? (size_t)EW : 0;
 #pragma omp parallel
     {
-      std::vector<int32_t> cells, eR, deg, colL, colR, perm;
-      std::vector<int32_t> pl, pr, pc;
+      std::vector<int32_t> members, slot_of, perm;
       std::vector<unsigned char> tmp;
 #pragma omp for schedule(dynamic, 64)
       for (int64_t t = 0; t < ntile; ++t) {
         const int nval = (int)std::min<int64_t>(kTile, nc - t * kTile);
-        auto member = [&](int ln, int s) { return nbr[((size_t)t * SL + s) * kTile + ln]; };
-        cells.clear();
+        members.resize((size_t)nval * ns);
+        slot_of.resize((size_t)nval * ns);
         for (int ln = 0; ln < nval; ++ln)
-          for (int s = 0; s < ns; ++s) cells.push_back(member(ln, s));
-        std::sort(cells.begin(), cells.end());
-        cells.erase(std::unique(cells.begin(), cells.end()), cells.end());
-        const int nr = (int)cells.size();
-        eR.assign((size_t)nval * ns, 0);
-        deg.assign(nr, 0);
-        int dmax = 0;
-        for (int ln = 0; ln < nval; ++ln)
-          for (int s = 0; s < ns; ++s) {
-            const int r = (int)(std::lower_bound(cells.begin(), cells.end(), member(ln, s)) -
-                                cells.begin());
-            eR[(size_t)ln * ns + s] = r;
-            dmax = std::max(dmax, ++deg[r]);
-          }
-        if (dmax > ns) continue;
-        colL.assign((size_t)nval * ns, -1);  // [lane][colour] -> member index
-        colR.assign((size_t)nr * ns, -1);    // [member][colour] -> lane
-        for (int ln = 0; ln < nval; ++ln)
-          for (int s = 0; s < ns; ++s) {
-            const int w = eR[(size_t)ln * ns + s];
-            int a = 0, b = 0;
-            while (colL[(size_t)ln * ns + a] >= 0) ++a;
-            while (colR[(size_t)w * ns + b] >= 0) ++b;
-            int c = a;
-            if (colR[(size_t)w * ns + a] >= 0) {
-              if (colL[(size_t)ln * ns + b] < 0) {
-                c = b;
-              } else {
-                // swap a and b along the alternating path from w (it cannot
-                // reach lane ln in a bipartite graph)
-                pl.clear(), pr.clear(), pc.clear();
-                int r = w, col = a;
-                while (true) {
-                  const int l = colR[(size_t)r * ns + col];
-                  if (l < 0) break;
-                  pl.push_back(l), pr.push_back(r), pc.push_back(col);
-                  const int col2 = col == a ? b : a;
-                  const int r2 = colL[(size_t)l * ns + col2];
-                  if (r2 < 0) break;
-                  pl.push_back(l), pr.push_back(r2), pc.push_back(col2);
-                  r = r2;
-                }
-                for (size_t i = 0; i < pl.size(); ++i) {
-                  colL[(size_t)pl[i] * ns + pc[i]] = -1;
-                  colR[(size_t)pr[i] * ns + pc[i]] = -1;
-                }
-                for (size_t i = 0; i < pl.size(); ++i) {
-                  const int o = pc[i] == a ? b : a;
-                  colL[(size_t)pl[i] * ns + o] = pr[i];
-                  colR[(size_t)pr[i] * ns + o] = pl[i];
-                }
-              }
-            }
-            colL[(size_t)ln * ns + c] = w;
-            colR[(size_t)w * ns + c] = ln;
-          }
-        // the colouring is proper: every lane has one member per colour and
-        // the two tables agree (else the tile keeps its order)
-        bool proper = true;
-        for (int ln = 0; ln < nval && proper; ++ln)
-          for (int c = 0; c < ns && proper; ++c) {
-            const int w = colL[(size_t)ln * ns + c];
-            proper = w >= 0 && colR[(size_t)w * ns + c] == ln;
-          }
-        if (!proper) continue;
+          for (int s = 0; s < ns; ++s)
+            members[(size_t)ln * ns + s] = nbr[((size_t)t * SL + s) * kTile + ln];
+        if (colour_slots(nval, ns, members.data(), slot_of.data()) != 1) continue;
         // move every lane's slot s to its colour
         perm.assign(ns, 0);
         for (int ln = 0; ln < nval; ++ln) {
-          for (int s = 0; s < ns; ++s) {
-            const int w = eR[(size_t)ln * ns + s];
-            int c = 0;
-            while (colL[(size_t)ln * ns + c] != w) ++c;
-            perm[s] = c;
-          }
+          for (int s = 0; s < ns; ++s) perm[s] = slot_of[(size_t)ln * ns + s];
           // entries s * per_slot + l of lane ln in a [tile][entry][lane] array
           auto permute = [&](auto* base, size_t stride_e, size_t per_slot) {
             using T = std::remove_pointer_t<decltype(base)>;
@@ -1558,6 +1578,12 @@ int teno_get_sizes(teno_ctx* ctx, int64_t* n_cell, int32_t* n_var, int32_t* m, i
   if (m) *m = ctx->m;
   if (n_s) *n_s = ctx->ns;
   return TENO_OK;
+}
+
+int teno_colour_slots(int32_t n_lanes, int32_t n_slots, const int32_t* members,
+                      int32_t* slot_of) {
+  const int r = colour_slots(n_lanes, n_slots, members, slot_of);
+  return r < 0 ? TENO_EINVAL : r;
 }
 
 int teno_set_state(teno_ctx* ctx, const double* U, int on_device) {

@@ -87,6 +87,7 @@ def lib(build_if_missing: bool = False):
         "teno_cfl_dt_noalloc": (C.c_int, [C.c_int, _vp, C.c_int32, C.c_int64, _vp, _vp,
                                           C.c_double, C.c_double, C.c_double, C.c_double, _vp,
                                           C.c_int]),
+        "teno_colour_slots": (C.c_int, [C.c_int32, C.c_int32, _vp, _vp]),
         "teno_profile": (C.c_int, [_vp, C.c_int]),
         "teno_profile_read": (C.c_int, [_vp, _vp, _vp]),
     }
@@ -153,6 +154,21 @@ def cfl_dt_noalloc(U, cell_len, dt_out=None, gamma: float = 1.4, adv=(1.0, 1.0),
     if rc != 0:
         raise TenoError(rc, "teno_cfl_dt_noalloc failed")
     return None
+
+
+def colour_slots(members):
+    """teno_colour_slots: slot of every stencil member so that no cell sits
+    in the same slot of two lanes.  members: int array [n_lanes][n_slots]
+    (distinct within a row).  Returns the int32 array of slots, or None when
+    some cell is a member of more than n_slots lanes."""
+    m = np.ascontiguousarray(members, dtype=np.int32)
+    if m.ndim != 2:
+        raise ValueError("members must be [n_lanes][n_slots]")
+    out = np.empty_like(m)
+    rc = lib().teno_colour_slots(m.shape[0], m.shape[1], m.ctypes.data, out.ctypes.data)
+    if rc < 0:
+        raise TenoError(rc, "teno_colour_slots: invalid members")
+    return out if rc == 1 else None
 
 
 SCHEME_TENO, SCHEME_CWENO = 0, 1
