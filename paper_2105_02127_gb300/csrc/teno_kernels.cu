@@ -3220,6 +3220,19 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), 3)
   int hb = 0;
   bool dead = false;
   if ((int64_t)blockIdx.x < n_tiles) prefetch(blockIdx.x, 0);
+  // the halo offsets and the selection byte of a tile, loaded a tile ahead
+  auto pre = [&](int64_t tile, int& h0, int& H, uint8_t& sl) {
+    h0 = 0, H = 0, sl = 0;
+    if (tile < n_tiles) {
+      h0 = h.off[tile];
+      H = h.off[tile + 1] - h0;
+      const int64_t cc = tile * kTile + lane;
+      if (cc < n_cell) sl = sel_in[(int64_t)v * n_pad + cc];
+    }
+  };
+  int h0n, Hn;
+  uint8_t seln;
+  pre(blockIdx.x, h0n, Hn, seln);
   for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, hb ^= 1) {
     consumer_sync();  // the previous tile's accumulator, flags and Uq_bar stage are released
     const int64_t nxt = tile + gridDim.x;
@@ -3227,11 +3240,12 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), 3)
       prefetch(nxt, hb ^ 1);
     else
       cp_async_commit();
-    const int h0 = h.off[tile], H = h.off[tile + 1] - h0;
+    const int h0 = h0n, H = Hn;
+    const uint8_t sel = seln;
+    pre(nxt, h0n, Hn, seln);
     for (int i = lane; i < H; i += kTile) hrow[i] = make_float2(0.f, 0.f);
     const int64_t c = tile * kTile + lane;
     const bool valid = c < n_cell;
-    const uint8_t sel = valid ? sel_in[(int64_t)v * n_pad + c] : (uint8_t)0;
     const bool vs = __any_sync(0xffffffffu, valid && vjp_needs_small(sel));
     if (lane == 0) need[v] = vs;
     cp_async_wait<1>();
