@@ -45,7 +45,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # captures summarised in profiles/ (64,800-cell vortex mesh; "adjoint_vjp":
 # the tiled reconstruction VJP); a launch's traffic is this times the cells
 # it processes.  Absent when the kernel changed since the capture.
-NCU_TRAFFIC_PER_CELL = {("fp64", 5): 5228.4, ("fp32_mixed", 5): 2668.1, ("fp64_native", 5): 5213.7}
+NCU_TRAFFIC_PER_CELL = {("fp64", 5): 5228.4, ("fp32_mixed", 5): 2668.1, ("fp64_native", 5): 5213.7,
+                        ("adjoint_vjp", 5): 2601.9}
 
 
 def ncu_traffic(precision, order, n_cell):
