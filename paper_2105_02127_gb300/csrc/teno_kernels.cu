@@ -3039,10 +3039,10 @@ __global__ void __launch_bounds__(128) recon_vjp_df_kernel(const float2* __restr
 // equal positions in lane order, by ranks the host stores next to the
 // positions; slots in stencil order: deterministic sums).  The host assigns
 // the large-stencil members to slots so that the lanes of a tile do not
-// share a cell within a slot, and these slots take one round.  At the end of the tile the
-// accumulator is written as one pair per (halo entry, variable), so the
-// reverse gather reads the few halo entries that hold a cell instead of
-// every stencil slot that holds it.  The tile's Uq_bar block is prefetched
+// share a cell within a slot, and these slots take one round.  At the end of
+// the tile the accumulator is written as one pair per (halo entry,
+// variable), so the reverse gather reads the few halo entries that hold a
+// cell instead of every stencil slot that holds it.  The tile's Uq_bar block is prefetched
 // with cp.async one tile ahead.
 constexpr int kRingV = 4;
 constexpr int kUbStride = 38;  // doubles per cell in the Uq_bar stage (16-byte rows)
@@ -3094,7 +3094,8 @@ struct VjpPlan {
   }
 };
 
-// some valid (cell, variable) of the tile keeps a directional stencil
+// the (cell, variable) of this selection byte keeps directional stencils:
+// its large stencil is cut and at least one directional stencil is kept
 __device__ __forceinline__ bool vjp_needs_small(uint8_t sel) {
   return !(sel & 8) && (sel & 7);
 }
