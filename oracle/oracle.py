@@ -77,13 +77,16 @@ class Oracle:
     def __init__(self, mesh, order: int = 3, n_var: int = 1, flux: int = FLUX_UPWIND,
                  linear: bool = False, ct: float = 1e-6, eps: float = 1e-12, gamma: float = 1.4,
                  adv=(1.0, 1.0), nq: int | None = None, rotation=None, scheme: str = "teno",
-                 cweno_dk: float = 1e4, charvar: bool = False):
+                 cweno_dk: float = 1e4, charvar: bool = False, positivity: bool = False):
         """rotation: (x_c, y_c, omega) or (x_c, y_c, omega, r1, r2) for scalar
         advection by the rigid rotation v = omega phi(r) (-(y - y_c), x - x_c)
         (the solid-body case of Sec. 5 is (0.5, 0.5, 1.0)), phi a smoothstep
         taper from 1 at r1 to 0 at r2 (none when omitted); otherwise the
         constant velocity adv.  charvar: Euler reconstruction in characteristic
-        variables per face (TENO only)."""
+        variables per face (TENO only).  positivity: Euler, scale each cell's
+        reconstruction towards its average so that density and pressure stay
+        positive at its face Gauss points (Zhang and Shu's scaling; not in the
+        paper; the adjoint entry points refuse it)."""
         self.mesh = mesh
         self.order, self.n_var = order, n_var
         self.m = n_unknowns(order)
@@ -99,7 +102,7 @@ class Oracle:
         if scheme not in ("teno", "cweno"):
             raise ValueError("scheme must be 'teno' or 'cweno'")
         iopt = np.array([order, self.nq, n_var, flux, int(linear), int(rotation is not None),
-                         int(scheme == "cweno"), int(charvar)], dtype=np.int32)
+                         int(scheme == "cweno"), int(charvar), int(positivity)], dtype=np.int32)
         dopt = np.array([ct, eps, gamma, adv[0], adv[1], rot[0], rot[1], rot[2], rot[3], rot[4],
                          cweno_dk], dtype=np.float64)
         st = C.c_int32(0)

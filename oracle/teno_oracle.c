@@ -175,6 +175,7 @@ typedef struct {
   double ct, eps, gam, adv[2], time;
   int scheme;     /* 0 TENO, 1 CWENO (the comparison scheme of Sec. 2.3) */
   int charvar;    /* Euler: reconstruct characteristic variables per face */
+  int pp;         /* Euler: positivity scaling of the reconstruction (not in the paper) */
   double cw_dk;   /* CWENO d'_K (d_K = 1 - 1/d'_K) */
   int field;      /* scalar advection velocity: 0 constant adv, 1 rigid rotation */
   double rot[5];  /* rotation centre (x, y), angular velocity omega, taper radii r1 < r2 */
@@ -794,6 +795,8 @@ static void char_faces(const omesh* M, int64_t t, const double* U, recon_t* out)
   out->charf = 1;
 }
 
+static void pp_scale(const omesh* M, int64_t t, const double* U, recon_t* R);
+
 static void reconstruct(const omesh* M, int64_t t, const double* U, const unsigned char* sel_in,
                         recon_t* out) {
   const int32_t* st = M->st + (int64_t)ST_TOTAL * t;
@@ -917,6 +920,7 @@ static void reconstruct(const omesh* M, int64_t t, const double* U, const unsign
   }
   out->charf = 0;
   if (M->charvar && M->nvar == 4 && M->scheme == 0) char_faces(M, t, U, out);
+  if (M->pp) pp_scale(M, t, U, out);
 }
 
 /* value of the reconstruction of cell t at physical point (x, y) */
@@ -939,6 +943,55 @@ static void eval_point(const omesh* M, int64_t t, const double* U, const recon_t
     for (int l = 0; l < M->m; ++l)
       s += cf[l] * (ipow(xi[0], M->ex[l][0]) * ipow(xi[1], M->ex[l][1]) - M->mean0[l]);
     val[v] = s;
+  }
+}
+
+/* Positivity scaling of a cell's reconstruction (an option, off by default;
+ * the paper states no positivity treatment).  The scaling limiter of Zhang
+ * and Shu: the polynomial's deviation from the cell average is multiplied by
+ * the largest theta <= 1 that keeps the density, then the pressure, at least
+ * eps = min(1e-13, its cell-average value) at every face Gauss point of the
+ * cell.  The cell average is unchanged (the basis has zero mean).  Density:
+ * theta = (rho_0 - eps) / (rho_0 - rho_q) where rho_q < eps; pressure,
+ * concave in the state along the segment from the average: bisection on the
+ * segment (60 halvings).  Conservative variables only. */
+static double pp_press(double g, const double* W) {
+  return (g - 1.0) * (W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]) / W[0]);
+}
+static void pp_scale(const omesh* M, int64_t t, const double* U, recon_t* R) {
+  if (M->nvar != 4 || R->charf) return;
+  double U0[4];
+  for (int v = 0; v < 4; ++v) U0[v] = U[(int64_t)v * M->nc + t];
+  const double er = fmin(1e-13, U0[0]), ep = fmin(1e-13, pp_press(M->gam, U0));
+  const double* P = M->P + 6 * t;
+  for (int pass = 0; pass < 2; ++pass) {  /* 0: density, 1: pressure */
+    double th = 1.0;
+    for (int e = 0; e < 3; ++e) {
+      const int e1 = (e + 1) % 3;
+      const double dx = P[2 * e1] - P[2 * e], dy = P[2 * e1 + 1] - P[2 * e + 1];
+      for (int k = 0; k < M->nq; ++k) {
+        double Uq[4];
+        eval_point(M, t, U, R, e, P[2 * e] + M->gt[k] * dx, P[2 * e + 1] + M->gt[k] * dy, Uq);
+        if (pass == 0) {
+          if (Uq[0] < er) th = fmin(th, (U0[0] - er) / (U0[0] - Uq[0]));
+        } else if (!(pp_press(M->gam, Uq) >= ep)) {
+          double lo = 0.0, hi = 1.0;
+          for (int it = 0; it < 60; ++it) {
+            const double s = 0.5 * (lo + hi);
+            double W[4];
+            for (int v = 0; v < 4; ++v) W[v] = U0[v] + s * (Uq[v] - U0[v]);
+            if (W[0] > 0.0 && pp_press(M->gam, W) >= ep)
+              lo = s;
+            else
+              hi = s;
+          }
+          th = fmin(th, lo);
+        }
+      }
+    }
+    if (th < 1.0)
+      for (int v = 0; v < 4; ++v)
+        for (int l = 0; l < M->m; ++l) R->coef[v][l] *= th;
   }
 }
 
@@ -1291,6 +1344,7 @@ void* oracle_new(int64_t nv, const double* xy, int64_t nc, const int32_t* tri, i
   M->rot[4] = dopt[9];
   M->scheme = iopt[6];
   M->charvar = iopt[7];
+  M->pp = iopt[8];
   M->cw_dk = dopt[10];
   M->r = M->order - 1;
   M->m = (M->r + 1) * (M->r + 2) / 2 - 1;
@@ -1634,7 +1688,8 @@ int oracle_rk3_step(void* h, double* U, double time, double dt) {
  * given by sel_in), flux branches frozen at the forward states */
 int oracle_residual_vjp(void* h, const double* U, double time, const double* w, double* vout,
                         const uint8_t* sel_in) {
-  if (((omesh*)h)->charvar || ((omesh*)h)->scheme) return E_INVAL; /* TENO, conservative variables */
+  if (((omesh*)h)->charvar || ((omesh*)h)->scheme || ((omesh*)h)->pp)
+    return E_INVAL; /* TENO in conservative variables, no positivity scaling */
   omesh* M = (omesh*)h;
   M->time = time;
   int rc = oracle_prepare(h, 0, NULL);
@@ -1766,7 +1821,8 @@ int oracle_residual_vjp(void* h, const double* U, double time, const double* w, 
  * lam_np1, selection frozen at each stage's state (sel1..3 optional) */
 int oracle_rk3_vjp(void* h, const double* Un, double time, double dt, const double* lam_np1,
                    double* lam_n) {
-  if (((omesh*)h)->charvar || ((omesh*)h)->scheme) return E_INVAL; /* TENO, conservative variables */
+  if (((omesh*)h)->charvar || ((omesh*)h)->scheme || ((omesh*)h)->pp)
+    return E_INVAL; /* TENO in conservative variables, no positivity scaling */
   omesh* M = (omesh*)h;
   int64_t N = M->nc * M->nvar;
   double* R = (double*)malloc(sizeof(double) * N);

@@ -818,3 +818,77 @@ def test_residual_brute_force_on_jump(oracle_mod):
     assert (sel != 8).mean() > 0.2
     Rb = _brute_residual(mesh, U, 3)
     np.testing.assert_allclose(R[0], Rb, rtol=0, atol=1e-10 * np.abs(Rb).max())
+
+
+# ---------------------------------------------------------------- positivity
+# The positivity scaling (an option outside the paper, Zhang and Shu's
+# limiter) multiplies a cell's polynomial deviation from its average by the
+# largest theta <= 1 that keeps density and pressure positive at its face
+# Gauss points.
+
+def _dmr(oracle_mod, nx, ny, order, flux, positivity):
+    mesh = inputs.jittered_mesh(nx, ny, 4.0, 1.0, seed=1003, periodic=False,
+                                bc_tagger=inputs.dmr_bc_tagger)
+    U = inputs.cell_average(mesh, inputs.dmr_state)
+    return mesh, U, oracle_mod.Oracle(mesh, order=order, n_var=4, flux=flux,
+                                      positivity=positivity)
+
+
+def test_positivity_inactive_on_smooth_states(oracle_mod):
+    """Where every Gauss state is physical theta = 1: the residual is the
+    same bits with and without the option."""
+    mesh = inputs.jittered_mesh(16, 16, 10.0, 10.0, seed=1004)
+    U = inputs.cell_average(mesh, inputs.isentropic_vortex)
+    for order in (3, 5, 6):
+        R0, s0, _ = oracle_mod.Oracle(mesh, order=order, n_var=4, flux=1).residual(U)
+        R1, s1, _ = oracle_mod.Oracle(mesh, order=order, n_var=4, flux=1,
+                                      positivity=True).residual(U)
+        assert np.array_equal(R0, R1) and np.array_equal(s0, s1)
+
+
+def test_positivity_conserves_and_keeps_gauss_states_physical(oracle_mod):
+    """The shock case's first residual: non-finite without the option (the
+    Mach-10 front), finite with it; the scaling keeps each cell's average, so
+    the residual still conserves (the face fluxes sum to the boundary fluxes:
+    here, on a periodic blast state, to zero)."""
+    _, U, o0 = _dmr(oracle_mod, 64, 16, 6, 2, False)
+    _, _, o1 = _dmr(oracle_mod, 64, 16, 6, 2, True)
+    assert not np.isfinite(o0.residual(U, time=0.0)[0]).all()
+    assert np.isfinite(o1.residual(U, time=0.0)[0]).all()
+    # conservation with the option active: a periodic state with a strong jump
+    mesh = inputs.jittered_mesh(16, 16, 10.0, 10.0, seed=1004)
+
+    def f(x, y):
+        inside = (np.abs(x - 5.0) < 2.0) & (np.abs(y - 5.0) < 2.0)
+        rho = np.where(inside, 10.0, 1.0)
+        p = np.where(inside, 300.0, 1.0)
+        return inputs.prim_to_cons(rho, 0.3 * np.ones_like(x), -0.2 * np.ones_like(x), p, 1.4)
+    Ub = inputs.cell_average(mesh, f)
+    # the scaling is active here: without it the residual is non-finite
+    assert not np.isfinite(oracle_mod.Oracle(mesh, order=6, n_var=4, flux=2).residual(Ub)[0]).all()
+    ob = oracle_mod.Oracle(mesh, order=6, n_var=4, flux=2, positivity=True)
+    R, _, _ = ob.residual(Ub)
+    assert np.isfinite(R).all()
+    area, _, _ = ob.geometry()
+    tot = (R * area).sum(axis=1)
+    assert np.abs(tot).max() <= 1e-12 * np.abs(R * area).sum(axis=1).max()
+
+
+def test_positivity_short_shock_run(oracle_mod):
+    """With the option and HLL the shock case stays physical over its first
+    20 SSP-RK3 steps at the CFL step (TENO6, 2,048 cells)."""
+    _, U, o = _dmr(oracle_mod, 64, 16, 6, 1, True)
+    t = 0.0
+    for _ in range(20):
+        dt = o.cfl_dt(U, 0.4)
+        U = o.rk3_step(U, dt, time=t)
+        t += dt
+        rho = U[0]
+        p = 0.4 * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / rho)
+        assert np.isfinite(U).all() and rho.min() > 0 and p.min() > 0
+
+
+def test_positivity_refused_by_adjoint(oracle_mod):
+    mesh, U, o = _dmr(oracle_mod, 16, 8, 3, 1, True)
+    with pytest.raises(oracle_mod.OracleError):
+        o.residual_vjp(U, np.ones_like(U))
