@@ -53,6 +53,8 @@ def lib():
         L.oracle_flux.argtypes = [C.c_void_p, _dp, _dp, C.c_double, C.c_double, C.c_double,
                                   C.c_double, _dp, C.c_void_p, C.c_void_p]
         L.oracle_geometry.argtypes = [C.c_void_p, _dp, _dp, _ip]
+        L.oracle_ghost.argtypes = [C.c_void_p, C.c_int, _dp, C.c_double, C.c_double, C.c_double,
+                                   C.c_double, C.c_double, _dp]
         L.oracle_char_basis.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp, _dp]
         L.oracle_gauss_legendre.argtypes = [C.c_int, _dp, _dp]
     return _lib
@@ -224,6 +226,15 @@ class Oracle:
             return F, JL, JR
         lib().oracle_flux(self._h, UL, UR, nx, ny, x, y, F, None, None)
         return F
+
+    def ghost(self, tag: int, UL, nx: float, ny: float, x: float = 0.0, y: float = 0.0,
+              time: float = 0.0):
+        """boundary ghost state of the shock case (tag 1 wall, 2 inflow, 3
+        outflow, 4 top) at face point (x, y), outward normal (nx, ny), time t"""
+        UL = np.ascontiguousarray(UL, dtype=np.float64)
+        UR = np.empty(self.n_var)
+        lib().oracle_ghost(self._h, tag, UL, nx, ny, x, y, time, UR)
+        return UR
 
     def char_basis(self, W, nx: float, ny: float):
         """left / right eigenvector matrices (4x4) of the Euler flux in

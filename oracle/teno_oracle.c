@@ -37,8 +37,7 @@
  * forward state, has no counterpart in the paper; flux Jacobians come from
  * forward-mode dual numbers.
  *
- * Readings where the paper is silent or garbled (each also listed in the
- * design notes): m = N_k - 1 unknowns and N_s = 2 N_k neighbours excluding
+ * Readings where the paper is silent or garbled: m = N_k - 1 unknowns and N_s = 2 N_k neighbours excluding
  * the target; basis order per degree d: xi^d, eta^d, xi^(d-1) eta, ...,
  * xi eta^(d-1); D^q P sums every multi-index |alpha| = q once; N_q = 2 (third,
  * fourth order) or 3 (fifth, sixth order) Gauss-Legendre points per edge with
@@ -1101,26 +1100,34 @@ static void num_flux(const omesh* M, const double* UL, const double* UR, double 
         Fx[k] = (SR * FL[k] - SL * FR[k] + SL * SR * (WR[k] - WL[k])) / (SR - SL);
     }
   } else {
-    /* HLLC (Toro): contact speed S* and star states */
+    /* HLLC (Toro): contact speed S* and star states.  The star energy is
+     * Toro's f (E/rho + (S* - u)(S* + p / (rho (S - u)))) multiplied out, so
+     * that no term divides by S - u.  S* is undefined when rho_L (S_L - u_L)
+     * = rho_R (S_R - u_R), which happens only when both bounds equal the
+     * particle speeds (zero sound speed on both sides, as at a reflecting
+     * wall whose Gauss state has zero pressure); there the flux is HLL's. */
     double rL = WL[0], uL = WL[1] / rL, vL = WL[2] / rL;
     double rR = WR[0], uR = WR[1] / rR, vR = WR[2] / rR;
     double pL = (g - 1.0) * (WL[3] - 0.5 * rL * (uL * uL + vL * vL));
     double pR = (g - 1.0) * (WR[3] - 0.5 * rR * (uR * uR + vR * vR));
-    double Ss = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) /
-                (rL * (SL - uL) - rR * (SR - uR));
+    double den = rL * (SL - uL) - rR * (SR - uR);
+    double Ss = (pR - pL + rL * uL * (SL - uL) - rR * uR * (SR - uR)) / den;
     if (0.0 <= SL) {
       for (int k = 0; k < 4; ++k) Fx[k] = FL[k];
     } else if (0.0 >= SR) {
       for (int k = 0; k < 4; ++k) Fx[k] = FR[k];
+    } else if (den == 0.0) {
+      for (int k = 0; k < 4; ++k)
+        Fx[k] = (SR * FL[k] - SL * FR[k] + SL * SR * (WR[k] - WL[k])) / (SR - SL);
     } else if (0.0 <= Ss) {
       double f = rL * (SL - uL) / (SL - Ss);
       double Us[4] = {f, f * Ss, f * vL,
-                      f * (WL[3] / rL + (Ss - uL) * (Ss + pL / (rL * (SL - uL))))};
+                      ((SL - uL) * WL[3] + (Ss - uL) * (rL * (SL - uL) * Ss + pL)) / (SL - Ss)};
       for (int k = 0; k < 4; ++k) Fx[k] = FL[k] + SL * (Us[k] - WL[k]);
     } else {
       double f = rR * (SR - uR) / (SR - Ss);
       double Us[4] = {f, f * Ss, f * vR,
-                      f * (WR[3] / rR + (Ss - uR) * (Ss + pR / (rR * (SR - uR))))};
+                      ((SR - uR) * WR[3] + (Ss - uR) * (rR * (SR - uR) * Ss + pR)) / (SR - Ss)};
       for (int k = 0; k < 4; ++k) Fx[k] = FR[k] + SR * (Us[k] - WR[k]);
     }
   }
@@ -1235,20 +1242,27 @@ static void num_flux_d(const omesh* M, const dual* UL, const dual* UR, double nx
     }
   } else {
     dual aL = dmul(rL, dsub(SL, uL)), aR = dmul(rR, dsub(SR, uR));
-    dual Ss = ddiv(dadd(dsub(pR, pL), dsub(dmul(aL, uL), dmul(aR, uR))), dsub(aL, aR));
+    dual dnm = dsub(aL, aR);
+    dual Ss = ddiv(dadd(dsub(pR, pL), dsub(dmul(aL, uL), dmul(aR, uR))), dnm);
     if (0.0 <= SL.v) {
       for (int k = 0; k < 4; ++k) Fx[k] = FL[k];
     } else if (0.0 >= SR.v) {
       for (int k = 0; k < 4; ++k) Fx[k] = FR[k];
+    } else if (dnm.v == 0.0) {
+      for (int k = 0; k < 4; ++k)
+        Fx[k] = ddiv(dadd(dsub(dmul(SR, FL[k]), dmul(SL, FR[k])),
+                          dmul(dmul(SL, SR), dsub(WR[k], WL[k]))),
+                     dsub(SR, SL));
     } else {
       int left = 0.0 <= Ss.v;
       dual r = left ? rL : rR, u = left ? uL : uR, v = left ? vL : vR, p = left ? pL : pR;
       dual S = left ? SL : SR;
       const dual* W = left ? WL : WR;
       const dual* FK = left ? FL : FR;
-      dual f = ddiv(dmul(r, dsub(S, u)), dsub(S, Ss));
-      dual e = dadd(ddiv(W[3], r), dmul(dsub(Ss, u), dadd(Ss, ddiv(p, dmul(r, dsub(S, u))))));
-      dual Us[4] = {f, dmul(f, Ss), dmul(f, v), dmul(f, e)};
+      dual Smu = dsub(S, u), SmS = dsub(S, Ss);
+      dual f = ddiv(dmul(r, Smu), SmS);
+      dual e = ddiv(dadd(dmul(Smu, W[3]), dmul(dsub(Ss, u), dadd(dmul(dmul(r, Smu), Ss), p))), SmS);
+      dual Us[4] = {f, dmul(f, Ss), dmul(f, v), e};
       for (int k = 0; k < 4; ++k) Fx[k] = dadd(FK[k], dmul(S, dsub(Us[k], W[k])));
     }
   }
@@ -1880,6 +1894,17 @@ void oracle_flux(void* h, const double* UL, const double* UR, double nx, double 
   omesh* M = (omesh*)h;
   num_flux(M, UL, UR, nx, ny, x, y, F);
   if (JL && JR) flux_jac(M, UL, UR, nx, ny, x, y, JL, JR);
+}
+
+/* boundary ghost state at face point (x, y) with outward unit normal
+ * (nx, ny) at time t, for pins: UR [nvar] */
+void oracle_ghost(void* h, int tag, const double* UL, double nx, double ny, double x, double y,
+                  double t, double* UR) {
+  omesh* M = (omesh*)h;
+  const double t_saved = M->time;
+  M->time = t;
+  ghost_state(M, tag, UL, nx, ny, x, y, UR);
+  M->time = t_saved;
 }
 
 void oracle_geometry(void* h, double* area, double* cen, int32_t* fnbr) {
