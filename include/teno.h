@@ -125,11 +125,31 @@ typedef struct teno_params {
                         does the projection, selection and evaluation in FP64.  The
                         selection output reports 8; the adjoint entry points take
                         conservative variables only. */
+  int32_t positivity; /* Euler, conservative variables: 1 scales each cell's reconstruction
+                        towards its cell average so that density, then pressure, stay at
+                        least min(1e-13, the average's value) at every face Gauss point
+                        (Zhang and Shu's limiter: the largest such factor <= 1; density by
+                        its closed form, pressure by 60 bisection halvings).  Not in the
+                        paper, which reports its schemes robust on the Mach-10 shock case
+                        (Sec. 5) without stating a positivity treatment; without it that
+                        case produces non-physical Gauss states at the incident front.
+                        Off by default; the adjoint entry points refuse it. */
+  int32_t debug;     /* test support, 0 in production.  Bit 0: the default FP64 Euler
+                        reconstruction (recon_variant 2) takes every cell's cutoff decision
+                        through its pair / FP64 fallback instead of the FP32 screen.  Bit 1:
+                        the consumer warps of the bulk-copy reconstruction kernels wait
+                        for each copy with a bound of zero polls, so the first wait of
+                        every block gives up: the kernel sets the error read by
+                        teno_check_state as TENO_ETIMEOUT, skips its remaining work and
+                        returns once the copies its producer issued have landed (the
+                        results of that call are then undefined).  This exercises the
+                        give-up path of the bounded waits without a copy that never
+                        lands. */
 } teno_params;
 
 /* Fills *p with the defaults above (order 5, n_var 4, HLL, FP64, recon_variant 2,
    cfl 0.4, adv (1, 1), adv_field 0, rotation centre (0.5, 0.5), omega 1, no taper,
-   scheme TENO, cweno_dk 1e4, charvar 0). */
+   scheme TENO, cweno_dk 1e4, charvar 0, positivity 0, debug 0). */
 void teno_default_params(teno_params* p);
 
 /* Create a context on CUDA device `device`, launching on `cuda_stream`
@@ -222,7 +242,8 @@ int teno_residual(teno_ctx* ctx, double* R, uint8_t* sel, int on_device);
 int teno_set_selection_override(teno_ctx* ctx, const uint8_t* sel, int on_device);
 
 /* dt = cfl * min_i (4|V_i| / perimeter_i) / (|v_i| + c_i) of the current
- * state (host result; synchronises). */
+ * state (host result; synchronises).  TENO_ENONPHYS when a cell is
+ * non-physical (rho <= 0, p <= 0 or NaN) or every speed is zero. */
 int teno_cfl_dt(teno_ctx* ctx, double* dt);
 
 /* One SSP-RK3 step (Eq. fv_time_discretization_01) of the current state.
@@ -230,6 +251,14 @@ int teno_cfl_dt(teno_ctx* ctx, double* dt);
  * dt_used (nullable, host) receives the step; passing it (or a failing
  * positivity check, see teno_check_state) synchronises the stream. */
 int teno_rk3_step(teno_ctx* ctx, double dt, double* dt_used);
+
+/* Input state of stage `stage` (1 or 2) of the last SSP-RK3 step
+ * (Eq. fv_time_discretization_01: U^(1) = U^n + dt L(U^n) for stage 1,
+ * U^(2) = 3/4 U^n + 1/4 (U^(1) + dt L(U^(1))) for stage 2), [n_var][n_cell]
+ * user order.  Measurement support: it lets a caller evaluate other
+ * precisions on the exact states a run passed through.  TENO_ESTATE before
+ * the first step; TENO_EINVAL for another stage or a null pointer. */
+int teno_get_stage_state(teno_ctx* ctx, int32_t stage, double* U, int on_device);
 
 /* n_steps SSP-RK3 steps without host synchronisation. */
 int teno_rk3_steps(teno_ctx* ctx, int32_t n_steps, double dt);
@@ -268,6 +297,14 @@ int teno_profile(teno_ctx* ctx, int enable);
  * Synchronises on the recorded events; either pointer may be NULL. */
 int teno_profile_read(teno_ctx* ctx, double* ms, int64_t* launches);
 
+/* Measured rate (flop/s, one FMA = 2 flops) of independent fused multiply-adds
+ * on every SM of `device`: precision 0 FP32, 1 FP64 (measurement support for
+ * roofline fractions; no counterpart in the paper).  Runs about 0.1 s of GPU
+ * work on `cuda_stream` (a cudaStream_t, NULL = legacy default) and
+ * synchronises; restores the calling thread's current device.  Errors:
+ * TENO_EINVAL, TENO_ECUDA. */
+int teno_fma_peak(int device, void* cuda_stream, int precision, double* flops_per_s);
+
 /* Largest n_cell that teno_cfl_dt_noalloc accepts. */
 #define TENO_NOALLOC_MAX_CELLS 8388608
 
@@ -285,18 +322,27 @@ int teno_profile_read(teno_ctx* ctx, double* ms, int64_t* launches);
  *  cell_len  device [n_cell], same cell order as U;
  *  dt        device pointer when dt_on_device != 0 (stream-ordered, not
  *            synchronised), else host pointer (the call synchronises).
+ * A state with a non-physical cell (rho <= 0, p <= 0 or NaN) or with every
+ * speed zero has no CFL step: the host-result call then returns
+ * TENO_ENONPHYS and leaves *dt unchanged, and the device-result call writes
+ * NaN to *dt (teno_cfl_dt returns TENO_ENONPHYS for the same states).
  * The caller owns every buffer.  Partial maxima go to a fixed device array of
  * (TENO_NOALLOC_MAX_CELLS / 2048 + 1) doubles = 32,776 bytes inside the
  * library, which every GPU that loads the library holds until the process
  * exits.  The first call on a device looks up that array's device address
- * with the device current; make that first call before any stream capture.
+ * with the device current and keeps it for the process; make that first call
+ * before any stream capture.  A cudaDeviceReset of that device invalidates the
+ * kept address: do not call this entry point for that device afterwards.
  * Every call shares the array and it keeps the last call's contents (each
  * slot is written before it is read, nothing needs clearing): calls that
  * overlap on the GPU (several streams or host threads) race and must be
- * serialised by the caller.
+ * serialised by the caller.  The calling thread's current device is restored
+ * before the call returns, and a CUDA error left pending by earlier work is
+ * cleared on entry rather than reported as this call's.
  * Errors: TENO_EINVAL (n_var not 1 or 4, n_cell < 1 or above
  * TENO_NOALLOC_MAX_CELLS, a null pointer, cfl <= 0, gamma <= 1 for Euler),
- * TENO_ECUDA.  Calls no cudaMalloc, cudaFree or allocating library routine. */
+ * TENO_ENONPHYS (host result only, see above), TENO_ECUDA.  Calls no
+ * cudaMalloc, cudaFree or allocating library routine. */
 int teno_cfl_dt_noalloc(int device, void* cuda_stream, int32_t n_var, int64_t n_cell,
                         const double* U, const double* cell_len, double gamma, double adv_x,
                         double adv_y, double cfl, double* dt, int dt_on_device);

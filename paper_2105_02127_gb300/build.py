@@ -1,7 +1,8 @@
 """Build libteno.so in-tree (paper_2105_02127_gb300/_build/) for sm_103a.
 
-Three translation units compiled in parallel -- the CUDA kernels and the
-no-allocation CFL entry point with nvcc, the host runtime with g++ (OpenMP) --
+Four translation units compiled in parallel -- the CUDA kernels, the
+no-allocation CFL entry point and the FMA pipe-peak measurement with nvcc,
+the host runtime with g++ (OpenMP) --
 linked by nvcc into one shared library with the C ABI of include/teno.h.
 """
 from __future__ import annotations
@@ -16,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libteno.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["teno_kernels.cu", "teno_noalloc.cu", "teno_host.cpp"]
+SOURCES = ["teno_kernels.cu", "teno_noalloc.cu", "teno_peaks.cu", "teno_host.cpp"]
 HEADERS = [os.path.join(CSRC, "teno_internal.h"), os.path.join(ROOT, "include", "teno.h")]
 
 
@@ -50,15 +51,18 @@ def build(force: bool = False, verbose: bool = False) -> str:
     pid = os.getpid()
     ko = os.path.join(OUT_DIR, f"teno_kernels.{pid}.o")
     no = os.path.join(OUT_DIR, f"teno_noalloc.{pid}.o")
+    po = os.path.join(OUT_DIR, f"teno_peaks.{pid}.o")
     ho = os.path.join(OUT_DIR, f"teno_host.{pid}.o")
     cmd_k = [nvcc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
              "-diag-suppress", "177", "-c", os.path.join(CSRC, "teno_kernels.cu"), "-o", ko]
     cmd_n = [nvcc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
              "-c", os.path.join(CSRC, "teno_noalloc.cu"), "-o", no]
+    cmd_p = [nvcc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
+             "-c", os.path.join(CSRC, "teno_peaks.cu"), "-o", po]
     cmd_h = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-ffp-contract=off",
              "-Wno-maybe-uninitialized", f"-I{inc}", "-c", os.path.join(CSRC, "teno_host.cpp"),
              "-o", ho]
-    cmds = (cmd_k, cmd_n, cmd_h)
+    cmds = (cmd_k, cmd_n, cmd_p, cmd_h)
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT) for c in cmds]
     for p, c in zip(procs, cmds):
         out, _ = p.communicate()
@@ -67,12 +71,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose and out:
             print(out.decode(errors="replace"))
     tmp = LIB + f".tmp{pid}"
-    cmd_l = [nvcc, *ARCH, "-shared", "-o", tmp, ko, no, ho, "-Xcompiler", "-fopenmp"]
+    cmd_l = [nvcc, *ARCH, "-shared", "-o", tmp, ko, no, po, ho, "-Xcompiler", "-fopenmp"]
     r = subprocess.run(cmd_l, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd_l)}\n{r.stdout.decode(errors='replace')}")
     os.replace(tmp, LIB)
-    for f in (ko, no, ho):
+    for f in (ko, no, po, ho):
         try:
             os.remove(f)
         except OSError:

@@ -75,6 +75,7 @@ struct teno_ctx {
   DevBuf b_Usplit;  // FP32 hi/lo split of the state being reconstructed (mixed precision)
   bool override_on = false;
   bool split_ok = false;  // b_Usplit holds split(b_U)
+  bool stages_ok = false; // b_U1, b_U2 hold the stage states of the last RK3 step
   // adjoint
   DevBuf b_rev_off, b_rev_idx, b_dbar, b_uself, b_Uqbar, b_l1, b_l2, b_lamn, b_vtmp, b_selA;
   DevBuf b_Uq_st[2], b_sel_st[2];  // stage 1, 2 reconstructions kept by the adjoint replay
@@ -1041,6 +1042,8 @@ int run_precompute(teno_ctx* ctx) {
   dm.scheme = p.scheme;
   dm.cweno_dk = p.cweno_dk;
   dm.charvar = p.charvar;
+  dm.positivity = p.positivity;
+  dm.debug = p.debug;
   dm.coef_out = nullptr;
   if (p.charvar && ctx->device >= 0) {
     int e4 = dev_alloc(ctx, ctx->b_coef, sizeof(double) * (size_t)npad * 4 * (m + 15));
@@ -1209,6 +1212,7 @@ int stage_flux(teno_ctx* ctx, const double* U, uint8_t* sel_out, double time,
   long pe = prof_begin(ctx, K_RECON);
   CK(launch_recon(ctx->dm, U, Us, uq, sel_out, sel_in, ctx->stream), "recon launch");
   if (ctx->dm.charvar) CK(launch_char_finish(ctx->dm, U, uq, ctx->stream), "char finish launch");
+  if (ctx->dm.positivity) CK(launch_positivity(ctx->dm, U, uq, ctx->stream), "positivity launch");
   prof_end(ctx, pe);
   pe = prof_begin(ctx, K_FLUX);
   CK(launch_face_flux(ctx->dm, uq, ctx->b_K.p, time, ctx->stream), "face flux launch");
@@ -1403,6 +1407,8 @@ void teno_default_params(teno_params* p) {
   p->scheme = 0;
   p->cweno_dk = 1e4;
   p->charvar = 0;
+  p->positivity = 0;
+  p->debug = 0;
   p->cfl = 0.4;
 }
 
@@ -1482,7 +1488,7 @@ int teno_mesh_load(teno_ctx* ctx, int64_t n_vert, const double* xy, int64_t n_ce
   if (period && !(period[0] > 0 && period[1] > 0))
     return fail(ctx, TENO_EINVAL, "mesh_load: non-positive period");
   if (ctx->device >= 0) CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  ctx->mesh_ok = ctx->pre_ok = ctx->state_ok = ctx->adj_ok = false;
+  ctx->mesh_ok = ctx->pre_ok = ctx->state_ok = ctx->adj_ok = ctx->stages_ok = false;
   ctx->override_on = false;
   ctx->has_time_bc = false;
   ctx->nv = n_vert;
@@ -1518,7 +1524,9 @@ int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
                              !std::isfinite(p->adv_cx) || !std::isfinite(p->adv_cy) ||
                              !std::isfinite(p->adv_r1) || !std::isfinite(p->adv_r2))) ||
       p->scheme < 0 || p->scheme > 1 || (p->scheme == 1 && !(p->cweno_dk > 1.0)) ||
-      p->charvar < 0 || p->charvar > 1 || (p->charvar == 1 && (p->n_var != 4 || p->scheme != 0)))
+      p->charvar < 0 || p->charvar > 1 || (p->charvar == 1 && (p->n_var != 4 || p->scheme != 0)) ||
+      p->positivity < 0 || p->positivity > 1 ||
+      (p->positivity == 1 && (p->n_var != 4 || p->charvar != 0)) || p->debug < 0 || p->debug > 3)
     return fail(ctx, TENO_EINVAL, "precompute: bad parameters");
   const int nq_default = p->order <= 4 ? 2 : 3;
   if (p->nq != 0 && p->nq != nq_default)
@@ -1526,7 +1534,7 @@ int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
   if (!ctx->periodic && p->n_var != 4)
     return fail(ctx, TENO_EINVAL, "precompute: boundary conditions need the Euler equations");
   if (ctx->device >= 0) CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  ctx->pre_ok = ctx->state_ok = ctx->adj_ok = false;
+  ctx->pre_ok = ctx->state_ok = ctx->adj_ok = ctx->stages_ok = false;
   ctx->override_on = false;
   ctx->prm = *p;
   ctx->nq = nq_default;
@@ -1595,6 +1603,7 @@ int teno_set_state(teno_ctx* ctx, const double* U, int on_device) {
   if (!on_device) CK(cudaStreamSynchronize(ctx->stream), "sync");
   ctx->state_ok = true;
   ctx->split_ok = false;
+  ctx->stages_ok = false;
   return TENO_OK;
 }
 
@@ -1711,6 +1720,7 @@ static int rk3_once(teno_ctx* ctx, double dt, double* dt_used) {
   if (!rc) rc = rk_stage(ctx, U, U2, U, 1.0 / 3.0, 2.0 / 3.0, dt, maxlam, t + 0.5 * dt, true);
   ctx->split_ok = ctx->prm.precision != TENO_FP64_NATIVE;
   if (rc) return rc;
+  ctx->stages_ok = true;
   if (dt > 0.0) ctx->time += dt;
   if (dt_used) *dt_used = dt;
   return TENO_OK;
@@ -1723,6 +1733,14 @@ int teno_rk3_step(teno_ctx* ctx, double dt, double* dt_used) {
   if (rc) return rc;
   if (dt_used) return teno_check_state(ctx);
   return TENO_OK;
+}
+
+int teno_get_stage_state(teno_ctx* ctx, int32_t stage, double* U, int on_device) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (!U || (stage != 1 && stage != 2)) return fail(ctx, TENO_EINVAL, "get_stage_state: bad args");
+  if (!ctx->stages_ok) return fail(ctx, TENO_ESTATE, "get_stage_state: no RK3 step taken");
+  return to_user(ctx, (const double*)(stage == 1 ? ctx->b_U1.p : ctx->b_U2.p), U, on_device);
 }
 
 int teno_rk3_steps(teno_ctx* ctx, int32_t n_steps, double dt) {
@@ -1752,8 +1770,9 @@ int teno_residual_vjp(teno_ctx* ctx, const double* w, double* v, int on_device) 
   if (!w || !v) return fail(ctx, TENO_EINVAL, "residual_vjp: null pointer");
   if (ctx->prm.precision == TENO_FP32_MIXED)
     return fail(ctx, TENO_EINVAL, "adjoint: FP64 precisions only");
-  if (ctx->prm.scheme != 0 || ctx->prm.charvar != 0)
-    return fail(ctx, TENO_EINVAL, "adjoint: TENO in conservative variables only");
+  if (ctx->prm.scheme != 0 || ctx->prm.charvar != 0 || ctx->prm.positivity != 0)
+    return fail(ctx, TENO_EINVAL,
+                "adjoint: TENO in conservative variables only, without positivity scaling");
   rc = ensure_adjoint(ctx);
   if (rc) return rc;
   rc = to_internal(ctx, w, (double*)ctx->b_l1.p, on_device);
@@ -1771,10 +1790,12 @@ int teno_adjoint_step(teno_ctx* ctx, double dt, const double* lam_np1, double* l
   if (!lam_np1 || !lam_n || !(dt > 0.0)) return fail(ctx, TENO_EINVAL, "adjoint_step: bad args");
   if (ctx->prm.precision == TENO_FP32_MIXED)
     return fail(ctx, TENO_EINVAL, "adjoint: FP64 precisions only");
-  if (ctx->prm.scheme != 0 || ctx->prm.charvar != 0)
-    return fail(ctx, TENO_EINVAL, "adjoint: TENO in conservative variables only");
+  if (ctx->prm.scheme != 0 || ctx->prm.charvar != 0 || ctx->prm.positivity != 0)
+    return fail(ctx, TENO_EINVAL,
+                "adjoint: TENO in conservative variables only, without positivity scaling");
   rc = ensure_adjoint(ctx);
   if (rc) return rc;
+  ctx->stages_ok = false;  // the replay below overwrites the stage buffers
   const int64_t n = (int64_t)ctx->prm.n_var * ctx->npad;
   double* U = (double*)ctx->b_U.p;
   double* U1 = (double*)ctx->b_U1.p;

@@ -61,6 +61,8 @@ struct DeviceMesh {
   double ct = 1e-6, eps = 1e-12, gamma = 1.4, adv_x = 1, adv_y = 1, cfl = 0.4;
   int scheme = 0;                    // 0 TENO, 1 CWENO
   int charvar = 0;                   // Euler TENO in characteristic variables
+  int positivity = 0;                // Euler: positivity scaling of the Gauss-point values
+  int debug = 0;                     // teno_params.debug bits (tests only)
   double* coef_out = nullptr;        // charvar: [n_pad][4][m+15] FP64 coefficients
   double cweno_dk = 1e4;             // CWENO d'_K
   int adv_field = 0;                 // scalar velocity: 0 constant, 1 rigid rotation
@@ -96,6 +98,9 @@ struct DeviceMesh {
 cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us, void* Uq,
                          uint8_t* sel_out, const uint8_t* sel_in, cudaStream_t st);
 cudaError_t launch_split(const DeviceMesh& dm, const double* U, float2* Us, cudaStream_t st);
+// Euler, positivity option: scale each cell's Gauss-point values towards its
+// average (Zhang and Shu) in place
+cudaError_t launch_positivity(const DeviceMesh& dm, const double* U, void* Uq, cudaStream_t st);
 // charvar: projection, per-field selection and Gauss-point values from the
 // coefficients the reconstruction wrote to dm.coef_out
 cudaError_t launch_char_finish(const DeviceMesh& dm, const double* U, void* Uq, cudaStream_t st);

@@ -279,6 +279,13 @@ __device__ __forceinline__ DF vmax(const DF& a, const DF& b) {
   return (a.h > b.h || (a.h == b.h && a.l >= b.l)) ? a : b;
 }
 // c + a*b and conversion to FP64 for every scalar type of the flux kernels
+// exact zero test (pairs: both parts; dual numbers: the value)
+__device__ __forceinline__ bool is_zero(double x) { return x == 0.0; }
+__device__ __forceinline__ bool is_zero(float x) { return x == 0.0f; }
+__device__ __forceinline__ bool is_zero(DF x) { return x.h == 0.0f && x.l == 0.0f; }
+template <int N, typename S>
+__device__ __forceinline__ bool is_zero(const Dual<N, S>& x) { return is_zero(x.v); }
+
 __device__ __forceinline__ double madd(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float madd(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ DF madd(DF a, DF b, DF c) { return a * b + c; }
@@ -375,27 +382,35 @@ __device__ __forceinline__ void euler_riemann(const T* UL, const T* UR, const Ri
   T WL[4] = {rL, mL, rL * utL, EL};
   T WR[4] = {rR, mR, rR * utR, ER};
   T Fx[4];
+  // HLLC's contact speed divides by aL - aR, zero only when both wave-speed
+  // bounds equal the particle speeds (zero sound speed on both sides, e.g. a
+  // wall Gauss state at zero pressure): the flux there is HLL's
+  const T aL = rL * (SL - unL), aR = rR * (SR - unR);
+  const T Dn = aL - aR;
   if (nonneg(SL)) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) Fx[k] = FL[k];
   } else if (nonneg(-SR)) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) Fx[k] = FR[k];
-  } else if (!hllc) {
+  } else if (!hllc || is_zero(Dn)) {
     T inv = one / (SR - SL);
     T sLR = SL * SR;
 #pragma unroll
     for (int k = 0; k < 4; ++k) Fx[k] = (SR * FL[k] - SL * FR[k] + sLR * (WR[k] - WL[k])) * inv;
   } else {
-    // HLLC: contact speed and star state of the side the face lies in
-    T aL = rL * (SL - unL), aR = rR * (SR - unR);
-    T Ss = (pR - pL + aL * unL - aR * unR) / (aL - aR);
+    // HLLC: contact speed and star state of the side the face lies in; the
+    // star energy f (E/r + (Ss - un)(Ss + p / (r (S - un)))) multiplied out,
+    // so that nothing divides by S - un
+    T Ss = (pR - pL + aL * unL - aR * unR) / Dn;
     bool left = nonneg(Ss);
     T r = left ? rL : rR, un = left ? unL : unR, ut = left ? utL : utR;
     T p = left ? pL : pR, S = left ? SL : SR, E = left ? EL : ER;
-    T f = r * (S - un) / (S - Ss);
-    T es = E / r + (Ss - un) * (Ss + p / (r * (S - un)));
-    T Us[4] = {f, f * Ss, f * ut, f * es};
+    T Smu = S - un, inv = one / (S - Ss);
+    T gq = r * Smu;
+    T f = gq * inv;
+    T es = (Smu * E + (Ss - un) * (gq * Ss + p)) * inv;
+    T Us[4] = {f, f * Ss, f * ut, es};
 #pragma unroll
     for (int k = 0; k < 4; ++k) Fx[k] = (left ? FL[k] : FR[k]) + S * (Us[k] - (left ? WL[k] : WR[k]));
   }
@@ -486,13 +501,14 @@ __device__ __forceinline__ void euler_riemann_vjp(const T* UL, const T* UR, cons
   T SLb = zero, SRb = zero;
   T rLb = zero, rRb = zero, unLb = zero, unRb = zero, utLb = zero, utRb = zero;
   T pLb = zero, pRb = zero, ELb = zero, ERb = zero;
+  const bool hll = !hllc || is_zero(rL * (SL - unL) - rR * (SR - unR));
   if (nonneg(SL)) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) FLb[k] = Fxb[k];
   } else if (nonneg(-SR)) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) FRb[k] = Fxb[k];
-  } else if (!hllc) {
+  } else if (hll) {
     const T inv = one / (SR - SL), sLR = SL * SR;
     T invb = zero, sLRb = zero;
 #pragma unroll
@@ -520,11 +536,11 @@ __device__ __forceinline__ void euler_riemann_vjp(const T* UL, const T* UR, cons
     const bool left = nonneg(Ss);
     const T r = left ? rL : rR, un = left ? unL : unR, ut = left ? utL : utR;
     const T p = left ? pL : pR, S = left ? SL : SR, E = left ? EL : ER;
-    const T gq = r * (S - un), den = S - Ss;
+    const T Smu = S - un, gq = r * Smu, den = S - Ss;
     const T f = gq / den;
-    const T h = p / gq;
-    const T es = E / r + (Ss - un) * (Ss + h);
-    const T Us[4] = {f, f * Ss, f * ut, f * es};
+    const T qs = gq * Ss + p;
+    const T es = (Smu * E + (Ss - un) * qs) / den;
+    const T Us[4] = {f, f * Ss, f * ut, es};
     const T* Wsd = left ? WL : WR;
     T Sb = zero, Ssb = zero, rb = zero, unb = zero, utb = zero, pb = zero, Eb = zero;
     T Usb[4];
@@ -543,28 +559,31 @@ __device__ __forceinline__ void euler_riemann_vjp(const T* UL, const T* UR, cons
         WRb[k] = zero - S * Fxb[k];
       }
     }
-    // Us = f * (1, Ss, ut, es)
-    const T fb = Usb[0] + Usb[1] * Ss + Usb[2] * ut + Usb[3] * es;
+    // Us = (f, f Ss, f ut, es)
+    const T fb = Usb[0] + Usb[1] * Ss + Usb[2] * ut;
     Ssb = Ssb + Usb[1] * f;
     utb = utb + Usb[2] * f;
-    const T esb = Usb[3] * f;
-    // es = E / r + (Ss - un) (Ss + h), h = p / gq, gq = r (S - un)
-    Eb = Eb + esb / r;
-    rb = rb - esb * E / (r * r);
-    const T t1 = esb * (Ss + h), t2 = esb * (Ss - un);
-    Ssb = Ssb + t1 + t2;
-    unb = unb - t1;
-    const T hb = t2;
-    pb = pb + hb / gq;
-    T gqb = zero - hb * h / gq;
-    // f = gq / den, den = S - Ss
+    const T esb = Usb[3];
+    // es = (Smu E + (Ss - un) qs) / den, qs = gq Ss + p
+    const T numb = esb / den;
+    T denb = zero - esb * es / den;
+    T Smub = numb * E;
+    Eb = Eb + numb * Smu;
+    Ssb = Ssb + numb * qs;
+    unb = unb - numb * qs;
+    const T qsb = numb * (Ss - un);
+    T gqb = qsb * Ss;
+    Ssb = Ssb + qsb * gq;
+    pb = pb + qsb;
+    // f = gq / den, den = S - Ss, gq = r Smu, Smu = S - un
     gqb = gqb + fb / den;
-    const T denb = zero - fb * f / den;
+    denb = denb - fb * f / den;
     Sb = Sb + denb;
     Ssb = Ssb - denb;
-    rb = rb + gqb * (S - un);
-    Sb = Sb + gqb * r;
-    unb = unb - gqb * r;
+    rb = rb + gqb * Smu;
+    Smub = Smub + gqb * r;
+    Sb = Sb + Smub;
+    unb = unb - Smub;
     // Ss = Nn / Dn, Nn = pR - pL + aL unL - aR unR, Dn = aL - aR
     const T Nb = Ssb / Dn, Dnb = zero - Ssb * Ss / Dn;
     pRb = pRb + Nb;
@@ -733,6 +752,8 @@ struct ReconArgs {
   int scheme;   // 0 TENO, 1 CWENO
   double cw_dK; // CWENO d_K = 1 - 1/d'_K
   double* coef_out;  // characteristic mode: [n_pad][4][m + 15] coefficients out
+  int force_near;       // W form: every cell decides through the pair / FP64 fallback
+  uint32_t wait_polls;  // bulk-copy kernels: consumer mbarrier poll limit (0: give up at once)
 };
 
 // characteristic mode: store the cell's large and directional coefficients of
@@ -1417,8 +1438,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 // as mbar_wait, also watching the block's abort flag: 1 phase complete, 0 gave
 // up, 2 another thread of the block gave up first
 __device__ __forceinline__ int mbar_wait_or_abort(uint64_t* bar, uint32_t parity,
-                                                  const volatile int* abort) {
-  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+                                                  const volatile int* abort,
+                                                  uint32_t limit = kWaitLimit) {
+  for (uint32_t i = 0; i < limit; ++i) {
     if (mbar_test(bar, parity)) return 1;
     if (*abort) return 2;
   }
@@ -1683,6 +1705,10 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
           bulk_g2s(dst + P::kNOff, sn + slot0 * P::kSlotN, bn, &full[b]);
         }
       }
+      // the block must not exit while a copy it issued is in flight (the
+      // consumers skip their waits once a wait has given up)
+      for (int64_t i = g > kRing ? g - kRing : 0; i < g; ++i)
+        mbar_wait(&full[i % kRing], (uint32_t)(i / kRing) & 1);
     }
     return;
   }
@@ -1745,7 +1771,8 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1))
       int64_t off;
       P::stage(j, slot0, nslot, off, bytes, k);
       if (!dead) {
-        const int w = mbar_wait_or_abort(&full[b], (uint32_t)(g / kRing) & 1, abort_flag);
+        const int w =
+            mbar_wait_or_abort(&full[b], (uint32_t)(g / kRing) & 1, abort_flag, a.wait_polls);
         if (w == 0) {
           atomicOr(err, 2);
           *abort_flag = 1;
@@ -2073,6 +2100,9 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
           bulk_g2s(dst + P::kNOff, sn + slot0 * P::kSlotN, bn, &full[b]);
         }
       }
+      // the block must not exit while a copy it issued is in flight
+      for (int64_t i = g > kR ? g - kR : 0; i < g; ++i)
+        mbar_wait(&full[i % kR], (uint32_t)(i / kR) & 1);
     }
     return;
   }
@@ -2153,7 +2183,7 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
           }
         }
         // chi lies within the factor f of its FP32 value under the beta bounds
-        bool near = !(rho < 0.25f);
+        bool near = a.force_near || !(rho < 0.25f);
         const float q = (1.f + rho) / (1.f - fminf(rho, 0.5f));
         const float q2 = q * q;
         const float f = q2 * q2 * q2 * 1.0001f;
@@ -2190,7 +2220,7 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
       int slot0, nslot, k, og, bg, ow, bw;
       P::stage(j, slot0, nslot, k, og, bg, ow, bw);
       if (!dead) {
-        const int w = mbar_wait_or_abort(&full[b], (uint32_t)(g / kR) & 1, abort_flag);
+        const int w = mbar_wait_or_abort(&full[b], (uint32_t)(g / kR) & 1, abort_flag, a.wait_polls);
         if (w == 0) {
           atomicOr(err, 2);
           *abort_flag = 1;
@@ -2373,6 +2403,82 @@ __global__ void __launch_bounds__(128) char_finish_kernel(
 }
 
 // FP32 hi/lo split of a state: hi = fl32(U), lo = fl32(U - hi)
+// Positivity scaling of the reconstruction (Euler; an option, not in the
+// paper, which reports its schemes robust on the Mach-10 shock case without
+// stating a positivity treatment): Zhang and Shu's limiter.  Each cell's
+// Gauss-point states U_q move towards the cell average, U_0 + theta (U_q -
+// U_0), with the largest theta <= 1 that keeps the density, then the
+// pressure, at least eps = min(1e-13, the average's value) at every face
+// Gauss point of the cell.  The reconstruction is linear in its coefficients,
+// so scaling the point values equals scaling the polynomial's deviation from
+// its mean (the average is unchanged).  Density: theta = (rho_0 - eps) /
+// (rho_0 - rho_q) where rho_q < eps; pressure (concave along the segment from
+// the average): 60 bisection halvings of [0, 1].  FP64; one thread per cell.
+__device__ __forceinline__ double pp_pressure(double g, const double* W) {
+  return (g - 1.0) * (W[3] - 0.5 * (W[1] * W[1] + W[2] * W[2]) / W[0]);
+}
+
+template <int NQ, typename TQ>
+__global__ void __launch_bounds__(128) positivity_kernel(const double* __restrict__ U,
+                                                         TQ* __restrict__ Uq, int64_t n_cell,
+                                                         int64_t n_pad, double g) {
+  constexpr int NP = 3 * NQ;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cell) return;
+  double U0[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) U0[v] = U[v * n_pad + c];
+  const double er = fmin(1e-13, U0[0]), ep = fmin(1e-13, pp_pressure(g, U0));
+  TQ* q0 = Uq + c * NP * 4;
+  double W[NP][4];
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) W[q][v] = to_d(q0[q * 4 + v]);
+  bool scaled = false;
+  // pass 0: density
+  double th = 1.0;
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+    if (W[q][0] < er) th = fmin(th, (U0[0] - er) / (U0[0] - W[q][0]));
+  if (th < 1.0) {
+    scaled = true;
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) W[q][v] = U0[v] + th * (W[q][v] - U0[v]);
+  }
+  // pass 1: pressure
+  th = 1.0;
+  for (int q = 0; q < NP; ++q) {
+    if (pp_pressure(g, W[q]) >= ep) continue;
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 60; ++it) {
+      const double sm = 0.5 * (lo + hi);
+      double X[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) X[v] = U0[v] + sm * (W[q][v] - U0[v]);
+      if (X[0] > 0.0 && pp_pressure(g, X) >= ep)
+        lo = sm;
+      else
+        hi = sm;
+    }
+    th = fmin(th, lo);
+  }
+  if (th < 1.0) {
+    scaled = true;
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) W[q][v] = U0[v] + th * (W[q][v] - U0[v]);
+  }
+  if (!scaled) return;
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) q0[q * 4 + v] = from_d<TQ>(W[q][v]);
+}
+
 __global__ void split_kernel(const double* __restrict__ U, float2* __restrict__ Us, int64_t n_cell,
                              int64_t n_pad, int n_var) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2623,6 +2729,9 @@ __global__ void __launch_bounds__(256) max_lambda_kernel(const double* __restric
       const double rho = U[c], u = U[n_pad + c] / rho, v = U[2 * n_pad + c] / rho;
       const double p = (gamma - 1.0) * (U[3 * n_pad + c] - 0.5 * rho * (u * u + v * v));
       s = sqrt(u * u + v * v) + sqrt(gamma * p / rho);
+      // a non-physical cell (rho <= 0, p <= 0 or NaN) makes the maximum infinite, which
+      // the host reports as TENO_ENONPHYS (fmax would drop a NaN speed)
+      if (!(rho > 0.0) || !(p > 0.0)) s = __longlong_as_double(0x7ff0000000000000LL);
     }
     lam = fmax(lam, s / cfl_len[c]);
   }
@@ -3185,6 +3294,9 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), 3)
           bulk_g2s(dst + VP::kNOff, sn + slot0 * VP::kSlotN, bn, &full[b]);
         }
       }
+      // the block must not exit while a copy it issued is in flight
+      for (int64_t i = g > kRingV ? g - kRingV : 0; i < g; ++i)
+        mbar_wait(&full[i % kRingV], (uint32_t)(i / kRingV) & 1);
     }
     return;
   }
@@ -3545,6 +3657,8 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
   a.scheme = dm.scheme;
   a.cw_dK = 1.0 - 1.0 / dm.cweno_dk;
   a.coef_out = dm.charvar ? dm.coef_out : nullptr;
+  a.force_near = dm.debug & 1;
+  a.wait_polls = (dm.debug & 2) ? 0u : kWaitLimit;
   const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
   return dispatch_order(dm.order, [&](auto Mc, auto NSc) -> cudaError_t {
     constexpr int M = decltype(Mc)::value, NS = decltype(NSc)::value;
@@ -3684,6 +3798,26 @@ cudaError_t launch_gather(const DeviceMesh& dm, const void* K, const double* Un,
     if (one) go(I1{}, TypeTag<float>{}); else go(I4{}, TypeTag<float>{});
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_positivity(const DeviceMesh& dm, const double* U, void* Uq,
+                              cudaStream_t st) {
+  if (dm.n_var != 4) return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)((dm.n_cell + 127) / 128);
+  auto go = [&](auto nq, auto tq) -> cudaError_t {
+    constexpr int NQ = decltype(nq)::value;
+    using TQ = typename decltype(tq)::type;
+    positivity_kernel<NQ, TQ><<<grid, 128, 0, st>>>(U, (TQ*)Uq, dm.n_cell, dm.n_pad, dm.gamma);
+    return cudaGetLastError();
+  };
+  auto by_type = [&](auto nq) -> cudaError_t {
+    if (dm.precision == TENO_FP64) return go(nq, TypeTag<DF>{});
+    if (dm.precision == TENO_FP32_MIXED) return go(nq, TypeTag<float>{});
+    return go(nq, TypeTag<double>{});
+  };
+  if (dm.nq == 2) return by_type(std::integral_constant<int, 2>{});
+  if (dm.nq == 3) return by_type(std::integral_constant<int, 3>{});
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_split(const DeviceMesh& dm, const double* U, float2* Us, cudaStream_t st) {

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "../../include/teno.h"
@@ -50,6 +51,9 @@ __global__ void __launch_bounds__(kThreads) cfl_partial(const double* __restrict
       const double rho = U[c], u = U[n + c] / rho, v = U[2 * n + c] / rho;
       const double p = (gamma - 1.0) * (U[3 * n + c] - 0.5 * rho * (u * u + v * v));
       s = sqrt(u * u + v * v) + sqrt(gamma * p / rho);
+      // a non-physical cell (rho <= 0, p <= 0 or NaN) makes the maximum infinite
+      // (fmax would drop a NaN speed)
+      if (!(rho > 0.0) || !(p > 0.0)) s = __longlong_as_double(0x7ff0000000000000LL);
     }
     lam = fmax(lam, s / len[c]);
   }
@@ -80,7 +84,12 @@ __global__ void __launch_bounds__(kThreads) cfl_final(const double* __restrict__
     lam = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
-    if (threadIdx.x == 0) *dt_out = cfl / lam;
+    // no finite positive maximum speed (a non-physical cell, or every speed
+    // zero): the documented NaN sentinel
+    if (threadIdx.x == 0)
+      *dt_out = (lam > 0.0 && lam < __longlong_as_double(0x7ff0000000000000LL))
+                    ? cfl / lam
+                    : __longlong_as_double(0x7ff8000000000000LL);
   }
 }
 
@@ -101,6 +110,20 @@ int scratch_for(int device, double** out) {
   return TENO_OK;
 }
 
+// restores the calling thread's current device on every return
+struct DeviceGuard {
+  int saved = -1;
+  DeviceGuard() {
+    if (cudaGetDevice(&saved) != cudaSuccess) {
+      saved = -1;
+      cudaGetLastError();
+    }
+  }
+  ~DeviceGuard() {
+    if (saved >= 0) cudaSetDevice(saved);
+  }
+};
+
 }  // namespace
 
 extern "C" int teno_cfl_dt_noalloc(int device, void* cuda_stream, int32_t n_var, int64_t n_cell,
@@ -111,6 +134,9 @@ extern "C" int teno_cfl_dt_noalloc(int device, void* cuda_stream, int32_t n_var,
   if (n_cell < 1 || n_cell > TENO_NOALLOC_MAX_CELLS) return TENO_EINVAL;
   if (!U || !cell_len || !dt || !(cfl > 0.0) || (n_var == 4 && !(gamma > 1.0)))
     return TENO_EINVAL;
+  // an error left by earlier, unrelated work is not this call's
+  cudaGetLastError();
+  DeviceGuard guard;
   if (cudaSetDevice(device) != cudaSuccess) {
     cudaGetLastError();
     return TENO_ECUDA;
@@ -126,12 +152,15 @@ extern "C" int teno_cfl_dt_noalloc(int device, void* cuda_stream, int32_t n_var,
   cfl_final<<<1, kThreads, 0, st>>>(scratch, nb, cfl, out);
   if (cudaGetLastError() != cudaSuccess) return TENO_ECUDA;
   if (!dt_on_device) {
-    if (cudaMemcpyAsync(dt, scratch + kMaxBlocks, sizeof(double), cudaMemcpyDeviceToHost, st) !=
+    double h = 0.0;
+    if (cudaMemcpyAsync(&h, scratch + kMaxBlocks, sizeof(double), cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
       cudaGetLastError();
       return TENO_ECUDA;
     }
+    if (!(h > 0.0) || !std::isfinite(h)) return TENO_ENONPHYS;
+    *dt = h;
   }
   return TENO_OK;
 }

@@ -20,6 +20,7 @@ TENO_EMESH, TENO_ESTENCIL, TENO_ENONPHYS, TENO_ETIMEOUT, TENO_ESTATE = -4, -5, -
 FLUX_UPWIND, FLUX_HLL, FLUX_HLLC = 0, 1, 2
 FP64, FP32_MIXED, FP64_NATIVE = 0, 1, 2
 SEL_LARGE = 8
+DEBUG_FORCE_FALLBACK, DEBUG_ZERO_POLL_WAITS = 1, 2
 
 _NAMES = {0: "TENO_OK", -1: "TENO_EINVAL", -2: "TENO_ENOMEM", -3: "TENO_ECUDA", -4: "TENO_EMESH",
           -5: "TENO_ESTENCIL", -6: "TENO_ENONPHYS", -7: "TENO_ETIMEOUT", -8: "TENO_ESTATE"}
@@ -39,7 +40,8 @@ class teno_params(C.Structure):
                 ("adv_x", C.c_double), ("adv_y", C.c_double), ("cfl", C.c_double),
                 ("adv_field", C.c_int32), ("adv_cx", C.c_double), ("adv_cy", C.c_double),
                 ("adv_omega", C.c_double), ("adv_r1", C.c_double), ("adv_r2", C.c_double),
-                ("scheme", C.c_int32), ("cweno_dk", C.c_double), ("charvar", C.c_int32)]
+                ("scheme", C.c_int32), ("cweno_dk", C.c_double), ("charvar", C.c_int32),
+                ("positivity", C.c_int32), ("debug", C.c_int32)]
 
 
 _lib = None
@@ -80,6 +82,7 @@ def lib(build_if_missing: bool = False):
         "teno_cfl_dt": (C.c_int, [_vp, _vp]),
         "teno_rk3_step": (C.c_int, [_vp, C.c_double, _vp]),
         "teno_rk3_steps": (C.c_int, [_vp, C.c_int32, C.c_double]),
+        "teno_get_stage_state": (C.c_int, [_vp, C.c_int32, _vp, C.c_int]),
         "teno_check_state": (C.c_int, [_vp]),
         "teno_residual_vjp": (C.c_int, [_vp, _vp, _vp, C.c_int]),
         "teno_adjoint_step": (C.c_int, [_vp, C.c_double, _vp, _vp, C.c_int]),
@@ -88,6 +91,7 @@ def lib(build_if_missing: bool = False):
                                           C.c_double, C.c_double, C.c_double, C.c_double, _vp,
                                           C.c_int]),
         "teno_colour_slots": (C.c_int, [C.c_int32, C.c_int32, _vp, _vp]),
+        "teno_fma_peak": (C.c_int, [C.c_int, _vp, C.c_int, _vp]),
         "teno_profile": (C.c_int, [_vp, C.c_int]),
         "teno_profile_read": (C.c_int, [_vp, _vp, _vp]),
     }
@@ -154,6 +158,15 @@ def cfl_dt_noalloc(U, cell_len, dt_out=None, gamma: float = 1.4, adv=(1.0, 1.0),
     if rc != 0:
         raise TenoError(rc, "teno_cfl_dt_noalloc failed")
     return None
+
+
+def fma_peak(precision: int = 1, device: int = 0, stream=None) -> float:
+    """Measured FMA rate (flop/s) on every SM: precision 0 FP32, 1 FP64."""
+    out = C.c_double()
+    rc = lib().teno_fma_peak(device, _stream_handle(stream), int(precision), C.addressof(out))
+    if rc != 0:
+        raise TenoError(rc, "teno_fma_peak failed")
+    return out.value
 
 
 def colour_slots(members):
@@ -329,6 +342,14 @@ class Teno:
             return used.value
         self._chk(lib().teno_rk3_step(self._h, float(dt), None))
         return None
+
+    def stage_state(self, stage: int, out=None):
+        """Input state of stage 1 or 2 of the last SSP-RK3 step (U^(1), U^(2))."""
+        if out is None:
+            out = np.empty((self.n_var, self.n_cell))
+        p, dev = _ptr(out)
+        self._chk(lib().teno_get_stage_state(self._h, int(stage), p, dev))
+        return out
 
     def rk3_steps(self, n: int, dt: float = 0.0):
         self._chk(lib().teno_rk3_steps(self._h, int(n), float(dt)))

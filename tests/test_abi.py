@@ -40,6 +40,7 @@ def test_default_params(teno):
     assert (p.order, p.n_var, p.flux, p.precision) == (5, 4, teno.FLUX_HLL, teno.FP64)
     assert p.ct == 1e-6 and p.eps == 1e-12 and p.cfl == 0.4 and p.gamma == 1.4
     assert p.recon_variant == 2 and p.adv_field == 0
+    assert p.positivity == 0 and p.debug == 0 and p.charvar == 0 and p.scheme == 0
     assert (p.adv_cx, p.adv_cy, p.adv_omega) == (0.5, 0.5, 1.0)
     q = teno.default_params(n_var=1, flux=0, rotation=(0.3, 0.6, -2.0))
     assert (q.adv_field, q.adv_cx, q.adv_cy, q.adv_omega) == (1, 0.3, 0.6, -2.0)
@@ -86,11 +87,16 @@ def test_errors(teno):
                dict(order=3, n_var=1, flux=0, ct=-1.0),
                dict(order=3, n_var=4, flux=1, rotation=(0.5, 0.5, 1.0)),
                dict(order=3, n_var=1, flux=0, adv_field=2),
-               dict(order=3, n_var=1, flux=0, rotation=(0.5, float("nan"), 1.0))]:
+               dict(order=3, n_var=1, flux=0, rotation=(0.5, float("nan"), 1.0)),
+               dict(order=3, n_var=1, flux=0, positivity=1),
+               dict(order=3, n_var=4, flux=1, positivity=1, charvar=1),
+               dict(order=3, n_var=4, flux=1, positivity=2),
+               dict(order=3, n_var=4, flux=1, debug=4)]:
         with pytest.raises(teno.TenoError) as e:
             t.precompute_stencils(**kw)
         assert e.value.code == teno.TENO_EINVAL
     t.precompute_stencils(order=3, n_var=1, flux=0, rotation=(0.5, 0.5, 1.0))
+    t.precompute_stencils(order=3, n_var=4, flux=1, positivity=1, debug=3)
     t.precompute_stencils(order=3, n_var=1, flux=0)
     with pytest.raises(teno.TenoError) as e:
         t.set_state(np.zeros((1, mesh.n_cell)))
