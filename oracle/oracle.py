@@ -44,7 +44,7 @@ def lib():
         L.oracle_residual.argtypes = [C.c_void_p, _dp, C.c_double, _dp, C.c_void_p, C.c_void_p,
                                       C.c_void_p]
         L.oracle_residual_cells.argtypes = [C.c_void_p, _dp, C.c_double, C.c_int64, _lp, _dp,
-                                            C.c_void_p, C.c_void_p]
+                                            C.c_void_p, C.c_void_p, C.c_void_p]
         L.oracle_cfl_dt.restype = C.c_double
         L.oracle_cfl_dt.argtypes = [C.c_void_p, _dp, C.c_double]
         L.oracle_rk3_step.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double]
@@ -178,15 +178,18 @@ class Oracle:
                   "residual")
         return R, sel, margin
 
-    def residual_cells(self, U, cells, time: float = 0.0):
+    def residual_cells(self, U, cells, time: float = 0.0, flux_scale: bool = False):
+        """(R, sel, margin) of the listed cells, [n][n_var] each; with
+        flux_scale also sum_faces |K_f| / |V| per cell and variable."""
         U = np.ascontiguousarray(U, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int64)
         R = np.empty((len(cells), self.n_var))
         sel = np.empty((len(cells), self.n_var), dtype=np.uint8)
         margin = np.empty((len(cells), self.n_var))
+        sc = np.empty((len(cells), self.n_var)) if flux_scale else None
         self._chk(lib().oracle_residual_cells(self._h, U, time, len(cells), cells, R, _opt(sel),
-                                              _opt(margin)), "residual_cells")
-        return R, sel, margin
+                                              _opt(margin), _opt(sc)), "residual_cells")
+        return (R, sel, margin, sc) if flux_scale else (R, sel, margin)
 
     def cfl_dt(self, U, cfl: float) -> float:
         U = np.ascontiguousarray(U, dtype=np.float64)

@@ -1597,8 +1597,13 @@ int oracle_residual(void* h, const double* U, double time, double* R, uint8_t* s
 /* residual at selected cells only: R_out [n][nvar]; sel_out [n][nvar] and
  * margin_out [n][nvar] of those cells and of their face neighbours folded in
  * (margin = min over the cell and its neighbours) */
+/* residuals of the listed cells; optional outputs: selection, cutoff margin
+ * (smallest over the cell and its face neighbours) and the flux-sum scale
+ * sum_faces |K_f| / |V| per variable (the size of the terms that cancel in
+ * R, for judging rounding differences) */
 int oracle_residual_cells(void* h, const double* U, double time, int64_t n, const int64_t* cells,
-                          double* R_out, uint8_t* sel_out, double* margin_out) {
+                          double* R_out, uint8_t* sel_out, double* margin_out,
+                          double* scale_out) {
   omesh* M = (omesh*)h;
   M->time = time;
   int nvar = M->nvar;
@@ -1619,7 +1624,7 @@ int oracle_residual_cells(void* h, const double* U, double time, int64_t n, cons
     int64_t c = cells[i];
     recon_t Rc, Rn;
     reconstruct(M, c, U, NULL, &Rc);
-    double acc[4] = {0, 0, 0, 0};
+    double acc[4] = {0, 0, 0, 0}, mag[4] = {0, 0, 0, 0};
     double mg[4];
     for (int v = 0; v < nvar; ++v) mg[v] = Rc.margin[v];
     for (int e = 0; e < 3; ++e) {
@@ -1637,9 +1642,11 @@ int oracle_residual_cells(void* h, const double* U, double time, int64_t n, cons
         face_flux(M, nb, M->fedge[3 * c + e], U, &Rn, &Rc, K, NULL, NULL);
         for (int v = 0; v < nvar; ++v) acc[v] -= K[v];
       }
+      for (int v = 0; v < nvar; ++v) mag[v] += fabs(K[v]);
     }
     for (int v = 0; v < nvar; ++v) {
       R_out[i * nvar + v] = -acc[v] / M->area[c];
+      if (scale_out) scale_out[i * nvar + v] = mag[v] / M->area[c];
       if (sel_out) sel_out[i * nvar + v] = Rc.sel[v];
       if (margin_out) margin_out[i * nvar + v] = mg[v];
     }

@@ -287,3 +287,30 @@ def dmr_bc_tagger(side: str, s: float) -> int:
 def random_directions(seed: int, n_dir: int, n_val: int) -> np.ndarray:
     """n_dir seeded directions of length n_val with entries uniform in [-1,1)."""
     return (2.0 * uniform(seed, 0, n_dir * n_val) - 1.0).reshape(n_dir, n_val)
+
+
+def smooth_directions(seed: int, n_dir: int, mesh: Mesh, n_var: int, n_modes: int = 4,
+                      k_max: int = 2) -> np.ndarray:
+    """n_dir seeded smooth directions [n_dir, n_var, n_cell]: per direction and
+    variable a sum of n_modes periodic Fourier modes a sin(2 pi (kx x / Lx +
+    ky y / Ly) + phi) at the cell centroids, with integer wavenumbers |kx|,
+    |ky| <= k_max (not both zero), amplitudes uniform in [-1, 1) and phases
+    uniform in [0, 2 pi).  Unlike cell-wise random entries they do not roughen
+    a nearly uniform state at the scale of the cells."""
+    c = mesh.unwrapped_vertices().mean(axis=1)
+    Lx, Ly = (mesh.period if mesh.period is not None else (1.0, 1.0))
+    per = n_var * n_modes
+    r = uniform(seed, 0, n_dir * per * 4).reshape(n_dir, n_var, n_modes, 4)
+    out = np.zeros((n_dir, n_var, c.shape[0]))
+    span = 2 * k_max + 1
+    for d in range(n_dir):
+        for v in range(n_var):
+            for m in range(n_modes):
+                kx = int(r[d, v, m, 0] * span) - k_max
+                ky = int(r[d, v, m, 1] * span) - k_max
+                if kx == 0 and ky == 0:
+                    kx = 1
+                a = 2.0 * r[d, v, m, 2] - 1.0
+                phi = 2.0 * np.pi * r[d, v, m, 3]
+                out[d, v] += a * np.sin(2.0 * np.pi * (kx * c[:, 0] / Lx + ky * c[:, 1] / Ly) + phi)
+    return out

@@ -530,15 +530,55 @@ def _dmr(nx, ny):
     return mesh, inputs.cell_average(mesh, inputs.dmr_state)
 
 
+# Positivity scaling holds a Gauss-point pressure at the floor 1e-13 where it
+# binds.  There the pressure E - |m|^2 / (2 rho) is a difference of terms of
+# size ~100 and is only known to about 1e-14: the sound speed, wave speeds
+# and fluxes at such a point are set by rounding.  Cells with a floor Gauss
+# point, and their face neighbours (which share the face fluxes), are held to
+# FLOOR_TOL instead of TOL; the rest of the field to TOL.
+PRESSURE_FLOOR = 1e-10  # a thousand times the limiter's floor
+FLOOR_TOL = 1e-9
+
+
+def positivity_parity(t, o, U, time, precision, gamma=1.4):
+    """Residual of the library against the oracle's positivity option at state
+    U; returns (error away from the floor, error at floor cells, floor cells)."""
+    t.set_time(time)
+    t.set_state(U)
+    R, sel = t.residual(want_sel=True)
+    Ro, selo, mg = o.residual(U, time=time)
+    assert np.isfinite(Ro).all() and np.isfinite(R).all()
+    if precision != 1:
+        assert np.all((sel == selo) | (mg <= MARGIN))
+        if np.any(sel != selo):
+            t.set_selection_override(selo)
+            R, _ = t.residual()
+            t.set_selection_override(None)
+    ev = t.edge_values()  # Gauss-point states after the scaling
+    p = (gamma - 1) * (ev[..., 3] - 0.5 * (ev[..., 1] ** 2 + ev[..., 2] ** 2) / ev[..., 0])
+    floor = p.reshape(len(p), -1).min(axis=1) <= PRESSURE_FLOOR
+    _, _, fnbr = o.geometry()
+    near = floor.copy()
+    for e in range(3):
+        nb = fnbr[:, e]
+        near[nb[(nb >= 0) & floor]] = True
+    scale = np.maximum(np.abs(Ro).max(axis=1), 1e-300)[:, None]
+    err = np.abs(R - Ro) / scale
+    far = float(err[:, ~near].max()) if (~near).any() else 0.0
+    at = float(err[:, near].max()) if near.any() else 0.0
+    t.check_state()
+    return far, at, int(floor.sum())
+
+
 @pytest.mark.parametrize("precision", [0, 2, 1], ids=["fp64", "fp64native", "mixed"])
 @pytest.mark.parametrize("order,flux", [(6, 2), (5, 1), (3, 2)])
 def test_positivity_scaling(T, oracle_mod, order, flux, precision):
     """Positivity scaling of the reconstruction (Zhang and Shu's limiter, an
     option: the paper states no positivity treatment) against the oracle's
     option on the shock case's initial state, where the plain scheme gives
-    non-physical Gauss states along the Mach-10 front (FP64 paths at the
-    1e-11 bar, FP32-mixed within 1e-4), and after five steps of the oracle's
-    own run."""
+    non-physical Gauss states along the Mach-10 front, and after five steps of
+    the oracle's own run.  FP64 paths: TOL away from Gauss points held at the
+    pressure floor, FLOOR_TOL next to them; FP32-mixed within 1e-4."""
     mesh, U = _dmr(64, 16)
     o = oracle_mod.Oracle(mesh, order=order, n_var=4, flux=flux, positivity=True)
     states = [(U, 0.0)]
@@ -551,22 +591,13 @@ def test_positivity_scaling(T, oracle_mod, order, flux, precision):
     t = T.Teno(device=0).load(mesh)
     t.precompute_stencils(order=order, n_var=4, flux=flux, precision=precision, positivity=1)
     for Us, time in states:
-        t.set_time(time)
-        t.set_state(Us)
-        R, sel = t.residual(want_sel=True)
-        Ro, selo, mg = o.residual(Us, time=time)
-        assert np.isfinite(Ro).all() and np.isfinite(R).all()
-        if precision != 1:
-            assert np.all((sel == selo) | (mg <= MARGIN))
-            if np.any(sel != selo):
-                t.set_selection_override(selo)
-                R, _ = t.residual()
-                t.set_selection_override(None)
-        e = rel(R, Ro)
+        far, at, nfloor = positivity_parity(t, o, Us, time, precision)
         print(f"positivity TENO{order} flux {flux} precision {precision} t={time:.4f}: "
-              f"rel err {e:.2e}")
-        assert e <= (TOL if precision != 1 else 1e-4)
-        t.check_state()
+              f"rel err {far:.2e} ({at:.2e} next to {nfloor} floor cells)")
+        if precision == 1:
+            assert max(far, at) <= 1e-4
+        else:
+            assert far <= TOL and at <= FLOOR_TOL
     if precision == 0:
         with pytest.raises(T.TenoError) as ei:
             t.residual_vjp(np.zeros_like(U))

@@ -158,6 +158,7 @@ def test_noalloc_keeps_current_device(env):
 def test_noalloc_rejects_oversize(env):
     torch, teno = env
     U = torch.ones((4, 8), dtype=torch.float64, device="cuda")
+    U[3] = 2.5  # rho = 1, u = v = 1, p = 0.6
     lens = torch.ones(8, dtype=torch.float64, device="cuda")
     import ctypes
     out = ctypes.c_double()
