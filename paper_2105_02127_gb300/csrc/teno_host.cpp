@@ -778,11 +778,13 @@ int run_precompute(teno_ctx* ctx) {
   const int store = p.precision;
   const size_t esz = store == TENO_FP32_MIXED ? sizeof(float) : 8;
   std::vector<unsigned char> ahat((size_t)ntile * E * kTile * esz, 0);
-  // Euler on the pair path with the TMA kernel: FP32 selection matrices with
-  // column sums of |G| (large slots M + 1 floats, directional slots 5 + 1) and
-  // W = Psi' G, the large polynomial's Gauss-point values per unit difference
-  const bool wform = store == TENO_FP64 && p.n_var == 4 && p.recon_variant == 2 && p.scheme == 0 &&
-                     p.charvar == 0;
+  // Euler on the FP64 paths with the bulk-copy kernel (the W form): FP32
+  // selection matrices with column sums of |G| (large slots M + 1 floats,
+  // directional slots 5 + 1) and W = Psi' G, the large polynomial's
+  // Gauss-point values per unit difference, as (hi, lo) pairs on the pair
+  // path and as doubles (the same 8 bytes) on the native path
+  const bool wform = (store == TENO_FP64 || store == TENO_FP64_NATIVE) && p.n_var == 4 &&
+                     p.recon_variant == 2 && p.scheme == 0 && p.charvar == 0;
   const int nq3 = 3 * ctx->nq;
   const int E32 = ns * (m + 1) + kSmallK * kSmallN * (kSmallM + 1), EW = ns * nq3;
   std::vector<float> g32(wform ? (size_t)ntile * E32 * kTile : 0, 0.f);
@@ -836,9 +838,14 @@ int run_precompute(teno_ctx* ctx) {
             for (int q = 0; q < nq3; ++q) {
               double w = 0.0;
               for (int l = 0; l < m; ++l) w += R.psi_t[q * kMaxM + l] * G[l * ns + s];
-              const float hi = (float)w;
-              wq[((size_t)tile * EW + s * nq3 + q) * kTile + lane] =
-                  make_float2(hi, (float)(w - (double)hi));
+              float2& dst = wq[((size_t)tile * EW + s * nq3 + q) * kTile + lane];
+              if (store == TENO_FP64_NATIVE) {
+                static_assert(sizeof(float2) == sizeof(double), "8-byte W entries");
+                memcpy(&dst, &w, sizeof(double));
+              } else {
+                const float hi = (float)w;
+                dst = make_float2(hi, (float)(w - (double)hi));
+              }
             }
           }
         }
@@ -1096,10 +1103,15 @@ int run_precompute(teno_ctx* ctx) {
     dm.eval_df.psi[i] = make_float2(hi, (float)(R.psi_t[i] - (double)hi));
   }
   dm.psi_df = nullptr;
-  if (wform) {
+  dm.psi_d = nullptr;
+  if (wform && store == TENO_FP64) {
     int e2 = upload(ctx, ctx->b_psi, dm.eval_df.psi, sizeof(dm.eval_df.psi));
     if (e2) return e2;
     dm.psi_df = (const float2*)ctx->b_psi.p;
+  } else if (wform) {
+    int e2 = upload(ctx, ctx->b_psi, dm.eval.psi, sizeof(dm.eval.psi));
+    if (e2) return e2;
+    dm.psi_d = (const double*)ctx->b_psi.p;
   }
   for (int k = 0; k < kMaxNq; ++k) {
     dm.gw[k] = k < ctx->nq ? R.gw[k] : 0.0;

@@ -72,12 +72,14 @@ struct DeviceMesh {
   const void* ahat = nullptr;     // double (FP64_NATIVE), float2 (FP64) or float (mixed)
   const int32_t* nbr = nullptr;   // [tile][ns+36][32] internal cell ids
   const uint8_t* smask = nullptr; // [n_pad] bit k: directional stencil k present
-  // Euler on the pair path, recon_variant 2 (else null): FP32 matrices for the
-  // selection, per slot the rows then sum_l |G_ls| ([tile][ns*(m+1) +
-  // 36*6][32]), and W = Psi' G as (hi, lo) pairs ([tile][ns*3*nq][32])
+  // Euler on the FP64 paths, recon_variant 2 (else null): FP32 matrices for
+  // the selection, per slot the rows then sum_l |G_ls| ([tile][ns*(m+1) +
+  // 36*6][32]), and W = Psi' G ([tile][ns*3*nq][32]) as (hi, lo) pairs on the
+  // pair path, as doubles (in the same 8 bytes) on the native path
   const float* g32 = nullptr;
   const float2* wq = nullptr;
-  const float2* psi_df = nullptr;   // device copy of eval_df.psi
+  const float2* psi_df = nullptr;   // device copy of eval_df.psi (pair W form)
+  const double* psi_d = nullptr;    // device copy of eval.psi (native W form)
   // faces
   const int32_t* f_cells = nullptr; // [n_face][2] owner, neighbour (-1 boundary)
   const int8_t* f_edges = nullptr;  // [n_face][2] local edge in owner / neighbour (bc tag if boundary)

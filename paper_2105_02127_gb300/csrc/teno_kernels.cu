@@ -2038,10 +2038,91 @@ __device__ __noinline__ void w_small_values(const float2* A, const uint16_t* nb,
   }
 }
 
-template <int M, int NS, int NQ>
+// The same two rare paths on the FP64 pipe (native FP64 W form): A is the
+// cell's FP64 matrices at its lane, st the tile's halo of FP64 states.
+template <int M, int NS>
+__device__ __noinline__ uint8_t w_select_native(const double* A, const uint16_t* nb,
+                                                const double* st, double u0, int present,
+                                                double ct, double eps) {
+  double al[M];
+#pragma unroll
+  for (int l = 0; l < M; ++l) al[l] = 0.0;
+  for (int s = 0; s < NS; ++s) {
+    const double d = st[nb[s * kTile] & kHaloPosMask] - u0;
+#pragma unroll
+    for (int l = 0; l < M; ++l) al[l] = fma(__ldg(A + (int64_t)(s * M + l) * kTile), d, al[l]);
+  }
+  double beta[kSmallK + 1];
+  {
+    double b = 0.0;
+#pragma unroll
+    for (int l = 0; l < M; ++l) b = fma(al[l], al[l], b);
+    beta[kSmallK] = b;
+  }
+#pragma unroll
+  for (int k = 0; k < kSmallK; ++k) {
+    double as[kSmallM];
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) as[l] = 0.0;
+    if ((present >> k) & 1) {
+      for (int s = 0; s < kSmallN; ++s) {
+        const double d = st[nb[(NS + k * kSmallN + s) * kTile] & kHaloPosMask] - u0;
+        const double* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
+#pragma unroll
+        for (int l = 0; l < kSmallM; ++l) as[l] = fma(__ldg(As + l * kTile), d, as[l]);
+      }
+    }
+    double q = 0.0;
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) q = fma(as[l], as[l], q);
+    beta[k] = q;
+  }
+  return select_fp64(beta, present, ct, eps);
+}
+
+template <int M, int NS, int NQ3, int NV>
+__device__ __noinline__ void w_small_native(const double* A, const uint16_t* nb, const double* st,
+                                            double u0, uint8_t sel, const double* psi,
+                                            double* out) {
+  double sum[kSmallM];
+#pragma unroll
+  for (int l = 0; l < kSmallM; ++l) sum[l] = 0.0;
+  for (int k = 0; k < kSmallK; ++k) {
+    if (!((sel >> k) & 1)) continue;
+    double as[kSmallM];
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) as[l] = 0.0;
+    for (int s = 0; s < kSmallN; ++s) {
+      const double d = st[nb[(NS + k * kSmallN + s) * kTile] & kHaloPosMask] - u0;
+      const double* As = A + (int64_t)(M * NS + (k * kSmallN + s) * kSmallM) * kTile;
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) as[l] = fma(__ldg(As + l * kTile), d, as[l]);
+    }
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) sum[l] += as[l];
+  }
+  const int nd = (sel & 1) + ((sel >> 1) & 1) + ((sel >> 2) & 1);
+  double cf[kSmallM];
+#pragma unroll
+  for (int l = 0; l < kSmallM; ++l) cf[l] = nd ? sum[l] / (double)nd : 0.0;
+  for (int p = 0; p < NQ3; ++p) {
+    double sp = 0.0;
+#pragma unroll
+    for (int l = 0; l < kSmallM; ++l) sp = fma(__ldg(psi + p * kMaxM + l), cf[l], sp);
+    out[p * NV] = u0 + sp;
+  }
+}
+
+// kN = false: the FP64 path in pairs (halo, W and Gauss values as (hi, lo)
+// FP32 pairs); kN = true: the native FP64 path (FP64 halo, W and values, the
+// multiply-adds on the FP64 pipe).  The FP32 cutoff screen is the same.
+template <int M, int NS, int NQ, bool kN>
 __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ, 3, 4>::kBlocks))
-    recon_tma_w_kernel(const ReconArgs a, const HaloArgs h, const float2* __restrict__ psi,
-                       const float* __restrict__ g32, const float2* __restrict__ wq, int* err) {
+    recon_tma_w_kernel(const ReconArgs a, const HaloArgs h, const void* __restrict__ psi_v,
+                       const float* __restrict__ g32, const void* __restrict__ wq, int* err) {
+  // 8-byte elements either way: halo states, W entries, Gauss-point values
+  using HT = typename std::conditional<kN, double, float2>::type;
+  using Acc = typename std::conditional<kN, double, DF>::type;
   constexpr int NQ3 = 3 * NQ;
   using P = WPlan<M, NS, NQ3, 3, 4>;
   constexpr int kR = P::kRingW;
@@ -2050,8 +2131,8 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
   constexpr int E = M * NS + kSmallEntries;
   constexpr int kPer = NQ3 * NV;  // Gauss-point pairs per cell
   extern __shared__ __align__(128) unsigned char smem[];
-  float2* halo = reinterpret_cast<float2*>(smem + (size_t)kR * P::kMat);  // [2][NV][kHaloMax]
-  float2* ostg = reinterpret_cast<float2*>(smem + P::kOutOff);
+  HT* halo = reinterpret_cast<HT*>(smem + (size_t)kR * P::kMat);  // [2][NV][kHaloMax]
+  HT* ostg = reinterpret_cast<HT*>(smem + P::kOutOff);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kR * P::kMat + P::kHaloBytes);
   uint64_t* empty = full + kR;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kR);
@@ -2114,8 +2195,14 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
     for (int i = tid; i < H; i += kConsumers * kTile) {
       const int id = __ldg(h.ids + h0 + i);
 #pragma unroll
-      for (int w = 0; w < NV; ++w)
-        cp_async8(&halo[(hb * NV + w) * kHaloMax + i], a.Us + (int64_t)w * a.n_pad + id);
+      for (int w = 0; w < NV; ++w) {
+        const void* src;
+        if constexpr (kN)
+          src = a.U + (int64_t)w * a.n_pad + id;
+        else
+          src = a.Us + (int64_t)w * a.n_pad + id;
+        cp_async8(&halo[(hb * NV + w) * kHaloMax + i], src);
+      }
     }
     cp_async_commit();
   };
@@ -2132,18 +2219,26 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
       cp_async_commit();
     cp_async_wait<1>();
     consumer_sync();
-    const float2* st = halo + (hb * NV + v) * kHaloMax;
+    const HT* st = halo + (hb * NV + v) * kHaloMax;
     const uint16_t* nb = h.nbr_loc + tile * (int64_t)SL * kTile + lane;
     const int64_t c = tile * kTile + lane;  // may be a pad lane of the last tile
-    const float2 u0s = a.Us[(int64_t)v * a.n_pad + (c < a.n_cell ? c : 0)];
-    auto dif = [&](int idx) -> DF {  // d_s = U_s - U_0 in pairs
-      const float2 q = st[idx];
-      DF t = two_sum(q.x, -u0s.x);
-      t.l += q.y - u0s.y;
-      return two_sum(t.h, t.l);
+    HT u0s;
+    if constexpr (kN)
+      u0s = a.U[(int64_t)v * a.n_pad + (c < a.n_cell ? c : 0)];
+    else
+      u0s = a.Us[(int64_t)v * a.n_pad + (c < a.n_cell ? c : 0)];
+    auto dif = [&](int idx) -> Acc {  // d_s = U_s - U_0 (pairs, or FP64)
+      if constexpr (kN) {
+        return st[idx] - u0s;
+      } else {
+        const float2 q = st[idx];
+        DF t = two_sum(q.x, -u0s.x);
+        t.l += q.y - u0s.y;
+        return two_sum(t.h, t.l);
+      }
     };
     float a32[M], s32[kSmallK][kSmallM], eL = 0.f, eS[kSmallK];
-    DF uq[NQ3];
+    Acc uq[NQ3];
 #pragma unroll
     for (int l = 0; l < M; ++l) a32[l] = 0.f;
 #pragma unroll
@@ -2153,11 +2248,11 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
       for (int l = 0; l < kSmallM; ++l) s32[k][l] = 0.f;
     }
 #pragma unroll
-    for (int p = 0; p < NQ3; ++p) uq[p] = DF{0.f, 0.f};
+    for (int p = 0; p < NQ3; ++p) uq[p] = Acc{};
     // selection and Gauss-point values of cell c (after all stages of its tile)
     auto finish_cell = [&](int64_t tile, int64_t c) {
       const int present = a.smask[c];
-      const float2* A = reinterpret_cast<const float2*>(a.ahat) + tile * (int64_t)E * kTile + lane;
+      const HT* A = reinterpret_cast<const HT*>(a.ahat) + tile * (int64_t)E * kTile + lane;
       uint8_t sel;
       if (a.sel_in) {
         sel = a.sel_in[(int64_t)v * a.n_pad + c];
@@ -2197,22 +2292,36 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
             if (((present >> k) & 1) && chi_keep32_bound(t, k, present & 7, ct, f, &near))
               sel |= (uint8_t)(1u << k);
         }
-        if (near) sel = w_select_pairs<M, NS>(A, nb, st, u0s, present, a.ct, a.eps);
+        if (near) {
+          if constexpr (kN)
+            sel = w_select_native<M, NS>(A, nb, st, u0s, present, a.ct, a.eps);
+          else
+            sel = w_select_pairs<M, NS>(A, nb, st, u0s, present, a.ct, a.eps);
+        }
       }
       if (a.sel_out) a.sel_out[(int64_t)v * a.n_pad + c] = sel;
-      // Gauss-point values as (hi, lo) pairs, to the output stage or to Uq
-      float2* __restrict__ out = TENO_STAGE_OUT_W
-                                     ? ostg + lane * (kPer + 1) + v
-                                     : reinterpret_cast<float2*>(a.Uq) + c * kPer + v;
+      // Gauss-point values ((hi, lo) pairs or FP64), to the output stage or to Uq
+      HT* __restrict__ out = TENO_STAGE_OUT_W ? ostg + lane * (kPer + 1) + v
+                                              : reinterpret_cast<HT*>(a.Uq) + c * kPer + v;
       if (sel & 8) {
-        const DF u0 = {u0s.x, u0s.y};
+        if constexpr (kN) {
 #pragma unroll
-        for (int p = 0; p < NQ3; ++p) {
-          const DF r = u0 + df_norm(uq[p]);
-          out[p * NV] = make_float2(r.h, r.l);
+          for (int p = 0; p < NQ3; ++p) out[p * NV] = u0s + uq[p];
+        } else {
+          const DF u0 = {u0s.x, u0s.y};
+#pragma unroll
+          for (int p = 0; p < NQ3; ++p) {
+            const DF r = u0 + df_norm(uq[p]);
+            out[p * NV] = make_float2(r.h, r.l);
+          }
         }
       } else {
-        w_small_values<M, NS, NQ3, NV>(A, nb, st, u0s, sel, psi, out);
+        if constexpr (kN)
+          w_small_native<M, NS, NQ3, NV>(A, nb, st, u0s, sel,
+                                         reinterpret_cast<const double*>(psi_v), out);
+        else
+          w_small_values<M, NS, NQ3, NV>(A, nb, st, u0s, sel,
+                                         reinterpret_cast<const float2*>(psi_v), out);
       }
     };
     for (int j = 0; j < P::kStages; ++j, ++g) {
@@ -2233,16 +2342,26 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
         // skip the stage
       } else if (k < 0) {
         const float* gm = reinterpret_cast<const float*>(buf) + lane;
-        const float2* wm = reinterpret_cast<const float2*>(buf + P::kWOff) + lane;
+        const HT* wm = reinterpret_cast<const HT*>(buf + P::kWOff) + lane;
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
           if (s < nslot) {
-            const DF d = dif(nl[s * kTile] & kHaloPosMask);
+            const Acc d = dif(nl[s * kTile] & kHaloPosMask);
+            float dh;
+            if constexpr (kN)
+              dh = (float)d;
+            else
+              dh = d.h;
 #pragma unroll
-            for (int l = 0; l < M; ++l) a32[l] = fmaf(gm[(s * P::kG + l) * kTile], d.h, a32[l]);
-            eL = fmaf(gm[(s * P::kG + M) * kTile], fabsf(d.h), eL);
+            for (int l = 0; l < M; ++l) a32[l] = fmaf(gm[(s * P::kG + l) * kTile], dh, a32[l]);
+            eL = fmaf(gm[(s * P::kG + M) * kTile], fabsf(dh), eL);
 #pragma unroll
-            for (int p = 0; p < NQ3; ++p) df_mac(uq[p], wm[(s * NQ3 + p) * kTile], d);
+            for (int p = 0; p < NQ3; ++p) {
+              if constexpr (kN)
+                uq[p] = fma(wm[(s * NQ3 + p) * kTile], d, uq[p]);
+              else
+                df_mac(uq[p], wm[(s * NQ3 + p) * kTile], d);
+            }
           }
         }
       } else {
@@ -2252,8 +2371,12 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
           if (kk != k) continue;
 #pragma unroll
           for (int s = 0; s < 4; ++s) {
-            const float2 q = st[nl[s * kTile] & kHaloPosMask];
-            const float dh = (q.x - u0s.x) + (q.y - u0s.y);
+            const HT q = st[nl[s * kTile] & kHaloPosMask];
+            float dh;
+            if constexpr (kN)
+              dh = (float)(q - u0s);
+            else
+              dh = (q.x - u0s.x) + (q.y - u0s.y);
 #pragma unroll
             for (int l = 0; l < kSmallM; ++l)
               s32[kk][l] = fmaf(gm[(s * P::kGs + l) * kTile], dh, s32[kk][l]);
@@ -2268,7 +2391,7 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
     if constexpr (TENO_STAGE_OUT_W != 0) {
       consumer_sync();  // the tile's values are staged
       if (!dead)
-        store_out_stage<kPer>(ostg, reinterpret_cast<float2*>(a.Uq) + tile * kTile * kPer,
+        store_out_stage<kPer>(ostg, reinterpret_cast<HT*>(a.Uq) + tile * kTile * kPer,
                               (int)min((int64_t)kTile, a.n_cell - tile * kTile), tid);
     }
   }
@@ -3592,11 +3715,11 @@ cudaError_t launch_recon_tma(const ReconArgs& a, const DeviceMesh& dm, int* err,
   return cudaGetLastError();
 }
 
-template <int M, int NS, int NQ>
+template <int M, int NS, int NQ, bool kN>
 cudaError_t launch_recon_tma_w(const ReconArgs& a, const DeviceMesh& dm, int* err,
                                cudaStream_t st) {
   using P = WPlan<M, NS, 3 * NQ, 3, 4>;
-  auto kern = recon_tma_w_kernel<M, NS, NQ>;
+  auto kern = recon_tma_w_kernel<M, NS, NQ, kN>;
   const int threads = kTile * (kConsumers + 1);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)P::kSmem);
@@ -3611,7 +3734,8 @@ cudaError_t launch_recon_tma_w(const ReconArgs& a, const DeviceMesh& dm, int* er
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)per_sm * sms);
-  kern<<<(unsigned)grid, threads, P::kSmem, st>>>(a, dm.halo, dm.psi_df, dm.g32, dm.wq, err);
+  const void* psi = kN ? (const void*)dm.psi_d : (const void*)dm.psi_df;
+  kern<<<(unsigned)grid, threads, P::kSmem, st>>>(a, dm.halo, psi, dm.g32, dm.wq, err);
   return cudaGetLastError();
 }
 
@@ -3669,6 +3793,12 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
       // take the TMA or the direct kernels: the halo kernel is compiled for
       // TENO in conservative variables only.
       const bool ext = dm.scheme != 0 || dm.charvar != 0;
+      // the native FP64 path has the W-form kernel only (no pair TMA kernel)
+      const bool wn = NV == 4 && dm.variant == 2 && dm.err_flag && dm.halo.off && !ext &&
+                      dm.precision == TENO_FP64_NATIVE && dm.g32 && dm.wq && dm.psi_d;
+      if constexpr (NV == 4) {
+        if (wn) return launch_recon_tma_w<M, NS, NQ, true>(a, dm, dm.err_flag, st);
+      }
       const bool tma = NV == 4 && dm.variant == 2 && dm.err_flag && dm.halo.off &&
                        dm.precision != TENO_FP64_NATIVE;
       if (!ext && (dm.variant == 0 || (dm.variant == 2 && !tma)) && dm.halo.off) {
@@ -3686,7 +3816,7 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
       if constexpr (NV == 4) {
         if (tma) {
           if (dm.precision == TENO_FP64 && dm.scheme == 0 && dm.g32 && dm.wq && dm.psi_df)
-            return launch_recon_tma_w<M, NS, NQ>(a, dm, dm.err_flag, st);
+            return launch_recon_tma_w<M, NS, NQ, false>(a, dm, dm.err_flag, st);
           if (ext) {
             if (dm.precision == TENO_FP64)
               return launch_recon_tma<M, NS, NQ, true, true>(a, dm, dm.err_flag, st);

@@ -106,8 +106,9 @@ def test_scalar_teno3_config1(T, oracle_mod):
     assert rel(t.get_state(), Uo) <= TOL
 
 
-@pytest.mark.parametrize("precision,variant", [(0, 0), (0, 1), (0, 2), (2, 0)],
-                         ids=["fp64-halo", "fp64-direct", "fp64-tma", "fp64native"])
+@pytest.mark.parametrize("precision,variant", [(0, 0), (0, 1), (0, 2), (2, 0), (2, 2)],
+                         ids=["fp64-halo", "fp64-direct", "fp64-tma", "fp64native-halo",
+                              "fp64native-w"])
 @pytest.mark.parametrize("order", [3, 4, 5, 6])
 def test_euler_vortex_hll(T, oracle_mod, order, precision, variant):
     """Isentropic vortex, HLL, FP64 (double-float with halo-staged, direct or
@@ -118,8 +119,9 @@ def test_euler_vortex_hll(T, oracle_mod, order, precision, variant):
     _check_residual(T, oracle_mod, mesh, U, order, 4, 1, precision=precision, variant=variant)
 
 
-@pytest.mark.parametrize("precision,variant", [(0, 0), (0, 1), (0, 2), (2, 0)],
-                         ids=["fp64-halo", "fp64-direct", "fp64-tma", "fp64native"])
+@pytest.mark.parametrize("precision,variant", [(0, 0), (0, 1), (0, 2), (2, 0), (2, 2)],
+                         ids=["fp64-halo", "fp64-direct", "fp64-tma", "fp64native-halo",
+                              "fp64native-w"])
 @pytest.mark.parametrize("order,flux", [(6, 2), (5, 1), (4, 2), (3, 1)])
 def test_euler_discontinuous(T, oracle_mod, order, flux, precision, variant):
     """A density/pressure square exercises the cutoff and the directional
@@ -470,19 +472,22 @@ def test_boundary_conditions_residual(T, oracle_mod, order, flux):
     assert rel(v, vo) <= 1e-10
 
 
+@pytest.mark.parametrize("precision", [0, 2], ids=["pairs", "native"])
 @pytest.mark.parametrize("order", [3, 4, 5, 6])
-def test_w_form_forced_fallback(T, oracle_mod, order):
-    """The default FP64 Euler kernel (W form) decides the cutoff from FP32
-    indicators with a rigorous bound and falls back to pairs and FP64 where
-    the bound does not separate chi from C_T.  With the debug bit that sends
-    every cell through that fallback, selections and residuals still match the
-    oracle on the vortex (large stencil everywhere) and on the discontinuous
-    state (directional stencils in use)."""
+def test_w_form_forced_fallback(T, oracle_mod, order, precision):
+    """The default FP64 Euler kernels (W form, pairs and native) decide the
+    cutoff from FP32 indicators with a rigorous bound and fall back to pairs
+    or FP64 and an FP64 decision where the bound does not separate chi from
+    C_T.  With the debug bit that sends every cell through that fallback,
+    selections and residuals still match the oracle on the vortex (large
+    stencil everywhere) and on the discontinuous state (directional stencils
+    in use)."""
     for mesh, kind, flux in [(inputs.jittered_mesh(33, 31, 10.0, 10.0, seed=1002), "vortex", 1),
                              (inputs.jittered_mesh(40, 40, 10.0, 10.0, seed=1007), "blast", 2)]:
         U = _blast(mesh) if kind == "blast" else inputs.cell_average(mesh, inputs.isentropic_vortex)
         t = T.Teno(device=0).load(mesh)
-        t.precompute_stencils(order=order, n_var=4, flux=flux, debug=T.DEBUG_FORCE_FALLBACK)
+        t.precompute_stencils(order=order, n_var=4, flux=flux, precision=precision,
+                              debug=T.DEBUG_FORCE_FALLBACK)
         t.set_state(U)
         R, sel = t.residual(want_sel=True)
         o = oracle_mod.Oracle(mesh, order=order, n_var=4, flux=flux)
