@@ -165,10 +165,16 @@ def algorithmic_vjp_bytes(order, nq):
 
 
 def algorithmic_fp64_flops(order, n_var, nq):
-    """FP64 flops per cell of the native reconstruction: differences,
-    matvecs, beta, selection and Gauss-point evaluation."""
+    """FP64 flops per cell of the native reconstruction in the W form (the
+    default native kernel, recon_tma_w_kernel<native>): per variable the
+    N_s + 36 stencil differences, the Gauss-point values U_0 + W d as
+    N_s x 3 N_q multiply-adds (2 flops each) and 3 N_q additions.  The
+    smoothness indicators and the cutoff run on the FP32 pipe (with the FP64
+    fallback where their error bound does not decide), so they are not FP64
+    work; the direct evaluation of the hot-path table (coefficients, beta,
+    evaluation: about 14.4k flops at TENO6) is the same mathematics."""
     m, ns, entries = sizes(order)
-    per_var = (ns + 36) + 2 * entries + 2 * (m + 15) + 25 + 2 * 3 * nq * m + 3 * nq
+    per_var = (ns + 36) + 2 * ns * 3 * nq + 3 * nq
     return per_var * n_var
 
 
@@ -297,7 +303,7 @@ def run_ours(args):
         nbytes = algorithmic_bytes(args.order, 4, key[path]) * n_cell
         gbs = nbytes / (rec_ms / 1e3) / 1e9
         if path == "native":
-            kernel = f"recon_halo_kernel <fp64_native> order {args.order}"
+            kernel = f"recon_tma_w_kernel <fp64 native> order {args.order}"
         elif path == "pairs":
             kernel = (f"recon_tma_w_kernel <fp64 pairs> order {args.order}" if scheme == "teno"
                       else f"recon_tma_kernel <fp64 pairs, CWENO> order {args.order}")

@@ -297,6 +297,93 @@ int teno_profile(teno_ctx* ctx, int enable);
  * Synchronises on the recorded events; either pointer may be NULL. */
 int teno_profile_read(teno_ctx* ctx, double* ms, int64_t* launches);
 
+/* ---- Partitioned meshes (one exchange per stage; no counterpart in the
+ * paper, whose code decomposes its meshes over MPI ranks, Sec. 5's
+ * efficiency note).  The mesh's cells are split into n_parts contiguous
+ * ranges of the Hilbert order made of whole 32-cell tiles ("owned" cells).
+ * A partition reconstructs its owned cells and the first layer of cells
+ * across its boundary (the face neighbours of owned cells), so that it
+ * evaluates every face flux its owned cells need by itself, and keeps the
+ * states of every cell those stencils reach (its "halo").  Per RK stage one
+ * halo exchange brings the stage state of the halo from the owners; the
+ * adjoint's reverse exchange returns the contributions to other parts' cells.
+ * Each partition's stencils, matrices and slot order are those of the whole
+ * mesh, and each face is evaluated with its whole-mesh orientation, so the
+ * residual and the RK3 update of every owned cell are the whole-mesh results
+ * bit for bit; the VJP sums the same terms in another order (equal up to
+ * rounding).
+ *
+ * Precompute part `part` of n_parts (stencils and matrices of its compute
+ * set only).  The same parameters as teno_precompute_stencils, with
+ * adv_field = 0 and charvar = 0.  n_parts = 1 is the whole mesh.  On a
+ * partition: teno_set_state and teno_set_selection_override take the whole
+ * mesh's array ([n_var][n_cell] user order) and keep the partition's cells;
+ * teno_get_state, teno_residual, teno_get_stage_state return the owned cells
+ * ([n_var][n_owned], in teno_partition_cells order); teno_cfl_dt is this
+ * part's step; teno_rk3_step(s), teno_residual_vjp and teno_adjoint_step
+ * return TENO_EINVAL (step with teno_group_rk3_step or teno_rk3_stage).
+ * Errors: those of teno_precompute_stencils; TENO_EINVAL for a bad part or
+ * more parts than tiles. */
+int teno_precompute_partition(teno_ctx* ctx, const teno_params* p, int32_t n_parts,
+                              int32_t part);
+
+/* *n_owned owned cells, *n_state cells of the state arrays (owned, first
+ * layer, halo, and inert padding lanes); recv_counts / send_counts host
+ * [n_parts] (nullable): cells received from / sent to each part per
+ * exchange (send counts are 0 until teno_partition_set_send). */
+int teno_partition_sizes(teno_ctx* ctx, int64_t* n_owned, int64_t* n_state, int64_t* recv_counts,
+                         int64_t* send_counts);
+
+/* owned_user host [n_owned]: user ids of the owned cells, in the order of
+ * the partition's owned arrays. */
+int teno_partition_cells(teno_ctx* ctx, int32_t* owned_user);
+
+/* user_ids host [recv_counts[peer]]: the cells this partition receives from
+ * `peer` per exchange, in the order the exchange buffers hold them (ascending
+ * Hilbert index).  Host-only contexts too. */
+int teno_partition_recv_cells(teno_ctx* ctx, int32_t peer, int32_t* user_ids);
+
+/* Declare the cells `peer` receives from this partition (user ids, host
+ * [n], in the peer's receive order: its teno_partition_recv_cells(peer ->
+ * this part)); every one must be owned here.  Host-only contexts too. */
+int teno_partition_set_send(teno_ctx* ctx, int32_t peer, int64_t n, const int32_t* user_ids);
+
+/* Exchange buffers, device [n_var][count] on the context's stream.  what =
+ * 0, 1, 2: the state U^n (also the state after a step), the stage-1 output
+ * U^(1), the stage-2 output U^(2): pack the owned cells `peer` receives,
+ * unpack the cells received from `peer` into the halo.  what = 3, the
+ * adjoint's reverse exchange: pack this part's contributions to the cells
+ * `peer` owns (its receive list), unpack adds the contributions from `peer`
+ * to the owned cells (its send list).  Send lists must be set. */
+int teno_halo_pack(teno_ctx* ctx, int32_t peer, int32_t what, double* buf);
+int teno_halo_unpack(teno_ctx* ctx, int32_t peer, int32_t what, const double* buf);
+
+/* Stage 1, 2 or 3 of an SSP-RK3 step with step dt on the updated cells
+ * (Eq. fv_time_discretization_01); the halo of the stage's input state must
+ * be current (U^n, U^(1), U^(2): exchange what = 0, 1, 2 first).  Stage 3
+ * advances the context's time by dt. */
+int teno_rk3_stage(teno_ctx* ctx, int32_t stage, double dt);
+
+/* Largest (|v| + c) / (4|V| / perimeter) over the updated cells (host
+ * result; synchronises): the CFL step of a partitioned mesh is
+ * cfl / (maximum over its parts). */
+int teno_local_max_speed(teno_ctx* ctx, double* lam);
+
+/* One SSP-RK3 step of all n parts of one mesh in this process (parts[i] is
+ * part i; one device and one stream): the step's dt (<= 0: the CFL step from
+ * the largest speed over all parts) and after every stage the copy-based
+ * halo exchange (pack on the owner, one device-to-device copy, unpack on the
+ * receiver).  The first call declares the send lists from the receive lists.
+ * dt_used (nullable, host) receives the step. */
+int teno_group_rk3_step(teno_ctx* const* parts, int32_t n, double dt, double* dt_used);
+
+/* v = (dR/dU)^T w for all n parts of one mesh in this process: each part
+ * takes the cotangents of its owned cells from w (host [n_var][n_cell], user
+ * order), runs the VJP with the selection frozen, and the reverse exchange
+ * returns the contributions to other parts' cells; v host [n_var][n_cell]
+ * user order (synchronises).  FP64 paths, TENO, no positivity scaling. */
+int teno_group_residual_vjp(teno_ctx* const* parts, int32_t n, const double* w, double* v);
+
 /* Measured rate (flop/s, one FMA = 2 flops) of independent fused multiply-adds
  * on every SM of `device`: precision 0 FP32, 1 FP64 (measurement support for
  * roofline fractions; no counterpart in the paper).  Runs about 0.1 s of GPU

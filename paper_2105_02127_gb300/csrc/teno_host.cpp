@@ -89,6 +89,20 @@ struct teno_ctx {
   std::vector<int32_t> hrev_idx_h;
   bool adj_tiled = false;
   double time = 0.0;
+  // state and output extents: the whole mesh (sn = nc cells, stride spad =
+  // npad, io_n = nc) or one partition (teno_precompute_partition)
+  int64_t sn = 0, spad = 0, io_n = 0;
+  int32_t part_n = 1, part_id = 0;
+  int64_t n_own = 0, n_comp = 0;
+  std::vector<int64_t> part_bounds;  // [part_n + 1] internal-id start of every part
+  std::vector<int32_t> loc2glob;     // local cell -> global internal id
+  std::vector<std::vector<int32_t>> recv_loc, send_loc;  // per peer, local cell ids
+  std::vector<DevBuf> b_recv_idx, b_send_idx, b_xbuf;     // per peer
+  DevBuf b_perm_in;                  // local cell -> global user id (partitions)
+  // global faces (internal ids), kept on the host for partitions
+  std::vector<int32_t> h_fcells, h_cfaces;
+  std::vector<int8_t> h_fedges;
+  std::vector<double> h_fgeom, h_inv_area, h_cfl_len;
   // kernel timing (teno_profile): event pairs around launches, per kind
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -765,12 +779,63 @@ int colour_slots(int nval, int ns, const int32_t* members, int32_t* slot_of) {
   return 1;
 }
 
-int run_precompute(teno_ctx* ctx) {
+// The cells of a partition (teno_precompute_partition): owned internal ids
+// [c0, c1), a range of whole 32-cell tiles of the Hilbert order; the compute
+// set (owned, then the first layer across the boundary: face neighbours of
+// owned cells, ascending); the halo (every other stencil member of the
+// compute set, ascending).  Local cell ids: compute set first, then halo.
+struct PartCells {
+  int64_t c0 = 0, c1 = 0;
+  std::vector<int32_t> layer1;  // global internal ids
+};
+
+int part_cells(const teno_ctx* ctx, int32_t n_parts, int32_t part, PartCells& pc,
+               std::vector<int64_t>& bounds) {
+  const int64_t nc = ctx->nc, ntile = (nc + kTile - 1) / kTile;
+  bounds.assign(n_parts + 1, 0);
+  for (int32_t q = 0; q <= n_parts; ++q)
+    bounds[q] = std::min<int64_t>(nc, kTile * (ntile * q / n_parts));
+  pc.c0 = bounds[part];
+  pc.c1 = bounds[part + 1];
+  if (pc.c1 <= pc.c0) return TENO_EINVAL;
+  std::vector<int32_t> l1;
+  for (int64_t c = pc.c0; c < pc.c1; ++c) {
+    const int32_t u = ctx->perm[c];
+    for (int e = 0; e < 3; ++e) {
+      const int32_t nu = ctx->fnbr[3 * u + e];
+      if (nu < 0) continue;
+      const int32_t n = ctx->iperm[nu];
+      if (n < pc.c0 || n >= pc.c1) l1.push_back(n);
+    }
+  }
+  std::sort(l1.begin(), l1.end());
+  l1.erase(std::unique(l1.begin(), l1.end()), l1.end());
+  pc.layer1.swap(l1);
+  return TENO_OK;
+}
+
+int run_precompute(teno_ctx* ctx, int32_t n_parts = 1, int32_t part = 0) {
   const teno_params& p = ctx->prm;
   RefData R;
   if (make_ref(p.order, ctx->nq, R)) return fail(ctx, TENO_EINVAL, "reference data");
   const int m = R.m, ns = ctx->ns, SL = ctx->SL, E = ctx->E;
-  const int64_t nc = ctx->nc, npad = ctx->npad, ntile = npad / kTile;
+  const int64_t nc = ctx->nc, ntile_g = ctx->npad / kTile;
+  // the global tiles whose cells are built: all of them, or those holding a
+  // partition's compute set (every lane of such a tile, for its slot colouring)
+  PartCells pc;
+  std::vector<int64_t> tiles_g;
+  if (n_parts > 1) {
+    int rc0 = part_cells(ctx, n_parts, part, pc, ctx->part_bounds);
+    if (rc0) return fail(ctx, rc0, "partition: empty part (more parts than tiles)");
+    for (int64_t t = pc.c0 / kTile; t * kTile < pc.c1; ++t) tiles_g.push_back(t);
+    for (int32_t c : pc.layer1) tiles_g.push_back(c / kTile);
+    std::sort(tiles_g.begin(), tiles_g.end());
+    tiles_g.erase(std::unique(tiles_g.begin(), tiles_g.end()), tiles_g.end());
+  } else {
+    tiles_g.resize(ntile_g);
+    for (int64_t t = 0; t < ntile_g; ++t) tiles_g[t] = t;
+  }
+  int64_t ntile = (int64_t)tiles_g.size();
   ctx->st_large.assign(nc * ns, -1);
   ctx->st_small.assign(nc * kSmallK * kSmallN, -1);
   // matrix storage: double (native FP64), (hi, lo) float pairs (FP64 via
@@ -790,94 +855,97 @@ int run_precompute(teno_ctx* ctx) {
   std::vector<float> g32(wform ? (size_t)ntile * E32 * kTile : 0, 0.f);
   std::vector<float2> wq(wform ? (size_t)ntile * EW * kTile : 0, make_float2(0.f, 0.f));
   std::vector<int32_t> nbr((size_t)ntile * SL * kTile, 0);
-  std::vector<uint8_t> smask(npad, 0);
+  std::vector<uint8_t> smask((size_t)ntile * kTile, 0);
   int rc = TENO_OK;
   int64_t bad = -1;
 #pragma omp parallel
   {
     Searcher S(ctx);
     std::vector<double> G(kMaxM * kMaxNs);
-#pragma omp for schedule(dynamic, 256)
-    for (int64_t i = 0; i < nc; ++i) {
-      if (rc != TENO_OK) continue;
-      const int32_t t = (int32_t)i;  // user id
-      int32_t* lg = &ctx->st_large[(size_t)t * ns];
-      int32_t* sm = &ctx->st_small[(size_t)t * kSmallK * kSmallN];
-      int r = find_stencils(S, t, ns, lg, sm);
-      const int64_t c = ctx->iperm[t];  // internal index
-      const int64_t tile = c / kTile, lane = c % kTile;
-      auto put = [&](int e, double x) {
-        size_t pos = ((size_t)tile * E + e) * kTile + lane;
-        if (store == TENO_FP64_NATIVE) {
-          reinterpret_cast<double*>(ahat.data())[pos] = x;
-        } else if (store == TENO_FP64) {
-          const float hi = (float)x;
-          reinterpret_cast<float*>(ahat.data())[2 * pos] = hi;
-          reinterpret_cast<float*>(ahat.data())[2 * pos + 1] = (float)(x - (double)hi);
-        } else {
-          reinterpret_cast<float*>(ahat.data())[pos] = (float)x;
-        }
-      };
-      // FP32 rows plus an upper bound of their absolute column sum
-      auto put32 = [&](int e0, const double* col, int stride, int rows) {
-        double cs = 0.0;
-        for (int l = 0; l < rows; ++l) {
-          const float x = (float)col[l * stride];
-          g32[((size_t)tile * E32 + e0 + l) * kTile + lane] = x;
-          cs += std::fabs((double)x);
-        }
-        g32[((size_t)tile * E32 + e0 + rows) * kTile + lane] = (float)(cs * (1.0 + 1e-6));
-      };
-      if (!r) r = stencil_matrix(ctx, R, t, lg, ns, m, G.data());
-      if (!r) {
-        for (int s = 0; s < ns; ++s) {
-          nbr[((size_t)tile * SL + s) * kTile + lane] = ctx->iperm[lg[s]];
-          for (int l = 0; l < m; ++l) put(s * m + l, G[l * ns + s]);
-          if (wform) {
-            put32(s * (m + 1), &G[s], ns, m);
-            for (int q = 0; q < nq3; ++q) {
-              double w = 0.0;
-              for (int l = 0; l < m; ++l) w += R.psi_t[q * kMaxM + l] * G[l * ns + s];
-              float2& dst = wq[((size_t)tile * EW + s * nq3 + q) * kTile + lane];
-              if (store == TENO_FP64_NATIVE) {
-                static_assert(sizeof(float2) == sizeof(double), "8-byte W entries");
-                memcpy(&dst, &w, sizeof(double));
-              } else {
-                const float hi = (float)w;
-                dst = make_float2(hi, (float)(w - (double)hi));
+#pragma omp for schedule(dynamic, 8)
+    for (int64_t k = 0; k < ntile; ++k) {
+      for (int64_t lane = 0; lane < kTile; ++lane) {
+        const int64_t c = tiles_g[k] * kTile + lane;  // internal index
+        if (c >= nc || rc != TENO_OK) continue;
+        const int32_t t = ctx->perm[c];  // user id
+        const int64_t tile = k;
+        int32_t* lg = &ctx->st_large[(size_t)t * ns];
+        int32_t* sm = &ctx->st_small[(size_t)t * kSmallK * kSmallN];
+        int r = find_stencils(S, t, ns, lg, sm);
+        auto put = [&](int e, double x) {
+          size_t pos = ((size_t)tile * E + e) * kTile + lane;
+          if (store == TENO_FP64_NATIVE) {
+            reinterpret_cast<double*>(ahat.data())[pos] = x;
+          } else if (store == TENO_FP64) {
+            const float hi = (float)x;
+            reinterpret_cast<float*>(ahat.data())[2 * pos] = hi;
+            reinterpret_cast<float*>(ahat.data())[2 * pos + 1] = (float)(x - (double)hi);
+          } else {
+            reinterpret_cast<float*>(ahat.data())[pos] = (float)x;
+          }
+        };
+        // FP32 rows plus an upper bound of their absolute column sum
+        auto put32 = [&](int e0, const double* col, int stride, int rows) {
+          double cs = 0.0;
+          for (int l = 0; l < rows; ++l) {
+            const float x = (float)col[l * stride];
+            g32[((size_t)tile * E32 + e0 + l) * kTile + lane] = x;
+            cs += std::fabs((double)x);
+          }
+          g32[((size_t)tile * E32 + e0 + rows) * kTile + lane] = (float)(cs * (1.0 + 1e-6));
+        };
+        if (!r) r = stencil_matrix(ctx, R, t, lg, ns, m, G.data());
+        if (!r) {
+          for (int s = 0; s < ns; ++s) {
+            nbr[((size_t)tile * SL + s) * kTile + lane] = ctx->iperm[lg[s]];
+            for (int l = 0; l < m; ++l) put(s * m + l, G[l * ns + s]);
+            if (wform) {
+              put32(s * (m + 1), &G[s], ns, m);
+              for (int q = 0; q < nq3; ++q) {
+                double w = 0.0;
+                for (int l = 0; l < m; ++l) w += R.psi_t[q * kMaxM + l] * G[l * ns + s];
+                float2& dst = wq[((size_t)tile * EW + s * nq3 + q) * kTile + lane];
+                if (store == TENO_FP64_NATIVE) {
+                  static_assert(sizeof(float2) == sizeof(double), "8-byte W entries");
+                  memcpy(&dst, &w, sizeof(double));
+                } else {
+                  const float hi = (float)w;
+                  dst = make_float2(hi, (float)(w - (double)hi));
+                }
               }
             }
           }
-        }
-        uint8_t mask = 0;
-        for (int j = 0; j < kSmallK && !r; ++j) {
-          const int32_t* ids = sm + j * kSmallN;
-          const int slot0 = ns + j * kSmallN;
-          if (ids[0] < 0) {
-            for (int s = 0; s < kSmallN; ++s) {
-              nbr[((size_t)tile * SL + slot0 + s) * kTile + lane] = (int32_t)c;
-              for (int l = 0; l < kSmallM; ++l) put(m * ns + (j * kSmallN + s) * kSmallM + l, 0.0);
+          uint8_t mask = 0;
+          for (int j = 0; j < kSmallK && !r; ++j) {
+            const int32_t* ids = sm + j * kSmallN;
+            const int slot0 = ns + j * kSmallN;
+            if (ids[0] < 0) {
+              for (int s = 0; s < kSmallN; ++s) {
+                nbr[((size_t)tile * SL + slot0 + s) * kTile + lane] = (int32_t)c;
+                for (int l = 0; l < kSmallM; ++l)
+                  put(m * ns + (j * kSmallN + s) * kSmallM + l, 0.0);
+              }
+              continue;
             }
-            continue;
+            r = stencil_matrix(ctx, R, t, ids, kSmallN, kSmallM, G.data());
+            if (r) break;
+            mask |= (uint8_t)(1u << j);
+            for (int s = 0; s < kSmallN; ++s) {
+              nbr[((size_t)tile * SL + slot0 + s) * kTile + lane] = ctx->iperm[ids[s]];
+              for (int l = 0; l < kSmallM; ++l)
+                put(m * ns + (j * kSmallN + s) * kSmallM + l, G[l * kSmallN + s]);
+              if (wform)
+                put32(ns * (m + 1) + (j * kSmallN + s) * (kSmallM + 1), &G[s], kSmallN, kSmallM);
+            }
           }
-          r = stencil_matrix(ctx, R, t, ids, kSmallN, kSmallM, G.data());
-          if (r) break;
-          mask |= (uint8_t)(1u << j);
-          for (int s = 0; s < kSmallN; ++s) {
-            nbr[((size_t)tile * SL + slot0 + s) * kTile + lane] = ctx->iperm[ids[s]];
-            for (int l = 0; l < kSmallM; ++l)
-              put(m * ns + (j * kSmallN + s) * kSmallM + l, G[l * kSmallN + s]);
-            if (wform)
-              put32(ns * (m + 1) + (j * kSmallN + s) * (kSmallM + 1), &G[s], kSmallN, kSmallM);
-          }
+          smask[(size_t)tile * kTile + lane] = mask;
         }
-        smask[c] = mask;
-      }
-      if (r) {
+        if (r) {
 #pragma omp critical
-        {
-          rc = r;
-          bad = t;
+          {
+            rc = r;
+            bad = t;
+          }
         }
       }
     }
@@ -885,10 +953,10 @@ int run_precompute(teno_ctx* ctx) {
   if (rc)
     return fail(ctx, rc, "stencil or least-squares failure at user cell " + std::to_string(bad));
   // pad lanes of the last tile point at cell 0
-  for (int64_t c = nc; c < npad; ++c) {
-    const int64_t tile = c / kTile, lane = c % kTile;
-    for (int s = 0; s < SL; ++s) nbr[((size_t)tile * SL + s) * kTile + lane] = 0;
-  }
+  for (int64_t k = 0; k < ntile; ++k)
+    for (int64_t lane = 0; lane < kTile; ++lane)
+      if (tiles_g[k] * kTile + lane >= nc)
+        for (int s = 0; s < SL; ++s) nbr[((size_t)k * SL + s) * kTile + lane] = 0;
   // Slot order of the large stencils (for the adjoint's halo accumulation):
   // within each tile the members of the cells' large stencils are assigned
   // to the ns slots by a proper edge colouring of the bipartite graph (lane,
@@ -898,7 +966,8 @@ int run_precompute(teno_ctx* ctx) {
   // theorem); it is built edge by edge, swapping the two colours along an
   // alternating path where needed.  Tiles with a busier cell keep the
   // stencil-search order.  Matrix columns move with their slots: the
-  // reconstruction is the same sum in another order.
+  // reconstruction is the same sum in another order.  A partition colours
+  // the global tiles its cells belong to, so every cell keeps its slot order.
   {
     const size_t E32s = wform ? (size_t)E32 : 0, EWs = wform ? (size_t)EW : 0;
 #pragma omp parallel
@@ -907,7 +976,7 @@ int run_precompute(teno_ctx* ctx) {
       std::vector<unsigned char> tmp;
 #pragma omp for schedule(dynamic, 64)
       for (int64_t t = 0; t < ntile; ++t) {
-        const int nval = (int)std::min<int64_t>(kTile, nc - t * kTile);
+        const int nval = (int)std::min<int64_t>(kTile, nc - tiles_g[t] * kTile);
         members.resize((size_t)nval * ns);
         slot_of.resize((size_t)nval * ns);
         for (int ln = 0; ln < nval; ++ln)
@@ -944,25 +1013,137 @@ int run_precompute(teno_ctx* ctx) {
       }
     }
   }
+  // cells reconstructed (n_valid, the first ones of the layout) and cells of
+  // the state arrays (n_state; stencil ids index them)
+  int64_t n_valid = nc, n_state = nc;
+  if (n_parts > 1) {
+    // ---- extract the partition's compute set into the local layout: owned
+    // cells keep their lanes (whole tiles), the boundary layer follows in
+    // ascending order, at most `fill` per tile so that each local tile's
+    // stencil halo stays within kHaloMax cells (the other lanes are inert:
+    // zero matrices, stencils at local cell 0, never read by a face)
+    const int64_t n_own = pc.c1 - pc.c0;
+    std::vector<int64_t> slot_of_tile(ntile_g, -1);
+    for (int64_t k = 0; k < ntile; ++k) slot_of_tile[tiles_g[k]] = k;
+    // halo-only cells: stencil members of the compute set outside it
+    std::vector<int32_t> comp;
+    comp.reserve(n_own + pc.layer1.size());
+    for (int64_t c = pc.c0; c < pc.c1; ++c) comp.push_back((int32_t)c);
+    comp.insert(comp.end(), pc.layer1.begin(), pc.layer1.end());
+    std::vector<char> in_comp(nc, 0);
+    for (int32_t c : comp) in_comp[c] = 1;
+    std::vector<int32_t> halo;
+    for (int32_t c : comp) {
+      const int64_t k = slot_of_tile[c / kTile], lane = c % kTile;
+      for (int s = 0; s < SL; ++s) {
+        const int32_t j = nbr[((size_t)k * SL + s) * kTile + lane];
+        if (!in_comp[j]) halo.push_back(j);
+      }
+    }
+    std::sort(halo.begin(), halo.end());
+    halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
+    for (int fill = kTile; fill >= 4; fill /= 2) {
+      // local positions of the compute set: owned cells at their own offsets,
+      // then `fill` boundary cells per tile
+      std::vector<int64_t> pos(comp.size());
+      for (int64_t i = 0; i < n_own; ++i) pos[i] = i;
+      int64_t next = (n_own + kTile - 1) / kTile * kTile;  // the owned tail tile is not shared
+      if (n_own % kTile == 0) next = n_own;
+      for (size_t i = 0; i < pc.layer1.size(); ++i) {
+        const int64_t slot = (int64_t)i % fill;
+        if (slot == 0 && i > 0) next = (next + kTile - 1) / kTile * kTile;
+        pos[n_own + i] = next++;
+      }
+      const int64_t n_recon = comp.empty() ? 0 : pos.back() + 1;
+      // local ids: compute cells at their positions (inert lanes hold no
+      // cell), then the halo
+      std::vector<int32_t> glob2loc(nc, -1);
+      const int64_t nrp = (n_recon + kTile - 1) / kTile * kTile;
+      for (size_t i = 0; i < comp.size(); ++i) glob2loc[comp[i]] = (int32_t)pos[i];
+      for (size_t i = 0; i < halo.size(); ++i) glob2loc[halo[i]] = (int32_t)(nrp + i);
+      const int64_t ntl = nrp / kTile;
+      std::vector<unsigned char> ahat_l((size_t)ntl * E * kTile * esz, 0);
+      std::vector<float> g32_l(wform ? (size_t)ntl * E32 * kTile : 0, 0.f);
+      std::vector<float2> wq_l(wform ? (size_t)ntl * EW * kTile : 0, make_float2(0.f, 0.f));
+      std::vector<int32_t> nbr_l((size_t)ntl * SL * kTile, 0);
+      std::vector<uint8_t> smask_l((size_t)ntl * kTile, 0);
+      for (size_t i = 0; i < comp.size(); ++i) {
+        const int32_t c = comp[i];
+        const int64_t k = slot_of_tile[c / kTile], lane = c % kTile;
+        const int64_t kl = pos[i] / kTile, ll = pos[i] % kTile;
+        for (int e = 0; e < E; ++e)
+          memcpy(&ahat_l[(((size_t)kl * E + e) * kTile + ll) * esz],
+                 &ahat[(((size_t)k * E + e) * kTile + lane) * esz], esz);
+        if (wform) {
+          for (int e = 0; e < E32; ++e)
+            g32_l[((size_t)kl * E32 + e) * kTile + ll] = g32[((size_t)k * E32 + e) * kTile + lane];
+          for (int e = 0; e < EW; ++e)
+            wq_l[((size_t)kl * EW + e) * kTile + ll] = wq[((size_t)k * EW + e) * kTile + lane];
+        }
+        for (int s = 0; s < SL; ++s)
+          nbr_l[((size_t)kl * SL + s) * kTile + ll] =
+              glob2loc[nbr[((size_t)k * SL + s) * kTile + lane]];
+        smask_l[(size_t)kl * kTile + ll] = smask[(size_t)k * kTile + lane];
+      }
+      // every local tile's halo within kHaloMax cells?
+      bool ok = true;
+      std::vector<int32_t> ids;
+      for (int64_t t = 0; t < ntl && ok; ++t) {
+        const int32_t* tn = &nbr_l[(size_t)t * SL * kTile];
+        ids.assign(tn, tn + (size_t)SL * kTile);
+        std::sort(ids.begin(), ids.end());
+        ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+        ok = (int)ids.size() <= kHaloMax;
+      }
+      if (!ok && fill > 4) continue;
+      ahat.swap(ahat_l);
+      g32.swap(g32_l);
+      wq.swap(wq_l);
+      nbr.swap(nbr_l);
+      smask.swap(smask_l);
+      ntile = ntl;
+      n_valid = n_recon;
+      n_state = nrp + (int64_t)halo.size();
+      ctx->n_own = n_own;
+      ctx->n_comp = n_recon;
+      ctx->loc2glob.assign(n_state, -1);
+      for (int64_t g = 0; g < nc; ++g)
+        if (glob2loc[g] >= 0) ctx->loc2glob[glob2loc[g]] = (int32_t)g;
+      // receive lists: halo and boundary-layer cells by owning part, ascending
+      // global id
+      ctx->recv_loc.assign(n_parts, {});
+      std::vector<int32_t> foreign(pc.layer1);
+      foreign.insert(foreign.end(), halo.begin(), halo.end());
+      std::sort(foreign.begin(), foreign.end());
+      for (int32_t g : foreign) {
+        const int32_t q = (int32_t)(std::upper_bound(ctx->part_bounds.begin(),
+                                                     ctx->part_bounds.end(), (int64_t)g) -
+                                    ctx->part_bounds.begin()) - 1;
+        ctx->recv_loc[q].push_back(glob2loc[g]);
+      }
+      break;
+    }
+  }
+  const int64_t npad = ntile * kTile;
   // reverse stencil adjacency (adjoint gather): for every cell the d_bar
   // entries (tile * SL + slot) * 32 + lane of the slots that hold it (int32:
   // built for meshes with npad * SL < 2^31; the adjoint refuses larger ones)
   ctx->rev_off_h.clear();
   ctx->rev_idx_h.clear();
   if ((int64_t)npad * SL < ((int64_t)1 << 31)) {
-    std::vector<int64_t> cnt(nc + 1, 0);
-    for (int64_t c = 0; c < nc; ++c) {
+    std::vector<int64_t> cnt(n_state + 1, 0);
+    for (int64_t c = 0; c < n_valid; ++c) {
       const int64_t tile = c / kTile, lane = c % kTile;
       for (int s = 0; s < SL; ++s) {
         if (s >= ns && !((smask[c] >> ((s - ns) / kSmallN)) & 1)) continue;
         cnt[nbr[((size_t)tile * SL + s) * kTile + lane] + 1]++;
       }
     }
-    for (int64_t c = 0; c < nc; ++c) cnt[c + 1] += cnt[c];
+    for (int64_t c = 0; c < n_state; ++c) cnt[c + 1] += cnt[c];
     ctx->rev_off_h = cnt;
-    ctx->rev_idx_h.assign(cnt[nc], 0);
+    ctx->rev_idx_h.assign(cnt[n_state], 0);
     std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
-    for (int64_t c = 0; c < nc; ++c) {
+    for (int64_t c = 0; c < n_valid; ++c) {
       const int64_t tile = c / kTile, lane = c % kTile;
       for (int s = 0; s < SL; ++s) {
         if (s >= ns && !((smask[c] >> ((s - ns) / kSmallN)) & 1)) continue;
@@ -988,7 +1169,7 @@ int run_precompute(teno_ctx* ctx) {
       }
       // halo position (bits 0-7) and, for the adjoint, the lane's rank among
       // the tile's valid lanes with the same position in the slot (bits 8-12)
-      const int nval = (int)std::min<int64_t>(kTile, nc - t * kTile);
+      const int nval = (int)std::min<int64_t>(kTile, n_valid - t * kTile);
       for (int s = 0; s < SL; ++s)
         for (int ln = 0; ln < kTile; ++ln) {
           const size_t i = (size_t)s * kTile + ln;
@@ -1007,9 +1188,9 @@ int run_precompute(teno_ctx* ctx) {
   ctx->hrev_off_h.clear();
   ctx->hrev_idx_h.clear();
   if (halo_ok) {
-    std::vector<int64_t> cnt(nc + 1, 0);
+    std::vector<int64_t> cnt(n_state + 1, 0);
     for (int32_t j : hids) cnt[(size_t)j + 1]++;
-    for (int64_t c = 0; c < nc; ++c) cnt[c + 1] += cnt[c];
+    for (int64_t c = 0; c < n_state; ++c) cnt[c + 1] += cnt[c];
     ctx->hrev_off_h = cnt;
     ctx->hrev_idx_h.assign(hids.size(), 0);
     std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
@@ -1195,7 +1376,21 @@ int upload_mesh(teno_ctx* ctx) {
   DeviceMesh& dm = ctx->dm;
   dm.n_cell = nc;
   dm.n_pad = npad;
+  dm.n_recon = nc;
+  dm.n_update = nc;
   dm.n_face = ctx->nface;
+  ctx->sn = nc;
+  ctx->spad = npad;
+  ctx->io_n = nc;
+  ctx->part_n = 1;
+  ctx->part_id = 0;
+  ctx->n_own = ctx->n_comp = nc;
+  ctx->h_fcells.swap(fcells);
+  ctx->h_fedges.swap(fedges);
+  ctx->h_fgeom.swap(fgeom);
+  ctx->h_cfaces.swap(cfaces);
+  ctx->h_inv_area.swap(inv_area);
+  ctx->h_cfl_len.swap(cfl_len);
   dm.f_cells = (const int32_t*)ctx->b_fcells.p;
   dm.f_edges = (const int8_t*)ctx->b_fedges.p;
   dm.f_geom = (const double*)ctx->b_fgeom.p;
@@ -1204,6 +1399,103 @@ int upload_mesh(teno_ctx* ctx) {
   dm.inv_area = (const double*)ctx->b_inv_area.p;
   dm.cfl_len = (const double*)ctx->b_cfl_len.p;
   dm.cfl_ilen2 = (const float2*)ctx->b_cfl_ilen2.p;
+  return TENO_OK;
+}
+
+// Device mesh of a partition (after run_precompute built its layout): the
+// faces touching owned cells (the global faces, owner and orientation
+// unchanged, so each face flux is the same computation as on the whole
+// mesh), the cell -> face map and geometry of the compute cells, and the
+// permutations of the state extraction (local cell -> global user id) and of
+// the owned output (identity).
+int upload_partition_mesh(teno_ctx* ctx) {
+  const int64_t nc = ctx->nc, n_own = ctx->n_own, n_comp = ctx->n_comp;
+  const int64_t sn = (int64_t)ctx->loc2glob.size();
+  const int64_t spad = (sn + kTile - 1) / kTile * kTile;
+  std::vector<int32_t> glob2loc(nc, -1);
+  for (int64_t l = 0; l < sn; ++l)
+    if (ctx->loc2glob[l] >= 0) glob2loc[ctx->loc2glob[l]] = (int32_t)l;
+  std::vector<int64_t> gf;
+  for (int64_t l = 0; l < n_own; ++l) {
+    const int32_t g = ctx->loc2glob[l];
+    for (int e = 0; e < 3; ++e) gf.push_back(ctx->h_cfaces[3 * (size_t)g + e] >> 1);
+  }
+  std::sort(gf.begin(), gf.end());
+  gf.erase(std::unique(gf.begin(), gf.end()), gf.end());
+  const int64_t nf = (int64_t)gf.size();
+  std::vector<int32_t> fcells(2 * nf), cfaces(3 * (size_t)spad, 0);
+  std::vector<int8_t> fedges(2 * nf);
+  std::vector<double> fgeom(5 * nf);
+  std::vector<float2> fgeom2(3 * nf);
+  for (int64_t f = 0; f < nf; ++f) {
+    const int64_t g = gf[f];
+    const int32_t o = ctx->h_fcells[2 * g], n = ctx->h_fcells[2 * g + 1];
+    fcells[2 * f] = glob2loc[o];
+    fcells[2 * f + 1] = n >= 0 ? glob2loc[n] : -1;
+    fedges[2 * f] = ctx->h_fedges[2 * g];
+    fedges[2 * f + 1] = ctx->h_fedges[2 * g + 1];
+    for (int i = 0; i < 5; ++i) fgeom[5 * f + i] = ctx->h_fgeom[5 * g + i];
+    for (int i = 0; i < 3; ++i) {
+      const double x = fgeom[5 * f + i];
+      const float h = (float)x;
+      fgeom2[3 * f + i] = make_float2(h, (float)(x - (double)h));
+    }
+    // both sides' cell -> face entries where the side is a compute cell
+    const int e0 = ctx->h_fedges[2 * g];
+    cfaces[3 * (size_t)glob2loc[o] + e0] = (int32_t)(2 * f);
+    if (n >= 0 && glob2loc[n] >= 0 && glob2loc[n] < n_comp)
+      cfaces[3 * (size_t)glob2loc[n] + ctx->h_fedges[2 * g + 1]] = (int32_t)(2 * f + 1);
+  }
+  std::vector<double> inv_area(spad, 0.0), cfl_len(spad, 1.0);
+  std::vector<float2> ilen2(spad);
+  std::vector<int32_t> perm_in(sn, 0), perm_out(n_own);
+  for (int64_t l = 0; l < spad; ++l) {
+    const int32_t g = l < sn ? ctx->loc2glob[l] : -1;
+    if (g >= 0 && l < n_comp) {
+      inv_area[l] = ctx->h_inv_area[g];
+      cfl_len[l] = ctx->h_cfl_len[g];
+    }
+    const double x = 1.0 / cfl_len[l];
+    const float h = (float)x;
+    ilen2[l] = make_float2(h, (float)(x - (double)h));
+    if (l < sn) perm_in[l] = g >= 0 ? ctx->perm[g] : 0;
+  }
+  for (int64_t l = 0; l < n_own; ++l) perm_out[l] = (int32_t)l;
+  int rc = upload(ctx, ctx->b_fcells, fcells.data(), std::max<size_t>(1, fcells.size()) * 4);
+  if (!rc) rc = upload(ctx, ctx->b_fedges, fedges.data(), std::max<size_t>(1, fedges.size()));
+  if (!rc) rc = upload(ctx, ctx->b_fgeom, fgeom.data(), std::max<size_t>(1, fgeom.size()) * 8);
+  if (!rc) rc = upload(ctx, ctx->b_fgeom2, fgeom2.data(), std::max<size_t>(1, fgeom2.size()) * 8);
+  if (!rc) rc = upload(ctx, ctx->b_cfaces, cfaces.data(), cfaces.size() * 4);
+  if (!rc) rc = upload(ctx, ctx->b_inv_area, inv_area.data(), inv_area.size() * 8);
+  if (!rc) rc = upload(ctx, ctx->b_cfl_len, cfl_len.data(), cfl_len.size() * 8);
+  if (!rc) rc = upload(ctx, ctx->b_cfl_ilen2, ilen2.data(), ilen2.size() * sizeof(float2));
+  if (!rc) rc = upload(ctx, ctx->b_perm_in, perm_in.data(), perm_in.size() * 4);
+  if (!rc) rc = upload(ctx, ctx->b_perm, perm_out.data(), std::max<size_t>(1, perm_out.size()) * 4);
+  const int32_t P = ctx->part_n;
+  ctx->b_recv_idx.resize(P);
+  ctx->b_send_idx.resize(P);
+  ctx->b_xbuf.resize(2 * P);
+  for (int32_t q = 0; q < P && !rc; ++q)
+    rc = upload(ctx, ctx->b_recv_idx[q], ctx->recv_loc[q].data(),
+                std::max<size_t>(1, ctx->recv_loc[q].size()) * 4);
+  if (rc) return rc;
+  DeviceMesh& dm = ctx->dm;
+  dm.n_cell = sn;
+  dm.n_pad = spad;
+  dm.n_recon = n_comp;
+  dm.n_update = n_own;
+  dm.n_face = nf;
+  dm.f_cells = (const int32_t*)ctx->b_fcells.p;
+  dm.f_edges = (const int8_t*)ctx->b_fedges.p;
+  dm.f_geom = (const double*)ctx->b_fgeom.p;
+  dm.f_geom2 = (const float2*)ctx->b_fgeom2.p;
+  dm.c_faces = (const int32_t*)ctx->b_cfaces.p;
+  dm.inv_area = (const double*)ctx->b_inv_area.p;
+  dm.cfl_len = (const double*)ctx->b_cfl_len.p;
+  dm.cfl_ilen2 = (const float2*)ctx->b_cfl_ilen2.p;
+  ctx->sn = sn;
+  ctx->spad = spad;
+  ctx->io_n = n_own;
   return TENO_OK;
 }
 
@@ -1242,6 +1534,8 @@ int check_ready(teno_ctx* ctx, bool need_state) {
 }
 
 // copy a user-order [n_var][n_cell] array into an internal-order buffer
+// (a partition extracts its state cells, owned and halo, from the whole
+// mesh's array)
 int to_internal(teno_ctx* ctx, const double* src, double* dst, int on_device) {
   const int64_t nc = ctx->nc;
   const int nvar = ctx->prm.n_var;
@@ -1252,17 +1546,19 @@ int to_internal(teno_ctx* ctx, const double* src, double* dst, int on_device) {
        "H2D");
     s = (const double*)ctx->b_tmp.p;
   }
-  CK(launch_permute(s, dst, (const int32_t*)ctx->b_perm.p, nc, nc, ctx->npad, nvar, 0,
-                    ctx->stream),
+  const bool part = ctx->part_n > 1;
+  CK(launch_permute(s, dst, (const int32_t*)(part ? ctx->b_perm_in.p : ctx->b_perm.p),
+                    part ? ctx->sn : nc, nc, ctx->spad, nvar, 0, ctx->stream),
      "permute");
   return TENO_OK;
 }
 
+// (a partition returns its owned cells, [n_var][n_owned] in its owned order)
 int to_user(teno_ctx* ctx, const double* src, double* dst, int on_device) {
-  const int64_t nc = ctx->nc;
+  const int64_t nc = ctx->io_n;
   const int nvar = ctx->prm.n_var;
   double* d = on_device ? dst : (double*)ctx->b_tmp.p;
-  CK(launch_permute(src, d, (const int32_t*)ctx->b_perm.p, nc, ctx->npad, nc, nvar, 1,
+  CK(launch_permute(src, d, (const int32_t*)ctx->b_perm.p, nc, ctx->spad, nc, nvar, 1,
                     ctx->stream),
      "permute");
   if (!on_device) {
@@ -1275,7 +1571,7 @@ int to_user(teno_ctx* ctx, const double* src, double* dst, int on_device) {
 
 int ensure_adjoint(teno_ctx* ctx) {
   if (ctx->adj_ok) return TENO_OK;
-  const int64_t npad = ctx->npad, nc = ctx->nc;
+  const int64_t npad = ctx->spad, nc = ctx->sn;
   const int nv = ctx->prm.n_var;
   const size_t ntile = npad / kTile;
   // tiled VJP with the W-form reconstruction (variant 2, FP64 path, Euler,
@@ -1315,6 +1611,10 @@ int ensure_adjoint(teno_ctx* ctx) {
     if (!rc) rc = dev_alloc(ctx, ctx->b_sel_st[k], (size_t)nv * npad);
   }
   if (rc) return rc;
+  // a partition's VJP leaves the Gauss slots of boundary-layer edges that
+  // face no owned cell, and the own terms of halo cells, unwritten: zero
+  CK(cudaMemsetAsync(ctx->b_Uqbar.p, 0, ctx->b_Uqbar.bytes, ctx->stream), "memset");
+  CK(cudaMemsetAsync(ctx->b_uself.p, 0, ctx->b_uself.bytes, ctx->stream), "memset");
   ctx->adj_ok = true;
   return TENO_OK;
 }
@@ -1477,6 +1777,9 @@ int teno_destroy(teno_ctx* ctx) {
                     &ctx->b_selA, &ctx->b_Uq_st[0], &ctx->b_Uq_st[1], &ctx->b_sel_st[0],
                     &ctx->b_sel_st[1]};
   for (DevBuf* b : bufs) dev_free(*b);
+  dev_free(ctx->b_perm_in);
+  for (auto* v : {&ctx->b_recv_idx, &ctx->b_send_idx, &ctx->b_xbuf})
+    for (DevBuf& b : *v) dev_free(b);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;
   return TENO_OK;
@@ -1524,7 +1827,7 @@ int teno_get_permutation(teno_ctx* ctx, int32_t* perm) {
   return TENO_OK;
 }
 
-int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
+static int precompute_impl(teno_ctx* ctx, const teno_params* p, int32_t n_parts, int32_t part) {
   if (!ctx || !p) return TENO_EINVAL;
   if (!ctx->mesh_ok) return fail(ctx, TENO_ESTATE, "precompute before mesh_load");
   if (p->order < 3 || p->order > 6 || (p->n_var != 1 && p->n_var != 4) ||
@@ -1545,8 +1848,16 @@ int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
     return fail(ctx, TENO_EINVAL, "precompute: only the default Gauss point count is built");
   if (!ctx->periodic && p->n_var != 4)
     return fail(ctx, TENO_EINVAL, "precompute: boundary conditions need the Euler equations");
+  if (n_parts > 1 && (p->adv_field != 0 || p->charvar != 0))
+    return fail(ctx, TENO_EINVAL,
+                "partition: constant advection velocity and conservative variables only");
   if (ctx->device >= 0) CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   ctx->pre_ok = ctx->state_ok = ctx->adj_ok = ctx->stages_ok = false;
+  if (ctx->part_n > 1 && n_parts == 1) {
+    // back from a partition to the whole mesh: its faces and geometry again
+    int r0 = upload_mesh(ctx);
+    if (r0) return r0;
+  }
   ctx->override_on = false;
   ctx->prm = *p;
   ctx->nq = nq_default;
@@ -1554,16 +1865,22 @@ int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
   ctx->ns = 2 * (ctx->m + 1);
   ctx->E = ctx->m * ctx->ns + kSmallK * kSmallN * kSmallM;
   ctx->SL = ctx->ns + kSmallK * kSmallN;
-  int rc = run_precompute(ctx);
-  if (rc) return rc;
-  const int64_t npad = ctx->npad;
+  ctx->part_n = n_parts;
+  ctx->part_id = part;
+  int rc = run_precompute(ctx, n_parts, part);
+  if (!rc && n_parts > 1) rc = upload_partition_mesh(ctx);
+  if (rc) {
+    ctx->part_n = 1;
+    return rc;
+  }
+  const int64_t npad = ctx->spad;
   const int nv = p->n_var;
   const size_t tsz = p->precision == TENO_FP32_MIXED ? 4 : 8;
   rc = dev_alloc(ctx, ctx->b_U, 8 * nv * npad);
   if (!rc) rc = dev_alloc(ctx, ctx->b_U1, 8 * nv * npad);
   if (!rc) rc = dev_alloc(ctx, ctx->b_U2, 8 * nv * npad);
   if (!rc) rc = dev_alloc(ctx, ctx->b_R, 8 * nv * npad);
-  if (!rc) rc = dev_alloc(ctx, ctx->b_tmp, 8 * nv * npad);
+  if (!rc) rc = dev_alloc(ctx, ctx->b_tmp, 8 * nv * std::max(npad, ctx->nc));
   if (!rc) rc = dev_alloc(ctx, ctx->b_Uq, tsz * npad * 3 * ctx->nq * nv);
   if (!rc) rc = dev_alloc(ctx, ctx->b_K, tsz * std::max<int64_t>(1, ctx->nface) * nv);
   if (!rc) rc = dev_alloc(ctx, ctx->b_sel, (size_t)nv * npad);
@@ -1578,9 +1895,23 @@ int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
   CK(cudaMemsetAsync(ctx->b_U.p, 0, ctx->b_U.bytes, ctx->stream), "memset");
   CK(cudaMemsetAsync(ctx->b_U1.p, 0, ctx->b_U1.bytes, ctx->stream), "memset");
   CK(cudaMemsetAsync(ctx->b_U2.p, 0, ctx->b_U2.bytes, ctx->stream), "memset");
+  if (ctx->b_Usplit.p)
+    CK(cudaMemsetAsync(ctx->b_Usplit.p, 0, ctx->b_Usplit.bytes, ctx->stream), "memset");
   CK(cudaStreamSynchronize(ctx->stream), "sync");
   ctx->pre_ok = true;
   return TENO_OK;
+}
+
+int teno_precompute_stencils(teno_ctx* ctx, const teno_params* p) {
+  return precompute_impl(ctx, p, 1, 0);
+}
+
+int teno_precompute_partition(teno_ctx* ctx, const teno_params* p, int32_t n_parts,
+                              int32_t part) {
+  if (!ctx || !p) return TENO_EINVAL;
+  if (n_parts < 1 || part < 0 || part >= n_parts)
+    return fail(ctx, TENO_EINVAL, "partition: bad part");
+  return precompute_impl(ctx, p, n_parts, part);
 }
 
 int teno_get_stencils(teno_ctx* ctx, int32_t* large, int32_t* small) {
@@ -1646,17 +1977,17 @@ int teno_residual(teno_ctx* ctx, double* R, uint8_t* sel, int on_device) {
     const uint8_t* src = ctx->override_on ? (const uint8_t*)ctx->b_sel_ovr.p
                                           : (const uint8_t*)ctx->b_sel.p;
     if (on_device) {
-      CK(launch_permute_u8(src, sel, (const int32_t*)ctx->b_perm.p, ctx->nc, ctx->npad, ctx->nc,
-                           ctx->prm.n_var, 1, ctx->stream),
+      CK(launch_permute_u8(src, sel, (const int32_t*)ctx->b_perm.p, ctx->io_n, ctx->spad,
+                           ctx->io_n, ctx->prm.n_var, 1, ctx->stream),
          "permute");
     } else {
-      rc = dev_alloc(ctx, ctx->b_vtmp, sizeof(double) * ctx->prm.n_var * ctx->npad);
+      rc = dev_alloc(ctx, ctx->b_vtmp, sizeof(double) * ctx->prm.n_var * ctx->spad);
       if (rc) return rc;
       uint8_t* d = (uint8_t*)ctx->b_vtmp.p;
-      CK(launch_permute_u8(src, d, (const int32_t*)ctx->b_perm.p, ctx->nc, ctx->npad, ctx->nc,
-                           ctx->prm.n_var, 1, ctx->stream),
+      CK(launch_permute_u8(src, d, (const int32_t*)ctx->b_perm.p, ctx->io_n, ctx->spad,
+                           ctx->io_n, ctx->prm.n_var, 1, ctx->stream),
          "permute");
-      CK(cudaMemcpyAsync(sel, d, (size_t)ctx->prm.n_var * ctx->nc, cudaMemcpyDeviceToHost,
+      CK(cudaMemcpyAsync(sel, d, (size_t)ctx->prm.n_var * ctx->io_n, cudaMemcpyDeviceToHost,
                          ctx->stream),
          "D2H");
     }
@@ -1679,8 +2010,10 @@ int teno_set_selection_override(teno_ctx* ctx, const uint8_t* sel, int on_device
        "H2D");
     s = (const uint8_t*)ctx->b_tmp.p;
   }
-  CK(launch_permute_u8(s, (uint8_t*)ctx->b_sel_ovr.p, (const int32_t*)ctx->b_perm.p, nc, nc,
-                       ctx->npad, nv, 0, ctx->stream),
+  const bool part = ctx->part_n > 1;
+  CK(launch_permute_u8(s, (uint8_t*)ctx->b_sel_ovr.p,
+                       (const int32_t*)(part ? ctx->b_perm_in.p : ctx->b_perm.p),
+                       part ? ctx->sn : nc, nc, ctx->spad, nv, 0, ctx->stream),
      "permute");
   CK(cudaStreamSynchronize(ctx->stream), "sync");
   ctx->override_on = true;
@@ -1741,6 +2074,9 @@ static int rk3_once(teno_ctx* ctx, double dt, double* dt_used) {
 int teno_rk3_step(teno_ctx* ctx, double dt, double* dt_used) {
   int rc = check_ready(ctx, true);
   if (rc) return rc;
+  if (ctx->part_n > 1)
+    return fail(ctx, TENO_EINVAL,
+                "partition: step with teno_group_rk3_step, or teno_rk3_stage and halo exchanges");
   rc = rk3_once(ctx, dt, dt_used);
   if (rc) return rc;
   if (dt_used) return teno_check_state(ctx);
@@ -1758,6 +2094,9 @@ int teno_get_stage_state(teno_ctx* ctx, int32_t stage, double* U, int on_device)
 int teno_rk3_steps(teno_ctx* ctx, int32_t n_steps, double dt) {
   int rc = check_ready(ctx, true);
   if (rc) return rc;
+  if (ctx->part_n > 1)
+    return fail(ctx, TENO_EINVAL,
+                "partition: step with teno_group_rk3_step, or teno_rk3_stage and halo exchanges");
   if (n_steps < 0) return fail(ctx, TENO_EINVAL, "rk3_steps: negative count");
   for (int32_t i = 0; i < n_steps && !rc; ++i) rc = rk3_once(ctx, dt, nullptr);
   return rc;
@@ -1779,6 +2118,9 @@ int teno_check_state(teno_ctx* ctx) {
 int teno_residual_vjp(teno_ctx* ctx, const double* w, double* v, int on_device) {
   int rc = check_ready(ctx, true);
   if (rc) return rc;
+  if (ctx->part_n > 1)
+    return fail(ctx, TENO_EINVAL, "partition: the VJP needs the reverse halo exchange "
+                                  "(teno_group_residual_vjp)");
   if (!w || !v) return fail(ctx, TENO_EINVAL, "residual_vjp: null pointer");
   if (ctx->prm.precision == TENO_FP32_MIXED)
     return fail(ctx, TENO_EINVAL, "adjoint: FP64 precisions only");
@@ -1799,6 +2141,8 @@ int teno_adjoint_step(teno_ctx* ctx, double dt, const double* lam_np1, double* l
                       int on_device) {
   int rc = check_ready(ctx, true);
   if (rc) return rc;
+  if (ctx->part_n > 1)
+    return fail(ctx, TENO_EINVAL, "partition: adjoint steps take the whole mesh");
   if (!lam_np1 || !lam_n || !(dt > 0.0)) return fail(ctx, TENO_EINVAL, "adjoint_step: bad args");
   if (ctx->prm.precision == TENO_FP32_MIXED)
     return fail(ctx, TENO_EINVAL, "adjoint: FP64 precisions only");
@@ -1808,7 +2152,7 @@ int teno_adjoint_step(teno_ctx* ctx, double dt, const double* lam_np1, double* l
   rc = ensure_adjoint(ctx);
   if (rc) return rc;
   ctx->stages_ok = false;  // the replay below overwrites the stage buffers
-  const int64_t n = (int64_t)ctx->prm.n_var * ctx->npad;
+  const int64_t n = (int64_t)ctx->prm.n_var * ctx->spad;
   double* U = (double*)ctx->b_U.p;
   double* U1 = (double*)ctx->b_U1.p;
   double* U2 = (double*)ctx->b_U2.p;
@@ -1854,12 +2198,12 @@ int teno_edge_values(teno_ctx* ctx, double* out) {
   std::vector<double> h64;
   std::vector<float> h32;
   if (f64) {
-    h64.resize(ctx->npad * per);
+    h64.resize(ctx->spad * per);
     CK(cudaMemcpyAsync(h64.data(), ctx->b_Uq.p, h64.size() * 8, cudaMemcpyDeviceToHost,
                        ctx->stream),
        "D2H");
   } else {
-    h32.resize(ctx->npad * per);
+    h32.resize(ctx->spad * per);
     CK(cudaMemcpyAsync(h32.data(), ctx->b_Uq.p, h32.size() * 4, cudaMemcpyDeviceToHost,
                        ctx->stream),
        "D2H");
@@ -1868,8 +2212,8 @@ int teno_edge_values(teno_ctx* ctx, double* out) {
   // the FP64 path keeps Gauss-point values as (hi, lo) float pairs
   const bool pairs = ctx->prm.precision == TENO_FP64;
   const float* hp = reinterpret_cast<const float*>(h64.data());
-  for (int64_t c = 0; c < ctx->nc; ++c) {
-    const int64_t u = ctx->perm[c];
+  for (int64_t c = 0; c < ctx->io_n; ++c) {
+    const int64_t u = ctx->part_n > 1 ? c : ctx->perm[c];
     for (int64_t i = 0; i < per; ++i) {
       const int64_t k = c * per + i;
       out[u * per + i] = pairs ? (double)hp[2 * k] + (double)hp[2 * k + 1]
@@ -1908,4 +2252,312 @@ int teno_profile_read(teno_ctx* ctx, double* ms, int64_t* launches) {
   return TENO_OK;
 }
 
+
+// ------------------------------------------------------------------ partitions
+
+int teno_partition_sizes(teno_ctx* ctx, int64_t* n_owned, int64_t* n_state,
+                         int64_t* recv_counts, int64_t* send_counts) {
+  if (!ctx) return TENO_EINVAL;
+  if (!ctx->pre_ok) return fail(ctx, TENO_ESTATE, "partition_sizes: no precompute");
+  if (n_owned) *n_owned = ctx->n_own;
+  if (n_state) *n_state = ctx->sn;
+  for (int32_t q = 0; q < ctx->part_n; ++q) {
+    const bool part = ctx->part_n > 1;
+    if (recv_counts) recv_counts[q] = part ? (int64_t)ctx->recv_loc[q].size() : 0;
+    if (send_counts)
+      send_counts[q] = part && (size_t)q < ctx->send_loc.size() ? (int64_t)ctx->send_loc[q].size()
+                                                                : 0;
+  }
+  return TENO_OK;
+}
+
+int teno_partition_cells(teno_ctx* ctx, int32_t* owned_user) {
+  if (!ctx || !owned_user) return TENO_EINVAL;
+  if (!ctx->pre_ok) return fail(ctx, TENO_ESTATE, "partition_cells: no precompute");
+  const int64_t c0 = ctx->part_n > 1 ? ctx->part_bounds[ctx->part_id] : 0;
+  for (int64_t l = 0; l < ctx->n_own; ++l) owned_user[l] = ctx->perm[c0 + l];
+  return TENO_OK;
+}
+
+int teno_partition_recv_cells(teno_ctx* ctx, int32_t peer, int32_t* user_ids) {
+  if (!ctx || !user_ids) return TENO_EINVAL;
+  if (!ctx->pre_ok || ctx->part_n < 2) return fail(ctx, TENO_ESTATE, "not a partition");
+  if (peer < 0 || peer >= ctx->part_n) return fail(ctx, TENO_EINVAL, "bad peer");
+  const std::vector<int32_t>& r = ctx->recv_loc[peer];
+  for (size_t i = 0; i < r.size(); ++i) user_ids[i] = ctx->perm[ctx->loc2glob[r[i]]];
+  return TENO_OK;
+}
+
+int teno_partition_set_send(teno_ctx* ctx, int32_t peer, int64_t n, const int32_t* user_ids) {
+  if (!ctx || (n > 0 && !user_ids) || n < 0) return TENO_EINVAL;
+  if (!ctx->pre_ok || ctx->part_n < 2) return fail(ctx, TENO_ESTATE, "not a partition");
+  if (peer < 0 || peer >= ctx->part_n || peer == ctx->part_id)
+    return fail(ctx, TENO_EINVAL, "bad peer");
+  const int64_t c0 = ctx->part_bounds[ctx->part_id], c1 = ctx->part_bounds[ctx->part_id + 1];
+  std::vector<int32_t> loc((size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t u = user_ids[i];
+    if (u < 0 || u >= ctx->nc) return fail(ctx, TENO_EINVAL, "set_send: user id out of range");
+    const int64_t g = ctx->iperm[u];
+    if (g < c0 || g >= c1) return fail(ctx, TENO_EINVAL, "set_send: cell not owned here");
+    loc[i] = (int32_t)(g - c0);
+  }
+  if (ctx->send_loc.size() != (size_t)ctx->part_n) ctx->send_loc.assign(ctx->part_n, {});
+  ctx->send_loc[peer].swap(loc);
+  if (ctx->device >= 0) {
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    int rc = upload(ctx, ctx->b_send_idx[peer], ctx->send_loc[peer].data(),
+                    std::max<size_t>(1, ctx->send_loc[peer].size()) * 4);
+    if (rc) return rc;
+  }
+  return TENO_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+double* stage_array(teno_ctx* ctx, int32_t what) {
+  return (double*)(what == 0 ? ctx->b_U.p : what == 1 ? ctx->b_U1.p
+                                          : what == 2 ? ctx->b_U2.p : ctx->b_vtmp.p);
+}
+
+// pack into buf: the owned cells `peer` receives (what 0..2: U^n, U^(1),
+// U^(2)), or this partition's adjoint contributions to the halo cells `peer`
+// owns (what 3)
+int halo_pack(teno_ctx* ctx, int32_t peer, int32_t what, double* buf) {
+  const bool rev = what == 3;
+  if (!rev && (ctx->send_loc.size() != (size_t)ctx->part_n))
+    return fail(ctx, TENO_ESTATE, "halo_pack: send lists not set");
+  const std::vector<int32_t>& l = rev ? ctx->recv_loc[peer] : ctx->send_loc[peer];
+  const DevBuf& idx = rev ? ctx->b_recv_idx[peer] : ctx->b_send_idx[peer];
+  CK(launch_halo_pack(stage_array(ctx, what), ctx->spad, (const int32_t*)idx.p, (int64_t)l.size(),
+                      ctx->prm.n_var, buf, ctx->stream),
+     "halo pack");
+  return TENO_OK;
+}
+
+// the inverse: write the received states into the halo (with their FP32
+// split on the pair and mixed paths), or add the received contributions to
+// the owned cells (what 3)
+int halo_unpack(teno_ctx* ctx, int32_t peer, int32_t what, const double* buf) {
+  const bool rev = what == 3;
+  if (rev && (ctx->send_loc.size() != (size_t)ctx->part_n))
+    return fail(ctx, TENO_ESTATE, "halo_unpack: send lists not set");
+  const std::vector<int32_t>& l = rev ? ctx->send_loc[peer] : ctx->recv_loc[peer];
+  const DevBuf& idx = rev ? ctx->b_send_idx[peer] : ctx->b_recv_idx[peer];
+  float2* Us = (!rev && ctx->prm.precision != TENO_FP64_NATIVE) ? (float2*)ctx->b_Usplit.p : nullptr;
+  CK(launch_halo_unpack(stage_array(ctx, what), ctx->spad, (const int32_t*)idx.p,
+                        (int64_t)l.size(), ctx->prm.n_var, buf, Us, rev ? 1 : 0, ctx->stream),
+     "halo unpack");
+  return TENO_OK;
+}
+
+// stage 1..3 of the SSP-RK3 step (Eq. fv_time_discretization_01) on the
+// updated cells; the halo of the stage's input state must be current
+int rk3_stage(teno_ctx* ctx, int32_t stage, double dt) {
+  double* U = (double*)ctx->b_U.p;
+  double* U1 = (double*)ctx->b_U1.p;
+  double* U2 = (double*)ctx->b_U2.p;
+  const double t = ctx->time;
+  int rc = TENO_OK;
+  if (stage == 1) {
+    rc = rk_stage(ctx, U, U, U1, 0.0, 1.0, dt, nullptr, t, ctx->split_ok);
+    ctx->stages_ok = false;
+  } else if (stage == 2) {
+    rc = rk_stage(ctx, U, U1, U2, 0.75, 0.25, dt, nullptr, t + dt, true);
+  } else {
+    rc = rk_stage(ctx, U, U2, U, 1.0 / 3.0, 2.0 / 3.0, dt, nullptr, t + 0.5 * dt, true);
+    if (!rc) {
+      ctx->time += dt;
+      ctx->stages_ok = true;
+    }
+  }
+  ctx->split_ok = ctx->prm.precision != TENO_FP64_NATIVE;
+  return rc;
+}
+
+// largest (|v| + c) / length over the updated cells (host; synchronises)
+int local_max_speed(teno_ctx* ctx, double* lam) {
+  CK(launch_max_lambda(ctx->dm, (const double*)ctx->b_U.p, (double*)ctx->b_maxlam.p, ctx->stream),
+     "max lambda launch");
+  CK(cudaMemcpyAsync(lam, ctx->b_maxlam.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+     "D2H");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return TENO_OK;
+}
+
+// checks of a group of partitions driven in one process: parts[i] is part i
+// of the same mesh, all on one device and one stream, with their states set
+int group_check(teno_ctx* const* parts, int32_t n) {
+  if (!parts || n < 1) return TENO_EINVAL;
+  for (int32_t i = 0; i < n; ++i) {
+    teno_ctx* c = parts[i];
+    if (!c) return TENO_EINVAL;
+    int rc = check_ready(c, true);
+    if (rc) return rc;
+    if (c->part_n != n || c->part_id != i || c->device != parts[0]->device ||
+        c->stream != parts[0]->stream || c->nc != parts[0]->nc ||
+        c->part_bounds != parts[0]->part_bounds || c->prm.n_var != parts[0]->prm.n_var)
+      return fail(c, TENO_EINVAL, "group: parts must be parts 0..n-1 of one mesh, on one "
+                                  "device and one stream");
+  }
+  return TENO_OK;
+}
+
+// the send lists of every part (the cells each peer receives), and the
+// exchange buffers: [q] towards q, [n + q] from q
+int group_link(teno_ctx* const* parts, int32_t n) {
+  for (int32_t p = 0; p < n; ++p) {
+    teno_ctx* cp = parts[p];
+    if (cp->send_loc.size() == (size_t)n) continue;
+    for (int32_t q = 0; q < n; ++q) {
+      if (q == p) continue;
+      const teno_ctx* cq = parts[q];
+      std::vector<int32_t> users(cq->recv_loc[p].size());
+      for (size_t i = 0; i < users.size(); ++i)
+        users[i] = cq->perm[cq->loc2glob[cq->recv_loc[p][i]]];
+      int rc = teno_partition_set_send(cp, q, (int64_t)users.size(), users.data());
+      if (rc) return rc;
+    }
+  }
+  for (int32_t p = 0; p < n; ++p) {
+    teno_ctx* cp = parts[p];
+    for (int32_t q = 0; q < n; ++q) {
+      if (q == p) continue;
+      const size_t nv = cp->prm.n_var;
+      int rc = dev_alloc(cp, cp->b_xbuf[q], 8 * nv * std::max<size_t>(1, cp->send_loc[q].size()));
+      if (!rc) rc = dev_alloc(cp, cp->b_xbuf[n + q],
+                              8 * nv * std::max<size_t>(1, cp->recv_loc[q].size()));
+      if (rc) return rc;
+    }
+  }
+  return TENO_OK;
+}
+
+// forward (what 0..2): every part's halo of that state from its owners;
+// reverse (what 3): every part's contributions to other parts' cells added
+// there, each owner adding its peers in ascending order.  Pack on the source
+// part, one device-to-device copy, unpack on the destination part.
+int group_exchange(teno_ctx* const* parts, int32_t n, int32_t what) {
+  const bool rev = what == 3;
+  for (int32_t dst = 0; dst < n; ++dst) {
+    teno_ctx* cd = parts[dst];
+    for (int32_t src = 0; src < n; ++src) {
+      if (src == dst) continue;
+      teno_ctx* cs = parts[src];
+      const size_t cnt = rev ? cs->recv_loc[dst].size() : cs->send_loc[dst].size();
+      if (cnt == 0) continue;
+      int rc = halo_pack(cs, dst, what, (double*)cs->b_xbuf[dst].p);
+      if (rc) return rc;
+      teno_ctx* ctx = cd;
+      CK(cudaMemcpyAsync(cd->b_xbuf[n + src].p, cs->b_xbuf[dst].p, 8 * cd->prm.n_var * cnt,
+                         cudaMemcpyDeviceToDevice, cd->stream),
+         "halo copy");
+      rc = halo_unpack(cd, src, what, (const double*)cd->b_xbuf[n + src].p);
+      if (rc) return rc;
+    }
+  }
+  return TENO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int teno_halo_pack(teno_ctx* ctx, int32_t peer, int32_t what, double* buf) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (ctx->part_n < 2 || peer < 0 || peer >= ctx->part_n || peer == ctx->part_id || what < 0 ||
+      what > 3 || !buf)
+    return fail(ctx, TENO_EINVAL, "halo_pack: bad arguments");
+  return halo_pack(ctx, peer, what, buf);
+}
+
+int teno_halo_unpack(teno_ctx* ctx, int32_t peer, int32_t what, const double* buf) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (ctx->part_n < 2 || peer < 0 || peer >= ctx->part_n || peer == ctx->part_id || what < 0 ||
+      what > 3 || !buf)
+    return fail(ctx, TENO_EINVAL, "halo_unpack: bad arguments");
+  return halo_unpack(ctx, peer, what, buf);
+}
+
+int teno_rk3_stage(teno_ctx* ctx, int32_t stage, double dt) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (stage < 1 || stage > 3 || !(dt > 0.0)) return fail(ctx, TENO_EINVAL, "rk3_stage: bad args");
+  return rk3_stage(ctx, stage, dt);
+}
+
+int teno_local_max_speed(teno_ctx* ctx, double* lam) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (!lam) return fail(ctx, TENO_EINVAL, "local_max_speed: null pointer");
+  return local_max_speed(ctx, lam);
+}
+
+int teno_group_rk3_step(teno_ctx* const* parts, int32_t n, double dt, double* dt_used) {
+  int rc = group_check(parts, n);
+  if (rc) return rc;
+  if (n > 1 && (rc = group_link(parts, n))) return rc;
+  if (dt <= 0.0) {
+    double lam = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+      double l = 0.0;
+      if ((rc = local_max_speed(parts[i], &l))) return rc;
+      lam = std::max(lam, l);
+    }
+    if (!(lam > 0.0) || !std::isfinite(lam))
+      return fail(parts[0], TENO_ENONPHYS, "group step: bad speed");
+    dt = parts[0]->prm.cfl / lam;
+  }
+  for (int32_t stage = 1; stage <= 3; ++stage) {
+    for (int32_t i = 0; i < n; ++i)
+      if ((rc = rk3_stage(parts[i], stage, dt))) return rc;
+    if (n > 1 && (rc = group_exchange(parts, n, stage == 3 ? 0 : stage))) return rc;
+  }
+  if (dt_used) *dt_used = dt;
+  return TENO_OK;
+}
+
+int teno_group_residual_vjp(teno_ctx* const* parts, int32_t n, const double* w, double* vout) {
+  int rc = group_check(parts, n);
+  if (rc) return rc;
+  if (!w || !vout) return fail(parts[0], TENO_EINVAL, "group vjp: null pointer");
+  if (n > 1 && (rc = group_link(parts, n))) return rc;
+  for (int32_t i = 0; i < n; ++i) {
+    teno_ctx* ctx = parts[i];
+    if (ctx->prm.precision == TENO_FP32_MIXED || ctx->prm.scheme != 0 || ctx->prm.positivity)
+      return fail(ctx, TENO_EINVAL, "adjoint: FP64 TENO without positivity scaling only");
+    if ((rc = ensure_adjoint(ctx))) return rc;
+    if ((rc = to_internal(ctx, w, (double*)ctx->b_l1.p, 0))) return rc;
+    // cotangents of the cells this part updates only
+    for (int k = 0; k < ctx->prm.n_var; ++k) {
+      double* row = (double*)ctx->b_l1.p + (size_t)k * ctx->spad;
+      CK(cudaMemsetAsync(row + ctx->n_own, 0, sizeof(double) * (ctx->spad - ctx->n_own),
+                         ctx->stream),
+         "memset");
+    }
+    if ((rc = vjp_internal(ctx, (const double*)ctx->b_U.p, (const double*)ctx->b_l1.p,
+                           (double*)ctx->b_vtmp.p, ctx->time)))
+      return rc;
+  }
+  if (n > 1 && (rc = group_exchange(parts, n, 3))) return rc;
+  const int nv = parts[0]->prm.n_var;
+  const int64_t nc = parts[0]->nc;
+  std::vector<double> h;
+  std::vector<int32_t> users;
+  for (int32_t i = 0; i < n; ++i) {
+    teno_ctx* ctx = parts[i];
+    h.resize((size_t)nv * ctx->n_own);
+    users.resize(ctx->n_own);
+    if ((rc = to_user(ctx, (const double*)ctx->b_vtmp.p, h.data(), 0))) return rc;
+    teno_partition_cells(ctx, users.data());
+    for (int k = 0; k < nv; ++k)
+      for (int64_t l = 0; l < ctx->n_own; ++l)
+        vout[(size_t)k * nc + users[l]] = h[(size_t)k * ctx->n_own + l];
+  }
+  return TENO_OK;
+}
 }  // extern "C"

@@ -52,7 +52,12 @@ struct HaloArgs {
 
 // Everything the kernels of one residual evaluation need (device pointers).
 struct DeviceMesh {
-  int64_t n_cell = 0, n_pad = 0, n_face = 0;
+  // n_cell: cells of the state arrays (stride n_pad); n_recon: cells
+  // reconstructed (the first n_recon); n_update: cells whose residual is
+  // gathered and updated (the first n_update).  All three are equal on a
+  // whole mesh; a partition reconstructs its owned cells and the first layer
+  // across its boundary, updates its owned cells and stores its halo too.
+  int64_t n_cell = 0, n_pad = 0, n_face = 0, n_recon = 0, n_update = 0;
   int n_var = 1, order = 3, m = 5, ns = 12, nq = 2, e_entries = 0;
   int flux = 0, precision = 0, linear = 0;
   int variant = 0;          // reconstruction: 0 halo-staged, 1 direct gathers, 2 TMA-staged
@@ -126,6 +131,13 @@ cudaError_t launch_permute_u8(const uint8_t* src, uint8_t* dst, const int32_t* p
                               cudaStream_t st);
 cudaError_t launch_axpby(double* out, const double* a, double ca, const double* b, double cb,
                          int64_t n, cudaStream_t st);
+// halo exchange of a partition: pack buf[v][i] = U[v][idx[i]] (v < n_var,
+// i < n); unpack writes (add = 0) or adds (add = 1) the buffer back, and the
+// FP32 hi/lo split of the written states when Us is non-null
+cudaError_t launch_halo_pack(const double* U, int64_t ld, const int32_t* idx, int64_t n,
+                             int n_var, double* buf, cudaStream_t st);
+cudaError_t launch_halo_unpack(double* U, int64_t ld, const int32_t* idx, int64_t n, int n_var,
+                               const double* buf, float2* Us, int add, cudaStream_t st);
 // adjoint kernels.  Uq_bar ([cell][edge point][var], 8 bytes an entry)
 // holds (hi, lo) float pairs on the TENO_FP64 path and doubles on the native
 // path; the reconstruction VJPs read it in the same form.

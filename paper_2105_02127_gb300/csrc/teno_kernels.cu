@@ -161,8 +161,12 @@ __device__ __forceinline__ T vmax(const T& a, const T& b) { return val(a) >= val
 
 // ------------------------------------------- double-float (FP32 pair) path
 // Values are unevaluated sums hi + lo of two floats (|lo| <= ulp(hi)/2), about
-// 48 significant bits.  Products use the exact FMA residual, sums Knuth's
-// two-sum; the per-cell matrices are stored as (hi, lo) pairs.
+// 48 significant bits: Dekker's double-length arithmetic ("A floating-point
+// technique for extending the available precision", 1971) on FP32.  Sums use
+// Knuth's two-sum (TAOCP vol. 2, 4.2.2), and Dekker's fast two-sum where the
+// operands are ordered; products take the exact residual of a fused
+// multiply-add in place of Dekker's splitting; the per-cell matrices are
+// stored as (hi, lo) pairs.
 // 8-byte aligned so that a pair moves through memory in one access
 struct __align__(8) DF {
   float h, l;
@@ -188,8 +192,10 @@ __device__ __forceinline__ double df_to_double(DF a) { return (double)a.h + (dou
 
 
 // arithmetic on pairs (the Riemann flux of the FP64 path): sums renormalise
-// once (fast two-sum), products use the exact FMA residual, quotients and
-// square roots take one correction step from their FP32 approximation
+// once (Dekker's fast two-sum), products use the exact FMA residual, and
+// quotients and square roots take Dekker's one correction step (div2, sqrt2
+// of the 1971 paper: the exact remainder of the FP32 approximation, from an
+// FMA, divided by the divisor or twice the root)
 __device__ __forceinline__ DF fast_two_sum(float a, float b) {
   const float s = a + b;
   return {s, b - (s - a)};
@@ -2602,6 +2608,35 @@ __global__ void __launch_bounds__(128) positivity_kernel(const double* __restric
     for (int v = 0; v < 4; ++v) q0[q * 4 + v] = from_d<TQ>(W[q][v]);
 }
 
+// Halo exchange of partitioned meshes (copy-based; each kernel touches only
+// its own context's arrays).  pack: buf[v][i] = U[v][idx[i]]; unpack: the
+// reverse, with the FP32 hi/lo split of the written states when Us is given;
+// add = 1 adds instead (the adjoint's contributions returned to their owner).
+__global__ void halo_pack_kernel(const double* __restrict__ U, int64_t ld,
+                                 const int32_t* __restrict__ idx, int64_t n, int n_var,
+                                 double* __restrict__ buf) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t c = idx[i];
+  for (int v = 0; v < n_var; ++v) buf[v * n + i] = U[v * ld + c];
+}
+__global__ void halo_unpack_kernel(double* __restrict__ U, int64_t ld,
+                                   const int32_t* __restrict__ idx, int64_t n, int n_var,
+                                   const double* __restrict__ buf, float2* __restrict__ Us,
+                                   int add) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t c = idx[i];
+  for (int v = 0; v < n_var; ++v) {
+    const double x = add ? U[v * ld + c] + buf[v * n + i] : buf[v * n + i];
+    U[v * ld + c] = x;
+    if (Us) {
+      const float hi = (float)x;
+      Us[v * ld + c] = make_float2(hi, (float)(x - (double)hi));
+    }
+  }
+}
+
 __global__ void split_kernel(const double* __restrict__ U, float2* __restrict__ Us, int64_t n_cell,
                              int64_t n_pad, int n_var) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -3709,7 +3744,7 @@ cudaError_t launch_recon_tma(const ReconArgs& a, const DeviceMesh& dm, int* err,
       cudaSuccess)
     return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
+  const int64_t tiles = (a.n_cell + kTile - 1) / kTile;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)per_sm * sms);
   kern<<<(unsigned)grid, threads, smem, st>>>(a, dm.halo, dm.eval_df, err);
   return cudaGetLastError();
@@ -3732,7 +3767,7 @@ cudaError_t launch_recon_tma_w(const ReconArgs& a, const DeviceMesh& dm, int* er
       cudaSuccess)
     return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
+  const int64_t tiles = (a.n_cell + kTile - 1) / kTile;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)per_sm * sms);
   const void* psi = kN ? (const void*)dm.psi_d : (const void*)dm.psi_df;
   kern<<<(unsigned)grid, threads, P::kSmem, st>>>(a, dm.halo, psi, dm.g32, dm.wq, err);
@@ -3741,7 +3776,7 @@ cudaError_t launch_recon_tma_w(const ReconArgs& a, const DeviceMesh& dm, int* er
 
 cudaError_t launch_char_finish(const DeviceMesh& dm, const double* U, void* Uq, cudaStream_t st) {
   if (!dm.coef_out || dm.n_var != 4) return cudaErrorInvalidValue;
-  const unsigned grid = (unsigned)((dm.n_cell * 3 + 127) / 128);
+  const unsigned grid = (unsigned)((dm.n_recon * 3 + 127) / 128);
   return dispatch_order(dm.order, [&](auto Mc, auto NSc) -> cudaError_t {
     constexpr int M = decltype(Mc)::value;
     (void)NSc;
@@ -3750,7 +3785,7 @@ cudaError_t launch_char_finish(const DeviceMesh& dm, const double* U, void* Uq, 
     auto go = [&](auto tq) -> cudaError_t {
       using TQ = typename decltype(tq)::type;
       char_finish_kernel<M, NQ, TQ><<<grid, 128, 0, st>>>(
-          dm.coef_out, U, dm.smask, dm.c_faces, dm.f_geom, dm.eval, (TQ*)Uq, dm.n_cell, dm.n_pad,
+          dm.coef_out, U, dm.smask, dm.c_faces, dm.f_geom, dm.eval, (TQ*)Uq, dm.n_recon, dm.n_pad,
           dm.gamma, dm.ct, dm.eps, dm.linear);
       return cudaGetLastError();
     };
@@ -3772,7 +3807,7 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
   a.Uq = Uq;
   a.sel_out = sel_out;
   a.sel_in = sel_in;
-  a.n_cell = dm.n_cell;
+  a.n_cell = dm.n_recon;  // the cells reconstructed (all cells, or a partition's compute set)
   a.n_pad = dm.n_pad;
   a.ct = dm.ct;
   a.eps = dm.eps;
@@ -3783,7 +3818,7 @@ cudaError_t launch_recon(const DeviceMesh& dm, const double* U, const float2* Us
   a.coef_out = dm.charvar ? dm.coef_out : nullptr;
   a.force_near = dm.debug & 1;
   a.wait_polls = (dm.debug & 2) ? 0u : kWaitLimit;
-  const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
+  const int64_t tiles = (a.n_cell + kTile - 1) / kTile;
   return dispatch_order(dm.order, [&](auto Mc, auto NSc) -> cudaError_t {
     constexpr int M = decltype(Mc)::value, NS = decltype(NSc)::value;
     auto go = [&](auto nqc, auto nvc) -> cudaError_t {
@@ -3909,8 +3944,8 @@ cudaError_t launch_face_flux(const DeviceMesh& dm, const void* Uq, void* K, doub
 cudaError_t launch_gather(const DeviceMesh& dm, const void* K, const double* Un, const double* Us,
                           double* out, int mode, double cn, double cs, double dt_fixed,
                           const double* max_lam, int* flag, float2* split, cudaStream_t st) {
-  GatherArgs a{dm.c_faces, dm.inv_area, dm.n_cell, dm.n_pad, dm.gamma};
-  const unsigned grid = (unsigned)((dm.n_cell + 255) / 256);
+  GatherArgs a{dm.c_faces, dm.inv_area, dm.n_update, dm.n_pad, dm.gamma};
+  const unsigned grid = (unsigned)((dm.n_update + 255) / 256);
   auto go = [&](auto nvc, auto tkc) {
     constexpr int NV = decltype(nvc)::value;
     using TK = typename decltype(tkc)::type;
@@ -3933,11 +3968,11 @@ cudaError_t launch_gather(const DeviceMesh& dm, const void* K, const double* Un,
 cudaError_t launch_positivity(const DeviceMesh& dm, const double* U, void* Uq,
                               cudaStream_t st) {
   if (dm.n_var != 4) return cudaErrorInvalidValue;
-  const unsigned grid = (unsigned)((dm.n_cell + 127) / 128);
+  const unsigned grid = (unsigned)((dm.n_recon + 127) / 128);
   auto go = [&](auto nq, auto tq) -> cudaError_t {
     constexpr int NQ = decltype(nq)::value;
     using TQ = typename decltype(tq)::type;
-    positivity_kernel<NQ, TQ><<<grid, 128, 0, st>>>(U, (TQ*)Uq, dm.n_cell, dm.n_pad, dm.gamma);
+    positivity_kernel<NQ, TQ><<<grid, 128, 0, st>>>(U, (TQ*)Uq, dm.n_recon, dm.n_pad, dm.gamma);
     return cudaGetLastError();
   };
   auto by_type = [&](auto nq) -> cudaError_t {
@@ -3950,6 +3985,20 @@ cudaError_t launch_positivity(const DeviceMesh& dm, const double* U, void* Uq,
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_halo_pack(const double* U, int64_t ld, const int32_t* idx, int64_t n,
+                             int n_var, double* buf, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  halo_pack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, ld, idx, n, n_var, buf);
+  return cudaGetLastError();
+}
+cudaError_t launch_halo_unpack(double* U, int64_t ld, const int32_t* idx, int64_t n, int n_var,
+                               const double* buf, float2* Us, int add, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  halo_unpack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, ld, idx, n, n_var, buf, Us,
+                                                                 add);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_split(const DeviceMesh& dm, const double* U, float2* Us, cudaStream_t st) {
   split_kernel<<<(unsigned)((dm.n_cell + 255) / 256), 256, 0, st>>>(U, Us, dm.n_cell, dm.n_pad,
                                                                     dm.n_var);
@@ -3960,16 +4009,16 @@ cudaError_t launch_max_lambda(const DeviceMesh& dm, const double* U, double* max
                               cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(max_lam, 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
-  int64_t blocks = (dm.n_cell + 255) / 256;
+  int64_t blocks = (dm.n_update + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   const double adv = sqrt(dm.adv_x * dm.adv_x + dm.adv_y * dm.adv_y);
   if (dm.n_var == 1)
     max_lambda_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(
-        U, dm.cfl_len, dm.n_cell, dm.n_pad, dm.gamma, adv, dm.cell_speed,
+        U, dm.cfl_len, dm.n_update, dm.n_pad, dm.gamma, adv, dm.cell_speed,
         (unsigned long long*)max_lam);
   else
     max_lambda_kernel<4><<<(unsigned)blocks, 256, 0, st>>>(
-        U, dm.cfl_len, dm.n_cell, dm.n_pad, dm.gamma, adv, nullptr,
+        U, dm.cfl_len, dm.n_update, dm.n_pad, dm.gamma, adv, nullptr,
         (unsigned long long*)max_lam);
   return cudaGetLastError();
 }
@@ -3979,10 +4028,10 @@ cudaError_t launch_max_lambda_split(const DeviceMesh& dm, const float2* Us, doub
   if (dm.n_var != 4 || !dm.cfl_ilen2 || !Us) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(max_lam, 0, sizeof(double), st);
   if (e != cudaSuccess) return e;
-  int64_t blocks = (dm.n_cell + 255) / 256;
+  int64_t blocks = (dm.n_update + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   max_lambda_split_kernel<<<(unsigned)blocks, 256, 0, st>>>(
-      Us, dm.cfl_ilen2, dm.n_cell, dm.n_pad, split2(dm.gamma), split2(dm.gamma - 1.0),
+      Us, dm.cfl_ilen2, dm.n_update, dm.n_pad, split2(dm.gamma), split2(dm.gamma - 1.0),
       (unsigned long long*)max_lam);
   return cudaGetLastError();
 }
@@ -4082,7 +4131,7 @@ cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const dou
 
 cudaError_t launch_recon_vjp(const DeviceMesh& dm, const uint8_t* sel, const double* Uq_bar,
                              double* d_bar, double* u_self, cudaStream_t st) {
-  const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
+  const int64_t tiles = (dm.n_recon + kTile - 1) / kTile;
   return dispatch_order(dm.order, [&](auto Mc, auto NSc) -> cudaError_t {
     constexpr int M = decltype(Mc)::value, NS = decltype(NSc)::value;
     constexpr int NQ = (M <= 9) ? 2 : 3;
@@ -4095,11 +4144,11 @@ cudaError_t launch_recon_vjp(const DeviceMesh& dm, const uint8_t* sel, const dou
       const unsigned grid = (unsigned)((tiles + TZ - 1) / TZ);
       if constexpr (std::is_same<TS, float2>::value)
         recon_vjp_df_kernel<M, NS, NQ, NV><<<grid, block, 0, st>>>(
-            (const float2*)dm.ahat, sel, Uq_bar, (DF*)d_bar, u_self, dm.n_cell, dm.n_pad,
+            (const float2*)dm.ahat, sel, Uq_bar, (DF*)d_bar, u_self, dm.n_recon, dm.n_pad,
             dm.eval_df);
       else
         recon_vjp_kernel<M, NS, NQ, NV, TS><<<grid, block, 0, st>>>(
-            (const TS*)dm.ahat, sel, Uq_bar, d_bar, u_self, dm.n_cell, dm.n_pad, dm.eval);
+            (const TS*)dm.ahat, sel, Uq_bar, d_bar, u_self, dm.n_recon, dm.n_pad, dm.eval);
     };
     using I1 = std::integral_constant<int, 1>;
     using I4 = std::integral_constant<int, 4>;
@@ -4131,10 +4180,10 @@ cudaError_t launch_recon_vjp_tma_t(const DeviceMesh& dm, const uint8_t* sel, con
       cudaSuccess)
     return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int64_t tiles = (dm.n_cell + kTile - 1) / kTile;
+  const int64_t tiles = (dm.n_recon + kTile - 1) / kTile;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)per_sm * sms);
   kern<<<(unsigned)grid, threads, VP::kSmem, st>>>((const float2*)dm.ahat, dm.wq, dm.halo, sel,
-                                                   Uq_bar, part, u_self, dm.n_cell, dm.n_pad,
+                                                   Uq_bar, part, u_self, dm.n_recon, dm.n_pad,
                                                    dm.eval_df, dm.err_flag);
   return cudaGetLastError();
 }

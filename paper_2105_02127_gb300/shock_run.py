@@ -1,0 +1,119 @@
+"""Double Mach reflection (Sec. 5) as a time run on one GPU.
+
+The Mach-10 shock at 60 degrees to a reflecting wall on [0,4]x[0,1], run to
+t = 0.2 with TENO (default TENO6), HLLC, SSP-RK3 at CFL 0.4 and the
+positivity scaling of the reconstruction, in FP64 (the double-float path)
+and FP32-mixed.  At sampled steps of the FP64 run the selections of the FP64
+and FP32-mixed paths are evaluated on the same stage input states (U^n,
+U^(1), U^(2)); their flip rate per stage is the fraction of (cell, variable)
+selections that differ.  Prints one JSON object.
+
+  python -m paper_2105_02127_gb300.shock_run [--nx 2048] [--ny 512] [--order 6]
+                                             [--t-end 0.2] [--sample-every 50]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+
+def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int | None = None):
+    import torch
+
+    from . import build, inputs, teno
+    build.build()
+    if flux is None:
+        flux = teno.FLUX_HLLC
+    mesh = inputs.jittered_mesh(nx, ny, 4.0, 1.0, seed=1003, periodic=False,
+                                bc_tagger=inputs.dmr_bc_tagger)
+    U0 = inputs.cell_average(mesh, inputs.dmr_state, n_quad=3)
+    n_cell = mesh.n_cell
+
+    def ctx(precision):
+        t = teno.Teno(device=0).load(mesh)
+        t.precompute_stencils(order=order, n_var=4, flux=flux, precision=precision, positivity=1)
+        return t
+
+    out = {"workload": f"double Mach reflection, [0,4]x[0,1], jittered {nx}x{ny} split quads = "
+                       f"{n_cell} triangles, TENO{order}, "
+                       f"{'HLLC' if flux == teno.FLUX_HLLC else 'HLL'}, SSP-RK3, CFL 0.4, "
+                       f"positivity scaling, t_end {t_end}",
+           "n_cell": n_cell}
+    probes = (ctx(teno.FP64), ctx(teno.FP32_MIXED))
+    Rb = torch.empty((4, n_cell), dtype=torch.float64, device="cuda")
+    sels = [torch.empty((4, n_cell), dtype=torch.uint8, device="cuda") for _ in range(2)]
+
+    def flips(Us, time_):
+        for p, sel in zip(probes, sels):
+            p.set_time(time_)
+            p.set_state(Us)
+            p.residual(out=Rb, sel=sel)
+        return float((sels[0] != sels[1]).double().mean().item())
+
+    for name, precision in (("fp64_pairs", teno.FP64), ("fp32_mixed", teno.FP32_MIXED)):
+        t = ctx(precision)
+        Ud = torch.from_numpy(U0).cuda()
+        t.set_state(Ud)
+        Un, U1, U2 = (torch.empty_like(Ud) for _ in range(3))
+        tm, n, per_stage = 0.0, 0, []
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        step_s = 0.0
+        while tm < t_end - 1e-14:
+            dt = min(t.cfl_dt(), t_end - tm)
+            sample = name == "fp64_pairs" and n % sample_every == 0
+            if sample:
+                t.get_state(Un)
+            s0 = time.perf_counter()
+            t.rk3_step(dt)
+            step_s += time.perf_counter() - s0
+            if sample:
+                t.stage_state(1, U1)
+                t.stage_state(2, U2)
+                per_stage.append([n, tm] + [flips(Us, tm) for Us in (Un, U1, U2)])
+            tm += dt
+            n += 1
+        t.check_state()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        U = t.get_state()
+        rho = U[0]
+        p = 0.4 * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / rho)
+        rec = {"steps": n, "t": tm, "wall_s": wall,
+               "cell_stage_per_s_in_steps": n_cell * 3 * n / step_s,
+               "finite": bool(np.isfinite(U).all()), "rho_min": float(rho.min()),
+               "p_min": float(p.min()), "rho_max": float(rho.max())}
+        if name == "fp64_pairs":
+            fl = np.array([r[2:] for r in per_stage])
+            rec["flip_rate_per_stage"] = {
+                "sampled_steps": len(per_stage), "every": sample_every,
+                "mean": fl.mean(axis=0).tolist(), "max": fl.max(axis=0).tolist(),
+                "overall_max": float(fl.max()), "overall_mean": float(fl.mean()),
+                "samples": [[int(r[0]), float(r[1])] + r[2:] for r in per_stage]}
+            rho64 = rho.copy()
+        else:
+            rec["mean_abs_rho_diff_vs_fp64_over_mean_rho"] = float(
+                np.abs(rho - rho64).mean() / np.abs(rho64).mean())
+        out[name] = rec
+        t.close()
+    for p in probes:
+        p.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nx", type=int, default=2048)
+    ap.add_argument("--ny", type=int, default=512)
+    ap.add_argument("--order", type=int, default=6)
+    ap.add_argument("--t-end", type=float, default=0.2)
+    ap.add_argument("--sample-every", type=int, default=50)
+    a = ap.parse_args()
+    print(json.dumps(run(a.nx, a.ny, a.order, a.t_end, a.sample_every)))
+
+
+if __name__ == "__main__":
+    main()

@@ -92,6 +92,17 @@ def lib(build_if_missing: bool = False):
                                           C.c_int]),
         "teno_colour_slots": (C.c_int, [C.c_int32, C.c_int32, _vp, _vp]),
         "teno_fma_peak": (C.c_int, [C.c_int, _vp, C.c_int, _vp]),
+        "teno_precompute_partition": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32]),
+        "teno_partition_sizes": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+        "teno_partition_cells": (C.c_int, [_vp, _vp]),
+        "teno_partition_recv_cells": (C.c_int, [_vp, C.c_int32, _vp]),
+        "teno_partition_set_send": (C.c_int, [_vp, C.c_int32, C.c_int64, _vp]),
+        "teno_halo_pack": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp]),
+        "teno_halo_unpack": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp]),
+        "teno_rk3_stage": (C.c_int, [_vp, C.c_int32, C.c_double]),
+        "teno_local_max_speed": (C.c_int, [_vp, _vp]),
+        "teno_group_rk3_step": (C.c_int, [_vp, C.c_int32, C.c_double, _vp]),
+        "teno_group_residual_vjp": (C.c_int, [_vp, C.c_int32, _vp, _vp]),
         "teno_profile": (C.c_int, [_vp, C.c_int]),
         "teno_profile_read": (C.c_int, [_vp, _vp, _vp]),
     }
@@ -279,6 +290,64 @@ class Teno:
         self.m, self.ns = m.value, ns.value
         return self
 
+    def precompute_partition(self, n_parts: int, part: int, params: teno_params | None = None,
+                             **kw):
+        """Stencils and matrices of part `part` of n_parts of the mesh (a range
+        of whole tiles of the Hilbert order; see teno_precompute_partition)."""
+        p = params if params is not None else default_params(**kw)
+        self._chk(lib().teno_precompute_partition(self._h, C.byref(p), int(n_parts), int(part)))
+        self.params = p
+        self.n_var = p.n_var
+        n = C.c_int64()
+        nv, m, ns = C.c_int32(), C.c_int32(), C.c_int32()
+        self._chk(lib().teno_get_sizes(self._h, C.byref(n), C.byref(nv), C.byref(m),
+                                       C.byref(ns)))
+        self.m, self.ns = m.value, ns.value
+        self.n_parts, self.part = int(n_parts), int(part)
+        return self
+
+    def partition_sizes(self):
+        """(n_owned, n_state, recv_counts[n_parts], send_counts[n_parts])"""
+        P = getattr(self, "n_parts", 1)
+        a, b = C.c_int64(), C.c_int64()
+        rc_, sc_ = np.zeros(P, dtype=np.int64), np.zeros(P, dtype=np.int64)
+        self._chk(lib().teno_partition_sizes(self._h, C.byref(a), C.byref(b), rc_.ctypes.data,
+                                             sc_.ctypes.data))
+        return a.value, b.value, rc_, sc_
+
+    def partition_cells(self):
+        """user ids of the owned cells, in the order of the owned arrays"""
+        out = np.empty(self.partition_sizes()[0], dtype=np.int32)
+        self._chk(lib().teno_partition_cells(self._h, out.ctypes.data))
+        return out
+
+    def partition_recv_cells(self, peer: int):
+        n = int(self.partition_sizes()[2][peer])
+        out = np.empty(max(n, 1), dtype=np.int32)
+        self._chk(lib().teno_partition_recv_cells(self._h, int(peer), out.ctypes.data))
+        return out[:n]
+
+    def partition_set_send(self, peer: int, user_ids):
+        u = np.ascontiguousarray(user_ids, dtype=np.int32)
+        self._chk(lib().teno_partition_set_send(self._h, int(peer), len(u),
+                                                u.ctypes.data if len(u) else None))
+
+    def halo_pack(self, peer: int, what: int, buf):
+        p, dev = _ptr(buf)
+        self._chk(lib().teno_halo_pack(self._h, int(peer), int(what), p))
+
+    def halo_unpack(self, peer: int, what: int, buf):
+        p, dev = _ptr(buf)
+        self._chk(lib().teno_halo_unpack(self._h, int(peer), int(what), p))
+
+    def rk3_stage(self, stage: int, dt: float):
+        self._chk(lib().teno_rk3_stage(self._h, int(stage), float(dt)))
+
+    def local_max_speed(self) -> float:
+        lam = C.c_double()
+        self._chk(lib().teno_local_max_speed(self._h, C.byref(lam)))
+        return lam.value
+
     def permutation(self):
         out = np.empty(self.n_cell, dtype=np.int32)
         self._chk(lib().teno_get_permutation(self._h, out.ctypes.data))
@@ -398,3 +467,28 @@ class Teno:
             raise ValueError("lam_np1 and out must both be host or both be device arrays")
         self._chk(lib().teno_adjoint_step(self._h, float(dt), lp, op, ldev))
         return out
+
+
+def _group(parts):
+    arr = (_vp * len(parts))(*[p._h for p in parts])
+    return arr
+
+
+def group_rk3_step(parts, dt: float = 0.0) -> float:
+    """One SSP-RK3 step of all parts of a partitioned mesh in this process
+    (teno_group_rk3_step); returns the step."""
+    used = C.c_double()
+    rc = lib().teno_group_rk3_step(_group(parts), len(parts), float(dt), C.byref(used))
+    if rc != 0:
+        raise TenoError(rc, lib().teno_last_error(parts[0]._h).decode())
+    return used.value
+
+
+def group_residual_vjp(parts, w):
+    """v = (dR/dU)^T w over all parts (host [n_var][n_cell] arrays, user order)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    v = np.zeros_like(w)
+    rc = lib().teno_group_residual_vjp(_group(parts), len(parts), w.ctypes.data, v.ctypes.data)
+    if rc != 0:
+        raise TenoError(rc, lib().teno_last_error(parts[0]._h).decode())
+    return v

@@ -33,11 +33,10 @@ def test_vjp_bytes():
 
 
 def test_native_flops():
-    # per variable: (N_s + 36) differences, 2E matvec, 2(m + 15) beta, 25 for
-    # the selection, 2 * 3N_q * m evaluation products and 3N_q sums
-    per_var = 66 + 2 * 600 + 2 * 29 + 25 + 2 * 9 * 14 + 9
-    assert per_var == 1610
-    assert bench.algorithmic_fp64_flops(5, 4, 3) == 4 * per_var
+    # W form, per variable: (N_s + 36) differences, N_s x 3N_q multiply-adds
+    # for U_0 + W d, 3N_q additions; TENO5 N_s = 30, TENO6 N_s = 42
+    assert bench.algorithmic_fp64_flops(5, 4, 3) == 4 * (66 + 2 * 30 * 9 + 9) == 4 * 615
+    assert bench.algorithmic_fp64_flops(6, 4, 3) == 4 * (78 + 2 * 42 * 9 + 9) == 4 * 843
 
 
 def test_traffic_table_keyed_by_kernel_source():
