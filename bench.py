@@ -362,38 +362,59 @@ def run_ours(args):
         return res
 
     def adjoint_leg(t, res):
-        # one adjoint SSP-RK3 step (its replay of the forward stages included)
+        # the adjoint of one SSP-RK3 step: from a recorded step (the reverse
+        # sweep of a checkpointed adjoint, whose segment replay records its
+        # steps), and with its own replay of the forward stages
         lam = torch.from_numpy(np.ones_like(U)).cuda()
         lam_out = torch.empty_like(lam)
-        t.set_state(Ud)
-        t.adjoint_step(1e-4, lam, lam_out)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+        dt_a = 1e-4
         na = max(2, args.steps // 4)
-        t.profile(True)
-        e0.record(stream)
-        for _ in range(na):
-            t.adjoint_step(1e-4, lam, lam_out)
-        e1.record(stream)
+        t.set_state(Ud)
+        t.tape_reserve(1)
+        t.rk3_step_record(0, dt_a)  # warm-up
+        t.adjoint_step_tape(0, lam, lam_out)
         torch.cuda.synchronize()
-        adj_ms = e0.elapsed_time(e1) / na
-        akms, alaunch = t.profile_read()
-        t.profile(False)
-        vjp_ms = akms[6] / max(1, alaunch[6])
+
+        def timed(fn):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            t.profile(True)
+            e0.record(stream)
+            for _ in range(na):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            kms, kl = t.profile_read()
+            t.profile(False)
+            return e0.elapsed_time(e1) / na, kms / na, kl
+
+        rec_ms, _, _ = timed(lambda: t.rk3_step_record(0, dt_a))
+        tape_ms, akms, alaunch = timed(lambda: t.adjoint_step_tape(0, lam, lam_out))
+        t.tape_reserve(0)
+        t.set_state(Ud)
+        t.adjoint_step(dt_a, lam, lam_out)
+        replay_ms, _, _ = timed(lambda: t.adjoint_step(dt_a, lam, lam_out))
+        vjp_ms = akms[6] * na / max(1, alaunch[6])
         vjp_gbs = algorithmic_vjp_bytes(args.order, nq) * n_cell / (vjp_ms / 1e3) / 1e9
+        fwd = res["ms_per_step"]
         res["adjoint"] = {
-            "ms_per_step": adj_ms, "forward_ms_per_step": res["ms_per_step"],
-            "adjoint_over_forward": adj_ms / res["ms_per_step"],
+            "ms_per_step": tape_ms, "forward_ms_per_step": fwd,
+            "adjoint_over_forward": tape_ms / fwd,
+            "record_ms_per_step": rec_ms, "record_over_forward": rec_ms / fwd,
+            "with_replay_ms_per_step": replay_ms, "with_replay_over_forward": replay_ms / fwd,
             "roofline": {"bound": "hbm", "achieved": vjp_gbs, "peak": hbm_gbs, "unit": "GB/s",
                          "frac": vjp_gbs / hbm_gbs,
                          "traffic": ncu_traffic("adjoint_vjp", args.order, n_cell),
                          "kernel": f"recon_vjp_tma_kernel <fp64 pairs> order {args.order}",
                          "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)",
                          "ms_per_launch": vjp_ms},
-            "kernel_ms_per_step": (akms / na).tolist(),
-            "note": "one adjoint SSP-RK3 step of the FP64 pair path, including the replay of "
-                    "its two forward stages"}
+            "kernel_ms_per_step": akms.tolist(),
+            "note": "FP64 pair path.  ms_per_step: the adjoint of a recorded step "
+                    "(teno_adjoint_step_tape: three flux and reconstruction VJPs, no "
+                    "reconstruction), the reverse sweep of a checkpointed adjoint; its segment "
+                    "replay records each step (record_ms_per_step, the forward step plus the "
+                    "copies of the stage states).  with_replay: teno_adjoint_step, which "
+                    "replays the step's forward stages itself."}
 
     def e2e_leg(t, res):
         # end to end through the C ABI with pinned host buffers

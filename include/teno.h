@@ -278,6 +278,25 @@ int teno_residual_vjp(teno_ctx* ctx, const double* w, double* v, int on_device);
 int teno_adjoint_step(teno_ctx* ctx, double dt, const double* lam_np1, double* lam_n,
                       int on_device);
 
+/* Adjoint tape (no counterpart in the paper).  A checkpointed adjoint replays
+ * each segment of steps forward before running its adjoint steps in reverse;
+ * recording the replay lets the adjoint steps skip every reconstruction.
+ * teno_tape_reserve allocates n_slots slots on the device (per slot the three
+ * stage input states, [n_var][n_cell] FP64, and per stage the Gauss-point
+ * values and selections: at 524,288 cells TENO5 about 0.5 GB); n_slots = 0
+ * frees them.  teno_rk3_step_record takes one SSP-RK3 step from the current
+ * state exactly as teno_rk3_step does (dt <= 0: the CFL step, host-side) and
+ * records it in `slot`.  teno_adjoint_step_tape is teno_adjoint_step for the
+ * recorded step: lam_n = (dU^{n+1}/dU^n)^T lam_np1 with the recorded
+ * selections and Gauss-point values (the same bits as teno_adjoint_step at
+ * the recorded U^n); the state is not used or changed.  Errors: TENO_EINVAL
+ * (slot outside the tape or not recorded, the adjoint's restrictions),
+ * TENO_ENOMEM. */
+int teno_tape_reserve(teno_ctx* ctx, int32_t n_slots);
+int teno_rk3_step_record(teno_ctx* ctx, int32_t slot, double dt);
+int teno_adjoint_step_tape(teno_ctx* ctx, int32_t slot, const double* lam_np1, double* lam_n,
+                           int on_device);
+
 /* Values of the last reconstruction at the edge Gauss points (inspection
  * support): out host [n_cell][3][nq][n_var] in user cell order, edge e of a
  * cell running from its vertex e to vertex e+1, points in ascending order

@@ -3,10 +3,12 @@
 `TenoStep` differentiates one SSP-RK3 step; `trajectory` differentiates n
 steps with RK-state checkpointing: the forward keeps the state every
 `checkpoint_every` steps, the backward replays one segment at a time from its
-checkpoint (keeping that segment's states) and runs the adjoint steps in
-reverse.  Every step of the forward and of the backward runs in libteno; the
-stencil selection and the flux branches of each stage are frozen at their
-forward values (the adjoint replays the same deterministic stages).
+checkpoint, recording every step on the library's adjoint tape (stage states,
+Gauss-point values, selections; the tape is reserved once for a segment), and
+runs the adjoint steps of the segment in reverse from the tape, so that no
+reconstruction is repeated.  Every step of the forward and of the backward
+runs in libteno; the stencil selection and the flux branches of each stage are
+frozen at their forward values.
 """
 from __future__ import annotations
 
@@ -57,21 +59,18 @@ class _Trajectory(torch.autograd.Function):
         solver, dt, n, every = ctx.solver, ctx.dt, ctx.n, ctx.every
         lam = grad.contiguous().clone()
         nxt = torch.empty_like(lam)
+        solver.tape_reserve(min(every, n))
         for seg in range(len(ctx.checkpoints) - 1, -1, -1):
             start = seg * every
             stop = min(n, start + every)
-            # replay the segment, keeping its step states
-            states = [ctx.checkpoints[seg]]
-            solver.set_state(states[0])
-            for _ in range(start + 1, stop):
-                solver.rk3_step(dt, sync=False)
-                buf = torch.empty_like(lam)
-                solver.get_state(buf)
-                states.append(buf)
-            for Uk in reversed(states):
-                solver.set_state(Uk)
-                solver.adjoint_step(dt, lam, nxt)
+            # replay the segment on the tape
+            solver.set_state(ctx.checkpoints[seg])
+            for k in range(stop - start):
+                solver.rk3_step_record(k, dt)
+            for k in range(stop - start - 1, -1, -1):
+                solver.adjoint_step_tape(k, lam, nxt)
                 lam, nxt = nxt, lam
+        solver.tape_reserve(0)
         return lam, None, None, None, None
 
 

@@ -99,6 +99,12 @@ struct teno_ctx {
   std::vector<std::vector<int32_t>> recv_loc, send_loc;  // per peer, local cell ids
   std::vector<DevBuf> b_recv_idx, b_send_idx, b_xbuf;     // per peer
   DevBuf b_perm_in;                  // local cell -> global user id (partitions)
+  // adjoint tape (teno_tape_reserve): one buffer per slot holding a step's
+  // U^n, U^(1), U^(2), then per stage its Gauss-point values and selection
+  std::vector<DevBuf> tape;
+  std::vector<double> tape_dt, tape_t;
+  std::vector<char> tape_ok;
+  size_t tape_sb = 0, tape_qb = 0, tape_selb = 0;  // aligned part sizes
   // global faces (internal ids), kept on the host for partitions
   std::vector<int32_t> h_fcells, h_cfaces;
   std::vector<int8_t> h_fedges;
@@ -120,6 +126,7 @@ int fail(teno_ctx* c, int code, const std::string& msg) {
 }
 
 int cuda_fail(teno_ctx* c, cudaError_t e, const char* where) {
+  cudaGetLastError();  // reported here: not left for a later call to find
   return fail(c, TENO_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
@@ -192,6 +199,7 @@ int upload(teno_ctx* ctx, DevBuf& b, const void* src, size_t bytes) {
   if (ctx->device < 0) return TENO_OK;  // host-only context
   int rc = dev_alloc(ctx, b, bytes);
   if (rc) return rc;
+  if (bytes == 0 || !src) return TENO_OK;  // an empty list: storage only
   CK(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, ctx->stream), "upload");
   CK(cudaStreamSynchronize(ctx->stream), "upload sync");
   return TENO_OK;
@@ -1461,23 +1469,23 @@ int upload_partition_mesh(teno_ctx* ctx) {
     if (l < sn) perm_in[l] = g >= 0 ? ctx->perm[g] : 0;
   }
   for (int64_t l = 0; l < n_own; ++l) perm_out[l] = (int32_t)l;
-  int rc = upload(ctx, ctx->b_fcells, fcells.data(), std::max<size_t>(1, fcells.size()) * 4);
-  if (!rc) rc = upload(ctx, ctx->b_fedges, fedges.data(), std::max<size_t>(1, fedges.size()));
-  if (!rc) rc = upload(ctx, ctx->b_fgeom, fgeom.data(), std::max<size_t>(1, fgeom.size()) * 8);
-  if (!rc) rc = upload(ctx, ctx->b_fgeom2, fgeom2.data(), std::max<size_t>(1, fgeom2.size()) * 8);
+  int rc = upload(ctx, ctx->b_fcells, fcells.data(), fcells.size() * 4);
+  if (!rc) rc = upload(ctx, ctx->b_fedges, fedges.data(), fedges.size());
+  if (!rc) rc = upload(ctx, ctx->b_fgeom, fgeom.data(), fgeom.size() * 8);
+  if (!rc) rc = upload(ctx, ctx->b_fgeom2, fgeom2.data(), fgeom2.size() * 8);
   if (!rc) rc = upload(ctx, ctx->b_cfaces, cfaces.data(), cfaces.size() * 4);
   if (!rc) rc = upload(ctx, ctx->b_inv_area, inv_area.data(), inv_area.size() * 8);
   if (!rc) rc = upload(ctx, ctx->b_cfl_len, cfl_len.data(), cfl_len.size() * 8);
   if (!rc) rc = upload(ctx, ctx->b_cfl_ilen2, ilen2.data(), ilen2.size() * sizeof(float2));
   if (!rc) rc = upload(ctx, ctx->b_perm_in, perm_in.data(), perm_in.size() * 4);
-  if (!rc) rc = upload(ctx, ctx->b_perm, perm_out.data(), std::max<size_t>(1, perm_out.size()) * 4);
+  if (!rc) rc = upload(ctx, ctx->b_perm, perm_out.data(), perm_out.size() * 4);
   const int32_t P = ctx->part_n;
   ctx->b_recv_idx.resize(P);
   ctx->b_send_idx.resize(P);
   ctx->b_xbuf.resize(2 * P);
   for (int32_t q = 0; q < P && !rc; ++q)
     rc = upload(ctx, ctx->b_recv_idx[q], ctx->recv_loc[q].data(),
-                std::max<size_t>(1, ctx->recv_loc[q].size()) * 4);
+                ctx->recv_loc[q].size() * 4);
   if (rc) return rc;
   DeviceMesh& dm = ctx->dm;
   dm.n_cell = sn;
@@ -1590,13 +1598,13 @@ int ensure_adjoint(teno_ctx* ctx) {
       rc = upload(ctx, ctx->b_hrev_off, ctx->hrev_off_h.data(), sizeof(int64_t) * (nc + 1));
     if (!rc)
       rc = upload(ctx, ctx->b_hrev_idx, ctx->hrev_idx_h.data(),
-                  sizeof(int32_t) * std::max<size_t>(1, ctx->hrev_idx_h.size()));
+                  sizeof(int32_t) * ctx->hrev_idx_h.size());
   } else {
     rc = dev_alloc(ctx, ctx->b_dbar, sizeof(double) * ntile * ctx->SL * nv * kTile);
     if (!rc) rc = upload(ctx, ctx->b_rev_off, ctx->rev_off_h.data(), sizeof(int64_t) * (nc + 1));
     if (!rc)
       rc = upload(ctx, ctx->b_rev_idx, ctx->rev_idx_h.data(),
-                  sizeof(int32_t) * std::max<size_t>(1, ctx->rev_idx_h.size()));
+                  sizeof(int32_t) * ctx->rev_idx_h.size());
     if (!rc) CK(cudaMemsetAsync(ctx->b_dbar.p, 0, ctx->b_dbar.bytes, ctx->stream), "memset");
   }
   if (!rc) rc = dev_alloc(ctx, ctx->b_uself, sizeof(double) * nv * npad);
@@ -1778,6 +1786,7 @@ int teno_destroy(teno_ctx* ctx) {
                     &ctx->b_sel_st[1]};
   for (DevBuf* b : bufs) dev_free(*b);
   dev_free(ctx->b_perm_in);
+  for (DevBuf& b : ctx->tape) dev_free(b);
   for (auto* v : {&ctx->b_recv_idx, &ctx->b_send_idx, &ctx->b_xbuf})
     for (DevBuf& b : *v) dev_free(b);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -2307,7 +2316,7 @@ int teno_partition_set_send(teno_ctx* ctx, int32_t peer, int64_t n, const int32_
   if (ctx->device >= 0) {
     CK(cudaSetDevice(ctx->device), "cudaSetDevice");
     int rc = upload(ctx, ctx->b_send_idx[peer], ctx->send_loc[peer].data(),
-                    std::max<size_t>(1, ctx->send_loc[peer].size()) * 4);
+                    ctx->send_loc[peer].size() * 4);
     if (rc) return rc;
   }
   return TENO_OK;
@@ -2559,5 +2568,122 @@ int teno_group_residual_vjp(teno_ctx* const* parts, int32_t n, const double* w, 
         vout[(size_t)k * nc + users[l]] = h[(size_t)k * ctx->n_own + l];
   }
   return TENO_OK;
+}
+
+// ------------------------------------------------------------------ adjoint tape
+
+int teno_tape_reserve(teno_ctx* ctx, int32_t n_slots) {
+  int rc = check_ready(ctx, false);
+  if (rc) return rc;
+  if (n_slots < 0) return fail(ctx, TENO_EINVAL, "tape_reserve: negative count");
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t nv = ctx->prm.n_var;
+  ctx->tape_sb = al(8 * nv * ctx->spad);
+  ctx->tape_qb = al(ctx->b_Uq.bytes);
+  ctx->tape_selb = al(nv * ctx->spad);
+  const size_t slot = 3 * (ctx->tape_sb + ctx->tape_qb + ctx->tape_selb);
+  for (size_t i = (size_t)n_slots; i < ctx->tape.size(); ++i) dev_free(ctx->tape[i]);
+  ctx->tape.resize(n_slots);
+  for (int32_t i = 0; i < n_slots; ++i) {
+    if (ctx->tape[i].bytes != slot) dev_free(ctx->tape[i]);
+    if ((rc = dev_alloc(ctx, ctx->tape[i], slot))) return rc;
+  }
+  ctx->tape_dt.assign(n_slots, 0.0);
+  ctx->tape_t.assign(n_slots, 0.0);
+  ctx->tape_ok.assign(n_slots, 0);
+  return TENO_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// parts of tape slot i: state k (0 U^n, 1 U^(1), 2 U^(2)); Gauss values and
+// selection of stage k (0..2)
+unsigned char* tape_part(teno_ctx* ctx, int32_t i, int kind, int k) {
+  unsigned char* b = (unsigned char*)ctx->tape[i].p;
+  const size_t s = ctx->tape_sb, q = ctx->tape_qb, l = ctx->tape_selb;
+  if (kind == 0) return b + k * s;
+  if (kind == 1) return b + 3 * s + k * q;
+  return b + 3 * s + 3 * q + k * l;
+}
+}  // namespace
+
+extern "C" {
+
+int teno_rk3_step_record(teno_ctx* ctx, int32_t slot, double dt) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (ctx->part_n > 1) return fail(ctx, TENO_EINVAL, "partition: adjoint steps take the whole mesh");
+  if (slot < 0 || slot >= (int32_t)ctx->tape.size())
+    return fail(ctx, TENO_EINVAL, "rk3_step_record: slot outside the reserved tape");
+  if (dt <= 0.0 && (rc = teno_cfl_dt(ctx, &dt))) return rc;
+  double* U = (double*)ctx->b_U.p;
+  double* Un = (double*)tape_part(ctx, slot, 0, 0);
+  double* U1 = (double*)tape_part(ctx, slot, 0, 1);
+  double* U2 = (double*)tape_part(ctx, slot, 0, 2);
+  CK(cudaMemcpyAsync(Un, U, 8 * (size_t)ctx->prm.n_var * ctx->spad, cudaMemcpyDeviceToDevice,
+                     ctx->stream),
+     "tape copy");
+  const double t = ctx->time;
+  rc = rk_stage(ctx, U, U, U1, 0.0, 1.0, dt, nullptr, t, ctx->split_ok, tape_part(ctx, slot, 1, 0),
+                tape_part(ctx, slot, 2, 0));
+  if (!rc)
+    rc = rk_stage(ctx, U, U1, U2, 0.75, 0.25, dt, nullptr, t + dt, true,
+                  tape_part(ctx, slot, 1, 1), tape_part(ctx, slot, 2, 1));
+  if (!rc)
+    rc = rk_stage(ctx, U, U2, U, 1.0 / 3.0, 2.0 / 3.0, dt, nullptr, t + 0.5 * dt, true,
+                  tape_part(ctx, slot, 1, 2), tape_part(ctx, slot, 2, 2));
+  ctx->split_ok = ctx->prm.precision != TENO_FP64_NATIVE;
+  ctx->stages_ok = false;  // the stage states went to the tape
+  if (rc) return rc;
+  ctx->tape_dt[slot] = dt;
+  ctx->tape_t[slot] = t;
+  ctx->tape_ok[slot] = 1;
+  ctx->time += dt;
+  return TENO_OK;
+}
+
+int teno_adjoint_step_tape(teno_ctx* ctx, int32_t slot, const double* lam_np1, double* lam_n,
+                           int on_device) {
+  int rc = check_ready(ctx, true);
+  if (rc) return rc;
+  if (!lam_np1 || !lam_n || slot < 0 || slot >= (int32_t)ctx->tape.size() || !ctx->tape_ok[slot])
+    return fail(ctx, TENO_EINVAL, "adjoint_step_tape: bad arguments or an unrecorded slot");
+  if (ctx->prm.precision == TENO_FP32_MIXED)
+    return fail(ctx, TENO_EINVAL, "adjoint: FP64 precisions only");
+  if (ctx->prm.scheme != 0 || ctx->prm.charvar != 0 || ctx->prm.positivity != 0)
+    return fail(ctx, TENO_EINVAL,
+                "adjoint: TENO in conservative variables only, without positivity scaling");
+  rc = ensure_adjoint(ctx);
+  if (rc) return rc;
+  const int64_t n = (int64_t)ctx->prm.n_var * ctx->spad;
+  const double dt = ctx->tape_dt[slot], t = ctx->tape_t[slot];
+  double* lam = (double*)ctx->b_R.p;
+  double* l1 = (double*)ctx->b_l1.p;
+  double* l2 = (double*)ctx->b_l2.p;
+  double* ln = (double*)ctx->b_lamn.p;
+  double* tmp = (double*)ctx->b_vtmp.p;
+  const double* Un = (const double*)tape_part(ctx, slot, 0, 0);
+  const double* U1 = (const double*)tape_part(ctx, slot, 0, 1);
+  const double* U2 = (const double*)tape_part(ctx, slot, 0, 2);
+  auto uq = [&](int k) { return (const void*)tape_part(ctx, slot, 1, k); };
+  auto sl = [&](int k) { return (const uint8_t*)tape_part(ctx, slot, 2, k); };
+  rc = to_internal(ctx, lam_np1, lam, on_device);
+  // stage 3: U^{n+1} = 1/3 U^n + 2/3 U2 + 2/3 dt R(U2)
+  if (!rc) rc = vjp_internal(ctx, U2, lam, tmp, t + 0.5 * dt, uq(2), sl(2));
+  if (rc) return rc;
+  CK(launch_axpby(l2, lam, 2.0 / 3.0, tmp, 2.0 / 3.0 * dt, n, ctx->stream), "axpby");
+  CK(launch_axpby(ln, lam, 1.0 / 3.0, lam, 0.0, n, ctx->stream), "axpby");
+  // stage 2: U2 = 3/4 U^n + 1/4 U1 + 1/4 dt R(U1)
+  rc = vjp_internal(ctx, U1, l2, tmp, t + dt, uq(1), sl(1));
+  if (rc) return rc;
+  CK(launch_axpby(l1, l2, 0.25, tmp, 0.25 * dt, n, ctx->stream), "axpby");
+  CK(launch_axpby(ln, ln, 1.0, l2, 0.75, n, ctx->stream), "axpby");
+  // stage 1: U1 = U^n + dt R(U^n)
+  rc = vjp_internal(ctx, Un, l1, tmp, t, uq(0), sl(0));
+  if (rc) return rc;
+  CK(launch_axpby(ln, ln, 1.0, l1, 1.0, n, ctx->stream), "axpby");
+  CK(launch_axpby(ln, ln, 1.0, tmp, dt, n, ctx->stream), "axpby");
+  return to_user(ctx, ln, lam_n, on_device);
 }
 }  // extern "C"

@@ -151,12 +151,19 @@ __device__ __forceinline__ double val(double x) { return x; }
 __device__ __forceinline__ float val(float x) { return x; }
 template <int N, typename S>
 __device__ __forceinline__ auto val(const Dual<N, S>& x) { return val(x.v); }
+// min / max that ignore a NaN operand, like C's fmin / fmax (a wave speed
+// from the sound speed of a state whose pressure rounds below zero is NaN;
+// the other bound is then taken)
 template <typename T>
-__device__ __forceinline__ T vmin(const T& a, const T& b) { return val(a) <= val(b) ? a : b; }
+__device__ __forceinline__ T vmin(const T& a, const T& b) {
+  return (val(a) <= val(b) || val(b) != val(b)) ? a : b;
+}
 template <typename T>
 __device__ __forceinline__ bool nonneg(const T& x) { return val(x) >= decltype(val(x))(0); }
 template <typename T>
-__device__ __forceinline__ T vmax(const T& a, const T& b) { return val(a) >= val(b) ? a : b; }
+__device__ __forceinline__ T vmax(const T& a, const T& b) {
+  return (val(a) >= val(b) || val(b) != val(b)) ? a : b;
+}
 
 
 // ------------------------------------------- double-float (FP32 pair) path
@@ -279,10 +286,10 @@ struct Cst<DF> {
   }
 };
 __device__ __forceinline__ DF vmin(const DF& a, const DF& b) {
-  return (a.h < b.h || (a.h == b.h && a.l <= b.l)) ? a : b;
+  return (a.h < b.h || (a.h == b.h && a.l <= b.l) || b.h != b.h) ? a : b;
 }
 __device__ __forceinline__ DF vmax(const DF& a, const DF& b) {
-  return (a.h > b.h || (a.h == b.h && a.l >= b.l)) ? a : b;
+  return (a.h > b.h || (a.h == b.h && a.l >= b.l) || b.h != b.h) ? a : b;
 }
 // c + a*b and conversion to FP64 for every scalar type of the flux kernels
 // exact zero test (pairs: both parts; dual numbers: the value)
@@ -318,11 +325,11 @@ __device__ __forceinline__ bool df_le(const DF& a, const DF& b) {
 }
 template <int N>
 __device__ __forceinline__ Dual<N, DF> vmin(const Dual<N, DF>& a, const Dual<N, DF>& b) {
-  return df_le(a.v, b.v) ? a : b;
+  return (df_le(a.v, b.v) || b.v.h != b.v.h) ? a : b;
 }
 template <int N>
 __device__ __forceinline__ Dual<N, DF> vmax(const Dual<N, DF>& a, const Dual<N, DF>& b) {
-  return df_le(b.v, a.v) ? a : b;
+  return (df_le(b.v, a.v) || b.v.h != b.v.h) ? a : b;
 }
 template <int N>
 __device__ __forceinline__ bool nonneg(const Dual<N, DF>& x) {
@@ -486,8 +493,10 @@ __device__ __forceinline__ void euler_riemann_vjp(const T* UL, const T* UR, cons
   const T ua = (unL + unR * D) * iden, va = (utL + utR * D) * iden;
   const T Ha = (HL + HR * D) * iden;
   const T ca = tsqrt(gm1 * (Ha - half * (ua * ua + va * va)));
-  const bool sl0 = le_ord(unL - cL, ua - ca);  // SL from the left state
-  const bool sr0 = le_ord(ua + ca, unR + cR);  // SR from the right state
+  // the branches vmin / vmax take in the forward solver (NaN operands ignored)
+  const T am = ua - ca, ap = ua + ca;
+  const bool sl0 = le_ord(unL - cL, am) || val(am) != val(am);  // SL from the left state
+  const bool sr0 = le_ord(ap, unR + cR) || val(ap) != val(ap);  // SR from the right state
   const T SL = sl0 ? unL - cL : ua - ca;
   const T SR = sr0 ? unR + cR : ua + ca;
   const T mL = rL * unL, mR = rR * unR;

@@ -20,7 +20,8 @@ import time
 import numpy as np
 
 
-def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int | None = None):
+def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int | None = None,
+        dump: str | None = None):
     import torch
 
     from . import build, inputs, teno
@@ -57,18 +58,24 @@ def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int
         t = ctx(precision)
         Ud = torch.from_numpy(U0).cuda()
         t.set_state(Ud)
-        Un, U1, U2 = (torch.empty_like(Ud) for _ in range(3))
+        Un, U1, U2, prev = (torch.empty_like(Ud) for _ in range(4))
         tm, n, per_stage = 0.0, 0, []
         torch.cuda.synchronize()
         w0 = time.perf_counter()
         step_s = 0.0
+        failure = None
         while tm < t_end - 1e-14:
             dt = min(t.cfl_dt(), t_end - tm)
             sample = name == "fp64_pairs" and n % sample_every == 0
+            t.get_state(prev)
             if sample:
-                t.get_state(Un)
+                Un.copy_(prev)
             s0 = time.perf_counter()
-            t.rk3_step(dt)
+            try:
+                t.rk3_step(dt)
+            except teno.TenoError as e:
+                failure = _failure(mesh, t, prev, n, tm, dt, str(e), dump, name)
+                break
             step_s += time.perf_counter() - s0
             if sample:
                 t.stage_state(1, U1)
@@ -76,23 +83,26 @@ def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int
                 per_stage.append([n, tm] + [flips(Us, tm) for Us in (Un, U1, U2)])
             tm += dt
             n += 1
-        t.check_state()
+        if failure is None:
+            t.check_state()
         torch.cuda.synchronize()
         wall = time.perf_counter() - w0
         U = t.get_state()
         rho = U[0]
         p = 0.4 * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / rho)
         rec = {"steps": n, "t": tm, "wall_s": wall,
-               "cell_stage_per_s_in_steps": n_cell * 3 * n / step_s,
+               "cell_stage_per_s_in_steps": n_cell * 3 * n / max(step_s, 1e-30),
+               "failure": failure,
                "finite": bool(np.isfinite(U).all()), "rho_min": float(rho.min()),
                "p_min": float(p.min()), "rho_max": float(rho.max())}
-        if name == "fp64_pairs":
+        if name == "fp64_pairs" and per_stage:
             fl = np.array([r[2:] for r in per_stage])
             rec["flip_rate_per_stage"] = {
                 "sampled_steps": len(per_stage), "every": sample_every,
                 "mean": fl.mean(axis=0).tolist(), "max": fl.max(axis=0).tolist(),
                 "overall_max": float(fl.max()), "overall_mean": float(fl.mean()),
                 "samples": [[int(r[0]), float(r[1])] + r[2:] for r in per_stage]}
+        if name == "fp64_pairs":
             rho64 = rho.copy()
         else:
             rec["mean_abs_rho_diff_vs_fp64_over_mean_rho"] = float(
@@ -104,6 +114,31 @@ def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int
     return out
 
 
+def _failure(mesh, t, prev, n, tm, dt, msg, dump, name):
+    """Where a step produced a non-physical state: the step, the time, the
+    first non-physical cells and their centroids; the state before the step
+    goes to `dump` (npz) when given."""
+    U = t.get_state()
+    rho = U[0]
+    p = 0.4 * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / rho)
+    bad = np.where(~(np.isfinite(U).all(axis=0) & (rho > 0) & (p > 0)))[0]
+    cen = mesh.unwrapped_vertices().mean(axis=1)
+    out = {"step": n, "t": tm, "dt": dt, "message": msg, "n_bad": int(len(bad)),
+           "bad_cells": bad[:20].tolist(), "centroids": cen[bad[:20]].tolist()}
+    if dump and len(bad):
+        # the state before the step within 0.1 of the failing cells: all that
+        # the residual of those cells depends on
+        Up = prev.cpu().numpy()
+        d2 = np.full(len(cen), np.inf)
+        for c in bad[:50]:
+            d2 = np.minimum(d2, ((cen - cen[c]) ** 2).sum(axis=1))
+        near = np.where(d2 < 0.01)[0]
+        np.savez_compressed(f"{dump}_{name}.npz", cells=near, U=Up[:, near], t=tm, dt=dt,
+                            step=n, bad=bad)
+        out["dump"] = f"{dump}_{name}.npz"
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--nx", type=int, default=2048)
@@ -111,8 +146,10 @@ def main():
     ap.add_argument("--order", type=int, default=6)
     ap.add_argument("--t-end", type=float, default=0.2)
     ap.add_argument("--sample-every", type=int, default=50)
+    ap.add_argument("--dump", default=None,
+                    help="path prefix: where a step fails, the state before it (npz)")
     a = ap.parse_args()
-    print(json.dumps(run(a.nx, a.ny, a.order, a.t_end, a.sample_every)))
+    print(json.dumps(run(a.nx, a.ny, a.order, a.t_end, a.sample_every, dump=a.dump)))
 
 
 if __name__ == "__main__":

@@ -93,6 +93,9 @@ def lib(build_if_missing: bool = False):
         "teno_colour_slots": (C.c_int, [C.c_int32, C.c_int32, _vp, _vp]),
         "teno_fma_peak": (C.c_int, [C.c_int, _vp, C.c_int, _vp]),
         "teno_precompute_partition": (C.c_int, [_vp, _vp, C.c_int32, C.c_int32]),
+        "teno_tape_reserve": (C.c_int, [_vp, C.c_int32]),
+        "teno_rk3_step_record": (C.c_int, [_vp, C.c_int32, C.c_double]),
+        "teno_adjoint_step_tape": (C.c_int, [_vp, C.c_int32, _vp, _vp, C.c_int]),
         "teno_partition_sizes": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
         "teno_partition_cells": (C.c_int, [_vp, _vp]),
         "teno_partition_recv_cells": (C.c_int, [_vp, C.c_int32, _vp]),
@@ -454,6 +457,27 @@ class Teno:
         if wdev != odev:
             raise ValueError("w and out must both be host or both be device arrays")
         self._chk(lib().teno_residual_vjp(self._h, wp, op, wdev))
+        return out
+
+    def tape_reserve(self, n_slots: int):
+        """Room for n_slots recorded SSP-RK3 steps (teno_tape_reserve)."""
+        self._chk(lib().teno_tape_reserve(self._h, int(n_slots)))
+
+    def rk3_step_record(self, slot: int, dt: float):
+        """One SSP-RK3 step recorded in tape slot `slot`."""
+        self._chk(lib().teno_rk3_step_record(self._h, int(slot), float(dt)))
+
+    def adjoint_step_tape(self, slot: int, lam_np1, out=None):
+        """The adjoint of the step recorded in `slot` (no reconstruction)."""
+        if isinstance(lam_np1, np.ndarray):
+            lam_np1 = np.ascontiguousarray(lam_np1, dtype=np.float64)
+        if out is None:
+            out = np.empty((self.n_var, self.n_cell))
+        lp, ldev = _ptr(lam_np1)
+        op, odev = _ptr(out)
+        if ldev != odev:
+            raise ValueError("lam_np1 and out must both be host or both be device arrays")
+        self._chk(lib().teno_adjoint_step_tape(self._h, int(slot), lp, op, ldev))
         return out
 
     def adjoint_step(self, dt: float, lam_np1, out=None):

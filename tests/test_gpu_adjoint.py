@@ -108,3 +108,43 @@ def test_vortex_objective_gradient_vs_fd(env):
     errs = np.array(errs)
     print("FD relative errors:", np.array2string(errs, precision=2))
     assert np.median(errs) < 1e-5 and (errs < 1e-4).mean() >= 0.8
+
+
+@pytest.mark.parametrize("precision,order,flux", [(0, 5, 1), (0, 6, 2), (2, 5, 1)],
+                         ids=["pairs-teno5", "pairs-teno6-hllc", "native-teno5"])
+def test_tape_adjoint_equals_replayed_adjoint(env, precision, order, flux):
+    """The adjoint of recorded steps (teno_adjoint_step_tape: no
+    reconstruction) is the same bits as teno_adjoint_step, which replays the
+    step's stages from its initial state."""
+    torch, teno, ag = env
+    mesh = inputs.jittered_mesh(17, 16, 10.0, 10.0, seed=1005)
+    U = inputs.cell_average(mesh, inputs.isentropic_vortex)
+    t = teno.Teno(device=0).load(mesh)
+    t.precompute_stencils(order=order, n_var=4, flux=flux, precision=precision)
+    dt = 0.02
+    t.set_state(U)
+    t.tape_reserve(3)
+    states = []
+    for k in range(3):
+        states.append(t.get_state())
+        t.rk3_step_record(k, dt)
+    end = t.get_state()
+    lam = inputs.random_directions(3006, 1, U.size)[0].reshape(U.shape)
+    taped, l = [], lam
+    for k in (2, 1, 0):
+        l = t.adjoint_step_tape(k, l)
+        taped.append(l)
+    assert np.array_equal(t.get_state(), end)  # the taped adjoint leaves the state alone
+    ref, l = [], lam
+    for k in (2, 1, 0):
+        t.set_state(states[k])
+        l = t.adjoint_step(dt, l)
+        ref.append(l)
+    for a, b in zip(taped, ref):
+        assert np.array_equal(a, b)
+    # the recorded forward steps are the plain steps
+    t.set_state(U)
+    for _ in range(3):
+        t.rk3_step(dt)
+    assert np.array_equal(t.get_state(), end)
+    t.tape_reserve(0)
