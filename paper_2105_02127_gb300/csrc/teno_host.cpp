@@ -2434,10 +2434,14 @@ int group_link(teno_ctx* const* parts, int32_t n) {
     teno_ctx* cp = parts[p];
     for (int32_t q = 0; q < n; ++q) {
       if (q == p) continue;
+      // each buffer serves both directions: the forward exchange sends the
+      // cells q receives and receives the cells q owns here; the reverse
+      // exchange the other way round
       const size_t nv = cp->prm.n_var;
-      int rc = dev_alloc(cp, cp->b_xbuf[q], 8 * nv * std::max<size_t>(1, cp->send_loc[q].size()));
-      if (!rc) rc = dev_alloc(cp, cp->b_xbuf[n + q],
-                              8 * nv * std::max<size_t>(1, cp->recv_loc[q].size()));
+      const size_t cnt = std::max<size_t>(
+          1, std::max(cp->send_loc[q].size(), cp->recv_loc[q].size()));
+      int rc = dev_alloc(cp, cp->b_xbuf[q], 8 * nv * cnt);
+      if (!rc) rc = dev_alloc(cp, cp->b_xbuf[n + q], 8 * nv * cnt);
       if (rc) return rc;
     }
   }
@@ -2457,6 +2461,9 @@ int group_exchange(teno_ctx* const* parts, int32_t n, int32_t what) {
       teno_ctx* cs = parts[src];
       const size_t cnt = rev ? cs->recv_loc[dst].size() : cs->send_loc[dst].size();
       if (cnt == 0) continue;
+      const size_t need = 8 * (size_t)cd->prm.n_var * cnt;
+      if (cs->b_xbuf[dst].bytes < need || cd->b_xbuf[n + src].bytes < need)
+        return fail(cd, TENO_EINVAL, "group exchange: buffer smaller than the list");
       int rc = halo_pack(cs, dst, what, (double*)cs->b_xbuf[dst].p);
       if (rc) return rc;
       teno_ctx* ctx = cd;

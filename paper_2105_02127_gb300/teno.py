@@ -291,6 +291,7 @@ class Teno:
         self._chk(lib().teno_get_sizes(self._h, C.byref(n), C.byref(nv), C.byref(m),
                                        C.byref(ns)))
         self.m, self.ns = m.value, ns.value
+        self.n_out = self.n_cell
         return self
 
     def precompute_partition(self, n_parts: int, part: int, params: teno_params | None = None,
@@ -307,6 +308,7 @@ class Teno:
                                        C.byref(ns)))
         self.m, self.ns = m.value, ns.value
         self.n_parts, self.part = int(n_parts), int(part)
+        self.n_out = self.partition_sizes()[0]  # a partition returns its owned cells
         return self
 
     def partition_sizes(self):
@@ -371,7 +373,7 @@ class Teno:
 
     def get_state(self, out=None):
         if out is None:
-            out = np.empty((self.n_var, self.n_cell))
+            out = np.empty((self.n_var, getattr(self, "n_out", self.n_cell)))
         p, dev = _ptr(out)
         self._chk(lib().teno_get_state(self._h, p, dev))
         return out
@@ -383,9 +385,10 @@ class Teno:
     def residual(self, out=None, sel=None, want_sel: bool = False):
         """R [n_var][n_cell] of the current state; returns (R, sel or None)."""
         if out is None:
-            out = np.empty((self.n_var, self.n_cell))
+            n = getattr(self, "n_out", self.n_cell)
+            out = np.empty((self.n_var, n))
             if want_sel and sel is None:
-                sel = np.empty((self.n_var, self.n_cell), dtype=np.uint8)
+                sel = np.empty((self.n_var, n), dtype=np.uint8)
         p, dev = _ptr(out)
         sp, sdev = _ptr(sel)
         if sel is not None and sdev != dev:
@@ -418,7 +421,7 @@ class Teno:
     def stage_state(self, stage: int, out=None):
         """Input state of stage 1 or 2 of the last SSP-RK3 step (U^(1), U^(2))."""
         if out is None:
-            out = np.empty((self.n_var, self.n_cell))
+            out = np.empty((self.n_var, getattr(self, "n_out", self.n_cell)))
         p, dev = _ptr(out)
         self._chk(lib().teno_get_stage_state(self._h, int(stage), p, dev))
         return out
