@@ -55,6 +55,7 @@ def lib():
         L.oracle_geometry.argtypes = [C.c_void_p, _dp, _dp, _ip]
         L.oracle_ghost.argtypes = [C.c_void_p, C.c_int, _dp, C.c_double, C.c_double, C.c_double,
                                    C.c_double, C.c_double, _dp]
+        L.oracle_face_flux.argtypes = [C.c_void_p, _dp, C.c_double, C.c_int64, C.c_int, _dp]
         L.oracle_char_basis.argtypes = [C.c_void_p, _dp, C.c_double, C.c_double, _dp, _dp]
         L.oracle_gauss_legendre.argtypes = [C.c_int, _dp, _dp]
     return _lib
@@ -229,6 +230,14 @@ class Oracle:
             return F, JL, JR
         lib().oracle_flux(self._h, UL, UR, nx, ny, x, y, F, None, None)
         return F
+
+    def face_flux(self, U, cell: int, edge: int, time: float = 0.0):
+        """K = |A| sum_k w_k F(U_L, U_R) of the face on local edge `edge` of
+        `cell` (which must own the face)"""
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        K = np.empty(self.n_var)
+        self._chk(lib().oracle_face_flux(self._h, U, time, cell, edge, K), "face_flux")
+        return K
 
     def ghost(self, tag: int, UL, nx: float, ny: float, x: float = 0.0, y: float = 0.0,
               time: float = 0.0):

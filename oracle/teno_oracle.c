@@ -42,7 +42,8 @@
  * xi eta^(d-1); D^q P sums every multi-index |alpha| = q once; N_q = 2 (third,
  * fourth order) or 3 (fifth, sixth order) Gauss-Legendre points per edge with
  * weights summing to one; chi_k = C_T counts as smooth; selection per cell and
- * per conservative variable; CFL length = 4|V|/perimeter.
+ * per conservative variable; CFL length = 4|V|/perimeter; at an outflow face
+ * both states are the cell average (zero gradient of the cell averages).
  *
  * Stencil readings (exact, so both implementations agree index for index):
  *   centroid c = ((v0 + v1) + v2) / 3 of the unwrapped vertices; the offset
@@ -1526,6 +1527,10 @@ static void face_flux(const omesh* M, int64_t c, int e, const double* U, const r
     double x = P[2 * e] + M->gt[k] * dx, y = P[2 * e + 1] + M->gt[k] * dy;
     double UL[4], UR[4], F[4];
     eval_point(M, c, U, Rc, e, x, y, UL);
+    /* outflow: the face takes the cell average (zero gradient of the cell
+     * averages), not the polynomial extrapolated to the boundary */
+    if (n < 0 && M->fbc[3 * c + e] == BC_OUTFLOW)
+      for (int v = 0; v < M->nvar; ++v) UL[v] = U[(int64_t)v * M->nc + c];
     if (n >= 0)
       eval_point(M, n, U, Rn, M->fedge[3 * c + e], x, y, UR);
     else
@@ -1719,8 +1724,10 @@ int oracle_residual_vjp(void* h, const double* U, double time, const double* w, 
   int nvar = M->nvar, nq = M->nq;
   recon_t* RC = (recon_t*)malloc(sizeof(recon_t) * nc);
   for (int64_t c = 0; c < nc; ++c) reconstruct(M, c, U, sel_in, &RC[c]);
-  /* adjoint of the Gauss-point values: Ubar[c][e][k][v] */
+  /* adjoint of the Gauss-point values: Ubar[c][e][k][v]; of the cell
+   * averages taken directly by outflow faces: direct[v][c] */
   double* Ubar = (double*)calloc(nc * 3 * nq * nvar, sizeof(double));
+  double* direct = (double*)calloc(nc * nvar, sizeof(double));
   for (int64_t c = 0; c < nc; ++c)
     for (int e = 0; e < 3; ++e) {
       if (!is_owner(M, c, e)) continue;
@@ -1740,6 +1747,9 @@ int oracle_residual_vjp(void* h, const double* U, double time, const double* w, 
         double x = P[2 * e] + M->gt[k] * dx, y = P[2 * e + 1] + M->gt[k] * dy;
         double UL[4], UR[4], JL[16], JR[16];
         eval_point(M, c, U, &RC[c], e, x, y, UL);
+        const int outflow = n < 0 && M->fbc[3 * c + e] == BC_OUTFLOW;
+        if (outflow)
+          for (int v = 0; v < nvar; ++v) UL[v] = U[(int64_t)v * nc + c];
         if (n >= 0)
           eval_point(M, n, U, &RC[n], M->fedge[3 * c + e], x, y, UR);
         else
@@ -1771,7 +1781,10 @@ int oracle_residual_vjp(void* h, const double* U, double time, const double* w, 
             for (int i = 0; i < nvar; ++i) bl[j] += G[i * nvar + j] * br[i];
         }
         for (int v = 0; v < nvar; ++v) {
-          Ubar[((c * 3 + e) * nq + k) * nvar + v] += bl[v];
+          if (outflow)
+            direct[(int64_t)v * nc + c] += bl[v];
+          else
+            Ubar[((c * 3 + e) * nq + k) * nvar + v] += bl[v];
           if (n >= 0) {
             /* the neighbour's point k on this face, stored by physical point */
             int en = M->fedge[3 * c + e];
@@ -1781,7 +1794,8 @@ int oracle_residual_vjp(void* h, const double* U, double time, const double* w, 
       }
     }
   /* adjoint of the reconstruction: P(x) = U0 + sum_l coef_l psi_l(x) */
-  for (int64_t i = 0; i < nvar * nc; ++i) vout[i] = 0.0;
+  for (int64_t i = 0; i < nvar * nc; ++i) vout[i] = direct[i];
+  free(direct);
   for (int64_t c = 0; c < nc; ++c) {
     const double* P = M->P + 6 * c;
     double cbar[MAXVAR][MAXM];
@@ -1901,6 +1915,23 @@ void oracle_flux(void* h, const double* UL, const double* UR, double nx, double 
   omesh* M = (omesh*)h;
   num_flux(M, UL, UR, nx, ny, x, y, F);
   if (JL && JR) flux_jac(M, UL, UR, nx, ny, x, y, JL, JR);
+}
+
+/* face flux K of owner cell c, local edge e (for pins): K [nvar]; the face
+ * must be owned by c (a boundary face, or c the smaller id) */
+int oracle_face_flux(void* h, const double* U, double time, int64_t c, int e, double* K) {
+  omesh* M = (omesh*)h;
+  if (c < 0 || c >= M->nc || e < 0 || e > 2 || !is_owner(M, c, e)) return E_INVAL;
+  const int64_t n = M->fnbr[3 * c + e];
+  int64_t cells[2] = {c, n >= 0 ? n : c};
+  int rc = oracle_prepare(h, 2, cells);
+  if (rc) return rc;
+  M->time = time;
+  recon_t Rc, Rn;
+  reconstruct(M, c, U, NULL, &Rc);
+  if (n >= 0) reconstruct(M, n, U, NULL, &Rn);
+  face_flux(M, c, e, U, &Rc, n >= 0 ? &Rn : NULL, K, NULL, NULL);
+  return E_OK;
 }
 
 /* boundary ghost state at face point (x, y) with outward unit normal

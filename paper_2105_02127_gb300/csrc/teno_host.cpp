@@ -62,6 +62,7 @@ struct teno_ctx {
   std::vector<int32_t> v2c_off, v2c;      // vertex -> cells (user)
   std::vector<int32_t> perm, iperm;       // perm[internal] = user, iperm[user] = internal
   bool has_time_bc = false;
+  bool has_outflow = false;  // some boundary face is an outflow face
   // scheme
   teno_params prm{};
   int m = 0, ns = 0, nq = 0, E = 0, SL = 0;
@@ -78,6 +79,7 @@ struct teno_ctx {
   bool stages_ok = false; // b_U1, b_U2 hold the stage states of the last RK3 step
   // adjoint
   DevBuf b_rev_off, b_rev_idx, b_dbar, b_uself, b_Uqbar, b_l1, b_l2, b_lamn, b_vtmp, b_selA;
+  DevBuf b_ubd;  // [cell][edge][var] cotangents of outflow faces' cell averages
   DevBuf b_Uq_st[2], b_sel_st[2];  // stage 1, 2 reconstructions kept by the adjoint replay
   bool adj_ok = false;
   std::vector<int64_t> rev_off_h;
@@ -312,6 +314,7 @@ int build_mesh(teno_ctx* ctx, const double* xy, const int32_t* tri, int64_t nbf,
         return fail(ctx, TENO_EMESH, "boundary edge without a bface entry");
       ctx->fbc[3 * ed[i].cell + ed[i].edge] = it->second;
       if (it->second == TENO_BC_TOP) ctx->has_time_bc = true;
+      if (it->second == TENO_BC_OUTFLOW) ctx->has_outflow = true;
     } else {
       return fail(ctx, TENO_EMESH, "edge shared by more than two cells");
     }
@@ -1527,7 +1530,7 @@ int stage_flux(teno_ctx* ctx, const double* U, uint8_t* sel_out, double time,
   if (ctx->dm.positivity) CK(launch_positivity(ctx->dm, U, uq, ctx->stream), "positivity launch");
   prof_end(ctx, pe);
   pe = prof_begin(ctx, K_FLUX);
-  CK(launch_face_flux(ctx->dm, uq, ctx->b_K.p, time, ctx->stream), "face flux launch");
+  CK(launch_face_flux(ctx->dm, U, uq, ctx->b_K.p, time, ctx->stream), "face flux launch");
   prof_end(ctx, pe);
   return TENO_OK;
 }
@@ -1623,6 +1626,12 @@ int ensure_adjoint(teno_ctx* ctx) {
   // face no owned cell, and the own terms of halo cells, unwritten: zero
   CK(cudaMemsetAsync(ctx->b_Uqbar.p, 0, ctx->b_Uqbar.bytes, ctx->stream), "memset");
   CK(cudaMemsetAsync(ctx->b_uself.p, 0, ctx->b_uself.bytes, ctx->stream), "memset");
+  if (ctx->has_outflow) {
+    // written for outflow edges only, zero elsewhere
+    rc = dev_alloc(ctx, ctx->b_ubd, sizeof(double) * 3 * nv * npad);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(ctx->b_ubd.p, 0, ctx->b_ubd.bytes, ctx->stream), "memset");
+  }
   ctx->adj_ok = true;
   return TENO_OK;
 }
@@ -1652,7 +1661,8 @@ int vjp_internal(teno_ctx* ctx, const double* U, const double* w, double* v, dou
     if (!sel_in) sel = sel_out;
   }
   long pe = prof_begin(ctx, K_FLUX_VJP);
-  CK(launch_face_flux_vjp(ctx->dm, uq, w, (double*)ctx->b_Uqbar.p, time, ctx->stream),
+  double* ubd = ctx->has_outflow ? (double*)ctx->b_ubd.p : nullptr;
+  CK(launch_face_flux_vjp(ctx->dm, U, uq, w, (double*)ctx->b_Uqbar.p, ubd, time, ctx->stream),
      "flux vjp launch");
   prof_end(ctx, pe);
   pe = prof_begin(ctx, K_RECON_VJP);
@@ -1669,12 +1679,12 @@ int vjp_internal(teno_ctx* ctx, const double* U, const double* w, double* v, dou
   if (ctx->adj_tiled)
     CK(launch_scatter_gather(ctx->dm, (const int64_t*)ctx->b_hrev_off.p,
                              (const int32_t*)ctx->b_hrev_idx.p, (const double*)ctx->b_hpart.p,
-                             (const double*)ctx->b_uself.p, v, ctx->stream),
+                             (const double*)ctx->b_uself.p, v, ubd, ctx->stream),
        "scatter launch");
   else
     CK(launch_scatter_gather(ctx->dm, (const int64_t*)ctx->b_rev_off.p,
                              (const int32_t*)ctx->b_rev_idx.p, (const double*)ctx->b_dbar.p,
-                             (const double*)ctx->b_uself.p, v, ctx->stream),
+                             (const double*)ctx->b_uself.p, v, ubd, ctx->stream),
        "scatter launch");
   prof_end(ctx, pe);
   return TENO_OK;
@@ -1786,6 +1796,7 @@ int teno_destroy(teno_ctx* ctx) {
                     &ctx->b_sel_st[1]};
   for (DevBuf* b : bufs) dev_free(*b);
   dev_free(ctx->b_perm_in);
+  dev_free(ctx->b_ubd);
   for (DevBuf& b : ctx->tape) dev_free(b);
   for (auto* v : {&ctx->b_recv_idx, &ctx->b_send_idx, &ctx->b_xbuf})
     for (DevBuf& b : *v) dev_free(b);
@@ -1815,6 +1826,7 @@ int teno_mesh_load(teno_ctx* ctx, int64_t n_vert, const double* xy, int64_t n_ce
   ctx->mesh_ok = ctx->pre_ok = ctx->state_ok = ctx->adj_ok = ctx->stages_ok = false;
   ctx->override_on = false;
   ctx->has_time_bc = false;
+  ctx->has_outflow = false;
   ctx->nv = n_vert;
   ctx->nc = n_cell;
   ctx->npad = (n_cell + kTile - 1) / kTile * kTile;

@@ -111,8 +111,9 @@ cudaError_t launch_positivity(const DeviceMesh& dm, const double* U, void* Uq, c
 // charvar: projection, per-field selection and Gauss-point values from the
 // coefficients the reconstruction wrote to dm.coef_out
 cudaError_t launch_char_finish(const DeviceMesh& dm, const double* U, void* Uq, cudaStream_t st);
-cudaError_t launch_face_flux(const DeviceMesh& dm, const void* Uq, void* K, double time,
-                             cudaStream_t st);
+// U: the cell averages (outflow faces take them on both sides)
+cudaError_t launch_face_flux(const DeviceMesh& dm, const double* U, const void* Uq, void* K,
+                             double time, cudaStream_t st);
 // mode 0: R = residual; mode 1: U_out = cn*Un + cs*(Us + dt*R), and (split
 // non-null) the FP32 hi/lo split of U_out
 cudaError_t launch_gather(const DeviceMesh& dm, const void* K, const double* Un, const double* Us,
@@ -141,8 +142,11 @@ cudaError_t launch_halo_unpack(double* U, int64_t ld, const int32_t* idx, int64_
 // adjoint kernels.  Uq_bar ([cell][edge point][var], 8 bytes an entry)
 // holds (hi, lo) float pairs on the TENO_FP64 path and doubles on the native
 // path; the reconstruction VJPs read it in the same form.
-cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const double* w,
-                                 double* Uq_bar, double time, cudaStream_t st);
+// ubd [cell][edge][var] (null on meshes without outflow faces): the cotangent of
+// the cell average an outflow face takes, summed over its Gauss points
+cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const double* U, const void* Uq,
+                                 const double* w, double* Uq_bar, double* ubd, double time,
+                                 cudaStream_t st);
 cudaError_t launch_recon_vjp(const DeviceMesh& dm, const uint8_t* sel, const double* Uq_bar,
                              double* d_bar, double* u_self, cudaStream_t st);
 // Tiled reconstruction VJP (FP64 path, Euler, per-tile halos present):
@@ -153,6 +157,7 @@ cudaError_t launch_recon_vjp_tma(const DeviceMesh& dm, const uint8_t* sel, const
                                  double* part, double* u_self, cudaStream_t st);
 cudaError_t launch_scatter_gather(const DeviceMesh& dm, const int64_t* rev_off,
                                   const int32_t* rev_idx, const double* d_bar,
-                                  const double* u_self, double* v, cudaStream_t st);
+                                  const double* u_self, double* v, const double* ubd,
+                                  cudaStream_t st);
 
 }  // namespace teno

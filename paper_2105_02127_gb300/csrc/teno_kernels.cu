@@ -2663,6 +2663,8 @@ struct FaceArgs {
   const int8_t* f_edges;
   const double* f_geom;
   const float2* f_geom2;  // [n_face][3] nx, ny, |A| as (hi, lo) pairs
+  const double* U;        // cell averages [n_var][n_pad] (outflow faces take them)
+  int64_t n_pad;
   int64_t n_face;
   double gamma, adv_x, adv_y, time;
   int adv_field;
@@ -2765,6 +2767,12 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const FaceArgs a, const 
     if (n >= 0) {
       ld_group<NV>(Uq + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV, UR);
     } else if constexpr (NV == 4) {
+      // an outflow face takes the cell average on both sides (zero gradient
+      // of the cell averages), not the polynomial extrapolated to it
+      if (en == TENO_BC_OUTFLOW) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) UL[v] = cst<T>(a.U[v * a.n_pad + o]);
+      }
       double x = a.f_geom[5 * f + 3] - ny * len * a.gt[k];
       ghost_state<T>(en, UL, nx, ny, x, a.time, a.gamma, UR);
     } else {
@@ -2996,6 +3004,8 @@ struct VjpArgs {
   const int8_t* f_edges;
   const double* f_geom;
   const float2* f_geom2;
+  const double* U;  // cell averages (outflow faces take them)
+  double* ubd;      // [cell][edge][var]: the cotangent of an outflow face's cell average
   float2 g2, gm12;
   int adv_field;
   double adv_cx, adv_cy, adv_omega, adv_r1, adv_r2;
@@ -3063,6 +3073,12 @@ __global__ void __launch_bounds__(128, TENO_VJP_MIN_BLOCKS > 0 ? TENO_VJP_MIN_BL
   S tl;  // |A| in the flux scalar type
   face_k<S>(a.f_geom, a.f_geom2, f, a.gamma, a.g2, a.gm12, rks, tl);
   const RiemannK<D> rk = riemann_k_dual<ND, S>(rks);
+  // an outflow face takes the owner's cell average (zero gradient of the cell
+  // averages): its cotangent goes to that average, summed over the points
+  const bool outflow = NV == 4 && n < 0 && en == TENO_BC_OUTFLOW;
+  double dl[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) dl[v] = 0.0;
   for (int k = 0; k < NQ; ++k) {
     TQ ul[NV], ur[NV];
     ld_group<NV>(Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV, ul);
@@ -3080,7 +3096,7 @@ __global__ void __launch_bounds__(128, TENO_VJP_MIN_BLOCKS > 0 ? TENO_VJP_MIN_BL
       S uL[NV], uR[NV], ULb[NV], URb[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        uL[v] = lift<S>(ul[v]);
+        uL[v] = outflow ? cst<S>(a.U[v * a.n_pad + o]) : lift<S>(ul[v]);
         ULb[v] = cst<S>(0.0);
         URb[v] = cst<S>(0.0);
       }
@@ -3092,6 +3108,13 @@ __global__ void __launch_bounds__(128, TENO_VJP_MIN_BLOCKS > 0 ? TENO_VJP_MIN_BL
       }
       euler_riemann_vjp<S>(uL, uR, rks, FLUX == TENO_FLUX_HLLC, Kw, ULb, URb);
       if (n < 0) ghost_vjp<S>(en, rks, URb, ULb);
+      if (outflow) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          dl[v] += to_d(ULb[v]);
+          ULb[v] = cst<S>(0.0);
+        }
+      }
       if constexpr (std::is_same<S, DF>::value) {
         st_group<NV>(reinterpret_cast<DF*>(outL), ULb);
         if (n >= 0) st_group<NV>(reinterpret_cast<DF*>(outR), URb);
@@ -3106,7 +3129,7 @@ __global__ void __launch_bounds__(128, TENO_VJP_MIN_BLOCKS > 0 ? TENO_VJP_MIN_BL
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           UL[v] = cst<D>(0.0);
-          UL[v].v = lift<S>(ul[v]);
+          UL[v].v = outflow ? cst<S>(a.U[v * a.n_pad + o]) : lift<S>(ul[v]);
           if (v >= dir0 && v < dir0 + ND) UL[v].d[v - dir0] = cst<S>(1.0);
         }
         if (n >= 0) {
@@ -3136,13 +3159,21 @@ __global__ void __launch_bounds__(128, TENO_VJP_MIN_BLOCKS > 0 ? TENO_VJP_MIN_BL
 #pragma unroll
           for (int i = 0; i < NV; ++i) sacc = madd(F[i].d[j], Kw[i], sacc);
           const int g = dir0 + j;
-          if (g < NV)
+          if (g < NV && outflow) {
+            dl[g] += to_d(sacc);
+            store_bar<S>(outL, g, cst<S>(0.0));
+          } else if (g < NV) {
             store_bar<S>(outL, g, sacc);
-          else if (n >= 0)
+          } else if (n >= 0) {
             store_bar<S>(outR, g - NV, sacc);
+          }
         }
       }
     }
+  }
+  if (outflow) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) a.ubd[((int64_t)o * 3 + eo) * NV + v] = dl[v];
   }
 }
 
@@ -3647,16 +3678,25 @@ template <int NV, typename TD>
 __global__ void __launch_bounds__(256) scatter_gather_kernel(const int64_t* __restrict__ rev_off,
                                                              const int32_t* __restrict__ rev_idx,
                                                              const TD* __restrict__ d_bar,
-                                                             const double* __restrict__ u_self,
+                                                             const double* __restrict__ u_self0,
                                                              double* __restrict__ out,
-                                                             int64_t n_cell, int64_t n_pad) {
+                                                             int64_t n_cell, int64_t n_pad,
+                                                             const double* __restrict__ ubd) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n_cell) return;
   const int64_t r0 = rev_off[j], r1 = rev_off[j + 1];
+  // the cell's own term, plus what its outflow faces (if any) owe its average
+  double u_self[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    u_self[v] = u_self0[v * n_pad + j];
+    if (ubd) u_self[v] += (ubd[(j * 3 + 0) * NV + v] + ubd[(j * 3 + 1) * NV + v]) +
+                          ubd[(j * 3 + 2) * NV + v];
+  }
   if constexpr (std::is_same<TD, DF>::value) {
     DF acc[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = d_to_df(u_self[v * n_pad + j]);
+    for (int v = 0; v < NV; ++v) acc[v] = d_to_df(u_self[v]);
     int64_t r = r0;
     if constexpr (NV == 4) {
       // kScatterBatch entries per round: every index, then every sector, is
@@ -3700,7 +3740,7 @@ __global__ void __launch_bounds__(256) scatter_gather_kernel(const int64_t* __re
   } else {
     double acc[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = u_self[v * n_pad + j];
+    for (int v = 0; v < NV; ++v) acc[v] = u_self[v];
     for (int64_t r = r0; r < r1; ++r) {
       const TD* e = d_bar + (int64_t)rev_idx[r] * NV;
       if constexpr (NV == 4) {
@@ -3901,6 +3941,8 @@ static FaceArgs face_args(const DeviceMesh& dm, double time) {
   a.f_edges = dm.f_edges;
   a.f_geom = dm.f_geom;
   a.f_geom2 = dm.f_geom2;
+  a.U = nullptr;
+  a.n_pad = dm.n_pad;
   a.n_face = dm.n_face;
   a.gamma = dm.gamma;
   a.adv_x = dm.adv_x;
@@ -3922,9 +3964,10 @@ static FaceArgs face_args(const DeviceMesh& dm, double time) {
   return a;
 }
 
-cudaError_t launch_face_flux(const DeviceMesh& dm, const void* Uq, void* K, double time,
-                             cudaStream_t st) {
+cudaError_t launch_face_flux(const DeviceMesh& dm, const double* U, const void* Uq, void* K,
+                             double time, cudaStream_t st) {
   FaceArgs a = face_args(dm, time);
+  a.U = U;
   const unsigned grid = (unsigned)((dm.n_face + 255) / 256);
   auto go = [&](auto nvc, auto nqc, auto flc) -> cudaError_t {
     constexpr int NV = decltype(nvc)::value, NQ = decltype(nqc)::value,
@@ -4072,13 +4115,16 @@ cudaError_t launch_axpby(double* out, const double* a, double ca, const double* 
 #endif
 constexpr int kVjpDirs = TENO_VJP_DIRS;
 
-cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const double* w,
-                                 double* Uq_bar, double time, cudaStream_t st) {
+cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const double* U, const void* Uq,
+                                 const double* w, double* Uq_bar, double* ubd, double time,
+                                 cudaStream_t st) {
   VjpArgs a;
   a.f_cells = dm.f_cells;
   a.f_edges = dm.f_edges;
   a.f_geom = dm.f_geom;
   a.f_geom2 = dm.f_geom2;
+  a.U = U;
+  a.ubd = ubd;
   a.g2 = split2(dm.gamma);
   a.gm12 = split2(dm.gamma - 1.0);
   a.inv_area = dm.inv_area;
@@ -4212,23 +4258,24 @@ cudaError_t launch_recon_vjp_tma(const DeviceMesh& dm, const uint8_t* sel, const
 
 cudaError_t launch_scatter_gather(const DeviceMesh& dm, const int64_t* rev_off,
                                   const int32_t* rev_idx, const double* d_bar,
-                                  const double* u_self, double* v, cudaStream_t st) {
+                                  const double* u_self, double* v, const double* ubd,
+                                  cudaStream_t st) {
   const unsigned grid = (unsigned)((dm.n_cell + 255) / 256);
   const bool pairs = dm.precision == TENO_FP64;  // d_bar holds (hi, lo) pairs
   if (dm.n_var == 1) {
     if (pairs)
       scatter_gather_kernel<1, DF><<<grid, 256, 0, st>>>(rev_off, rev_idx, (const DF*)d_bar,
-                                                         u_self, v, dm.n_cell, dm.n_pad);
+                                                         u_self, v, dm.n_cell, dm.n_pad, ubd);
     else
       scatter_gather_kernel<1, double><<<grid, 256, 0, st>>>(rev_off, rev_idx, d_bar, u_self, v,
-                                                             dm.n_cell, dm.n_pad);
+                                                             dm.n_cell, dm.n_pad, ubd);
   } else {
     if (pairs)
       scatter_gather_kernel<4, DF><<<grid, 256, 0, st>>>(rev_off, rev_idx, (const DF*)d_bar,
-                                                         u_self, v, dm.n_cell, dm.n_pad);
+                                                         u_self, v, dm.n_cell, dm.n_pad, ubd);
     else
       scatter_gather_kernel<4, double><<<grid, 256, 0, st>>>(rev_off, rev_idx, d_bar, u_self, v,
-                                                             dm.n_cell, dm.n_pad);
+                                                             dm.n_cell, dm.n_pad, ubd);
   }
   return cudaGetLastError();
 }

@@ -1049,3 +1049,38 @@ def test_hllc_zero_sound_speed(oracle_mod):
     assert np.isfinite(F0).all()
     F1 = o.flux(_euler(2.0, -3.0 * nx, -3.0 * ny, 1e-12), UR, nx, ny)
     np.testing.assert_allclose(F0, F1, rtol=1e-5, atol=1e-5)
+
+
+def test_outflow_face_takes_the_cell_average(oracle_mod):
+    """At an outflow face both states are the cell average (zero gradient of
+    the cell averages): the face flux is |A| F(U_0).n exactly (HLL and HLLC are
+    consistent), although the cell's polynomial differs from its average on
+    that face.  Extrapolating the sixth-order polynomial to the outflow face
+    instead made seeded noise at the shock case's outflow corner grow."""
+    mesh = inputs.jittered_mesh(24, 8, 4.0, 1.0, seed=1003, periodic=False,
+                                bc_tagger=inputs.dmr_bc_tagger)
+
+    def f(x, y):
+        return inputs.prim_to_cons(1.4 + 0.3 * np.sin(3 * x + 2 * y), 0.2 + 0.1 * np.cos(2 * y),
+                                   -0.1 + 0.05 * x, 1.0 + 0.2 * np.sin(x * y), 1.4)
+    U = inputs.cell_average(mesh, f)
+    V = mesh.unwrapped_vertices()
+    tags = {}
+    for a, b, t in mesh.bface:
+        tags[(min(a, b), max(a, b))] = t
+    checked = 0
+    for flux in (1, 2):
+        o = oracle_mod.Oracle(mesh, order=6, n_var=4, flux=flux)
+        for c in range(mesh.n_cell):
+            for e in range(3):
+                a, b = mesh.tri[c, e], mesh.tri[c, (e + 1) % 3]
+                if tags.get((min(a, b), max(a, b))) != 3:
+                    continue
+                d = V[c, (e + 1) % 3] - V[c, e]
+                ln = np.hypot(*d)
+                nx, ny = d[1] / ln, -d[0] / ln
+                K = o.face_flux(U, c, e)
+                np.testing.assert_allclose(K, ln * _phys_flux_n(U[:, c], nx, ny), rtol=1e-13,
+                                           atol=1e-13)
+                checked += 1
+    assert checked >= 16
