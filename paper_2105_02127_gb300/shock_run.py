@@ -9,7 +9,8 @@ U^(1), U^(2)); their flip rate per stage is the fraction of (cell, variable)
 selections that differ.  Prints one JSON object.
 
   python -m paper_2105_02127_gb300.shock_run [--nx 2048] [--ny 512] [--order 6]
-                                             [--t-end 0.2] [--sample-every 50]
+                                             [--t-end 0.2] [--sample-every 50] [--cfl 0.4]
+                                             [--legs fp64_pairs,fp32_mixed] [--dump PREFIX]
 """
 from __future__ import annotations
 
@@ -21,7 +22,7 @@ import numpy as np
 
 
 def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int | None = None,
-        dump: str | None = None):
+        dump: str | None = None, cfl: float = 0.4, legs=("fp64_pairs", "fp32_mixed")):
     import torch
 
     from . import build, inputs, teno
@@ -35,12 +36,13 @@ def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int
 
     def ctx(precision):
         t = teno.Teno(device=0).load(mesh)
-        t.precompute_stencils(order=order, n_var=4, flux=flux, precision=precision, positivity=1)
+        t.precompute_stencils(order=order, n_var=4, flux=flux, precision=precision, positivity=1,
+                              cfl=cfl)
         return t
 
     out = {"workload": f"double Mach reflection, [0,4]x[0,1], jittered {nx}x{ny} split quads = "
                        f"{n_cell} triangles, TENO{order}, "
-                       f"{'HLLC' if flux == teno.FLUX_HLLC else 'HLL'}, SSP-RK3, CFL 0.4, "
+                       f"{'HLLC' if flux == teno.FLUX_HLLC else 'HLL'}, SSP-RK3, CFL {cfl}, "
                        f"positivity scaling, t_end {t_end}",
            "n_cell": n_cell}
     probes = (ctx(teno.FP64), ctx(teno.FP32_MIXED))
@@ -54,7 +56,10 @@ def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int
             p.residual(out=Rb, sel=sel)
         return float((sels[0] != sels[1]).double().mean().item())
 
+    rho64 = None
     for name, precision in (("fp64_pairs", teno.FP64), ("fp32_mixed", teno.FP32_MIXED)):
+        if name not in legs:
+            continue
         t = ctx(precision)
         Ud = torch.from_numpy(U0).cuda()
         t.set_state(Ud)
@@ -104,7 +109,7 @@ def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int
                 "samples": [[int(r[0]), float(r[1])] + r[2:] for r in per_stage]}
         if name == "fp64_pairs":
             rho64 = rho.copy()
-        else:
+        elif rho64 is not None:
             rec["mean_abs_rho_diff_vs_fp64_over_mean_rho"] = float(
                 np.abs(rho - rho64).mean() / np.abs(rho64).mean())
         out[name] = rec
@@ -116,14 +121,21 @@ def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int
 
 def _failure(mesh, t, prev, n, tm, dt, msg, dump, name):
     """Where a step produced a non-physical state: the step, the time, the
-    first non-physical cells and their centroids; the state before the step
-    goes to `dump` (npz) when given."""
-    U = t.get_state()
-    rho = U[0]
-    p = 0.4 * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / rho)
-    bad = np.where(~(np.isfinite(U).all(axis=0) & (rho > 0) & (p > 0)))[0]
+    stage (1, 2: the stage outputs U^(1), U^(2); 3: the new state), the first
+    non-physical cells and their centroids; the state before the step goes to
+    `dump` (npz) when given."""
+    def bad_cells(U):
+        rho = U[0]
+        p = 0.4 * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / rho)
+        return np.where(~(np.isfinite(U).all(axis=0) & (rho > 0) & (p > 0)))[0]
+    bad, stage = np.array([], dtype=np.int64), 0
+    for k, U in ((1, t.stage_state(1)), (2, t.stage_state(2)), (3, t.get_state())):
+        b = bad_cells(U)
+        if len(b):
+            bad, stage = b, k
+            break
     cen = mesh.unwrapped_vertices().mean(axis=1)
-    out = {"step": n, "t": tm, "dt": dt, "message": msg, "n_bad": int(len(bad)),
+    out = {"step": n, "t": tm, "dt": dt, "message": msg, "stage": stage, "n_bad": int(len(bad)),
            "bad_cells": bad[:20].tolist(), "centroids": cen[bad[:20]].tolist()}
     if dump and len(bad):
         # the state before the step within 0.1 of the failing cells: all that
@@ -148,8 +160,11 @@ def main():
     ap.add_argument("--sample-every", type=int, default=50)
     ap.add_argument("--dump", default=None,
                     help="path prefix: where a step fails, the state before it (npz)")
+    ap.add_argument("--cfl", type=float, default=0.4)
+    ap.add_argument("--legs", default="fp64_pairs,fp32_mixed")
     a = ap.parse_args()
-    print(json.dumps(run(a.nx, a.ny, a.order, a.t_end, a.sample_every, dump=a.dump)))
+    print(json.dumps(run(a.nx, a.ny, a.order, a.t_end, a.sample_every, dump=a.dump, cfl=a.cfl,
+                         legs=tuple(a.legs.split(",")))))
 
 
 if __name__ == "__main__":
