@@ -1021,13 +1021,17 @@ static void euler_fx(double g, const double* W, double* F) {
 }
 
 /* Einfeldt wave speeds from Roe averages (Eq. wavespeed), in the rotated
- * frame; the Roe sound speed uses both velocity components */
+ * frame; the Roe sound speed uses both velocity components.  The side sound
+ * speeds take a negative pressure as zero (a NaN pressure stays NaN): a
+ * Gauss state at the positivity floor has a pressure some 1e-15 of its
+ * energy, below what a lower-precision evaluation resolves, and its wave
+ * speed is then the particle speed, not the Roe bound alone. */
 static void wave_speeds(double g, const double* WL, const double* WR, double* SL, double* SR) {
   double rL = WL[0], uL = WL[1] / rL, vL = WL[2] / rL;
   double rR = WR[0], uR = WR[1] / rR, vR = WR[2] / rR;
   double pL = (g - 1.0) * (WL[3] - 0.5 * rL * (uL * uL + vL * vL));
   double pR = (g - 1.0) * (WR[3] - 0.5 * rR * (uR * uR + vR * vR));
-  double cL = sqrt(g * pL / rL), cR = sqrt(g * pR / rR);
+  double cL = sqrt(g * (pL < 0.0 ? 0.0 : pL) / rL), cR = sqrt(g * (pR < 0.0 ? 0.0 : pR) / rR);
   double HL = (WL[3] + pL) / rL, HR = (WR[3] + pR) / rR;
   double D = sqrt(rR / rL);
   double ut = (uL + uR * D) / (1.0 + D);
@@ -1181,9 +1185,12 @@ static dual dscale(double s, dual a) {
 static dual dsqrt(dual a) {
   dual r;
   r.v = sqrt(a.v);
-  for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] / (2.0 * r.v);
+  /* the root of a constant zero (a clamped pressure) has no derivative */
+  for (int i = 0; i < ND; ++i) r.d[i] = r.v == 0.0 ? 0.0 : a.d[i] / (2.0 * r.v);
   return r;
 }
+/* a negative pressure taken as zero in a sound speed (see wave_speeds) */
+static dual dpos(dual a) { return a.v < 0.0 ? dc(0.0) : a; }
 static dual dmin(dual a, dual b) { return a.v <= b.v ? a : b; }
 static dual dmax(dual a, dual b) { return a.v >= b.v ? a : b; }
 
@@ -1220,7 +1227,7 @@ static void num_flux_d(const omesh* M, const dual* UL, const dual* UR, double nx
   dual rR = WR[0], uR = ddiv(WR[1], rR), vR = ddiv(WR[2], rR);
   dual pL = dscale(g - 1.0, dsub(WL[3], dscale(0.5, dmul(rL, dadd(dmul(uL, uL), dmul(vL, vL))))));
   dual pR = dscale(g - 1.0, dsub(WR[3], dscale(0.5, dmul(rR, dadd(dmul(uR, uR), dmul(vR, vR))))));
-  dual cL = dsqrt(ddiv(dscale(g, pL), rL)), cR = dsqrt(ddiv(dscale(g, pR), rR));
+  dual cL = dsqrt(ddiv(dscale(g, dpos(pL)), rL)), cR = dsqrt(ddiv(dscale(g, dpos(pR)), rR));
   dual HL = ddiv(dadd(WL[3], pL), rL), HR = ddiv(dadd(WR[3], pR), rR);
   dual D = dsqrt(ddiv(rR, rL));
   dual den = dadd(dc(1.0), D);

@@ -138,11 +138,15 @@ __device__ __forceinline__ Dual<N, S> operator/(const Dual<N, S>& a, const Dual<
   for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
   return r;
 }
+__device__ __forceinline__ double val(double x);
+__device__ __forceinline__ float val(float x);
 template <int N, typename S>
 __device__ __forceinline__ Dual<N, S> tsqrt(const Dual<N, S>& a) {
   Dual<N, S> r;
   r.v = tsqrt(a.v);
-  const S h = Cst<S>::from(0.5) / r.v;
+  // the root of a zero (a clamped pressure) carries no derivative
+  const bool z = val(r.v) == decltype(val(r.v))(0);
+  const S h = z ? r.v : Cst<S>::from(0.5) / r.v;
 #pragma unroll
   for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * h;
   return r;
@@ -335,6 +339,15 @@ template <int N>
 __device__ __forceinline__ bool nonneg(const Dual<N, DF>& x) {
   return x.v.h > 0.f || (x.v.h == 0.f && x.v.l >= 0.f);
 }
+// a pressure in a side sound speed: negative values as zero, NaN kept.  A
+// Gauss state at the positivity floor has a pressure about 1e-15 of its
+// energy, below the resolution of the pair and FP32 evaluations; its sound
+// speed is then zero, so the wave-speed bound is the particle speed and not
+// the Roe bound alone.
+template <typename T>
+__device__ __forceinline__ T pos_part(const T& x) {
+  return (nonneg(x) || val(x) != val(x)) ? x : x - x;
+}
 
 // ---------------------------------------------------------------- fluxes
 // Euler flux through a face with unit normal n = (nx, ny): the state is
@@ -377,7 +390,7 @@ __device__ __forceinline__ void euler_riemann(const T* UL, const T* UR, const Ri
   T EL = UL[3], ER = UR[3];
   T pL = gm1 * (EL - half * rL * (unL * unL + utL * utL));
   T pR = gm1 * (ER - half * rR * (unR * unR + utR * utR));
-  T cL = tsqrt(gg * pL * irL), cR = tsqrt(gg * pR * irR);
+  T cL = tsqrt(gg * pos_part(pL) * irL), cR = tsqrt(gg * pos_part(pR) * irR);
   T HL = (EL + pL) * irL, HR = (ER + pR) * irR;
   // Roe averages and Einfeldt wave speeds (Eq. wavespeed)
   T D = tsqrt(rR * irL);
@@ -486,7 +499,7 @@ __device__ __forceinline__ void euler_riemann_vjp(const T* UL, const T* UR, cons
   const T EL = UL[3], ER = UR[3];
   const T qL = unL * unL + utL * utL, qR = unR * unR + utR * utR;
   const T pL = gm1 * (EL - half * rL * qL), pR = gm1 * (ER - half * rR * qR);
-  const T cL = tsqrt(gg * pL * irL), cR = tsqrt(gg * pR * irR);
+  const T cL = tsqrt(gg * pos_part(pL) * irL), cR = tsqrt(gg * pos_part(pR) * irR);
   const T HL = (EL + pL) * irL, HR = (ER + pR) * irR;
   const T D = tsqrt(rR * irL);
   const T iden = one / (one + D);
@@ -676,10 +689,11 @@ __device__ __forceinline__ void euler_riemann_vjp(const T* UL, const T* UR, cons
   pRb = pRb + HRb * irR;
   irRb = irRb + HRb * (ER + pR);
   {
-    const T c2b = cLb / (two * cL);
+    // a zero sound speed (clamped or zero pressure) passes nothing back
+    const T c2b = is_zero(cL) ? zero : cLb / (two * cL);
     pLb = pLb + c2b * gg * irL;
     irLb = irLb + c2b * gg * pL;
-    const T c2bR = cRb / (two * cR);
+    const T c2bR = is_zero(cR) ? zero : cRb / (two * cR);
     pRb = pRb + c2bR * gg * irR;
     irRb = irRb + c2bR * gg * pR;
   }
