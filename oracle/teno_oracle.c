@@ -42,8 +42,11 @@
  * xi eta^(d-1); D^q P sums every multi-index |alpha| = q once; N_q = 2 (third,
  * fourth order) or 3 (fifth, sixth order) Gauss-Legendre points per edge with
  * weights summing to one; chi_k = C_T counts as smooth; selection per cell and
- * per conservative variable; CFL length = 4|V|/perimeter; at an outflow face
- * both states are the cell average (zero gradient of the cell averages).
+ * per conservative variable; CFL length = 4|V|/perimeter; a cell with a face
+ * on an outflow boundary enters every face flux with its cell average (first
+ * order in that cell layer; at the outflow face both states are that average,
+ * zero gradient of the cell averages): its high-order polynomial, from
+ * one-sided stencils, makes a boundary closure with a growing mode.
  *
  * Stencil readings (exact, so both implementations agree index for index):
  *   centroid c = ((v0 + v1) + v2) / 3 of the unwrapped vertices; the offset
@@ -190,6 +193,7 @@ typedef struct {
   int32_t* fnbr;  /* [nc][3] */
   int32_t* fedge; /* [nc][3] */
   int32_t* fbc;   /* [nc][3] */
+  unsigned char* fo; /* [nc] 1: the cell has a face on an outflow boundary */
   /* stencils and reconstruction matrices, built on demand */
   unsigned char* built;
   int32_t* st;   /* [nc][ST_TOTAL] (-1 padding) */
@@ -357,6 +361,10 @@ static int build_topology(omesh* M, int64_t nbf, const int32_t* bface) {
     i = j;
   }
   free(rec);
+  M->fo = (unsigned char*)calloc(nc, 1);
+  for (int64_t c = 0; c < nc; ++c)
+    for (int k = 0; k < 3; ++k)
+      if (M->fnbr[3 * c + k] < 0 && M->fbc[3 * c + k] == BC_OUTFLOW) M->fo[c] = 1;
   return rc;
 }
 
@@ -1410,6 +1418,7 @@ void oracle_free(void* h) {
   free(M->fnbr);
   free(M->fedge);
   free(M->fbc);
+  free(M->fo);
   free(M);
 }
 
@@ -1533,12 +1542,15 @@ static void face_flux(const omesh* M, int64_t c, int e, const double* U, const r
   for (int k = 0; k < M->nq; ++k) {
     double x = P[2 * e] + M->gt[k] * dx, y = P[2 * e + 1] + M->gt[k] * dy;
     double UL[4], UR[4], F[4];
-    eval_point(M, c, U, Rc, e, x, y, UL);
-    /* outflow: the face takes the cell average (zero gradient of the cell
-     * averages), not the polynomial extrapolated to the boundary */
-    if (n < 0 && M->fbc[3 * c + e] == BC_OUTFLOW)
+    /* a cell of the outflow layer enters with its cell average (at the
+     * outflow face itself: zero gradient of the cell averages) */
+    if (M->fo[c])
       for (int v = 0; v < M->nvar; ++v) UL[v] = U[(int64_t)v * M->nc + c];
-    if (n >= 0)
+    else
+      eval_point(M, c, U, Rc, e, x, y, UL);
+    if (n >= 0 && M->fo[n])
+      for (int v = 0; v < M->nvar; ++v) UR[v] = U[(int64_t)v * M->nc + n];
+    else if (n >= 0)
       eval_point(M, n, U, Rn, M->fedge[3 * c + e], x, y, UR);
     else
       ghost_state(M, M->fbc[3 * c + e], UL, nx, ny, x, y, UR);
@@ -1732,7 +1744,7 @@ int oracle_residual_vjp(void* h, const double* U, double time, const double* w, 
   recon_t* RC = (recon_t*)malloc(sizeof(recon_t) * nc);
   for (int64_t c = 0; c < nc; ++c) reconstruct(M, c, U, sel_in, &RC[c]);
   /* adjoint of the Gauss-point values: Ubar[c][e][k][v]; of the cell
-   * averages taken directly by outflow faces: direct[v][c] */
+   * averages taken directly by outflow-layer cells: direct[v][c] */
   double* Ubar = (double*)calloc(nc * 3 * nq * nvar, sizeof(double));
   double* direct = (double*)calloc(nc * nvar, sizeof(double));
   for (int64_t c = 0; c < nc; ++c)
@@ -1753,11 +1765,15 @@ int oracle_residual_vjp(void* h, const double* U, double time, const double* w, 
       for (int k = 0; k < nq; ++k) {
         double x = P[2 * e] + M->gt[k] * dx, y = P[2 * e + 1] + M->gt[k] * dy;
         double UL[4], UR[4], JL[16], JR[16];
-        eval_point(M, c, U, &RC[c], e, x, y, UL);
-        const int outflow = n < 0 && M->fbc[3 * c + e] == BC_OUTFLOW;
-        if (outflow)
+        /* outflow-layer sides take the cell average (as in face_flux) */
+        const int fl = M->fo[c], fr = n >= 0 && M->fo[n];
+        if (fl)
           for (int v = 0; v < nvar; ++v) UL[v] = U[(int64_t)v * nc + c];
-        if (n >= 0)
+        else
+          eval_point(M, c, U, &RC[c], e, x, y, UL);
+        if (fr)
+          for (int v = 0; v < nvar; ++v) UR[v] = U[(int64_t)v * nc + n];
+        else if (n >= 0)
           eval_point(M, n, U, &RC[n], M->fedge[3 * c + e], x, y, UR);
         else
           ghost_state(M, M->fbc[3 * c + e], UL, nx, ny, x, y, UR);
@@ -1788,11 +1804,13 @@ int oracle_residual_vjp(void* h, const double* U, double time, const double* w, 
             for (int i = 0; i < nvar; ++i) bl[j] += G[i * nvar + j] * br[i];
         }
         for (int v = 0; v < nvar; ++v) {
-          if (outflow)
+          if (fl)
             direct[(int64_t)v * nc + c] += bl[v];
           else
             Ubar[((c * 3 + e) * nq + k) * nvar + v] += bl[v];
-          if (n >= 0) {
+          if (fr) {
+            direct[(int64_t)v * nc + n] += br[v];
+          } else if (n >= 0) {
             /* the neighbour's point k on this face, stored by physical point */
             int en = M->fedge[3 * c + e];
             Ubar[((n * 3 + en) * nq + (nq - 1 - k)) * nvar + v] += br[v];
