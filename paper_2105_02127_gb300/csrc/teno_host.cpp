@@ -72,6 +72,7 @@ struct teno_ctx {
   DevBuf b_halo_off, b_halo_ids, b_halo_loc, b_g32, b_wq, b_psi, b_cspeed, b_coef;
   DevBuf b_ahat, b_nbr, b_smask, b_fcells, b_fedges, b_fgeom, b_fgeom2, b_cfaces, b_inv_area, b_cfl_len, b_cfl_ilen2,
       b_perm;
+  DevBuf b_fo;  // [n_pad] 1: the cell has an outflow face (uploaded when some face is one)
   DevBuf b_U, b_U1, b_U2, b_R, b_tmp, b_Uq, b_K, b_sel, b_sel_ovr, b_maxlam, b_flag;
   DevBuf b_Usplit;  // FP32 hi/lo split of the state being reconstructed (mixed precision)
   bool override_on = false;
@@ -111,6 +112,7 @@ struct teno_ctx {
   std::vector<int32_t> h_fcells, h_cfaces;
   std::vector<int8_t> h_fedges;
   std::vector<double> h_fgeom, h_inv_area, h_cfl_len;
+  std::vector<uint8_t> h_fo;
   // kernel timing (teno_profile): event pairs around launches, per kind
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -1354,10 +1356,15 @@ int upload_mesh(teno_ctx* ctx) {
   }
   ctx->nface = (int64_t)fcells.size() / 2;
   std::vector<double> inv_area(npad, 0.0), cfl_len(npad, 1.0);
+  // the outflow layer: cells with a face on an outflow boundary enter every
+  // face flux with their cell average
+  std::vector<uint8_t> fo(npad, 0);
   for (int64_t c = 0; c < nc; ++c) {
     const int32_t u = ctx->perm[c];
     inv_area[c] = 1.0 / ctx->area[u];
     cfl_len[c] = 4.0 * ctx->area[u] / ctx->perim[u];
+    for (int e = 0; e < 3; ++e)
+      if (ctx->fnbr[3 * u + e] < 0 && ctx->fbc[3 * u + e] == TENO_BC_OUTFLOW) fo[c] = 1;
   }
   int rc = upload(ctx, ctx->b_fcells, fcells.data(), fcells.size() * 4);
   if (!rc) rc = upload(ctx, ctx->b_fedges, fedges.data(), fedges.size());
@@ -1383,6 +1390,7 @@ int upload_mesh(teno_ctx* ctx) {
     rc = upload(ctx, ctx->b_cfl_ilen2, ilen2.data(), ilen2.size() * sizeof(float2));
   }
   if (!rc) rc = upload(ctx, ctx->b_perm, ctx->perm.data(), ctx->perm.size() * 4);
+  if (!rc && ctx->has_outflow) rc = upload(ctx, ctx->b_fo, fo.data(), fo.size());
   if (rc) return rc;
   DeviceMesh& dm = ctx->dm;
   dm.n_cell = nc;
@@ -1402,6 +1410,8 @@ int upload_mesh(teno_ctx* ctx) {
   ctx->h_cfaces.swap(cfaces);
   ctx->h_inv_area.swap(inv_area);
   ctx->h_cfl_len.swap(cfl_len);
+  ctx->h_fo.swap(fo);
+  dm.fo = ctx->has_outflow ? (const uint8_t*)ctx->b_fo.p : nullptr;
   dm.f_cells = (const int32_t*)ctx->b_fcells.p;
   dm.f_edges = (const int8_t*)ctx->b_fedges.p;
   dm.f_geom = (const double*)ctx->b_fgeom.p;
@@ -1460,12 +1470,14 @@ int upload_partition_mesh(teno_ctx* ctx) {
   std::vector<double> inv_area(spad, 0.0), cfl_len(spad, 1.0);
   std::vector<float2> ilen2(spad);
   std::vector<int32_t> perm_in(sn, 0), perm_out(n_own);
+  std::vector<uint8_t> fo(spad, 0);
   for (int64_t l = 0; l < spad; ++l) {
     const int32_t g = l < sn ? ctx->loc2glob[l] : -1;
     if (g >= 0 && l < n_comp) {
       inv_area[l] = ctx->h_inv_area[g];
       cfl_len[l] = ctx->h_cfl_len[g];
     }
+    if (g >= 0 && ctx->has_outflow) fo[l] = ctx->h_fo[g];
     const double x = 1.0 / cfl_len[l];
     const float h = (float)x;
     ilen2[l] = make_float2(h, (float)(x - (double)h));
@@ -1482,6 +1494,7 @@ int upload_partition_mesh(teno_ctx* ctx) {
   if (!rc) rc = upload(ctx, ctx->b_cfl_ilen2, ilen2.data(), ilen2.size() * sizeof(float2));
   if (!rc) rc = upload(ctx, ctx->b_perm_in, perm_in.data(), perm_in.size() * 4);
   if (!rc) rc = upload(ctx, ctx->b_perm, perm_out.data(), perm_out.size() * 4);
+  if (!rc && ctx->has_outflow) rc = upload(ctx, ctx->b_fo, fo.data(), fo.size());
   const int32_t P = ctx->part_n;
   ctx->b_recv_idx.resize(P);
   ctx->b_send_idx.resize(P);
@@ -1496,6 +1509,7 @@ int upload_partition_mesh(teno_ctx* ctx) {
   dm.n_recon = n_comp;
   dm.n_update = n_own;
   dm.n_face = nf;
+  dm.fo = ctx->has_outflow ? (const uint8_t*)ctx->b_fo.p : nullptr;
   dm.f_cells = (const int32_t*)ctx->b_fcells.p;
   dm.f_edges = (const int8_t*)ctx->b_fedges.p;
   dm.f_geom = (const double*)ctx->b_fgeom.p;

@@ -92,6 +92,9 @@ struct DeviceMesh {
   const float2* f_geom2 = nullptr;  // [n_face][3] nx, ny, |A| as (hi, lo) float pairs
   const int32_t* c_faces = nullptr; // [n_pad][3] face*2 + (1 if the cell is the neighbour)
   const double* inv_area = nullptr; // [n_pad]
+  // [n_pad] 1: the cell has an outflow face and enters every face flux with
+  // its cell average (first order in the outflow layer); null without outflow
+  const uint8_t* fo = nullptr;
   const double* cfl_len = nullptr;    // [n_pad] 4|V|/perimeter
   const float2* cfl_ilen2 = nullptr;  // [n_pad] 1 / cfl_len as (hi, lo) pairs
   EvalTable eval;

@@ -2677,7 +2677,8 @@ struct FaceArgs {
   const int8_t* f_edges;
   const double* f_geom;
   const float2* f_geom2;  // [n_face][3] nx, ny, |A| as (hi, lo) pairs
-  const double* U;        // cell averages [n_var][n_pad] (outflow faces take them)
+  const double* U;        // cell averages [n_var][n_pad] (the outflow layer takes them)
+  const uint8_t* fo;      // [n_pad] 1: outflow-layer cell, or null
   int64_t n_pad;
   int64_t n_face;
   double gamma, adv_x, adv_y, time;
@@ -2774,19 +2775,25 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const FaceArgs a, const 
   RiemannK<T> rk;
   T tl;
   face_k<T>(a.f_geom, a.f_geom2, f, a.gamma, a.g2, a.gm12, rk, tl);
+  // a side in the outflow layer enters with its cell average (at the outflow
+  // face itself both states are that average: zero gradient of the averages)
+  const bool fl = NV == 4 && a.fo && a.fo[o];
+  const bool fr = NV == 4 && n >= 0 && a.fo && a.fo[n];
 #pragma unroll (std::is_same<T, DF>::value ? kFluxUnrollPairs : 4)
   for (int k = 0; k < NQ; ++k) {
     T UL[NV], UR[NV], F[NV];
-    ld_group<NV>(Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV, UL);
-    if (n >= 0) {
+    if (fl) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) UL[v] = cst<T>(a.U[v * a.n_pad + o]);
+    } else {
+      ld_group<NV>(Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV, UL);
+    }
+    if (fr) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) UR[v] = cst<T>(a.U[v * a.n_pad + n]);
+    } else if (n >= 0) {
       ld_group<NV>(Uq + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV, UR);
     } else if constexpr (NV == 4) {
-      // an outflow face takes the cell average on both sides (zero gradient
-      // of the cell averages), not the polynomial extrapolated to it
-      if (en == TENO_BC_OUTFLOW) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) UL[v] = cst<T>(a.U[v * a.n_pad + o]);
-      }
       double x = a.f_geom[5 * f + 3] - ny * len * a.gt[k];
       ghost_state<T>(en, UL, nx, ny, x, a.time, a.gamma, UR);
     } else {
@@ -3018,8 +3025,9 @@ struct VjpArgs {
   const int8_t* f_edges;
   const double* f_geom;
   const float2* f_geom2;
-  const double* U;  // cell averages (outflow faces take them)
-  double* ubd;      // [cell][edge][var]: the cotangent of an outflow face's cell average
+  const double* U;      // cell averages (the outflow layer takes them)
+  const uint8_t* fo;    // [n_pad] 1: outflow-layer cell, or null
+  double* ubd;          // [cell][edge][var]: cotangents of outflow-layer cell averages
   float2 g2, gm12;
   int adv_field;
   double adv_cx, adv_cy, adv_omega, adv_r1, adv_r2;
@@ -3087,12 +3095,13 @@ __global__ void __launch_bounds__(128, TENO_VJP_MIN_BLOCKS > 0 ? TENO_VJP_MIN_BL
   S tl;  // |A| in the flux scalar type
   face_k<S>(a.f_geom, a.f_geom2, f, a.gamma, a.g2, a.gm12, rks, tl);
   const RiemannK<D> rk = riemann_k_dual<ND, S>(rks);
-  // an outflow face takes the owner's cell average (zero gradient of the cell
-  // averages): its cotangent goes to that average, summed over the points
-  const bool outflow = NV == 4 && n < 0 && en == TENO_BC_OUTFLOW;
-  double dl[NV];
+  // a side in the outflow layer enters with its cell average: its cotangent
+  // goes to that average (summed over the points), none to its Gauss values
+  const bool fl = NV == 4 && a.fo && a.fo[o];
+  const bool fr = NV == 4 && n >= 0 && a.fo && a.fo[n];
+  double dl[NV], dr[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) dl[v] = 0.0;
+  for (int v = 0; v < NV; ++v) dl[v] = dr[v] = 0.0;
   for (int k = 0; k < NQ; ++k) {
     TQ ul[NV], ur[NV];
     ld_group<NV>(Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV, ul);
@@ -3110,23 +3119,30 @@ __global__ void __launch_bounds__(128, TENO_VJP_MIN_BLOCKS > 0 ? TENO_VJP_MIN_BL
       S uL[NV], uR[NV], ULb[NV], URb[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        uL[v] = outflow ? cst<S>(a.U[v * a.n_pad + o]) : lift<S>(ul[v]);
+        uL[v] = fl ? cst<S>(a.U[v * a.n_pad + o]) : lift<S>(ul[v]);
         ULb[v] = cst<S>(0.0);
         URb[v] = cst<S>(0.0);
       }
       if (n >= 0) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) uR[v] = lift<S>(ur[v]);
+        for (int v = 0; v < NV; ++v) uR[v] = fr ? cst<S>(a.U[v * a.n_pad + n]) : lift<S>(ur[v]);
       } else {
         ghost_state<S>(en, uL, nx, ny, xq(), a.time, a.gamma, uR);
       }
       euler_riemann_vjp<S>(uL, uR, rks, FLUX == TENO_FLUX_HLLC, Kw, ULb, URb);
       if (n < 0) ghost_vjp<S>(en, rks, URb, ULb);
-      if (outflow) {
+      if (fl) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           dl[v] += to_d(ULb[v]);
           ULb[v] = cst<S>(0.0);
+        }
+      }
+      if (fr) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          dr[v] += to_d(URb[v]);
+          URb[v] = cst<S>(0.0);
         }
       }
       if constexpr (std::is_same<S, DF>::value) {
@@ -3143,14 +3159,14 @@ __global__ void __launch_bounds__(128, TENO_VJP_MIN_BLOCKS > 0 ? TENO_VJP_MIN_BL
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           UL[v] = cst<D>(0.0);
-          UL[v].v = outflow ? cst<S>(a.U[v * a.n_pad + o]) : lift<S>(ul[v]);
+          UL[v].v = fl ? cst<S>(a.U[v * a.n_pad + o]) : lift<S>(ul[v]);
           if (v >= dir0 && v < dir0 + ND) UL[v].d[v - dir0] = cst<S>(1.0);
         }
         if (n >= 0) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             UR[v] = cst<D>(0.0);
-            UR[v].v = lift<S>(ur[v]);
+            UR[v].v = fr ? cst<S>(a.U[v * a.n_pad + n]) : lift<S>(ur[v]);
             if (NV + v >= dir0 && NV + v < dir0 + ND) UR[v].d[NV + v - dir0] = cst<S>(1.0);
           }
         } else if constexpr (NV == 4) {
@@ -3173,11 +3189,14 @@ __global__ void __launch_bounds__(128, TENO_VJP_MIN_BLOCKS > 0 ? TENO_VJP_MIN_BL
 #pragma unroll
           for (int i = 0; i < NV; ++i) sacc = madd(F[i].d[j], Kw[i], sacc);
           const int g = dir0 + j;
-          if (g < NV && outflow) {
+          if (g < NV && fl) {
             dl[g] += to_d(sacc);
             store_bar<S>(outL, g, cst<S>(0.0));
           } else if (g < NV) {
             store_bar<S>(outL, g, sacc);
+          } else if (n >= 0 && fr) {
+            dr[g - NV] += to_d(sacc);
+            store_bar<S>(outR, g - NV, cst<S>(0.0));
           } else if (n >= 0) {
             store_bar<S>(outR, g - NV, sacc);
           }
@@ -3185,9 +3204,13 @@ __global__ void __launch_bounds__(128, TENO_VJP_MIN_BLOCKS > 0 ? TENO_VJP_MIN_BL
       }
     }
   }
-  if (outflow) {
+  if (fl) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) a.ubd[((int64_t)o * 3 + eo) * NV + v] = dl[v];
+  }
+  if (fr) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) a.ubd[((int64_t)n * 3 + en) * NV + v] = dr[v];
   }
 }
 
@@ -3956,6 +3979,7 @@ static FaceArgs face_args(const DeviceMesh& dm, double time) {
   a.f_geom = dm.f_geom;
   a.f_geom2 = dm.f_geom2;
   a.U = nullptr;
+  a.fo = dm.fo;
   a.n_pad = dm.n_pad;
   a.n_face = dm.n_face;
   a.gamma = dm.gamma;
@@ -4138,6 +4162,7 @@ cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const double* U, const vo
   a.f_geom = dm.f_geom;
   a.f_geom2 = dm.f_geom2;
   a.U = U;
+  a.fo = dm.fo;
   a.ubd = ubd;
   a.g2 = split2(dm.gamma);
   a.gm12 = split2(dm.gamma - 1.0);

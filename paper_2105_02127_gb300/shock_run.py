@@ -6,7 +6,11 @@ positivity scaling of the reconstruction, in FP64 (the double-float path)
 and FP32-mixed.  At sampled steps of the FP64 run the selections of the FP64
 and FP32-mixed paths are evaluated on the same stage input states (U^n,
 U^(1), U^(2)); their flip rate per stage is the fraction of (cell, variable)
-selections that differ.  Prints one JSON object.
+selections that differ.  At the same steps of both runs the largest
+deviation from the pre-shock state ahead of the incident shock (more than
+0.05 ahead of its exact position and above y = 0.5, clear of the Mach
+stem: there the exact solution is that state)
+is recorded with its location.  Prints one JSON object.
 
   python -m paper_2105_02127_gb300.shock_run [--nx 2048] [--ny 512] [--order 6]
                                              [--t-end 0.2] [--sample-every 50] [--cfl 0.4]
@@ -46,6 +50,16 @@ def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int
                        f"positivity scaling, t_end {t_end}",
            "n_cell": n_cell}
     probes = (ctx(teno.FP64), ctx(teno.FP32_MIXED))
+    cen = torch.from_numpy(mesh.unwrapped_vertices().mean(axis=1)).cuda()
+    pre = torch.tensor([1.4, 0.0, 0.0, 2.5], dtype=torch.float64, device="cuda")[:, None]
+
+    def ahead_dev(Us, time_):
+        # ahead of the incident shock x_s(y, t) = 1/6 + (y + 20 t) / sqrt(3),
+        # above the Mach stem (which runs ahead of it along the wall)
+        ahead = (cen[:, 0] > 0.1667 + (cen[:, 1] + 20.0 * time_) / 1.732 + 0.05) & (cen[:, 1] > 0.5)
+        d = (Us - pre).abs().amax(dim=0) * ahead
+        i = int(torch.argmax(d).item())
+        return [float(d[i].item()), float(cen[i, 0].item()), float(cen[i, 1].item())]
     Rb = torch.empty((4, n_cell), dtype=torch.float64, device="cuda")
     sels = [torch.empty((4, n_cell), dtype=torch.uint8, device="cuda") for _ in range(2)]
 
@@ -64,7 +78,7 @@ def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int
         Ud = torch.from_numpy(U0).cuda()
         t.set_state(Ud)
         Un, U1, U2, prev = (torch.empty_like(Ud) for _ in range(4))
-        tm, n, per_stage = 0.0, 0, []
+        tm, n, per_stage, dev = 0.0, 0, [], []
         torch.cuda.synchronize()
         w0 = time.perf_counter()
         step_s = 0.0
@@ -73,6 +87,8 @@ def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int
             dt = min(t.cfl_dt(), t_end - tm)
             sample = name == "fp64_pairs" and n % sample_every == 0
             t.get_state(prev)
+            if n % sample_every == 0:
+                dev.append([n, tm] + ahead_dev(prev, tm))
             if sample:
                 Un.copy_(prev)
             s0 = time.perf_counter()
@@ -100,6 +116,10 @@ def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int
                "failure": failure,
                "finite": bool(np.isfinite(U).all()), "rho_min": float(rho.min()),
                "p_min": float(p.min()), "rho_max": float(rho.max())}
+        dv = np.array([r[2] for r in dev]) if dev else np.zeros(1)
+        rec["ahead_of_shock_deviation"] = {
+            "every": sample_every, "max": float(dv.max()), "final": float(dv[-1]),
+            "samples": dev[::max(1, len(dev) // 40)] + dev[-1:]}
         if name == "fp64_pairs" and per_stage:
             fl = np.array([r[2:] for r in per_stage])
             rec["flip_rate_per_stage"] = {

@@ -94,6 +94,29 @@ def test_partitioned_vjp(T, P, precision):
     assert err.max() <= 1e-13
 
 
+@pytest.mark.parametrize("P", [2, 3])
+def test_partitioned_vjp_boundaries(T, P):
+    """The residual VJP on the shock-case boundaries (wall, inflow, outflow
+    layer, moving top state) on a smooth state, HLL: the parts with the
+    reverse halo exchange equal the whole mesh to rounding."""
+    mesh = inputs.jittered_mesh(48, 12, 4.0, 1.0, seed=1003, periodic=False,
+                                bc_tagger=inputs.dmr_bc_tagger)
+
+    def f(x, y):
+        return inputs.prim_to_cons(1.4 + 0.3 * np.sin(3 * x + 2 * y), 0.2 + 0.1 * np.cos(2 * y),
+                                   -0.1 + 0.05 * x, 1.0 + 0.2 * np.sin(x * y), 1.4)
+    U = inputs.cell_average(mesh, f)
+    whole, parts = _contexts(T, mesh, P, order=4, n_var=4, flux=1)
+    for t in [whole] + parts:
+        t.set_time(0.05)
+        t.set_state(U)
+    w = inputs.random_directions(3006, 1, U.size)[0].reshape(U.shape)
+    v = whole.residual_vjp(w)
+    vp = T.group_residual_vjp(parts, w)
+    err = np.abs(vp - v).max(axis=1) / np.abs(v).max(axis=1)
+    assert err.max() <= 1e-13
+
+
 def test_partitioned_shock_case(T):
     """Shock-case geometry (non-periodic, the four boundary conditions, the
     time-dependent top state), TENO6, HLLC, positivity scaling: two parts step
