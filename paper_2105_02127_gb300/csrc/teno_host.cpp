@@ -72,7 +72,7 @@ struct teno_ctx {
   DevBuf b_halo_off, b_halo_ids, b_halo_loc, b_g32, b_wq, b_psi, b_cspeed, b_coef;
   DevBuf b_ahat, b_nbr, b_smask, b_fcells, b_fedges, b_fgeom, b_fgeom2, b_cfaces, b_inv_area, b_cfl_len, b_cfl_ilen2,
       b_perm;
-  DevBuf b_fo;  // [n_pad] 1: the cell has an outflow face (uploaded when some face is one)
+  DevBuf b_fo;  // the outflow layer: local ids of the cells with an outflow face
   DevBuf b_U, b_U1, b_U2, b_R, b_tmp, b_Uq, b_K, b_sel, b_sel_ovr, b_maxlam, b_flag;
   DevBuf b_Usplit;  // FP32 hi/lo split of the state being reconstructed (mixed precision)
   bool override_on = false;
@@ -80,7 +80,7 @@ struct teno_ctx {
   bool stages_ok = false; // b_U1, b_U2 hold the stage states of the last RK3 step
   // adjoint
   DevBuf b_rev_off, b_rev_idx, b_dbar, b_uself, b_Uqbar, b_l1, b_l2, b_lamn, b_vtmp, b_selA;
-  DevBuf b_ubd;  // [cell][edge][var] cotangents of outflow faces' cell averages
+  DevBuf b_ubd;  // [cell][edge][var] cotangents of the outflow layer's cell averages
   DevBuf b_Uq_st[2], b_sel_st[2];  // stage 1, 2 reconstructions kept by the adjoint replay
   bool adj_ok = false;
   std::vector<int64_t> rev_off_h;
@@ -1390,7 +1390,10 @@ int upload_mesh(teno_ctx* ctx) {
     rc = upload(ctx, ctx->b_cfl_ilen2, ilen2.data(), ilen2.size() * sizeof(float2));
   }
   if (!rc) rc = upload(ctx, ctx->b_perm, ctx->perm.data(), ctx->perm.size() * 4);
-  if (!rc && ctx->has_outflow) rc = upload(ctx, ctx->b_fo, fo.data(), fo.size());
+  std::vector<int32_t> fo_list;
+  for (int64_t c = 0; c < nc; ++c)
+    if (fo[c]) fo_list.push_back((int32_t)c);
+  if (!rc && !fo_list.empty()) rc = upload(ctx, ctx->b_fo, fo_list.data(), fo_list.size() * 4);
   if (rc) return rc;
   DeviceMesh& dm = ctx->dm;
   dm.n_cell = nc;
@@ -1411,7 +1414,8 @@ int upload_mesh(teno_ctx* ctx) {
   ctx->h_inv_area.swap(inv_area);
   ctx->h_cfl_len.swap(cfl_len);
   ctx->h_fo.swap(fo);
-  dm.fo = ctx->has_outflow ? (const uint8_t*)ctx->b_fo.p : nullptr;
+  dm.fo_n = (int64_t)fo_list.size();
+  dm.fo_list = dm.fo_n ? (const int32_t*)ctx->b_fo.p : nullptr;
   dm.f_cells = (const int32_t*)ctx->b_fcells.p;
   dm.f_edges = (const int8_t*)ctx->b_fedges.p;
   dm.f_geom = (const double*)ctx->b_fgeom.p;
@@ -1470,14 +1474,14 @@ int upload_partition_mesh(teno_ctx* ctx) {
   std::vector<double> inv_area(spad, 0.0), cfl_len(spad, 1.0);
   std::vector<float2> ilen2(spad);
   std::vector<int32_t> perm_in(sn, 0), perm_out(n_own);
-  std::vector<uint8_t> fo(spad, 0);
+  std::vector<int32_t> fo_list;  // outflow-layer cells among the reconstructed ones
   for (int64_t l = 0; l < spad; ++l) {
     const int32_t g = l < sn ? ctx->loc2glob[l] : -1;
     if (g >= 0 && l < n_comp) {
       inv_area[l] = ctx->h_inv_area[g];
       cfl_len[l] = ctx->h_cfl_len[g];
     }
-    if (g >= 0 && ctx->has_outflow) fo[l] = ctx->h_fo[g];
+    if (g >= 0 && l < n_comp && ctx->has_outflow && ctx->h_fo[g]) fo_list.push_back((int32_t)l);
     const double x = 1.0 / cfl_len[l];
     const float h = (float)x;
     ilen2[l] = make_float2(h, (float)(x - (double)h));
@@ -1494,7 +1498,7 @@ int upload_partition_mesh(teno_ctx* ctx) {
   if (!rc) rc = upload(ctx, ctx->b_cfl_ilen2, ilen2.data(), ilen2.size() * sizeof(float2));
   if (!rc) rc = upload(ctx, ctx->b_perm_in, perm_in.data(), perm_in.size() * 4);
   if (!rc) rc = upload(ctx, ctx->b_perm, perm_out.data(), perm_out.size() * 4);
-  if (!rc && ctx->has_outflow) rc = upload(ctx, ctx->b_fo, fo.data(), fo.size());
+  if (!rc && !fo_list.empty()) rc = upload(ctx, ctx->b_fo, fo_list.data(), fo_list.size() * 4);
   const int32_t P = ctx->part_n;
   ctx->b_recv_idx.resize(P);
   ctx->b_send_idx.resize(P);
@@ -1509,7 +1513,8 @@ int upload_partition_mesh(teno_ctx* ctx) {
   dm.n_recon = n_comp;
   dm.n_update = n_own;
   dm.n_face = nf;
-  dm.fo = ctx->has_outflow ? (const uint8_t*)ctx->b_fo.p : nullptr;
+  dm.fo_n = (int64_t)fo_list.size();
+  dm.fo_list = dm.fo_n ? (const int32_t*)ctx->b_fo.p : nullptr;
   dm.f_cells = (const int32_t*)ctx->b_fcells.p;
   dm.f_edges = (const int8_t*)ctx->b_fedges.p;
   dm.f_geom = (const double*)ctx->b_fgeom.p;
@@ -1542,9 +1547,10 @@ int stage_flux(teno_ctx* ctx, const double* U, uint8_t* sel_out, double time,
   CK(launch_recon(ctx->dm, U, Us, uq, sel_out, sel_in, ctx->stream), "recon launch");
   if (ctx->dm.charvar) CK(launch_char_finish(ctx->dm, U, uq, ctx->stream), "char finish launch");
   if (ctx->dm.positivity) CK(launch_positivity(ctx->dm, U, uq, ctx->stream), "positivity launch");
+  CK(launch_layer_fill(ctx->dm, U, uq, ctx->stream), "layer fill launch");
   prof_end(ctx, pe);
   pe = prof_begin(ctx, K_FLUX);
-  CK(launch_face_flux(ctx->dm, U, uq, ctx->b_K.p, time, ctx->stream), "face flux launch");
+  CK(launch_face_flux(ctx->dm, uq, ctx->b_K.p, time, ctx->stream), "face flux launch");
   prof_end(ctx, pe);
   return TENO_OK;
 }
@@ -1641,7 +1647,7 @@ int ensure_adjoint(teno_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->b_Uqbar.p, 0, ctx->b_Uqbar.bytes, ctx->stream), "memset");
   CK(cudaMemsetAsync(ctx->b_uself.p, 0, ctx->b_uself.bytes, ctx->stream), "memset");
   if (ctx->has_outflow) {
-    // written for outflow edges only, zero elsewhere
+    // written for the edges of outflow-layer cells only, zero elsewhere
     rc = dev_alloc(ctx, ctx->b_ubd, sizeof(double) * 3 * nv * npad);
     if (rc) return rc;
     CK(cudaMemsetAsync(ctx->b_ubd.p, 0, ctx->b_ubd.bytes, ctx->stream), "memset");
@@ -1670,14 +1676,16 @@ int vjp_internal(teno_ctx* ctx, const double* U, const double* w, double* v, dou
     }
     long pr = prof_begin(ctx, K_RECON);
     CK(launch_recon(ctx->dm, U, Us, ctx->b_Uq.p, sel_out, sel_in, ctx->stream), "recon launch");
+    CK(launch_layer_fill(ctx->dm, U, ctx->b_Uq.p, ctx->stream), "layer fill launch");
     prof_end(ctx, pr);
     uq = ctx->b_Uq.p;
     if (!sel_in) sel = sel_out;
   }
   long pe = prof_begin(ctx, K_FLUX_VJP);
-  double* ubd = ctx->has_outflow ? (double*)ctx->b_ubd.p : nullptr;
-  CK(launch_face_flux_vjp(ctx->dm, U, uq, w, (double*)ctx->b_Uqbar.p, ubd, time, ctx->stream),
+  double* ubd = ctx->dm.fo_n ? (double*)ctx->b_ubd.p : nullptr;
+  CK(launch_face_flux_vjp(ctx->dm, uq, w, (double*)ctx->b_Uqbar.p, time, ctx->stream),
      "flux vjp launch");
+  CK(launch_layer_vjp(ctx->dm, (double*)ctx->b_Uqbar.p, ubd, ctx->stream), "layer vjp launch");
   prof_end(ctx, pe);
   pe = prof_begin(ctx, K_RECON_VJP);
   if (ctx->adj_tiled)

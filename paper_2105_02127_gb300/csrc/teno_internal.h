@@ -92,9 +92,11 @@ struct DeviceMesh {
   const float2* f_geom2 = nullptr;  // [n_face][3] nx, ny, |A| as (hi, lo) float pairs
   const int32_t* c_faces = nullptr; // [n_pad][3] face*2 + (1 if the cell is the neighbour)
   const double* inv_area = nullptr; // [n_pad]
-  // [n_pad] 1: the cell has an outflow face and enters every face flux with
-  // its cell average (first order in the outflow layer); null without outflow
-  const uint8_t* fo = nullptr;
+  // the outflow layer: the cells (local ids, among the reconstructed ones)
+  // with a face on an outflow boundary, which enter every face flux with
+  // their cell average; fo_n = 0 without outflow faces
+  const int32_t* fo_list = nullptr;
+  int64_t fo_n = 0;
   const double* cfl_len = nullptr;    // [n_pad] 4|V|/perimeter
   const float2* cfl_ilen2 = nullptr;  // [n_pad] 1 / cfl_len as (hi, lo) pairs
   EvalTable eval;
@@ -114,9 +116,11 @@ cudaError_t launch_positivity(const DeviceMesh& dm, const double* U, void* Uq, c
 // charvar: projection, per-field selection and Gauss-point values from the
 // coefficients the reconstruction wrote to dm.coef_out
 cudaError_t launch_char_finish(const DeviceMesh& dm, const double* U, void* Uq, cudaStream_t st);
-// U: the cell averages (outflow faces take them on both sides)
-cudaError_t launch_face_flux(const DeviceMesh& dm, const double* U, const void* Uq, void* K,
-                             double time, cudaStream_t st);
+// the outflow layer (dm.fo_list): every Gauss value of those cells := the
+// cell average (after the reconstruction and its positivity scaling)
+cudaError_t launch_layer_fill(const DeviceMesh& dm, const double* U, void* Uq, cudaStream_t st);
+cudaError_t launch_face_flux(const DeviceMesh& dm, const void* Uq, void* K, double time,
+                             cudaStream_t st);
 // mode 0: R = residual; mode 1: U_out = cn*Un + cs*(Us + dt*R), and (split
 // non-null) the FP32 hi/lo split of U_out
 cudaError_t launch_gather(const DeviceMesh& dm, const void* K, const double* Un, const double* Us,
@@ -145,11 +149,11 @@ cudaError_t launch_halo_unpack(double* U, int64_t ld, const int32_t* idx, int64_
 // adjoint kernels.  Uq_bar ([cell][edge point][var], 8 bytes an entry)
 // holds (hi, lo) float pairs on the TENO_FP64 path and doubles on the native
 // path; the reconstruction VJPs read it in the same form.
-// ubd [cell][edge][var] (null on meshes without outflow faces): the cotangent of
-// the cell average an outflow face takes, summed over its Gauss points
-cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const double* U, const void* Uq,
-                                 const double* w, double* Uq_bar, double* ubd, double time,
-                                 cudaStream_t st);
+cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const double* w,
+                                 double* Uq_bar, double time, cudaStream_t st);
+// adjoint of launch_layer_fill: ubd [cell][edge][var] := the outflow layer's
+// Gauss-slot cotangents summed per edge; those slots of Uq_bar := 0
+cudaError_t launch_layer_vjp(const DeviceMesh& dm, double* Uq_bar, double* ubd, cudaStream_t st);
 cudaError_t launch_recon_vjp(const DeviceMesh& dm, const uint8_t* sel, const double* Uq_bar,
                              double* d_bar, double* u_self, cudaStream_t st);
 // Tiled reconstruction VJP (FP64 path, Euler, per-tile halos present):

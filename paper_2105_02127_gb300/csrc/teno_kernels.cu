@@ -1671,8 +1671,11 @@ struct HaloPipe {
 // the tile's stencil halo in a double-buffered shared-memory area, prefetched
 // with cp.async one tile ahead; stencil differences from the halo, matrices
 // from the ring.  kDF: FP64 path (double-float); !kDF: FP32-mixed path.
+// The pair kernel with the CWENO and characteristic branches (kDF && kExt)
+// is held to two blocks per SM: uncapped it took 252 registers at TENO6, one
+// block (five warps) per SM.
 template <int M, int NS, int NQ, bool kDF, bool kExt>
-__global__ void __launch_bounds__(kTile * (kConsumers + 1))
+__global__ void __launch_bounds__(kTile * (kConsumers + 1), (kDF && kExt) ? 2 : 0)
     recon_tma_kernel(const ReconArgs a, const HaloArgs h, const DFTable ev, int* err) {
   using TR = TmaTraits<kDF, M, NS, NQ>;
   using TE = typename TR::TE;
@@ -1943,20 +1946,36 @@ struct WPlan {
 
 // Upper bound of |beta_fp32 - beta| relative to beta_fp32 + eps for m FP32
 // coefficients a32_l from n-term FP32 dot products.  Coefficient l errs by at
-// most e_l = (n + 6) u S_l with S_l = sum_s |G_ls| |d_s| (u = 2^-24; the
-// stored matrix and difference roundings included), and sum_l S_l = e_abs =
-// sum_s colsum_s |d_s|.  With E = sum_l e_l, Cauchy-Schwarz gives
+// most e_l = (n + 7) u S_l with S_l = sum_s |G_ls| |d_s| (u = 2^-24; the
+// stored matrix rounding and a difference conversion of up to 2u -- the FP64
+// path truncates -- included), and sum_l S_l = e_abs = sum_s colsum_s |d_s|.
+// With E = sum_l e_l, Cauchy-Schwarz gives
 // |sum a32^2 - sum a^2| <= sum e_l (2 |a32_l| + e_l) <= 2 E sqrt(beta32) + E^2;
 // the FP32 sum of squares adds (m + 2) u beta32.  Returns a value >= 1 when
 // the bound is not informative.
 __device__ __forceinline__ float beta_rel_bound(float beta32, float e_abs, int n, int m,
                                                 float eps) {
   const float u = 5.9604645e-8f;
-  const float E = (float)(n + 6) * u * e_abs * 1.0001f;
+  const float E = (float)(n + 7) * u * e_abs * 1.0001f;
   const float eb = (float)(m + 2) * u * beta32 + E * (2.f * sqrtf(beta32) + E);
   const float t = beta32 + eps;
   if (!(eb < 0.5f * t)) return 1.f;
   return eb / (t - eb);
+}
+
+// FP64 -> FP32 by truncation of the significand, in integer instructions
+// (the conversion instruction would take a slot of the FP64 pipe, which bounds
+// the FP64 path's reconstruction).  Relative error below 2^-23 for results in
+// the normal FP32 range; magnitudes below it give a signed zero (an absolute
+// error under 1.2e-38), magnitudes above it, infinities and NaN give an
+// infinity, which the cutoff screen sends to its FP64 fallback.
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
 }
 
 // pair difference U_s - U_0 of a halo cell (FP32 hi/lo splits of the states)
@@ -2378,7 +2397,7 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
             const Acc d = dif(nl[s * kTile] & kHaloPosMask);
             float dh;
             if constexpr (kN)
-              dh = (float)d;
+              dh = d2f_trunc(d);
             else
               dh = d.h;
 #pragma unroll
@@ -2403,7 +2422,7 @@ __global__ void __launch_bounds__(kTile * (kConsumers + 1), (WPlan<M, NS, 3 * NQ
             const HT q = st[nl[s * kTile] & kHaloPosMask];
             float dh;
             if constexpr (kN)
-              dh = (float)(q - u0s);
+              dh = d2f_trunc(q - u0s);
             else
               dh = (q.x - u0s.x) + (q.y - u0s.y);
 #pragma unroll
@@ -2631,6 +2650,53 @@ __global__ void __launch_bounds__(128) positivity_kernel(const double* __restric
     for (int v = 0; v < 4; ++v) q0[q * 4 + v] = from_d<TQ>(W[q][v]);
 }
 
+// The outflow layer (cells with a face on an outflow boundary) enters every
+// face flux with its cell average: after the reconstruction, each Gauss slot
+// of such a cell takes U_0 (in the Gauss-value type of the path).  One thread
+// per (layer cell, slot).
+template <int NQ3, typename TQ>
+__global__ void layer_fill_kernel(const double* __restrict__ U, TQ* __restrict__ Uq,
+                                  const int32_t* __restrict__ list, int64_t n, int64_t n_pad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * NQ3) return;
+  const int64_t c = list[i / NQ3];
+  const int p = (int)(i % NQ3);
+  TQ* o = Uq + (c * NQ3 + p) * 4;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) o[v] = from_d<TQ>(U[v * n_pad + c]);
+}
+
+// Adjoint of layer_fill_kernel: a layer cell's Gauss-slot cotangents (pairs
+// on the pair path, FP64 otherwise) go to its cell average, summed per edge
+// into ubd[cell][edge][var] (added to the cell's adjoint by the reverse
+// gather), and the slots are cleared so that the reconstruction's adjoint
+// sends nothing through the cell's polynomial.  One thread per (cell, edge).
+template <int NQ, bool kPairs>
+__global__ void layer_vjp_kernel(double* __restrict__ Uq_bar, double* __restrict__ ubd,
+                                 const int32_t* __restrict__ list, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * 3) return;
+  const int64_t c = list[i / 3];
+  const int e = (int)(i % 3);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t b = ((c * 3 + e) * NQ) * 4;
+  for (int q = 0; q < NQ; ++q)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int64_t j = b + q * 4 + v;
+      if constexpr (kPairs) {
+        float2* u = reinterpret_cast<float2*>(Uq_bar) + j;
+        acc[v] += (double)u->x + (double)u->y;
+        *u = make_float2(0.f, 0.f);
+      } else {
+        acc[v] += Uq_bar[j];
+        Uq_bar[j] = 0.0;
+      }
+    }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) ubd[(c * 3 + e) * 4 + v] = acc[v];
+}
+
 // Halo exchange of partitioned meshes (copy-based; each kernel touches only
 // its own context's arrays).  pack: buf[v][i] = U[v][idx[i]]; unpack: the
 // reverse, with the FP32 hi/lo split of the written states when Us is given;
@@ -2677,8 +2743,6 @@ struct FaceArgs {
   const int8_t* f_edges;
   const double* f_geom;
   const float2* f_geom2;  // [n_face][3] nx, ny, |A| as (hi, lo) pairs
-  const double* U;        // cell averages [n_var][n_pad] (the outflow layer takes them)
-  const uint8_t* fo;      // [n_pad] 1: outflow-layer cell, or null
   int64_t n_pad;
   int64_t n_face;
   double gamma, adv_x, adv_y, time;
@@ -2775,23 +2839,13 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const FaceArgs a, const 
   RiemannK<T> rk;
   T tl;
   face_k<T>(a.f_geom, a.f_geom2, f, a.gamma, a.g2, a.gm12, rk, tl);
-  // a side in the outflow layer enters with its cell average (at the outflow
-  // face itself both states are that average: zero gradient of the averages)
-  const bool fl = NV == 4 && a.fo && a.fo[o];
-  const bool fr = NV == 4 && n >= 0 && a.fo && a.fo[n];
+  // (the Gauss values of an outflow-layer cell are its cell average, written
+  // by layer_fill_kernel: at an outflow face both states are that average)
 #pragma unroll (std::is_same<T, DF>::value ? kFluxUnrollPairs : 4)
   for (int k = 0; k < NQ; ++k) {
     T UL[NV], UR[NV], F[NV];
-    if (fl) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) UL[v] = cst<T>(a.U[v * a.n_pad + o]);
-    } else {
-      ld_group<NV>(Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV, UL);
-    }
-    if (fr) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) UR[v] = cst<T>(a.U[v * a.n_pad + n]);
-    } else if (n >= 0) {
+    ld_group<NV>(Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV, UL);
+    if (n >= 0) {
       ld_group<NV>(Uq + ((int64_t)(n * 3 + en) * NQ + (NQ - 1 - k)) * NV, UR);
     } else if constexpr (NV == 4) {
       double x = a.f_geom[5 * f + 3] - ny * len * a.gt[k];
@@ -3025,9 +3079,6 @@ struct VjpArgs {
   const int8_t* f_edges;
   const double* f_geom;
   const float2* f_geom2;
-  const double* U;      // cell averages (the outflow layer takes them)
-  const uint8_t* fo;    // [n_pad] 1: outflow-layer cell, or null
-  double* ubd;          // [cell][edge][var]: cotangents of outflow-layer cell averages
   float2 g2, gm12;
   int adv_field;
   double adv_cx, adv_cy, adv_omega, adv_r1, adv_r2;
@@ -3095,13 +3146,6 @@ __global__ void __launch_bounds__(128, TENO_VJP_MIN_BLOCKS > 0 ? TENO_VJP_MIN_BL
   S tl;  // |A| in the flux scalar type
   face_k<S>(a.f_geom, a.f_geom2, f, a.gamma, a.g2, a.gm12, rks, tl);
   const RiemannK<D> rk = riemann_k_dual<ND, S>(rks);
-  // a side in the outflow layer enters with its cell average: its cotangent
-  // goes to that average (summed over the points), none to its Gauss values
-  const bool fl = NV == 4 && a.fo && a.fo[o];
-  const bool fr = NV == 4 && n >= 0 && a.fo && a.fo[n];
-  double dl[NV], dr[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) dl[v] = dr[v] = 0.0;
   for (int k = 0; k < NQ; ++k) {
     TQ ul[NV], ur[NV];
     ld_group<NV>(Uq + ((int64_t)(o * 3 + eo) * NQ + k) * NV, ul);
@@ -3119,32 +3163,18 @@ __global__ void __launch_bounds__(128, TENO_VJP_MIN_BLOCKS > 0 ? TENO_VJP_MIN_BL
       S uL[NV], uR[NV], ULb[NV], URb[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        uL[v] = fl ? cst<S>(a.U[v * a.n_pad + o]) : lift<S>(ul[v]);
+        uL[v] = lift<S>(ul[v]);
         ULb[v] = cst<S>(0.0);
         URb[v] = cst<S>(0.0);
       }
       if (n >= 0) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) uR[v] = fr ? cst<S>(a.U[v * a.n_pad + n]) : lift<S>(ur[v]);
+        for (int v = 0; v < NV; ++v) uR[v] = lift<S>(ur[v]);
       } else {
         ghost_state<S>(en, uL, nx, ny, xq(), a.time, a.gamma, uR);
       }
       euler_riemann_vjp<S>(uL, uR, rks, FLUX == TENO_FLUX_HLLC, Kw, ULb, URb);
       if (n < 0) ghost_vjp<S>(en, rks, URb, ULb);
-      if (fl) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          dl[v] += to_d(ULb[v]);
-          ULb[v] = cst<S>(0.0);
-        }
-      }
-      if (fr) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          dr[v] += to_d(URb[v]);
-          URb[v] = cst<S>(0.0);
-        }
-      }
       if constexpr (std::is_same<S, DF>::value) {
         st_group<NV>(reinterpret_cast<DF*>(outL), ULb);
         if (n >= 0) st_group<NV>(reinterpret_cast<DF*>(outR), URb);
@@ -3159,14 +3189,14 @@ __global__ void __launch_bounds__(128, TENO_VJP_MIN_BLOCKS > 0 ? TENO_VJP_MIN_BL
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           UL[v] = cst<D>(0.0);
-          UL[v].v = fl ? cst<S>(a.U[v * a.n_pad + o]) : lift<S>(ul[v]);
+          UL[v].v = lift<S>(ul[v]);
           if (v >= dir0 && v < dir0 + ND) UL[v].d[v - dir0] = cst<S>(1.0);
         }
         if (n >= 0) {
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
             UR[v] = cst<D>(0.0);
-            UR[v].v = fr ? cst<S>(a.U[v * a.n_pad + n]) : lift<S>(ur[v]);
+            UR[v].v = lift<S>(ur[v]);
             if (NV + v >= dir0 && NV + v < dir0 + ND) UR[v].d[NV + v - dir0] = cst<S>(1.0);
           }
         } else if constexpr (NV == 4) {
@@ -3189,28 +3219,13 @@ __global__ void __launch_bounds__(128, TENO_VJP_MIN_BLOCKS > 0 ? TENO_VJP_MIN_BL
 #pragma unroll
           for (int i = 0; i < NV; ++i) sacc = madd(F[i].d[j], Kw[i], sacc);
           const int g = dir0 + j;
-          if (g < NV && fl) {
-            dl[g] += to_d(sacc);
-            store_bar<S>(outL, g, cst<S>(0.0));
-          } else if (g < NV) {
+          if (g < NV)
             store_bar<S>(outL, g, sacc);
-          } else if (n >= 0 && fr) {
-            dr[g - NV] += to_d(sacc);
-            store_bar<S>(outR, g - NV, cst<S>(0.0));
-          } else if (n >= 0) {
+          else if (n >= 0)
             store_bar<S>(outR, g - NV, sacc);
-          }
         }
       }
     }
-  }
-  if (fl) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) a.ubd[((int64_t)o * 3 + eo) * NV + v] = dl[v];
-  }
-  if (fr) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) a.ubd[((int64_t)n * 3 + en) * NV + v] = dr[v];
   }
 }
 
@@ -3722,7 +3737,8 @@ __global__ void __launch_bounds__(256) scatter_gather_kernel(const int64_t* __re
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n_cell) return;
   const int64_t r0 = rev_off[j], r1 = rev_off[j + 1];
-  // the cell's own term, plus what its outflow faces (if any) owe its average
+  // the cell's own term, plus what its Gauss slots owe its average (outflow
+  // layer cells, written by layer_vjp_kernel; zero elsewhere)
   double u_self[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -3978,8 +3994,6 @@ static FaceArgs face_args(const DeviceMesh& dm, double time) {
   a.f_edges = dm.f_edges;
   a.f_geom = dm.f_geom;
   a.f_geom2 = dm.f_geom2;
-  a.U = nullptr;
-  a.fo = dm.fo;
   a.n_pad = dm.n_pad;
   a.n_face = dm.n_face;
   a.gamma = dm.gamma;
@@ -4002,10 +4016,9 @@ static FaceArgs face_args(const DeviceMesh& dm, double time) {
   return a;
 }
 
-cudaError_t launch_face_flux(const DeviceMesh& dm, const double* U, const void* Uq, void* K,
-                             double time, cudaStream_t st) {
+cudaError_t launch_face_flux(const DeviceMesh& dm, const void* Uq, void* K, double time,
+                             cudaStream_t st) {
   FaceArgs a = face_args(dm, time);
-  a.U = U;
   const unsigned grid = (unsigned)((dm.n_face + 255) / 256);
   auto go = [&](auto nvc, auto nqc, auto flc) -> cudaError_t {
     constexpr int NV = decltype(nvc)::value, NQ = decltype(nqc)::value,
@@ -4051,6 +4064,46 @@ cudaError_t launch_gather(const DeviceMesh& dm, const void* K, const double* Un,
     if (one) go(I1{}, TypeTag<DF>{}); else go(I4{}, TypeTag<DF>{});
   } else {
     if (one) go(I1{}, TypeTag<float>{}); else go(I4{}, TypeTag<float>{});
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layer_fill(const DeviceMesh& dm, const double* U, void* Uq, cudaStream_t st) {
+  if (!dm.fo_n) return cudaSuccess;
+  const int64_t nt = dm.fo_n * 3 * dm.nq;
+  const unsigned grid = (unsigned)((nt + 255) / 256);
+  auto go = [&](auto nqc) {
+    constexpr int NQ3 = 3 * decltype(nqc)::value;
+    if (dm.precision == TENO_FP64)
+      layer_fill_kernel<NQ3, DF><<<grid, 256, 0, st>>>(U, (DF*)Uq, dm.fo_list, dm.fo_n, dm.n_pad);
+    else if (dm.precision == TENO_FP32_MIXED)
+      layer_fill_kernel<NQ3, float><<<grid, 256, 0, st>>>(U, (float*)Uq, dm.fo_list, dm.fo_n,
+                                                          dm.n_pad);
+    else
+      layer_fill_kernel<NQ3, double><<<grid, 256, 0, st>>>(U, (double*)Uq, dm.fo_list, dm.fo_n,
+                                                           dm.n_pad);
+  };
+  if (dm.nq == 2)
+    go(std::integral_constant<int, 2>{});
+  else
+    go(std::integral_constant<int, 3>{});
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layer_vjp(const DeviceMesh& dm, double* Uq_bar, double* ubd, cudaStream_t st) {
+  if (!dm.fo_n) return cudaSuccess;
+  const unsigned grid = (unsigned)((dm.fo_n * 3 + 255) / 256);
+  const bool pairs = dm.precision == TENO_FP64;
+  if (dm.nq == 2) {
+    if (pairs)
+      layer_vjp_kernel<2, true><<<grid, 256, 0, st>>>(Uq_bar, ubd, dm.fo_list, dm.fo_n);
+    else
+      layer_vjp_kernel<2, false><<<grid, 256, 0, st>>>(Uq_bar, ubd, dm.fo_list, dm.fo_n);
+  } else {
+    if (pairs)
+      layer_vjp_kernel<3, true><<<grid, 256, 0, st>>>(Uq_bar, ubd, dm.fo_list, dm.fo_n);
+    else
+      layer_vjp_kernel<3, false><<<grid, 256, 0, st>>>(Uq_bar, ubd, dm.fo_list, dm.fo_n);
   }
   return cudaGetLastError();
 }
@@ -4153,17 +4206,13 @@ cudaError_t launch_axpby(double* out, const double* a, double ca, const double* 
 #endif
 constexpr int kVjpDirs = TENO_VJP_DIRS;
 
-cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const double* U, const void* Uq,
-                                 const double* w, double* Uq_bar, double* ubd, double time,
-                                 cudaStream_t st) {
+cudaError_t launch_face_flux_vjp(const DeviceMesh& dm, const void* Uq, const double* w,
+                                 double* Uq_bar, double time, cudaStream_t st) {
   VjpArgs a;
   a.f_cells = dm.f_cells;
   a.f_edges = dm.f_edges;
   a.f_geom = dm.f_geom;
   a.f_geom2 = dm.f_geom2;
-  a.U = U;
-  a.fo = dm.fo;
-  a.ubd = ubd;
   a.g2 = split2(dm.gamma);
   a.gm12 = split2(dm.gamma - 1.0);
   a.inv_area = dm.inv_area;
