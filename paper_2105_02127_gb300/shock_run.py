@@ -2,19 +2,21 @@
 
 The Mach-10 shock at 60 degrees to a reflecting wall on [0,4]x[0,1], run to
 t = 0.2 with TENO (default TENO6), HLLC, SSP-RK3 at CFL 0.4 and the
-positivity scaling of the reconstruction, in FP64 (the double-float path)
-and FP32-mixed.  At sampled steps of the FP64 run the selections of the FP64
-and FP32-mixed paths are evaluated on the same stage input states (U^n,
-U^(1), U^(2)); their flip rate per stage is the fraction of (cell, variable)
-selections that differ.  At the same steps of both runs the largest
+positivity scaling of the reconstruction, in FP64 (the double-float path),
+FP32-mixed and, when asked for, FP64 on the FP64 pipe (leg fp64_native).  At
+sampled steps of the double-float run the selections of the FP64 and
+FP32-mixed paths are evaluated on the same stage input states (U^n, U^(1),
+U^(2)); their flip rate per stage is the fraction of (cell, variable)
+selections that differ.  At the same steps of every run the largest
 deviation from the pre-shock state ahead of the incident shock (more than
-0.05 ahead of its exact position and above y = 0.5, clear of the Mach
-stem: there the exact solution is that state)
-is recorded with its location.  Prints one JSON object.
+0.05 ahead of its exact position and above y = 0.5, clear of the Mach stem:
+there the exact solution is that state) is recorded with its location.
+Prints one JSON object.
 
   python -m paper_2105_02127_gb300.shock_run [--nx 2048] [--ny 512] [--order 6]
                                              [--t-end 0.2] [--sample-every 50] [--cfl 0.4]
-                                             [--legs fp64_pairs,fp32_mixed] [--dump PREFIX]
+                                             [--legs fp64_pairs,fp32_mixed,fp64_native]
+                                             [--dump PREFIX]
 """
 from __future__ import annotations
 
@@ -71,7 +73,8 @@ def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int
         return float((sels[0] != sels[1]).double().mean().item())
 
     rho64 = None
-    for name, precision in (("fp64_pairs", teno.FP64), ("fp32_mixed", teno.FP32_MIXED)):
+    for name, precision in (("fp64_pairs", teno.FP64), ("fp32_mixed", teno.FP32_MIXED),
+                            ("fp64_native", teno.FP64_NATIVE)):
         if name not in legs:
             continue
         t = ctx(precision)
@@ -130,7 +133,7 @@ def run(nx: int, ny: int, order: int, t_end: float, sample_every: int, flux: int
         if name == "fp64_pairs":
             rho64 = rho.copy()
         elif rho64 is not None:
-            rec["mean_abs_rho_diff_vs_fp64_over_mean_rho"] = float(
+            rec["mean_abs_rho_diff_vs_fp64_pairs_over_mean_rho"] = float(
                 np.abs(rho - rho64).mean() / np.abs(rho64).mean())
         out[name] = rec
         t.close()
