@@ -92,7 +92,9 @@ def parse():
                     help="quads per side, 2 n^2 triangles (shear 2048, vortex 512)")
     ap.add_argument("--order", type=int, default=None, help="TENO order (shear 6, vortex 5)")
     ap.add_argument("--extras", default="pairs,mixed,adjoint,cweno,e2e,cpu",
-                    help="comma list of extra legs: pairs, mixed, adjoint, cweno, e2e, cpu")
+                    help="comma list of extra legs: pairs, mixed, adjoint, cweno, e2e, cpu, "
+                         "charvar (characteristic-variable TENO on the pair path; not in the "
+                         "default list)")
     ap.add_argument("--no-extras", action="store_true", help="the primary line only")
     ap.add_argument("--primary", default="native", choices=["native", "pairs", "mixed"],
                     help="path timed as the primary line: native FP64 (default), the "
@@ -301,8 +303,9 @@ def run_ours(args):
 
     def make(path, scheme="teno"):
         t = teno.Teno(device=dev, stream=stream).load(mesh)
+        kw = {"charvar": 1} if scheme == "charvar" else {"scheme": scheme}
         t.precompute_stencils(order=args.order, n_var=4, flux=teno.FLUX_HLL,
-                              precision=code[path], scheme=scheme)
+                              precision=code[path], **kw)
         t.set_state(Ud)
         return t
 
@@ -312,8 +315,10 @@ def run_ours(args):
         if path == "native":
             kernel = f"recon_tma_w_kernel <fp64 native> order {args.order}"
         elif path == "pairs":
-            kernel = (f"recon_tma_w_kernel <fp64 pairs> order {args.order}" if scheme == "teno"
-                      else f"recon_tma_kernel <fp64 pairs, CWENO> order {args.order}")
+            kernel = {"teno": f"recon_tma_w_kernel <fp64 pairs> order {args.order}",
+                      "cweno": f"recon_tma_kernel <fp64 pairs, CWENO> order {args.order}",
+                      "charvar": f"recon_tma_kernel <fp64 pairs, coefficients> + "
+                                 f"char_finish_kernel order {args.order}"}[scheme]
         else:
             kernel = f"recon_tma_kernel <fp32_mixed> order {args.order}"
         traffic = ncu_traffic(key[path], args.order, n_cell) if scheme == "teno" else None
@@ -462,6 +467,9 @@ def run_ours(args):
     cweno = None
     if "cweno" in ex:
         cweno = leg("pairs", scheme="cweno", steps=max(2, args.steps // 4))
+    charvar = None
+    if "charvar" in ex:
+        charvar = leg("pairs", scheme="charvar", steps=max(2, args.steps // 4))
     # selection flips against the FP64 path on the same (initial) state
     ref = legs.get("native", legs[args.primary])["_sel"]
     for r in list(legs.values()) + ([cweno] if cweno else []):
@@ -494,6 +502,12 @@ def run_ours(args):
         cweno["scheme"] = "CWENO, d'_K = 1e4, eps = 1e-14"
         cweno["cweno_over_teno_time"] = cweno["ms_per_step"] / legs["pairs"]["ms_per_step"] \
             if "pairs" in legs else None
+    if charvar:
+        # selections are per edge and field in this mode (the residual reports 8)
+        # and the oracle legs above reconstruct conservative variables
+        charvar["scheme"] = "TENO in characteristic variables per edge"
+        charvar["charvar_over_teno_time"] = \
+            charvar["ms_per_step"] / legs["pairs"]["ms_per_step"] if "pairs" in legs else None
 
     def public(r):
         return {k: v for k, v in r.items() if not k.startswith("_") and k not in ("e2e",)}
@@ -532,6 +546,8 @@ def run_ours(args):
             line["adjoint"] = main["adjoint"]
         if cweno:
             line["cweno"] = public(cweno)
+        if charvar:
+            line["charvar"] = public(charvar)
         if "e2e" in main:
             line["e2e"] = main["e2e"]
         if cpu is not None:

@@ -2513,6 +2513,11 @@ __global__ void __launch_bounds__(128) char_finish_kernel(
   }
   const int present = smask[c];
   const double* cv = coef + c * 4 * C;
+  // coefficient l of characteristic field i (recomputed where it is needed:
+  // holding a field's C coefficients, and the full L and R, spilled)
+  auto chc = [&](int i, int l) {
+    return L[i][0] * cv[l] + L[i][1] * cv[C + l] + L[i][2] * cv[2 * C + l] + L[i][3] * cv[3 * C + l];
+  };
   double corr[4][NQ];
 #pragma unroll
   for (int v = 0; v < 4; ++v)
@@ -2520,51 +2525,60 @@ __global__ void __launch_bounds__(128) char_finish_kernel(
     for (int q = 0; q < NQ; ++q) corr[v][q] = 0.0;
 #pragma unroll 1
   for (int i = 0; i < 4; ++i) {
-    double ch[C];
-#pragma unroll
-    for (int l = 0; l < C; ++l)
-      ch[l] = L[i][0] * cv[l] + L[i][1] * cv[C + l] + L[i][2] * cv[2 * C + l] +
-              L[i][3] * cv[3 * C + l];
     uint8_t sel = 8;
     if (!linear) {
       double beta[kSmallK + 1];
       double b = 0.0;
-#pragma unroll
-      for (int l = 0; l < M; ++l) b = fma(ch[l], ch[l], b);
+#pragma unroll 4
+      for (int l = 0; l < M; ++l) {
+        const double x = chc(i, l);
+        b = fma(x, x, b);
+      }
       beta[kSmallK] = b;
 #pragma unroll
       for (int k = 0; k < kSmallK; ++k) {
         double bq = 0.0;
 #pragma unroll
-        for (int l = 0; l < kSmallM; ++l) bq = fma(ch[M + k * kSmallM + l], ch[M + k * kSmallM + l], bq);
+        for (int l = 0; l < kSmallM; ++l) {
+          const double x = chc(i, M + k * kSmallM + l);
+          bq = fma(x, x, bq);
+        }
         beta[k] = bq;
       }
       sel = select_fp64(beta, present, ct, eps);
     }
-    double cfin[M];
-    if (sel & 8) {
+    double gq[NQ];
 #pragma unroll
-      for (int l = 0; l < M; ++l) cfin[l] = ch[l];
+    for (int q = 0; q < NQ; ++q) gq[q] = 0.0;
+    if (sel & 8) {
+#pragma unroll 4
+      for (int l = 0; l < M; ++l) {
+        const double x = chc(i, l);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) gq[q] = fma(x, ev.psi[(e * NQ + q) * kMaxM + l], gq[q]);
+      }
     } else {
+      // equal weights over the kept directional quadratics (kSmallM terms)
       const int nd = (sel & 1) + ((sel >> 1) & 1) + ((sel >> 2) & 1);
       const double w = nd ? 1.0 / nd : 0.0;
+      double cfin[kSmallM];
 #pragma unroll
-      for (int l = 0; l < M; ++l) cfin[l] = 0.0;
+      for (int l = 0; l < kSmallM; ++l) cfin[l] = 0.0;
 #pragma unroll
       for (int k = 0; k < kSmallK; ++k) {
         if (!((sel >> k) & 1)) continue;
 #pragma unroll
-        for (int l = 0; l < kSmallM; ++l) cfin[l] = fma(w, ch[M + k * kSmallM + l], cfin[l]);
+        for (int l = 0; l < kSmallM; ++l) cfin[l] = fma(w, chc(i, M + k * kSmallM + l), cfin[l]);
       }
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) gq[q] = fma(cfin[l], ev.psi[(e * NQ + q) * kMaxM + l], gq[q]);
     }
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      double gq = 0.0;
+    for (int q = 0; q < NQ; ++q)
 #pragma unroll
-      for (int l = 0; l < M; ++l) gq = fma(cfin[l], ev.psi[(e * NQ + q) * kMaxM + l], gq);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) corr[v][q] = fma(R[v][i], gq, corr[v][q]);
-    }
+      for (int v = 0; v < 4; ++v) corr[v][q] = fma(R[v][i], gq[q], corr[v][q]);
   }
   TQ* out = Uq + ((int64_t)(c * 3 + e) * NQ) * 4;
 #pragma unroll
