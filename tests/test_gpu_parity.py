@@ -472,6 +472,37 @@ def test_boundary_conditions_residual(T, oracle_mod, order, flux):
     assert rel(v, vo) <= 1e-10
 
 
+@pytest.mark.parametrize("precision", [0, 2, 1], ids=["pairs", "native", "mixed"])
+@pytest.mark.parametrize("flux", [2, 1], ids=["hllc", "hll"])
+def test_outflow_layer_quiescent_gas(T, oracle_mod, precision, flux):
+    """Seeded noise of 1e-8 on a gas at rest in the unit square (TENO6, 512
+    cells, outflow on the right, walls elsewhere) stays at its level over 400
+    SSP-RK3 steps at the device CFL step: the outflow layer enters every face
+    flux with its cell average (on its high-order one-sided polynomials the
+    oracle's noise grew about 20-fold per 100 steps).  The first residual
+    matches the oracle's (1e-11 of the field's largest term on the FP64 paths,
+    where the residual of a gas at rest is its rounding: a small absolute
+    bound), and FP32-mixed stays within its own rounding noise."""
+    def tag(side, s):
+        return inputs.BC_OUTFLOW if side == "right" else inputs.BC_WALL
+    mesh = inputs.jittered_mesh(16, 16, 1.0, 1.0, seed=77, periodic=False, bc_tagger=tag)
+    U0 = np.zeros((4, mesh.n_cell))
+    U0[0], U0[3] = 1.4, 2.5
+    U = U0 + 1e-8 * np.random.default_rng(5).standard_normal(U0.shape)
+    t = _setup(T, mesh, 6, 4, flux, precision)
+    t.set_state(U)
+    R, _ = t.residual()
+    Ro, _, _ = oracle_mod.Oracle(mesh, order=6, n_var=4, flux=flux).residual(U)
+    if precision != 1:
+        assert np.abs(R - Ro).max() <= 1e-11 * max(np.abs(Ro).max(), 1.0)
+    t.rk3_steps(400, 0.0)
+    t.check_state()
+    Uf = t.get_state()
+    dev0 = np.abs(U - U0).max()
+    bound = 2.0 * dev0 if precision != 1 else 1e-4
+    assert np.isfinite(Uf).all() and np.abs(Uf - U0).max() < bound
+
+
 @pytest.mark.parametrize("precision", [0, 2], ids=["pairs", "native"])
 @pytest.mark.parametrize("order", [3, 4, 5, 6])
 def test_w_form_forced_fallback(T, oracle_mod, order, precision):
