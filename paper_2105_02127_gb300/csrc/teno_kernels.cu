@@ -786,18 +786,36 @@ struct ReconArgs {
 };
 
 // characteristic mode: store the cell's large and directional coefficients of
-// variable v in FP64 for char_finish_kernel, in place of selection and
-// evaluation
+// variable v for the characteristic finish, in place of selection and
+// evaluation: FP64 on the native path, (hi, lo) FP32 pairs on the pair and
+// mixed paths (whose finish runs in pair arithmetic on the FP32 pipe)
 template <int M, typename TC>
 __device__ __forceinline__ void store_coefs(const ReconArgs& a, int64_t c, int v, const TC* acc,
                                             const TC (&as)[kSmallK][kSmallM]) {
-  double* o = a.coef_out + ((int64_t)c * 4 + v) * (M + kSmallK * kSmallM);
+  const int64_t base = ((int64_t)c * 4 + v) * (M + kSmallK * kSmallM);
+  if constexpr (std::is_same<TC, double>::value) {
+    double* o = a.coef_out + base;
 #pragma unroll
-  for (int l = 0; l < M; ++l) o[l] = to_d(acc[l]);
+    for (int l = 0; l < M; ++l) o[l] = acc[l];
 #pragma unroll
-  for (int k = 0; k < kSmallK; ++k)
+    for (int k = 0; k < kSmallK; ++k)
 #pragma unroll
-    for (int l = 0; l < kSmallM; ++l) o[M + k * kSmallM + l] = to_d(as[k][l]);
+      for (int l = 0; l < kSmallM; ++l) o[M + k * kSmallM + l] = as[k][l];
+  } else {
+    float2* o = reinterpret_cast<float2*>(a.coef_out) + base;
+    auto pr = [](const TC& x) {
+      if constexpr (std::is_same<TC, DF>::value)
+        return make_float2(x.h, x.l);
+      else
+        return make_float2(x, 0.f);
+    };
+#pragma unroll
+    for (int l = 0; l < M; ++l) o[l] = pr(acc[l]);
+#pragma unroll
+    for (int k = 0; k < kSmallK; ++k)
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) o[M + k * kSmallM + l] = pr(as[k][l]);
+  }
   if (a.sel_out) a.sel_out[(int64_t)v * a.n_pad + c] = 8;
 }
 
@@ -2587,6 +2605,161 @@ __global__ void __launch_bounds__(128) char_finish_kernel(
     for (int v = 0; v < 4; ++v) out[q * 4 + v] = from_d<TQ>(W[v] + corr[v][q]);
 }
 
+// The characteristic finish of the pair and mixed paths in pair arithmetic
+// on the FP32 pipe (the FP64 version above is FP64-pipe bound): the same
+// steps, from the (hi, lo) coefficients the reconstruction wrote.  The
+// selection is screened in FP32 with the guard band of the pair path and
+// decided in FP64 inside it; the Gauss values are written as pairs (pair
+// path) or FP32 (mixed path).
+template <int M, int NQ, typename TQ>
+__global__ void __launch_bounds__(128) char_finish_df_kernel(
+    const float2* __restrict__ coef, const double* __restrict__ U,
+    const uint8_t* __restrict__ smask, const int32_t* __restrict__ c_faces,
+    const double* __restrict__ f_geom, const DFTable ev, TQ* __restrict__ Uq, int64_t n_cell,
+    int64_t n_pad, double g, double ct, double eps, int linear) {
+  constexpr int C = M + kSmallK * kSmallM;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_cell * 3) return;
+  const int64_t c = idx / 3;
+  const int e = (int)(idx % 3);
+  const int cf = c_faces[3 * c + e];
+  const int64_t f = cf >> 1;
+  const double sg = (cf & 1) ? -1.0 : 1.0;  // the neighbour's normal is the opposite one
+  const DF nx = cst<DF>(sg * f_geom[5 * f]), ny = cst<DF>(sg * f_geom[5 * f + 1]);
+  const DF one = {1.f, 0.f}, half = {0.5f, 0.f}, zero = {0.f, 0.f};
+  const DF gm1 = cst<DF>(g - 1.0), gg = cst<DF>(g);
+  DF W[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) W[v] = cst<DF>(U[(int64_t)v * n_pad + c]);
+  // eigenvectors at the cell average, in the edge frame, then rotated
+  const DF ir = one / W[0];
+  const DF un = (W[1] * nx + W[2] * ny) * ir, ut = (W[2] * nx - W[1] * ny) * ir;
+  const DF q2 = un * un + ut * ut;
+  const DF p = gm1 * (W[3] - half * W[0] * q2);
+  const DF cs = tsqrt(gg * p * ir), ics = one / cs, H = (W[3] + p) * ir;
+  const DF b1 = gm1 * ics * ics, b2 = half * b1 * q2;
+  const DF Lf[4][4] = {{half * (b2 + un * ics), half * (-(b1 * un) - ics), -(half * b1 * ut), half * b1},
+                       {one - b2, b1 * un, b1 * ut, -b1},
+                       {-ut, zero, one, zero},
+                       {half * (b2 - un * ics), half * (-(b1 * un) + ics), -(half * b1 * ut), half * b1}};
+  const DF Rf[4][4] = {{one, one, zero, one},
+                       {un - cs, un, zero, un + cs},
+                       {ut, ut, one, ut},
+                       {H - un * cs, half * q2, ut, H + un * cs}};
+  DF L[4][4], R[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    L[i][0] = Lf[i][0];
+    L[i][1] = Lf[i][1] * nx - Lf[i][2] * ny;
+    L[i][2] = Lf[i][1] * ny + Lf[i][2] * nx;
+    L[i][3] = Lf[i][3];
+    R[0][i] = Rf[0][i];
+    R[1][i] = nx * Rf[1][i] - ny * Rf[2][i];
+    R[2][i] = ny * Rf[1][i] + nx * Rf[2][i];
+    R[3][i] = Rf[3][i];
+  }
+  const int present = smask[c];
+  const float2* cv = coef + c * 4 * C;
+  auto cp = [&](int j) { const float2 x = cv[j]; return DF{x.x, x.y}; };
+  // coefficient l of characteristic field i (recomputed where it is needed)
+  auto chc = [&](int i, int l) {
+    return ((L[i][0] * cp(l) + L[i][1] * cp(C + l)) + L[i][2] * cp(2 * C + l)) +
+           L[i][3] * cp(3 * C + l);
+  };
+  DF corr[4][NQ];
+#pragma unroll
+  for (int v = 0; v < 4; ++v)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) corr[v][q] = zero;
+#pragma unroll 1
+  for (int i = 0; i < 4; ++i) {
+    uint8_t sel = 8;
+    if (!linear) {
+      DF bt[kSmallK + 1];
+      {
+        DF b = zero;
+#pragma unroll 4
+        for (int l = 0; l < M; ++l) {
+          const DF x = chc(i, l);
+          df_mac(b, make_float2(x.h, x.l), x);
+        }
+        bt[kSmallK] = df_norm(b);
+#pragma unroll
+        for (int k = 0; k < kSmallK; ++k) {
+          DF q = zero;
+#pragma unroll
+          for (int l = 0; l < kSmallM; ++l) {
+            const DF x = chc(i, M + k * kSmallM + l);
+            df_mac(q, make_float2(x.h, x.l), x);
+          }
+          bt[k] = df_norm(q);
+        }
+      }
+      float t[kSmallK + 1];
+#pragma unroll
+      for (int k = 0; k <= kSmallK; ++k) t[k] = bt[k].h + (float)eps;
+      bool near = false;
+      if (chi_keep32(t, kSmallK, present | 8, (float)ct, &near)) {
+        sel = 8;
+      } else {
+        sel = 0;
+#pragma unroll
+        for (int k = 0; k < kSmallK; ++k)
+          if (((present >> k) & 1) && chi_keep32(t, k, present & 7, (float)ct, &near))
+            sel |= (uint8_t)(1u << k);
+      }
+      if (near) {
+        double beta[kSmallK + 1];
+#pragma unroll
+        for (int k = 0; k <= kSmallK; ++k) beta[k] = df_to_double(bt[k]);
+        sel = select_fp64(beta, present, ct, eps);
+      }
+    }
+    DF gq[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) gq[q] = zero;
+    if (sel & 8) {
+#pragma unroll 4
+      for (int l = 0; l < M; ++l) {
+        const DF x = chc(i, l);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) df_mac(gq[q], ev.psi[(e * NQ + q) * kMaxM + l], x);
+      }
+    } else {
+      // equal weights over the kept directional quadratics (kSmallM terms)
+      const int nd = (sel & 1) + ((sel >> 1) & 1) + ((sel >> 2) & 1);
+      const DF fn = {(float)(nd ? nd : 1), 0.f};
+#pragma unroll
+      for (int l = 0; l < kSmallM; ++l) {
+        DF sum = zero;
+#pragma unroll
+        for (int k = 0; k < kSmallK; ++k)
+          if ((sel >> k) & 1) sum = sum + chc(i, M + k * kSmallM + l);
+        const DF x = nd ? sum / fn : zero;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) df_mac(gq[q], ev.psi[(e * NQ + q) * kMaxM + l], x);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const DF gn = df_norm(gq[q]);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) corr[v][q] = corr[v][q] + R[v][i] * gn;
+    }
+  }
+  TQ* out = Uq + ((int64_t)(c * 3 + e) * NQ) * 4;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const DF r = W[v] + corr[v][q];
+      if constexpr (std::is_same<TQ, DF>::value)
+        out[q * 4 + v] = r;
+      else
+        out[q * 4 + v] = r.h;
+    }
+}
+
 // FP32 hi/lo split of a state: hi = fl32(U), lo = fl32(U - hi)
 // Positivity scaling of the reconstruction (Euler; an option, not in the
 // paper, which reports its schemes robust on the Mach-10 shock case without
@@ -3900,9 +4073,14 @@ cudaError_t launch_char_finish(const DeviceMesh& dm, const double* U, void* Uq, 
     if (dm.nq != NQ) return cudaErrorInvalidValue;
     auto go = [&](auto tq) -> cudaError_t {
       using TQ = typename decltype(tq)::type;
-      char_finish_kernel<M, NQ, TQ><<<grid, 128, 0, st>>>(
-          dm.coef_out, U, dm.smask, dm.c_faces, dm.f_geom, dm.eval, (TQ*)Uq, dm.n_recon, dm.n_pad,
-          dm.gamma, dm.ct, dm.eps, dm.linear);
+      if constexpr (std::is_same<TQ, double>::value)
+        char_finish_kernel<M, NQ, TQ><<<grid, 128, 0, st>>>(
+            dm.coef_out, U, dm.smask, dm.c_faces, dm.f_geom, dm.eval, (TQ*)Uq, dm.n_recon,
+            dm.n_pad, dm.gamma, dm.ct, dm.eps, dm.linear);
+      else
+        char_finish_df_kernel<M, NQ, TQ><<<grid, 128, 0, st>>>(
+            reinterpret_cast<const float2*>(dm.coef_out), U, dm.smask, dm.c_faces, dm.f_geom,
+            dm.eval_df, (TQ*)Uq, dm.n_recon, dm.n_pad, dm.gamma, dm.ct, dm.eps, dm.linear);
       return cudaGetLastError();
     };
     if (dm.precision == TENO_FP64) return go(TypeTag<DF>{});
