@@ -50,6 +50,13 @@ enum teno_status {
   TENO_ESTATE = -8    /* calls made in the wrong order */
 };
 
+/* Numerical fluxes (Sec. 4): upwind (scalar advection), HLL with the Einfeldt
+ * wave speeds of Eq. wavespeed (the Roe sound speed with both velocity
+ * components), HLLC (cited in Sec. 5) with Toro's contact speed and star
+ * states on the same bounds.  The side sound speeds take a negative pressure
+ * as zero (a Gauss state at the positivity floor can round below it); where
+ * HLLC's contact speed is 0/0 (zero sound speed on both sides) the flux is
+ * HLL's. */
 enum teno_flux { TENO_FLUX_UPWIND = 0, TENO_FLUX_HLL = 1, TENO_FLUX_HLLC = 2 };
 /* TENO_FP64: FP64-accurate path -- matvecs, smoothness indicators and Gauss
  *   evaluation in double-float (pairs of FP32 numbers, ~48 significant bits)
@@ -61,7 +68,14 @@ enum teno_flux { TENO_FLUX_UPWIND = 0, TENO_FLUX_HLL = 1, TENO_FLUX_HLLC = 2 };
  * TENO_FP64_NATIVE: everything in FP64 on the FP64 pipe. */
 enum teno_precision { TENO_FP64 = 0, TENO_FP32_MIXED = 1, TENO_FP64_NATIVE = 2 };
 
-/* Boundary tags of non-periodic meshes (bface[:,2]). */
+/* Boundary tags of non-periodic meshes (bface[:,2]); the ghost state at each
+ * boundary Gauss point of the shock case (Sec. 5, double Mach reflection):
+ * WALL mirrors the normal momentum; INFLOW is the post-shock state; OUTFLOW
+ * copies the inner state, and a cell with an outflow face enters every face
+ * flux with its cell average (first order in that cell layer: on its one-sided
+ * high-order polynomial the boundary closure has a growing mode); TOP is the
+ * post- or pre-shock state on either side of the exact shock trace at the
+ * call's time (teno_set_time). */
 enum teno_bc { TENO_BC_WALL = 1, TENO_BC_INFLOW = 2, TENO_BC_OUTFLOW = 3, TENO_BC_TOP = 4 };
 
 /* Scheme options.  Defaults (teno_default_params) follow the paper:
