@@ -2841,16 +2841,16 @@ __global__ void __launch_bounds__(128) positivity_kernel(const double* __restric
 // face flux with its cell average: after the reconstruction, each Gauss slot
 // of such a cell takes U_0 (in the Gauss-value type of the path).  One thread
 // per (layer cell, slot).
-template <int NQ3, typename TQ>
+template <int NV, int NQ3, typename TQ>
 __global__ void layer_fill_kernel(const double* __restrict__ U, TQ* __restrict__ Uq,
                                   const int32_t* __restrict__ list, int64_t n, int64_t n_pad) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * NQ3) return;
   const int64_t c = list[i / NQ3];
   const int p = (int)(i % NQ3);
-  TQ* o = Uq + (c * NQ3 + p) * 4;
+  TQ* o = Uq + (c * NQ3 + p) * NV;
 #pragma unroll
-  for (int v = 0; v < 4; ++v) o[v] = from_d<TQ>(U[v * n_pad + c]);
+  for (int v = 0; v < NV; ++v) o[v] = from_d<TQ>(U[v * n_pad + c]);
 }
 
 // Adjoint of layer_fill_kernel: a layer cell's Gauss-slot cotangents (pairs
@@ -2858,19 +2858,21 @@ __global__ void layer_fill_kernel(const double* __restrict__ U, TQ* __restrict__
 // into ubd[cell][edge][var] (added to the cell's adjoint by the reverse
 // gather), and the slots are cleared so that the reconstruction's adjoint
 // sends nothing through the cell's polynomial.  One thread per (cell, edge).
-template <int NQ, bool kPairs>
+template <int NV, int NQ, bool kPairs>
 __global__ void layer_vjp_kernel(double* __restrict__ Uq_bar, double* __restrict__ ubd,
                                  const int32_t* __restrict__ list, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * 3) return;
   const int64_t c = list[i / 3];
   const int e = (int)(i % 3);
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  const int64_t b = ((c * 3 + e) * NQ) * 4;
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  const int64_t b = ((c * 3 + e) * NQ) * NV;
   for (int q = 0; q < NQ; ++q)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int64_t j = b + q * 4 + v;
+    for (int v = 0; v < NV; ++v) {
+      const int64_t j = b + q * NV + v;
       if constexpr (kPairs) {
         float2* u = reinterpret_cast<float2*>(Uq_bar) + j;
         acc[v] += (double)u->x + (double)u->y;
@@ -2881,7 +2883,7 @@ __global__ void layer_vjp_kernel(double* __restrict__ Uq_bar, double* __restrict
       }
     }
 #pragma unroll
-  for (int v = 0; v < 4; ++v) ubd[(c * 3 + e) * 4 + v] = acc[v];
+  for (int v = 0; v < NV; ++v) ubd[(c * 3 + e) * NV + v] = acc[v];
 }
 
 // Halo exchange of partitioned meshes (copy-based; each kernel touches only
@@ -4264,21 +4266,27 @@ cudaError_t launch_layer_fill(const DeviceMesh& dm, const double* U, void* Uq, c
   if (!dm.fo_n) return cudaSuccess;
   const int64_t nt = dm.fo_n * 3 * dm.nq;
   const unsigned grid = (unsigned)((nt + 255) / 256);
-  auto go = [&](auto nqc) {
-    constexpr int NQ3 = 3 * decltype(nqc)::value;
+  auto go = [&](auto nvc, auto nqc) {
+    constexpr int NV = decltype(nvc)::value, NQ3 = 3 * decltype(nqc)::value;
     if (dm.precision == TENO_FP64)
-      layer_fill_kernel<NQ3, DF><<<grid, 256, 0, st>>>(U, (DF*)Uq, dm.fo_list, dm.fo_n, dm.n_pad);
+      layer_fill_kernel<NV, NQ3, DF><<<grid, 256, 0, st>>>(U, (DF*)Uq, dm.fo_list, dm.fo_n,
+                                                            dm.n_pad);
     else if (dm.precision == TENO_FP32_MIXED)
-      layer_fill_kernel<NQ3, float><<<grid, 256, 0, st>>>(U, (float*)Uq, dm.fo_list, dm.fo_n,
-                                                          dm.n_pad);
+      layer_fill_kernel<NV, NQ3, float><<<grid, 256, 0, st>>>(U, (float*)Uq, dm.fo_list,
+                                                              dm.fo_n, dm.n_pad);
     else
-      layer_fill_kernel<NQ3, double><<<grid, 256, 0, st>>>(U, (double*)Uq, dm.fo_list, dm.fo_n,
-                                                           dm.n_pad);
+      layer_fill_kernel<NV, NQ3, double><<<grid, 256, 0, st>>>(U, (double*)Uq, dm.fo_list,
+                                                               dm.fo_n, dm.n_pad);
   };
-  if (dm.nq == 2)
-    go(std::integral_constant<int, 2>{});
-  else
-    go(std::integral_constant<int, 3>{});
+  using I1 = std::integral_constant<int, 1>;
+  using I4 = std::integral_constant<int, 4>;
+  using Q2 = std::integral_constant<int, 2>;
+  using Q3 = std::integral_constant<int, 3>;
+  if (dm.n_var == 1) {
+    if (dm.nq == 2) go(I1{}, Q2{}); else go(I1{}, Q3{});
+  } else {
+    if (dm.nq == 2) go(I4{}, Q2{}); else go(I4{}, Q3{});
+  }
   return cudaGetLastError();
 }
 
@@ -4286,16 +4294,21 @@ cudaError_t launch_layer_vjp(const DeviceMesh& dm, double* Uq_bar, double* ubd, 
   if (!dm.fo_n) return cudaSuccess;
   const unsigned grid = (unsigned)((dm.fo_n * 3 + 255) / 256);
   const bool pairs = dm.precision == TENO_FP64;
-  if (dm.nq == 2) {
+  auto go = [&](auto nvc, auto nqc) {
+    constexpr int NV = decltype(nvc)::value, NQ = decltype(nqc)::value;
     if (pairs)
-      layer_vjp_kernel<2, true><<<grid, 256, 0, st>>>(Uq_bar, ubd, dm.fo_list, dm.fo_n);
+      layer_vjp_kernel<NV, NQ, true><<<grid, 256, 0, st>>>(Uq_bar, ubd, dm.fo_list, dm.fo_n);
     else
-      layer_vjp_kernel<2, false><<<grid, 256, 0, st>>>(Uq_bar, ubd, dm.fo_list, dm.fo_n);
+      layer_vjp_kernel<NV, NQ, false><<<grid, 256, 0, st>>>(Uq_bar, ubd, dm.fo_list, dm.fo_n);
+  };
+  using I1 = std::integral_constant<int, 1>;
+  using I4 = std::integral_constant<int, 4>;
+  using Q2 = std::integral_constant<int, 2>;
+  using Q3 = std::integral_constant<int, 3>;
+  if (dm.n_var == 1) {
+    if (dm.nq == 2) go(I1{}, Q2{}); else go(I1{}, Q3{});
   } else {
-    if (pairs)
-      layer_vjp_kernel<3, true><<<grid, 256, 0, st>>>(Uq_bar, ubd, dm.fo_list, dm.fo_n);
-    else
-      layer_vjp_kernel<3, false><<<grid, 256, 0, st>>>(Uq_bar, ubd, dm.fo_list, dm.fo_n);
+    if (dm.nq == 2) go(I4{}, Q2{}); else go(I4{}, Q3{});
   }
   return cudaGetLastError();
 }

@@ -112,6 +112,13 @@ def test_errors(teno):
         small.precompute_stencils(order=6, n_var=1, flux=0)
     assert e.value.code == teno.TENO_ESTENCIL
     small.precompute_stencils(order=3, n_var=1, flux=0)  # the third-order stencils fit
+    # boundary conditions are Euler ghost states: a scalar precompute on a
+    # bounded mesh is refused
+    mbd = inputs.jittered_mesh(16, 8, 4.0, 1.0, seed=1003, periodic=False,
+                               bc_tagger=inputs.dmr_bc_tagger)
+    with pytest.raises(teno.TenoError) as e:
+        teno.Teno(device=-1).load(mbd).precompute_stencils(order=3, n_var=1, flux=0)
+    assert e.value.code == teno.TENO_EINVAL
     # a boundary edge without a bface entry
     mb = inputs.jittered_mesh(6, 6, seed=3, periodic=False)
     with pytest.raises(teno.TenoError) as e:
