@@ -641,6 +641,10 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        # rank 0 alone runs the oracle: give it the host cores it has at N = 1
+        # (the launcher sets one OpenMP thread per rank by default)
+        os.environ["OMP_NUM_THREADS"] = str(os.cpu_count() or 1)
     from oracle import build as ob
     ob.build()
     from oracle.oracle import Oracle
