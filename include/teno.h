@@ -314,7 +314,9 @@ int teno_adjoint_step_tape(teno_ctx* ctx, int32_t slot, const double* lam_np1, d
 /* Values of the last reconstruction at the edge Gauss points (inspection
  * support): out host [n_cell][3][nq][n_var] in user cell order, edge e of a
  * cell running from its vertex e to vertex e+1, points in ascending order
- * along the edge.  Synchronises. */
+ * along the edge; the states the face fluxes took (after the positivity
+ * scaling, and the cell average for cells with an outflow face).
+ * Synchronises. */
 int teno_edge_values(teno_ctx* ctx, double* out);
 
 /* Kernel timing of this context (measurement support; no counterpart in the
