@@ -1160,6 +1160,35 @@ def test_outflow_layer_keeps_a_quiescent_gas_quiescent(oracle_mod, flux, bcs):
     assert np.isfinite(U).all() and np.abs(U - U0).max() < 2.0 * dev0
 
 
+@pytest.mark.parametrize("flux", [1, 2])
+def test_bounded_mesh_conservation(oracle_mod, flux):
+    """Discrete conservation on the shock-case boundaries with the outflow
+    layer: the residual's cell sum, sum_c |V_c| R_c, is minus the sum of the
+    boundary faces' fluxes (every interior face cancels between its two
+    cells), to rounding, at TENO3 and TENO6."""
+    mesh = inputs.jittered_mesh(24, 8, 4.0, 1.0, seed=1003, periodic=False,
+                                bc_tagger=inputs.dmr_bc_tagger)
+
+    def f(x, y):
+        return inputs.prim_to_cons(1.4 + 0.3 * np.sin(3 * x + 2 * y), 0.2 + 0.1 * np.cos(2 * y),
+                                   -0.1 + 0.05 * x, 1.0 + 0.2 * np.sin(x * y), 1.4)
+    U = inputs.cell_average(mesh, f)
+    for order in (3, 6):
+        o = oracle_mod.Oracle(mesh, order=order, n_var=4, flux=flux)
+        R, _, _ = o.residual(U, time=0.05)
+        area, _, fnbr = o.geometry()
+        total = (R * area).sum(axis=1)
+        bnd = np.zeros(4)
+        scale = 0.0
+        for c in range(mesh.n_cell):
+            for e in range(3):
+                if fnbr[c, e] < 0:
+                    K = o.face_flux(U, c, e, time=0.05)
+                    bnd += K
+                    scale = max(scale, np.abs(K).max())
+        np.testing.assert_allclose(total, -bnd, rtol=0, atol=1e-12 * max(scale, 1.0) * mesh.n_cell)
+
+
 def test_outflow_face_takes_the_cell_average(oracle_mod):
     """At an outflow face both states are the cell average (zero gradient of
     the cell averages): the face flux is |A| F(U_0).n exactly (HLL and HLLC are
